@@ -1,0 +1,210 @@
+"""Independent physics results used to pin the oracle (no oracle code used here).
+
+* e+e- -> mu+mu- via photon + Z: textbook helicity amplitudes for massless
+  fermions (Peskin & Schroeder Sec. 5.2; the Z adds a chiral coupling and a
+  Breit-Wigner propagator).
+* g g -> Q Q~: the Combridge (1979) formula as printed in Ellis, Stirling &
+  Webber, "QCD and collider physics", Ch. 10 (spin and colour averaged).
+* g g -> q q~ + n g, massless: colour-ordered Parke-Taylor amplitudes in the
+  spinor-helicity formalism (Mangano & Parke, Phys. Rept. 200 (1991) 301;
+  Dixon, TASI 1995 lectures, hep-ph/9601359) with the colour decomposition
+  into ordered products of generators, summed over colours with a colour
+  matrix computed here from its own Gell-Mann matrices.
+"""
+from __future__ import annotations
+
+import itertools
+import math
+
+import numpy as np
+
+
+def mdot(a, b):
+    return a[..., 0] * b[..., 0] - (a[..., 1:] * b[..., 1:]).sum(-1)
+
+
+# ----------------------------------------------------------------------------
+# e+ e- -> mu+ mu-
+# ----------------------------------------------------------------------------
+def ee_mumu_closed_form(p, mz, wz, sw2, alpha):
+    """(e^4/4) sum_{l,l'} |Q^2 + g_l g_l' s/(sW^2 cW^2 (s - mZ^2 + i mZ GZ))|^2 (1 + eta cos)^2."""
+    e2 = 4.0 * math.pi * alpha
+    cw2 = 1.0 - sw2
+    gl, gr = -0.5 + sw2, sw2
+    s = mdot(p[:, 0] + p[:, 1], p[:, 0] + p[:, 1])
+    n_e = p[:, 1, 1:] / np.linalg.norm(p[:, 1, 1:], axis=1)[:, None]
+    n_mu = p[:, 3, 1:] / np.linalg.norm(p[:, 3, 1:], axis=1)[:, None]
+    c = (n_e * n_mu).sum(1)
+    prop = s / (s - mz * mz + 1j * mz * wz)
+    tot = 0.0
+    for i, ge in enumerate((gl, gr)):
+        for j, gm in enumerate((gl, gr)):
+            eta = 1.0 if i == j else -1.0
+            tot = tot + np.abs(1.0 + ge * gm / (sw2 * cw2) * prop) ** 2 * (1.0 + eta * c) ** 2
+    return e2 * e2 / 4.0 * tot
+
+
+def qed_limit_closed_form(p, alpha):
+    """e^4 (1 + cos^2 theta): pure photon exchange (Peskin & Schroeder eq. 5.10)."""
+    e2 = 4.0 * math.pi * alpha
+    n_e = p[:, 1, 1:] / np.linalg.norm(p[:, 1, 1:], axis=1)[:, None]
+    n_mu = p[:, 3, 1:] / np.linalg.norm(p[:, 3, 1:], axis=1)[:, None]
+    c = (n_e * n_mu).sum(1)
+    return e2 * e2 * (1.0 + c * c)
+
+
+# ----------------------------------------------------------------------------
+# g g -> Q Q~ (Combridge)
+# ----------------------------------------------------------------------------
+def gg_qq_combridge(p, m, alphas):
+    """g_s^4 (1/(6 t1 t2) - 3/8)(t1^2 + t2^2 + rho - rho^2/(4 t1 t2)), t_i = 2 k_i.p_Q / s."""
+    gs2 = 4.0 * math.pi * alphas
+    k1, k2, pq = p[:, 0], p[:, 1], p[:, 2]
+    s = mdot(k1 + k2, k1 + k2)
+    t1 = 2.0 * mdot(k1, pq) / s
+    t2 = 2.0 * mdot(k2, pq) / s
+    rho = 4.0 * m * m / s
+    return gs2 * gs2 * (1.0 / (6.0 * t1 * t2) - 3.0 / 8.0) * (t1 * t1 + t2 * t2 + rho
+                                                              - rho * rho / (4.0 * t1 * t2))
+
+
+# ----------------------------------------------------------------------------
+# spinor helicity, Parke-Taylor
+# ----------------------------------------------------------------------------
+def _lam(k):
+    """Holomorphic and anti-holomorphic spinors of a massless momentum (needs k^+ > 0).
+
+    Negative-energy momenta (crossed incoming particles) use lambda(-k) times i;
+    the constant phase is common to all colour orderings and drops out of
+    the colour-summed |M|^2.
+    """
+    neg = k[..., 0] < 0
+    kk = np.where(neg[..., None], -k, k)
+    kp = kk[..., 0] + kk[..., 3]
+    sq = np.sqrt(kp)
+    lam = np.stack([sq + 0j, (kk[..., 1] + 1j * kk[..., 2]) / sq], axis=-1)
+    lamt = np.stack([sq + 0j, (kk[..., 1] - 1j * kk[..., 2]) / sq], axis=-1)
+    ph = np.where(neg, 1j, 1.0)
+    return lam * ph[..., None], lamt * ph[..., None]
+
+
+def _angle(li, lj):
+    return li[..., 0] * lj[..., 1] - li[..., 1] * lj[..., 0]
+
+
+def _t_matrices():
+    """Generators t^a = lambda^a/2 built from the su(3) basis (own construction)."""
+    t = []
+    for (i, j) in ((0, 1), (0, 2), (1, 2)):
+        s = np.zeros((3, 3), complex)
+        s[i, j] = s[j, i] = 0.5
+        a = np.zeros((3, 3), complex)
+        a[i, j] = -0.5j
+        a[j, i] = 0.5j
+        t += [s, a]
+    d3 = np.diag([0.5, -0.5, 0.0]).astype(complex)
+    d8 = np.diag([1.0, 1.0, -2.0]).astype(complex) / (2.0 * math.sqrt(3.0))
+    return np.array(t + [d3, d8])
+
+
+def flow_colour_matrix(ngl):
+    """C_{s,s'} = sum_colours conj((t^s1..t^sn)_{ij}) (t^s'1..t^s'n)_{ij} over orderings s."""
+    t = _t_matrices()
+    perms = list(itertools.permutations(range(ngl)))
+    words = []
+    for perm in perms:
+        # tensor over (a_1..a_n, i, j) of the ordered product t^{a_perm0} ... t^{a_perm(n-1)}
+        idx = [chr(ord("a") + g) for g in range(ngl)]
+        chain = ",".join(f"{idx[g]}{chr(ord('p') + k)}{chr(ord('p') + k + 1)}"
+                         for k, g in enumerate(perm))
+        out = "".join(idx) + "p" + chr(ord("p") + ngl)
+        words.append(np.einsum(chain + "->" + out, *([t] * ngl)).reshape(-1))
+    w = np.array(words)
+    return perms, (w.conj() @ w.T).real
+
+
+def parke_taylor_helicity(p, alphas, q_hel, qb_hel, gl_hel_out):
+    """Colour-summed |A|^2 (not averaged) for one all-outgoing helicity configuration.
+
+    p: [N, 4+n, 4] rows g g q q~ g...; gl_hel_out: outgoing-convention helicities
+    of the gluons in row order (an incoming gluon of helicity h is an outgoing
+    one of helicity -h).  Returns None when the configuration is neither MHV
+    nor anti-MHV (no Parke-Taylor formula); vanishing configurations give 0.
+    """
+    nev, npart, _ = p.shape
+    ngl = npart - 2
+    if q_hel == qb_hel:
+        return np.zeros(nev)          # helicity conserved along a massless quark line
+    nneg = sum(1 for h in gl_hel_out if h < 0)
+    if nneg in (0, ngl):
+        return np.zeros(nev)
+    if nneg == 1:
+        pick, special = 0, list(gl_hel_out).index(-1)   # MHV: angle brackets
+    elif nneg == ngl - 1:
+        pick, special = 1, list(gl_hel_out).index(1)    # anti-MHV: square brackets
+    else:
+        return None
+    out_mom = [-p[:, 0], -p[:, 1]] + [p[:, r] for r in range(4, npart)]
+    lq, lqb = _lam(p[:, 2]), _lam(p[:, 3])
+    lg = [_lam(k) for k in out_mom]
+    br = lambda a, b: _angle(a[pick], b[pick])
+    li = lg[special]
+    # MHV: A(qbar-, q+, .., i-, ..) ~ <qbar i>^3 <q i>;  A(qbar+, q-, ..) ~ <q i>^3 <qbar i>.
+    # anti-MHV is the parity conjugate (angle -> square, all helicities flipped).
+    qbar_minus_mhv = (qb_hel < 0) if pick == 0 else (qb_hel > 0)
+    if qbar_minus_mhv:
+        num = br(lqb, li) ** 3 * br(lq, li)
+    else:
+        num = br(lq, li) ** 3 * br(lqb, li)
+    perms, cmat = flow_colour_matrix(ngl)
+    amps = []
+    for perm in perms:
+        chain = [lqb, lq] + [lg[g] for g in perm]
+        den = np.ones(nev, complex)
+        for k in range(len(chain)):
+            den = den * br(chain[k], chain[(k + 1) % len(chain)])
+        amps.append(1j * num / den)
+    a = np.stack(amps, axis=1)
+    gs2 = 4.0 * math.pi * alphas
+    # T^a = sqrt(2) t^a in the colour decomposition: a factor 2 per generator in |M|^2
+    return np.real(np.einsum("ns,st,nt->n", a.conj(), cmat, a)) * gs2 ** ngl * 2.0 ** ngl
+
+
+def parke_taylor_me2(p, alphas):
+    """Colour-summed, averaged |M|^2 of g g -> q q~ + n g (n <= 1), massless quarks."""
+    nev, npart, _ = p.shape
+    ngl = npart - 2
+    assert ngl <= 3, "beyond five partons not every helicity amplitude is MHV"
+    total = np.zeros(nev)
+    for gh in itertools.product((-1, 1), repeat=ngl):
+        for qh in (-1, 1):
+            v = parke_taylor_helicity(p, alphas, qh, -qh, gh)
+            total += v
+    avg = 1.0 / (4.0 * 64.0 * math.factorial(ngl - 2))
+    return total * avg
+
+
+def random_rotation(seed):
+    g = np.random.default_rng(seed)
+    q, r = np.linalg.qr(g.normal(size=(3, 3)))
+    q = q * np.sign(np.diag(r))
+    if np.linalg.det(q) < 0:
+        q[:, 0] = -q[:, 0]
+    return q
+
+
+def rotate(p, rot):
+    out = p.copy()
+    out[..., 1:] = p[..., 1:] @ rot.T
+    return out
+
+
+def boost(p, beta):
+    b = np.asarray(beta, dtype=np.float64)
+    b2 = b @ b
+    gam = 1.0 / math.sqrt(1.0 - b2)
+    bp = p[..., 1:] @ b
+    out = p.copy()
+    out[..., 0] = gam * (p[..., 0] + bp)
+    out[..., 1:] = p[..., 1:] + ((gam - 1.0) * bp / b2)[..., None] * b + (gam * p[..., 0])[..., None] * b
+    return out
