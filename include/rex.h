@@ -1,0 +1,141 @@
+/*
+ * rex.h -- C ABI of the B300 (sm_103a) LO matrix-element reweighting library.
+ *
+ * What the library computes (paper Sec. 3, the weight factorisation
+ * w' = w |M'|^2 / |M|^2, and the teaRex normaliser of Sec. 3.1 that maps 1/0 to 0):
+ * for every event e of one subprocess and every parameter point j,
+ *
+ *     w_out[e][j] = w_in[e] * |M(p_e; theta_j)|^2 / |M(p_e; theta_0)|^2
+ *                 = 0                       if |M(p_e; theta_0)|^2 == 0,
+ *
+ * where |M|^2 is the tree-level, helicity-summed (Sec. 4.1: only
+ * helicity-summed reweighting) and colour-summed squared matrix element,
+ * averaged over initial spins and colours, theta_0 the parameter point set
+ * with rex_set_params and theta_j the j-th entry of param_sets.
+ *
+ * Momenta enter exactly as the paper's amplitude bridge receives them
+ * (Sec. 4.2: only the particle momenta, the flat per-process momentum
+ * vector): one flat FP64 array [nev][npart][4] with components
+ * (E, px, py, pz) per particle, particles in the order the process name
+ * states.  Events must already be sorted into the subprocess and their
+ * partons reordered to that order (Rex's eventBelongs, Sec. 2).
+ *
+ * Conventions for all calls:
+ *  - return value 0 = success, negative = error (REX_E*); rex_last_error()
+ *    returns a message for the calling thread's last failure;
+ *  - device pointers must be 8-byte aligned device (or managed) memory of
+ *    the current device; the caller owns every array passed in;
+ *  - stream is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream); calls taking a stream only enqueue work on it and return
+ *    without synchronising; asynchronous kernel faults surface at the
+ *    caller's next synchronisation of that stream;
+ *  - nev == 0 or k == 0 is a no-op that returns 0;
+ *  - non-finite momenta give NaN in that event's outputs (no trap).
+ */
+#ifndef REX_B300_H
+#define REX_B300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define REX_OK 0
+#define REX_EINVAL (-1)      /* bad handle, name, size, null or misaligned pointer */
+#define REX_ENOTINIT (-2)    /* rex_reweight before rex_set_params */
+#define REX_ECUDA (-3)       /* a CUDA call failed; see rex_last_error() */
+#define REX_ENOMEM (-4)      /* a library-owned allocation failed */
+#define REX_EUNSUPPORTED (-5) /* precision mode not available for this process */
+
+/* Precision modes (the paper's fptype option, Sec. 4.1, re-cut for B300):
+ * REX_FP64: every step in FP64.
+ * REX_MIXED: wavefunctions and amplitudes in FP32, colour sum on tensor
+ *            cores (FP16 operands, FP32 accumulation), helicity sum and
+ *            weight ratio in FP64. */
+#define REX_FP64 0
+#define REX_MIXED 1
+
+/* Options (rex_set_flags). */
+#define REX_FLAG_NO_DEDUPE 1u  /* evaluate the amplitude once per parameter
+                                  point instead of once per distinct (mt, Gamma_t) */
+
+typedef struct rex_proc rex_proc; /* opaque, library-owned */
+
+/* One parameter point.  Fields a process does not use are ignored.
+ *   QCD processes (gg_ttx, gg_ttxg, gg_ttxgg): mt, wt (top mass and width,
+ *     GeV), alphas (strong coupling, fixed; g_s = sqrt(4 pi alphas)).
+ *     mt enters the top propagators and the external top spinors; momenta
+ *     are kept as given.
+ *   ee_mumu: mz, wz (Z mass and width, GeV), sw2 (sin^2 theta_W),
+ *     alpha (electromagnetic coupling); independent inputs, cW^2 = 1 - sW^2. */
+typedef struct {
+  double mt, wt, alphas;
+  double mz, wz, sw2, alpha;
+} rex_params;
+
+/* Create a handle for one subprocess.
+ * name: "ee_mumu"  e+(1) e-(2) -> mu+(3) mu-(4), photon + Z, massless leptons;
+ *       "gg_ttx"   g(1) g(2) -> t(3) t~(4);
+ *       "gg_ttxg"  g(1) g(2) -> t(3) t~(4) g(5);
+ *       "gg_ttxgg" g(1) g(2) -> t(3) t~(4) g(5) g(6).
+ * precision: REX_FP64 or REX_MIXED.
+ * On success *out receives a handle the caller releases with rex_free_process.
+ * Errors: REX_EINVAL (null out, unknown name or precision). */
+int rex_init_process(const char *name, int precision, rex_proc **out);
+
+/* Number of particles (npart) of the handle's process, or REX_EINVAL. */
+int rex_process_npart(const rex_proc *proc);
+
+/* Set option flags (REX_FLAG_*).  Errors: REX_EINVAL. */
+int rex_set_flags(rex_proc *proc, unsigned flags);
+
+/* Set the original parameter point theta_0 (host pointer, copied).
+ * This is the point the input weights were generated at (paper Sec. 3.1:
+ * the normaliser is |M|^2 at the original card).
+ * Errors: REX_EINVAL (null pointer, non-positive mass or coupling). */
+int rex_set_params(rex_proc *proc, const rex_params *original);
+
+/* Reweight nev events to k parameter points (paper Sec. 3, the factorised
+ * weight w' = w |M'|^2/|M|^2; Sec. 3.1 normaliser 1/0 -> 0).
+ *   momenta    device, [nev][npart][4] FP64, (E, px, py, pz)
+ *   w_in       device, [nev] FP64 original weights
+ *   param_sets host, [k] points (copied before return)
+ *   w_out      device, [nev][k] FP64, row-major (event-major), written
+ * One launch evaluates |M|^2 at theta_0 and at every point.  The call only
+ * enqueues on stream; it allocates nothing and may be captured in a CUDA graph.
+ * Errors: REX_EINVAL, REX_ENOTINIT, REX_ECUDA. */
+int rex_reweight(rex_proc *proc, const double *momenta, const double *w_in,
+                 int64_t nev, const rex_params *param_sets, int k,
+                 double *w_out, void *stream);
+
+/* Same computation with HOST arrays: copies momenta and w_in to the device,
+ * reweights, copies w_out back and synchronises stream before returning.
+ * Page-locked host memory makes the copies asynchronous DMA.  Device
+ * buffers are library-owned, grown on demand and kept until rex_free_process.
+ * Errors: as rex_reweight, plus REX_ENOMEM. */
+int rex_reweight_host(rex_proc *proc, const double *momenta, const double *w_in,
+                      int64_t nev, const rex_params *param_sets, int k,
+                      double *w_out, void *stream);
+
+/* |M|^2 per event at one parameter point (spin/colour summed and averaged).
+ *   momenta device [nev][npart][4]; me2_out device [nev].  Enqueue only.
+ * Errors: REX_EINVAL, REX_ECUDA. */
+int rex_me2(rex_proc *proc, const double *momenta, int64_t nev,
+            const rex_params *point, double *me2_out, void *stream);
+
+/* Release a handle (NULL is ignored).  Synchronises nothing; the caller must
+ * make sure no work enqueued with the handle is still running. */
+void rex_free_process(rex_proc *proc);
+
+/* Message of the calling thread's most recent error ("" if none). */
+const char *rex_last_error(void);
+
+/* Library version string. */
+const char *rex_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* REX_B300_H */

@@ -1,0 +1,239 @@
+// Device building blocks for tree-level helicity amplitudes (sm_103a).
+//
+// Written for this library from the chiral-basis definitions; the routine
+// names echo the HELAS families they play the role of (external wavefunctions
+// ixxxxx/oxxxxx/vxxxxx, vertex currents VVV1P0_1 / FFV1_1, closures FFV1_0).
+//
+// Conventions: metric (+,-,-,-); chiral basis, gamma^mu = [[0, sigma^mu],
+// [sigmabar^mu, 0]], spinor components ordered (left-handed 0,1 | right-handed
+// 2,3).  Lorentz vectors are upper-index (E, px, py, pz).
+//
+// Helicity sums are basis independent, so:
+//  * gluons use REAL linear polarisation vectors e1, e2 (transverse, orthonormal);
+//    every pure-gluon current built from them is a real 4-vector;
+//  * fermions use helicity spinors in this file's own phase convention.
+//
+// Mass in external spinors when a parameter point changes a mass while the
+// momentum is kept: omega_+ = sqrt(E + |p|), omega_- = m / omega_+ (equal to
+// sqrt(E - |p|) on shell).  This is the spinor of the on-shell momentum with the
+// same direction and the same E + |p| as p, with mass m.
+#pragma once
+#if defined(__CUDACC__)
+#include <cuda_runtime.h>
+#endif
+
+namespace rex {
+
+template <typename R>
+struct cx {
+  R re, im;
+};
+
+template <typename R>
+__device__ __forceinline__ cx<R> cmk(R a, R b) { return cx<R>{a, b}; }
+template <typename R>
+__device__ __forceinline__ cx<R> operator+(cx<R> a, cx<R> b) { return cx<R>{a.re + b.re, a.im + b.im}; }
+template <typename R>
+__device__ __forceinline__ cx<R> operator-(cx<R> a, cx<R> b) { return cx<R>{a.re - b.re, a.im - b.im}; }
+template <typename R>
+__device__ __forceinline__ cx<R> operator-(cx<R> a) { return cx<R>{-a.re, -a.im}; }
+template <typename R>
+__device__ __forceinline__ cx<R> operator*(cx<R> a, cx<R> b) {
+  return cx<R>{a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re};
+}
+template <typename R>
+__device__ __forceinline__ cx<R> operator*(R s, cx<R> a) { return cx<R>{s * a.re, s * a.im}; }
+template <typename R>
+__device__ __forceinline__ cx<R> conjg(cx<R> a) { return cx<R>{a.re, -a.im}; }
+// conj(a) * b
+template <typename R>
+__device__ __forceinline__ cx<R> cdot1(cx<R> a, cx<R> b) {
+  return cx<R>{a.re * b.re + a.im * b.im, a.re * b.im - a.im * b.re};
+}
+
+template <typename R>
+__device__ __forceinline__ R mdot(const R* a, const R* b) {
+  return a[0] * b[0] - a[1] * b[1] - a[2] * b[2] - a[3] * b[3];
+}
+
+// ---------------------------------------------------------------------------
+// external wavefunctions
+// ---------------------------------------------------------------------------
+
+// Linear polarisation vector e_{which} (which = 0, 1) of a massless momentum k:
+// e1 = (0, kx kz, ky kz, -kT^2)/(|k| kT), e2 = (0, -ky, kx, 0)/kT; along the
+// beam axis e1 = x-hat, e2 = y-hat.  (vxxxxx role, linear basis.)
+template <typename R>
+__device__ __forceinline__ void pol_linear(const R* k, int which, R* eps) {
+  const R kx = k[1], ky = k[2], kz = k[3];
+  const R kt2 = kx * kx + ky * ky;
+  eps[0] = R(0);
+  if (kt2 > R(0)) {
+    const R kt = sqrt(kt2);
+    const R kabs = sqrt(kt2 + kz * kz);
+    if (which == 0) {
+      const R f = kz / (kabs * kt);
+      eps[1] = kx * f;
+      eps[2] = ky * f;
+      eps[3] = -kt / kabs;
+    } else {
+      eps[1] = -ky / kt;
+      eps[2] = kx / kt;
+      eps[3] = R(0);
+    }
+  } else {
+    eps[1] = which == 0 ? R(1) : R(0);
+    eps[2] = which == 0 ? R(0) : R(1);
+    eps[3] = R(0);
+  }
+}
+
+// Two-component helicity eigenvectors chi_+, chi_- of (p-hat . sigma).
+// chi_+ = (|p|+pz, px + i py)/N, chi_- = (-px + i py, |p|+pz)/N, N^2 = 2|p|(|p|+pz);
+// |p|+pz is taken as pT^2/(|p|-pz) for pz < 0 to avoid cancellation.
+template <typename R>
+__device__ __forceinline__ void chi_pair(const R* p, R pabs, cx<R>* chip, cx<R>* chim) {
+  const R px = p[1], py = p[2], pz = p[3];
+  const R pt2 = px * px + py * py;
+  if (pt2 > R(0)) {
+    const R a = pz >= R(0) ? pabs + pz : pt2 / (pabs - pz);
+    const R nrm = rsqrt(R(2) * pabs * a);
+    const R an = a * nrm;
+    chip[0] = cx<R>{an, R(0)};
+    chip[1] = cx<R>{px * nrm, py * nrm};
+    chim[0] = cx<R>{-px * nrm, py * nrm};
+    chim[1] = cx<R>{an, R(0)};
+  } else if (pz >= R(0)) {           // along +z, or at rest (take +z)
+    chip[0] = cx<R>{R(1), R(0)};
+    chip[1] = cx<R>{R(0), R(0)};
+    chim[0] = cx<R>{R(0), R(0)};
+    chim[1] = cx<R>{R(1), R(0)};
+  } else {                           // along -z
+    chip[0] = cx<R>{R(0), R(0)};
+    chip[1] = cx<R>{R(1), R(0)};
+    chim[0] = cx<R>{R(-1), R(0)};
+    chim[1] = cx<R>{R(0), R(0)};
+  }
+}
+
+// omega_+ = sqrt(E + |p|), omega_- = m / omega_+.
+template <typename R>
+__device__ __forceinline__ void omegas(const R* p, R m, R* pabs, R* wp, R* wm) {
+  const R a = sqrt(p[1] * p[1] + p[2] * p[2] + p[3] * p[3]);
+  *pabs = a;
+  const R w = sqrt(p[0] + a);
+  *wp = w;
+  *wm = m / w;
+}
+
+// u(p, hel) of an outgoing fermion, to be closed as ubar (oxxxxx role):
+// u(+) = (w- chi+, w+ chi+), u(-) = (w+ chi-, w- chi-).
+template <typename R>
+__device__ __forceinline__ void spinor_u(const R* p, R m, int hel, cx<R>* u) {
+  R pabs, wp, wm;
+  omegas(p, m, &pabs, &wp, &wm);
+  cx<R> cp[2], cm[2];
+  chi_pair(p, pabs, cp, cm);
+  if (hel > 0) {
+    u[0] = wm * cp[0]; u[1] = wm * cp[1]; u[2] = wp * cp[0]; u[3] = wp * cp[1];
+  } else {
+    u[0] = wp * cm[0]; u[1] = wp * cm[1]; u[2] = wm * cm[0]; u[3] = wm * cm[1];
+  }
+}
+
+// v(p, hel) of an outgoing antifermion (ixxxxx role): eta = chi_{-hel},
+// v(+) = (w+ chi-, -w- chi-), v(-) = (w- chi+, -w+ chi+).
+template <typename R>
+__device__ __forceinline__ void spinor_v(const R* p, R m, int hel, cx<R>* v) {
+  R pabs, wp, wm;
+  omegas(p, m, &pabs, &wp, &wm);
+  cx<R> cp[2], cm[2];
+  chi_pair(p, pabs, cp, cm);
+  if (hel > 0) {
+    v[0] = wp * cm[0]; v[1] = wp * cm[1]; v[2] = (-wm) * cm[0]; v[3] = (-wm) * cm[1];
+  } else {
+    v[0] = wm * cp[0]; v[1] = wm * cp[1]; v[2] = (-wp) * cp[0]; v[3] = (-wp) * cp[1];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// fermion-line operations
+// ---------------------------------------------------------------------------
+
+// out += s * (gamma . a) psi for a real 4-vector a.
+template <typename R>
+__device__ __forceinline__ void slash_acc(R s, const R* a, const cx<R>* psi, cx<R>* out) {
+  const R am = s * (a[0] - a[3]), ap = s * (a[0] + a[3]);
+  const R a1 = s * a[1], a2 = s * a[2];
+  // (a1 - i a2) * z and (a1 + i a2) * z
+  const cx<R> m3 = cx<R>{a1 * psi[3].re + a2 * psi[3].im, a1 * psi[3].im - a2 * psi[3].re};
+  const cx<R> p2 = cx<R>{a1 * psi[2].re - a2 * psi[2].im, a1 * psi[2].im + a2 * psi[2].re};
+  const cx<R> m1 = cx<R>{a1 * psi[1].re + a2 * psi[1].im, a1 * psi[1].im - a2 * psi[1].re};
+  const cx<R> p0 = cx<R>{a1 * psi[0].re - a2 * psi[0].im, a1 * psi[0].im + a2 * psi[0].re};
+  out[0] = out[0] + am * psi[2] - m3;
+  out[1] = out[1] - p2 + ap * psi[3];
+  out[2] = out[2] + ap * psi[0] + m1;
+  out[3] = out[3] + p0 + am * psi[1];
+}
+
+// out = -(q-slash + m) in * invden  (fermion propagator, the -1 = i*i of
+// propagator and vertex factors; FFV1_1 role).
+template <typename R>
+__device__ __forceinline__ void fermion_prop(const R* q, R m, cx<R> invden, const cx<R>* in, cx<R>* out) {
+  cx<R> t[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) t[i] = m * in[i];
+  slash_acc(R(1), q, in, t);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) out[i] = -(t[i] * invden);
+}
+
+// Same with a real inverse denominator (zero width).
+template <typename R>
+__device__ __forceinline__ void fermion_prop_real(const R* q, R m, R invden, const cx<R>* in, cx<R>* out) {
+  cx<R> t[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) t[i] = m * in[i];
+  slash_acc(R(1), q, in, t);
+  const R f = -invden;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) out[i] = f * t[i];
+}
+
+// ubar(u) . x = u_L^dag x_R + u_R^dag x_L  (FFV1_0 closure role).
+template <typename R>
+__device__ __forceinline__ cx<R> ubar_dot(const cx<R>* u, const cx<R>* x) {
+  return cdot1(u[0], x[2]) + cdot1(u[1], x[3]) + cdot1(u[2], x[0]) + cdot1(u[3], x[1]);
+}
+
+// ---------------------------------------------------------------------------
+// colour-ordered gluon vertices (VVV1P0_1 / VVVV roles), real currents
+// ---------------------------------------------------------------------------
+
+// out += s * [ (X.Y)(PY - PX) - (X.(PX + 2 PY)) Y + (Y.(2 PX + PY)) X ]
+template <typename R>
+__device__ __forceinline__ void vvv_acc(R s, const R* jx, const R* px, const R* jy, const R* py, R* out) {
+  R a[4], b[4];
+#pragma unroll
+  for (int m = 0; m < 4; ++m) {
+    a[m] = px[m] + R(2) * py[m];
+    b[m] = R(2) * px[m] + py[m];
+  }
+  const R xy = s * mdot(jx, jy);
+  const R xa = s * mdot(jx, a);
+  const R yb = s * mdot(jy, b);
+#pragma unroll
+  for (int m = 0; m < 4; ++m) out[m] += xy * (py[m] - px[m]) - xa * jy[m] + yb * jx[m];
+}
+
+// out += s * [ (X.Y) Z + (Y.Z) X - 2 (X.Z) Y ]
+template <typename R>
+__device__ __forceinline__ void vvvv_acc(R s, const R* jx, const R* jy, const R* jz, R* out) {
+  const R xy = s * mdot(jx, jy);
+  const R yz = s * mdot(jy, jz);
+  const R xz2 = R(-2) * s * mdot(jx, jz);
+#pragma unroll
+  for (int m = 0; m < 4; ++m) out[m] += xy * jz[m] + yz * jx[m] + xz2 * jy[m];
+}
+
+}  // namespace rex

@@ -1,0 +1,57 @@
+// Internal launch descriptors shared by the kernels and the C ABI.
+#pragma once
+#include <cstdint>
+
+namespace rex {
+
+// Distinct (mass, width) evaluations per launch and parameter points per launch.
+// The whole table travels as a __grid_constant__ kernel parameter (< 8 KB), so
+// a launch needs no device allocation and no host-to-device copy.
+constexpr int MAX_MASS = 64;
+constexpr int MAX_POINTS = 256;
+
+enum ProcKind : int { PROC_EE_MUMU = 0, PROC_GG_TTX = 1, PROC_GG_TTXG = 2, PROC_GG_TTXGG = 3 };
+enum OutMode : int { OUT_RATIO = 0, OUT_ME2 = 1 };
+
+// QCD processes: the amplitude is evaluated once per mass slot (slot 0 is the
+// original point) with unit coupling; point j then takes
+//   |M|^2_j = acc[slot[j]] * factor[j],  factor = avg * (4 pi alphas)^n / colour_den.
+struct QcdLaunch {
+  int nmass;
+  int k;
+  int mode;           // OutMode
+  int has_width;      // any non-zero width among the slots
+  int64_t out_stride; // row stride of the output (elements)
+  double factor0;     // factor of the original point
+  double mass[MAX_MASS];
+  double width[MAX_MASS];
+  int slot[MAX_POINTS];
+  double factor[MAX_POINTS];
+};
+
+// e+e- -> mu+mu-: per point, couplings of the photon and Z terms (index 0 is
+// the original point, 1..k the new ones).
+//   amp = e2qq/s (Je.Jm) + sum_{X,Y in L,R} gzz[XY] / (s - mz2 + i mzwz) (JeX.JmY)
+struct EwPoint {
+  double e2qq;
+  double gzz[4];  // LL, LR, RL, RR
+  double mz2, mzwz;
+  double avg;     // 1/4 spin average times nothing else
+};
+
+constexpr int MAX_EW_POINTS = 128;
+
+struct EwLaunch {
+  int k;          // new points (table holds k+1 entries)
+  int mode;
+  int64_t out_stride;
+  EwPoint pt[MAX_EW_POINTS + 1];
+};
+
+// Launchers (defined in the kernel translation units).  Return cudaError_t as int.
+int launch_qcd(int proc, int mixed, const double* mom, const double* w_in, int64_t nev,
+               const QcdLaunch& lp, double* out, void* stream);
+int launch_ee(const double* mom, const double* w_in, int64_t nev, const EwLaunch& lp,
+              double* out, void* stream);
+
+}  // namespace rex

@@ -1,0 +1,191 @@
+"""Python binding of the C ABI in include/rex.h (argument marshalling only).
+
+Every step of the computation runs in the CUDA kernels of librex_b300.so; this
+module converts torch tensors / numpy arrays to pointers and error codes to
+exceptions.  Importing it fails loudly when the shared library is missing:
+there is no CPU fallback.
+
+    import torch
+    from paper_2510_05100_b300 import rex
+    proc = rex.Process("gg_ttxg", precision=rex.FP64)
+    proc.set_params(mt=173.0, alphas=0.118)
+    w_out = proc.reweight(momenta_cuda, w_in_cuda, [dict(mt=171.0, alphas=0.118), ...])
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Iterable, Sequence
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "librex_b300.so")
+
+REX_OK = 0
+REX_EINVAL = -1
+REX_ENOTINIT = -2
+REX_ECUDA = -3
+REX_ENOMEM = -4
+REX_EUNSUPPORTED = -5
+FP64 = 0
+MIXED = 1
+FLAG_NO_DEDUPE = 1
+
+# symbols declared in include/rex.h
+EXPORTS = (
+    "rex_init_process", "rex_process_npart", "rex_set_flags", "rex_set_params",
+    "rex_reweight", "rex_reweight_host", "rex_me2", "rex_free_process",
+    "rex_last_error", "rex_version",
+)
+
+
+class RexError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"rex error {code}: {msg}")
+        self.code = code
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("mt", ctypes.c_double), ("wt", ctypes.c_double), ("alphas", ctypes.c_double),
+                ("mz", ctypes.c_double), ("wz", ctypes.c_double), ("sw2", ctypes.c_double),
+                ("alpha", ctypes.c_double)]
+
+
+def params(d: dict) -> Params:
+    return Params(d.get("mt", 0.0), d.get("wt", 0.0), d.get("alphas", 0.0),
+                  d.get("mz", 0.0), d.get("wz", 0.0), d.get("sw2", 0.0), d.get("alpha", 0.0))
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Load librex_b300.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"{path} is missing: build it with `python -m paper_2510_05100_b300.build`")
+    lib = ctypes.CDLL(path)
+    vp, i64, dp = ctypes.c_void_p, ctypes.c_int64, ctypes.POINTER(ctypes.c_double)
+    pp = ctypes.POINTER(Params)
+    lib.rex_init_process.argtypes = [ctypes.c_char_p, ctypes.c_int, ctypes.POINTER(vp)]
+    lib.rex_init_process.restype = ctypes.c_int
+    lib.rex_process_npart.argtypes = [vp]
+    lib.rex_process_npart.restype = ctypes.c_int
+    lib.rex_set_flags.argtypes = [vp, ctypes.c_uint]
+    lib.rex_set_flags.restype = ctypes.c_int
+    lib.rex_set_params.argtypes = [vp, pp]
+    lib.rex_set_params.restype = ctypes.c_int
+    lib.rex_reweight.argtypes = [vp, vp, vp, i64, pp, ctypes.c_int, vp, vp]
+    lib.rex_reweight.restype = ctypes.c_int
+    lib.rex_reweight_host.argtypes = [vp, vp, vp, i64, pp, ctypes.c_int, vp, vp]
+    lib.rex_reweight_host.restype = ctypes.c_int
+    lib.rex_me2.argtypes = [vp, vp, i64, pp, vp, vp]
+    lib.rex_me2.restype = ctypes.c_int
+    lib.rex_free_process.argtypes = [vp]
+    lib.rex_free_process.restype = None
+    lib.rex_last_error.argtypes = []
+    lib.rex_last_error.restype = ctypes.c_char_p
+    lib.rex_version.argtypes = []
+    lib.rex_version.restype = ctypes.c_char_p
+    _lib = lib
+    return lib
+
+
+def _check(rc: int) -> None:
+    if rc != REX_OK:
+        raise RexError(rc, load().rex_last_error().decode())
+
+
+def _ptr(t) -> int:
+    """Device or host address of a torch tensor / numpy array (contiguous float64)."""
+    if t is None:
+        return 0
+    if hasattr(t, "data_ptr"):
+        if not t.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return t.data_ptr()
+    if not t.flags["C_CONTIGUOUS"]:
+        raise ValueError("array must be C-contiguous")
+    return t.ctypes.data
+
+
+def _stream_ptr(stream) -> int:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if hasattr(stream, "cuda_stream"):
+        return stream.cuda_stream
+    return int(stream)
+
+
+def _param_array(points: Sequence[dict]):
+    arr = (Params * max(1, len(points)))()
+    for i, d in enumerate(points):
+        arr[i] = params(d)
+    return arr
+
+
+class Process:
+    """One subprocess handle (rex_init_process / rex_free_process)."""
+
+    def __init__(self, name: str, precision: int = FP64):
+        lib = load()
+        h = ctypes.c_void_p()
+        _check(lib.rex_init_process(name.encode(), precision, ctypes.byref(h)))
+        self._h = h
+        self.name = name
+        self.precision = precision
+        self.npart = lib.rex_process_npart(h)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().rex_free_process(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_flags(self, flags: int) -> None:
+        _check(load().rex_set_flags(self._h, flags))
+
+    def set_params(self, point: dict | None = None, **kw) -> None:
+        d = dict(point or {})
+        d.update(kw)
+        p = params(d)
+        _check(load().rex_set_params(self._h, ctypes.byref(p)))
+
+    def reweight(self, momenta, w_in, points: Sequence[dict], w_out=None, stream=None):
+        """Device tensors in, device tensor [nev, k] out (enqueued on ``stream``)."""
+        import torch
+        nev = momenta.shape[0]
+        k = len(points)
+        if w_out is None:
+            w_out = torch.empty((nev, k), dtype=torch.float64, device=momenta.device)
+        arr = _param_array(points)
+        _check(load().rex_reweight(self._h, _ptr(momenta), _ptr(w_in), nev, arr, k,
+                                   _ptr(w_out), _stream_ptr(stream)))
+        return w_out
+
+    def reweight_host(self, momenta, w_in, points: Sequence[dict], w_out, stream=None) -> None:
+        """Host arrays in and out (copies inside the call; blocks until w_out is written)."""
+        arr = _param_array(points)
+        _check(load().rex_reweight_host(self._h, _ptr(momenta), _ptr(w_in), momenta.shape[0], arr,
+                                        len(points), _ptr(w_out), _stream_ptr(stream)))
+
+    def me2(self, momenta, point: dict, out=None, stream=None):
+        import torch
+        nev = momenta.shape[0]
+        if out is None:
+            out = torch.empty((nev,), dtype=torch.float64, device=momenta.device)
+        p = params(point)
+        _check(load().rex_me2(self._h, _ptr(momenta), nev, ctypes.byref(p), _ptr(out),
+                              _stream_ptr(stream)))
+        return out
+
+
+def version() -> str:
+    return load().rex_version().decode()

@@ -1,0 +1,82 @@
+"""C ABI checks that need no GPU: the library loads, exports every symbol the
+header declares, and host-side validation returns the documented codes
+(no call here reaches the CUDA runtime)."""
+import ctypes
+
+import numpy as np
+import pytest
+
+from rexlib import declared_symbols, ensure_built
+
+
+@pytest.fixture(scope="module")
+def rex():
+    return ensure_built()
+
+
+def test_header_declares_the_boundary():
+    syms = declared_symbols()
+    for s in ("rex_init_process", "rex_set_params", "rex_reweight", "rex_me2", "rex_free_process",
+              "rex_last_error"):
+        assert s in syms
+
+
+def test_library_exports_every_declared_symbol(rex):
+    lib = rex.load()
+    for s in declared_symbols():
+        assert hasattr(lib, s), s
+    assert set(rex.EXPORTS) == set(declared_symbols())
+    assert "sm_103a" in rex.version()
+
+
+def test_init_errors(rex):
+    lib = rex.load()
+    h = ctypes.c_void_p()
+    assert lib.rex_init_process(b"no_such_process", 0, ctypes.byref(h)) == rex.REX_EINVAL
+    assert b"unknown process" in lib.rex_last_error()
+    assert lib.rex_init_process(b"gg_ttxg", 7, ctypes.byref(h)) == rex.REX_EINVAL
+    assert lib.rex_init_process(None, 0, ctypes.byref(h)) == rex.REX_EINVAL
+    assert lib.rex_init_process(b"gg_ttxg", 0, None) == rex.REX_EINVAL
+    assert lib.rex_init_process(b"ee_mumu", rex.MIXED, ctypes.byref(h)) == rex.REX_EUNSUPPORTED
+
+
+@pytest.mark.parametrize("name,npart", [("ee_mumu", 4), ("gg_ttx", 4), ("gg_ttxg", 5), ("gg_ttxgg", 6)])
+def test_handle_lifecycle(rex, name, npart):
+    p = rex.Process(name)
+    assert p.npart == npart
+    p.close()
+
+
+def test_validation_before_any_device_work(rex):
+    lib = rex.load()
+    p = rex.Process("gg_ttxg")
+    pts = (rex.Params * 1)(rex.params(dict(mt=171.0, alphas=0.118)))
+    fake = ctypes.c_void_p(0x10000)     # never dereferenced: validation fails first
+    # not initialised
+    assert lib.rex_reweight(p._h, fake, fake, 10, pts, 1, fake, None) == rex.REX_ENOTINIT
+    p.set_params(mt=173.0, alphas=0.118)
+    assert lib.rex_reweight(p._h, fake, fake, -1, pts, 1, fake, None) == rex.REX_EINVAL
+    assert lib.rex_reweight(p._h, fake, fake, 10, pts, -1, fake, None) == rex.REX_EINVAL
+    assert lib.rex_reweight(p._h, None, fake, 10, pts, 1, fake, None) == rex.REX_EINVAL
+    assert lib.rex_reweight(p._h, ctypes.c_void_p(0x10008), fake, 10, pts, 1, fake, None) == rex.REX_EINVAL
+    assert b"aligned" in lib.rex_last_error()
+    # empty work is a no-op that succeeds without touching the pointers
+    assert lib.rex_reweight(p._h, None, None, 0, pts, 1, None, None) == rex.REX_OK
+    assert lib.rex_reweight(p._h, None, None, 10, pts, 0, None, None) == rex.REX_OK
+    # bad points
+    bad = (rex.Params * 1)(rex.params(dict(mt=-1.0, alphas=0.118)))
+    assert lib.rex_reweight(p._h, fake, fake, 10, bad, 1, fake, None) == rex.REX_EINVAL
+    with pytest.raises(rex.RexError):
+        p.set_params(mt=173.0, alphas=0.0)
+    with pytest.raises(rex.RexError):
+        p.set_flags(0x80)
+    assert lib.rex_reweight(None, fake, fake, 10, pts, 1, fake, None) == rex.REX_EINVAL
+    p.close()
+
+
+def test_ee_point_validation(rex):
+    p = rex.Process("ee_mumu")
+    with pytest.raises(rex.RexError):
+        p.set_params(mz=91.1876, wz=2.4952, sw2=1.5, alpha=1 / 132.507)
+    p.set_params(mz=91.1876, wz=2.4952, sw2=0.2312, alpha=1 / 132.507)
+    p.close()

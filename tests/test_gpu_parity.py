@@ -1,0 +1,220 @@
+"""CUDA path vs the FP64 oracle, through the C ABI (needs a B300).
+
+Tolerances:
+* FP64 mode: 1e-12 relative per event on |M|^2 and on every new weight.
+* unchanged parameter point: new weight == input weight exactly (same mass
+  slot, same coupling factor, w * (x / x) = w).
+* mixed mode (FP32 amplitudes): the bound measured per process, see MIXED_TOL.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from rexlib import ensure_built
+from oracle import reweight as oracle_rw
+from paper_2510_05100_b300 import phase_space as ps
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+FP64_TOL = 1e-12
+# max relative error of a new weight in mixed precision (FP32 amplitudes,
+# FP64 colour/helicity sums and ratio), measured over the parity samples
+MIXED_TOL = {"gg_ttx": 2e-4, "gg_ttxg": 2e-3, "gg_ttxgg": 2e-2}
+
+ORIG_QCD = dict(mt=173.0, wt=0.0, alphas=0.118)
+SIZES = {"ee_mumu": 300, "gg_ttx": 101, "gg_ttxg": 53, "gg_ttxgg": 19}
+NGLUON = {"gg_ttx": 2, "gg_ttxg": 3, "gg_ttxgg": 4}
+
+
+@pytest.fixture(scope="module")
+def rex():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return ensure_built()
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def original(proc):
+    return ps.EE_ORIGINAL if proc == "ee_mumu" else ORIG_QCD
+
+
+def new_points(proc):
+    if proc == "ee_mumu":
+        return [ps.EE_NEW]
+    if proc == "gg_ttx":
+        return ps.grid_gg_ttx()
+    if proc == "gg_ttxg":
+        return ps.grid_gg_ttxg()
+    return [dict(mt=171.0, wt=0.0, alphas=0.118), dict(mt=175.0, wt=0.0, alphas=0.124),
+            dict(mt=173.0, wt=0.0, alphas=0.112)]
+
+
+def make(proc, rex, precision=0):
+    p = rex.Process(proc, precision)
+    p.set_params(original(proc))
+    return p
+
+
+def rel(a, b):
+    return np.abs(a / b - 1.0)
+
+
+@pytest.mark.parametrize("proc", ["ee_mumu", "gg_ttx", "gg_ttxg", "gg_ttxgg"])
+def test_me2_parity_fp64(rex, proc):
+    n = SIZES[proc]
+    mom = ps.make_events(proc, n, 101)
+    p = make(proc, rex)
+    for pt in [original(proc)] + new_points(proc)[:2]:
+        got = p.me2(dev(mom), pt).cpu().numpy()
+        ref = oracle_rw.me2(proc, mom, pt)
+        assert np.max(rel(got, ref)) < FP64_TOL, (proc, pt, np.max(rel(got, ref)))
+
+
+@pytest.mark.parametrize("proc", ["ee_mumu", "gg_ttx", "gg_ttxg", "gg_ttxgg"])
+def test_reweight_parity_fp64(rex, proc):
+    n = SIZES[proc]
+    mom = ps.make_events(proc, n, 202)
+    w = np.random.default_rng(3).uniform(0.5, 2.0, n)
+    pts = new_points(proc)
+    p = make(proc, rex)
+    got = p.reweight(dev(mom), dev(w), pts).cpu().numpy()
+    ref = oracle_rw.reweight(proc, mom, w, original(proc), pts)
+    assert got.shape == (n, len(pts))
+    assert np.max(rel(got, ref)) < FP64_TOL
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("proc", ["ee_mumu", "gg_ttx", "gg_ttxg", "gg_ttxgg"])
+def test_unchanged_point_gives_input_weight_exactly(rex, proc, precision):
+    if proc == "ee_mumu" and precision == 1:
+        pytest.skip("ee_mumu is FP64 only")
+    n = SIZES[proc]
+    mom = ps.make_events(proc, n, 303)
+    w = np.random.default_rng(4).uniform(0.5, 2.0, n)
+    p = make(proc, rex, precision)
+    got = p.reweight(dev(mom), dev(w), [original(proc)] * 3).cpu().numpy()
+    assert np.array_equal(got, np.repeat(w[:, None], 3, axis=1))
+
+
+@pytest.mark.parametrize("proc", ["gg_ttx", "gg_ttxg"])
+def test_alphas_only_points_scale_exactly(rex, proc):
+    n = SIZES[proc]
+    mom = ps.make_events(proc, n, 404)
+    w = np.ones(n)
+    p = make(proc, rex)
+    got = p.reweight(dev(mom), dev(w), [dict(mt=173.0, wt=0.0, alphas=0.124)]).cpu().numpy()
+    assert np.allclose(got, (0.124 / 0.118) ** NGLUON[proc], rtol=1e-14, atol=0)
+
+
+def test_dedupe_matches_per_point_evaluation_bitwise(rex):
+    mom = dev(ps.make_events("gg_ttxg", 77, 505))
+    w = dev(np.linspace(0.5, 1.5, 77))
+    pts = ps.grid_gg_ttxg()
+    a = make("gg_ttxg", rex)
+    b = make("gg_ttxg", rex)
+    b.set_flags(rex.FLAG_NO_DEDUPE)
+    assert torch.equal(a.reweight(mom, w, pts), b.reweight(mom, w, pts))
+
+
+def test_point_lists_longer_than_one_launch(rex):
+    """300 points with 75 distinct masses: several launches, columns stitched."""
+    n = 40
+    mom = ps.make_events("gg_ttx", n, 606)
+    w = np.ones(n)
+    mts = np.linspace(165.0, 180.0, 75)
+    pts = [dict(mt=float(mts[i % 75]), wt=0.0, alphas=0.110 + 0.0001 * (i % 4)) for i in range(300)]
+    p = make("gg_ttx", rex)
+    got = p.reweight(dev(mom), dev(w), pts).cpu().numpy()
+    sub = [0, 1, 63, 64, 74, 75, 150, 255, 256, 299]
+    ref = oracle_rw.reweight("gg_ttx", mom, w, ORIG_QCD, [pts[i] for i in sub])
+    assert np.max(rel(got[:, sub], ref)) < FP64_TOL
+
+
+def test_top_width(rex):
+    n = 33
+    mom = ps.make_events("gg_ttxg", n, 707)
+    w = np.ones(n)
+    orig = dict(mt=173.0, wt=1.4, alphas=0.118)
+    pts = [dict(mt=172.0, wt=1.3, alphas=0.118), dict(mt=174.0, wt=0.0, alphas=0.120)]
+    p = rex.Process("gg_ttxg")
+    p.set_params(orig)
+    got = p.reweight(dev(mom), dev(w), pts).cpu().numpy()
+    ref = oracle_rw.reweight("gg_ttxg", mom, w, orig, pts)
+    assert np.max(rel(got, ref)) < FP64_TOL
+
+
+@pytest.mark.parametrize("n", [1, 2, 15, 16, 17])
+def test_ragged_tails(rex, n):
+    mom = ps.make_events("gg_ttxg", n, 808)
+    w = np.ones(n)
+    pts = ps.grid_gg_ttxg()[:5]
+    p = make("gg_ttxg", rex)
+    got = p.reweight(dev(mom), dev(w), pts).cpu().numpy()
+    ref = oracle_rw.reweight("gg_ttxg", mom, w, ORIG_QCD, pts)
+    assert np.max(rel(got, ref)) < FP64_TOL
+
+
+def test_empty_inputs_leave_outputs_untouched(rex):
+    p = make("gg_ttxg", rex)
+    mom = dev(ps.make_events("gg_ttxg", 4, 1))
+    w = dev(np.ones(4))
+    out = torch.full((4, 2), 7.0, dtype=torch.float64, device="cuda")
+    p.reweight(mom[:0], w[:0], ps.grid_gg_ttxg()[:2], w_out=out[:0])
+    p.reweight(mom, w, [], w_out=out)
+    torch.cuda.synchronize()
+    assert torch.all(out == 7.0)
+
+
+def test_nonfinite_momenta_give_nan_for_that_event_only(rex):
+    mom = ps.make_events("gg_ttxg", 20, 909)
+    mom[5, 4, 1] = np.nan
+    p = make("gg_ttxg", rex)
+    got = p.reweight(dev(mom), dev(np.ones(20)), ps.grid_gg_ttxg()[:3]).cpu().numpy()
+    assert np.all(np.isnan(got[5]))
+    assert np.all(np.isfinite(np.delete(got, 5, axis=0)))
+
+
+def test_host_entry_point_matches_device_entry_point(rex):
+    n = 90
+    mom = ps.make_events("gg_ttxg", n, 111)
+    w = np.random.default_rng(5).uniform(0.5, 2.0, n)
+    pts = ps.grid_gg_ttxg()
+    p = make("gg_ttxg", rex)
+    dev_out = p.reweight(dev(mom), dev(w), pts).cpu().numpy()
+    host_out = np.zeros((n, len(pts)))
+    p.reweight_host(mom, w, pts, host_out)
+    assert np.array_equal(dev_out, host_out)
+
+
+@pytest.mark.parametrize("proc", ["gg_ttx", "gg_ttxg", "gg_ttxgg"])
+def test_mixed_precision_error_bound(rex, proc):
+    n = SIZES[proc] * 2
+    mom = ps.make_events(proc, n, 222)
+    w = np.ones(n)
+    pts = new_points(proc)
+    p = make(proc, rex, precision=1)
+    got = p.reweight(dev(mom), dev(w), pts).cpu().numpy()
+    ref = oracle_rw.reweight(proc, mom, w, ORIG_QCD, pts)
+    err = np.max(rel(got, ref))
+    assert err < MIXED_TOL[proc], err
+
+
+def test_full_size_workload_sampled(rex):
+    """The benchmark workload (2^20 g g -> t t~ g events, 16 points) in the launch
+    configuration the benchmark times, checked on sampled events."""
+    n = 1 << 20
+    mom = ps.make_events("gg_ttxg", n, 3)
+    w = np.ones(n)
+    pts = ps.grid_gg_ttxg()
+    p = make("gg_ttxg", rex)
+    got = p.reweight(dev(mom), dev(w), pts).cpu().numpy()
+    assert np.all(np.isfinite(got)) and np.all(got > 0)
+    idx = np.random.default_rng(6).choice(n, 24, replace=False)
+    idx = np.concatenate([idx, [0, n - 1]])
+    ref = oracle_rw.reweight("gg_ttxg", mom[idx], w[idx], ORIG_QCD, pts)
+    assert np.max(rel(got[idx], ref)) < FP64_TOL
