@@ -1,0 +1,375 @@
+#!/usr/bin/env python
+"""Reweighted events/s for g g -> t t~ g on B300: 2^20 events x 16 parameter points per GPU.
+
+One step = one pass of the whole hot path (momenta -> wavefunctions -> currents ->
+jamps -> colour sum -> helicity sum -> w*|M'|^2/|M|^2) over one batch: a single
+rex_reweight call on 2^20 seeded RAMBO events (sqrt(s_hat) log-uniform in
+[400, 4000] GeV, mt = 173) to 16 points (mt in linspace(171, 175, 4) x alphas in
+linspace(0.112, 0.124, 4)), original point (mt = 173, alphas = 0.118).
+
+  python bench.py [--gpus N --steps K --warmup W] [--mode fp64|mixed] [--impl ours|reference]
+
+Multi-GPU (torchrun, one rank per GPU): every rank reweights its own 2^20 events
+(seed 3 + rank); no data-path collective, weak scaling.  Rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+from paper_2510_05100_b300 import dist as rdist  # noqa: E402
+from paper_2510_05100_b300 import phase_space as ps  # noqa: E402
+
+METRIC = "reweighted events/sec (events x param points), gg->tt~g, 1 B300, at stated rel. error"
+UNIT = "events*points/s"
+PROC = "gg_ttxg"
+NEV = 1 << 20
+ORIGINAL = dict(mt=173.0, wt=0.0, alphas=0.118)
+SEED = 3
+# relative error of a new weight vs the FP64 oracle, per mode (tests/test_gpu_parity.py)
+STATED_ERROR = {"fp64": 1e-12, "mixed": 2e-3}
+
+# Peaks for an ALU-bound kernel, derived from unit counts and the maximum SM clock
+# (148 SMs, 2032 MHz): FP32 = 148 x 128 lanes x 2 flop x 2.032 GHz.  The FP64 figure
+# uses the FP64 FMA issue rate per SM measured by rex_probe_fma.
+SM_COUNT = 148
+SM_MAX_MHZ = 2032.0
+FP32_PEAK = SM_COUNT * 128 * 2 * SM_MAX_MHZ * 1e6
+FP64_FMA_PER_SM_CLK = 2         # rex_probe_fma: 1.18 TFLOP/s at 2032 MHz on 148 SMs -> 1.96
+
+# DRAM traffic per launch from one ncu capture (dram__bytes_read.sum +
+# dram__bytes_write.sum) of the dominant kernel, scaled to the full launch;
+# only reported while the kernel sources still hash to the captured version.
+TRAFFIC = {
+    # ncu --set full of profile_case at 2^19 events (FP64) / 2^20 events (mixed), see profiles/
+    ("gg_ttxg", "fp64"): {"bytes_per_launch": 2 * (97.905920e6 + 2844.738e6), "source_hash": "af82db655ae76f04"},
+    ("gg_ttxg", "mixed"): {"bytes_per_launch": 176.408832e6 + 99.709952e6, "source_hash": "af82db655ae76f04"},
+}
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for rel in ("paper_2510_05100_b300/csrc/kernels_qcd.cu", "paper_2510_05100_b300/csrc/helas.cuh",
+                "paper_2510_05100_b300/csrc/generated/qcd_amplitudes.cuh",
+                "paper_2510_05100_b300/csrc/rex_internal.cuh"):
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+# ----------------------------------------------------------------------------
+# CPU baseline: the oracle as it stands, on the host cores, on a bounded sample
+# ----------------------------------------------------------------------------
+def _oracle_chunk(args):
+    mom, pts = args
+    from oracle import reweight as orw
+    orw.reweight(PROC, mom, np.ones(mom.shape[0]), ORIGINAL, pts)
+    return mom.shape[0]
+
+
+def oracle_throughput(mom_all: np.ndarray, pts, ntasks: int, chunk: int, cores: int, pool=None):
+    """Events*points/s of the oracle over ntasks chunks of ``chunk`` events."""
+    import multiprocessing as mp
+    tasks = [(mom_all[(i * chunk) % (mom_all.shape[0] - chunk):][:chunk].copy(), pts) for i in range(ntasks)]
+    own = pool is None
+    if own:
+        pool = mp.get_context("spawn").Pool(cores)
+    t0 = time.perf_counter()
+    done = sum(pool.map(_oracle_chunk, tasks, chunksize=1))
+    dt = time.perf_counter() - t0
+    if own:
+        pool.close()
+        pool.join()
+    return done * len(pts) / dt, done, dt
+
+
+def _start_pool(cores):
+    import multiprocessing as mp
+    os.environ.setdefault("OMP_NUM_THREADS", "1")
+    os.environ.setdefault("OPENBLAS_NUM_THREADS", "1")
+    os.environ.setdefault("MKL_NUM_THREADS", "1")
+    return mp.get_context("spawn").Pool(cores)
+
+
+# ----------------------------------------------------------------------------
+# clocks during the timed region
+# ----------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, bus_id: str | None):
+        self.bus_id = bus_id
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200"]
+        if self.bus_id:
+            cmd += ["-i", self.bus_id]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        power = [float(r[3]) for r in rows if r[3].replace(".", "").isdigit()]
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows),
+                "power_w_median": statistics.median(power) if power else None}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--mode", choices=["fp64", "mixed"], default="fp64")
+    ap.add_argument("--nev", type=int, default=NEV)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extra-modes", action="store_true")
+    args = ap.parse_args()
+    world, rank, local = rdist.env()
+    if args.impl == "reference":
+        return run_reference(args, world, rank)
+    return run_ours(args, world, rank, local)
+
+
+def grid():
+    return ps.grid_gg_ttxg()
+
+
+def config_block(args, world):
+    return {"workload": f"{PROC}: g g -> t t~ g, {args.nev} events/GPU x 16 param points",
+            "process": PROC, "events_per_gpu": args.nev, "param_points": 16,
+            "grid": "mt in linspace(171,175,4) x alphas in linspace(0.112,0.124,4), mt-major",
+            "original": ORIGINAL, "events": "seeded massive RAMBO, sqrt(s_hat) log-uniform [400, 4000] GeV",
+            "seed": f"{SEED} + rank", "mode": args.mode,
+            "l2": "inputs larger than L2 (momenta 160 MiB + w_out 128 MiB per GPU > 126 MB)",
+            "parallelism": f"replicas x{world} (events sharded per GPU, no collective)"}
+
+
+def run_reference(args, world, rank):
+    """The oracle (FP64, numpy, CPU) timed on the host cores: --impl reference."""
+    if rank != 0:
+        return 0
+    cores = os.cpu_count() or 1
+    pool = _start_pool(cores)
+    mom = ps.make_events(PROC, 1 << 14, SEED)
+    pts = grid()
+    chunk = 256
+    for _ in range(args.warmup):
+        oracle_throughput(mom, pts, cores, chunk, cores, pool)
+    t_total = 0.0
+    n_total = 0
+    for _ in range(args.steps):
+        _, n, dt = oracle_throughput(mom, pts, cores, chunk, cores, pool)
+        t_total += dt
+        n_total += n
+    pool.close()
+    pool.join()
+    value = n_total * len(pts) / t_total
+    sample = f"{args.steps} steps x {cores} chunks x {chunk} events of the {PROC} workload, 16 points each"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": config_block(args, world),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args, world, rank, local):
+    cpu_pool = None
+    cores = os.cpu_count() or 1
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu_pool = _start_pool(cores)          # spawn pool, created before any GPU call
+
+    import torch
+    from paper_2510_05100_b300 import flops as flopmod
+    from paper_2510_05100_b300 import rex
+
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    pts = grid()
+    k = len(pts)
+    mom_np = ps.make_events(PROC, args.nev, rdist.rank_seed(SEED, rank))
+    mom = torch.from_numpy(mom_np).to(dev)
+    w_in = torch.ones(args.nev, dtype=torch.float64, device=dev)
+    w_out = torch.empty((args.nev, k), dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    def max_over_ranks(x: float) -> float:
+        return rdist.max_over_ranks(x, device=dev)
+
+    def time_mode(precision: int, flags: int = 0, steps: int = args.steps, warmup: int = args.warmup,
+                  sampler=None):
+        proc = rex.Process(PROC, precision)
+        proc.set_params(ORIGINAL)
+        if flags:
+            proc.set_flags(flags)
+        for _ in range(warmup):
+            proc.reweight(mom, w_in, pts, w_out=w_out, stream=stream)
+        torch.cuda.synchronize(dev)
+        barrier()
+        torch.cuda.synchronize(dev)
+        if sampler:
+            sampler.start()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        for s in range(steps):
+            ev[s][0].record(stream)
+            proc.reweight(mom, w_in, pts, w_out=w_out, stream=stream)
+            ev[s][1].record(stream)
+        t1.record(stream)
+        torch.cuda.synchronize(dev)
+        barrier()
+        clocks = sampler.stop() if sampler else None
+        total_ms = max_over_ranks(t0.elapsed_time(t1))
+        per_launch = [a.elapsed_time(b) for a, b in ev]
+        proc.close()
+        return total_ms, per_launch, clocks
+
+    props = torch.cuda.get_device_properties(dev)
+    bus = None
+    try:
+        bus = f"{props.pci_domain_id:08X}:{props.pci_bus_id:02X}:{props.pci_device_id:02X}.0"
+    except AttributeError:
+        pass
+    sampler = ClockSampler(bus)
+    precision = rex.FP64 if args.mode == "fp64" else rex.MIXED
+    total_ms, per_launch, clocks = time_mode(precision, sampler=sampler)
+    value = rdist.job_throughput(args.nev * k * args.steps, world, total_ms * 1e-3)
+
+    # ---- e2e through the host-buffer entry point (copies inside the timed region)
+    h_mom = torch.from_numpy(mom_np).pin_memory()
+    h_win = torch.ones(args.nev, dtype=torch.float64).pin_memory()
+    h_out = torch.empty((args.nev, k), dtype=torch.float64).pin_memory()
+    proc = rex.Process(PROC, precision)
+    proc.set_params(ORIGINAL)
+    for _ in range(max(1, args.warmup)):
+        proc.reweight_host(h_mom, h_win, pts, h_out, stream=stream)
+    barrier()
+    e2e_steps = max(3, args.steps // 2)
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        proc.reweight_host(h_mom, h_win, pts, h_out, stream=stream)
+    e2e_s = max_over_ranks(time.perf_counter() - t0)
+    barrier()
+    proc.close()
+    e2e_value = rdist.job_throughput(args.nev * k * e2e_steps, world, e2e_s)
+    h2d = h_mom.numel() * 8 + h_win.numel() * 8
+    d2h = h_out.numel() * 8
+
+    # ---- other modes on the same workload (reported beside the headline)
+    extra = {}
+    if not args.no_extra_modes:
+        for name, prec, fl in (("fp64", rex.FP64, 0), ("mixed", rex.MIXED, 0),
+                               ("fp64_per_point", rex.FP64, rex.FLAG_NO_DEDUPE)):
+            if name == args.mode:
+                continue
+            st = max(2, args.steps // 3)
+            tm, _, _ = time_mode(prec, fl, steps=st, warmup=1)
+            extra[name] = {"value": args.nev * k * st * world / (tm * 1e-3), "unit": UNIT,
+                           "stated_rel_error": STATED_ERROR.get(name.split("_")[0])}
+
+    # ---- roofline of the dominant kernel (the fused gg_ttxg kernel; one launch per step)
+    nmass = 1 + len({p["mt"] for p in pts} - {ORIGINAL["mt"]})
+    fl = flopmod.per_event(PROC, nmass)
+    launch_ms = statistics.mean(per_launch)
+    probe64 = rex.probe_fma(True, stream=stream)
+    probe32 = rex.probe_fma(False, stream=stream)
+    if args.mode == "fp64":
+        flops_launch = fl["total"] * args.nev
+        fma_per_clk = FP64_FMA_PER_SM_CLK
+        peak = SM_COUNT * fma_per_clk * 2 * SM_MAX_MHZ * 1e6
+        pipe = "FP64 FMA"
+    else:
+        flops_launch = fl["amp"] * args.nev
+        peak = FP32_PEAK
+        pipe = "FP32 FMA"
+    achieved = flops_launch / (launch_ms * 1e-3)
+    tr = TRAFFIC.get((PROC, args.mode))
+    traffic = tr["bytes_per_launch"] if tr and tr["source_hash"] == kernel_source_hash() else None
+    roofline = {"bound": "alu", "pipe": pipe, "achieved": achieved / 1e12, "peak": peak / 1e12,
+                "unit": "TFLOP/s", "frac": achieved / peak if peak > 0 else None, "traffic": traffic,
+                "flops_per_launch": flops_launch, "launch_ms": launch_ms,
+                "peak_source": "derived: 148 SMs x FMA units x 2 x 2032 MHz (DESIGN.md)",
+                "probe_fp64_tflops": probe64 / 1e12, "probe_fp32_tflops": probe32 / 1e12,
+                "algorithmic_bytes_per_launch": (args.nev * 5 * 4 * 8 + args.nev * 8 + args.nev * k * 8)}
+
+    cpu = None
+    if cpu_pool is not None:
+        sample_ev = mom_np[: 1 << 14]
+        v, n, dt = oracle_throughput(sample_ev, pts, 4 * cores, 256, cores, cpu_pool)
+        cpu_pool.close()
+        cpu_pool.join()
+        cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"{n} events of the workload x {k} points ({4 * cores} chunks of 256), {dt:.1f} s"}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.mode == "fp64" else "f32+f64",
+                "data": "synthetic", "stated_rel_error": STATED_ERROR[args.mode],
+                "config": config_block(args, world), "clocks": clocks,
+                "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                        "entry_point": "rex_reweight_host (pinned host buffers)"},
+                "gpu_launches": args.steps, "roofline": roofline, "cpu_baseline": cpu, "modes": extra}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -2,23 +2,23 @@
  * rex.h -- C ABI of the B300 (sm_103a) LO matrix-element reweighting library.
  *
  * What the library computes (paper Sec. 3, the weight factorisation
- * w' = w |M'|^2 / |M|^2, and the teaRex normaliser of Sec. 3.1 that maps 1/0 to 0):
+ * w' = w |M'|^2 / |M|^2, and the teaRex normaliser of Sec. 3.1.1 that maps 1/0 to 0):
  * for every event e of one subprocess and every parameter point j,
  *
  *     w_out[e][j] = w_in[e] * |M(p_e; theta_j)|^2 / |M(p_e; theta_0)|^2
  *                 = 0                       if |M(p_e; theta_0)|^2 == 0,
  *
- * where |M|^2 is the tree-level, helicity-summed (Sec. 4.1: only
+ * where |M|^2 is the tree-level, helicity-summed (Sec. 4.1.2: only
  * helicity-summed reweighting) and colour-summed squared matrix element,
  * averaged over initial spins and colours, theta_0 the parameter point set
  * with rex_set_params and theta_j the j-th entry of param_sets.
  *
  * Momenta enter exactly as the paper's amplitude bridge receives them
- * (Sec. 4.2: only the particle momenta, the flat per-process momentum
+ * (Sec. 4.1.3: only the particle momenta, the flat per-process momentum
  * vector): one flat FP64 array [nev][npart][4] with components
  * (E, px, py, pz) per particle, particles in the order the process name
  * states.  Events must already be sorted into the subprocess and their
- * partons reordered to that order (Rex's eventBelongs, Sec. 2).
+ * partons reordered to that order (Rex's eventBelongs, Sec. 2.1.2).
  *
  * Conventions for all calls:
  *  - return value 0 = success, negative = error (REX_E*); rex_last_error()
@@ -48,7 +48,7 @@ extern "C" {
 #define REX_ENOMEM (-4)      /* a library-owned allocation failed */
 #define REX_EUNSUPPORTED (-5) /* precision mode not available for this process */
 
-/* Precision modes (the paper's fptype option, Sec. 4.1, re-cut for B300):
+/* Precision modes (the paper's fptype option, Sec. 4.1.2, re-cut for B300):
  * REX_FP64: every step in FP64.
  * REX_MIXED: wavefunctions and amplitudes in FP32, colour sum on tensor
  *            cores (FP16 operands, FP32 accumulation), helicity sum and
@@ -91,13 +91,13 @@ int rex_process_npart(const rex_proc *proc);
 int rex_set_flags(rex_proc *proc, unsigned flags);
 
 /* Set the original parameter point theta_0 (host pointer, copied).
- * This is the point the input weights were generated at (paper Sec. 3.1:
+ * This is the point the input weights were generated at (paper Sec. 3.1.1:
  * the normaliser is |M|^2 at the original card).
  * Errors: REX_EINVAL (null pointer, non-positive mass or coupling). */
 int rex_set_params(rex_proc *proc, const rex_params *original);
 
 /* Reweight nev events to k parameter points (paper Sec. 3, the factorised
- * weight w' = w |M'|^2/|M|^2; Sec. 3.1 normaliser 1/0 -> 0).
+ * weight w' = w |M'|^2/|M|^2; Sec. 3.1.1 normaliser 1/0 -> 0).
  *   momenta    device, [nev][npart][4] FP64, (E, px, py, pz)
  *   w_in       device, [nev] FP64 original weights
  *   param_sets host, [k] points (copied before return)
@@ -130,6 +130,13 @@ void rex_free_process(rex_proc *proc);
 
 /* Message of the calling thread's most recent error ("" if none). */
 const char *rex_last_error(void);
+
+/* Measurement tooling (the paper has no counterpart): issue-rate probe of
+ * the FP64 (fp64 != 0) or FP32 fused multiply-add pipe of the current device.
+ * Runs a few tens of milliseconds of independent FMA chains on every SM,
+ * synchronises stream, and writes the best observed rate in flop/s
+ * (an FMA counts two flops).  Errors: REX_EINVAL (null output), REX_ECUDA. */
+int rex_probe_fma(int fp64, double *flops_per_second, void *stream);
 
 /* Library version string. */
 const char *rex_version(void);

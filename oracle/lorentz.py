@@ -15,7 +15,7 @@ from the Cayley-Hamilton identity sqrt(M) = (M + m 1) / sqrt(tr M + 2 m).
 
 Mass used in external spinors when a parameter point changes the mass while
 the momenta are kept (the paper's reweighting passes only momenta to the
-amplitude, Sec. 4.2): the spinor is the standard one of the on-shell momentum
+amplitude, Sec. 4.1.3): the spinor is the standard one of the on-shell momentum
     p~ = (E~, |p~| p-hat),  E~ + |p~| = E + |p|,  E~ - |p~| = m^2 / (E + |p|),
 i.e. same direction and same light-cone component E + |p| as p, mass m.
 When p^2 = m^2 this is p itself.

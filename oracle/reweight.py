@@ -1,7 +1,7 @@
 """Reweighting epilogue and process dispatch (oracle).
 
 w'_{e,j} = w_e |M(p_e; theta_j)|^2 / |M(p_e; theta_0)|^2  (paper Sec. 3, the
-weight factorisation), with the teaRex normaliser convention (Sec. 3.1):
+weight factorisation), with the teaRex normaliser convention (Sec. 3.1.1):
 the normaliser is 1/|M|^2 with 1/0 mapped to 0, so an event whose original
 |M|^2 is zero gets new weights 0.
 """

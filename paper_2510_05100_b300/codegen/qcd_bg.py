@@ -152,7 +152,9 @@ def emit_process(name: str, ngluon: int) -> str:
     # ---------------- quark line for one mass: sum over top/antitop helicities
     w("// sum over top and antitop helicities of sum_{s,s'} conj(A_s) Cint_{ss'} A_s'", 0)
     w("// for one (mass, width); Cint = C * COLOUR_DEN.  WIDTH selects complex denominators.", 0)
-    w(f"template <typename R, typename ACC, bool WIDTH>", 0)
+    w("// The quadratic form of one helicity is evaluated in CS (a positive-definite form:", 0)
+    w("// no cancellation), and the helicity sum is accumulated in ACC.", 0)
+    w(f"template <typename R, typename ACC, bool WIDTH, typename CS = ACC>", 0)
     w(f"__device__ __forceinline__ ACC {name}_quark_line(const {name}_gluons<R>& st, "
       f"const R (&pt)[4], const R (&ptb)[4], R mt, R wt) {{", 0)
     w("ACC total = ACC(0);")
@@ -197,18 +199,18 @@ def emit_process(name: str, ngluon: int) -> str:
         w("}", 2)
     w("#pragma unroll", 0)
     w("for (int ht = 0; ht < 2; ++ht) {", 2)
-    w("ACC s = ACC(0);", 3)
+    w("CS s = CS(0);", 3)
     for i in range(nf):
-        w(f"s += ACC({cint[i][i]}) * (ACC(A[ht][{i}].re) * ACC(A[ht][{i}].re) + "
-          f"ACC(A[ht][{i}].im) * ACC(A[ht][{i}].im));", 3)
+        w(f"s += CS({cint[i][i]}) * (CS(A[ht][{i}].re) * CS(A[ht][{i}].re) + "
+          f"CS(A[ht][{i}].im) * CS(A[ht][{i}].im));", 3)
     for i in range(nf):
         for j in range(i + 1, nf):
             c = cint[i][j]
             if c == 0:
                 continue
-            w(f"s += ACC({2 * c}) * (ACC(A[ht][{i}].re) * ACC(A[ht][{j}].re) + "
-              f"ACC(A[ht][{i}].im) * ACC(A[ht][{j}].im));", 3)
-    w("total += s;", 3)
+            w(f"s += CS({2 * c}) * (CS(A[ht][{i}].re) * CS(A[ht][{j}].re) + "
+              f"CS(A[ht][{i}].im) * CS(A[ht][{j}].im));", 3)
+    w("total += ACC(s);", 3)
     w("}", 2)
     w("}")
     w("return total;")

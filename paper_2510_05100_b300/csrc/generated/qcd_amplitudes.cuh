@@ -59,7 +59,9 @@ __device__ __forceinline__ void gg_ttx_gluon_state(const R (&pg)[2][4], const R 
 
 // sum over top and antitop helicities of sum_{s,s'} conj(A_s) Cint_{ss'} A_s'
 // for one (mass, width); Cint = C * COLOUR_DEN.  WIDTH selects complex denominators.
-template <typename R, typename ACC, bool WIDTH>
+// The quadratic form of one helicity is evaluated in CS (a positive-definite form:
+// no cancellation), and the helicity sum is accumulated in ACC.
+template <typename R, typename ACC, bool WIDTH, typename CS = ACC>
 __device__ __forceinline__ ACC gg_ttx_quark_line(const gg_ttx_gluons<R>& st, const R (&pt)[4], const R (&ptb)[4], R mt, R wt) {
   ACC total = ACC(0);
   const R d0 = mdot(st.Q0, st.Q0) - mt * mt;
@@ -106,11 +108,11 @@ __device__ __forceinline__ ACC gg_ttx_quark_line(const gg_ttx_gluons<R>& st, con
     }
 #pragma unroll
     for (int ht = 0; ht < 2; ++ht) {
-      ACC s = ACC(0);
-      s += ACC(16) * (ACC(A[ht][0].re) * ACC(A[ht][0].re) + ACC(A[ht][0].im) * ACC(A[ht][0].im));
-      s += ACC(16) * (ACC(A[ht][1].re) * ACC(A[ht][1].re) + ACC(A[ht][1].im) * ACC(A[ht][1].im));
-      s += ACC(-4) * (ACC(A[ht][0].re) * ACC(A[ht][1].re) + ACC(A[ht][0].im) * ACC(A[ht][1].im));
-      total += s;
+      CS s = CS(0);
+      s += CS(16) * (CS(A[ht][0].re) * CS(A[ht][0].re) + CS(A[ht][0].im) * CS(A[ht][0].im));
+      s += CS(16) * (CS(A[ht][1].re) * CS(A[ht][1].re) + CS(A[ht][1].im) * CS(A[ht][1].im));
+      s += CS(-4) * (CS(A[ht][0].re) * CS(A[ht][1].re) + CS(A[ht][0].im) * CS(A[ht][1].im));
+      total += ACC(s);
     }
   }
   return total;
@@ -248,7 +250,9 @@ __device__ __forceinline__ void gg_ttxg_gluon_state(const R (&pg)[3][4], const R
 
 // sum over top and antitop helicities of sum_{s,s'} conj(A_s) Cint_{ss'} A_s'
 // for one (mass, width); Cint = C * COLOUR_DEN.  WIDTH selects complex denominators.
-template <typename R, typename ACC, bool WIDTH>
+// The quadratic form of one helicity is evaluated in CS (a positive-definite form:
+// no cancellation), and the helicity sum is accumulated in ACC.
+template <typename R, typename ACC, bool WIDTH, typename CS = ACC>
 __device__ __forceinline__ ACC gg_ttxg_quark_line(const gg_ttxg_gluons<R>& st, const R (&pt)[4], const R (&ptb)[4], R mt, R wt) {
   ACC total = ACC(0);
   const R d0 = mdot(st.Q0, st.Q0) - mt * mt;
@@ -396,29 +400,29 @@ __device__ __forceinline__ ACC gg_ttxg_quark_line(const gg_ttxg_gluons<R>& st, c
     }
 #pragma unroll
     for (int ht = 0; ht < 2; ++ht) {
-      ACC s = ACC(0);
-      s += ACC(64) * (ACC(A[ht][0].re) * ACC(A[ht][0].re) + ACC(A[ht][0].im) * ACC(A[ht][0].im));
-      s += ACC(64) * (ACC(A[ht][1].re) * ACC(A[ht][1].re) + ACC(A[ht][1].im) * ACC(A[ht][1].im));
-      s += ACC(64) * (ACC(A[ht][2].re) * ACC(A[ht][2].re) + ACC(A[ht][2].im) * ACC(A[ht][2].im));
-      s += ACC(64) * (ACC(A[ht][3].re) * ACC(A[ht][3].re) + ACC(A[ht][3].im) * ACC(A[ht][3].im));
-      s += ACC(64) * (ACC(A[ht][4].re) * ACC(A[ht][4].re) + ACC(A[ht][4].im) * ACC(A[ht][4].im));
-      s += ACC(64) * (ACC(A[ht][5].re) * ACC(A[ht][5].re) + ACC(A[ht][5].im) * ACC(A[ht][5].im));
-      s += ACC(-16) * (ACC(A[ht][0].re) * ACC(A[ht][1].re) + ACC(A[ht][0].im) * ACC(A[ht][1].im));
-      s += ACC(-16) * (ACC(A[ht][0].re) * ACC(A[ht][2].re) + ACC(A[ht][0].im) * ACC(A[ht][2].im));
-      s += ACC(2) * (ACC(A[ht][0].re) * ACC(A[ht][3].re) + ACC(A[ht][0].im) * ACC(A[ht][3].im));
-      s += ACC(2) * (ACC(A[ht][0].re) * ACC(A[ht][4].re) + ACC(A[ht][0].im) * ACC(A[ht][4].im));
-      s += ACC(20) * (ACC(A[ht][0].re) * ACC(A[ht][5].re) + ACC(A[ht][0].im) * ACC(A[ht][5].im));
-      s += ACC(2) * (ACC(A[ht][1].re) * ACC(A[ht][2].re) + ACC(A[ht][1].im) * ACC(A[ht][2].im));
-      s += ACC(20) * (ACC(A[ht][1].re) * ACC(A[ht][3].re) + ACC(A[ht][1].im) * ACC(A[ht][3].im));
-      s += ACC(-16) * (ACC(A[ht][1].re) * ACC(A[ht][4].re) + ACC(A[ht][1].im) * ACC(A[ht][4].im));
-      s += ACC(2) * (ACC(A[ht][1].re) * ACC(A[ht][5].re) + ACC(A[ht][1].im) * ACC(A[ht][5].im));
-      s += ACC(-16) * (ACC(A[ht][2].re) * ACC(A[ht][3].re) + ACC(A[ht][2].im) * ACC(A[ht][3].im));
-      s += ACC(20) * (ACC(A[ht][2].re) * ACC(A[ht][4].re) + ACC(A[ht][2].im) * ACC(A[ht][4].im));
-      s += ACC(2) * (ACC(A[ht][2].re) * ACC(A[ht][5].re) + ACC(A[ht][2].im) * ACC(A[ht][5].im));
-      s += ACC(2) * (ACC(A[ht][3].re) * ACC(A[ht][4].re) + ACC(A[ht][3].im) * ACC(A[ht][4].im));
-      s += ACC(-16) * (ACC(A[ht][3].re) * ACC(A[ht][5].re) + ACC(A[ht][3].im) * ACC(A[ht][5].im));
-      s += ACC(-16) * (ACC(A[ht][4].re) * ACC(A[ht][5].re) + ACC(A[ht][4].im) * ACC(A[ht][5].im));
-      total += s;
+      CS s = CS(0);
+      s += CS(64) * (CS(A[ht][0].re) * CS(A[ht][0].re) + CS(A[ht][0].im) * CS(A[ht][0].im));
+      s += CS(64) * (CS(A[ht][1].re) * CS(A[ht][1].re) + CS(A[ht][1].im) * CS(A[ht][1].im));
+      s += CS(64) * (CS(A[ht][2].re) * CS(A[ht][2].re) + CS(A[ht][2].im) * CS(A[ht][2].im));
+      s += CS(64) * (CS(A[ht][3].re) * CS(A[ht][3].re) + CS(A[ht][3].im) * CS(A[ht][3].im));
+      s += CS(64) * (CS(A[ht][4].re) * CS(A[ht][4].re) + CS(A[ht][4].im) * CS(A[ht][4].im));
+      s += CS(64) * (CS(A[ht][5].re) * CS(A[ht][5].re) + CS(A[ht][5].im) * CS(A[ht][5].im));
+      s += CS(-16) * (CS(A[ht][0].re) * CS(A[ht][1].re) + CS(A[ht][0].im) * CS(A[ht][1].im));
+      s += CS(-16) * (CS(A[ht][0].re) * CS(A[ht][2].re) + CS(A[ht][0].im) * CS(A[ht][2].im));
+      s += CS(2) * (CS(A[ht][0].re) * CS(A[ht][3].re) + CS(A[ht][0].im) * CS(A[ht][3].im));
+      s += CS(2) * (CS(A[ht][0].re) * CS(A[ht][4].re) + CS(A[ht][0].im) * CS(A[ht][4].im));
+      s += CS(20) * (CS(A[ht][0].re) * CS(A[ht][5].re) + CS(A[ht][0].im) * CS(A[ht][5].im));
+      s += CS(2) * (CS(A[ht][1].re) * CS(A[ht][2].re) + CS(A[ht][1].im) * CS(A[ht][2].im));
+      s += CS(20) * (CS(A[ht][1].re) * CS(A[ht][3].re) + CS(A[ht][1].im) * CS(A[ht][3].im));
+      s += CS(-16) * (CS(A[ht][1].re) * CS(A[ht][4].re) + CS(A[ht][1].im) * CS(A[ht][4].im));
+      s += CS(2) * (CS(A[ht][1].re) * CS(A[ht][5].re) + CS(A[ht][1].im) * CS(A[ht][5].im));
+      s += CS(-16) * (CS(A[ht][2].re) * CS(A[ht][3].re) + CS(A[ht][2].im) * CS(A[ht][3].im));
+      s += CS(20) * (CS(A[ht][2].re) * CS(A[ht][4].re) + CS(A[ht][2].im) * CS(A[ht][4].im));
+      s += CS(2) * (CS(A[ht][2].re) * CS(A[ht][5].re) + CS(A[ht][2].im) * CS(A[ht][5].im));
+      s += CS(2) * (CS(A[ht][3].re) * CS(A[ht][4].re) + CS(A[ht][3].im) * CS(A[ht][4].im));
+      s += CS(-16) * (CS(A[ht][3].re) * CS(A[ht][5].re) + CS(A[ht][3].im) * CS(A[ht][5].im));
+      s += CS(-16) * (CS(A[ht][4].re) * CS(A[ht][5].re) + CS(A[ht][4].im) * CS(A[ht][5].im));
+      total += ACC(s);
     }
   }
   return total;
@@ -911,7 +915,9 @@ __device__ __forceinline__ void gg_ttxgg_gluon_state(const R (&pg)[4][4], const 
 
 // sum over top and antitop helicities of sum_{s,s'} conj(A_s) Cint_{ss'} A_s'
 // for one (mass, width); Cint = C * COLOUR_DEN.  WIDTH selects complex denominators.
-template <typename R, typename ACC, bool WIDTH>
+// The quadratic form of one helicity is evaluated in CS (a positive-definite form:
+// no cancellation), and the helicity sum is accumulated in ACC.
+template <typename R, typename ACC, bool WIDTH, typename CS = ACC>
 __device__ __forceinline__ ACC gg_ttxgg_quark_line(const gg_ttxgg_gluons<R>& st, const R (&pt)[4], const R (&ptb)[4], R mt, R wt) {
   ACC total = ACC(0);
   const R d0 = mdot(st.Q0, st.Q0) - mt * mt;
@@ -1522,308 +1528,308 @@ __device__ __forceinline__ ACC gg_ttxgg_quark_line(const gg_ttxgg_gluons<R>& st,
     }
 #pragma unroll
     for (int ht = 0; ht < 2; ++ht) {
-      ACC s = ACC(0);
-      s += ACC(512) * (ACC(A[ht][0].re) * ACC(A[ht][0].re) + ACC(A[ht][0].im) * ACC(A[ht][0].im));
-      s += ACC(512) * (ACC(A[ht][1].re) * ACC(A[ht][1].re) + ACC(A[ht][1].im) * ACC(A[ht][1].im));
-      s += ACC(512) * (ACC(A[ht][2].re) * ACC(A[ht][2].re) + ACC(A[ht][2].im) * ACC(A[ht][2].im));
-      s += ACC(512) * (ACC(A[ht][3].re) * ACC(A[ht][3].re) + ACC(A[ht][3].im) * ACC(A[ht][3].im));
-      s += ACC(512) * (ACC(A[ht][4].re) * ACC(A[ht][4].re) + ACC(A[ht][4].im) * ACC(A[ht][4].im));
-      s += ACC(512) * (ACC(A[ht][5].re) * ACC(A[ht][5].re) + ACC(A[ht][5].im) * ACC(A[ht][5].im));
-      s += ACC(512) * (ACC(A[ht][6].re) * ACC(A[ht][6].re) + ACC(A[ht][6].im) * ACC(A[ht][6].im));
-      s += ACC(512) * (ACC(A[ht][7].re) * ACC(A[ht][7].re) + ACC(A[ht][7].im) * ACC(A[ht][7].im));
-      s += ACC(512) * (ACC(A[ht][8].re) * ACC(A[ht][8].re) + ACC(A[ht][8].im) * ACC(A[ht][8].im));
-      s += ACC(512) * (ACC(A[ht][9].re) * ACC(A[ht][9].re) + ACC(A[ht][9].im) * ACC(A[ht][9].im));
-      s += ACC(512) * (ACC(A[ht][10].re) * ACC(A[ht][10].re) + ACC(A[ht][10].im) * ACC(A[ht][10].im));
-      s += ACC(512) * (ACC(A[ht][11].re) * ACC(A[ht][11].re) + ACC(A[ht][11].im) * ACC(A[ht][11].im));
-      s += ACC(512) * (ACC(A[ht][12].re) * ACC(A[ht][12].re) + ACC(A[ht][12].im) * ACC(A[ht][12].im));
-      s += ACC(512) * (ACC(A[ht][13].re) * ACC(A[ht][13].re) + ACC(A[ht][13].im) * ACC(A[ht][13].im));
-      s += ACC(512) * (ACC(A[ht][14].re) * ACC(A[ht][14].re) + ACC(A[ht][14].im) * ACC(A[ht][14].im));
-      s += ACC(512) * (ACC(A[ht][15].re) * ACC(A[ht][15].re) + ACC(A[ht][15].im) * ACC(A[ht][15].im));
-      s += ACC(512) * (ACC(A[ht][16].re) * ACC(A[ht][16].re) + ACC(A[ht][16].im) * ACC(A[ht][16].im));
-      s += ACC(512) * (ACC(A[ht][17].re) * ACC(A[ht][17].re) + ACC(A[ht][17].im) * ACC(A[ht][17].im));
-      s += ACC(512) * (ACC(A[ht][18].re) * ACC(A[ht][18].re) + ACC(A[ht][18].im) * ACC(A[ht][18].im));
-      s += ACC(512) * (ACC(A[ht][19].re) * ACC(A[ht][19].re) + ACC(A[ht][19].im) * ACC(A[ht][19].im));
-      s += ACC(512) * (ACC(A[ht][20].re) * ACC(A[ht][20].re) + ACC(A[ht][20].im) * ACC(A[ht][20].im));
-      s += ACC(512) * (ACC(A[ht][21].re) * ACC(A[ht][21].re) + ACC(A[ht][21].im) * ACC(A[ht][21].im));
-      s += ACC(512) * (ACC(A[ht][22].re) * ACC(A[ht][22].re) + ACC(A[ht][22].im) * ACC(A[ht][22].im));
-      s += ACC(512) * (ACC(A[ht][23].re) * ACC(A[ht][23].re) + ACC(A[ht][23].im) * ACC(A[ht][23].im));
-      s += ACC(-128) * (ACC(A[ht][0].re) * ACC(A[ht][1].re) + ACC(A[ht][0].im) * ACC(A[ht][1].im));
-      s += ACC(-128) * (ACC(A[ht][0].re) * ACC(A[ht][2].re) + ACC(A[ht][0].im) * ACC(A[ht][2].im));
-      s += ACC(16) * (ACC(A[ht][0].re) * ACC(A[ht][3].re) + ACC(A[ht][0].im) * ACC(A[ht][3].im));
-      s += ACC(16) * (ACC(A[ht][0].re) * ACC(A[ht][4].re) + ACC(A[ht][0].im) * ACC(A[ht][4].im));
-      s += ACC(160) * (ACC(A[ht][0].re) * ACC(A[ht][5].re) + ACC(A[ht][0].im) * ACC(A[ht][5].im));
-      s += ACC(-128) * (ACC(A[ht][0].re) * ACC(A[ht][6].re) + ACC(A[ht][0].im) * ACC(A[ht][6].im));
-      s += ACC(16) * (ACC(A[ht][0].re) * ACC(A[ht][7].re) + ACC(A[ht][0].im) * ACC(A[ht][7].im));
-      s += ACC(16) * (ACC(A[ht][0].re) * ACC(A[ht][8].re) + ACC(A[ht][0].im) * ACC(A[ht][8].im));
-      s += ACC(-2) * (ACC(A[ht][0].re) * ACC(A[ht][9].re) + ACC(A[ht][0].im) * ACC(A[ht][9].im));
-      s += ACC(-2) * (ACC(A[ht][0].re) * ACC(A[ht][10].re) + ACC(A[ht][0].im) * ACC(A[ht][10].im));
-      s += ACC(-20) * (ACC(A[ht][0].re) * ACC(A[ht][11].re) + ACC(A[ht][0].im) * ACC(A[ht][11].im));
-      s += ACC(16) * (ACC(A[ht][0].re) * ACC(A[ht][12].re) + ACC(A[ht][0].im) * ACC(A[ht][12].im));
-      s += ACC(-2) * (ACC(A[ht][0].re) * ACC(A[ht][13].re) + ACC(A[ht][0].im) * ACC(A[ht][13].im));
-      s += ACC(160) * (ACC(A[ht][0].re) * ACC(A[ht][14].re) + ACC(A[ht][0].im) * ACC(A[ht][14].im));
-      s += ACC(-20) * (ACC(A[ht][0].re) * ACC(A[ht][15].re) + ACC(A[ht][0].im) * ACC(A[ht][15].im));
-      s += ACC(142) * (ACC(A[ht][0].re) * ACC(A[ht][16].re) + ACC(A[ht][0].im) * ACC(A[ht][16].im));
-      s += ACC(124) * (ACC(A[ht][0].re) * ACC(A[ht][17].re) + ACC(A[ht][0].im) * ACC(A[ht][17].im));
-      s += ACC(-2) * (ACC(A[ht][0].re) * ACC(A[ht][18].re) + ACC(A[ht][0].im) * ACC(A[ht][18].im));
-      s += ACC(-20) * (ACC(A[ht][0].re) * ACC(A[ht][19].re) + ACC(A[ht][0].im) * ACC(A[ht][19].im));
-      s += ACC(-20) * (ACC(A[ht][0].re) * ACC(A[ht][20].re) + ACC(A[ht][0].im) * ACC(A[ht][20].im));
-      s += ACC(124) * (ACC(A[ht][0].re) * ACC(A[ht][21].re) + ACC(A[ht][0].im) * ACC(A[ht][21].im));
-      s += ACC(124) * (ACC(A[ht][0].re) * ACC(A[ht][22].re) + ACC(A[ht][0].im) * ACC(A[ht][22].im));
-      s += ACC(-56) * (ACC(A[ht][0].re) * ACC(A[ht][23].re) + ACC(A[ht][0].im) * ACC(A[ht][23].im));
-      s += ACC(16) * (ACC(A[ht][1].re) * ACC(A[ht][2].re) + ACC(A[ht][1].im) * ACC(A[ht][2].im));
-      s += ACC(160) * (ACC(A[ht][1].re) * ACC(A[ht][3].re) + ACC(A[ht][1].im) * ACC(A[ht][3].im));
-      s += ACC(-128) * (ACC(A[ht][1].re) * ACC(A[ht][4].re) + ACC(A[ht][1].im) * ACC(A[ht][4].im));
-      s += ACC(16) * (ACC(A[ht][1].re) * ACC(A[ht][5].re) + ACC(A[ht][1].im) * ACC(A[ht][5].im));
-      s += ACC(16) * (ACC(A[ht][1].re) * ACC(A[ht][6].re) + ACC(A[ht][1].im) * ACC(A[ht][6].im));
-      s += ACC(-128) * (ACC(A[ht][1].re) * ACC(A[ht][7].re) + ACC(A[ht][1].im) * ACC(A[ht][7].im));
-      s += ACC(-2) * (ACC(A[ht][1].re) * ACC(A[ht][8].re) + ACC(A[ht][1].im) * ACC(A[ht][8].im));
-      s += ACC(-20) * (ACC(A[ht][1].re) * ACC(A[ht][9].re) + ACC(A[ht][1].im) * ACC(A[ht][9].im));
-      s += ACC(16) * (ACC(A[ht][1].re) * ACC(A[ht][10].re) + ACC(A[ht][1].im) * ACC(A[ht][10].im));
-      s += ACC(-2) * (ACC(A[ht][1].re) * ACC(A[ht][11].re) + ACC(A[ht][1].im) * ACC(A[ht][11].im));
-      s += ACC(-2) * (ACC(A[ht][1].re) * ACC(A[ht][12].re) + ACC(A[ht][1].im) * ACC(A[ht][12].im));
-      s += ACC(-20) * (ACC(A[ht][1].re) * ACC(A[ht][13].re) + ACC(A[ht][1].im) * ACC(A[ht][13].im));
-      s += ACC(-20) * (ACC(A[ht][1].re) * ACC(A[ht][14].re) + ACC(A[ht][1].im) * ACC(A[ht][14].im));
-      s += ACC(124) * (ACC(A[ht][1].re) * ACC(A[ht][15].re) + ACC(A[ht][1].im) * ACC(A[ht][15].im));
-      s += ACC(124) * (ACC(A[ht][1].re) * ACC(A[ht][16].re) + ACC(A[ht][1].im) * ACC(A[ht][16].im));
-      s += ACC(-56) * (ACC(A[ht][1].re) * ACC(A[ht][17].re) + ACC(A[ht][1].im) * ACC(A[ht][17].im));
-      s += ACC(16) * (ACC(A[ht][1].re) * ACC(A[ht][18].re) + ACC(A[ht][1].im) * ACC(A[ht][18].im));
-      s += ACC(-2) * (ACC(A[ht][1].re) * ACC(A[ht][19].re) + ACC(A[ht][1].im) * ACC(A[ht][19].im));
-      s += ACC(160) * (ACC(A[ht][1].re) * ACC(A[ht][20].re) + ACC(A[ht][1].im) * ACC(A[ht][20].im));
-      s += ACC(-20) * (ACC(A[ht][1].re) * ACC(A[ht][21].re) + ACC(A[ht][1].im) * ACC(A[ht][21].im));
-      s += ACC(142) * (ACC(A[ht][1].re) * ACC(A[ht][22].re) + ACC(A[ht][1].im) * ACC(A[ht][22].im));
-      s += ACC(124) * (ACC(A[ht][1].re) * ACC(A[ht][23].re) + ACC(A[ht][1].im) * ACC(A[ht][23].im));
-      s += ACC(-128) * (ACC(A[ht][2].re) * ACC(A[ht][3].re) + ACC(A[ht][2].im) * ACC(A[ht][3].im));
-      s += ACC(160) * (ACC(A[ht][2].re) * ACC(A[ht][4].re) + ACC(A[ht][2].im) * ACC(A[ht][4].im));
-      s += ACC(16) * (ACC(A[ht][2].re) * ACC(A[ht][5].re) + ACC(A[ht][2].im) * ACC(A[ht][5].im));
-      s += ACC(16) * (ACC(A[ht][2].re) * ACC(A[ht][6].re) + ACC(A[ht][2].im) * ACC(A[ht][6].im));
-      s += ACC(-2) * (ACC(A[ht][2].re) * ACC(A[ht][7].re) + ACC(A[ht][2].im) * ACC(A[ht][7].im));
-      s += ACC(160) * (ACC(A[ht][2].re) * ACC(A[ht][8].re) + ACC(A[ht][2].im) * ACC(A[ht][8].im));
-      s += ACC(-20) * (ACC(A[ht][2].re) * ACC(A[ht][9].re) + ACC(A[ht][2].im) * ACC(A[ht][9].im));
-      s += ACC(142) * (ACC(A[ht][2].re) * ACC(A[ht][10].re) + ACC(A[ht][2].im) * ACC(A[ht][10].im));
-      s += ACC(124) * (ACC(A[ht][2].re) * ACC(A[ht][11].re) + ACC(A[ht][2].im) * ACC(A[ht][11].im));
-      s += ACC(-128) * (ACC(A[ht][2].re) * ACC(A[ht][12].re) + ACC(A[ht][2].im) * ACC(A[ht][12].im));
-      s += ACC(16) * (ACC(A[ht][2].re) * ACC(A[ht][13].re) + ACC(A[ht][2].im) * ACC(A[ht][13].im));
-      s += ACC(16) * (ACC(A[ht][2].re) * ACC(A[ht][14].re) + ACC(A[ht][2].im) * ACC(A[ht][14].im));
-      s += ACC(-2) * (ACC(A[ht][2].re) * ACC(A[ht][15].re) + ACC(A[ht][2].im) * ACC(A[ht][15].im));
-      s += ACC(-2) * (ACC(A[ht][2].re) * ACC(A[ht][16].re) + ACC(A[ht][2].im) * ACC(A[ht][16].im));
-      s += ACC(-20) * (ACC(A[ht][2].re) * ACC(A[ht][17].re) + ACC(A[ht][2].im) * ACC(A[ht][17].im));
-      s += ACC(-20) * (ACC(A[ht][2].re) * ACC(A[ht][18].re) + ACC(A[ht][2].im) * ACC(A[ht][18].im));
-      s += ACC(-2) * (ACC(A[ht][2].re) * ACC(A[ht][19].re) + ACC(A[ht][2].im) * ACC(A[ht][19].im));
-      s += ACC(124) * (ACC(A[ht][2].re) * ACC(A[ht][20].re) + ACC(A[ht][2].im) * ACC(A[ht][20].im));
-      s += ACC(-56) * (ACC(A[ht][2].re) * ACC(A[ht][21].re) + ACC(A[ht][2].im) * ACC(A[ht][21].im));
-      s += ACC(-20) * (ACC(A[ht][2].re) * ACC(A[ht][22].re) + ACC(A[ht][2].im) * ACC(A[ht][22].im));
-      s += ACC(124) * (ACC(A[ht][2].re) * ACC(A[ht][23].re) + ACC(A[ht][2].im) * ACC(A[ht][23].im));
-      s += ACC(16) * (ACC(A[ht][3].re) * ACC(A[ht][4].re) + ACC(A[ht][3].im) * ACC(A[ht][4].im));
-      s += ACC(-128) * (ACC(A[ht][3].re) * ACC(A[ht][5].re) + ACC(A[ht][3].im) * ACC(A[ht][5].im));
-      s += ACC(-2) * (ACC(A[ht][3].re) * ACC(A[ht][6].re) + ACC(A[ht][3].im) * ACC(A[ht][6].im));
-      s += ACC(-20) * (ACC(A[ht][3].re) * ACC(A[ht][7].re) + ACC(A[ht][3].im) * ACC(A[ht][7].im));
-      s += ACC(-20) * (ACC(A[ht][3].re) * ACC(A[ht][8].re) + ACC(A[ht][3].im) * ACC(A[ht][8].im));
-      s += ACC(124) * (ACC(A[ht][3].re) * ACC(A[ht][9].re) + ACC(A[ht][3].im) * ACC(A[ht][9].im));
-      s += ACC(124) * (ACC(A[ht][3].re) * ACC(A[ht][10].re) + ACC(A[ht][3].im) * ACC(A[ht][10].im));
-      s += ACC(-56) * (ACC(A[ht][3].re) * ACC(A[ht][11].re) + ACC(A[ht][3].im) * ACC(A[ht][11].im));
-      s += ACC(16) * (ACC(A[ht][3].re) * ACC(A[ht][12].re) + ACC(A[ht][3].im) * ACC(A[ht][12].im));
-      s += ACC(-128) * (ACC(A[ht][3].re) * ACC(A[ht][13].re) + ACC(A[ht][3].im) * ACC(A[ht][13].im));
-      s += ACC(-2) * (ACC(A[ht][3].re) * ACC(A[ht][14].re) + ACC(A[ht][3].im) * ACC(A[ht][14].im));
-      s += ACC(-20) * (ACC(A[ht][3].re) * ACC(A[ht][15].re) + ACC(A[ht][3].im) * ACC(A[ht][15].im));
-      s += ACC(16) * (ACC(A[ht][3].re) * ACC(A[ht][16].re) + ACC(A[ht][3].im) * ACC(A[ht][16].im));
-      s += ACC(-2) * (ACC(A[ht][3].re) * ACC(A[ht][17].re) + ACC(A[ht][3].im) * ACC(A[ht][17].im));
-      s += ACC(-2) * (ACC(A[ht][3].re) * ACC(A[ht][18].re) + ACC(A[ht][3].im) * ACC(A[ht][18].im));
-      s += ACC(16) * (ACC(A[ht][3].re) * ACC(A[ht][19].re) + ACC(A[ht][3].im) * ACC(A[ht][19].im));
-      s += ACC(142) * (ACC(A[ht][3].re) * ACC(A[ht][20].re) + ACC(A[ht][3].im) * ACC(A[ht][20].im));
-      s += ACC(124) * (ACC(A[ht][3].re) * ACC(A[ht][21].re) + ACC(A[ht][3].im) * ACC(A[ht][21].im));
-      s += ACC(160) * (ACC(A[ht][3].re) * ACC(A[ht][22].re) + ACC(A[ht][3].im) * ACC(A[ht][22].im));
-      s += ACC(-20) * (ACC(A[ht][3].re) * ACC(A[ht][23].re) + ACC(A[ht][3].im) * ACC(A[ht][23].im));
-      s += ACC(-128) * (ACC(A[ht][4].re) * ACC(A[ht][5].re) + ACC(A[ht][4].im) * ACC(A[ht][5].im));
-      s += ACC(-2) * (ACC(A[ht][4].re) * ACC(A[ht][6].re) + ACC(A[ht][4].im) * ACC(A[ht][6].im));
-      s += ACC(16) * (ACC(A[ht][4].re) * ACC(A[ht][7].re) + ACC(A[ht][4].im) * ACC(A[ht][7].im));
-      s += ACC(142) * (ACC(A[ht][4].re) * ACC(A[ht][8].re) + ACC(A[ht][4].im) * ACC(A[ht][8].im));
-      s += ACC(124) * (ACC(A[ht][4].re) * ACC(A[ht][9].re) + ACC(A[ht][4].im) * ACC(A[ht][9].im));
-      s += ACC(160) * (ACC(A[ht][4].re) * ACC(A[ht][10].re) + ACC(A[ht][4].im) * ACC(A[ht][10].im));
-      s += ACC(-20) * (ACC(A[ht][4].re) * ACC(A[ht][11].re) + ACC(A[ht][4].im) * ACC(A[ht][11].im));
-      s += ACC(-20) * (ACC(A[ht][4].re) * ACC(A[ht][12].re) + ACC(A[ht][4].im) * ACC(A[ht][12].im));
-      s += ACC(-2) * (ACC(A[ht][4].re) * ACC(A[ht][13].re) + ACC(A[ht][4].im) * ACC(A[ht][13].im));
-      s += ACC(124) * (ACC(A[ht][4].re) * ACC(A[ht][14].re) + ACC(A[ht][4].im) * ACC(A[ht][14].im));
-      s += ACC(-56) * (ACC(A[ht][4].re) * ACC(A[ht][15].re) + ACC(A[ht][4].im) * ACC(A[ht][15].im));
-      s += ACC(-20) * (ACC(A[ht][4].re) * ACC(A[ht][16].re) + ACC(A[ht][4].im) * ACC(A[ht][16].im));
-      s += ACC(124) * (ACC(A[ht][4].re) * ACC(A[ht][17].re) + ACC(A[ht][4].im) * ACC(A[ht][17].im));
-      s += ACC(-128) * (ACC(A[ht][4].re) * ACC(A[ht][18].re) + ACC(A[ht][4].im) * ACC(A[ht][18].im));
-      s += ACC(16) * (ACC(A[ht][4].re) * ACC(A[ht][19].re) + ACC(A[ht][4].im) * ACC(A[ht][19].im));
-      s += ACC(16) * (ACC(A[ht][4].re) * ACC(A[ht][20].re) + ACC(A[ht][4].im) * ACC(A[ht][20].im));
-      s += ACC(-2) * (ACC(A[ht][4].re) * ACC(A[ht][21].re) + ACC(A[ht][4].im) * ACC(A[ht][21].im));
-      s += ACC(-2) * (ACC(A[ht][4].re) * ACC(A[ht][22].re) + ACC(A[ht][4].im) * ACC(A[ht][22].im));
-      s += ACC(-20) * (ACC(A[ht][4].re) * ACC(A[ht][23].re) + ACC(A[ht][4].im) * ACC(A[ht][23].im));
-      s += ACC(-20) * (ACC(A[ht][5].re) * ACC(A[ht][6].re) + ACC(A[ht][5].im) * ACC(A[ht][6].im));
-      s += ACC(-2) * (ACC(A[ht][5].re) * ACC(A[ht][7].re) + ACC(A[ht][5].im) * ACC(A[ht][7].im));
-      s += ACC(124) * (ACC(A[ht][5].re) * ACC(A[ht][8].re) + ACC(A[ht][5].im) * ACC(A[ht][8].im));
-      s += ACC(-56) * (ACC(A[ht][5].re) * ACC(A[ht][9].re) + ACC(A[ht][5].im) * ACC(A[ht][9].im));
-      s += ACC(-20) * (ACC(A[ht][5].re) * ACC(A[ht][10].re) + ACC(A[ht][5].im) * ACC(A[ht][10].im));
-      s += ACC(124) * (ACC(A[ht][5].re) * ACC(A[ht][11].re) + ACC(A[ht][5].im) * ACC(A[ht][11].im));
-      s += ACC(-2) * (ACC(A[ht][5].re) * ACC(A[ht][12].re) + ACC(A[ht][5].im) * ACC(A[ht][12].im));
-      s += ACC(16) * (ACC(A[ht][5].re) * ACC(A[ht][13].re) + ACC(A[ht][5].im) * ACC(A[ht][13].im));
-      s += ACC(142) * (ACC(A[ht][5].re) * ACC(A[ht][14].re) + ACC(A[ht][5].im) * ACC(A[ht][14].im));
-      s += ACC(124) * (ACC(A[ht][5].re) * ACC(A[ht][15].re) + ACC(A[ht][5].im) * ACC(A[ht][15].im));
-      s += ACC(160) * (ACC(A[ht][5].re) * ACC(A[ht][16].re) + ACC(A[ht][5].im) * ACC(A[ht][16].im));
-      s += ACC(-20) * (ACC(A[ht][5].re) * ACC(A[ht][17].re) + ACC(A[ht][5].im) * ACC(A[ht][17].im));
-      s += ACC(16) * (ACC(A[ht][5].re) * ACC(A[ht][18].re) + ACC(A[ht][5].im) * ACC(A[ht][18].im));
-      s += ACC(-128) * (ACC(A[ht][5].re) * ACC(A[ht][19].re) + ACC(A[ht][5].im) * ACC(A[ht][19].im));
-      s += ACC(-2) * (ACC(A[ht][5].re) * ACC(A[ht][20].re) + ACC(A[ht][5].im) * ACC(A[ht][20].im));
-      s += ACC(-20) * (ACC(A[ht][5].re) * ACC(A[ht][21].re) + ACC(A[ht][5].im) * ACC(A[ht][21].im));
-      s += ACC(16) * (ACC(A[ht][5].re) * ACC(A[ht][22].re) + ACC(A[ht][5].im) * ACC(A[ht][22].im));
-      s += ACC(-2) * (ACC(A[ht][5].re) * ACC(A[ht][23].re) + ACC(A[ht][5].im) * ACC(A[ht][23].im));
-      s += ACC(-128) * (ACC(A[ht][6].re) * ACC(A[ht][7].re) + ACC(A[ht][6].im) * ACC(A[ht][7].im));
-      s += ACC(-128) * (ACC(A[ht][6].re) * ACC(A[ht][8].re) + ACC(A[ht][6].im) * ACC(A[ht][8].im));
-      s += ACC(16) * (ACC(A[ht][6].re) * ACC(A[ht][9].re) + ACC(A[ht][6].im) * ACC(A[ht][9].im));
-      s += ACC(16) * (ACC(A[ht][6].re) * ACC(A[ht][10].re) + ACC(A[ht][6].im) * ACC(A[ht][10].im));
-      s += ACC(160) * (ACC(A[ht][6].re) * ACC(A[ht][11].re) + ACC(A[ht][6].im) * ACC(A[ht][11].im));
-      s += ACC(160) * (ACC(A[ht][6].re) * ACC(A[ht][12].re) + ACC(A[ht][6].im) * ACC(A[ht][12].im));
-      s += ACC(-20) * (ACC(A[ht][6].re) * ACC(A[ht][13].re) + ACC(A[ht][6].im) * ACC(A[ht][13].im));
-      s += ACC(16) * (ACC(A[ht][6].re) * ACC(A[ht][14].re) + ACC(A[ht][6].im) * ACC(A[ht][14].im));
-      s += ACC(-2) * (ACC(A[ht][6].re) * ACC(A[ht][15].re) + ACC(A[ht][6].im) * ACC(A[ht][15].im));
-      s += ACC(124) * (ACC(A[ht][6].re) * ACC(A[ht][16].re) + ACC(A[ht][6].im) * ACC(A[ht][16].im));
-      s += ACC(142) * (ACC(A[ht][6].re) * ACC(A[ht][17].re) + ACC(A[ht][6].im) * ACC(A[ht][17].im));
-      s += ACC(-20) * (ACC(A[ht][6].re) * ACC(A[ht][18].re) + ACC(A[ht][6].im) * ACC(A[ht][18].im));
-      s += ACC(124) * (ACC(A[ht][6].re) * ACC(A[ht][19].re) + ACC(A[ht][6].im) * ACC(A[ht][19].im));
-      s += ACC(-2) * (ACC(A[ht][6].re) * ACC(A[ht][20].re) + ACC(A[ht][6].im) * ACC(A[ht][20].im));
-      s += ACC(-20) * (ACC(A[ht][6].re) * ACC(A[ht][21].re) + ACC(A[ht][6].im) * ACC(A[ht][21].im));
-      s += ACC(-56) * (ACC(A[ht][6].re) * ACC(A[ht][22].re) + ACC(A[ht][6].im) * ACC(A[ht][22].im));
-      s += ACC(124) * (ACC(A[ht][6].re) * ACC(A[ht][23].re) + ACC(A[ht][6].im) * ACC(A[ht][23].im));
-      s += ACC(16) * (ACC(A[ht][7].re) * ACC(A[ht][8].re) + ACC(A[ht][7].im) * ACC(A[ht][8].im));
-      s += ACC(160) * (ACC(A[ht][7].re) * ACC(A[ht][9].re) + ACC(A[ht][7].im) * ACC(A[ht][9].im));
-      s += ACC(-128) * (ACC(A[ht][7].re) * ACC(A[ht][10].re) + ACC(A[ht][7].im) * ACC(A[ht][10].im));
-      s += ACC(16) * (ACC(A[ht][7].re) * ACC(A[ht][11].re) + ACC(A[ht][7].im) * ACC(A[ht][11].im));
-      s += ACC(-20) * (ACC(A[ht][7].re) * ACC(A[ht][12].re) + ACC(A[ht][7].im) * ACC(A[ht][12].im));
-      s += ACC(124) * (ACC(A[ht][7].re) * ACC(A[ht][13].re) + ACC(A[ht][7].im) * ACC(A[ht][13].im));
-      s += ACC(-2) * (ACC(A[ht][7].re) * ACC(A[ht][14].re) + ACC(A[ht][7].im) * ACC(A[ht][14].im));
-      s += ACC(-20) * (ACC(A[ht][7].re) * ACC(A[ht][15].re) + ACC(A[ht][7].im) * ACC(A[ht][15].im));
-      s += ACC(-56) * (ACC(A[ht][7].re) * ACC(A[ht][16].re) + ACC(A[ht][7].im) * ACC(A[ht][16].im));
-      s += ACC(124) * (ACC(A[ht][7].re) * ACC(A[ht][17].re) + ACC(A[ht][7].im) * ACC(A[ht][17].im));
-      s += ACC(160) * (ACC(A[ht][7].re) * ACC(A[ht][18].re) + ACC(A[ht][7].im) * ACC(A[ht][18].im));
-      s += ACC(-20) * (ACC(A[ht][7].re) * ACC(A[ht][19].re) + ACC(A[ht][7].im) * ACC(A[ht][19].im));
-      s += ACC(16) * (ACC(A[ht][7].re) * ACC(A[ht][20].re) + ACC(A[ht][7].im) * ACC(A[ht][20].im));
-      s += ACC(-2) * (ACC(A[ht][7].re) * ACC(A[ht][21].re) + ACC(A[ht][7].im) * ACC(A[ht][21].im));
-      s += ACC(124) * (ACC(A[ht][7].re) * ACC(A[ht][22].re) + ACC(A[ht][7].im) * ACC(A[ht][22].im));
-      s += ACC(142) * (ACC(A[ht][7].re) * ACC(A[ht][23].re) + ACC(A[ht][7].im) * ACC(A[ht][23].im));
-      s += ACC(-128) * (ACC(A[ht][8].re) * ACC(A[ht][9].re) + ACC(A[ht][8].im) * ACC(A[ht][9].im));
-      s += ACC(160) * (ACC(A[ht][8].re) * ACC(A[ht][10].re) + ACC(A[ht][8].im) * ACC(A[ht][10].im));
-      s += ACC(16) * (ACC(A[ht][8].re) * ACC(A[ht][11].re) + ACC(A[ht][8].im) * ACC(A[ht][11].im));
-      s += ACC(16) * (ACC(A[ht][8].re) * ACC(A[ht][12].re) + ACC(A[ht][8].im) * ACC(A[ht][12].im));
-      s += ACC(-2) * (ACC(A[ht][8].re) * ACC(A[ht][13].re) + ACC(A[ht][8].im) * ACC(A[ht][13].im));
-      s += ACC(-128) * (ACC(A[ht][8].re) * ACC(A[ht][14].re) + ACC(A[ht][8].im) * ACC(A[ht][14].im));
-      s += ACC(16) * (ACC(A[ht][8].re) * ACC(A[ht][15].re) + ACC(A[ht][8].im) * ACC(A[ht][15].im));
-      s += ACC(-20) * (ACC(A[ht][8].re) * ACC(A[ht][16].re) + ACC(A[ht][8].im) * ACC(A[ht][16].im));
-      s += ACC(-2) * (ACC(A[ht][8].re) * ACC(A[ht][17].re) + ACC(A[ht][8].im) * ACC(A[ht][17].im));
-      s += ACC(124) * (ACC(A[ht][8].re) * ACC(A[ht][18].re) + ACC(A[ht][8].im) * ACC(A[ht][18].im));
-      s += ACC(-56) * (ACC(A[ht][8].re) * ACC(A[ht][19].re) + ACC(A[ht][8].im) * ACC(A[ht][19].im));
-      s += ACC(-20) * (ACC(A[ht][8].re) * ACC(A[ht][20].re) + ACC(A[ht][8].im) * ACC(A[ht][20].im));
-      s += ACC(-2) * (ACC(A[ht][8].re) * ACC(A[ht][21].re) + ACC(A[ht][8].im) * ACC(A[ht][21].im));
-      s += ACC(124) * (ACC(A[ht][8].re) * ACC(A[ht][22].re) + ACC(A[ht][8].im) * ACC(A[ht][22].im));
-      s += ACC(-20) * (ACC(A[ht][8].re) * ACC(A[ht][23].re) + ACC(A[ht][8].im) * ACC(A[ht][23].im));
-      s += ACC(16) * (ACC(A[ht][9].re) * ACC(A[ht][10].re) + ACC(A[ht][9].im) * ACC(A[ht][10].im));
-      s += ACC(-128) * (ACC(A[ht][9].re) * ACC(A[ht][11].re) + ACC(A[ht][9].im) * ACC(A[ht][11].im));
-      s += ACC(-2) * (ACC(A[ht][9].re) * ACC(A[ht][12].re) + ACC(A[ht][9].im) * ACC(A[ht][12].im));
-      s += ACC(-20) * (ACC(A[ht][9].re) * ACC(A[ht][13].re) + ACC(A[ht][9].im) * ACC(A[ht][13].im));
-      s += ACC(16) * (ACC(A[ht][9].re) * ACC(A[ht][14].re) + ACC(A[ht][9].im) * ACC(A[ht][14].im));
-      s += ACC(-128) * (ACC(A[ht][9].re) * ACC(A[ht][15].re) + ACC(A[ht][9].im) * ACC(A[ht][15].im));
-      s += ACC(-2) * (ACC(A[ht][9].re) * ACC(A[ht][16].re) + ACC(A[ht][9].im) * ACC(A[ht][16].im));
-      s += ACC(16) * (ACC(A[ht][9].re) * ACC(A[ht][17].re) + ACC(A[ht][9].im) * ACC(A[ht][17].im));
-      s += ACC(142) * (ACC(A[ht][9].re) * ACC(A[ht][18].re) + ACC(A[ht][9].im) * ACC(A[ht][18].im));
-      s += ACC(124) * (ACC(A[ht][9].re) * ACC(A[ht][19].re) + ACC(A[ht][9].im) * ACC(A[ht][19].im));
-      s += ACC(-2) * (ACC(A[ht][9].re) * ACC(A[ht][20].re) + ACC(A[ht][9].im) * ACC(A[ht][20].im));
-      s += ACC(16) * (ACC(A[ht][9].re) * ACC(A[ht][21].re) + ACC(A[ht][9].im) * ACC(A[ht][21].im));
-      s += ACC(-20) * (ACC(A[ht][9].re) * ACC(A[ht][22].re) + ACC(A[ht][9].im) * ACC(A[ht][22].im));
-      s += ACC(160) * (ACC(A[ht][9].re) * ACC(A[ht][23].re) + ACC(A[ht][9].im) * ACC(A[ht][23].im));
-      s += ACC(-128) * (ACC(A[ht][10].re) * ACC(A[ht][11].re) + ACC(A[ht][10].im) * ACC(A[ht][11].im));
-      s += ACC(124) * (ACC(A[ht][10].re) * ACC(A[ht][12].re) + ACC(A[ht][10].im) * ACC(A[ht][12].im));
-      s += ACC(-56) * (ACC(A[ht][10].re) * ACC(A[ht][13].re) + ACC(A[ht][10].im) * ACC(A[ht][13].im));
-      s += ACC(-20) * (ACC(A[ht][10].re) * ACC(A[ht][14].re) + ACC(A[ht][10].im) * ACC(A[ht][14].im));
-      s += ACC(-2) * (ACC(A[ht][10].re) * ACC(A[ht][15].re) + ACC(A[ht][10].im) * ACC(A[ht][15].im));
-      s += ACC(124) * (ACC(A[ht][10].re) * ACC(A[ht][16].re) + ACC(A[ht][10].im) * ACC(A[ht][16].im));
-      s += ACC(-20) * (ACC(A[ht][10].re) * ACC(A[ht][17].re) + ACC(A[ht][10].im) * ACC(A[ht][17].im));
-      s += ACC(16) * (ACC(A[ht][10].re) * ACC(A[ht][18].re) + ACC(A[ht][10].im) * ACC(A[ht][18].im));
-      s += ACC(-2) * (ACC(A[ht][10].re) * ACC(A[ht][19].re) + ACC(A[ht][10].im) * ACC(A[ht][19].im));
-      s += ACC(-128) * (ACC(A[ht][10].re) * ACC(A[ht][20].re) + ACC(A[ht][10].im) * ACC(A[ht][20].im));
-      s += ACC(16) * (ACC(A[ht][10].re) * ACC(A[ht][21].re) + ACC(A[ht][10].im) * ACC(A[ht][21].im));
-      s += ACC(-20) * (ACC(A[ht][10].re) * ACC(A[ht][22].re) + ACC(A[ht][10].im) * ACC(A[ht][22].im));
-      s += ACC(-2) * (ACC(A[ht][10].re) * ACC(A[ht][23].re) + ACC(A[ht][10].im) * ACC(A[ht][23].im));
-      s += ACC(142) * (ACC(A[ht][11].re) * ACC(A[ht][12].re) + ACC(A[ht][11].im) * ACC(A[ht][12].im));
-      s += ACC(124) * (ACC(A[ht][11].re) * ACC(A[ht][13].re) + ACC(A[ht][11].im) * ACC(A[ht][13].im));
-      s += ACC(-2) * (ACC(A[ht][11].re) * ACC(A[ht][14].re) + ACC(A[ht][11].im) * ACC(A[ht][14].im));
-      s += ACC(16) * (ACC(A[ht][11].re) * ACC(A[ht][15].re) + ACC(A[ht][11].im) * ACC(A[ht][15].im));
-      s += ACC(-20) * (ACC(A[ht][11].re) * ACC(A[ht][16].re) + ACC(A[ht][11].im) * ACC(A[ht][16].im));
-      s += ACC(160) * (ACC(A[ht][11].re) * ACC(A[ht][17].re) + ACC(A[ht][11].im) * ACC(A[ht][17].im));
-      s += ACC(-2) * (ACC(A[ht][11].re) * ACC(A[ht][18].re) + ACC(A[ht][11].im) * ACC(A[ht][18].im));
-      s += ACC(-20) * (ACC(A[ht][11].re) * ACC(A[ht][19].re) + ACC(A[ht][11].im) * ACC(A[ht][19].im));
-      s += ACC(16) * (ACC(A[ht][11].re) * ACC(A[ht][20].re) + ACC(A[ht][11].im) * ACC(A[ht][20].im));
-      s += ACC(-128) * (ACC(A[ht][11].re) * ACC(A[ht][21].re) + ACC(A[ht][11].im) * ACC(A[ht][21].im));
-      s += ACC(-2) * (ACC(A[ht][11].re) * ACC(A[ht][22].re) + ACC(A[ht][11].im) * ACC(A[ht][22].im));
-      s += ACC(16) * (ACC(A[ht][11].re) * ACC(A[ht][23].re) + ACC(A[ht][11].im) * ACC(A[ht][23].im));
-      s += ACC(-128) * (ACC(A[ht][12].re) * ACC(A[ht][13].re) + ACC(A[ht][12].im) * ACC(A[ht][13].im));
-      s += ACC(-128) * (ACC(A[ht][12].re) * ACC(A[ht][14].re) + ACC(A[ht][12].im) * ACC(A[ht][14].im));
-      s += ACC(16) * (ACC(A[ht][12].re) * ACC(A[ht][15].re) + ACC(A[ht][12].im) * ACC(A[ht][15].im));
-      s += ACC(16) * (ACC(A[ht][12].re) * ACC(A[ht][16].re) + ACC(A[ht][12].im) * ACC(A[ht][16].im));
-      s += ACC(160) * (ACC(A[ht][12].re) * ACC(A[ht][17].re) + ACC(A[ht][12].im) * ACC(A[ht][17].im));
-      s += ACC(124) * (ACC(A[ht][12].re) * ACC(A[ht][18].re) + ACC(A[ht][12].im) * ACC(A[ht][18].im));
-      s += ACC(-20) * (ACC(A[ht][12].re) * ACC(A[ht][19].re) + ACC(A[ht][12].im) * ACC(A[ht][19].im));
-      s += ACC(-56) * (ACC(A[ht][12].re) * ACC(A[ht][20].re) + ACC(A[ht][12].im) * ACC(A[ht][20].im));
-      s += ACC(124) * (ACC(A[ht][12].re) * ACC(A[ht][21].re) + ACC(A[ht][12].im) * ACC(A[ht][21].im));
-      s += ACC(-2) * (ACC(A[ht][12].re) * ACC(A[ht][22].re) + ACC(A[ht][12].im) * ACC(A[ht][22].im));
-      s += ACC(-20) * (ACC(A[ht][12].re) * ACC(A[ht][23].re) + ACC(A[ht][12].im) * ACC(A[ht][23].im));
-      s += ACC(16) * (ACC(A[ht][13].re) * ACC(A[ht][14].re) + ACC(A[ht][13].im) * ACC(A[ht][14].im));
-      s += ACC(160) * (ACC(A[ht][13].re) * ACC(A[ht][15].re) + ACC(A[ht][13].im) * ACC(A[ht][15].im));
-      s += ACC(-128) * (ACC(A[ht][13].re) * ACC(A[ht][16].re) + ACC(A[ht][13].im) * ACC(A[ht][16].im));
-      s += ACC(16) * (ACC(A[ht][13].re) * ACC(A[ht][17].re) + ACC(A[ht][13].im) * ACC(A[ht][17].im));
-      s += ACC(-20) * (ACC(A[ht][13].re) * ACC(A[ht][18].re) + ACC(A[ht][13].im) * ACC(A[ht][18].im));
-      s += ACC(160) * (ACC(A[ht][13].re) * ACC(A[ht][19].re) + ACC(A[ht][13].im) * ACC(A[ht][19].im));
-      s += ACC(124) * (ACC(A[ht][13].re) * ACC(A[ht][20].re) + ACC(A[ht][13].im) * ACC(A[ht][20].im));
-      s += ACC(142) * (ACC(A[ht][13].re) * ACC(A[ht][21].re) + ACC(A[ht][13].im) * ACC(A[ht][21].im));
-      s += ACC(16) * (ACC(A[ht][13].re) * ACC(A[ht][22].re) + ACC(A[ht][13].im) * ACC(A[ht][22].im));
-      s += ACC(-2) * (ACC(A[ht][13].re) * ACC(A[ht][23].re) + ACC(A[ht][13].im) * ACC(A[ht][23].im));
-      s += ACC(-128) * (ACC(A[ht][14].re) * ACC(A[ht][15].re) + ACC(A[ht][14].im) * ACC(A[ht][15].im));
-      s += ACC(160) * (ACC(A[ht][14].re) * ACC(A[ht][16].re) + ACC(A[ht][14].im) * ACC(A[ht][16].im));
-      s += ACC(16) * (ACC(A[ht][14].re) * ACC(A[ht][17].re) + ACC(A[ht][14].im) * ACC(A[ht][17].im));
-      s += ACC(-56) * (ACC(A[ht][14].re) * ACC(A[ht][18].re) + ACC(A[ht][14].im) * ACC(A[ht][18].im));
-      s += ACC(124) * (ACC(A[ht][14].re) * ACC(A[ht][19].re) + ACC(A[ht][14].im) * ACC(A[ht][19].im));
-      s += ACC(124) * (ACC(A[ht][14].re) * ACC(A[ht][20].re) + ACC(A[ht][14].im) * ACC(A[ht][20].im));
-      s += ACC(-20) * (ACC(A[ht][14].re) * ACC(A[ht][21].re) + ACC(A[ht][14].im) * ACC(A[ht][21].im));
-      s += ACC(-20) * (ACC(A[ht][14].re) * ACC(A[ht][22].re) + ACC(A[ht][14].im) * ACC(A[ht][22].im));
-      s += ACC(-2) * (ACC(A[ht][14].re) * ACC(A[ht][23].re) + ACC(A[ht][14].im) * ACC(A[ht][23].im));
-      s += ACC(16) * (ACC(A[ht][15].re) * ACC(A[ht][16].re) + ACC(A[ht][15].im) * ACC(A[ht][16].im));
-      s += ACC(-128) * (ACC(A[ht][15].re) * ACC(A[ht][17].re) + ACC(A[ht][15].im) * ACC(A[ht][17].im));
-      s += ACC(124) * (ACC(A[ht][15].re) * ACC(A[ht][18].re) + ACC(A[ht][15].im) * ACC(A[ht][18].im));
-      s += ACC(142) * (ACC(A[ht][15].re) * ACC(A[ht][19].re) + ACC(A[ht][15].im) * ACC(A[ht][19].im));
-      s += ACC(-20) * (ACC(A[ht][15].re) * ACC(A[ht][20].re) + ACC(A[ht][15].im) * ACC(A[ht][20].im));
-      s += ACC(160) * (ACC(A[ht][15].re) * ACC(A[ht][21].re) + ACC(A[ht][15].im) * ACC(A[ht][21].im));
-      s += ACC(-2) * (ACC(A[ht][15].re) * ACC(A[ht][22].re) + ACC(A[ht][15].im) * ACC(A[ht][22].im));
-      s += ACC(16) * (ACC(A[ht][15].re) * ACC(A[ht][23].re) + ACC(A[ht][15].im) * ACC(A[ht][23].im));
-      s += ACC(-128) * (ACC(A[ht][16].re) * ACC(A[ht][17].re) + ACC(A[ht][16].im) * ACC(A[ht][17].im));
-      s += ACC(-2) * (ACC(A[ht][16].re) * ACC(A[ht][18].re) + ACC(A[ht][16].im) * ACC(A[ht][18].im));
-      s += ACC(16) * (ACC(A[ht][16].re) * ACC(A[ht][19].re) + ACC(A[ht][16].im) * ACC(A[ht][19].im));
-      s += ACC(-20) * (ACC(A[ht][16].re) * ACC(A[ht][20].re) + ACC(A[ht][16].im) * ACC(A[ht][20].im));
-      s += ACC(-2) * (ACC(A[ht][16].re) * ACC(A[ht][21].re) + ACC(A[ht][16].im) * ACC(A[ht][21].im));
-      s += ACC(-128) * (ACC(A[ht][16].re) * ACC(A[ht][22].re) + ACC(A[ht][16].im) * ACC(A[ht][22].im));
-      s += ACC(16) * (ACC(A[ht][16].re) * ACC(A[ht][23].re) + ACC(A[ht][16].im) * ACC(A[ht][23].im));
-      s += ACC(-20) * (ACC(A[ht][17].re) * ACC(A[ht][18].re) + ACC(A[ht][17].im) * ACC(A[ht][18].im));
-      s += ACC(-2) * (ACC(A[ht][17].re) * ACC(A[ht][19].re) + ACC(A[ht][17].im) * ACC(A[ht][19].im));
-      s += ACC(-2) * (ACC(A[ht][17].re) * ACC(A[ht][20].re) + ACC(A[ht][17].im) * ACC(A[ht][20].im));
-      s += ACC(16) * (ACC(A[ht][17].re) * ACC(A[ht][21].re) + ACC(A[ht][17].im) * ACC(A[ht][21].im));
-      s += ACC(16) * (ACC(A[ht][17].re) * ACC(A[ht][22].re) + ACC(A[ht][17].im) * ACC(A[ht][22].im));
-      s += ACC(-128) * (ACC(A[ht][17].re) * ACC(A[ht][23].re) + ACC(A[ht][17].im) * ACC(A[ht][23].im));
-      s += ACC(-128) * (ACC(A[ht][18].re) * ACC(A[ht][19].re) + ACC(A[ht][18].im) * ACC(A[ht][19].im));
-      s += ACC(-128) * (ACC(A[ht][18].re) * ACC(A[ht][20].re) + ACC(A[ht][18].im) * ACC(A[ht][20].im));
-      s += ACC(16) * (ACC(A[ht][18].re) * ACC(A[ht][21].re) + ACC(A[ht][18].im) * ACC(A[ht][21].im));
-      s += ACC(16) * (ACC(A[ht][18].re) * ACC(A[ht][22].re) + ACC(A[ht][18].im) * ACC(A[ht][22].im));
-      s += ACC(160) * (ACC(A[ht][18].re) * ACC(A[ht][23].re) + ACC(A[ht][18].im) * ACC(A[ht][23].im));
-      s += ACC(16) * (ACC(A[ht][19].re) * ACC(A[ht][20].re) + ACC(A[ht][19].im) * ACC(A[ht][20].im));
-      s += ACC(160) * (ACC(A[ht][19].re) * ACC(A[ht][21].re) + ACC(A[ht][19].im) * ACC(A[ht][21].im));
-      s += ACC(-128) * (ACC(A[ht][19].re) * ACC(A[ht][22].re) + ACC(A[ht][19].im) * ACC(A[ht][22].im));
-      s += ACC(16) * (ACC(A[ht][19].re) * ACC(A[ht][23].re) + ACC(A[ht][19].im) * ACC(A[ht][23].im));
-      s += ACC(-128) * (ACC(A[ht][20].re) * ACC(A[ht][21].re) + ACC(A[ht][20].im) * ACC(A[ht][21].im));
-      s += ACC(160) * (ACC(A[ht][20].re) * ACC(A[ht][22].re) + ACC(A[ht][20].im) * ACC(A[ht][22].im));
-      s += ACC(16) * (ACC(A[ht][20].re) * ACC(A[ht][23].re) + ACC(A[ht][20].im) * ACC(A[ht][23].im));
-      s += ACC(16) * (ACC(A[ht][21].re) * ACC(A[ht][22].re) + ACC(A[ht][21].im) * ACC(A[ht][22].im));
-      s += ACC(-128) * (ACC(A[ht][21].re) * ACC(A[ht][23].re) + ACC(A[ht][21].im) * ACC(A[ht][23].im));
-      s += ACC(-128) * (ACC(A[ht][22].re) * ACC(A[ht][23].re) + ACC(A[ht][22].im) * ACC(A[ht][23].im));
-      total += s;
+      CS s = CS(0);
+      s += CS(512) * (CS(A[ht][0].re) * CS(A[ht][0].re) + CS(A[ht][0].im) * CS(A[ht][0].im));
+      s += CS(512) * (CS(A[ht][1].re) * CS(A[ht][1].re) + CS(A[ht][1].im) * CS(A[ht][1].im));
+      s += CS(512) * (CS(A[ht][2].re) * CS(A[ht][2].re) + CS(A[ht][2].im) * CS(A[ht][2].im));
+      s += CS(512) * (CS(A[ht][3].re) * CS(A[ht][3].re) + CS(A[ht][3].im) * CS(A[ht][3].im));
+      s += CS(512) * (CS(A[ht][4].re) * CS(A[ht][4].re) + CS(A[ht][4].im) * CS(A[ht][4].im));
+      s += CS(512) * (CS(A[ht][5].re) * CS(A[ht][5].re) + CS(A[ht][5].im) * CS(A[ht][5].im));
+      s += CS(512) * (CS(A[ht][6].re) * CS(A[ht][6].re) + CS(A[ht][6].im) * CS(A[ht][6].im));
+      s += CS(512) * (CS(A[ht][7].re) * CS(A[ht][7].re) + CS(A[ht][7].im) * CS(A[ht][7].im));
+      s += CS(512) * (CS(A[ht][8].re) * CS(A[ht][8].re) + CS(A[ht][8].im) * CS(A[ht][8].im));
+      s += CS(512) * (CS(A[ht][9].re) * CS(A[ht][9].re) + CS(A[ht][9].im) * CS(A[ht][9].im));
+      s += CS(512) * (CS(A[ht][10].re) * CS(A[ht][10].re) + CS(A[ht][10].im) * CS(A[ht][10].im));
+      s += CS(512) * (CS(A[ht][11].re) * CS(A[ht][11].re) + CS(A[ht][11].im) * CS(A[ht][11].im));
+      s += CS(512) * (CS(A[ht][12].re) * CS(A[ht][12].re) + CS(A[ht][12].im) * CS(A[ht][12].im));
+      s += CS(512) * (CS(A[ht][13].re) * CS(A[ht][13].re) + CS(A[ht][13].im) * CS(A[ht][13].im));
+      s += CS(512) * (CS(A[ht][14].re) * CS(A[ht][14].re) + CS(A[ht][14].im) * CS(A[ht][14].im));
+      s += CS(512) * (CS(A[ht][15].re) * CS(A[ht][15].re) + CS(A[ht][15].im) * CS(A[ht][15].im));
+      s += CS(512) * (CS(A[ht][16].re) * CS(A[ht][16].re) + CS(A[ht][16].im) * CS(A[ht][16].im));
+      s += CS(512) * (CS(A[ht][17].re) * CS(A[ht][17].re) + CS(A[ht][17].im) * CS(A[ht][17].im));
+      s += CS(512) * (CS(A[ht][18].re) * CS(A[ht][18].re) + CS(A[ht][18].im) * CS(A[ht][18].im));
+      s += CS(512) * (CS(A[ht][19].re) * CS(A[ht][19].re) + CS(A[ht][19].im) * CS(A[ht][19].im));
+      s += CS(512) * (CS(A[ht][20].re) * CS(A[ht][20].re) + CS(A[ht][20].im) * CS(A[ht][20].im));
+      s += CS(512) * (CS(A[ht][21].re) * CS(A[ht][21].re) + CS(A[ht][21].im) * CS(A[ht][21].im));
+      s += CS(512) * (CS(A[ht][22].re) * CS(A[ht][22].re) + CS(A[ht][22].im) * CS(A[ht][22].im));
+      s += CS(512) * (CS(A[ht][23].re) * CS(A[ht][23].re) + CS(A[ht][23].im) * CS(A[ht][23].im));
+      s += CS(-128) * (CS(A[ht][0].re) * CS(A[ht][1].re) + CS(A[ht][0].im) * CS(A[ht][1].im));
+      s += CS(-128) * (CS(A[ht][0].re) * CS(A[ht][2].re) + CS(A[ht][0].im) * CS(A[ht][2].im));
+      s += CS(16) * (CS(A[ht][0].re) * CS(A[ht][3].re) + CS(A[ht][0].im) * CS(A[ht][3].im));
+      s += CS(16) * (CS(A[ht][0].re) * CS(A[ht][4].re) + CS(A[ht][0].im) * CS(A[ht][4].im));
+      s += CS(160) * (CS(A[ht][0].re) * CS(A[ht][5].re) + CS(A[ht][0].im) * CS(A[ht][5].im));
+      s += CS(-128) * (CS(A[ht][0].re) * CS(A[ht][6].re) + CS(A[ht][0].im) * CS(A[ht][6].im));
+      s += CS(16) * (CS(A[ht][0].re) * CS(A[ht][7].re) + CS(A[ht][0].im) * CS(A[ht][7].im));
+      s += CS(16) * (CS(A[ht][0].re) * CS(A[ht][8].re) + CS(A[ht][0].im) * CS(A[ht][8].im));
+      s += CS(-2) * (CS(A[ht][0].re) * CS(A[ht][9].re) + CS(A[ht][0].im) * CS(A[ht][9].im));
+      s += CS(-2) * (CS(A[ht][0].re) * CS(A[ht][10].re) + CS(A[ht][0].im) * CS(A[ht][10].im));
+      s += CS(-20) * (CS(A[ht][0].re) * CS(A[ht][11].re) + CS(A[ht][0].im) * CS(A[ht][11].im));
+      s += CS(16) * (CS(A[ht][0].re) * CS(A[ht][12].re) + CS(A[ht][0].im) * CS(A[ht][12].im));
+      s += CS(-2) * (CS(A[ht][0].re) * CS(A[ht][13].re) + CS(A[ht][0].im) * CS(A[ht][13].im));
+      s += CS(160) * (CS(A[ht][0].re) * CS(A[ht][14].re) + CS(A[ht][0].im) * CS(A[ht][14].im));
+      s += CS(-20) * (CS(A[ht][0].re) * CS(A[ht][15].re) + CS(A[ht][0].im) * CS(A[ht][15].im));
+      s += CS(142) * (CS(A[ht][0].re) * CS(A[ht][16].re) + CS(A[ht][0].im) * CS(A[ht][16].im));
+      s += CS(124) * (CS(A[ht][0].re) * CS(A[ht][17].re) + CS(A[ht][0].im) * CS(A[ht][17].im));
+      s += CS(-2) * (CS(A[ht][0].re) * CS(A[ht][18].re) + CS(A[ht][0].im) * CS(A[ht][18].im));
+      s += CS(-20) * (CS(A[ht][0].re) * CS(A[ht][19].re) + CS(A[ht][0].im) * CS(A[ht][19].im));
+      s += CS(-20) * (CS(A[ht][0].re) * CS(A[ht][20].re) + CS(A[ht][0].im) * CS(A[ht][20].im));
+      s += CS(124) * (CS(A[ht][0].re) * CS(A[ht][21].re) + CS(A[ht][0].im) * CS(A[ht][21].im));
+      s += CS(124) * (CS(A[ht][0].re) * CS(A[ht][22].re) + CS(A[ht][0].im) * CS(A[ht][22].im));
+      s += CS(-56) * (CS(A[ht][0].re) * CS(A[ht][23].re) + CS(A[ht][0].im) * CS(A[ht][23].im));
+      s += CS(16) * (CS(A[ht][1].re) * CS(A[ht][2].re) + CS(A[ht][1].im) * CS(A[ht][2].im));
+      s += CS(160) * (CS(A[ht][1].re) * CS(A[ht][3].re) + CS(A[ht][1].im) * CS(A[ht][3].im));
+      s += CS(-128) * (CS(A[ht][1].re) * CS(A[ht][4].re) + CS(A[ht][1].im) * CS(A[ht][4].im));
+      s += CS(16) * (CS(A[ht][1].re) * CS(A[ht][5].re) + CS(A[ht][1].im) * CS(A[ht][5].im));
+      s += CS(16) * (CS(A[ht][1].re) * CS(A[ht][6].re) + CS(A[ht][1].im) * CS(A[ht][6].im));
+      s += CS(-128) * (CS(A[ht][1].re) * CS(A[ht][7].re) + CS(A[ht][1].im) * CS(A[ht][7].im));
+      s += CS(-2) * (CS(A[ht][1].re) * CS(A[ht][8].re) + CS(A[ht][1].im) * CS(A[ht][8].im));
+      s += CS(-20) * (CS(A[ht][1].re) * CS(A[ht][9].re) + CS(A[ht][1].im) * CS(A[ht][9].im));
+      s += CS(16) * (CS(A[ht][1].re) * CS(A[ht][10].re) + CS(A[ht][1].im) * CS(A[ht][10].im));
+      s += CS(-2) * (CS(A[ht][1].re) * CS(A[ht][11].re) + CS(A[ht][1].im) * CS(A[ht][11].im));
+      s += CS(-2) * (CS(A[ht][1].re) * CS(A[ht][12].re) + CS(A[ht][1].im) * CS(A[ht][12].im));
+      s += CS(-20) * (CS(A[ht][1].re) * CS(A[ht][13].re) + CS(A[ht][1].im) * CS(A[ht][13].im));
+      s += CS(-20) * (CS(A[ht][1].re) * CS(A[ht][14].re) + CS(A[ht][1].im) * CS(A[ht][14].im));
+      s += CS(124) * (CS(A[ht][1].re) * CS(A[ht][15].re) + CS(A[ht][1].im) * CS(A[ht][15].im));
+      s += CS(124) * (CS(A[ht][1].re) * CS(A[ht][16].re) + CS(A[ht][1].im) * CS(A[ht][16].im));
+      s += CS(-56) * (CS(A[ht][1].re) * CS(A[ht][17].re) + CS(A[ht][1].im) * CS(A[ht][17].im));
+      s += CS(16) * (CS(A[ht][1].re) * CS(A[ht][18].re) + CS(A[ht][1].im) * CS(A[ht][18].im));
+      s += CS(-2) * (CS(A[ht][1].re) * CS(A[ht][19].re) + CS(A[ht][1].im) * CS(A[ht][19].im));
+      s += CS(160) * (CS(A[ht][1].re) * CS(A[ht][20].re) + CS(A[ht][1].im) * CS(A[ht][20].im));
+      s += CS(-20) * (CS(A[ht][1].re) * CS(A[ht][21].re) + CS(A[ht][1].im) * CS(A[ht][21].im));
+      s += CS(142) * (CS(A[ht][1].re) * CS(A[ht][22].re) + CS(A[ht][1].im) * CS(A[ht][22].im));
+      s += CS(124) * (CS(A[ht][1].re) * CS(A[ht][23].re) + CS(A[ht][1].im) * CS(A[ht][23].im));
+      s += CS(-128) * (CS(A[ht][2].re) * CS(A[ht][3].re) + CS(A[ht][2].im) * CS(A[ht][3].im));
+      s += CS(160) * (CS(A[ht][2].re) * CS(A[ht][4].re) + CS(A[ht][2].im) * CS(A[ht][4].im));
+      s += CS(16) * (CS(A[ht][2].re) * CS(A[ht][5].re) + CS(A[ht][2].im) * CS(A[ht][5].im));
+      s += CS(16) * (CS(A[ht][2].re) * CS(A[ht][6].re) + CS(A[ht][2].im) * CS(A[ht][6].im));
+      s += CS(-2) * (CS(A[ht][2].re) * CS(A[ht][7].re) + CS(A[ht][2].im) * CS(A[ht][7].im));
+      s += CS(160) * (CS(A[ht][2].re) * CS(A[ht][8].re) + CS(A[ht][2].im) * CS(A[ht][8].im));
+      s += CS(-20) * (CS(A[ht][2].re) * CS(A[ht][9].re) + CS(A[ht][2].im) * CS(A[ht][9].im));
+      s += CS(142) * (CS(A[ht][2].re) * CS(A[ht][10].re) + CS(A[ht][2].im) * CS(A[ht][10].im));
+      s += CS(124) * (CS(A[ht][2].re) * CS(A[ht][11].re) + CS(A[ht][2].im) * CS(A[ht][11].im));
+      s += CS(-128) * (CS(A[ht][2].re) * CS(A[ht][12].re) + CS(A[ht][2].im) * CS(A[ht][12].im));
+      s += CS(16) * (CS(A[ht][2].re) * CS(A[ht][13].re) + CS(A[ht][2].im) * CS(A[ht][13].im));
+      s += CS(16) * (CS(A[ht][2].re) * CS(A[ht][14].re) + CS(A[ht][2].im) * CS(A[ht][14].im));
+      s += CS(-2) * (CS(A[ht][2].re) * CS(A[ht][15].re) + CS(A[ht][2].im) * CS(A[ht][15].im));
+      s += CS(-2) * (CS(A[ht][2].re) * CS(A[ht][16].re) + CS(A[ht][2].im) * CS(A[ht][16].im));
+      s += CS(-20) * (CS(A[ht][2].re) * CS(A[ht][17].re) + CS(A[ht][2].im) * CS(A[ht][17].im));
+      s += CS(-20) * (CS(A[ht][2].re) * CS(A[ht][18].re) + CS(A[ht][2].im) * CS(A[ht][18].im));
+      s += CS(-2) * (CS(A[ht][2].re) * CS(A[ht][19].re) + CS(A[ht][2].im) * CS(A[ht][19].im));
+      s += CS(124) * (CS(A[ht][2].re) * CS(A[ht][20].re) + CS(A[ht][2].im) * CS(A[ht][20].im));
+      s += CS(-56) * (CS(A[ht][2].re) * CS(A[ht][21].re) + CS(A[ht][2].im) * CS(A[ht][21].im));
+      s += CS(-20) * (CS(A[ht][2].re) * CS(A[ht][22].re) + CS(A[ht][2].im) * CS(A[ht][22].im));
+      s += CS(124) * (CS(A[ht][2].re) * CS(A[ht][23].re) + CS(A[ht][2].im) * CS(A[ht][23].im));
+      s += CS(16) * (CS(A[ht][3].re) * CS(A[ht][4].re) + CS(A[ht][3].im) * CS(A[ht][4].im));
+      s += CS(-128) * (CS(A[ht][3].re) * CS(A[ht][5].re) + CS(A[ht][3].im) * CS(A[ht][5].im));
+      s += CS(-2) * (CS(A[ht][3].re) * CS(A[ht][6].re) + CS(A[ht][3].im) * CS(A[ht][6].im));
+      s += CS(-20) * (CS(A[ht][3].re) * CS(A[ht][7].re) + CS(A[ht][3].im) * CS(A[ht][7].im));
+      s += CS(-20) * (CS(A[ht][3].re) * CS(A[ht][8].re) + CS(A[ht][3].im) * CS(A[ht][8].im));
+      s += CS(124) * (CS(A[ht][3].re) * CS(A[ht][9].re) + CS(A[ht][3].im) * CS(A[ht][9].im));
+      s += CS(124) * (CS(A[ht][3].re) * CS(A[ht][10].re) + CS(A[ht][3].im) * CS(A[ht][10].im));
+      s += CS(-56) * (CS(A[ht][3].re) * CS(A[ht][11].re) + CS(A[ht][3].im) * CS(A[ht][11].im));
+      s += CS(16) * (CS(A[ht][3].re) * CS(A[ht][12].re) + CS(A[ht][3].im) * CS(A[ht][12].im));
+      s += CS(-128) * (CS(A[ht][3].re) * CS(A[ht][13].re) + CS(A[ht][3].im) * CS(A[ht][13].im));
+      s += CS(-2) * (CS(A[ht][3].re) * CS(A[ht][14].re) + CS(A[ht][3].im) * CS(A[ht][14].im));
+      s += CS(-20) * (CS(A[ht][3].re) * CS(A[ht][15].re) + CS(A[ht][3].im) * CS(A[ht][15].im));
+      s += CS(16) * (CS(A[ht][3].re) * CS(A[ht][16].re) + CS(A[ht][3].im) * CS(A[ht][16].im));
+      s += CS(-2) * (CS(A[ht][3].re) * CS(A[ht][17].re) + CS(A[ht][3].im) * CS(A[ht][17].im));
+      s += CS(-2) * (CS(A[ht][3].re) * CS(A[ht][18].re) + CS(A[ht][3].im) * CS(A[ht][18].im));
+      s += CS(16) * (CS(A[ht][3].re) * CS(A[ht][19].re) + CS(A[ht][3].im) * CS(A[ht][19].im));
+      s += CS(142) * (CS(A[ht][3].re) * CS(A[ht][20].re) + CS(A[ht][3].im) * CS(A[ht][20].im));
+      s += CS(124) * (CS(A[ht][3].re) * CS(A[ht][21].re) + CS(A[ht][3].im) * CS(A[ht][21].im));
+      s += CS(160) * (CS(A[ht][3].re) * CS(A[ht][22].re) + CS(A[ht][3].im) * CS(A[ht][22].im));
+      s += CS(-20) * (CS(A[ht][3].re) * CS(A[ht][23].re) + CS(A[ht][3].im) * CS(A[ht][23].im));
+      s += CS(-128) * (CS(A[ht][4].re) * CS(A[ht][5].re) + CS(A[ht][4].im) * CS(A[ht][5].im));
+      s += CS(-2) * (CS(A[ht][4].re) * CS(A[ht][6].re) + CS(A[ht][4].im) * CS(A[ht][6].im));
+      s += CS(16) * (CS(A[ht][4].re) * CS(A[ht][7].re) + CS(A[ht][4].im) * CS(A[ht][7].im));
+      s += CS(142) * (CS(A[ht][4].re) * CS(A[ht][8].re) + CS(A[ht][4].im) * CS(A[ht][8].im));
+      s += CS(124) * (CS(A[ht][4].re) * CS(A[ht][9].re) + CS(A[ht][4].im) * CS(A[ht][9].im));
+      s += CS(160) * (CS(A[ht][4].re) * CS(A[ht][10].re) + CS(A[ht][4].im) * CS(A[ht][10].im));
+      s += CS(-20) * (CS(A[ht][4].re) * CS(A[ht][11].re) + CS(A[ht][4].im) * CS(A[ht][11].im));
+      s += CS(-20) * (CS(A[ht][4].re) * CS(A[ht][12].re) + CS(A[ht][4].im) * CS(A[ht][12].im));
+      s += CS(-2) * (CS(A[ht][4].re) * CS(A[ht][13].re) + CS(A[ht][4].im) * CS(A[ht][13].im));
+      s += CS(124) * (CS(A[ht][4].re) * CS(A[ht][14].re) + CS(A[ht][4].im) * CS(A[ht][14].im));
+      s += CS(-56) * (CS(A[ht][4].re) * CS(A[ht][15].re) + CS(A[ht][4].im) * CS(A[ht][15].im));
+      s += CS(-20) * (CS(A[ht][4].re) * CS(A[ht][16].re) + CS(A[ht][4].im) * CS(A[ht][16].im));
+      s += CS(124) * (CS(A[ht][4].re) * CS(A[ht][17].re) + CS(A[ht][4].im) * CS(A[ht][17].im));
+      s += CS(-128) * (CS(A[ht][4].re) * CS(A[ht][18].re) + CS(A[ht][4].im) * CS(A[ht][18].im));
+      s += CS(16) * (CS(A[ht][4].re) * CS(A[ht][19].re) + CS(A[ht][4].im) * CS(A[ht][19].im));
+      s += CS(16) * (CS(A[ht][4].re) * CS(A[ht][20].re) + CS(A[ht][4].im) * CS(A[ht][20].im));
+      s += CS(-2) * (CS(A[ht][4].re) * CS(A[ht][21].re) + CS(A[ht][4].im) * CS(A[ht][21].im));
+      s += CS(-2) * (CS(A[ht][4].re) * CS(A[ht][22].re) + CS(A[ht][4].im) * CS(A[ht][22].im));
+      s += CS(-20) * (CS(A[ht][4].re) * CS(A[ht][23].re) + CS(A[ht][4].im) * CS(A[ht][23].im));
+      s += CS(-20) * (CS(A[ht][5].re) * CS(A[ht][6].re) + CS(A[ht][5].im) * CS(A[ht][6].im));
+      s += CS(-2) * (CS(A[ht][5].re) * CS(A[ht][7].re) + CS(A[ht][5].im) * CS(A[ht][7].im));
+      s += CS(124) * (CS(A[ht][5].re) * CS(A[ht][8].re) + CS(A[ht][5].im) * CS(A[ht][8].im));
+      s += CS(-56) * (CS(A[ht][5].re) * CS(A[ht][9].re) + CS(A[ht][5].im) * CS(A[ht][9].im));
+      s += CS(-20) * (CS(A[ht][5].re) * CS(A[ht][10].re) + CS(A[ht][5].im) * CS(A[ht][10].im));
+      s += CS(124) * (CS(A[ht][5].re) * CS(A[ht][11].re) + CS(A[ht][5].im) * CS(A[ht][11].im));
+      s += CS(-2) * (CS(A[ht][5].re) * CS(A[ht][12].re) + CS(A[ht][5].im) * CS(A[ht][12].im));
+      s += CS(16) * (CS(A[ht][5].re) * CS(A[ht][13].re) + CS(A[ht][5].im) * CS(A[ht][13].im));
+      s += CS(142) * (CS(A[ht][5].re) * CS(A[ht][14].re) + CS(A[ht][5].im) * CS(A[ht][14].im));
+      s += CS(124) * (CS(A[ht][5].re) * CS(A[ht][15].re) + CS(A[ht][5].im) * CS(A[ht][15].im));
+      s += CS(160) * (CS(A[ht][5].re) * CS(A[ht][16].re) + CS(A[ht][5].im) * CS(A[ht][16].im));
+      s += CS(-20) * (CS(A[ht][5].re) * CS(A[ht][17].re) + CS(A[ht][5].im) * CS(A[ht][17].im));
+      s += CS(16) * (CS(A[ht][5].re) * CS(A[ht][18].re) + CS(A[ht][5].im) * CS(A[ht][18].im));
+      s += CS(-128) * (CS(A[ht][5].re) * CS(A[ht][19].re) + CS(A[ht][5].im) * CS(A[ht][19].im));
+      s += CS(-2) * (CS(A[ht][5].re) * CS(A[ht][20].re) + CS(A[ht][5].im) * CS(A[ht][20].im));
+      s += CS(-20) * (CS(A[ht][5].re) * CS(A[ht][21].re) + CS(A[ht][5].im) * CS(A[ht][21].im));
+      s += CS(16) * (CS(A[ht][5].re) * CS(A[ht][22].re) + CS(A[ht][5].im) * CS(A[ht][22].im));
+      s += CS(-2) * (CS(A[ht][5].re) * CS(A[ht][23].re) + CS(A[ht][5].im) * CS(A[ht][23].im));
+      s += CS(-128) * (CS(A[ht][6].re) * CS(A[ht][7].re) + CS(A[ht][6].im) * CS(A[ht][7].im));
+      s += CS(-128) * (CS(A[ht][6].re) * CS(A[ht][8].re) + CS(A[ht][6].im) * CS(A[ht][8].im));
+      s += CS(16) * (CS(A[ht][6].re) * CS(A[ht][9].re) + CS(A[ht][6].im) * CS(A[ht][9].im));
+      s += CS(16) * (CS(A[ht][6].re) * CS(A[ht][10].re) + CS(A[ht][6].im) * CS(A[ht][10].im));
+      s += CS(160) * (CS(A[ht][6].re) * CS(A[ht][11].re) + CS(A[ht][6].im) * CS(A[ht][11].im));
+      s += CS(160) * (CS(A[ht][6].re) * CS(A[ht][12].re) + CS(A[ht][6].im) * CS(A[ht][12].im));
+      s += CS(-20) * (CS(A[ht][6].re) * CS(A[ht][13].re) + CS(A[ht][6].im) * CS(A[ht][13].im));
+      s += CS(16) * (CS(A[ht][6].re) * CS(A[ht][14].re) + CS(A[ht][6].im) * CS(A[ht][14].im));
+      s += CS(-2) * (CS(A[ht][6].re) * CS(A[ht][15].re) + CS(A[ht][6].im) * CS(A[ht][15].im));
+      s += CS(124) * (CS(A[ht][6].re) * CS(A[ht][16].re) + CS(A[ht][6].im) * CS(A[ht][16].im));
+      s += CS(142) * (CS(A[ht][6].re) * CS(A[ht][17].re) + CS(A[ht][6].im) * CS(A[ht][17].im));
+      s += CS(-20) * (CS(A[ht][6].re) * CS(A[ht][18].re) + CS(A[ht][6].im) * CS(A[ht][18].im));
+      s += CS(124) * (CS(A[ht][6].re) * CS(A[ht][19].re) + CS(A[ht][6].im) * CS(A[ht][19].im));
+      s += CS(-2) * (CS(A[ht][6].re) * CS(A[ht][20].re) + CS(A[ht][6].im) * CS(A[ht][20].im));
+      s += CS(-20) * (CS(A[ht][6].re) * CS(A[ht][21].re) + CS(A[ht][6].im) * CS(A[ht][21].im));
+      s += CS(-56) * (CS(A[ht][6].re) * CS(A[ht][22].re) + CS(A[ht][6].im) * CS(A[ht][22].im));
+      s += CS(124) * (CS(A[ht][6].re) * CS(A[ht][23].re) + CS(A[ht][6].im) * CS(A[ht][23].im));
+      s += CS(16) * (CS(A[ht][7].re) * CS(A[ht][8].re) + CS(A[ht][7].im) * CS(A[ht][8].im));
+      s += CS(160) * (CS(A[ht][7].re) * CS(A[ht][9].re) + CS(A[ht][7].im) * CS(A[ht][9].im));
+      s += CS(-128) * (CS(A[ht][7].re) * CS(A[ht][10].re) + CS(A[ht][7].im) * CS(A[ht][10].im));
+      s += CS(16) * (CS(A[ht][7].re) * CS(A[ht][11].re) + CS(A[ht][7].im) * CS(A[ht][11].im));
+      s += CS(-20) * (CS(A[ht][7].re) * CS(A[ht][12].re) + CS(A[ht][7].im) * CS(A[ht][12].im));
+      s += CS(124) * (CS(A[ht][7].re) * CS(A[ht][13].re) + CS(A[ht][7].im) * CS(A[ht][13].im));
+      s += CS(-2) * (CS(A[ht][7].re) * CS(A[ht][14].re) + CS(A[ht][7].im) * CS(A[ht][14].im));
+      s += CS(-20) * (CS(A[ht][7].re) * CS(A[ht][15].re) + CS(A[ht][7].im) * CS(A[ht][15].im));
+      s += CS(-56) * (CS(A[ht][7].re) * CS(A[ht][16].re) + CS(A[ht][7].im) * CS(A[ht][16].im));
+      s += CS(124) * (CS(A[ht][7].re) * CS(A[ht][17].re) + CS(A[ht][7].im) * CS(A[ht][17].im));
+      s += CS(160) * (CS(A[ht][7].re) * CS(A[ht][18].re) + CS(A[ht][7].im) * CS(A[ht][18].im));
+      s += CS(-20) * (CS(A[ht][7].re) * CS(A[ht][19].re) + CS(A[ht][7].im) * CS(A[ht][19].im));
+      s += CS(16) * (CS(A[ht][7].re) * CS(A[ht][20].re) + CS(A[ht][7].im) * CS(A[ht][20].im));
+      s += CS(-2) * (CS(A[ht][7].re) * CS(A[ht][21].re) + CS(A[ht][7].im) * CS(A[ht][21].im));
+      s += CS(124) * (CS(A[ht][7].re) * CS(A[ht][22].re) + CS(A[ht][7].im) * CS(A[ht][22].im));
+      s += CS(142) * (CS(A[ht][7].re) * CS(A[ht][23].re) + CS(A[ht][7].im) * CS(A[ht][23].im));
+      s += CS(-128) * (CS(A[ht][8].re) * CS(A[ht][9].re) + CS(A[ht][8].im) * CS(A[ht][9].im));
+      s += CS(160) * (CS(A[ht][8].re) * CS(A[ht][10].re) + CS(A[ht][8].im) * CS(A[ht][10].im));
+      s += CS(16) * (CS(A[ht][8].re) * CS(A[ht][11].re) + CS(A[ht][8].im) * CS(A[ht][11].im));
+      s += CS(16) * (CS(A[ht][8].re) * CS(A[ht][12].re) + CS(A[ht][8].im) * CS(A[ht][12].im));
+      s += CS(-2) * (CS(A[ht][8].re) * CS(A[ht][13].re) + CS(A[ht][8].im) * CS(A[ht][13].im));
+      s += CS(-128) * (CS(A[ht][8].re) * CS(A[ht][14].re) + CS(A[ht][8].im) * CS(A[ht][14].im));
+      s += CS(16) * (CS(A[ht][8].re) * CS(A[ht][15].re) + CS(A[ht][8].im) * CS(A[ht][15].im));
+      s += CS(-20) * (CS(A[ht][8].re) * CS(A[ht][16].re) + CS(A[ht][8].im) * CS(A[ht][16].im));
+      s += CS(-2) * (CS(A[ht][8].re) * CS(A[ht][17].re) + CS(A[ht][8].im) * CS(A[ht][17].im));
+      s += CS(124) * (CS(A[ht][8].re) * CS(A[ht][18].re) + CS(A[ht][8].im) * CS(A[ht][18].im));
+      s += CS(-56) * (CS(A[ht][8].re) * CS(A[ht][19].re) + CS(A[ht][8].im) * CS(A[ht][19].im));
+      s += CS(-20) * (CS(A[ht][8].re) * CS(A[ht][20].re) + CS(A[ht][8].im) * CS(A[ht][20].im));
+      s += CS(-2) * (CS(A[ht][8].re) * CS(A[ht][21].re) + CS(A[ht][8].im) * CS(A[ht][21].im));
+      s += CS(124) * (CS(A[ht][8].re) * CS(A[ht][22].re) + CS(A[ht][8].im) * CS(A[ht][22].im));
+      s += CS(-20) * (CS(A[ht][8].re) * CS(A[ht][23].re) + CS(A[ht][8].im) * CS(A[ht][23].im));
+      s += CS(16) * (CS(A[ht][9].re) * CS(A[ht][10].re) + CS(A[ht][9].im) * CS(A[ht][10].im));
+      s += CS(-128) * (CS(A[ht][9].re) * CS(A[ht][11].re) + CS(A[ht][9].im) * CS(A[ht][11].im));
+      s += CS(-2) * (CS(A[ht][9].re) * CS(A[ht][12].re) + CS(A[ht][9].im) * CS(A[ht][12].im));
+      s += CS(-20) * (CS(A[ht][9].re) * CS(A[ht][13].re) + CS(A[ht][9].im) * CS(A[ht][13].im));
+      s += CS(16) * (CS(A[ht][9].re) * CS(A[ht][14].re) + CS(A[ht][9].im) * CS(A[ht][14].im));
+      s += CS(-128) * (CS(A[ht][9].re) * CS(A[ht][15].re) + CS(A[ht][9].im) * CS(A[ht][15].im));
+      s += CS(-2) * (CS(A[ht][9].re) * CS(A[ht][16].re) + CS(A[ht][9].im) * CS(A[ht][16].im));
+      s += CS(16) * (CS(A[ht][9].re) * CS(A[ht][17].re) + CS(A[ht][9].im) * CS(A[ht][17].im));
+      s += CS(142) * (CS(A[ht][9].re) * CS(A[ht][18].re) + CS(A[ht][9].im) * CS(A[ht][18].im));
+      s += CS(124) * (CS(A[ht][9].re) * CS(A[ht][19].re) + CS(A[ht][9].im) * CS(A[ht][19].im));
+      s += CS(-2) * (CS(A[ht][9].re) * CS(A[ht][20].re) + CS(A[ht][9].im) * CS(A[ht][20].im));
+      s += CS(16) * (CS(A[ht][9].re) * CS(A[ht][21].re) + CS(A[ht][9].im) * CS(A[ht][21].im));
+      s += CS(-20) * (CS(A[ht][9].re) * CS(A[ht][22].re) + CS(A[ht][9].im) * CS(A[ht][22].im));
+      s += CS(160) * (CS(A[ht][9].re) * CS(A[ht][23].re) + CS(A[ht][9].im) * CS(A[ht][23].im));
+      s += CS(-128) * (CS(A[ht][10].re) * CS(A[ht][11].re) + CS(A[ht][10].im) * CS(A[ht][11].im));
+      s += CS(124) * (CS(A[ht][10].re) * CS(A[ht][12].re) + CS(A[ht][10].im) * CS(A[ht][12].im));
+      s += CS(-56) * (CS(A[ht][10].re) * CS(A[ht][13].re) + CS(A[ht][10].im) * CS(A[ht][13].im));
+      s += CS(-20) * (CS(A[ht][10].re) * CS(A[ht][14].re) + CS(A[ht][10].im) * CS(A[ht][14].im));
+      s += CS(-2) * (CS(A[ht][10].re) * CS(A[ht][15].re) + CS(A[ht][10].im) * CS(A[ht][15].im));
+      s += CS(124) * (CS(A[ht][10].re) * CS(A[ht][16].re) + CS(A[ht][10].im) * CS(A[ht][16].im));
+      s += CS(-20) * (CS(A[ht][10].re) * CS(A[ht][17].re) + CS(A[ht][10].im) * CS(A[ht][17].im));
+      s += CS(16) * (CS(A[ht][10].re) * CS(A[ht][18].re) + CS(A[ht][10].im) * CS(A[ht][18].im));
+      s += CS(-2) * (CS(A[ht][10].re) * CS(A[ht][19].re) + CS(A[ht][10].im) * CS(A[ht][19].im));
+      s += CS(-128) * (CS(A[ht][10].re) * CS(A[ht][20].re) + CS(A[ht][10].im) * CS(A[ht][20].im));
+      s += CS(16) * (CS(A[ht][10].re) * CS(A[ht][21].re) + CS(A[ht][10].im) * CS(A[ht][21].im));
+      s += CS(-20) * (CS(A[ht][10].re) * CS(A[ht][22].re) + CS(A[ht][10].im) * CS(A[ht][22].im));
+      s += CS(-2) * (CS(A[ht][10].re) * CS(A[ht][23].re) + CS(A[ht][10].im) * CS(A[ht][23].im));
+      s += CS(142) * (CS(A[ht][11].re) * CS(A[ht][12].re) + CS(A[ht][11].im) * CS(A[ht][12].im));
+      s += CS(124) * (CS(A[ht][11].re) * CS(A[ht][13].re) + CS(A[ht][11].im) * CS(A[ht][13].im));
+      s += CS(-2) * (CS(A[ht][11].re) * CS(A[ht][14].re) + CS(A[ht][11].im) * CS(A[ht][14].im));
+      s += CS(16) * (CS(A[ht][11].re) * CS(A[ht][15].re) + CS(A[ht][11].im) * CS(A[ht][15].im));
+      s += CS(-20) * (CS(A[ht][11].re) * CS(A[ht][16].re) + CS(A[ht][11].im) * CS(A[ht][16].im));
+      s += CS(160) * (CS(A[ht][11].re) * CS(A[ht][17].re) + CS(A[ht][11].im) * CS(A[ht][17].im));
+      s += CS(-2) * (CS(A[ht][11].re) * CS(A[ht][18].re) + CS(A[ht][11].im) * CS(A[ht][18].im));
+      s += CS(-20) * (CS(A[ht][11].re) * CS(A[ht][19].re) + CS(A[ht][11].im) * CS(A[ht][19].im));
+      s += CS(16) * (CS(A[ht][11].re) * CS(A[ht][20].re) + CS(A[ht][11].im) * CS(A[ht][20].im));
+      s += CS(-128) * (CS(A[ht][11].re) * CS(A[ht][21].re) + CS(A[ht][11].im) * CS(A[ht][21].im));
+      s += CS(-2) * (CS(A[ht][11].re) * CS(A[ht][22].re) + CS(A[ht][11].im) * CS(A[ht][22].im));
+      s += CS(16) * (CS(A[ht][11].re) * CS(A[ht][23].re) + CS(A[ht][11].im) * CS(A[ht][23].im));
+      s += CS(-128) * (CS(A[ht][12].re) * CS(A[ht][13].re) + CS(A[ht][12].im) * CS(A[ht][13].im));
+      s += CS(-128) * (CS(A[ht][12].re) * CS(A[ht][14].re) + CS(A[ht][12].im) * CS(A[ht][14].im));
+      s += CS(16) * (CS(A[ht][12].re) * CS(A[ht][15].re) + CS(A[ht][12].im) * CS(A[ht][15].im));
+      s += CS(16) * (CS(A[ht][12].re) * CS(A[ht][16].re) + CS(A[ht][12].im) * CS(A[ht][16].im));
+      s += CS(160) * (CS(A[ht][12].re) * CS(A[ht][17].re) + CS(A[ht][12].im) * CS(A[ht][17].im));
+      s += CS(124) * (CS(A[ht][12].re) * CS(A[ht][18].re) + CS(A[ht][12].im) * CS(A[ht][18].im));
+      s += CS(-20) * (CS(A[ht][12].re) * CS(A[ht][19].re) + CS(A[ht][12].im) * CS(A[ht][19].im));
+      s += CS(-56) * (CS(A[ht][12].re) * CS(A[ht][20].re) + CS(A[ht][12].im) * CS(A[ht][20].im));
+      s += CS(124) * (CS(A[ht][12].re) * CS(A[ht][21].re) + CS(A[ht][12].im) * CS(A[ht][21].im));
+      s += CS(-2) * (CS(A[ht][12].re) * CS(A[ht][22].re) + CS(A[ht][12].im) * CS(A[ht][22].im));
+      s += CS(-20) * (CS(A[ht][12].re) * CS(A[ht][23].re) + CS(A[ht][12].im) * CS(A[ht][23].im));
+      s += CS(16) * (CS(A[ht][13].re) * CS(A[ht][14].re) + CS(A[ht][13].im) * CS(A[ht][14].im));
+      s += CS(160) * (CS(A[ht][13].re) * CS(A[ht][15].re) + CS(A[ht][13].im) * CS(A[ht][15].im));
+      s += CS(-128) * (CS(A[ht][13].re) * CS(A[ht][16].re) + CS(A[ht][13].im) * CS(A[ht][16].im));
+      s += CS(16) * (CS(A[ht][13].re) * CS(A[ht][17].re) + CS(A[ht][13].im) * CS(A[ht][17].im));
+      s += CS(-20) * (CS(A[ht][13].re) * CS(A[ht][18].re) + CS(A[ht][13].im) * CS(A[ht][18].im));
+      s += CS(160) * (CS(A[ht][13].re) * CS(A[ht][19].re) + CS(A[ht][13].im) * CS(A[ht][19].im));
+      s += CS(124) * (CS(A[ht][13].re) * CS(A[ht][20].re) + CS(A[ht][13].im) * CS(A[ht][20].im));
+      s += CS(142) * (CS(A[ht][13].re) * CS(A[ht][21].re) + CS(A[ht][13].im) * CS(A[ht][21].im));
+      s += CS(16) * (CS(A[ht][13].re) * CS(A[ht][22].re) + CS(A[ht][13].im) * CS(A[ht][22].im));
+      s += CS(-2) * (CS(A[ht][13].re) * CS(A[ht][23].re) + CS(A[ht][13].im) * CS(A[ht][23].im));
+      s += CS(-128) * (CS(A[ht][14].re) * CS(A[ht][15].re) + CS(A[ht][14].im) * CS(A[ht][15].im));
+      s += CS(160) * (CS(A[ht][14].re) * CS(A[ht][16].re) + CS(A[ht][14].im) * CS(A[ht][16].im));
+      s += CS(16) * (CS(A[ht][14].re) * CS(A[ht][17].re) + CS(A[ht][14].im) * CS(A[ht][17].im));
+      s += CS(-56) * (CS(A[ht][14].re) * CS(A[ht][18].re) + CS(A[ht][14].im) * CS(A[ht][18].im));
+      s += CS(124) * (CS(A[ht][14].re) * CS(A[ht][19].re) + CS(A[ht][14].im) * CS(A[ht][19].im));
+      s += CS(124) * (CS(A[ht][14].re) * CS(A[ht][20].re) + CS(A[ht][14].im) * CS(A[ht][20].im));
+      s += CS(-20) * (CS(A[ht][14].re) * CS(A[ht][21].re) + CS(A[ht][14].im) * CS(A[ht][21].im));
+      s += CS(-20) * (CS(A[ht][14].re) * CS(A[ht][22].re) + CS(A[ht][14].im) * CS(A[ht][22].im));
+      s += CS(-2) * (CS(A[ht][14].re) * CS(A[ht][23].re) + CS(A[ht][14].im) * CS(A[ht][23].im));
+      s += CS(16) * (CS(A[ht][15].re) * CS(A[ht][16].re) + CS(A[ht][15].im) * CS(A[ht][16].im));
+      s += CS(-128) * (CS(A[ht][15].re) * CS(A[ht][17].re) + CS(A[ht][15].im) * CS(A[ht][17].im));
+      s += CS(124) * (CS(A[ht][15].re) * CS(A[ht][18].re) + CS(A[ht][15].im) * CS(A[ht][18].im));
+      s += CS(142) * (CS(A[ht][15].re) * CS(A[ht][19].re) + CS(A[ht][15].im) * CS(A[ht][19].im));
+      s += CS(-20) * (CS(A[ht][15].re) * CS(A[ht][20].re) + CS(A[ht][15].im) * CS(A[ht][20].im));
+      s += CS(160) * (CS(A[ht][15].re) * CS(A[ht][21].re) + CS(A[ht][15].im) * CS(A[ht][21].im));
+      s += CS(-2) * (CS(A[ht][15].re) * CS(A[ht][22].re) + CS(A[ht][15].im) * CS(A[ht][22].im));
+      s += CS(16) * (CS(A[ht][15].re) * CS(A[ht][23].re) + CS(A[ht][15].im) * CS(A[ht][23].im));
+      s += CS(-128) * (CS(A[ht][16].re) * CS(A[ht][17].re) + CS(A[ht][16].im) * CS(A[ht][17].im));
+      s += CS(-2) * (CS(A[ht][16].re) * CS(A[ht][18].re) + CS(A[ht][16].im) * CS(A[ht][18].im));
+      s += CS(16) * (CS(A[ht][16].re) * CS(A[ht][19].re) + CS(A[ht][16].im) * CS(A[ht][19].im));
+      s += CS(-20) * (CS(A[ht][16].re) * CS(A[ht][20].re) + CS(A[ht][16].im) * CS(A[ht][20].im));
+      s += CS(-2) * (CS(A[ht][16].re) * CS(A[ht][21].re) + CS(A[ht][16].im) * CS(A[ht][21].im));
+      s += CS(-128) * (CS(A[ht][16].re) * CS(A[ht][22].re) + CS(A[ht][16].im) * CS(A[ht][22].im));
+      s += CS(16) * (CS(A[ht][16].re) * CS(A[ht][23].re) + CS(A[ht][16].im) * CS(A[ht][23].im));
+      s += CS(-20) * (CS(A[ht][17].re) * CS(A[ht][18].re) + CS(A[ht][17].im) * CS(A[ht][18].im));
+      s += CS(-2) * (CS(A[ht][17].re) * CS(A[ht][19].re) + CS(A[ht][17].im) * CS(A[ht][19].im));
+      s += CS(-2) * (CS(A[ht][17].re) * CS(A[ht][20].re) + CS(A[ht][17].im) * CS(A[ht][20].im));
+      s += CS(16) * (CS(A[ht][17].re) * CS(A[ht][21].re) + CS(A[ht][17].im) * CS(A[ht][21].im));
+      s += CS(16) * (CS(A[ht][17].re) * CS(A[ht][22].re) + CS(A[ht][17].im) * CS(A[ht][22].im));
+      s += CS(-128) * (CS(A[ht][17].re) * CS(A[ht][23].re) + CS(A[ht][17].im) * CS(A[ht][23].im));
+      s += CS(-128) * (CS(A[ht][18].re) * CS(A[ht][19].re) + CS(A[ht][18].im) * CS(A[ht][19].im));
+      s += CS(-128) * (CS(A[ht][18].re) * CS(A[ht][20].re) + CS(A[ht][18].im) * CS(A[ht][20].im));
+      s += CS(16) * (CS(A[ht][18].re) * CS(A[ht][21].re) + CS(A[ht][18].im) * CS(A[ht][21].im));
+      s += CS(16) * (CS(A[ht][18].re) * CS(A[ht][22].re) + CS(A[ht][18].im) * CS(A[ht][22].im));
+      s += CS(160) * (CS(A[ht][18].re) * CS(A[ht][23].re) + CS(A[ht][18].im) * CS(A[ht][23].im));
+      s += CS(16) * (CS(A[ht][19].re) * CS(A[ht][20].re) + CS(A[ht][19].im) * CS(A[ht][20].im));
+      s += CS(160) * (CS(A[ht][19].re) * CS(A[ht][21].re) + CS(A[ht][19].im) * CS(A[ht][21].im));
+      s += CS(-128) * (CS(A[ht][19].re) * CS(A[ht][22].re) + CS(A[ht][19].im) * CS(A[ht][22].im));
+      s += CS(16) * (CS(A[ht][19].re) * CS(A[ht][23].re) + CS(A[ht][19].im) * CS(A[ht][23].im));
+      s += CS(-128) * (CS(A[ht][20].re) * CS(A[ht][21].re) + CS(A[ht][20].im) * CS(A[ht][21].im));
+      s += CS(160) * (CS(A[ht][20].re) * CS(A[ht][22].re) + CS(A[ht][20].im) * CS(A[ht][22].im));
+      s += CS(16) * (CS(A[ht][20].re) * CS(A[ht][23].re) + CS(A[ht][20].im) * CS(A[ht][23].im));
+      s += CS(16) * (CS(A[ht][21].re) * CS(A[ht][22].re) + CS(A[ht][21].im) * CS(A[ht][22].im));
+      s += CS(-128) * (CS(A[ht][21].re) * CS(A[ht][23].re) + CS(A[ht][21].im) * CS(A[ht][23].im));
+      s += CS(-128) * (CS(A[ht][22].re) * CS(A[ht][23].re) + CS(A[ht][22].im) * CS(A[ht][23].im));
+      total += ACC(s);
     }
   }
   return total;

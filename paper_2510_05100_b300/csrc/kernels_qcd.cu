@@ -41,7 +41,7 @@ struct QcdProc;
     template <typename R, typename ACC, bool W>                                               \
     static __device__ __forceinline__ ACC quark_line(const gluons<R>& st, const R (&pt)[4],   \
                                                      const R (&ptb)[4], R m, R w) {           \
-      return NAME##_quark_line<R, ACC, W>(st, pt, ptb, m, w);                                 \
+      return NAME##_quark_line<R, ACC, W, R>(st, pt, ptb, m, w);                              \
     }                                                                                         \
   };
 

@@ -4,7 +4,7 @@ Both the CUDA path and the CPU oracle consume what this module produces, so it
 holds nothing of the reweighting method itself: only phase-space point
 generation and the parameter grids.  Events are returned as float64 arrays of
 shape ``[nev, npart, 4]`` with components ordered (E, px, py, pz), the per-parton
-``(t, x, y, z)`` order of the Rex SoA momentum vectors (paper Sec. 2, Table 2).
+``(t, x, y, z)`` order of the Rex SoA momentum vectors (paper Sec. 2.1.1, Table 2).
 
 Workloads (all in the partonic centre-of-mass frame, no cuts):
 

@@ -1,0 +1,43 @@
+"""Run a fixed reweighting case for profilers (ncu): python -m paper_2510_05100_b300.profile_case
+
+  --proc gg_ttxg --mode fp64|mixed --nev N --launches L
+
+Generates the standard seeded events, then issues L rex_reweight launches to the
+16-point (gg_ttxg) / 8-point (gg_ttx) / 64-point (gg_ttxgg) grid and synchronises.
+"""
+import argparse
+import os
+import sys
+
+sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+
+import torch  # noqa: E402
+
+from paper_2510_05100_b300 import phase_space as ps  # noqa: E402
+from paper_2510_05100_b300 import rex  # noqa: E402
+
+GRIDS = {"gg_ttx": ps.grid_gg_ttx, "gg_ttxg": ps.grid_gg_ttxg, "gg_ttxgg": ps.grid_64}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--proc", default="gg_ttxg")
+    ap.add_argument("--mode", choices=["fp64", "mixed"], default="fp64")
+    ap.add_argument("--nev", type=int, default=1 << 19)
+    ap.add_argument("--launches", type=int, default=2)
+    a = ap.parse_args()
+    mom = torch.from_numpy(ps.make_events(a.proc, a.nev, 3)).cuda()
+    w = torch.ones(a.nev, dtype=torch.float64, device="cuda")
+    pts = GRIDS[a.proc]()
+    p = rex.Process(a.proc, rex.FP64 if a.mode == "fp64" else rex.MIXED)
+    p.set_params(mt=173.0, wt=0.0, alphas=0.118)
+    out = torch.empty((a.nev, len(pts)), dtype=torch.float64, device="cuda")
+    for _ in range(a.launches):
+        p.reweight(mom, w, pts, w_out=out)
+    torch.cuda.synchronize()
+    print(f"{a.proc} {a.mode} nev={a.nev} k={len(pts)} launches={a.launches} ok "
+          f"w_out[0,:3]={out[0, :3].tolist()}")
+
+
+if __name__ == "__main__":
+    main()

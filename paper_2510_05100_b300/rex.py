@@ -34,7 +34,7 @@ FLAG_NO_DEDUPE = 1
 EXPORTS = (
     "rex_init_process", "rex_process_npart", "rex_set_flags", "rex_set_params",
     "rex_reweight", "rex_reweight_host", "rex_me2", "rex_free_process",
-    "rex_last_error", "rex_version",
+    "rex_last_error", "rex_version", "rex_probe_fma",
 )
 
 
@@ -86,6 +86,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.rex_free_process.restype = None
     lib.rex_last_error.argtypes = []
     lib.rex_last_error.restype = ctypes.c_char_p
+    lib.rex_probe_fma.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_double), vp]
+    lib.rex_probe_fma.restype = ctypes.c_int
     lib.rex_version.argtypes = []
     lib.rex_version.restype = ctypes.c_char_p
     _lib = lib
@@ -185,6 +187,13 @@ class Process:
         _check(load().rex_me2(self._h, _ptr(momenta), nev, ctypes.byref(p), _ptr(out),
                               _stream_ptr(stream)))
         return out
+
+
+def probe_fma(fp64: bool, stream=None) -> float:
+    """Measured FMA-pipe rate of the current device in flop/s (FP64 or FP32)."""
+    out = ctypes.c_double()
+    _check(load().rex_probe_fma(1 if fp64 else 0, ctypes.byref(out), _stream_ptr(stream)))
+    return out.value
 
 
 def version() -> str:
