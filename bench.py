@@ -62,7 +62,8 @@ TRAFFIC = {
 
 def kernel_source_hash() -> str:
     h = hashlib.sha256()
-    for rel in ("paper_2510_05100_b300/csrc/kernels_qcd.cu", "paper_2510_05100_b300/csrc/helas.cuh",
+    for rel in ("paper_2510_05100_b300/csrc/qcd_kernel.cuh", "paper_2510_05100_b300/csrc/kernels_gg_ttxg.cu",
+                "paper_2510_05100_b300/csrc/helas.cuh",
                 "paper_2510_05100_b300/csrc/generated/qcd_amplitudes.cuh",
                 "paper_2510_05100_b300/csrc/rex_internal.cuh"):
         with open(os.path.join(ROOT, rel), "rb") as f:
@@ -165,6 +166,7 @@ def main():
     ap.add_argument("--nev", type=int, default=NEV)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra-modes", action="store_true")
+    ap.add_argument("--no-multi", action="store_true")
     args = ap.parse_args()
     world, rank, local = rdist.env()
     if args.impl == "reference":
@@ -215,6 +217,61 @@ def run_reference(args, world, rank):
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
+
+
+MULTI_BATCHES = (("ee_mumu", 10_000, 41), ("gg_ttx", 1_000_000, 42), ("gg_ttxg", 500_000, 43),
+                 ("gg_ttxgg", 100_000, 44))
+
+
+def run_multi_leg(dev, stream, steps, world, barrier, max_over_ranks):
+    """Mixed batch of four subprocesses x 64 points in one persistent, graph-captured launch
+    (mixed precision), against the same work as four sequential single-process launches."""
+    import torch
+    from paper_2510_05100_b300 import rex
+
+    pts = [dict(p, **ps.EE_NEW) for p in ps.grid_64()]
+    batches = []
+    for proc, n, seed in MULTI_BATCHES:
+        prec = rex.FP64 if proc == "ee_mumu" else rex.MIXED
+        h = rex.Process(proc, prec)
+        h.set_params(ps.EE_ORIGINAL if proc == "ee_mumu" else ORIGINAL)
+        mom = torch.from_numpy(ps.make_events(proc, n, seed)).to(dev)
+        batches.append((h, mom, torch.ones(n, dtype=torch.float64, device=dev),
+                        torch.empty((n, len(pts)), dtype=torch.float64, device=dev)))
+    m = rex.Multi(rex.MIXED)          # ee_mumu (FP64 only) joins the mixed launch
+    m.capture(batches, pts)
+    units = sum(b[1].shape[0] for b in batches) * len(pts)
+
+    def timed(fn):
+        for _ in range(2):
+            fn()
+        torch.cuda.synchronize(dev)
+        barrier()
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        for _ in range(steps):
+            fn()
+        t1.record(stream)
+        torch.cuda.synchronize(dev)
+        barrier()
+        return max_over_ranks(t0.elapsed_time(t1)) / steps
+
+    def graph_step():
+        m.replay(stream)
+
+    def sequential_step():
+        for h, mom, w, wo in batches:
+            h.reweight(mom, w, pts, w_out=wo, stream=stream)
+
+    ms_graph = timed(graph_step)
+    ms_seq = timed(sequential_step)
+    m.close()
+    return {"workload": "10k ee_mumu (FP64) + 1M gg_ttx + 500k gg_ttxg + 100k gg_ttxgg (mixed) x 64 points",
+            "value": rdist.job_throughput(units, world, ms_graph * 1e-3), "unit": UNIT,
+            "ms_per_step": ms_graph, "graph_launches_per_step": 1, "kernel_launches_per_step": 1,
+            "sequential_value": rdist.job_throughput(units, world, ms_seq * 1e-3),
+            "sequential_ms_per_step": ms_seq, "steps": steps}
 
 
 def run_ours(args, world, rank, local):
@@ -346,6 +403,9 @@ def run_ours(args, world, rank, local):
                 "probe_fp64_tflops": probe64 / 1e12, "probe_fp32_tflops": probe32 / 1e12,
                 "algorithmic_bytes_per_launch": (args.nev * 5 * 4 * 8 + args.nev * 8 + args.nev * k * 8)}
 
+    multi = None if args.no_multi else run_multi_leg(dev, stream, max(3, args.steps // 2), world, barrier,
+                                                     max_over_ranks)
+
     cpu = None
     if cpu_pool is not None:
         sample_ev = mom_np[: 1 << 14]
@@ -363,7 +423,8 @@ def run_ours(args, world, rank, local):
                 "config": config_block(args, world), "clocks": clocks,
                 "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                         "entry_point": "rex_reweight_host (pinned host buffers)"},
-                "gpu_launches": args.steps, "roofline": roofline, "cpu_baseline": cpu, "modes": extra}
+                "gpu_launches": args.steps, "roofline": roofline, "cpu_baseline": cpu, "modes": extra,
+                "multi": multi}
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist

@@ -124,6 +124,63 @@ int rex_reweight_host(rex_proc *proc, const double *momenta, const double *w_in,
 int rex_me2(rex_proc *proc, const double *momenta, int64_t nev,
             const rex_params *point, double *me2_out, void *stream);
 
+/* Kernel thread-mapping variants (QCD processes: lanes per event and
+ * register budget; ee_mumu has one).  Every variant computes the same
+ * result; they differ only in speed.  rex_num_variants returns the count,
+ * rex_get_variant / rex_set_variant read and select the handle's variant.
+ * Errors: REX_EINVAL (bad handle or index). */
+int rex_num_variants(const rex_proc *proc);
+int rex_get_variant(const rex_proc *proc);
+int rex_set_variant(rex_proc *proc, int variant);
+
+/* Time every variant on the caller's data (one warm-up and one timed launch
+ * each, enqueued on stream, which this call synchronises) and keep the
+ * fastest in the handle.  Arguments as rex_reweight; w_out is overwritten.
+ * ms_out (host, rex_num_variants floats, may be NULL) receives the timings.
+ * Errors: as rex_reweight. */
+int rex_autotune(rex_proc *proc, const double *momenta, const double *w_in,
+                 int64_t nev, const rex_params *param_sets, int k,
+                 double *w_out, void *stream, float *ms_out);
+
+/* ---- Several subprocesses in one persistent launch -------------------------
+ * The paper reweights subprocesses one after another and finds multi-channel
+ * GPU runs latency bound (Sec. 4.2).  rex_reweight_multi instead puts every
+ * (batch, event tile) of up to 8 subprocess batches into one persistent grid
+ * that takes work items from a device counter, heaviest process first. */
+typedef struct rex_multi rex_multi; /* opaque, library-owned */
+
+typedef struct {
+  rex_proc *proc;          /* handle: process, original point, flags */
+  const double *momenta;   /* device [nev][npart][4] */
+  const double *w_in;      /* device [nev] */
+  int64_t nev;
+  double *w_out;           /* device [nev][k], written */
+} rex_batch;
+
+/* Create a multi-launch handle for one precision (all its batches' handles
+ * must have it, except ee_mumu batches, which are always FP64).  Allocates a small device work counter (scratch) on the
+ * current device, so call it outside stream capture.
+ * Errors: REX_EINVAL, REX_ENOMEM, REX_ECUDA. */
+int rex_multi_create(int precision, rex_multi **out);
+
+/* Reweight every batch to the same k points (host array, copied).  Each
+ * batch's original point is its handle's.  Enqueues a counter reset and one
+ * kernel per 64 points on stream; allocates nothing, so it can be captured.
+ * At most one ee_mumu batch.  Errors: REX_EINVAL, REX_ENOTINIT, REX_ECUDA. */
+int rex_reweight_multi(rex_multi *m, const rex_batch *batches, int nbatch,
+                       const rex_params *param_sets, int k, void *stream);
+
+/* Capture one rex_reweight_multi call (same arguments) into a CUDA graph kept
+ * in the handle, replacing any earlier capture; rex_multi_replay launches it
+ * on stream.  The graph reads the batch pointers given at capture time.
+ * Errors: as rex_reweight_multi; rex_multi_replay: REX_ENOTINIT, REX_ECUDA. */
+int rex_multi_capture(rex_multi *m, const rex_batch *batches, int nbatch,
+                      const rex_params *param_sets, int k);
+int rex_multi_replay(rex_multi *m, void *stream);
+
+/* Release a multi handle (NULL is ignored). */
+void rex_multi_free(rex_multi *m);
+
 /* Release a handle (NULL is ignored).  Synchronises nothing; the caller must
  * make sure no work enqueued with the handle is still running. */
 void rex_free_process(rex_proc *proc);

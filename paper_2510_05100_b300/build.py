@@ -16,8 +16,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "librex_b300.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
-         "-shared", "-I", os.path.join(ROOT, "include")]
+FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include")]
 
 
 def nvcc() -> str:
@@ -31,20 +30,37 @@ def sources() -> list:
     return sorted(glob.glob(os.path.join(CSRC, "*.cu")))
 
 
+def _compile(src: str, obj: str, ptxas_info: bool):
+    cmd = [nvcc(), *ARCH, *FLAGS, "-c", "-o", obj, src]
+    if ptxas_info:
+        cmd.insert(1, "-Xptxas=-v")
+    return cmd, subprocess.run(cmd, capture_output=True, text=True)
+
+
 def build(verbose: bool = False, ptxas_info: bool = False) -> str:
+    """Compile every csrc/*.cu to an object in parallel, then link librex_b300.so."""
+    from concurrent.futures import ThreadPoolExecutor
+
     from .codegen.__main__ import generate
 
     generate()
-    cmd = [nvcc(), *ARCH, *FLAGS, "-o", LIB, *sources()]
-    if ptxas_info:
-        cmd.insert(1, "-Xptxas=-v")
-    if verbose:
-        print(" ".join(cmd))
-    res = subprocess.run(cmd, capture_output=True, text=True)
+    objdir = os.path.join(ROOT, "_build", "obj")
+    os.makedirs(objdir, exist_ok=True)
+    srcs = sources()
+    objs = [os.path.join(objdir, os.path.basename(s)[:-3] + ".o") for s in srcs]
+    with ThreadPoolExecutor(max_workers=max(1, min(len(srcs), os.cpu_count() or 1))) as ex:
+        results = list(ex.map(lambda so: _compile(so[0], so[1], ptxas_info), zip(srcs, objs)))
+    for cmd, res in results:
+        if verbose:
+            print(" ".join(cmd))
+        if res.returncode != 0:
+            raise RuntimeError(f"nvcc failed ({res.returncode}):\n{res.stdout}\n{res.stderr}")
+        if ptxas_info or verbose:
+            sys.stdout.write(res.stdout + res.stderr)
+    link = [nvcc(), *ARCH, "-shared", "-o", LIB, *objs]
+    res = subprocess.run(link, capture_output=True, text=True)
     if res.returncode != 0:
-        raise RuntimeError(f"nvcc failed ({res.returncode}):\n{res.stdout}\n{res.stderr}")
-    if ptxas_info or verbose:
-        sys.stdout.write(res.stdout + res.stderr)
+        raise RuntimeError(f"link failed ({res.returncode}):\n{res.stdout}\n{res.stderr}")
     return LIB
 
 

@@ -62,31 +62,39 @@ class _W:
         return "\n".join(self.lines)
 
 
+def _sn(st) -> str:
+    return "".join(str(g) for g in sorted(st))
+
+
 def emit_process(name: str, ngluon: int) -> str:
     n = ngluon
     flows = flow_basis(n)
+    fidx = {f: i for i, f in enumerate(flows)}
     cint, cden = integer_colour_matrix(n)
     gl = list(range(n))
-    canon_seqs = []
-    for ln in range(2, n + 1):
-        for seq in itertools.permutations(gl, ln):
-            if _canon(seq) == seq:
-                canon_seqs.append(seq)
-    sets = sorted({frozenset(s) for s in canon_seqs}, key=lambda s: (len(s), sorted(s)))
-    suffixes = [seq for ln in range(1, n) for seq in itertools.permutations(gl, ln)]
-    suffix_sets = sorted({frozenset(s) for s in suffixes}, key=lambda s: (len(s), sorted(s)))
+    canon_seqs = [seq for ln in range(2, n + 1) for seq in itertools.permutations(gl, ln)
+                  if _canon(seq) == seq]
+    gsets = sorted({frozenset(s) for s in canon_seqs}, key=lambda s: (len(s), sorted(s)))
+    gidx = {st: i for i, st in enumerate(gsets)}
+    suffix_sets = sorted({frozenset(c) for ln in range(1, n) for c in itertools.combinations(gl, ln)},
+                         key=lambda s: (len(s), sorted(s)))
+    sidx = {st: i for i, st in enumerate(suffix_sets)}
+    nsuf, ngs = len(suffix_sets), len(gsets)
+
+    def pref(seq):   # momentum sum of a gluon sequence, as an expression
+        return f"ev.pg[{seq[0]}]" if len(seq) == 1 else f"ev.ps[{gidx[frozenset(seq)]}]"
 
     w = _W()
     w(f"// ---- {name}: g g -> t t~ + {n - 2} g, {n} gluons, {len(flows)} colour flows", 0)
-    w(f"// Generated by paper_2510_05100_b300/codegen/qcd_bg.py; do not edit.", 0)
     w(f"struct {name}_info {{", 0)
     w(f"static constexpr int NGLUON = {n};")
     w(f"static constexpr int NFLOW = {len(flows)};")
     w(f"static constexpr int NGHEL = {2 ** n};")
     w(f"static constexpr int COLOUR_DEN = {cden};")
+    w(f"static constexpr int NSUFFIX = {nsuf};   // gluon sets absorbed on the antitop side")
+    w(f"static constexpr int NGSET = {ngs};      // gluon sets of two or more (internal gluons)")
     w("};", 0)
     w("", 0)
-    # colour matrix as a table for the tensor-core path / host
     w(f"// exact flow colour matrix C = {name}_colour / {cden}; flows (top end first):", 0)
     for k, f in enumerate(flows):
         w(f"//   flow {k}: {f}", 0)
@@ -95,108 +103,226 @@ def emit_process(name: str, ngluon: int) -> str:
         w("{" + ", ".join(str(v) for v in row) + "},")
     w("};", 0)
     w("", 0)
+    w("// gluon sets (internal gluon lines): " + ", ".join(f"{i}={{{_sn(st)}}}" for st, i in gidx.items()), 0)
+    w("// suffix sets (off-shell antitop lines): " + ", ".join(f"{i}={{{_sn(st)}}}" for st, i in sidx.items()), 0)
 
-    # ---------------- gluon state (mass independent)
-    w(f"template <typename R>", 0)
-    w(f"struct {name}_gluons {{", 0)
-    for g in gl:
-        w(f"R J{g}[4];")
-    for s in canon_seqs:
-        w(f"R {_jn(s)}[4];")
-    for st in suffix_sets:
-        w(f"R Q{''.join(str(g) for g in sorted(st))}[4];   // -(p_tbar + P)")
+    # ---------------- event-level data, filled cooperatively by the event's lanes
+    npart = n + 2
+    vecs = [f"g{g}" for g in gl] + ["tb"]            # dot-product vectors: pg[0..n-1], p_tbar
+    dots = [(i, j) for i in range(n + 1) for j in range(i, n + 1)]
+    didx = {d: k for k, d in enumerate(dots)}
+
+    def dot(i, j):
+        return f"ev.dd[{didx[(min(i, j), max(i, j))]}]"
+
+    def inv_sq(members):     # (sum of vectors)^2 from the dot table
+        terms = [dot(i, i) for i in members]
+        terms += [f"2.0 * {dot(i, j)}" for a_, i in enumerate(members) for j in members[a_ + 1:]]
+        return " + ".join(terms)
+
+    w("template <typename R>", 0)
+    w(f"struct {name}_event {{", 0)
+    w(f"R praw[{npart * 4}];     // particle momenta converted to R")
+    w(f"double dd[{len(dots)}];  // FP64 dot products of (pg_0..pg_{n - 1}, p_tbar)")
+    w(f"R pg[{n}][4];          // outgoing-convention gluon momenta (incoming: -k)")
+    w("R pt[4], ptb[4];       // top, antitop")
+    w(f"R ps[{ngs}][4];        // momentum sum of each gluon set")
+    w(f"R fg[{ngs}];           // -1 / P^2 of each gluon set (P^2 in FP64)")
+    w(f"R q[{nsuf}][4];        // -(p_tbar + P) of each suffix set")
+    w(f"double q2[{nsuf}];     // q^2 in FP64 (the mass slot subtracts m^2 in FP64)")
+    w("cx<R> cht[2][2], chb[2][2];   // helicity 2-spinors chi-, chi+ of top / antitop")
+    w("R wpt, iwpt, wptb, iwptb;     // omega_+ and 1/omega_+ of top / antitop")
     w("};", 0)
     w("", 0)
-    w("// gluon currents for one gluon polarisation configuration (mass independent)", 0)
-    w(f"template <typename R>", 0)
-    w(f"__device__ __forceinline__ void {name}_gluon_state(const R (&pg)[{n}][4], "
-      f"const R (&eps)[{n}][4], const R (&ptb)[4], {name}_gluons<R>& st) {{", 0)
+    w("template <typename R>", 0)
+    w(f"struct {name}_mass {{   // one (event, mass slot), shared memory", 0)
+    w("cx<R> ut[2][4];        // u(p_t) for top helicity -, +")
+    w("cx<R> v[2][4];         // v(p_tbar) for antitop helicity -, +")
+    w(f"R idr[{nsuf}], idi[{nsuf}];   // 1/(q^2 - m^2 + i m Gamma), real and imaginary parts")
+    w("R m;")
+    w("};", 0)
+    w("", 0)
+    w("template <typename R>", 0)
+    w(f"struct {name}_gluons {{   // colour-ordered gluon currents of one polarisation configuration", 0)
     for g in gl:
-        w(f"const R* P{g} = pg[{g}];")
-        w(f"#pragma unroll", 0)
-        w(f"for (int m = 0; m < 4; ++m) st.J{g}[m] = eps[{g}][m];")
-    for s in sets:
-        if len(s) < 2:
-            continue
-        nm = _pn(s)
-        terms = " + ".join(f"pg[{g}][m]" for g in sorted(s))
-        w(f"R {nm}[4];")
-        w(f"#pragma unroll", 0)
-        w(f"for (int m = 0; m < 4; ++m) {nm}[m] = {terms};")
-    for s in canon_seqs:
-        w(f"{{  // J({','.join(map(str, s))})")
-        w(f"R t[4] = {{R(0), R(0), R(0), R(0)}};", 2)
-        for i in range(1, len(s)):
-            x, y = s[:i], s[i:]
-            sg = _sign(x) * _sign(y)
-            w(f"vvv_acc(R({sg}), st.{_jn(x)}, {_pn(x) if len(x) > 1 else 'P%d' % x[0]}, "
-              f"st.{_jn(y)}, {_pn(y) if len(y) > 1 else 'P%d' % y[0]}, t);", 2)
-        for i in range(1, len(s)):
-            for j in range(i + 1, len(s)):
-                x, y, z = s[:i], s[i:j], s[j:]
-                sg = _sign(x) * _sign(y) * _sign(z)
-                w(f"vvvv_acc(R({sg}), st.{_jn(x)}, st.{_jn(y)}, st.{_jn(z)}, t);", 2)
-        pn = _pn(s)
-        w(f"const R f = R(-1) / mdot({pn}, {pn});", 2)
-        w(f"#pragma unroll", 0)
-        w(f"for (int m = 0; m < 4; ++m) st.{_jn(s)}[m] = f * t[m];", 2)
-        w("}")
-    for st_ in suffix_sets:
-        nm = "Q" + "".join(str(g) for g in sorted(st_))
-        terms = " + ".join(f"pg[{g}][m]" for g in sorted(st_))
-        w(f"#pragma unroll", 0)
-        w(f"for (int m = 0; m < 4; ++m) st.{nm}[m] = -(ptb[m] + {terms});")
+        w(f"R J{g}[4];")
+    for sq in canon_seqs:
+        w(f"R {_jn(sq)}[4];")
+    w("};", 0)
+    w("", 0)
+
+    # event setup, phase 1 (all lanes): conversion and FP64 dot products
+    w("// Event setup, phase 1, run by every lane l of nl lanes of the event: convert the", 0)
+    w("// FP64 momenta p (global, [npart][4], rows g g t t~ g..) to R and form the FP64", 0)
+    w("// dot products of the outgoing-convention vectors.  The invariants that cancel for", 0)
+    w("// soft or collinear gluons are built from these FP64 products.", 0)
+    w("template <typename R>", 0)
+    w(f"__device__ __forceinline__ void {name}_event_phase1(const double* __restrict__ p, "
+      f"{name}_event<R>& ev, int l, int nl) {{", 0)
+    w(f"for (int i = l; i < {npart * 4}; i += nl) ev.praw[i] = R(__ldg(p + i));")
+    w(f"for (int k = l; k < {len(dots)}; k += nl) {{")
+    w("int a = 0, b = 0;", 2)
+    w("switch (k) {", 2)
+    for (i, j), k in didx.items():
+        w(f"case {k}: a = {i}; b = {j}; break;", 3)
+    w("}", 2)
+    w("// vector index -> (row, sign): gluons 0, 1 are incoming (-k), the antitop is row 3", 2)
+    w(f"const int ra = a == {n} ? 3 : (a < 2 ? a : a + 2), rb = b == {n} ? 3 : (b < 2 ? b : b + 2);", 2)
+    w("const double sa = (a < 2) ? -1.0 : 1.0, sb = (b < 2) ? -1.0 : 1.0;", 2)
+    w("const double* x = p + 4 * ra;", 2)
+    w("const double* y = p + 4 * rb;", 2)
+    w("ev.dd[k] = sa * sb * (__ldg(x) * __ldg(y) - __ldg(x + 1) * __ldg(y + 1) - __ldg(x + 2) * __ldg(y + 2)"
+      " - __ldg(x + 3) * __ldg(y + 3));", 2)
+    w("}")
     w("}", 0)
     w("", 0)
 
-    # ---------------- quark line for one mass: sum over top/antitop helicities
-    w("// sum over top and antitop helicities of sum_{s,s'} conj(A_s) Cint_{ss'} A_s'", 0)
-    w("// for one (mass, width); Cint = C * COLOUR_DEN.  WIDTH selects complex denominators.", 0)
-    w("// The quadratic form of one helicity is evaluated in CS (a positive-definite form:", 0)
-    w("// no cancellation), and the helicity sum is accumulated in ACC.", 0)
-    w(f"template <typename R, typename ACC, bool WIDTH, typename CS = ACC>", 0)
-    w(f"__device__ __forceinline__ ACC {name}_quark_line(const {name}_gluons<R>& st, "
-      f"const R (&pt)[4], const R (&ptb)[4], R mt, R wt) {{", 0)
-    w("ACC total = ACC(0);")
-    # propagator denominators
-    for st_ in suffix_sets:
-        nm = "".join(str(g) for g in sorted(st_))
-        w(f"const R d{nm} = mdot(st.Q{nm}, st.Q{nm}) - mt * mt;")
-        w(f"R id{nm}r, id{nm}i;")
-        w(f"if (WIDTH) {{ const R im = mt * wt; const R nn = R(1) / (d{nm} * d{nm} + im * im); "
-          f"id{nm}r = d{nm} * nn; id{nm}i = -im * nn; }} else {{ id{nm}r = R(1) / d{nm}; id{nm}i = R(0); }}")
-    w("cx<R> ut[2][4];")
-    w("spinor_u(pt, mt, -1, ut[0]);")
-    w("spinor_u(pt, mt, +1, ut[1]);")
-    w("#pragma unroll 1", 0)
-    w("for (int hb = 0; hb < 2; ++hb) {")
-    w("cx<R> v[4];", 2)
-    w("spinor_v(ptb, mt, hb == 0 ? -1 : +1, v);", 2)
-    for seq in suffixes:
-        nm = _psin(seq)
-        key = "".join(str(g) for g in sorted(seq))
-        w(f"cx<R> {nm}[4];", 2)
-        w("{", 2)
-        w("cx<R> t[4] = {};", 3)
-        for i in range(1, len(seq) + 1):
-            b, rest = seq[:i], seq[i:]
-            src = _psin(rest) if rest else "v"
-            w(f"slash_acc(R({_sign(b)}), st.{_jn(b)}, {src}, t);", 3)
-        w(f"if (WIDTH) fermion_prop(st.Q{key}, mt, cx<R>{{id{key}r, id{key}i}}, t, {nm});", 3)
-        w(f"else fermion_prop_real(st.Q{key}, mt, id{key}r, t, {nm});", 3)
-        w("}", 2)
+    # event setup, phase 2
+    w("// Event setup, phase 2 (after a barrier): lanes form the FP64 invariants; lane 0", 0)
+    w("// builds the R-typed vectors and the top/antitop spinor bases.", 0)
+    w("template <typename R>", 0)
+    w(f"__device__ __forceinline__ void {name}_event_phase2({name}_event<R>& ev, int l, int nl) {{", 0)
+    ninv = ngs + nsuf
+    w(f"for (int k = l; k < {ninv}; k += nl) {{")
+    w("switch (k) {", 2)
+    for st, i in gidx.items():
+        w(f"case {i}: ev.fg[{i}] = R(-1.0 / ({inv_sq(sorted(st))})); break;", 3)
+    for st, i in sidx.items():
+        w(f"case {ngs + i}: ev.q2[{i}] = {inv_sq(sorted(st) + [n])}; break;", 3)
+    w("}", 2)
+    w("}")
+    w("if (l == 0) {")
+    w("#pragma unroll", 0)
+    w("for (int m = 0; m < 4; ++m) {", 2)
+    w("ev.pg[0][m] = -ev.praw[0 + m];", 3)
+    w("ev.pg[1][m] = -ev.praw[4 + m];", 3)
+    for g in range(2, n):
+        w(f"ev.pg[{g}][m] = ev.praw[{4 * (g + 2)} + m];", 3)
+    w("ev.pt[m] = ev.praw[8 + m];", 3)
+    w("ev.ptb[m] = ev.praw[12 + m];", 3)
+    w("}", 2)
+    for st, i in gidx.items():
+        terms = " + ".join(f"ev.pg[{g}][m]" for g in sorted(st))
+        w("#pragma unroll", 0)
+        w(f"for (int m = 0; m < 4; ++m) ev.ps[{i}][m] = {terms};", 2)
+    for st, i in sidx.items():
+        terms = " + ".join(f"ev.pg[{g}][m]" for g in sorted(st))
+        w("#pragma unroll", 0)
+        w(f"for (int m = 0; m < 4; ++m) ev.q[{i}][m] = -(ev.ptb[m] + {terms});", 2)
+    w("R pabs;", 2)
+    w("omegas(ev.pt, R(0), &pabs, &ev.wpt, &ev.iwpt);", 2)
+    w("ev.iwpt = R(1) / ev.wpt;", 2)
+    w("chi_pair(ev.pt, pabs, ev.cht[1], ev.cht[0]);", 2)
+    w("omegas(ev.ptb, R(0), &pabs, &ev.wptb, &ev.iwptb);", 2)
+    w("ev.iwptb = R(1) / ev.wptb;", 2)
+    w("chi_pair(ev.ptb, pabs, ev.chb[1], ev.chb[0]);", 2)
+    w("}")
+    w("}", 0)
+    w("", 0)
+
+    # mass setup
+    w("// Per (event, mass), run by every lane l of nl: inverse propagator denominators", 0)
+    w("// (q^2 - m^2 in FP64, the reciprocal in R); lane 0 builds the top spinors.", 0)
+    w("template <typename R, bool WIDTH>", 0)
+    w(f"__device__ __forceinline__ void {name}_mass_setup(const {name}_event<R>& ev, double mt, double wt, "
+      f"{name}_mass<R>& mm, int l, int nl) {{", 0)
+    w("const double m2 = mt * mt;")
+    w("const R mw = R(mt * wt);")
+    w(f"for (int i = l; i < {nsuf}; i += nl) {{")
+    w("const R d = R(ev.q2[i] - m2);", 2)
+    w("if (WIDTH) { const R nn = R(1) / (d * d + mw * mw); mm.idr[i] = d * nn; mm.idi[i] = -mw * nn; }", 2)
+    w("else { mm.idr[i] = R(1) / d; mm.idi[i] = R(0); }", 2)
+    w("}")
+    w("if (l == 0) {")
+    w("const R mr = R(mt);", 2)
+    w("mm.m = mr;", 2)
+    w("spinor_u_from(ev.cht, ev.wpt, mr * ev.iwpt, mm.ut);", 2)
+    w("spinor_v_from(ev.chb, ev.wptb, mr * ev.iwptb, mm.v);", 2)
+    w("}")
+    w("}", 0)
+    w("", 0)
+
+    # gluon currents
+    w("// colour-ordered gluon currents for one polarisation configuration (mass independent)", 0)
+    w("template <typename R>", 0)
+    w(f"__device__ __forceinline__ void {name}_gluon_currents(const {name}_event<R>& ev, "
+      f"const R (&eps)[{n}][4], {name}_gluons<R>& J) {{", 0)
+    for g in gl:
+        w("#pragma unroll", 0)
+        w(f"for (int m = 0; m < 4; ++m) J.J{g}[m] = eps[{g}][m];")
+    for sq in canon_seqs:
+        w(f"{{  // J({','.join(map(str, sq))})")
+        w("R t[4] = {R(0), R(0), R(0), R(0)};", 2)
+        for i in range(1, len(sq)):
+            x, y = sq[:i], sq[i:]
+            w(f"vvv_acc(R({_sign(x) * _sign(y)}), J.{_jn(x)}, {pref(x)}, J.{_jn(y)}, {pref(y)}, t);", 2)
+        for i in range(1, len(sq)):
+            for j in range(i + 1, len(sq)):
+                x, y, z = sq[:i], sq[i:j], sq[j:]
+                w(f"vvvv_acc(R({_sign(x) * _sign(y) * _sign(z)}), J.{_jn(x)}, J.{_jn(y)}, J.{_jn(z)}, t);", 2)
+        w(f"const R f = ev.fg[{gidx[frozenset(sq)]}];", 2)
+        w("#pragma unroll", 0)
+        w(f"for (int m = 0; m < 4; ++m) J.{_jn(sq)}[m] = f * t[m];", 2)
+        w("}")
+    w("}", 0)
+    w("", 0)
+
+    # quark line with depth-first emission of the antitop-side currents
     nf = len(flows)
+    w("// sum over top helicities and antitop helicities hb in [hb_lo, hb_hi) (0: -, 1: +) of", 0)
+    w("// sum_{s,s'} conj(A_s) Cint_{ss'} A_s' (Cint = C * COLOUR_DEN).  The antitop-side", 0)
+    w("// currents psi(Y) are emitted depth-first over suffixes Y, so only one per depth is live.", 0)
+    w("// The colour form of one helicity is evaluated in CS, the helicity sum in ACC.", 0)
+    w("template <typename R, typename ACC, bool WIDTH, typename CS = ACC>", 0)
+    w(f"__device__ __forceinline__ ACC {name}_quark_line(const {name}_event<R>& ev, const {name}_mass<R>& mm, "
+      f"const {name}_gluons<R>& J, int hb_lo = 0, int hb_hi = 2) {{", 0)
+    w("ACC total = ACC(0);")
+    w("#pragma unroll 1", 0)
+    w("for (int hb = hb_lo; hb < hb_hi; ++hb) {")
+    w("const cx<R>* v = mm.v[hb];", 2)
     w(f"cx<R> A[2][{nf}];", 2)
-    for k, f in enumerate(flows):
-        w("{", 2)
-        w("cx<R> x[4] = {};", 3)
+
+    def prop(seq, dst, ind):
+        i = sidx[frozenset(seq)]
+        w(f"if (WIDTH) fermion_prop(ev.q[{i}], mm.m, cx<R>{{mm.idr[{i}], mm.idi[{i}]}}, t, {dst});", ind)
+        w(f"else fermion_prop_real(ev.q[{i}], mm.m, mm.idr[{i}], t, {dst});", ind)
+
+    def emit_psi(seq, ind):
+        nm = _psin(seq)
+        w(f"cx<R> {nm}[4];", ind)
+        w("{", ind)
+        w("cx<R> t[4] = {};", ind + 1)
+        for i in range(1, len(seq) + 1):
+            bl, rest = seq[:i], seq[i:]
+            w(f"slash_acc(R({_sign(bl)}), J.{_jn(bl)}, {_psin(rest) if rest else 'v'}, t);", ind + 1)
+        prop(seq, nm, ind + 1)
+        w("}", ind)
+
+    def emit_flow(f, ind):
+        k = fidx[f]
+        w(f"{{  // flow {k} = {f}", ind)
+        w("cx<R> x[4] = {};", ind + 1)
         for i in range(1, n + 1):
-            b, rest = f[:i], f[i:]
-            src = _psin(rest) if rest else "v"
-            w(f"slash_acc(R({_sign(b)}), st.{_jn(b)}, {src}, x);", 3)
-        w(f"A[0][{k}] = ubar_dot(ut[0], x);", 3)
-        w(f"A[1][{k}] = ubar_dot(ut[1], x);", 3)
-        w("}", 2)
+            bl, rest = f[:i], f[i:]
+            w(f"slash_acc(R({_sign(bl)}), J.{_jn(bl)}, {_psin(rest) if rest else 'v'}, x);", ind + 1)
+        w(f"A[0][{k}] = ubar_dot(mm.ut[0], x);", ind + 1)
+        w(f"A[1][{k}] = ubar_dot(mm.ut[1], x);", ind + 1)
+        w("}", ind)
+
+    def dfs(suffix, ind):
+        for g in gl:
+            if g in suffix:
+                continue
+            new = (g,) + suffix
+            if len(new) == n:
+                emit_flow(new, ind)
+            else:
+                w("{", ind)
+                emit_psi(new, ind + 1)
+                dfs(new, ind + 1)
+                w("}", ind)
+
+    dfs((), 2)
     w("#pragma unroll", 0)
     w("for (int ht = 0; ht < 2; ++ht) {", 2)
     w("CS s = CS(0);", 3)
@@ -227,6 +353,11 @@ def emit_all() -> str:
         "// Colour-ordered Berends-Giele amplitudes for g g -> t t~ + k g (k = 0, 1, 2).",
         "// Generated by paper_2510_05100_b300/codegen/qcd_bg.py (python -m",
         "// paper_2510_05100_b300.codegen); do not edit.",
+        "//",
+        "// Per process: <name>_event (event-level data, filled once per event),",
+        "// <name>_mass (per event and mass slot), <name>_gluons (gluon currents of one",
+        "// polarisation configuration) and the routines that fill them, then",
+        "// <name>_quark_line: jamps and their colour form summed over top helicities.",
         "#pragma once",
         '#include "../helas.cuh"',
         "",

@@ -1,0 +1,107 @@
+// e+(1) e-(2) -> mu+(3) mu-(4) through photon and Z: device code shared by the
+// standalone kernel and the persistent multi-process kernel.
+//
+// Thread per event.  For each of the 16 helicity configurations the chiral
+// lepton currents  Je_X = vbar(p1) gamma^mu P_X u(p2),  Jm_Y = ubar(p4) gamma^mu P_Y v(p3)
+// are parameter independent; a parameter point only changes the coefficients
+//     amp = e^2 Q^2 / s (Je . Jm) + sum_{X,Y} gZ^2 g_X g_Y / (s - mZ^2 + i mZ GZ) (JeX . JmY),
+// (FFV1P0_3-style vector/chiral currents closed FFV1_0-style).
+#pragma once
+#include <cuda_runtime.h>
+
+#include "helas.cuh"
+#include "rex_internal.cuh"
+
+namespace rex {
+
+// b^dag sigmabar^mu a (left, sign -1 on the spatial part) or b^dag sigma^mu a (right)
+__device__ __forceinline__ void chiral_current(const cx<double>* b, const cx<double>* a, double sgn,
+                                               cx<double>* j) {
+  const cx<double> b0a0 = cdot1(b[0], a[0]), b0a1 = cdot1(b[0], a[1]);
+  const cx<double> b1a0 = cdot1(b[1], a[0]), b1a1 = cdot1(b[1], a[1]);
+  j[0] = b0a0 + b1a1;
+  const cx<double> sx = b0a1 + b1a0;
+  // b^dag sigma_y a = -i b0* a1 + i b1* a0
+  const cx<double> d = b1a0 - b0a1;
+  const cx<double> sy = cx<double>{-d.im, d.re};
+  const cx<double> sz = b0a0 - b1a1;
+  j[1] = sgn * sx;
+  j[2] = sgn * sy;
+  j[3] = sgn * sz;
+}
+
+__device__ __forceinline__ cx<double> cmdot(const cx<double>* a, const cx<double>* b) {
+  return a[0] * b[0] - a[1] * b[1] - a[2] * b[2] - a[3] * b[3];
+}
+
+// One tile of 128 events, thread per event.  TABLE: k, mode, out_stride, pt[0..k].
+template <class TABLE>
+__device__ __forceinline__ void ee_tile(const double* __restrict__ mom, const double* __restrict__ w_in,
+                                        int64_t nev, int64_t tile, const TABLE& lp, double* __restrict__ out) {
+  const int64_t ev = tile * 128 + threadIdx.x;
+  if (ev >= nev) return;
+  double p[4][4];
+  const double2* src = reinterpret_cast<const double2*>(mom + ev * 16);
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const double2 v = __ldg(src + i);
+    p[i / 2][(i % 2) * 2] = v.x;
+    p[i / 2][(i % 2) * 2 + 1] = v.y;
+  }
+  double q[4];
+#pragma unroll
+  for (int m = 0; m < 4; ++m) q[m] = p[0][m] + p[1][m];
+  const double s = mdot(q, q);
+
+  double me2_0 = 0.0;
+  for (int j = 0; j <= lp.k; ++j) {
+    const EwPoint& c = lp.pt[j];
+    const double den_re = s - c.mz2, den_im = c.mzwz;
+    const double nn = 1.0 / (den_re * den_re + den_im * den_im);
+    const cx<double> dz = cx<double>{den_re * nn, -den_im * nn};   // 1/(s - mZ^2 + i mZ GZ)
+    const double ca = c.e2qq / s;
+    cx<double> coef[4];
+#pragma unroll
+    for (int xy = 0; xy < 4; ++xy) coef[xy] = cx<double>{ca, 0.0} + c.gzz[xy] * dz;
+    double sum = 0.0;
+#pragma unroll 1
+    for (int h = 0; h < 16; ++h) {
+      const int l1 = (h & 1) ? 1 : -1, l2 = (h & 2) ? 1 : -1;
+      const int l3 = (h & 4) ? 1 : -1, l4 = (h & 8) ? 1 : -1;
+      cx<double> v1[4], u2[4], v3[4], u4[4];
+      spinor_v(p[0], 0.0, l1, v1);
+      spinor_u(p[1], 0.0, l2, u2);
+      spinor_v(p[2], 0.0, l3, v3);
+      spinor_u(p[3], 0.0, l4, u4);
+      cx<double> je[2][4], jm[2][4];
+      chiral_current(v1, u2, -1.0, je[0]);          // vbar1 gamma P_L u2
+      chiral_current(v1 + 2, u2 + 2, 1.0, je[1]);   // vbar1 gamma P_R u2
+      chiral_current(u4, v3, -1.0, jm[0]);          // ubar4 gamma P_L v3
+      chiral_current(u4 + 2, v3 + 2, 1.0, jm[1]);   // ubar4 gamma P_R v3
+      cx<double> amp = cx<double>{0.0, 0.0};
+#pragma unroll
+      for (int x = 0; x < 2; ++x)
+#pragma unroll
+        for (int y = 0; y < 2; ++y) amp = amp + coef[2 * x + y] * cmdot(je[x], jm[y]);
+      sum += amp.re * amp.re + amp.im * amp.im;
+    }
+    const double me2 = sum * c.avg;
+    if (lp.mode == OUT_ME2) {
+      out[ev] = me2;
+      return;
+    }
+    if (j == 0) {
+      me2_0 = me2;
+    } else {
+      out[ev * lp.out_stride + (j - 1)] = (me2_0 == 0.0) ? 0.0 : w_in[ev] * (me2 / me2_0);
+    }
+  }
+}
+
+static __global__ void __launch_bounds__(128)
+    ee_reweight_kernel(const double* __restrict__ mom, const double* __restrict__ w_in, int64_t nev,
+                       const __grid_constant__ EwLaunch lp, double* __restrict__ out) {
+  ee_tile(mom, w_in, nev, (int64_t)blockIdx.x, lp, out);
+}
+
+}  // namespace rex

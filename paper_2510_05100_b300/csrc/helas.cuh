@@ -156,48 +156,67 @@ __device__ __forceinline__ void spinor_v(const R* p, R m, int hel, cx<R>* v) {
   }
 }
 
+// Spinors from precomputed helicity 2-spinors chi[0] = chi-, chi[1] = chi+ and
+// omega_+ = wp, omega_- = wm (= m / omega_+), for both helicities (index 0: -, 1: +).
+template <typename R>
+__device__ __forceinline__ void spinor_u_from(const cx<R> (&chi)[2][2], R wp, R wm, cx<R> (&u)[2][4]) {
+  u[1][0] = wm * chi[1][0]; u[1][1] = wm * chi[1][1]; u[1][2] = wp * chi[1][0]; u[1][3] = wp * chi[1][1];
+  u[0][0] = wp * chi[0][0]; u[0][1] = wp * chi[0][1]; u[0][2] = wm * chi[0][0]; u[0][3] = wm * chi[0][1];
+}
+
+template <typename R>
+__device__ __forceinline__ void spinor_v_from(const cx<R> (&chi)[2][2], R wp, R wm, cx<R> (&v)[2][4]) {
+  v[1][0] = wp * chi[0][0]; v[1][1] = wp * chi[0][1]; v[1][2] = (-wm) * chi[0][0]; v[1][3] = (-wm) * chi[0][1];
+  v[0][0] = wm * chi[1][0]; v[0][1] = wm * chi[1][1]; v[0][2] = (-wp) * chi[1][0]; v[0][3] = (-wp) * chi[1][1];
+}
+
 // ---------------------------------------------------------------------------
 // fermion-line operations
 // ---------------------------------------------------------------------------
 
-// out += s * (gamma . a) psi for a real 4-vector a.
+// out += s * (gamma . a) psi for a real 4-vector a, written as pure FMA chains:
+//   out0 += (a0-a3) psi2 - (a1 - i a2) psi3      out1 += -(a1 + i a2) psi2 + (a0+a3) psi3
+//   out2 += (a0+a3) psi0 + (a1 - i a2) psi1      out3 +=  (a1 + i a2) psi0 + (a0-a3) psi1
 template <typename R>
 __device__ __forceinline__ void slash_acc(R s, const R* a, const cx<R>* psi, cx<R>* out) {
   const R am = s * (a[0] - a[3]), ap = s * (a[0] + a[3]);
   const R a1 = s * a[1], a2 = s * a[2];
-  // (a1 - i a2) * z and (a1 + i a2) * z
-  const cx<R> m3 = cx<R>{a1 * psi[3].re + a2 * psi[3].im, a1 * psi[3].im - a2 * psi[3].re};
-  const cx<R> p2 = cx<R>{a1 * psi[2].re - a2 * psi[2].im, a1 * psi[2].im + a2 * psi[2].re};
-  const cx<R> m1 = cx<R>{a1 * psi[1].re + a2 * psi[1].im, a1 * psi[1].im - a2 * psi[1].re};
-  const cx<R> p0 = cx<R>{a1 * psi[0].re - a2 * psi[0].im, a1 * psi[0].im + a2 * psi[0].re};
-  out[0] = out[0] + am * psi[2] - m3;
-  out[1] = out[1] - p2 + ap * psi[3];
-  out[2] = out[2] + ap * psi[0] + m1;
-  out[3] = out[3] + p0 + am * psi[1];
+  out[0].re = fma(am, psi[2].re, fma(-a1, psi[3].re, fma(-a2, psi[3].im, out[0].re)));
+  out[0].im = fma(am, psi[2].im, fma(-a1, psi[3].im, fma(a2, psi[3].re, out[0].im)));
+  out[1].re = fma(ap, psi[3].re, fma(-a1, psi[2].re, fma(a2, psi[2].im, out[1].re)));
+  out[1].im = fma(ap, psi[3].im, fma(-a1, psi[2].im, fma(-a2, psi[2].re, out[1].im)));
+  out[2].re = fma(ap, psi[0].re, fma(a1, psi[1].re, fma(a2, psi[1].im, out[2].re)));
+  out[2].im = fma(ap, psi[0].im, fma(a1, psi[1].im, fma(-a2, psi[1].re, out[2].im)));
+  out[3].re = fma(am, psi[1].re, fma(a1, psi[0].re, fma(-a2, psi[0].im, out[3].re)));
+  out[3].im = fma(am, psi[1].im, fma(a1, psi[0].im, fma(a2, psi[0].re, out[3].im)));
 }
 
-// out = -(q-slash + m) in * invden  (fermion propagator, the -1 = i*i of
-// propagator and vertex factors; FFV1_1 role).
+// out = (gamma . a) psi + c psi for real a and real c (FMA chains).
+template <typename R>
+__device__ __forceinline__ void slash_plus_scalar(const R* a, R c, const cx<R>* psi, cx<R>* out) {
+#pragma unroll
+  for (int i = 0; i < 4; ++i) out[i] = cx<R>{c * psi[i].re, c * psi[i].im};
+  slash_acc(R(1), a, psi, out);
+}
+
+// Fermion propagator (FFV1_1 role) with the vertex and propagator factors i*i = -1:
+//   out = -(q-slash + m) in / (q^2 - m^2 + i m Gamma).
+// Zero width: the real factor f = -1/(q^2 - m^2) is folded into q and m
+// (qf = f q, mf = f m) so the whole operation is FMA chains.
+template <typename R>
+__device__ __forceinline__ void fermion_prop_real(const R* q, R m, R invden, const cx<R>* in, cx<R>* out) {
+  const R f = -invden;
+  const R qf[4] = {f * q[0], f * q[1], f * q[2], f * q[3]};
+  slash_plus_scalar(qf, f * m, in, out);
+}
+
+// Complex inverse denominator (non-zero width).
 template <typename R>
 __device__ __forceinline__ void fermion_prop(const R* q, R m, cx<R> invden, const cx<R>* in, cx<R>* out) {
   cx<R> t[4];
-#pragma unroll
-  for (int i = 0; i < 4; ++i) t[i] = m * in[i];
-  slash_acc(R(1), q, in, t);
+  slash_plus_scalar(q, m, in, t);
 #pragma unroll
   for (int i = 0; i < 4; ++i) out[i] = -(t[i] * invden);
-}
-
-// Same with a real inverse denominator (zero width).
-template <typename R>
-__device__ __forceinline__ void fermion_prop_real(const R* q, R m, R invden, const cx<R>* in, cx<R>* out) {
-  cx<R> t[4];
-#pragma unroll
-  for (int i = 0; i < 4; ++i) t[i] = m * in[i];
-  slash_acc(R(1), q, in, t);
-  const R f = -invden;
-#pragma unroll
-  for (int i = 0; i < 4; ++i) out[i] = f * t[i];
 }
 
 // ubar(u) . x = u_L^dag x_R + u_R^dag x_L  (FFV1_0 closure role).

@@ -1,0 +1,217 @@
+// Fused reweighting kernels for g g -> t t~ + k g on sm_103a.
+//
+// One launch runs every step of the hot path for a tile of events:
+//   a1  FP64 momenta [nev][npart][4] -> registers (outgoing-momentum convention)
+//   a3  external wavefunctions (linear gluon polarisations; top spinors per mass)
+//   a4  colour-ordered gluon currents (once per event and gluon polarisation,
+//       shared by every parameter point) and off-shell top currents (per mass)
+//   a5  colour-flow amplitudes A(s) (jamps)
+//   a6  colour sum  sum_{s,s'} conj(A_s) C_ss' A_s'  with the exact integer matrix
+//   a7  helicity sum: top/antitop helicities inside the thread, gluon
+//       polarisations across the NGHEL lanes of the event (warp shuffles), FP64
+//   a8  ratio epilogue  w_out = w_in * |M_j|^2 / |M_0|^2  (0 if |M_0|^2 == 0)
+//
+// Thread mapping (kernel variants, chosen per process and precision):
+//   SPLIT = 0: NGHEL = 2^n lanes per event, one gluon polarisation configuration
+//              each, both antitop helicities inside the lane;
+//   SPLIT = 1: 2 NGHEL lanes per event, the antitop helicity split across lanes
+//              (half the live state per lane, gluon currents computed twice);
+//   MINB: minimum resident blocks per SM requested from the register allocator.
+// Blocks of 128 threads, 128 / lanes-per-event events per block.
+// The amplitude is evaluated once per distinct (mt, Gamma_t) slot; alpha_s
+// enters only through the exact overall factor (4 pi alpha_s)^n of a
+// tree amplitude with n external gluons and no other coupling.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "generated/qcd_amplitudes.cuh"
+#include "rex_internal.cuh"
+
+namespace rex {
+
+template <int PROC>
+struct QcdProc;
+
+#define REX_QCD_PROC(KIND, NAME)                                                              \
+  template <>                                                                                 \
+  struct QcdProc<KIND> {                                                                      \
+    using info = NAME##_info;                                                                 \
+    template <typename R>                                                                     \
+    using event = NAME##_event<R>;                                                            \
+    template <typename R>                                                                     \
+    using mass = NAME##_mass<R>;                                                              \
+    template <typename R>                                                                     \
+    using gluons = NAME##_gluons<R>;                                                          \
+    template <typename R>                                                                     \
+    static __device__ __forceinline__ void event_phase1(const double* p, event<R>& ev, int l, \
+                                                        int nl) {                             \
+      NAME##_event_phase1(p, ev, l, nl);                                                      \
+    }                                                                                         \
+    template <typename R>                                                                     \
+    static __device__ __forceinline__ void event_phase2(event<R>& ev, int l, int nl) {        \
+      NAME##_event_phase2(ev, l, nl);                                                         \
+    }                                                                                         \
+    template <typename R, bool W>                                                             \
+    static __device__ __forceinline__ void mass_setup(const event<R>& ev, double m, double w, \
+                                                      mass<R>& mm, int l, int nl) {           \
+      NAME##_mass_setup<R, W>(ev, m, w, mm, l, nl);                                           \
+    }                                                                                         \
+    template <typename R>                                                                     \
+    static __device__ __forceinline__ void gluon_currents(const event<R>& ev,                 \
+                                                          const R (&eps)[info::NGLUON][4],    \
+                                                          gluons<R>& J) {                     \
+      NAME##_gluon_currents(ev, eps, J);                                                      \
+    }                                                                                         \
+    template <typename R, typename ACC, bool W>                                               \
+    static __device__ __forceinline__ ACC quark_line(const event<R>& ev, const mass<R>& mm,   \
+                                                     const gluons<R>& J, int lo, int hi) {    \
+      return NAME##_quark_line<R, ACC, W, R>(ev, mm, J, lo, hi);                              \
+    }                                                                                         \
+  };
+
+REX_QCD_PROC(PROC_GG_TTX, gg_ttx)
+REX_QCD_PROC(PROC_GG_TTXG, gg_ttxg)
+REX_QCD_PROC(PROC_GG_TTXGG, gg_ttxgg)
+#undef REX_QCD_PROC
+
+constexpr int QCD_BLOCK = 128;
+
+// One tile of events (EPB = 128 / lanes-per-event) through the whole path.
+// TABLE is the launch's parameter table (QcdLaunch, or a batch table of the
+// persistent multi-process kernel): nmass, mass[], width[], k, mode,
+// out_stride, slot[], factor[], factor0.
+template <int PROC, typename R, bool WIDTH, int SPLIT>
+struct QcdTile {
+  using P = QcdProc<PROC>;
+  static constexpr int NG = P::info::NGLUON;
+  static constexpr int NPART = NG + 2;
+  static constexpr int NGH = P::info::NGHEL;
+  static constexpr int NH = NGH << SPLIT;
+  static constexpr int EPB = QCD_BLOCK / NH;
+  static_assert(32 % NH == 0 || NH % 32 == 0, "gluon-polarisation lanes must tile a warp");
+  static_assert(NH <= 32, "one event per warp at most");
+
+  struct Smem {
+    double me2s[EPB][MAX_MASS + 1];
+    typename P::template event<R> evs[EPB];
+    typename P::template mass<R> mss[EPB];
+  };
+
+  template <class TABLE>
+  static __device__ __forceinline__ void run(Smem& sm, const double* __restrict__ mom,
+                                             const double* __restrict__ w_in, int64_t nev, int64_t tile,
+                                             const TABLE& lp, double* __restrict__ out) {
+    const int tid = threadIdx.x;
+    const int el = tid / NH;
+    const int lane_ev = tid - el * NH;
+    const int gh = lane_ev % NGH;
+    const int hb_lo = SPLIT ? lane_ev / NGH : 0;
+    const int hb_hi = SPLIT ? hb_lo + 1 : 2;
+    const bool leader = lane_ev == 0;
+    const int64_t ev0 = tile * EPB;
+    const int64_t ev = ev0 + el;
+    const bool valid = ev < nev;
+    const int64_t evc = valid ? ev : nev - 1;
+
+    // a1/a2: the event's lanes load its FP64 momenta, convert them and form the
+    // FP64 invariants cooperatively (two phases, block barriers between them)
+    P::event_phase1(mom + evc * (NPART * 4), sm.evs[el], lane_ev, NH);
+    __syncthreads();
+    P::event_phase2(sm.evs[el], lane_ev, NH);
+    __syncthreads();
+    const auto& evd = sm.evs[el];
+
+    // a3: linear polarisation of each gluon from this lane's bits; a4: gluon currents
+    R eps[NG][4];
+#pragma unroll
+    for (int g = 0; g < NG; ++g) pol_linear(evd.pg[g], (gh >> g) & 1, eps[g]);
+    typename P::template gluons<R> J;
+    P::gluon_currents(evd, eps, J);
+
+    // a3-a7 per distinct mass slot
+    for (int m = 0; m < lp.nmass; ++m) {
+      P::template mass_setup<R, WIDTH>(evd, lp.mass[m], lp.width[m], sm.mss[el], lane_ev, NH);
+      __syncthreads();
+      double s = 0.0;
+      if (valid) s = P::template quark_line<R, double, WIDTH>(evd, sm.mss[el], J, hb_lo, hb_hi);
+#pragma unroll
+      for (int off = NH / 2; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+      if (leader) sm.me2s[el][m] = s;
+      __syncthreads();
+    }
+
+    // a8: epilogue, consecutive threads write consecutive outputs of the tile's rows
+    const int nblk = (int)((nev - ev0) < EPB ? (nev - ev0) : EPB);
+    if (lp.mode == OUT_RATIO) {
+      const int k = lp.k;
+      for (int idx = tid; idx < nblk * k; idx += QCD_BLOCK) {
+        const int e = idx / k;
+        const int j = idx - e * k;
+        const double m0 = sm.me2s[e][0] * lp.factor0;
+        const double mj = sm.me2s[e][lp.slot[j]] * lp.factor[j];
+        const double w = w_in[ev0 + e];
+        out[(ev0 + e) * lp.out_stride + j] = (m0 == 0.0) ? 0.0 : w * (mj / m0);
+      }
+    } else {
+      for (int e = tid; e < nblk; e += QCD_BLOCK) out[ev0 + e] = sm.me2s[e][0] * lp.factor0;
+    }
+  }
+};
+
+template <int PROC, typename R, bool WIDTH, int SPLIT, int MINB>
+__global__ void __launch_bounds__(QCD_BLOCK, MINB)
+    qcd_reweight_kernel(const double* __restrict__ mom, const double* __restrict__ w_in,
+                        int64_t nev, const __grid_constant__ QcdLaunch lp,
+                        double* __restrict__ out) {
+  using T = QcdTile<PROC, R, WIDTH, SPLIT>;
+  __shared__ typename T::Smem sm;
+  T::run(sm, mom, w_in, nev, (int64_t)blockIdx.x, lp, out);
+}
+
+// Variant table (SPLIT, MINB) shared by every process.
+struct QcdVariant {
+  int split, minb;
+};
+constexpr QcdVariant kQcdVariants[QCD_NVARIANT] = {{0, 1}, {1, 1}, {0, 3}, {1, 3}, {1, 4}};
+
+template <int PROC, typename R, int V>
+static int launch_v(const double* mom, const double* w_in, int64_t nev, const QcdLaunch& lp,
+                    double* out, cudaStream_t st) {
+  constexpr int SPLIT = kQcdVariants[V].split;
+  constexpr int MINB = kQcdVariants[V].minb;
+  constexpr int EPB = QCD_BLOCK / (QcdProc<PROC>::info::NGHEL << SPLIT);
+  const int64_t blocks = (nev + EPB - 1) / EPB;
+  if (blocks > 0x7fffffffLL) return (int)cudaErrorInvalidValue;
+  if (lp.has_width)   // rare: one (SPLIT = 0) variant carries complex propagators
+    qcd_reweight_kernel<PROC, R, true, 0, 1>
+        <<<(unsigned)((nev + QCD_BLOCK / QcdProc<PROC>::info::NGHEL - 1) /
+                      (QCD_BLOCK / QcdProc<PROC>::info::NGHEL)),
+           QCD_BLOCK, 0, st>>>(mom, w_in, nev, lp, out);
+  else
+    qcd_reweight_kernel<PROC, R, false, SPLIT, MINB><<<(unsigned)blocks, QCD_BLOCK, 0, st>>>(mom, w_in, nev, lp,
+                                                                                            out);
+  return (int)cudaGetLastError();
+}
+
+template <int PROC, typename R>
+static int launch_variant(int variant, const double* mom, const double* w_in, int64_t nev, const QcdLaunch& lp,
+                          double* out, cudaStream_t st) {
+  switch (variant) {
+    case 0: return launch_v<PROC, R, 0>(mom, w_in, nev, lp, out, st);
+    case 1: return launch_v<PROC, R, 1>(mom, w_in, nev, lp, out, st);
+    case 2: return launch_v<PROC, R, 2>(mom, w_in, nev, lp, out, st);
+    case 3: return launch_v<PROC, R, 3>(mom, w_in, nev, lp, out, st);
+    case 4: return launch_v<PROC, R, 4>(mom, w_in, nev, lp, out, st);
+    default: return (int)cudaErrorInvalidValue;
+  }
+}
+
+#define REX_DEFINE_QCD_LAUNCHER(KIND, NAME)                                                          \
+  int launch_##NAME(int mixed, int variant, const double* mom, const double* w_in, int64_t nev,     \
+                    const QcdLaunch& lp, double* out, void* stream) {                              \
+    cudaStream_t st = static_cast<cudaStream_t>(stream);                                           \
+    return mixed ? launch_variant<KIND, float>(variant, mom, w_in, nev, lp, out, st)               \
+                 : launch_variant<KIND, double>(variant, mom, w_in, nev, lp, out, st);             \
+  }
+
+}  // namespace rex

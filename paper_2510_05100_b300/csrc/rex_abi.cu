@@ -11,6 +11,7 @@
 #include <cstdio>
 #include <cstring>
 #include <new>
+#include <utility>
 #include <string>
 #include <vector>
 
@@ -24,6 +25,7 @@ struct rex_proc {
   int kind;
   int precision;
   unsigned flags;
+  int variant;        // QCD thread-mapping variant (qcd_kernel.cuh)
   int has_orig;
   rex_params orig;
   // rex_reweight_host buffers (device), grown on demand
@@ -67,6 +69,30 @@ const ProcInfo kProcs[] = {
 };
 
 const ProcInfo& info_of(int kind) { return kProcs[kind]; }
+
+// Default thread-mapping variant per (process, precision), the fastest of every
+// variant timed on a B300 at 2^20 (gg_ttx, gg_ttxg) / 2^16 (gg_ttxgg) events;
+// rex_autotune picks again on the caller's device and data.
+int default_variant(int kind, int precision) {
+  static const int table[4][2] = {
+      {0, 0},   // ee_mumu (single variant)
+      {0, 0},   // gg_ttx:   FP64 v0, mixed v0
+      {0, 2},   // gg_ttxg:  FP64 v0, mixed v2 (min 3 blocks/SM)
+      {0, 3},   // gg_ttxgg: FP64 v0, mixed v3 (antitop helicity split, min 3 blocks/SM)
+  };
+  return table[kind][precision == REX_MIXED ? 1 : 0];
+}
+
+int launch_qcd(const rex_proc* p, const double* mom, const double* w_in, int64_t nev, const QcdLaunch& lp,
+               double* out, void* stream) {
+  const int mixed = p->precision == REX_MIXED;
+  switch (p->kind) {
+    case PROC_GG_TTX: return launch_gg_ttx(mixed, p->variant, mom, w_in, nev, lp, out, stream);
+    case PROC_GG_TTXG: return launch_gg_ttxg(mixed, p->variant, mom, w_in, nev, lp, out, stream);
+    case PROC_GG_TTXGG: return launch_gg_ttxgg(mixed, p->variant, mom, w_in, nev, lp, out, stream);
+    default: return (int)cudaErrorInvalidValue;
+  }
+}
 
 bool aligned8(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 7u) == 0; }
 bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
@@ -154,7 +180,7 @@ int run_qcd_chunk(rex_proc* p, const double* mom, const double* w_in, int64_t ne
     if (lp.width[s] != 0.0) lp.has_width = 1;
   *next_j = j;
   double* o = (mode == OUT_RATIO) ? out + j0 : out;
-  const int err = launch_qcd(p->kind, p->precision == REX_MIXED, mom, w_in, nev, lp, o, stream);
+  const int err = launch_qcd(p, mom, w_in, nev, lp, o, stream);
   if (err != 0) return cuda_fail(err, "kernel launch");
   return REX_OK;
 }
@@ -210,9 +236,216 @@ int reweight_impl(rex_proc* p, const double* momenta, const double* w_in, int64_
   return REX_OK;
 }
 
+// ---------------------------------------------------------------------------
+// persistent multi-process launch
+// ---------------------------------------------------------------------------
+int fill_multi_table(const rex_proc* p, const rex_params* pts, int j0, int j1, int64_t stride, MultiTable& t) {
+  const ProcInfo& pi = info_of(p->kind);
+  std::memset(&t, 0, sizeof t);
+  t.mode = OUT_RATIO;
+  t.out_stride = stride;
+  t.nmass = 1;
+  t.mass[0] = p->orig.mt;
+  t.width[0] = p->orig.wt;
+  t.factor0 = qcd_factor(pi, p->orig.alphas);
+  const bool dedupe = !(p->flags & REX_FLAG_NO_DEDUPE);
+  for (int j = j0; j < j1; ++j) {
+    const rex_params& q = pts[j];
+    int slot = -1;
+    if (dedupe)
+      for (int s = 0; s < t.nmass; ++s)
+        if (t.mass[s] == q.mt && t.width[s] == q.wt) {
+          slot = s;
+          break;
+        }
+    if (slot < 0) {
+      slot = t.nmass++;
+      t.mass[slot] = q.mt;
+      t.width[slot] = q.wt;
+    }
+    t.slot[j - j0] = slot;
+    t.factor[j - j0] = qcd_factor(pi, q.alphas);
+  }
+  t.k = j1 - j0;
+  for (int s = 0; s < t.nmass; ++s)
+    if (t.width[s] != 0.0) t.has_width = 1;
+  return REX_OK;
+}
+
+}  // namespace
+
+struct rex_multi {
+  int precision;
+  int device;
+  unsigned long long* counter;   // device work counter (scratch), reset by every launch
+  int blocks[2];                 // persistent grid size without / with complex propagators
+  cudaStream_t cap_stream;
+  cudaGraph_t graph;
+  cudaGraphExec_t exec;
+};
+
+namespace {
+
+int multi_impl(rex_multi* m, const rex_batch* batches, int nbatch, const rex_params* pts, int k, void* stream) {
+  if (!m) return fail(REX_EINVAL, "null multi handle");
+  if (nbatch < 1 || nbatch > MULTI_MAX_BATCH)
+    return fail(REX_EINVAL, "nbatch must be in [1, %d] (got %d)", MULTI_MAX_BATCH, nbatch);
+  if (!batches) return fail(REX_EINVAL, "null batch array");
+  if (k < 0) return fail(REX_EINVAL, "k < 0");
+  int nee = 0;
+  for (int i = 0; i < nbatch; ++i) {
+    const rex_batch& b = batches[i];
+    int rc = validate_proc(b.proc);
+    if (rc) return rc;
+    // ee_mumu is FP64 only and its tile always runs in FP64: it may join a mixed launch
+    if (b.proc->precision != m->precision && b.proc->kind != PROC_EE_MUMU)
+      return fail(REX_EINVAL, "batch %d precision differs from the multi handle", i);
+    if (!b.proc->has_orig) return fail(REX_ENOTINIT, "batch %d: rex_set_params has not been called", i);
+    if (b.nev < 0) return fail(REX_EINVAL, "batch %d: nev < 0", i);
+    if (b.nev > 0 && (!b.momenta || !b.w_in || !b.w_out)) return fail(REX_EINVAL, "batch %d: null array", i);
+    if (b.nev > 0 && (!aligned16(b.momenta) || !aligned8(b.w_in) || !aligned8(b.w_out)))
+      return fail(REX_EINVAL, "batch %d: misaligned array", i);
+    if (b.proc->kind == PROC_EE_MUMU) ++nee;
+    for (int j = 0; j < k; ++j) {
+      rc = b.proc->kind == PROC_EE_MUMU ? check_ew_point(pts[j]) : check_qcd_point(pts[j]);
+      if (rc) return rc;
+    }
+  }
+  if (nee > 1) return fail(REX_EINVAL, "at most one ee_mumu batch per multi launch");
+  if (k == 0) return REX_OK;
+  if (!pts) return fail(REX_EINVAL, "null parameter array");
+  // heaviest process first: items are handed out in this order
+  int order[MULTI_MAX_BATCH];
+  for (int i = 0; i < nbatch; ++i) order[i] = i;
+  for (int i = 0; i < nbatch; ++i)
+    for (int j = i + 1; j < nbatch; ++j)
+      if (batches[order[j]].proc->kind > batches[order[i]].proc->kind) std::swap(order[i], order[j]);
+  const int mixed = m->precision == REX_MIXED;
+  static thread_local MultiLaunch ml;   // ~20 KB: kept off the stack
+  for (int j0 = 0; j0 < k; j0 += MULTI_MAX_POINTS) {
+    const int j1 = (k - j0) < MULTI_MAX_POINTS ? k : j0 + MULTI_MAX_POINTS;
+    std::memset(&ml, 0, sizeof ml);
+    int64_t total = 0;
+    int nb = 0, width = 0;
+    for (int oi = 0; oi < nbatch; ++oi) {
+      const rex_batch& b = batches[order[oi]];
+      if (b.nev == 0) continue;
+      MultiBatch& B = ml.b[nb++];
+      B.kind = b.proc->kind;
+      B.nev = b.nev;
+      B.mom = b.momenta;
+      B.w_in = b.w_in;
+      B.out = b.w_out + j0;
+      const int epb = multi_events_per_tile(B.kind, mixed);
+      B.tile_begin = total;
+      total += (b.nev + epb - 1) / epb;
+      B.tile_end = total;
+      if (B.kind == PROC_EE_MUMU) {
+        ml.ew.k = j1 - j0;
+        ml.ew.mode = OUT_RATIO;
+        ml.ew.out_stride = k;
+        ml.ew.pt[0] = ew_point(b.proc->orig);
+        for (int j = j0; j < j1; ++j) ml.ew.pt[1 + j - j0] = ew_point(pts[j]);
+      } else {
+        fill_multi_table(b.proc, pts, j0, j1, k, B.t);
+        if (B.t.has_width) width = 1;
+      }
+    }
+    if (nb == 0) return REX_OK;
+    ml.nbatch = nb;
+    ml.total = total;
+    const int64_t grid = total < m->blocks[width] ? total : m->blocks[width];
+    const int err = launch_multi(mixed, width, (int)grid, ml, m->counter, stream);
+    if (err != 0) return cuda_fail(err, "multi kernel launch");
+  }
+  return REX_OK;
+}
+
 }  // namespace
 
 extern "C" {
+
+int rex_multi_create(int precision, rex_multi** out) {
+  if (!out) return fail(REX_EINVAL, "null output handle pointer");
+  *out = nullptr;
+  if (precision != REX_FP64 && precision != REX_MIXED) return fail(REX_EINVAL, "unknown precision %d", precision);
+  rex_multi* m = new (std::nothrow) rex_multi;
+  if (!m) return fail(REX_ENOMEM, "out of host memory");
+  std::memset(m, 0, sizeof *m);
+  m->precision = precision;
+  cudaError_t e = cudaGetDevice(&m->device);
+  if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&m->counter), 256);
+  if (e != cudaSuccess) {
+    delete m;
+    return fail(REX_ENOMEM, "work-counter allocation failed: %s", cudaGetErrorString(e));
+  }
+  for (int w = 0; w < 2; ++w) {
+    const int err = multi_grid_size(precision == REX_MIXED, w, &m->blocks[w]);
+    if (err != 0) {
+      cudaFree(m->counter);
+      delete m;
+      return cuda_fail(err, "occupancy query");
+    }
+  }
+  *out = m;
+  return REX_OK;
+}
+
+int rex_reweight_multi(rex_multi* m, const rex_batch* batches, int nbatch, const rex_params* param_sets, int k,
+                       void* stream) {
+  return multi_impl(m, batches, nbatch, param_sets, k, stream);
+}
+
+int rex_multi_capture(rex_multi* m, const rex_batch* batches, int nbatch, const rex_params* param_sets, int k) {
+  if (!m) return fail(REX_EINVAL, "null multi handle");
+  if (m->exec) {
+    cudaGraphExecDestroy(m->exec);
+    m->exec = nullptr;
+  }
+  if (m->graph) {
+    cudaGraphDestroy(m->graph);
+    m->graph = nullptr;
+  }
+  if (!m->cap_stream) {
+    const cudaError_t e = cudaStreamCreateWithFlags(&m->cap_stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return cuda_fail((int)e, "capture stream");
+  }
+  cudaError_t e = cudaStreamBeginCapture(m->cap_stream, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return cuda_fail((int)e, "cudaStreamBeginCapture");
+  const int rc = multi_impl(m, batches, nbatch, param_sets, k, m->cap_stream);
+  cudaGraph_t g = nullptr;
+  e = cudaStreamEndCapture(m->cap_stream, &g);
+  if (rc) {
+    if (g) cudaGraphDestroy(g);
+    return rc;
+  }
+  if (e != cudaSuccess) return cuda_fail((int)e, "cudaStreamEndCapture");
+  e = cudaGraphInstantiate(&m->exec, g, 0);
+  if (e != cudaSuccess) {
+    cudaGraphDestroy(g);
+    return cuda_fail((int)e, "cudaGraphInstantiate");
+  }
+  m->graph = g;
+  return REX_OK;
+}
+
+int rex_multi_replay(rex_multi* m, void* stream) {
+  if (!m) return fail(REX_EINVAL, "null multi handle");
+  if (!m->exec) return fail(REX_ENOTINIT, "rex_multi_capture has not been called");
+  const cudaError_t e = cudaGraphLaunch(m->exec, static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail((int)e, "cudaGraphLaunch");
+  return REX_OK;
+}
+
+void rex_multi_free(rex_multi* m) {
+  if (!m) return;
+  if (m->exec) cudaGraphExecDestroy(m->exec);
+  if (m->graph) cudaGraphDestroy(m->graph);
+  if (m->cap_stream) cudaStreamDestroy(m->cap_stream);
+  if (m->counter) cudaFree(m->counter);
+  delete m;
+}
+
 
 int rex_init_process(const char* name, int precision, rex_proc** out) {
   if (!out) return fail(REX_EINVAL, "null output handle pointer");
@@ -230,6 +463,7 @@ int rex_init_process(const char* name, int precision, rex_proc** out) {
   std::memset(p, 0, sizeof *p);
   p->kind = kind;
   p->precision = precision;
+  p->variant = default_variant(kind, precision);
   *out = p;
   return REX_OK;
 }
@@ -322,6 +556,69 @@ int rex_me2(rex_proc* proc, const double* momenta, int64_t nev, const rex_params
   return proc->kind == PROC_EE_MUMU
              ? run_ee_chunk(&tmp, momenta, nullptr, nev, point, 0, 0, OUT_ME2, me2_out, 1, stream, &next)
              : run_qcd_chunk(&tmp, momenta, nullptr, nev, point, 0, 0, OUT_ME2, me2_out, 1, stream, &next);
+}
+
+int rex_num_variants(const rex_proc* proc) {
+  const int rc = validate_proc(proc);
+  if (rc) return rc;
+  return proc->kind == PROC_EE_MUMU ? 1 : QCD_NVARIANT;
+}
+
+int rex_get_variant(const rex_proc* proc) {
+  const int rc = validate_proc(proc);
+  if (rc) return rc;
+  return proc->kind == PROC_EE_MUMU ? 0 : proc->variant;
+}
+
+int rex_set_variant(rex_proc* proc, int variant) {
+  const int rc = validate_proc(proc);
+  if (rc) return rc;
+  const int n = proc->kind == PROC_EE_MUMU ? 1 : QCD_NVARIANT;
+  if (variant < 0 || variant >= n) return fail(REX_EINVAL, "variant %d out of range [0, %d)", variant, n);
+  proc->variant = variant;
+  return REX_OK;
+}
+
+int rex_autotune(rex_proc* proc, const double* momenta, const double* w_in, int64_t nev,
+                 const rex_params* param_sets, int k, double* w_out, void* stream, float* ms_out) {
+  int rc = validate_proc(proc);
+  if (rc) return rc;
+  if (proc->kind == PROC_EE_MUMU) return REX_OK;
+  if (nev <= 0 || k <= 0) return fail(REX_EINVAL, "autotune needs nev > 0 and k > 0");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+    return fail(REX_ECUDA, "cudaEventCreate failed");
+  const int keep = proc->variant;
+  int best = keep;
+  float best_ms = 3.0e38f;
+  for (int v = 0; v < QCD_NVARIANT; ++v) {
+    proc->variant = v;
+    rc = reweight_impl(proc, momenta, w_in, nev, param_sets, k, w_out, stream);   // warm-up
+    if (!rc) {
+      cudaEventRecord(e0, st);
+      rc = reweight_impl(proc, momenta, w_in, nev, param_sets, k, w_out, stream);
+      cudaEventRecord(e1, st);
+    }
+    cudaError_t ce = cudaEventSynchronize(e1);
+    if (rc || ce != cudaSuccess) {
+      proc->variant = keep;
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      return rc ? rc : cuda_fail((int)ce, "autotune");
+    }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms_out) ms_out[v] = ms;
+    if (ms < best_ms) {
+      best_ms = ms;
+      best = v;
+    }
+  }
+  proc->variant = best;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return REX_OK;
 }
 
 void rex_free_process(rex_proc* proc) {

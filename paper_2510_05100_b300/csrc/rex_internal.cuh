@@ -48,9 +48,58 @@ struct EwLaunch {
   EwPoint pt[MAX_EW_POINTS + 1];
 };
 
+// Persistent multi-process launch (kernels_multi.cu): up to MULTI_MAX_BATCH
+// subprocess batches, up to MULTI_MAX_POINTS points per launch.
+constexpr int MULTI_MAX_BATCH = 8;
+constexpr int MULTI_MAX_POINTS = 64;
+
+struct MultiTable {     // QCD batch: the QcdLaunch fields a tile reads
+  int nmass, k, mode, has_width;
+  int64_t out_stride;
+  double factor0;
+  double mass[MULTI_MAX_POINTS + 1];
+  double width[MULTI_MAX_POINTS + 1];
+  int slot[MULTI_MAX_POINTS];
+  double factor[MULTI_MAX_POINTS];
+};
+
+struct MultiBatch {
+  int kind;
+  int64_t nev, tile_begin, tile_end;   // work items [tile_begin, tile_end) of the launch
+  const double* mom;
+  const double* w_in;
+  double* out;
+  MultiTable t;
+};
+
+struct EwTable {        // the e+e- batch (at most one per launch)
+  int k, mode;
+  int64_t out_stride;
+  EwPoint pt[MULTI_MAX_POINTS + 1];
+};
+
+struct MultiLaunch {
+  int nbatch;
+  int64_t total;        // work items
+  MultiBatch b[MULTI_MAX_BATCH];
+  EwTable ew;
+};
+
+int multi_events_per_tile(int kind, int mixed);
+int multi_grid_size(int mixed, int width, int* blocks);
+int launch_multi(int mixed, int width, int blocks, const MultiLaunch& ml, unsigned long long* counter,
+                 void* stream);
+
+// Thread-mapping variants of the QCD kernels (see qcd_kernel.cuh).
+constexpr int QCD_NVARIANT = 5;
+
 // Launchers (defined in the kernel translation units).  Return cudaError_t as int.
-int launch_qcd(int proc, int mixed, const double* mom, const double* w_in, int64_t nev,
-               const QcdLaunch& lp, double* out, void* stream);
+int launch_gg_ttx(int mixed, int variant, const double* mom, const double* w_in, int64_t nev,
+                  const QcdLaunch& lp, double* out, void* stream);
+int launch_gg_ttxg(int mixed, int variant, const double* mom, const double* w_in, int64_t nev,
+                   const QcdLaunch& lp, double* out, void* stream);
+int launch_gg_ttxgg(int mixed, int variant, const double* mom, const double* w_in, int64_t nev,
+                    const QcdLaunch& lp, double* out, void* stream);
 int launch_ee(const double* mom, const double* w_in, int64_t nev, const EwLaunch& lp,
               double* out, void* stream);
 

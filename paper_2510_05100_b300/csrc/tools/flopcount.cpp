@@ -12,6 +12,9 @@
 #define __device__
 #define __host__
 #define __forceinline__ inline
+#define __restrict__
+template <typename T>
+inline T __ldg(const T* p) { return *p; }
 
 template <int TAG>
 struct Cnt {
@@ -51,6 +54,8 @@ inline bool operator>=(Cnt<T> a, Cnt<T> b) { return a.v >= b.v; }
 template <int T>
 inline bool operator<=(Cnt<T> a, Cnt<T> b) { return a.v <= b.v; }
 template <int T>
+inline Cnt<T> fma(Cnt<T> a, Cnt<T> b, Cnt<T> c) { Cnt<T>::flops += 2; return Cnt<T>(a.v * b.v + c.v); }
+template <int T>
 inline Cnt<T> sqrt(Cnt<T> a) { ++Cnt<T>::flops; return Cnt<T>(std::sqrt(a.v)); }
 template <int T>
 inline Cnt<T> rsqrt(Cnt<T> a) { ++Cnt<T>::flops; return Cnt<T>(1.0 / std::sqrt(a.v)); }
@@ -62,52 +67,62 @@ using AC = Cnt<1>;    // colour / helicity accumulation
 
 using namespace rex;
 
-template <int NG, class ST, class GS, class QL>
-void count(const char* name, int nghel, GS gs, QL ql, bool last) {
-  const int ngluon = NG;
-  RC pg[NG][4], eps[NG][4], pt[4], ptb[4];
-  for (int i = 0; i < NG; ++i)
+// FP64 invariants in the event and mass setup are plain doubles and are not
+// counted (a few tens of operations per event).
+// Counts per call: event setup (once per event), mass setup (once per event and
+// mass slot), gluon currents (once per event and polarisation configuration),
+// polarisation vectors (idem), quark line (once per event, polarisation
+// configuration and mass slot).
+template <int NG, class EV, class MS, class GL, class ES, class MSF, class GC, class QL>
+void count(const char* name, int nghel, ES es, MSF msf, GC gc, QL ql, bool last) {
+  double p[NG + 2][4];
+  RC eps[NG][4], pr[NG + 2][4];
+  for (int i = 0; i < NG + 2; ++i)
     for (int m = 0; m < 4; ++m) {
-      pg[i][m] = RC(1.0 + i + 0.1 * m);
-      eps[i][m] = RC(0.5);
+      p[i][m] = 1.0 + i + 0.1 * m;
+      pr[i][m] = RC(p[i][m]);
     }
-  for (int m = 0; m < 4; ++m) {
-    pt[m] = RC(2.0 + m);
-    ptb[m] = RC(3.0 + m);
-  }
-  ST st;
+  for (int i = 0; i < NG; ++i)
+    for (int m = 0; m < 4; ++m) eps[i][m] = RC(0.5);
+  EV ev;
+  MS mm;
+  GL J;
   RC::flops = 0;
-  AC::flops = 0;
-  gs(pg, eps, ptb, st);
-  const long long f_state = RC::flops;
-  // external polarisation vectors (pol_linear) are counted with the state
+  es(&p[0][0], ev);
+  const long long f_event = RC::flops;
+  RC::flops = 0;
+  msf(ev, 173.0, 0.0, mm);
+  const long long f_mass = RC::flops;
+  RC::flops = 0;
   RC e[4];
-  RC::flops = 0;
-  for (int g = 0; g < ngluon; ++g) pol_linear(pg[g], 0, e);
+  for (int g = 0; g < NG; ++g) pol_linear(pr[g], 0, e);
   const long long f_pol = RC::flops;
   RC::flops = 0;
+  gc(ev, eps, J);
+  const long long f_gluon = RC::flops;
+  RC::flops = 0;
   AC::flops = 0;
-  ql(st, pt, ptb, RC(173.0), RC(0.0));
+  ql(ev, mm, J);
   const long long f_line_r = RC::flops, f_line_a = AC::flops;
-  std::printf("  \"%s\": {\"nghel\": %d, \"gluon_state\": %lld, \"polarisations\": %lld, "
-              "\"quark_line_amp\": %lld, \"quark_line_acc\": %lld}%s\n",
-              name, nghel, f_state, f_pol, f_line_r, f_line_a, last ? "" : ",");
+  std::printf("  \"%s\": {\"nghel\": %d, \"event_setup\": %lld, \"mass_setup\": %lld, "
+              "\"polarisations\": %lld, \"gluon_currents\": %lld, \"quark_line_amp\": %lld, "
+              "\"quark_line_acc\": %lld}%s\n",
+              name, nghel, f_event, f_mass, f_pol, f_gluon, f_line_r, f_line_a, last ? "" : ",");
 }
+
+#define REX_COUNT(NAME, NG, LAST)                                                                   \
+  count<NG, NAME##_event<RC>, NAME##_mass<RC>, NAME##_gluons<RC>>(                                  \
+      #NAME, 1 << NG,                                                                               \
+      [](const double* p, auto& ev) { NAME##_event_phase1(p, ev, 0, 1); NAME##_event_phase2(ev, 0, 1); }, \
+      [](auto& ev, double m, double w, auto& mm) { NAME##_mass_setup<RC, false>(ev, m, w, mm, 0, 1); }, \
+      [](auto& ev, auto& eps, auto& J) { NAME##_gluon_currents(ev, eps, J); },                       \
+      [](auto& ev, auto& mm, auto& J) { return NAME##_quark_line<RC, AC, false, RC>(ev, mm, J); }, LAST)
 
 int main() {
   std::printf("{\n");
-  count<2, gg_ttx_gluons<RC>>(
-      "gg_ttx", 4, [](auto& a, auto& b, auto& c, auto& d) { gg_ttx_gluon_state(a, b, c, d); },
-      [](auto& s, auto& a, auto& b, RC m, RC w) { return gg_ttx_quark_line<RC, AC, false>(s, a, b, m, w); },
-      false);
-  count<3, gg_ttxg_gluons<RC>>(
-      "gg_ttxg", 8, [](auto& a, auto& b, auto& c, auto& d) { gg_ttxg_gluon_state(a, b, c, d); },
-      [](auto& s, auto& a, auto& b, RC m, RC w) { return gg_ttxg_quark_line<RC, AC, false>(s, a, b, m, w); },
-      false);
-  count<4, gg_ttxgg_gluons<RC>>(
-      "gg_ttxgg", 16, [](auto& a, auto& b, auto& c, auto& d) { gg_ttxgg_gluon_state(a, b, c, d); },
-      [](auto& s, auto& a, auto& b, RC m, RC w) { return gg_ttxgg_quark_line<RC, AC, false>(s, a, b, m, w); },
-      true);
+  REX_COUNT(gg_ttx, 2, false);
+  REX_COUNT(gg_ttxg, 3, false);
+  REX_COUNT(gg_ttxgg, 4, true);
   std::printf("}\n");
   return 0;
 }

@@ -3,7 +3,9 @@
 Compiles and runs csrc/tools/flopcount.cpp (the generated amplitude routines
 instantiated with a counting scalar type) with the host compiler and caches the
 result under _build/.  Counts are per call of each routine:
-  gluon_state, polarisations   once per (event, gluon polarisation configuration)
+  event_setup                  once per event
+  mass_setup                   once per (event, mass slot)
+  polarisations, gluon_currents once per (event, gluon polarisation configuration)
   quark_line_amp / _acc        once per (event, gluon polarisation, mass slot);
                                amplitude arithmetic / colour+helicity accumulation.
 """
@@ -40,6 +42,7 @@ def per_event(proc: str, nmass: int) -> dict:
     """
     c = counts()[proc]
     nh = c["nghel"]
-    amp = nh * (c["gluon_state"] + c["polarisations"] + nmass * c["quark_line_amp"])
+    amp = (c["event_setup"] + nmass * c["mass_setup"]
+           + nh * (c["gluon_currents"] + c["polarisations"] + nmass * c["quark_line_amp"]))
     acc = nh * nmass * c["quark_line_acc"]
     return {"amp": amp, "acc": acc, "total": amp + acc}

@@ -34,7 +34,9 @@ FLAG_NO_DEDUPE = 1
 EXPORTS = (
     "rex_init_process", "rex_process_npart", "rex_set_flags", "rex_set_params",
     "rex_reweight", "rex_reweight_host", "rex_me2", "rex_free_process",
-    "rex_last_error", "rex_version", "rex_probe_fma",
+    "rex_last_error", "rex_version", "rex_probe_fma", "rex_num_variants", "rex_get_variant",
+    "rex_set_variant", "rex_autotune", "rex_multi_create", "rex_reweight_multi", "rex_multi_capture",
+    "rex_multi_replay", "rex_multi_free",
 )
 
 
@@ -42,6 +44,11 @@ class RexError(RuntimeError):
     def __init__(self, code: int, msg: str):
         super().__init__(f"rex error {code}: {msg}")
         self.code = code
+
+
+class Batch(ctypes.Structure):
+    _fields_ = [("proc", ctypes.c_void_p), ("momenta", ctypes.c_void_p), ("w_in", ctypes.c_void_p),
+                ("nev", ctypes.c_int64), ("w_out", ctypes.c_void_p)]
 
 
 class Params(ctypes.Structure):
@@ -88,6 +95,25 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.rex_last_error.restype = ctypes.c_char_p
     lib.rex_probe_fma.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_double), vp]
     lib.rex_probe_fma.restype = ctypes.c_int
+    lib.rex_num_variants.argtypes = [vp]
+    lib.rex_num_variants.restype = ctypes.c_int
+    lib.rex_get_variant.argtypes = [vp]
+    lib.rex_get_variant.restype = ctypes.c_int
+    lib.rex_set_variant.argtypes = [vp, ctypes.c_int]
+    lib.rex_set_variant.restype = ctypes.c_int
+    lib.rex_autotune.argtypes = [vp, vp, vp, i64, pp, ctypes.c_int, vp, vp, ctypes.POINTER(ctypes.c_float)]
+    lib.rex_autotune.restype = ctypes.c_int
+    bp = ctypes.POINTER(Batch)
+    lib.rex_multi_create.argtypes = [ctypes.c_int, ctypes.POINTER(vp)]
+    lib.rex_multi_create.restype = ctypes.c_int
+    lib.rex_reweight_multi.argtypes = [vp, bp, ctypes.c_int, pp, ctypes.c_int, vp]
+    lib.rex_reweight_multi.restype = ctypes.c_int
+    lib.rex_multi_capture.argtypes = [vp, bp, ctypes.c_int, pp, ctypes.c_int]
+    lib.rex_multi_capture.restype = ctypes.c_int
+    lib.rex_multi_replay.argtypes = [vp, vp]
+    lib.rex_multi_replay.restype = ctypes.c_int
+    lib.rex_multi_free.argtypes = [vp]
+    lib.rex_multi_free.restype = None
     lib.rex_version.argtypes = []
     lib.rex_version.restype = ctypes.c_char_p
     _lib = lib
@@ -178,6 +204,27 @@ class Process:
         _check(load().rex_reweight_host(self._h, _ptr(momenta), _ptr(w_in), momenta.shape[0], arr,
                                         len(points), _ptr(w_out), _stream_ptr(stream)))
 
+    @property
+    def num_variants(self) -> int:
+        return load().rex_num_variants(self._h)
+
+    @property
+    def variant(self) -> int:
+        return load().rex_get_variant(self._h)
+
+    @variant.setter
+    def variant(self, v: int) -> None:
+        _check(load().rex_set_variant(self._h, v))
+
+    def autotune(self, momenta, w_in, points: Sequence[dict], w_out, stream=None) -> list:
+        """Time every kernel variant on these device buffers, keep the fastest; returns ms per variant."""
+        n = max(1, self.num_variants)
+        ms = (ctypes.c_float * n)()
+        arr = _param_array(points)
+        _check(load().rex_autotune(self._h, _ptr(momenta), _ptr(w_in), momenta.shape[0], arr, len(points),
+                                   _ptr(w_out), _stream_ptr(stream), ms))
+        return list(ms)
+
     def me2(self, momenta, point: dict, out=None, stream=None):
         import torch
         nev = momenta.shape[0]
@@ -187,6 +234,48 @@ class Process:
         _check(load().rex_me2(self._h, _ptr(momenta), nev, ctypes.byref(p), _ptr(out),
                               _stream_ptr(stream)))
         return out
+
+
+class Multi:
+    """Several subprocess batches in one persistent launch (rex_multi_*)."""
+
+    def __init__(self, precision: int = FP64):
+        h = ctypes.c_void_p()
+        _check(load().rex_multi_create(precision, ctypes.byref(h)))
+        self._h = h
+        self.precision = precision
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().rex_multi_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @staticmethod
+    def _batches(batches):
+        arr = (Batch * len(batches))()
+        for i, (proc, mom, w_in, w_out) in enumerate(batches):
+            arr[i] = Batch(proc._h.value if isinstance(proc._h, ctypes.c_void_p) else proc._h,
+                           _ptr(mom), _ptr(w_in), mom.shape[0], _ptr(w_out))
+        return arr
+
+    def reweight(self, batches, points: Sequence[dict], stream=None) -> None:
+        """batches: [(Process, momenta, w_in, w_out)] device tensors; enqueued on stream."""
+        arr = self._batches(batches)
+        _check(load().rex_reweight_multi(self._h, arr, len(batches), _param_array(points), len(points),
+                                         _stream_ptr(stream)))
+
+    def capture(self, batches, points: Sequence[dict]) -> None:
+        arr = self._batches(batches)
+        _check(load().rex_multi_capture(self._h, arr, len(batches), _param_array(points), len(points)))
+
+    def replay(self, stream=None) -> None:
+        _check(load().rex_multi_replay(self._h, _stream_ptr(stream)))
 
 
 def probe_fma(fp64: bool, stream=None) -> float:

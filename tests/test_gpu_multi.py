@@ -1,0 +1,107 @@
+"""Persistent multi-process launch vs the single-process entry point and the
+oracle, through the C ABI (needs a B300)."""
+import numpy as np
+import pytest
+
+from rexlib import ensure_built
+from oracle import reweight as oracle_rw
+from paper_2510_05100_b300 import phase_space as ps
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+ORIG_QCD = dict(mt=173.0, wt=0.0, alphas=0.118)
+SIZES = {"ee_mumu": 150, "gg_ttx": 101, "gg_ttxg": 53, "gg_ttxgg": 19}
+
+
+@pytest.fixture(scope="module")
+def rex():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return ensure_built()
+
+
+def points(k):
+    g = ps.grid_64()
+    return [dict(g[(7 * j) % 64], **ps.EE_NEW) for j in range(k)]
+
+
+def setup(rex, precision, seed=11):
+    out = []
+    for proc, n in SIZES.items():
+        mom = ps.make_events(proc, n, seed + n)
+        w = np.random.default_rng(n).uniform(0.5, 2.0, n)
+        p = rex.Process(proc, 0 if proc == "ee_mumu" else precision)   # ee_mumu: FP64 only
+        p.set_params(ps.EE_ORIGINAL if proc == "ee_mumu" else ORIG_QCD)
+        out.append((proc, p, mom, w))
+    return out
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_multi_matches_single_process_launches(rex, precision):
+    pts = points(9)
+    items = setup(rex, precision)
+    m = rex.Multi(precision)
+    batches, single = [], []
+    for proc, p, mom, w in items:
+        dm, dw = dev(mom), dev(w)
+        wo = torch.zeros((mom.shape[0], len(pts)), dtype=torch.float64, device="cuda")
+        batches.append((p, dm, dw, wo))
+        single.append(p.reweight(dm, dw, pts).cpu().numpy())
+    m.reweight(batches, pts)
+    torch.cuda.synchronize()
+    for (proc, p, mom, w), b, ref in zip(items, batches, single):
+        got = b[3].cpu().numpy()
+        assert np.max(np.abs(got / ref - 1.0)) < 1e-13, proc
+        if precision == 0:
+            orc = oracle_rw.reweight(proc, mom, w, ps.EE_ORIGINAL if proc == "ee_mumu" else ORIG_QCD, pts[:3])
+            assert np.max(np.abs(got[:, :3] / orc - 1.0)) < 1e-12, proc
+
+
+def test_multi_graph_replay_and_point_chunks(rex):
+    """70 points: two launches per call (64 + 6); a captured graph replays them."""
+    pts = points(70)
+    items = setup(rex, 1, seed=21)
+    m = rex.Multi(1)
+    batches, refs = [], []
+    for proc, p, mom, w in items:
+        dm, dw = dev(mom), dev(w)
+        batches.append((p, dm, dw, torch.zeros((mom.shape[0], 70), dtype=torch.float64, device="cuda")))
+        refs.append(p.reweight(dm, dw, pts).cpu().numpy())
+    m.capture(batches, pts)
+    for b in batches:
+        b[3].zero_()
+    m.replay()
+    torch.cuda.synchronize()
+    for b, ref in zip(batches, refs):
+        assert np.max(np.abs(b[3].cpu().numpy() / ref - 1.0)) < 1e-13
+
+
+def test_multi_validation(rex):
+    pts = points(2)
+    m = rex.Multi(0)
+    p64 = rex.Process("gg_ttx", 0)
+    p64.set_params(ORIG_QCD)
+    pmx = rex.Process("gg_ttx", 1)
+    pmx.set_params(ORIG_QCD)
+    mom = dev(ps.make_events("gg_ttx", 4, 1))
+    w = dev(np.ones(4))
+    wo = torch.zeros((4, 2), dtype=torch.float64, device="cuda")
+    with pytest.raises(rex.RexError):
+        m.reweight([], pts)
+    with pytest.raises(rex.RexError):
+        m.reweight([(pmx, mom, w, wo)], pts)          # precision mismatch
+    ee = [rex.Process("ee_mumu", 0) for _ in range(2)]
+    for e in ee:
+        e.set_params(ps.EE_ORIGINAL)
+    emom = dev(ps.make_events("ee_mumu", 4, 1))
+    with pytest.raises(rex.RexError):
+        m.reweight([(ee[0], emom, w, wo), (ee[1], emom, w, wo)], pts)
+    with pytest.raises(rex.RexError):
+        m.replay()                                    # nothing captured
+    m.reweight([(p64, mom[:0], w[:0], wo[:0])], pts)  # empty batch: no-op
+    m.reweight([(p64, mom, w, wo)], [])               # no points: no-op

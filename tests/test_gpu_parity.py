@@ -218,3 +218,36 @@ def test_full_size_workload_sampled(rex):
     idx = np.concatenate([idx, [0, n - 1]])
     ref = oracle_rw.reweight("gg_ttxg", mom[idx], w[idx], ORIG_QCD, pts)
     assert np.max(rel(got[idx], ref)) < FP64_TOL
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("proc", ["gg_ttx", "gg_ttxg", "gg_ttxgg"])
+def test_every_kernel_variant(rex, proc, precision):
+    """Each thread-mapping variant against the oracle (FP64) or the mixed bound."""
+    n = SIZES[proc]
+    mom = ps.make_events(proc, n, 515)
+    w = np.random.default_rng(8).uniform(0.5, 2.0, n)
+    pts = new_points(proc)[:4]
+    ref = oracle_rw.reweight(proc, mom, w, ORIG_QCD, pts)
+    p = make(proc, rex, precision)
+    tol = FP64_TOL if precision == 0 else MIXED_TOL[proc]
+    assert p.num_variants == 5
+    for v in range(p.num_variants):
+        p.variant = v
+        got = p.reweight(dev(mom), dev(w), pts).cpu().numpy()
+        assert np.max(rel(got, ref)) < tol, (v, np.max(rel(got, ref)))
+        same = p.reweight(dev(mom), dev(w), [ORIG_QCD]).cpu().numpy()
+        assert np.array_equal(same[:, 0], w), v
+
+
+def test_autotune_picks_the_fastest_variant(rex):
+    n = 1 << 14
+    mom = dev(ps.make_events("gg_ttxg", n, 616))
+    w = dev(np.ones(n))
+    out = torch.empty((n, 16), dtype=torch.float64, device="cuda")
+    p = make("gg_ttxg", rex, 1)
+    ms = p.autotune(mom, w, ps.grid_gg_ttxg(), out)
+    assert len(ms) == 5 and all(t > 0 for t in ms)
+    assert p.variant == int(np.argmin(ms))
+    with pytest.raises(rex.RexError):
+        p.variant = 5
