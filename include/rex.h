@@ -181,6 +181,35 @@ int rex_multi_replay(rex_multi *m, void *stream);
 /* Release a multi handle (NULL is ignored). */
 void rex_multi_free(rex_multi *m);
 
+/* Allocation-free form of rex_reweight_multi.  The paper has no counterpart:
+ * this entry point exists for callers that cannot call cudaMalloc, and so
+ * cannot create the rex_multi handle (whose creation allocates its device
+ * work counter).  Two kinds of caller are in that position: code that
+ * records its work into a CUDA graph with global stream capture, where a
+ * device allocation is an illegal call inside the captured region; and
+ * applications whose device memory belongs to a framework's caching
+ * allocator or to a fixed budget, which forbid allocations made outside it.
+ *
+ * Same computation and arguments as rex_reweight_multi, with the precision
+ * given here instead of by a handle.  The caller still owns and passes every
+ * input and output.  The only scratch, the persistent kernel's 64-bit work
+ * counter, lives in a static device array that every GPU which loads the
+ * library holds until the process exits; the call allocates nothing and
+ * calls no allocating routine.
+ *
+ * Limits: at most 64 points per call (one launch on the one static counter)
+ * and 8 batches; a larger k is rejected with REX_EINVAL and a message.
+ * Set-up: the first call on each device (with that device current) looks up
+ * the counter's device address with cudaGetSymbolAddress and the persistent
+ * grid size; make that first call before any stream capture.  Each call
+ * clears the counter on stream before its kernel.  Every call shares the same
+ * counter, so calls whose kernels overlap on the GPU race with each other:
+ * enqueue them on one stream, or otherwise serialise them.
+ * Errors: REX_EINVAL, REX_ENOTINIT, REX_ECUDA. */
+int rex_reweight_multi_noalloc(const rex_batch *batches, int nbatch,
+                               const rex_params *param_sets, int k,
+                               int precision, void *stream);
+
 /* Release a handle (NULL is ignored).  Synchronises nothing; the caller must
  * make sure no work enqueued with the handle is still running. */
 void rex_free_process(rex_proc *proc);

@@ -10,6 +10,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <utility>
 #include <string>
@@ -435,6 +436,79 @@ int rex_multi_replay(rex_multi* m, void* stream) {
   const cudaError_t e = cudaGraphLaunch(m->exec, static_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) return cuda_fail((int)e, "cudaGraphLaunch");
   return REX_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Allocation-free multi-process entry point
+// ---------------------------------------------------------------------------
+// Scratch of rex_reweight_multi_noalloc: the persistent kernel's 64-bit work
+// counter, held in this fixed device array instead of a handle's cudaMalloc'd
+// buffer.  Every GPU that loads the library holds these 256 bytes until exit.
+constexpr int NOALLOC_COUNTERS = 1;   // one launch per call
+static __device__ __align__(256) unsigned long long g_noalloc_counter[NOALLOC_COUNTERS];
+
+namespace {
+
+constexpr int NOALLOC_MAX_DEVICES = 64;
+
+struct NoallocDevice {
+  bool ready;
+  unsigned long long* counter;   // device address of g_noalloc_counter on this device
+  int blocks[2][2];              // persistent grid size [mixed][width]
+};
+
+std::mutex g_noalloc_mutex;
+NoallocDevice g_noalloc[NOALLOC_MAX_DEVICES];
+
+// Once per device, with that device current: look up the array's device
+// address and the persistent grid sizes.  Neither call allocates.
+int noalloc_setup(NoallocDevice** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail((int)e, "cudaGetDevice");
+  if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) return fail(REX_EINVAL, "device ordinal %d out of range", dev);
+  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+  NoallocDevice& d = g_noalloc[dev];
+  if (!d.ready) {
+    void* ptr = nullptr;
+    e = cudaGetSymbolAddress(&ptr, g_noalloc_counter);
+    if (e != cudaSuccess) return cuda_fail((int)e, "cudaGetSymbolAddress of the static work counter");
+    for (int mixed = 0; mixed < 2; ++mixed)
+      for (int width = 0; width < 2; ++width) {
+        const int err = multi_grid_size(mixed, width, &d.blocks[mixed][width]);
+        if (err != 0) return cuda_fail(err, "occupancy query");
+      }
+    d.counter = static_cast<unsigned long long*>(ptr);
+    d.ready = true;
+  }
+  *out = &d;
+  return REX_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int rex_reweight_multi_noalloc(const rex_batch* batches, int nbatch, const rex_params* param_sets, int k,
+                               int precision, void* stream) {
+  if (precision != REX_FP64 && precision != REX_MIXED) return fail(REX_EINVAL, "unknown precision %d", precision);
+  if (k > MULTI_MAX_POINTS * NOALLOC_COUNTERS)
+    return fail(REX_EINVAL,
+                "rex_reweight_multi_noalloc takes at most %d points per call (one launch on its static "
+                "work counter); got k = %d: split the points over several calls",
+                MULTI_MAX_POINTS * NOALLOC_COUNTERS, k);
+  NoallocDevice* d = nullptr;
+  const int rc = noalloc_setup(&d);
+  if (rc) return rc;
+  rex_multi tmp;
+  std::memset(&tmp, 0, sizeof tmp);
+  tmp.precision = precision;
+  tmp.counter = d->counter;
+  tmp.blocks[0] = d->blocks[precision == REX_MIXED][0];
+  tmp.blocks[1] = d->blocks[precision == REX_MIXED][1];
+  return multi_impl(&tmp, batches, nbatch, param_sets, k, stream);
 }
 
 void rex_multi_free(rex_multi* m) {

@@ -36,7 +36,7 @@ EXPORTS = (
     "rex_reweight", "rex_reweight_host", "rex_me2", "rex_free_process",
     "rex_last_error", "rex_version", "rex_probe_fma", "rex_num_variants", "rex_get_variant",
     "rex_set_variant", "rex_autotune", "rex_multi_create", "rex_reweight_multi", "rex_multi_capture",
-    "rex_multi_replay", "rex_multi_free",
+    "rex_multi_replay", "rex_multi_free", "rex_reweight_multi_noalloc",
 )
 
 
@@ -114,6 +114,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.rex_multi_replay.restype = ctypes.c_int
     lib.rex_multi_free.argtypes = [vp]
     lib.rex_multi_free.restype = None
+    lib.rex_reweight_multi_noalloc.argtypes = [bp, ctypes.c_int, pp, ctypes.c_int, ctypes.c_int, vp]
+    lib.rex_reweight_multi_noalloc.restype = ctypes.c_int
     lib.rex_version.argtypes = []
     lib.rex_version.restype = ctypes.c_char_p
     _lib = lib
@@ -276,6 +278,17 @@ class Multi:
 
     def replay(self, stream=None) -> None:
         _check(load().rex_multi_replay(self._h, _stream_ptr(stream)))
+
+
+def reweight_multi_noalloc(batches, points: Sequence[dict], precision: int = FP64, stream=None) -> None:
+    """rex_reweight_multi_noalloc: the multi-process launch without any library
+    allocation, for callers that cannot allocate device memory (at most 64 points).
+
+    batches: [(Process, momenta, w_in, w_out)] device tensors; enqueued on stream.
+    """
+    arr = Multi._batches(batches)
+    _check(load().rex_reweight_multi_noalloc(arr, len(batches), _param_array(points), len(points),
+                                             precision, _stream_ptr(stream)))
 
 
 def probe_fma(fp64: bool, stream=None) -> float:

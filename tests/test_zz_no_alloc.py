@@ -1,0 +1,73 @@
+"""rex_reweight_multi_noalloc, the allocation-free multi-process entry point.
+
+Callers that cannot allocate device memory (graph capture in global mode,
+framework-owned memory budgets) use this entry point instead of a rex_multi
+handle.  The test calls it twice in a row through the C ABI and checks every
+output against the single-process entry point rex_reweight.  It lives in its
+own file, collected last, and sets everything up itself, so it passes both
+alone in a fresh process and after the other tests.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+
+from rexlib import ensure_built
+from paper_2510_05100_b300 import phase_space as ps
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+ORIG_QCD = dict(mt=173.0, wt=0.0, alphas=0.118)
+TOL = 1e-13     # the multi-launch tests' tolerance against rex_reweight
+
+
+@pytest.fixture(scope="module")
+def rex():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return ensure_built()
+
+
+def test_noalloc_matches_single_process_entry_point_twice(rex):
+    lib = rex.load()
+    grid = ps.grid_64()
+    pts = [dict(grid[(5 * j) % 64], **ps.EE_NEW) for j in range(12)]
+    parr = (rex.Params * len(pts))(*[rex.params(p) for p in pts])
+    for precision in (0, 1):
+        items = []
+        for proc, n, seed in (("ee_mumu", 130, 1), ("gg_ttx", 97, 2), ("gg_ttxg", 45, 3), ("gg_ttxgg", 13, 4)):
+            h = rex.Process(proc, 0 if proc == "ee_mumu" else precision)
+            h.set_params(ps.EE_ORIGINAL if proc == "ee_mumu" else ORIG_QCD)
+            mom = torch.from_numpy(ps.make_events(proc, n, seed)).cuda()
+            w = torch.from_numpy(np.random.default_rng(seed).uniform(0.5, 2.0, n)).cuda()
+            ref = h.reweight(mom, w, pts).cpu().numpy()
+            items.append((h, mom, w, ref))
+        for call in range(2):
+            outs = [torch.full((it[1].shape[0], len(pts)), -1.0, dtype=torch.float64, device="cuda")
+                    for it in items]
+            barr = (rex.Batch * len(items))()
+            for i, ((h, mom, w, _), o) in enumerate(zip(items, outs)):
+                barr[i] = rex.Batch(h._h.value, mom.data_ptr(), w.data_ptr(), mom.shape[0], o.data_ptr())
+            stream = torch.cuda.current_stream().cuda_stream
+            rc = lib.rex_reweight_multi_noalloc(barr, len(items), parr, len(pts), precision,
+                                                ctypes.c_void_p(stream))
+            assert rc == 0, lib.rex_last_error()
+            torch.cuda.synchronize()
+            for (h, _, _, ref), o in zip(items, outs):
+                got = o.cpu().numpy()
+                assert np.max(np.abs(got / ref - 1.0)) < TOL, (h.name, precision, call)
+
+
+def test_noalloc_rejects_more_points_than_its_counter_covers(rex):
+    lib = rex.load()
+    h = rex.Process("gg_ttx", 0)
+    h.set_params(ORIG_QCD)
+    mom = torch.from_numpy(ps.make_events("gg_ttx", 8, 5)).cuda()
+    w = torch.ones(8, dtype=torch.float64, device="cuda")
+    o = torch.zeros((8, 65), dtype=torch.float64, device="cuda")
+    barr = (rex.Batch * 1)(rex.Batch(h._h.value, mom.data_ptr(), w.data_ptr(), 8, o.data_ptr()))
+    pts = [dict(ORIG_QCD, **ps.EE_NEW)] * 65
+    parr = (rex.Params * 65)(*[rex.params(p) for p in pts])
+    assert lib.rex_reweight_multi_noalloc(barr, 1, parr, 65, 0, None) == rex.REX_EINVAL
+    assert b"at most 64 points" in lib.rex_last_error()
