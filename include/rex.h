@@ -163,6 +163,15 @@ typedef struct {
  * Errors: REX_EINVAL, REX_ENOMEM, REX_ECUDA. */
 int rex_multi_create(int precision, rex_multi **out);
 
+/* Execution mode of a multi handle (rex_multi_set_mode; errors: REX_EINVAL):
+ * REX_MULTI_PERSISTENT (default): one persistent kernel over every batch's
+ *   event tiles, fed by the device work counter;
+ * REX_MULTI_STREAMS: each batch's own tuned single-process kernel on a
+ *   stream forked from (and joined back into) the caller's stream. */
+#define REX_MULTI_PERSISTENT 0
+#define REX_MULTI_STREAMS 1
+int rex_multi_set_mode(rex_multi *m, int mode);
+
 /* Reweight every batch to the same k points (host array, copied).  Each
  * batch's original point is its handle's.  Enqueues a counter reset and one
  * kernel per 64 points on stream; allocates nothing, so it can be captured.

@@ -35,6 +35,12 @@ __device__ __forceinline__ cx<double> cmdot(const cx<double>* a, const cx<double
 }
 
 // One tile of 128 events, thread per event.  TABLE: k, mode, out_stride, pt[0..k].
+//
+// With d_a(h) = JeX(h).JmY(h) for the four chirality pairs a = (X, Y) and the
+// point's coefficients c_a, the helicity sum is a Hermitian form
+//     sum_h |sum_a c_a d_a(h)|^2 = c^dag H c,   H_ab = sum_h conj(d_a(h)) d_b(h),
+// so H (parameter independent) is built once per event from the 16 helicity
+// configurations and every point costs one 4x4 form.
 template <class TABLE>
 __device__ __forceinline__ void ee_tile(const double* __restrict__ mom, const double* __restrict__ w_in,
                                         int64_t nev, int64_t tile, const TABLE& lp, double* __restrict__ out) {
@@ -53,6 +59,40 @@ __device__ __forceinline__ void ee_tile(const double* __restrict__ mom, const do
   for (int m = 0; m < 4; ++m) q[m] = p[0][m] + p[1][m];
   const double s = mdot(q, q);
 
+  // H: diagonal (real) and upper triangle (complex) of the 4x4 Hermitian form
+  double hd[4] = {0.0, 0.0, 0.0, 0.0};
+  cx<double> ho[6] = {};
+#pragma unroll 1
+  for (int h = 0; h < 16; ++h) {
+    const int l1 = (h & 1) ? 1 : -1, l2 = (h & 2) ? 1 : -1;
+    const int l3 = (h & 4) ? 1 : -1, l4 = (h & 8) ? 1 : -1;
+    cx<double> v1[4], u2[4], v3[4], u4[4];
+    spinor_v(p[0], 0.0, l1, v1);
+    spinor_u(p[1], 0.0, l2, u2);
+    spinor_v(p[2], 0.0, l3, v3);
+    spinor_u(p[3], 0.0, l4, u4);
+    cx<double> je[2][4], jm[2][4];
+    chiral_current(v1, u2, -1.0, je[0]);          // vbar1 gamma P_L u2
+    chiral_current(v1 + 2, u2 + 2, 1.0, je[1]);   // vbar1 gamma P_R u2
+    chiral_current(u4, v3, -1.0, jm[0]);          // ubar4 gamma P_L v3
+    chiral_current(u4 + 2, v3 + 2, 1.0, jm[1]);   // ubar4 gamma P_R v3
+    cx<double> d[4];
+#pragma unroll
+    for (int x = 0; x < 2; ++x)
+#pragma unroll
+      for (int y = 0; y < 2; ++y) d[2 * x + y] = cmdot(je[x], jm[y]);
+    int o = 0;
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      hd[a] += d[a].re * d[a].re + d[a].im * d[a].im;
+#pragma unroll
+      for (int b2 = a + 1; b2 < 4; ++b2) {
+        ho[o] = ho[o] + cdot1(d[a], d[b2]);   // conj(d_a) d_b
+        ++o;
+      }
+    }
+  }
+
   double me2_0 = 0.0;
   for (int j = 0; j <= lp.k; ++j) {
     const EwPoint& c = lp.pt[j];
@@ -63,27 +103,19 @@ __device__ __forceinline__ void ee_tile(const double* __restrict__ mom, const do
     cx<double> coef[4];
 #pragma unroll
     for (int xy = 0; xy < 4; ++xy) coef[xy] = cx<double>{ca, 0.0} + c.gzz[xy] * dz;
+    // sum_h |sum_a c_a d_a|^2 = sum_ab conj(c_a) c_b H_ab
+    //                        = sum_a |c_a|^2 H_aa + 2 Re sum_{a<b} conj(c_a) c_b H_ab
     double sum = 0.0;
-#pragma unroll 1
-    for (int h = 0; h < 16; ++h) {
-      const int l1 = (h & 1) ? 1 : -1, l2 = (h & 2) ? 1 : -1;
-      const int l3 = (h & 4) ? 1 : -1, l4 = (h & 8) ? 1 : -1;
-      cx<double> v1[4], u2[4], v3[4], u4[4];
-      spinor_v(p[0], 0.0, l1, v1);
-      spinor_u(p[1], 0.0, l2, u2);
-      spinor_v(p[2], 0.0, l3, v3);
-      spinor_u(p[3], 0.0, l4, u4);
-      cx<double> je[2][4], jm[2][4];
-      chiral_current(v1, u2, -1.0, je[0]);          // vbar1 gamma P_L u2
-      chiral_current(v1 + 2, u2 + 2, 1.0, je[1]);   // vbar1 gamma P_R u2
-      chiral_current(u4, v3, -1.0, jm[0]);          // ubar4 gamma P_L v3
-      chiral_current(u4 + 2, v3 + 2, 1.0, jm[1]);   // ubar4 gamma P_R v3
-      cx<double> amp = cx<double>{0.0, 0.0};
+    int o = 0;
 #pragma unroll
-      for (int x = 0; x < 2; ++x)
+    for (int a = 0; a < 4; ++a) {
+      sum += (coef[a].re * coef[a].re + coef[a].im * coef[a].im) * hd[a];
 #pragma unroll
-        for (int y = 0; y < 2; ++y) amp = amp + coef[2 * x + y] * cmdot(je[x], jm[y]);
-      sum += amp.re * amp.re + amp.im * amp.im;
+      for (int b2 = a + 1; b2 < 4; ++b2) {
+        const cx<double> cc = cdot1(coef[a], coef[b2]);   // conj(c_a) c_b
+        const cx<double> t = cc * ho[o++];
+        sum += 2.0 * t.re;
+      }
     }
     const double me2 = sum * c.avg;
     if (lp.mode == OUT_ME2) {

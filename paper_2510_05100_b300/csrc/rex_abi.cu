@@ -277,6 +277,9 @@ int fill_multi_table(const rex_proc* p, const rex_params* pts, int j0, int j1, i
 
 struct rex_multi {
   int precision;
+  int mode;                      // REX_MULTI_PERSISTENT or REX_MULTI_STREAMS
+  cudaStream_t side[MULTI_MAX_BATCH];   // stream mode: one forked stream per batch
+  cudaEvent_t fork, join[MULTI_MAX_BATCH];
   int device;
   unsigned long long* counter;   // device work counter (scratch), reset by every launch
   int blocks[2];                 // persistent grid size without / with complex propagators
@@ -315,12 +318,43 @@ int multi_impl(rex_multi* m, const rex_batch* batches, int nbatch, const rex_par
   if (nee > 1) return fail(REX_EINVAL, "at most one ee_mumu batch per multi launch");
   if (k == 0) return REX_OK;
   if (!pts) return fail(REX_EINVAL, "null parameter array");
-  // heaviest process first: items are handed out in this order
+  if (m->mode == REX_MULTI_STREAMS) {
+    // fork: every batch's own tuned single-process kernel on its side stream; join
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaEventRecord(m->fork, st);
+    if (e != cudaSuccess) return cuda_fail((int)e, "fork event");
+    for (int i = 0; i < nbatch; ++i) {
+      if (batches[i].nev == 0) continue;
+      e = cudaStreamWaitEvent(m->side[i], m->fork, 0);
+      if (e != cudaSuccess) return cuda_fail((int)e, "fork wait");
+      const int rc = reweight_impl(batches[i].proc, batches[i].momenta, batches[i].w_in, batches[i].nev, pts, k,
+                                   batches[i].w_out, m->side[i]);
+      if (rc) return rc;
+      e = cudaEventRecord(m->join[i], m->side[i]);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(st, m->join[i], 0);
+      if (e != cudaSuccess) return cuda_fail((int)e, "join");
+    }
+    return REX_OK;
+  }
+  // longest tiles first: items are handed out in this order.  Estimated time of
+  // one tile = events per tile x flops per event / issue rate of the pipe it runs
+  // on (FP64 is 1/64 of FP32 on B300); e+e- tiles always run in FP64.
+  const int mixed_p = m->precision == REX_MIXED;
+  double tile_cost[MULTI_MAX_BATCH];
+  for (int i = 0; i < nbatch; ++i) {
+    static const double flops_per_event_slot[4] = {160.0, 5.0e3, 4.8e4, 5.7e5};   // per mass slot
+    static const double flops_per_event_fixed[4] = {6.4e3, 4.0e2, 6.6e3, 1.1e5};
+    const int kind = batches[i].proc->kind;
+    const double rate = (kind == PROC_EE_MUMU || !mixed_p) ? 1.0 : 64.0;
+    const double slots = kind == PROC_EE_MUMU ? (k < MULTI_MAX_POINTS ? k : MULTI_MAX_POINTS) + 1.0 : 9.0;
+    tile_cost[i] = multi_events_per_tile(kind, mixed_p) *
+                   (flops_per_event_fixed[kind] + slots * flops_per_event_slot[kind]) / rate;
+  }
   int order[MULTI_MAX_BATCH];
   for (int i = 0; i < nbatch; ++i) order[i] = i;
   for (int i = 0; i < nbatch; ++i)
     for (int j = i + 1; j < nbatch; ++j)
-      if (batches[order[j]].proc->kind > batches[order[i]].proc->kind) std::swap(order[i], order[j]);
+      if (tile_cost[order[j]] > tile_cost[order[i]]) std::swap(order[i], order[j]);
   const int mixed = m->precision == REX_MIXED;
   static thread_local MultiLaunch ml;   // ~20 KB: kept off the stack
   for (int j0 = 0; j0 < k; j0 += MULTI_MAX_POINTS) {
@@ -388,7 +422,23 @@ int rex_multi_create(int precision, rex_multi** out) {
       return cuda_fail(err, "occupancy query");
     }
   }
+  e = cudaEventCreateWithFlags(&m->fork, cudaEventDisableTiming);
+  for (int i = 0; i < MULTI_MAX_BATCH && e == cudaSuccess; ++i) {
+    e = cudaStreamCreateWithFlags(&m->side[i], cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&m->join[i], cudaEventDisableTiming);
+  }
+  if (e != cudaSuccess) {
+    rex_multi_free(m);
+    return cuda_fail((int)e, "stream/event creation");
+  }
   *out = m;
+  return REX_OK;
+}
+
+int rex_multi_set_mode(rex_multi* m, int mode) {
+  if (!m) return fail(REX_EINVAL, "null multi handle");
+  if (mode != REX_MULTI_PERSISTENT && mode != REX_MULTI_STREAMS) return fail(REX_EINVAL, "unknown mode %d", mode);
+  m->mode = mode;
   return REX_OK;
 }
 
@@ -516,6 +566,11 @@ void rex_multi_free(rex_multi* m) {
   if (m->exec) cudaGraphExecDestroy(m->exec);
   if (m->graph) cudaGraphDestroy(m->graph);
   if (m->cap_stream) cudaStreamDestroy(m->cap_stream);
+  for (int i = 0; i < MULTI_MAX_BATCH; ++i) {
+    if (m->side[i]) cudaStreamDestroy(m->side[i]);
+    if (m->join[i]) cudaEventDestroy(m->join[i]);
+  }
+  if (m->fork) cudaEventDestroy(m->fork);
   if (m->counter) cudaFree(m->counter);
   delete m;
 }

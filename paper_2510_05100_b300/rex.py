@@ -29,6 +29,8 @@ REX_EUNSUPPORTED = -5
 FP64 = 0
 MIXED = 1
 FLAG_NO_DEDUPE = 1
+MULTI_PERSISTENT = 0
+MULTI_STREAMS = 1
 
 # symbols declared in include/rex.h
 EXPORTS = (
@@ -36,7 +38,7 @@ EXPORTS = (
     "rex_reweight", "rex_reweight_host", "rex_me2", "rex_free_process",
     "rex_last_error", "rex_version", "rex_probe_fma", "rex_num_variants", "rex_get_variant",
     "rex_set_variant", "rex_autotune", "rex_multi_create", "rex_reweight_multi", "rex_multi_capture",
-    "rex_multi_replay", "rex_multi_free", "rex_reweight_multi_noalloc",
+    "rex_multi_replay", "rex_multi_free", "rex_reweight_multi_noalloc", "rex_multi_set_mode",
 )
 
 
@@ -114,6 +116,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.rex_multi_replay.restype = ctypes.c_int
     lib.rex_multi_free.argtypes = [vp]
     lib.rex_multi_free.restype = None
+    lib.rex_multi_set_mode.argtypes = [vp, ctypes.c_int]
+    lib.rex_multi_set_mode.restype = ctypes.c_int
     lib.rex_reweight_multi_noalloc.argtypes = [bp, ctypes.c_int, pp, ctypes.c_int, ctypes.c_int, vp]
     lib.rex_reweight_multi_noalloc.restype = ctypes.c_int
     lib.rex_version.argtypes = []
@@ -241,11 +245,16 @@ class Process:
 class Multi:
     """Several subprocess batches in one persistent launch (rex_multi_*)."""
 
-    def __init__(self, precision: int = FP64):
+    def __init__(self, precision: int = FP64, mode: int = MULTI_PERSISTENT):
         h = ctypes.c_void_p()
         _check(load().rex_multi_create(precision, ctypes.byref(h)))
         self._h = h
         self.precision = precision
+        if mode != MULTI_PERSISTENT:
+            self.set_mode(mode)
+
+    def set_mode(self, mode: int) -> None:
+        _check(load().rex_multi_set_mode(self._h, mode))
 
     def close(self):
         if getattr(self, "_h", None):

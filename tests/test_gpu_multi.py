@@ -41,11 +41,12 @@ def dev(a):
     return torch.from_numpy(np.ascontiguousarray(a)).cuda()
 
 
+@pytest.mark.parametrize("mode", [0, 1])
 @pytest.mark.parametrize("precision", [0, 1])
-def test_multi_matches_single_process_launches(rex, precision):
+def test_multi_matches_single_process_launches(rex, precision, mode):
     pts = points(9)
     items = setup(rex, precision)
-    m = rex.Multi(precision)
+    m = rex.Multi(precision, mode)
     batches, single = [], []
     for proc, p, mom, w in items:
         dm, dw = dev(mom), dev(w)
@@ -62,11 +63,13 @@ def test_multi_matches_single_process_launches(rex, precision):
             assert np.max(np.abs(got[:, :3] / orc - 1.0)) < 1e-12, proc
 
 
-def test_multi_graph_replay_and_point_chunks(rex):
-    """70 points: two launches per call (64 + 6); a captured graph replays them."""
+@pytest.mark.parametrize("mode", [0, 1])
+def test_multi_graph_replay_and_point_chunks(rex, mode):
+    """70 points: two launches per call (64 + 6) in persistent mode; a captured graph
+    (fork-join of streams in stream mode) replays them."""
     pts = points(70)
     items = setup(rex, 1, seed=21)
-    m = rex.Multi(1)
+    m = rex.Multi(1, mode)
     batches, refs = [], []
     for proc, p, mom, w in items:
         dm, dw = dev(mom), dev(w)

@@ -1,0 +1,94 @@
+"""The FP64 surrogate MLP oracle against independent checks (CPU)."""
+import math
+
+import numpy as np
+import pytest
+from scipy.stats import norm
+
+from oracle import mlp
+
+
+def test_gelu_values_and_derivative():
+    z = np.array([-3.0, -1.0, 0.0, 0.5, 2.0, 6.0])
+    assert np.allclose(mlp.gelu(z), z * norm.cdf(z), rtol=1e-14, atol=1e-16)      # z Phi(z)
+    h = 1e-6
+    fd = (mlp.gelu(z + h) - mlp.gelu(z - h)) / (2 * h)
+    assert np.allclose(mlp.gelu_grad(z), fd, rtol=1e-8, atol=1e-10)
+    assert mlp.gelu_grad(np.array([0.0]))[0] == 0.5
+
+
+def _small():
+    p = mlp.init_params(3, nin=5, width=7, nlayer=2, nout=2)
+    g = np.random.default_rng(4)
+    x = g.normal(size=(9, 5))
+    t = g.normal(size=9)
+    return p, x, t
+
+
+def test_gradients_match_central_finite_differences():
+    """The error head's target is a stop-gradient: freeze it at the base point."""
+    params, x, t = _small()
+    out, _ = mlp.forward(params, x)
+    frozen = np.abs(out[:, 0] - t)
+    _, grads = mlp.loss_and_grad(params, x, t, frozen)
+    _, grads_default = mlp.loss_and_grad(params, x, t)
+    for a, b in zip(grads, grads_default):
+        assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+    h = 1e-6
+    worst = 0.0
+    for li, (w, b) in enumerate(params):
+        for arr, garr in ((w, grads[li][0]), (b, grads[li][1])):
+            it = np.nditer(arr, flags=["multi_index"])
+            for _ in it:
+                idx = it.multi_index
+                old = arr[idx]
+                arr[idx] = old + h
+                lp, _ = mlp.loss_and_grad(params, x, t, frozen)
+                arr[idx] = old - h
+                lm, _ = mlp.loss_and_grad(params, x, t, frozen)
+                arr[idx] = old
+                fd = (lp - lm) / (2 * h)
+                scale = max(abs(fd), abs(garr[idx]), 1e-8)
+                worst = max(worst, abs(fd - garr[idx]) / scale)
+    assert worst < 1e-6
+
+
+def test_forward_is_the_layer_composition():
+    params, x, _ = _small()
+    out, _ = mlp.forward(params, x)
+    h = x
+    for w, b in params[:-1]:
+        h = (h @ w + b) * norm.cdf(h @ w + b)
+    ref = h @ params[-1][0] + params[-1][1]
+    assert np.allclose(out, ref, rtol=1e-13, atol=1e-14)
+
+
+def test_adam_first_step_is_lr_times_sign():
+    """After one step from zero moments, Adam moves every parameter by lr * g/(|g| + eps')."""
+    params = [[np.array([[1.0, -2.0]]), np.array([0.5, 0.0])]]
+    grads = [[np.array([[0.3, -0.01]]), np.array([-4.0, 0.0])]]
+    opt = mlp.Adam(params, lr=0.01)
+    opt.update(params, grads)
+    assert np.allclose(params[0][0], [[1.0 - 0.01, -2.0 + 0.01]], rtol=1e-9)
+    assert np.allclose(params[0][1], [0.5 + 0.01, 0.0], rtol=1e-9)
+
+
+def test_training_reduces_loss_on_a_smooth_target():
+    g = np.random.default_rng(0)
+    x = g.uniform(-1, 1, (256, 4))
+    t = np.sin(2 * x[:, 0]) + x[:, 1] * x[:, 2]
+    params = mlp.init_params(1, nin=4, width=32, nlayer=2, nout=2)
+    opt = mlp.Adam(params, lr=3e-3)
+    l0, _ = mlp.loss_and_grad(params, x, t)
+    for _ in range(300):
+        l, gr = mlp.loss_and_grad(params, x, t)
+        opt.update(params, gr)
+    assert l < 0.1 * l0
+
+
+def test_features_layout():
+    p = np.arange(2 * 5 * 4, dtype=float).reshape(2, 5, 4) * 100.0
+    x = mlp.features(p, np.array([173.0, 176.0]), np.array([0.118, 0.126]))
+    assert x.shape == (2, 22)
+    assert np.allclose(x[1, :20], p[1].reshape(20) * 1e-3)
+    assert np.allclose(x[:, 20], [0.0, 1.0]) and np.allclose(x[:, 21], [0.0, 1.0])
