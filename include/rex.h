@@ -219,6 +219,64 @@ int rex_reweight_multi_noalloc(const rex_batch *batches, int nbatch,
                                const rex_params *param_sets, int k,
                                int precision, void *stream);
 
+/* ---- Learned surrogate of the weight ratio ---------------------------------
+ * The paper has no learned component.  An MLP (22 inputs -> 4 hidden layers of
+ * 256 with GELU -> 2 outputs) predicts r = log(|M(p;theta)|^2/|M(p;theta_0)|^2)
+ * for g g -> t t~ g events (inputs: the 20 momentum components in TeV,
+ * (mt - 173)/3, (alphas - 0.118)/0.008) and an estimate of its own absolute
+ * error.  Weights are FP32 masters with BF16 copies; GEMMs run on tensor cores
+ * in BF16 with FP32 accumulation.  Parameter layout (rex_surrogate_num_params
+ * floats, every matrix [in][out] row-major): W1 [32][256] (rows 22..31 zero),
+ * b1 [256], W2 [256][256], b2, W3, b3, W4, b4, W5 [256][2], b5 [2].
+ * Loss: mean of (y - t)^2 + (e - |y - t|)^2, the error head's target held
+ * constant; Adam (beta1 0.9, beta2 0.999, eps 1e-8).
+ * All calls return REX_OK or a negative REX_E* code; the message of a
+ * surrogate call's failure is in rex_surrogate_last_error(). */
+typedef struct rex_surrogate rex_surrogate; /* opaque, library-owned */
+
+int64_t rex_surrogate_num_params(void);
+const char *rex_surrogate_last_error(void);
+
+/* Create a network with He-normal weights drawn from seed; allocates its
+ * parameters, optimiser state and (on demand) work buffers on the current device. */
+int rex_surrogate_create(unsigned long long seed, rex_surrogate **out);
+
+/* Copy all parameters from / to a host FP32 array of num_params floats
+ * (setting resets the optimiser state).  Synchronises the device. */
+int rex_surrogate_set_weights(rex_surrogate *s, const float *host, int64_t n);
+int rex_surrogate_get_weights(rex_surrogate *s, float *host, int64_t n);
+
+/* Loss and gradient (no update) of n samples, n a multiple of 32: sample i is
+ * momenta[i] (device [n][5][4]) at point (mt[i], alphas[i]) (device) with
+ * target log(ratio[i]) (device).  Writes the mean loss (host float) and the
+ * gradient (host, num_params floats); synchronises stream. */
+int rex_surrogate_loss_grad(rex_surrogate *s, const double *momenta, const double *ratio,
+                            const double *mt, const double *alphas, int64_t n,
+                            float *loss, float *grad, void *stream);
+
+/* Train for steps Adam steps of batch samples (a multiple of 128) drawn with
+ * SplitMix64 from the nev x k pairs (event e, point j) of momenta (device
+ * [nev][5][4]) and exact weight ratios ratio (device [nev][k], e.g. rex_reweight
+ * output with w_in = 1).  losses (host, steps floats) may be NULL; if given the
+ * call synchronises stream. */
+int rex_surrogate_train(rex_surrogate *s, const double *momenta, const double *ratio, int64_t nev,
+                        const rex_params *param_sets, int k, int steps, int batch, float lr,
+                        unsigned long long seed, float *losses, void *stream);
+
+/* Surrogate reweighting of nev events to k points (k <= 4096):
+ * pred, err (device [nev][k] floats, may be NULL) receive the predicted log
+ * ratio and error estimate; w_out (device [nev][k], may be NULL) receives
+ * w_in * exp(pred), and then every event with some err > tau (or NaN) is
+ * recomputed exactly with the handle exact (rex_reweight on those events).
+ * n_fallback (host, may be NULL) receives the number of such events.  With
+ * w_out set the call synchronises stream (to size the fallback). */
+int rex_surrogate_reweight(rex_surrogate *s, rex_proc *exact, const double *momenta,
+                           const double *w_in, int64_t nev, const rex_params *param_sets, int k,
+                           float tau, double *w_out, float *pred, float *err,
+                           int64_t *n_fallback, void *stream);
+
+void rex_surrogate_free(rex_surrogate *s);
+
 /* Release a handle (NULL is ignored).  Synchronises nothing; the caller must
  * make sure no work enqueued with the handle is still running. */
 void rex_free_process(rex_proc *proc);

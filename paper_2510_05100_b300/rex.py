@@ -39,6 +39,9 @@ EXPORTS = (
     "rex_last_error", "rex_version", "rex_probe_fma", "rex_num_variants", "rex_get_variant",
     "rex_set_variant", "rex_autotune", "rex_multi_create", "rex_reweight_multi", "rex_multi_capture",
     "rex_multi_replay", "rex_multi_free", "rex_reweight_multi_noalloc", "rex_multi_set_mode",
+    "rex_surrogate_num_params", "rex_surrogate_last_error", "rex_surrogate_create",
+    "rex_surrogate_set_weights", "rex_surrogate_get_weights", "rex_surrogate_loss_grad",
+    "rex_surrogate_train", "rex_surrogate_reweight", "rex_surrogate_free",
 )
 
 
@@ -120,6 +123,27 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.rex_multi_set_mode.restype = ctypes.c_int
     lib.rex_reweight_multi_noalloc.argtypes = [bp, ctypes.c_int, pp, ctypes.c_int, ctypes.c_int, vp]
     lib.rex_reweight_multi_noalloc.restype = ctypes.c_int
+    fp = ctypes.POINTER(ctypes.c_float)
+    lib.rex_surrogate_num_params.argtypes = []
+    lib.rex_surrogate_num_params.restype = ctypes.c_int64
+    lib.rex_surrogate_last_error.argtypes = []
+    lib.rex_surrogate_last_error.restype = ctypes.c_char_p
+    lib.rex_surrogate_create.argtypes = [ctypes.c_ulonglong, ctypes.POINTER(vp)]
+    lib.rex_surrogate_create.restype = ctypes.c_int
+    lib.rex_surrogate_set_weights.argtypes = [vp, vp, i64]
+    lib.rex_surrogate_set_weights.restype = ctypes.c_int
+    lib.rex_surrogate_get_weights.argtypes = [vp, vp, i64]
+    lib.rex_surrogate_get_weights.restype = ctypes.c_int
+    lib.rex_surrogate_loss_grad.argtypes = [vp, vp, vp, vp, vp, i64, fp, vp, vp]
+    lib.rex_surrogate_loss_grad.restype = ctypes.c_int
+    lib.rex_surrogate_train.argtypes = [vp, vp, vp, i64, pp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                        ctypes.c_float, ctypes.c_ulonglong, vp, vp]
+    lib.rex_surrogate_train.restype = ctypes.c_int
+    lib.rex_surrogate_reweight.argtypes = [vp, vp, vp, vp, i64, pp, ctypes.c_int, ctypes.c_float, vp, vp, vp,
+                                           ctypes.POINTER(ctypes.c_int64), vp]
+    lib.rex_surrogate_reweight.restype = ctypes.c_int
+    lib.rex_surrogate_free.argtypes = [vp]
+    lib.rex_surrogate_free.restype = None
     lib.rex_version.argtypes = []
     lib.rex_version.restype = ctypes.c_char_p
     _lib = lib
@@ -298,6 +322,69 @@ def reweight_multi_noalloc(batches, points: Sequence[dict], precision: int = FP6
     arr = Multi._batches(batches)
     _check(load().rex_reweight_multi_noalloc(arr, len(batches), _param_array(points), len(points),
                                              precision, _stream_ptr(stream)))
+
+
+def _scheck(rc: int) -> None:
+    if rc != REX_OK:
+        raise RexError(rc, load().rex_surrogate_last_error().decode())
+
+
+class Surrogate:
+    """MLP surrogate of the log weight ratio (rex_surrogate_*); g g -> t t~ g events."""
+
+    def __init__(self, seed: int = 0):
+        h = ctypes.c_void_p()
+        _scheck(load().rex_surrogate_create(seed, ctypes.byref(h)))
+        self._h = h
+        self.nparam = load().rex_surrogate_num_params()
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().rex_surrogate_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def get_weights(self):
+        import numpy as np
+        out = np.empty(self.nparam, dtype=np.float32)
+        _scheck(load().rex_surrogate_get_weights(self._h, out.ctypes.data, self.nparam))
+        return out
+
+    def set_weights(self, w) -> None:
+        import numpy as np
+        w = np.ascontiguousarray(w, dtype=np.float32)
+        _scheck(load().rex_surrogate_set_weights(self._h, w.ctypes.data, w.size))
+
+    def loss_grad(self, momenta, ratio, mt, alphas, stream=None):
+        import numpy as np
+        loss = ctypes.c_float()
+        grad = np.empty(self.nparam, dtype=np.float32)
+        _scheck(load().rex_surrogate_loss_grad(self._h, _ptr(momenta), _ptr(ratio), _ptr(mt), _ptr(alphas),
+                                               momenta.shape[0], ctypes.byref(loss), grad.ctypes.data,
+                                               _stream_ptr(stream)))
+        return loss.value, grad
+
+    def train(self, momenta, ratio, points, steps, batch=8192, lr=1e-3, seed=0, stream=None):
+        import numpy as np
+        losses = np.empty(max(1, steps), dtype=np.float32)
+        _scheck(load().rex_surrogate_train(self._h, _ptr(momenta), _ptr(ratio), momenta.shape[0],
+                                           _param_array(points), len(points), steps, batch, lr, seed,
+                                           losses.ctypes.data, _stream_ptr(stream)))
+        return losses[:steps]
+
+    def reweight(self, momenta, w_in, points, tau=float("inf"), exact=None, w_out=None, pred=None, err=None,
+                 stream=None) -> int:
+        nfb = ctypes.c_int64(0)
+        _scheck(load().rex_surrogate_reweight(self._h, exact._h if exact is not None else None, _ptr(momenta),
+                                              _ptr(w_in), momenta.shape[0], _param_array(points), len(points),
+                                              tau, _ptr(w_out), _ptr(pred), _ptr(err), ctypes.byref(nfb),
+                                              _stream_ptr(stream)))
+        return nfb.value
 
 
 def probe_fma(fp64: bool, stream=None) -> float:
