@@ -17,7 +17,7 @@ def ensure_built():
 
 def declared_symbols():
     text = open(HEADER).read()
-    return sorted(set(re.findall(r"^(?:int|void|const char \*)\s*\*?\s*(rex_\w+)\s*\(", text, re.M)))
+    return sorted(set(re.findall(r"^(?:int64_t|int|void|const char \*)\s*\*?\s*(rex_\w+)\s*\(", text, re.M)))
 
 
 def cuda_available():
