@@ -102,6 +102,13 @@ def emit_process(name: str, ngluon: int) -> str:
     for row in cint:
         w("{" + ", ".join(str(v) for v in row) + "},")
     w("};", 0)
+    w("#if defined(__CUDACC__)", 0)
+    w(f"// device copy for lane-indexed reads (tensor-core colour form)", 0)
+    w(f"__constant__ int {name}_colour_dev[{len(flows)}][{len(flows)}] = {{", 0)
+    for row in cint:
+        w("{" + ", ".join(str(v) for v in row) + "},")
+    w("};", 0)
+    w("#endif", 0)
     w("", 0)
     w("// gluon sets (internal gluon lines): " + ", ".join(f"{i}={{{_sn(st)}}}" for st, i in gidx.items()), 0)
     w("// suffix sets (off-shell antitop lines): " + ", ".join(f"{i}={{{_sn(st)}}}" for st, i in sidx.items()), 0)
@@ -273,9 +280,11 @@ def emit_process(name: str, ngluon: int) -> str:
     w("// sum_{s,s'} conj(A_s) Cint_{ss'} A_s' (Cint = C * COLOUR_DEN).  The antitop-side", 0)
     w("// currents psi(Y) are emitted depth-first over suffixes Y, so only one per depth is live.", 0)
     w("// The colour form of one helicity is evaluated in CS, the helicity sum in ACC.", 0)
-    w("template <typename R, typename ACC, bool WIDTH, typename CS = ACC>", 0)
+    w("// FORM, if given, replaces the scalar colour form: form(A) returns this lane's", 0)
+    w("// contribution for both top helicities (e.g. the tensor-core form).", 0)
+    w("template <typename R, typename ACC, bool WIDTH, typename CS = ACC, typename FORM = NoColourForm>", 0)
     w(f"__device__ __forceinline__ ACC {name}_quark_line(const {name}_event<R>& ev, const {name}_mass<R>& mm, "
-      f"const {name}_gluons<R>& J, int hb_lo = 0, int hb_hi = 2) {{", 0)
+      f"const {name}_gluons<R>& J, int hb_lo = 0, int hb_hi = 2, const FORM& form = FORM()) {{", 0)
     w("ACC total = ACC(0);")
     w("#pragma unroll 1", 0)
     w("for (int hb = hb_lo; hb < hb_hi; ++hb) {")
@@ -323,6 +332,9 @@ def emit_process(name: str, ngluon: int) -> str:
                 w("}", ind)
 
     dfs((), 2)
+    w("if constexpr (!std::is_same<FORM, NoColourForm>::value) {", 2)
+    w("total += ACC(form(A));", 3)
+    w("} else {", 2)
     w("#pragma unroll", 0)
     w("for (int ht = 0; ht < 2; ++ht) {", 2)
     w("CS s = CS(0);", 3)
@@ -337,6 +349,7 @@ def emit_process(name: str, ngluon: int) -> str:
             w(f"s += CS({2 * c}) * (CS(A[ht][{i}].re) * CS(A[ht][{j}].re) + "
               f"CS(A[ht][{i}].im) * CS(A[ht][{j}].im));", 3)
     w("total += ACC(s);", 3)
+    w("}", 2)
     w("}", 2)
     w("}")
     w("return total;")
@@ -359,9 +372,14 @@ def emit_all() -> str:
         "// polarisation configuration) and the routines that fill them, then",
         "// <name>_quark_line: jamps and their colour form summed over top helicities.",
         "#pragma once",
+        "#include <type_traits>",
+        "",
         '#include "../helas.cuh"',
         "",
         "namespace rex {",
+        "",
+        "// marker: no replacement colour form (use the scalar quadratic form)",
+        "struct NoColourForm {};",
         "",
     ]
     for name, n in PROCESSES:

@@ -7,9 +7,14 @@
 // polarisation configuration) and the routines that fill them, then
 // <name>_quark_line: jamps and their colour form summed over top helicities.
 #pragma once
+#include <type_traits>
+
 #include "../helas.cuh"
 
 namespace rex {
+
+// marker: no replacement colour form (use the scalar quadratic form)
+struct NoColourForm {};
 
 // ---- gg_ttx: g g -> t t~ + 0 g, 2 gluons, 2 colour flows
 struct gg_ttx_info {
@@ -28,6 +33,13 @@ constexpr int gg_ttx_colour[2][2] = {
   {16, -2},
   {-2, 16},
 };
+#if defined(__CUDACC__)
+// device copy for lane-indexed reads (tensor-core colour form)
+__constant__ int gg_ttx_colour_dev[2][2] = {
+  {16, -2},
+  {-2, 16},
+};
+#endif
 
 // gluon sets (internal gluon lines): 0={01}
 // suffix sets (off-shell antitop lines): 0={0}, 1={1}
@@ -160,8 +172,10 @@ __device__ __forceinline__ void gg_ttx_gluon_currents(const gg_ttx_event<R>& ev,
 // sum_{s,s'} conj(A_s) Cint_{ss'} A_s' (Cint = C * COLOUR_DEN).  The antitop-side
 // currents psi(Y) are emitted depth-first over suffixes Y, so only one per depth is live.
 // The colour form of one helicity is evaluated in CS, the helicity sum in ACC.
-template <typename R, typename ACC, bool WIDTH, typename CS = ACC>
-__device__ __forceinline__ ACC gg_ttx_quark_line(const gg_ttx_event<R>& ev, const gg_ttx_mass<R>& mm, const gg_ttx_gluons<R>& J, int hb_lo = 0, int hb_hi = 2) {
+// FORM, if given, replaces the scalar colour form: form(A) returns this lane's
+// contribution for both top helicities (e.g. the tensor-core form).
+template <typename R, typename ACC, bool WIDTH, typename CS = ACC, typename FORM = NoColourForm>
+__device__ __forceinline__ ACC gg_ttx_quark_line(const gg_ttx_event<R>& ev, const gg_ttx_mass<R>& mm, const gg_ttx_gluons<R>& J, int hb_lo = 0, int hb_hi = 2, const FORM& form = FORM()) {
   ACC total = ACC(0);
 #pragma unroll 1
   for (int hb = hb_lo; hb < hb_hi; ++hb) {
@@ -199,6 +213,9 @@ __device__ __forceinline__ ACC gg_ttx_quark_line(const gg_ttx_event<R>& ev, cons
         A[1][0] = ubar_dot(mm.ut[1], x);
       }
     }
+    if constexpr (!std::is_same<FORM, NoColourForm>::value) {
+      total += ACC(form(A));
+    } else {
 #pragma unroll
     for (int ht = 0; ht < 2; ++ht) {
       CS s = CS(0);
@@ -206,6 +223,7 @@ __device__ __forceinline__ ACC gg_ttx_quark_line(const gg_ttx_event<R>& ev, cons
       s += CS(16) * (CS(A[ht][1].re) * CS(A[ht][1].re) + CS(A[ht][1].im) * CS(A[ht][1].im));
       s += CS(-4) * (CS(A[ht][0].re) * CS(A[ht][1].re) + CS(A[ht][0].im) * CS(A[ht][1].im));
       total += ACC(s);
+    }
     }
   }
   return total;
@@ -236,6 +254,17 @@ constexpr int gg_ttxg_colour[6][6] = {
   {1, -8, 10, 1, 64, -8},
   {10, 1, 1, -8, -8, 64},
 };
+#if defined(__CUDACC__)
+// device copy for lane-indexed reads (tensor-core colour form)
+__constant__ int gg_ttxg_colour_dev[6][6] = {
+  {64, -8, -8, 1, 1, 10},
+  {-8, 64, 1, 10, -8, 1},
+  {-8, 1, 64, -8, 10, 1},
+  {1, 10, -8, 64, 1, -8},
+  {1, -8, 10, 1, 64, -8},
+  {10, 1, 1, -8, -8, 64},
+};
+#endif
 
 // gluon sets (internal gluon lines): 0={01}, 1={02}, 2={12}, 3={012}
 // suffix sets (off-shell antitop lines): 0={0}, 1={1}, 2={2}, 3={01}, 4={02}, 5={12}
@@ -443,8 +472,10 @@ __device__ __forceinline__ void gg_ttxg_gluon_currents(const gg_ttxg_event<R>& e
 // sum_{s,s'} conj(A_s) Cint_{ss'} A_s' (Cint = C * COLOUR_DEN).  The antitop-side
 // currents psi(Y) are emitted depth-first over suffixes Y, so only one per depth is live.
 // The colour form of one helicity is evaluated in CS, the helicity sum in ACC.
-template <typename R, typename ACC, bool WIDTH, typename CS = ACC>
-__device__ __forceinline__ ACC gg_ttxg_quark_line(const gg_ttxg_event<R>& ev, const gg_ttxg_mass<R>& mm, const gg_ttxg_gluons<R>& J, int hb_lo = 0, int hb_hi = 2) {
+// FORM, if given, replaces the scalar colour form: form(A) returns this lane's
+// contribution for both top helicities (e.g. the tensor-core form).
+template <typename R, typename ACC, bool WIDTH, typename CS = ACC, typename FORM = NoColourForm>
+__device__ __forceinline__ ACC gg_ttxg_quark_line(const gg_ttxg_event<R>& ev, const gg_ttxg_mass<R>& mm, const gg_ttxg_gluons<R>& J, int hb_lo = 0, int hb_hi = 2, const FORM& form = FORM()) {
   ACC total = ACC(0);
 #pragma unroll 1
   for (int hb = hb_lo; hb < hb_hi; ++hb) {
@@ -585,6 +616,9 @@ __device__ __forceinline__ ACC gg_ttxg_quark_line(const gg_ttxg_event<R>& ev, co
         }
       }
     }
+    if constexpr (!std::is_same<FORM, NoColourForm>::value) {
+      total += ACC(form(A));
+    } else {
 #pragma unroll
     for (int ht = 0; ht < 2; ++ht) {
       CS s = CS(0);
@@ -610,6 +644,7 @@ __device__ __forceinline__ ACC gg_ttxg_quark_line(const gg_ttxg_event<R>& ev, co
       s += CS(-16) * (CS(A[ht][3].re) * CS(A[ht][5].re) + CS(A[ht][3].im) * CS(A[ht][5].im));
       s += CS(-16) * (CS(A[ht][4].re) * CS(A[ht][5].re) + CS(A[ht][4].im) * CS(A[ht][5].im));
       total += ACC(s);
+    }
     }
   }
   return total;
@@ -676,6 +711,35 @@ constexpr int gg_ttxgg_colour[24][24] = {
   {62, 71, -10, 80, -1, 8, -28, 62, 62, -10, -10, -1, -1, 8, -10, -1, -64, 8, 8, -64, 80, 8, 512, -64},
   {-28, 62, 62, -10, -10, -1, 62, 71, -10, 80, -1, 8, -10, -1, -1, 8, 8, -64, 80, 8, 8, -64, -64, 512},
 };
+#if defined(__CUDACC__)
+// device copy for lane-indexed reads (tensor-core colour form)
+__constant__ int gg_ttxgg_colour_dev[24][24] = {
+  {512, -64, -64, 8, 8, 80, -64, 8, 8, -1, -1, -10, 8, -1, 80, -10, 71, 62, -1, -10, -10, 62, 62, -28},
+  {-64, 512, 8, 80, -64, 8, 8, -64, -1, -10, 8, -1, -1, -10, -10, 62, 62, -28, 8, -1, 80, -10, 71, 62},
+  {-64, 8, 512, -64, 80, 8, 8, -1, 80, -10, 71, 62, -64, 8, 8, -1, -1, -10, -10, -1, 62, -28, -10, 62},
+  {8, 80, -64, 512, 8, -64, -1, -10, -10, 62, 62, -28, 8, -64, -1, -10, 8, -1, -1, 8, 71, 62, 80, -10},
+  {8, -64, 80, 8, 512, -64, -1, 8, 71, 62, 80, -10, -10, -1, 62, -28, -10, 62, -64, 8, 8, -1, -1, -10},
+  {80, 8, 8, -64, -64, 512, -10, -1, 62, -28, -10, 62, -1, 8, 71, 62, 80, -10, 8, -64, -1, -10, 8, -1},
+  {-64, 8, 8, -1, -1, -10, 512, -64, -64, 8, 8, 80, 80, -10, 8, -1, 62, 71, -10, 62, -1, -10, -28, 62},
+  {8, -64, -1, -10, 8, -1, -64, 512, 8, 80, -64, 8, -10, 62, -1, -10, -28, 62, 80, -10, 8, -1, 62, 71},
+  {8, -1, 80, -10, 71, 62, -64, 8, 512, -64, 80, 8, 8, -1, -64, 8, -10, -1, 62, -28, -10, -1, 62, -10},
+  {-1, -10, -10, 62, 62, -28, 8, 80, -64, 512, 8, -64, -1, -10, 8, -64, -1, 8, 71, 62, -1, 8, -10, 80},
+  {-1, 8, 71, 62, 80, -10, 8, -64, 80, 8, 512, -64, 62, -28, -10, -1, 62, -10, 8, -1, -64, 8, -10, -1},
+  {-10, -1, 62, -28, -10, 62, 80, 8, 8, -64, -64, 512, 71, 62, -1, 8, -10, 80, -1, -10, 8, -64, -1, 8},
+  {8, -1, -64, 8, -10, -1, 80, -10, 8, -1, 62, 71, 512, -64, -64, 8, 8, 80, 62, -10, -28, 62, -1, -10},
+  {-1, -10, 8, -64, -1, 8, -10, 62, -1, -10, -28, 62, -64, 512, 8, 80, -64, 8, -10, 80, 62, 71, 8, -1},
+  {80, -10, 8, -1, 62, 71, 8, -1, -64, 8, -10, -1, -64, 8, 512, -64, 80, 8, -28, 62, 62, -10, -10, -1},
+  {-10, 62, -1, -10, -28, 62, -1, -10, 8, -64, -1, 8, 8, 80, -64, 512, 8, -64, 62, 71, -10, 80, -1, 8},
+  {71, 62, -1, 8, -10, 80, 62, -28, -10, -1, 62, -10, 8, -64, 80, 8, 512, -64, -1, 8, -10, -1, -64, 8},
+  {62, -28, -10, -1, 62, -10, 71, 62, -1, 8, -10, 80, 80, 8, 8, -64, -64, 512, -10, -1, -1, 8, 8, -64},
+  {-1, 8, -10, -1, -64, 8, -10, 80, 62, 71, 8, -1, 62, -10, -28, 62, -1, -10, 512, -64, -64, 8, 8, 80},
+  {-10, -1, -1, 8, 8, -64, 62, -10, -28, 62, -1, -10, -10, 80, 62, 71, 8, -1, -64, 512, 8, 80, -64, 8},
+  {-10, 80, 62, 71, 8, -1, -1, 8, -10, -1, -64, 8, -28, 62, 62, -10, -10, -1, -64, 8, 512, -64, 80, 8},
+  {62, -10, -28, 62, -1, -10, -10, -1, -1, 8, 8, -64, 62, 71, -10, 80, -1, 8, 8, 80, -64, 512, 8, -64},
+  {62, 71, -10, 80, -1, 8, -28, 62, 62, -10, -10, -1, -1, 8, -10, -1, -64, 8, 8, -64, 80, 8, 512, -64},
+  {-28, 62, 62, -10, -10, -1, 62, 71, -10, 80, -1, 8, -10, -1, -1, 8, 8, -64, 80, 8, 8, -64, -64, 512},
+};
+#endif
 
 // gluon sets (internal gluon lines): 0={01}, 1={02}, 2={03}, 3={12}, 4={13}, 5={23}, 6={012}, 7={013}, 8={023}, 9={123}, 10={0123}
 // suffix sets (off-shell antitop lines): 0={0}, 1={1}, 2={2}, 3={3}, 4={01}, 5={02}, 6={03}, 7={12}, 8={13}, 9={23}, 10={012}, 11={013}, 12={023}, 13={123}
@@ -1207,8 +1271,10 @@ __device__ __forceinline__ void gg_ttxgg_gluon_currents(const gg_ttxgg_event<R>&
 // sum_{s,s'} conj(A_s) Cint_{ss'} A_s' (Cint = C * COLOUR_DEN).  The antitop-side
 // currents psi(Y) are emitted depth-first over suffixes Y, so only one per depth is live.
 // The colour form of one helicity is evaluated in CS, the helicity sum in ACC.
-template <typename R, typename ACC, bool WIDTH, typename CS = ACC>
-__device__ __forceinline__ ACC gg_ttxgg_quark_line(const gg_ttxgg_event<R>& ev, const gg_ttxgg_mass<R>& mm, const gg_ttxgg_gluons<R>& J, int hb_lo = 0, int hb_hi = 2) {
+// FORM, if given, replaces the scalar colour form: form(A) returns this lane's
+// contribution for both top helicities (e.g. the tensor-core form).
+template <typename R, typename ACC, bool WIDTH, typename CS = ACC, typename FORM = NoColourForm>
+__device__ __forceinline__ ACC gg_ttxgg_quark_line(const gg_ttxgg_event<R>& ev, const gg_ttxgg_mass<R>& mm, const gg_ttxgg_gluons<R>& J, int hb_lo = 0, int hb_hi = 2, const FORM& form = FORM()) {
   ACC total = ACC(0);
 #pragma unroll 1
   for (int hb = hb_lo; hb < hb_hi; ++hb) {
@@ -1850,6 +1916,9 @@ __device__ __forceinline__ ACC gg_ttxgg_quark_line(const gg_ttxgg_event<R>& ev, 
         }
       }
     }
+    if constexpr (!std::is_same<FORM, NoColourForm>::value) {
+      total += ACC(form(A));
+    } else {
 #pragma unroll
     for (int ht = 0; ht < 2; ++ht) {
       CS s = CS(0);
@@ -2154,6 +2223,7 @@ __device__ __forceinline__ ACC gg_ttxgg_quark_line(const gg_ttxgg_event<R>& ev, 
       s += CS(-128) * (CS(A[ht][21].re) * CS(A[ht][23].re) + CS(A[ht][21].im) * CS(A[ht][23].im));
       s += CS(-128) * (CS(A[ht][22].re) * CS(A[ht][23].re) + CS(A[ht][22].im) * CS(A[ht][23].im));
       total += ACC(s);
+    }
     }
   }
   return total;

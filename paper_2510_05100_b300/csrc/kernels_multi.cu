@@ -15,12 +15,12 @@
 
 namespace rex {
 
-template <typename R, bool WIDTH, int MINB, int S_TTX, int S_TTXG, int S_TTXGG>
+template <typename R, bool WIDTH, int MINB, int S_TTX, int S_TTXG, int S_TTXGG, bool TC_TTXGG>
 __global__ void __launch_bounds__(QCD_BLOCK, MINB)
     multi_reweight_kernel(const __grid_constant__ MultiLaunch ml, unsigned long long* __restrict__ counter) {
   using T1 = QcdTile<PROC_GG_TTX, R, WIDTH, S_TTX>;
   using T2 = QcdTile<PROC_GG_TTXG, R, WIDTH, S_TTXG>;
-  using T3 = QcdTile<PROC_GG_TTXGG, R, WIDTH, S_TTXGG>;
+  using T3 = QcdTile<PROC_GG_TTXGG, R, WIDTH, S_TTXGG, TC_TTXGG>;
   union Smem {
     typename T1::Smem a;
     typename T2::Smem b;
@@ -50,22 +50,25 @@ __global__ void __launch_bounds__(QCD_BLOCK, MINB)
 }
 
 // Lanes-per-event split of each QCD process in the multi kernel (the defaults of
-// the single-process kernels: FP64 no split; mixed: split only for gg_ttxgg).
+// the single-process kernels: FP64 no split; mixed: no split, and the tensor-core
+// colour form for gg_ttxgg).
 template <typename R>
 struct MultiSplit;
 template <>
 struct MultiSplit<double> {
   static constexpr int TTX = 0, TTXG = 0, TTXGG = 0, MINB = 1;
+  static constexpr bool TC_TTXGG = false;
 };
 template <>
 struct MultiSplit<float> {
-  static constexpr int TTX = 0, TTXG = 0, TTXGG = 1, MINB = 3;
+  static constexpr int TTX = 0, TTXG = 0, TTXGG = 0, MINB = 3;
+  static constexpr bool TC_TTXGG = true;   // 24 colour flows: the tensor-core colour form
 };
 
 template <typename R, bool WIDTH>
 static auto multi_kernel_ptr() {
   using S = MultiSplit<R>;
-  return multi_reweight_kernel<R, WIDTH, S::MINB, S::TTX, S::TTXG, S::TTXGG>;
+  return multi_reweight_kernel<R, WIDTH, S::MINB, S::TTX, S::TTXG, S::TTXGG, S::TC_TTXGG>;
 }
 
 int multi_events_per_tile(int kind, int mixed) {
@@ -97,7 +100,7 @@ int multi_grid_size(int mixed, int width, int* blocks) {
 template <typename R, bool WIDTH>
 static void launch_multi_t(int blocks, const MultiLaunch& ml, unsigned long long* counter, cudaStream_t st) {
   using S = MultiSplit<R>;
-  multi_reweight_kernel<R, WIDTH, S::MINB, S::TTX, S::TTXG, S::TTXGG><<<blocks, QCD_BLOCK, 0, st>>>(ml, counter);
+  multi_reweight_kernel<R, WIDTH, S::MINB, S::TTX, S::TTXG, S::TTXGG, S::TC_TTXGG><<<blocks, QCD_BLOCK, 0, st>>>(ml, counter);
 }
 
 int launch_multi(int mixed, int width, int blocks, const MultiLaunch& ml, unsigned long long* counter,

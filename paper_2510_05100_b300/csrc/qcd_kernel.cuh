@@ -24,6 +24,9 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
+#include "colour_tc.cuh"
 #include "generated/qcd_amplitudes.cuh"
 #include "rex_internal.cuh"
 
@@ -62,10 +65,14 @@ struct QcdProc;
                                                           gluons<R>& J) {                     \
       NAME##_gluon_currents(ev, eps, J);                                                      \
     }                                                                                         \
-    template <typename R, typename ACC, bool W>                                               \
+    template <typename R, typename ACC, bool W, typename FORM = NoColourForm>                 \
     static __device__ __forceinline__ ACC quark_line(const event<R>& ev, const mass<R>& mm,   \
-                                                     const gluons<R>& J, int lo, int hi) {    \
-      return NAME##_quark_line<R, ACC, W, R>(ev, mm, J, lo, hi);                              \
+                                                     const gluons<R>& J, int lo, int hi,      \
+                                                     const FORM& form = FORM()) {             \
+      return NAME##_quark_line<R, ACC, W, R, FORM>(ev, mm, J, lo, hi, form);                  \
+    }                                                                                         \
+    static __device__ __forceinline__ const int (&colour())[info::NFLOW][info::NFLOW] {       \
+      return NAME##_colour_dev;                                                               \
     }                                                                                         \
   };
 
@@ -80,14 +87,17 @@ constexpr int QCD_BLOCK = 128;
 // TABLE is the launch's parameter table (QcdLaunch, or a batch table of the
 // persistent multi-process kernel): nmass, mass[], width[], k, mode,
 // out_stride, slot[], factor[], factor0.
-template <int PROC, typename R, bool WIDTH, int SPLIT>
+template <int PROC, typename R, bool WIDTH, int SPLIT, bool TC_REQ = false>
 struct QcdTile {
   using P = QcdProc<PROC>;
   static constexpr int NG = P::info::NGLUON;
+  static constexpr int NF = P::info::NFLOW;
   static constexpr int NPART = NG + 2;
   static constexpr int NGH = P::info::NGHEL;
   static constexpr int NH = NGH << SPLIT;
   static constexpr int EPB = QCD_BLOCK / NH;
+  // tensor-core colour form: FP32 amplitudes and events of >= 8 lanes only
+  static constexpr bool TC = TC_REQ && std::is_same<R, float>::value && NH >= 8;
   static_assert(32 % NH == 0 || NH % 32 == 0, "gluon-polarisation lanes must tile a warp");
   static_assert(NH <= 32, "one event per warp at most");
 
@@ -95,6 +105,7 @@ struct QcdTile {
     double me2s[EPB][MAX_MASS + 1];
     typename P::template event<R> evs[EPB];
     typename P::template mass<R> mss[EPB];
+    alignas(16) __half tc[TC ? QCD_BLOCK / 32 : 1][TC ? ColourTc<NF>::WARP_HALVES : 1];
   };
 
   template <class TABLE>
@@ -128,12 +139,24 @@ struct QcdTile {
     typename P::template gluons<R> J;
     P::gluon_currents(evd, eps, J);
 
+    // a6 on tensor cores: the colour matrix as MMA B fragments in this warp's smem
+    if constexpr (TC) ColourTc<NF>::load(P::colour(), sm.tc[tid >> 5]);
+
     // a3-a7 per distinct mass slot
     for (int m = 0; m < lp.nmass; ++m) {
       P::template mass_setup<R, WIDTH>(evd, lp.mass[m], lp.width[m], sm.mss[el], lane_ev, NH);
       __syncthreads();
       double s = 0.0;
-      if (valid) s = P::template quark_line<R, double, WIDTH>(evd, sm.mss[el], J, hb_lo, hb_hi);
+      if constexpr (TC) {
+        // every lane takes part in the warp-wide MMA form; lane 8t of the warp
+        // receives the colour sum of m16 tile t (part of its event), the others 0
+        __half* tcs = sm.tc[tid >> 5];
+        auto form = [&](const cx<float> (&A)[2][NF]) { return ColourTc<NF>::template form<NH>(A, tcs); };
+        s = P::template quark_line<R, double, WIDTH>(evd, sm.mss[el], J, hb_lo, hb_hi, form);
+        if (!valid) s = 0.0;
+      } else {
+        if (valid) s = P::template quark_line<R, double, WIDTH>(evd, sm.mss[el], J, hb_lo, hb_hi);
+      }
 #pragma unroll
       for (int off = NH / 2; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
       if (leader) sm.me2s[el][m] = s;
@@ -158,27 +181,31 @@ struct QcdTile {
   }
 };
 
-template <int PROC, typename R, bool WIDTH, int SPLIT, int MINB>
+template <int PROC, typename R, bool WIDTH, int SPLIT, int MINB, bool TC = false>
 __global__ void __launch_bounds__(QCD_BLOCK, MINB)
     qcd_reweight_kernel(const double* __restrict__ mom, const double* __restrict__ w_in,
                         int64_t nev, const __grid_constant__ QcdLaunch lp,
                         double* __restrict__ out) {
-  using T = QcdTile<PROC, R, WIDTH, SPLIT>;
+  using T = QcdTile<PROC, R, WIDTH, SPLIT, TC>;
   __shared__ typename T::Smem sm;
   T::run(sm, mom, w_in, nev, (int64_t)blockIdx.x, lp, out);
 }
 
-// Variant table (SPLIT, MINB) shared by every process.
+// Variant table (SPLIT, MINB, TC) shared by every process.  TC selects the
+// tensor-core colour form (mixed precision, >= 8 lanes per event; the scalar
+// form otherwise).
 struct QcdVariant {
-  int split, minb;
+  int split, minb, tc;
 };
-constexpr QcdVariant kQcdVariants[QCD_NVARIANT] = {{0, 1}, {1, 1}, {0, 3}, {1, 3}, {1, 4}};
+constexpr QcdVariant kQcdVariants[QCD_NVARIANT] = {{0, 1, 0}, {1, 1, 0}, {0, 3, 0}, {1, 3, 0},
+                                                   {1, 4, 0}, {0, 3, 1}, {1, 3, 1}};
 
 template <int PROC, typename R, int V>
 static int launch_v(const double* mom, const double* w_in, int64_t nev, const QcdLaunch& lp,
                     double* out, cudaStream_t st) {
   constexpr int SPLIT = kQcdVariants[V].split;
   constexpr int MINB = kQcdVariants[V].minb;
+  constexpr bool TC = kQcdVariants[V].tc != 0 && std::is_same<R, float>::value;
   constexpr int EPB = QCD_BLOCK / (QcdProc<PROC>::info::NGHEL << SPLIT);
   const int64_t blocks = (nev + EPB - 1) / EPB;
   if (blocks > 0x7fffffffLL) return (int)cudaErrorInvalidValue;
@@ -188,8 +215,8 @@ static int launch_v(const double* mom, const double* w_in, int64_t nev, const Qc
                       (QCD_BLOCK / QcdProc<PROC>::info::NGHEL)),
            QCD_BLOCK, 0, st>>>(mom, w_in, nev, lp, out);
   else
-    qcd_reweight_kernel<PROC, R, false, SPLIT, MINB><<<(unsigned)blocks, QCD_BLOCK, 0, st>>>(mom, w_in, nev, lp,
-                                                                                            out);
+    qcd_reweight_kernel<PROC, R, false, SPLIT, MINB, TC><<<(unsigned)blocks, QCD_BLOCK, 0, st>>>(mom, w_in, nev,
+                                                                                                lp, out);
   return (int)cudaGetLastError();
 }
 
@@ -202,6 +229,8 @@ static int launch_variant(int variant, const double* mom, const double* w_in, in
     case 2: return launch_v<PROC, R, 2>(mom, w_in, nev, lp, out, st);
     case 3: return launch_v<PROC, R, 3>(mom, w_in, nev, lp, out, st);
     case 4: return launch_v<PROC, R, 4>(mom, w_in, nev, lp, out, st);
+    case 5: return launch_v<PROC, R, 5>(mom, w_in, nev, lp, out, st);
+    case 6: return launch_v<PROC, R, 6>(mom, w_in, nev, lp, out, st);
     default: return (int)cudaErrorInvalidValue;
   }
 }

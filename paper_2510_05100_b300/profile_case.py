@@ -25,7 +25,20 @@ def main():
     ap.add_argument("--mode", choices=["fp64", "mixed"], default="fp64")
     ap.add_argument("--nev", type=int, default=1 << 19)
     ap.add_argument("--launches", type=int, default=2)
+    ap.add_argument("--surrogate-steps", type=int, default=0,
+                    help="instead: train the surrogate for this many steps of 8192 samples")
     a = ap.parse_args()
+    if a.surrogate_steps:
+        mom = torch.from_numpy(ps.make_events("gg_ttxg", a.nev, 3)).cuda()
+        pts = ps.grid_gg_ttxg()
+        ex = rex.Process("gg_ttxg", rex.FP64)
+        ex.set_params(mt=173.0, wt=0.0, alphas=0.118)
+        ratio = ex.reweight(mom, torch.ones(a.nev, dtype=torch.float64, device="cuda"), pts)
+        s = rex.Surrogate(1)
+        losses = s.train(mom, ratio, pts, steps=a.surrogate_steps, batch=8192)
+        torch.cuda.synchronize()
+        print(f"surrogate {a.surrogate_steps} steps ok, loss {losses[0]:.4g} -> {losses[-1]:.4g}")
+        return
     mom = torch.from_numpy(ps.make_events(a.proc, a.nev, 3)).cuda()
     w = torch.ones(a.nev, dtype=torch.float64, device="cuda")
     pts = GRIDS[a.proc]()
