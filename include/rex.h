@@ -275,6 +275,16 @@ int rex_surrogate_reweight(rex_surrogate *s, rex_proc *exact, const double *mome
                            float tau, double *w_out, float *pred, float *err,
                            int64_t *n_fallback, void *stream);
 
+/* Exact coupling part of the target.  At tree level |M|^2 is proportional to
+ * alphas^power (power = 3 for g g -> t t~ g: one factor g_s^2 per QCD vertex
+ * pair, Sec. 3), so log r = power * log(alphas / alphas0) + f(p, mt) with
+ * f independent of alphas.  After this call the network learns f only:
+ * training targets become log(ratio) - power * log(alphas / alphas0), and
+ * inference adds the term back to pred (err is unchanged).  power = 0 (the
+ * default) learns the whole log ratio.  alphas0 is the original point's
+ * alphas.  Errors: REX_EINVAL for power outside 0..8 or alphas0 <= 0. */
+int rex_surrogate_set_exact_alphas(rex_surrogate *s, double alphas0, int power);
+
 void rex_surrogate_free(rex_surrogate *s);
 
 /* Release a handle (NULL is ignored).  Synchronises nothing; the caller must

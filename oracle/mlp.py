@@ -19,6 +19,11 @@ Loss of a batch of n samples with targets t:
 where the error head's target |y_i - t_i| is treated as a constant (no gradient
 flows from the second term into y).
 
+Exact coupling part (optional): tree-level |M|^2 is proportional to alphas^n
+(n = 3 for g g -> t t~ g), so log r = n log(alphas / alphas0) + f(p, mt).  With
+n > 0 the network's target is t = log r - n log(alphas / alphas0), and the
+prediction of log r is y + n log(alphas / alphas0).
+
 Adam (Kingma & Ba 2015): m <- b1 m + (1-b1) g, v <- b2 v + (1-b2) g^2,
 theta <- theta - lr (m / (1 - b1^s)) / (sqrt(v / (1 - b2^s)) + eps).
 """
@@ -127,3 +132,13 @@ def features(p: np.ndarray, mt: np.ndarray, alphas: np.ndarray) -> np.ndarray:
     x[:, 20] = (np.asarray(mt) - MT_REF) * MT_SCALE
     x[:, 21] = (np.asarray(alphas) - AS_REF) * AS_SCALE
     return x
+
+
+def coupling_part(alphas, alphas0: float, power: int):
+    """n log(alphas / alphas0): the exact alphas dependence of the log ratio."""
+    return power * np.log(np.asarray(alphas, dtype=np.float64) / alphas0)
+
+
+def target(ratio, alphas, alphas0: float = 0.118, power: int = 0):
+    """Training target: log(ratio) minus the exact coupling part."""
+    return np.log(np.asarray(ratio, dtype=np.float64)) - coupling_part(alphas, alphas0, power)

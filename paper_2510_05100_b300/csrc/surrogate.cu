@@ -79,11 +79,11 @@ __device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
 //   explicit_order = 0: sample i is the pair idx = SplitMix64(seed, step, i) mod (nev k),
 //                       event idx / k, point idx % k, ratio[e][j] (training).
 // Features: momenta in TeV, (mt - 173)/3, (alphas - 0.118)/0.008, zero padding to 32;
-// target log(ratio).
+// target log(ratio) - apow * log(alphas / as0) (the exact coupling part removed).
 __global__ void features_kernel(const double* __restrict__ mom, const double* __restrict__ ratio,
                                 const double* __restrict__ pmt, const double* __restrict__ pas, int64_t nev, int k,
-                                int n, int explicit_order, uint64_t seed, uint64_t step, __nv_bfloat16* __restrict__ X,
-                                float* __restrict__ T) {
+                                int n, int explicit_order, uint64_t seed, uint64_t step, double as0, int apow,
+                                __nv_bfloat16* __restrict__ X, float* __restrict__ T) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   int64_t e, j, r;
@@ -106,7 +106,7 @@ __global__ void features_kernel(const double* __restrict__ mom, const double* __
   x[21] = __float2bfloat16((float)((pas[j] - AS_REF) * AS_SCALE));
 #pragma unroll
   for (int c = NIN; c < NINP; ++c) x[c] = __float2bfloat16(0.f);
-  T[i] = (float)log(ratio[r]);
+  T[i] = (float)(log(ratio[r]) - (apow ? apow * log(pas[j] / as0) : 0.0));
 }
 
 // Output head, loss and their gradients.  One warp per sample.
@@ -219,9 +219,12 @@ __global__ void event_features_kernel(const double* __restrict__ mom, int64_t ne
 }
 
 __global__ void point_part_kernel(const float* __restrict__ P, const double* __restrict__ pmt,
-                                  const double* __restrict__ pas, int k, float* __restrict__ P1) {
+                                  const double* __restrict__ pas, int k, double as0, int apow,
+                                  float* __restrict__ P1, float* __restrict__ OFF) {
   const int j = blockIdx.x, c = threadIdx.x;
   if (j >= k || c >= WID) return;
+  // exact coupling part of the log ratio, added back to the network's output
+  if (c == 0) OFF[j] = apow ? (float)(apow * log(pas[j] / as0)) : 0.f;
   // the point features round to BF16 exactly as in training
   const float f0 = __bfloat162float(__float2bfloat16((float)((pmt[j] - MT_REF) * MT_SCALE)));
   const float f1 = __bfloat162float(__float2bfloat16((float)((pas[j] - AS_REF) * AS_SCALE)));
@@ -245,10 +248,12 @@ __global__ void expand_kernel(const float* __restrict__ E1, const float* __restr
   reinterpret_cast<__nv_bfloat162*>(A1)[t] = __floats2bfloat162_rn(gelu_f(z0), gelu_f(z1));
 }
 
-// Inference head: pred, err per pair; new weight w_in * exp(pred); flag events
-// whose predicted error exceeds tau.  One warp per pair.
+// Inference head: pred = network output + exact coupling part OFF[j], err per
+// pair; new weight w_in * exp(pred); flag events whose predicted error exceeds
+// tau.  One warp per pair.
 __global__ void __launch_bounds__(256) head_infer_kernel(const __nv_bfloat16* __restrict__ A4, const float* __restrict__ P,
-                                                          int64_t pairs, int k, int64_t ev_base,
+                                                          const float* __restrict__ OFF, int64_t pairs, int k,
+                                                          int64_t ev_base,
                                                           const double* __restrict__ w_in, float tau,
                                                           float* __restrict__ pred, float* __restrict__ err,
                                                           double* __restrict__ w_out, int* __restrict__ flag) {
@@ -272,9 +277,9 @@ __global__ void __launch_bounds__(256) head_infer_kernel(const __nv_bfloat16* __
     e += __shfl_xor_sync(0xffffffffu, e, off);
   }
   if (lane == 0) {
-    y += P[OFF_B5];
-    e += P[OFF_B5 + 1];
     const int64_t ev = ev_base + pr / k;
+    y += P[OFF_B5] + OFF[pr - (pr / k) * k];
+    e += P[OFF_B5 + 1];
     if (pred) pred[ev_base * k + pr] = y;
     if (err) err[ev_base * k + pr] = e;
     if (w_out) w_out[ev_base * k + pr] = w_in[ev] * exp((double)y);
@@ -350,8 +355,10 @@ struct rex_surrogate {
   float *params, *grads, *m, *v;
   __nv_bfloat16* wb[4];
   int step;
+  double as0 = 0.118;   // exact coupling part: apow * log(alphas / as0)
+  int apow = 0;
   // work buffers, grown on demand
-  DevBuf X, T, Z[4], A[4], dZa, dZb, part, pmt, pas, E1, P1, flag, cnt, list, gmom, gw, gout;
+  DevBuf X, T, Z[4], A[4], dZa, dZb, part, pmt, pas, E1, P1, OFFS, flag, cnt, list, gmom, gw, gout;
 };
 
 namespace {
@@ -362,7 +369,7 @@ void release(rex_surrogate* s) {
   cudaFree(s->m);
   cudaFree(s->v);
   for (auto& w : s->wb) cudaFree(w);
-  for (DevBuf* b : {&s->X, &s->T, &s->dZa, &s->dZb, &s->part, &s->pmt, &s->pas, &s->E1, &s->P1, &s->flag, &s->cnt,
+  for (DevBuf* b : {&s->X, &s->T, &s->dZa, &s->dZb, &s->part, &s->pmt, &s->pas, &s->E1, &s->P1, &s->OFFS, &s->flag, &s->cnt,
                     &s->list, &s->gmom, &s->gw, &s->gout})
     b->release();
   for (int l = 0; l < 4; ++l) {
@@ -562,7 +569,8 @@ int rex_surrogate_loss_grad(rex_surrogate* s, const double* momenta, const doubl
   if (e != cudaSuccess) return sfail(REX_ENOMEM, "batch buffers: %s", cudaGetErrorString(e));
   // sample i = event i with its own point (mt[i], alphas[i]) and ratio[i]
   features_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(momenta, ratio, mt, alphas, n, 1, (int)n, 1, 0, 0,
-                                                               s->X.as<__nv_bfloat16>(), s->T.as<float>());
+                                                               s->as0, s->apow, s->X.as<__nv_bfloat16>(),
+                                                               s->T.as<float>());
   DevBuf& loss = s->gout;
   if ((e = loss.ensure(8)) != cudaSuccess) return sfail(REX_ENOMEM, "loss buffer");
   rc = forward_backward(s, (int)n, loss.as<float>(), st);
@@ -604,7 +612,7 @@ int rex_surrogate_train(rex_surrogate* s, const double* momenta, const double* r
   for (int it = 0; it < steps; ++it) {
     features_kernel<<<(unsigned)((batch + 255) / 256), 256, 0, st>>>(
         momenta, ratio, s->pmt.as<double>(), s->pas.as<double>(), nev, k, batch, 0, seed, (uint64_t)s->step,
-        s->X.as<__nv_bfloat16>(), s->T.as<float>());
+        s->as0, s->apow, s->X.as<__nv_bfloat16>(), s->T.as<float>());
     rc = forward_backward(s, batch, s->gout.as<float>() + it, st);
     if (rc) return rc;
     s->step += 1;
@@ -642,6 +650,7 @@ int rex_surrogate_reweight(rex_surrogate* s, rex_proc* exact, const double* mome
   cudaError_t e = s->X.ensure(cev * NINP * 2);
   if (e == cudaSuccess) e = s->E1.ensure(cev * WID * 4);
   if (e == cudaSuccess) e = s->P1.ensure((size_t)k * WID * 4);
+  if (e == cudaSuccess) e = s->OFFS.ensure((size_t)k * 4);
   if (e == cudaSuccess) e = s->pmt.ensure((size_t)k * 8);
   if (e == cudaSuccess) e = s->pas.ensure((size_t)k * 8);
   if (e == cudaSuccess) e = s->A[0].ensure(cpairs * WID * 2);
@@ -657,7 +666,8 @@ int rex_surrogate_reweight(rex_surrogate* s, rex_proc* exact, const double* mome
   if (e == cudaSuccess) e = cudaMemcpyAsync(s->pas.p, ha.data(), k * 8, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess && w_out) e = cudaMemsetAsync(s->flag.p, 0, nev * 4, st);
   if (e != cudaSuccess) return scuda(e, "inference set-up");
-  point_part_kernel<<<k, WID, 0, st>>>(s->params, s->pmt.as<double>(), s->pas.as<double>(), k, s->P1.as<float>());
+  point_part_kernel<<<k, WID, 0, st>>>(s->params, s->pmt.as<double>(), s->pas.as<double>(), k, s->as0, s->apow,
+                                       s->P1.as<float>(), s->OFFS.as<float>());
   for (int64_t e0 = 0; e0 < nev; e0 += chunk) {
     const int64_t ne = (nev - e0) < chunk ? (nev - e0) : chunk;
     const int64_t np = ne * k;
@@ -698,7 +708,8 @@ int rex_surrogate_reweight(rex_surrogate* s, rex_proc* exact, const double* mome
       if ((e = gemm<false, false, EPI_FWD>(f, 1, st)) != cudaSuccess) return scuda(e, "hidden gemm");
       std::swap(cur, nxt);
     }
-    head_infer_kernel<<<(unsigned)((np + 7) / 8), 256, 0, st>>>(cur, s->params, np, k, e0, w_in, tau, pred, err,
+    head_infer_kernel<<<(unsigned)((np + 7) / 8), 256, 0, st>>>(cur, s->params, s->OFFS.as<float>(), np, k, e0,
+                                                                 w_in, tau, pred, err,
                                                                  w_out, w_out ? s->flag.as<int>() : nullptr);
     if ((e = cudaGetLastError()) != cudaSuccess) return scuda(e, "inference head");
   }
@@ -726,6 +737,15 @@ int rex_surrogate_reweight(rex_surrogate* s, rex_proc* exact, const double* mome
                                                                               s->gout.as<double>(), w_out);
   e = cudaGetLastError();
   return e == cudaSuccess ? REX_OK : scuda(e, "fallback scatter");
+}
+
+int rex_surrogate_set_exact_alphas(rex_surrogate* s, double alphas0, int power) {
+  const int rc = check_handle(s);
+  if (rc) return rc;
+  if (power < 0 || power > 8 || !(alphas0 > 0.0)) return sfail(REX_EINVAL, "need 0 <= power <= 8 and alphas0 > 0");
+  s->as0 = alphas0;
+  s->apow = power;
+  return REX_OK;
 }
 
 void rex_surrogate_free(rex_surrogate* s) {

@@ -41,7 +41,7 @@ EXPORTS = (
     "rex_multi_replay", "rex_multi_free", "rex_reweight_multi_noalloc", "rex_multi_set_mode",
     "rex_surrogate_num_params", "rex_surrogate_last_error", "rex_surrogate_create",
     "rex_surrogate_set_weights", "rex_surrogate_get_weights", "rex_surrogate_loss_grad",
-    "rex_surrogate_train", "rex_surrogate_reweight", "rex_surrogate_free",
+    "rex_surrogate_train", "rex_surrogate_reweight", "rex_surrogate_set_exact_alphas", "rex_surrogate_free",
 )
 
 
@@ -142,6 +142,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.rex_surrogate_reweight.argtypes = [vp, vp, vp, vp, i64, pp, ctypes.c_int, ctypes.c_float, vp, vp, vp,
                                            ctypes.POINTER(ctypes.c_int64), vp]
     lib.rex_surrogate_reweight.restype = ctypes.c_int
+    lib.rex_surrogate_set_exact_alphas.argtypes = [vp, ctypes.c_double, ctypes.c_int]
+    lib.rex_surrogate_set_exact_alphas.restype = ctypes.c_int
     lib.rex_surrogate_free.argtypes = [vp]
     lib.rex_surrogate_free.restype = None
     lib.rex_version.argtypes = []
@@ -359,6 +361,10 @@ class Surrogate:
         import numpy as np
         w = np.ascontiguousarray(w, dtype=np.float32)
         _scheck(load().rex_surrogate_set_weights(self._h, w.ctypes.data, w.size))
+
+    def set_exact_alphas(self, alphas0: float, power: int) -> None:
+        """Make the alphas^power dependence of |M|^2 exact; the network learns the rest."""
+        _scheck(load().rex_surrogate_set_exact_alphas(self._h, float(alphas0), int(power)))
 
     def loss_grad(self, momenta, ratio, mt, alphas, stream=None):
         import numpy as np

@@ -92,3 +92,21 @@ def test_features_layout():
     assert x.shape == (2, 22)
     assert np.allclose(x[1, :20], p[1].reshape(20) * 1e-3)
     assert np.allclose(x[:, 20], [0.0, 1.0]) and np.allclose(x[:, 21], [0.0, 1.0])
+
+
+def test_coupling_part_removes_the_exact_alphas_dependence():
+    """With the coupling part removed, the target of an alphas-only reweighting is
+    zero: the oracle's |M|^2 scales exactly as alphas^3 for g g -> t t~ g."""
+    from oracle import reweight
+    from paper_2510_05100_b300 import phase_space as ps
+    p = ps.make_events("gg_ttxg", 3, 12)
+    orig = dict(mt=173.0, wt=0.0, alphas=0.118)
+    pts = [dict(mt=173.0, wt=0.0, alphas=a) for a in (0.110, 0.121, 0.126)]
+    r = reweight.reweight("gg_ttxg", p, np.ones(3), orig, pts)
+    al = np.array([q["alphas"] for q in pts])[None, :]
+    t = mlp.target(r, al, 0.118, 3)
+    assert np.max(np.abs(t)) < 1e-13
+    # the full log ratio is recovered by adding the part back
+    assert np.allclose(t + mlp.coupling_part(al, 0.118, 3), np.log(r), rtol=0, atol=1e-15)
+    # power 0 leaves the target as log(ratio)
+    assert np.array_equal(mlp.target(r, al, 0.118, 0), np.log(r))
