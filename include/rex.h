@@ -221,7 +221,8 @@ int rex_reweight_multi_noalloc(const rex_batch *batches, int nbatch,
 
 /* ---- Learned surrogate of the weight ratio ---------------------------------
  * The paper has no learned component.  An MLP (22 inputs -> 4 hidden layers of
- * 256 with GELU -> 2 outputs) predicts r = log(|M(p;theta)|^2/|M(p;theta_0)|^2)
+ * 256 with GELU in its tanh form, z (1 + tanh(sqrt(2/pi) (z + 0.044715 z^3))) / 2
+ * -> 2 outputs) predicts r = log(|M(p;theta)|^2/|M(p;theta_0)|^2)
  * for g g -> t t~ g events (inputs: the 20 momentum components in TeV,
  * (mt - 173)/3, (alphas - 0.118)/0.008) and an estimate of its own absolute
  * error.  Weights are FP32 masters with BF16 copies; GEMMs run on tensor cores
@@ -284,6 +285,20 @@ int rex_surrogate_reweight(rex_surrogate *s, rex_proc *exact, const double *mome
  * default) learns the whole log ratio.  alphas0 is the original point's
  * alphas.  Errors: REX_EINVAL for power outside 0..8 or alphas0 <= 0. */
 int rex_surrogate_set_exact_alphas(rex_surrogate *s, double alphas0, int power);
+
+/* Inference kernel of rex_surrogate_reweight.
+ *   REX_SURROGATE_FUSED (default): one persistent kernel per call; each tile of
+ *     128 (event, point) pairs runs all layers on the tcgen05 tensor cores with
+ *     the accumulator in tensor memory and the activations in shared memory.
+ *   REX_SURROGATE_LAYERED: layer-by-layer mma.sync GEMMs over event chunks, the
+ *     activations stored in global memory between layers.
+ * Both compute the same network in the same precision (BF16 operands and
+ * activations, FP32 accumulation); their results agree to FP32 summation order.
+ * With the fused kernel a bounded internal wait that gives up makes the call
+ * return REX_ECUDA when it synchronises (w_out set).  Errors: REX_EINVAL. */
+#define REX_SURROGATE_FUSED 0
+#define REX_SURROGATE_LAYERED 1
+int rex_surrogate_set_kernel(rex_surrogate *s, int kind);
 
 void rex_surrogate_free(rex_surrogate *s);
 

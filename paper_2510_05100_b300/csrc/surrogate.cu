@@ -23,6 +23,7 @@
 #include <vector>
 
 #include "../../include/rex.h"
+#include "surrogate_fused.cuh"
 #include "surrogate_gemm.cuh"
 
 using namespace rex;
@@ -233,6 +234,17 @@ __global__ void point_part_kernel(const float* __restrict__ P, const double* __r
   P1[j * WID + c] = f0 * w0 + f1 * w1 + P[OFF_B1 + c];
 }
 
+// Per-point table of the fused kernel: the two point features rounded to BF16
+// (as in training) and the exact coupling part.
+__global__ void point_table_kernel(const double* __restrict__ pmt, const double* __restrict__ pas, int k,
+                                   double as0, int apow, float4* __restrict__ ptab) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= k) return;
+  const float f0 = __bfloat162float(__float2bfloat16((float)((pmt[j] - MT_REF) * MT_SCALE)));
+  const float f1 = __bfloat162float(__float2bfloat16((float)((pas[j] - AS_REF) * AS_SCALE)));
+  ptab[j] = make_float4(f0, f1, apow ? (float)(apow * log(pas[j] / as0)) : 0.f, 0.f);
+}
+
 // A1[(e, j)] = gelu(E1[e] + P1[j]) for the pairs of an event chunk (pair = e * k + j)
 __global__ void expand_kernel(const float* __restrict__ E1, const float* __restrict__ P1, int64_t nev, int k,
                               __nv_bfloat16* __restrict__ A1) {
@@ -357,8 +369,10 @@ struct rex_surrogate {
   int step;
   double as0 = 0.118;   // exact coupling part: apow * log(alphas / as0)
   int apow = 0;
+  int kernel = REX_SURROGATE_FUSED;   // inference kernel
   // work buffers, grown on demand
   DevBuf X, T, Z[4], A[4], dZa, dZb, part, pmt, pas, E1, P1, OFFS, flag, cnt, list, gmom, gw, gout;
+  DevBuf PK, PTAB, STATUS;   // fused inference: packed weight images, point table, wait status
 };
 
 namespace {
@@ -370,7 +384,7 @@ void release(rex_surrogate* s) {
   cudaFree(s->v);
   for (auto& w : s->wb) cudaFree(w);
   for (DevBuf* b : {&s->X, &s->T, &s->dZa, &s->dZb, &s->part, &s->pmt, &s->pas, &s->E1, &s->P1, &s->OFFS, &s->flag, &s->cnt,
-                    &s->list, &s->gmom, &s->gw, &s->gout})
+                    &s->list, &s->gmom, &s->gw, &s->gout, &s->PK, &s->PTAB, &s->STATUS})
     b->release();
   for (int l = 0; l < 4; ++l) {
     s->Z[l].release();
@@ -485,6 +499,145 @@ int forward_backward(rex_surrogate* s, int n, float* loss_dev, cudaStream_t st) 
   }
   if ((e = cudaGetLastError()) != cudaSuccess) return scuda(e, "backward");
   return REX_OK;
+}
+
+// Layer-by-layer inference: per event chunk, the layer-1 GEMM on event features
+// plus the per-point part, then three mma.sync GEMMs with fused bias/GELU and
+// the head kernel (activations round-trip through global memory).
+int infer_layered(rex_surrogate* s, const double* momenta, const double* w_in, int64_t nev, const rex_params* pts,
+                  int k, float tau, double* w_out, float* pred, float* err, cudaStream_t st) {
+  // events per chunk: at most 8192 events and 2^19 (event, point) pairs
+  int64_t chunk = ((int64_t)1 << 19) / k;
+  if (chunk > 8192) chunk = 8192;
+  if (chunk < 1) chunk = 1;
+  const int64_t cev = nev < chunk ? nev : chunk;
+  const int64_t cpairs = cev * k;
+  cudaError_t e = s->X.ensure(cev * NINP * 2);
+  if (e == cudaSuccess) e = s->E1.ensure(cev * WID * 4);
+  if (e == cudaSuccess) e = s->P1.ensure((size_t)k * WID * 4);
+  if (e == cudaSuccess) e = s->OFFS.ensure((size_t)k * 4);
+  if (e == cudaSuccess) e = s->pmt.ensure((size_t)k * 8);
+  if (e == cudaSuccess) e = s->pas.ensure((size_t)k * 8);
+  if (e == cudaSuccess) e = s->A[0].ensure(cpairs * WID * 2);
+  if (e == cudaSuccess) e = s->A[1].ensure(cpairs * WID * 2);
+  if (e == cudaSuccess && w_out) e = s->flag.ensure(nev * 4);
+  if (e != cudaSuccess) return sfail(REX_ENOMEM, "inference buffers: %s", cudaGetErrorString(e));
+  std::vector<double> hm(k), ha(k);
+  for (int j = 0; j < k; ++j) {
+    hm[j] = pts[j].mt;
+    ha[j] = pts[j].alphas;
+  }
+  e = cudaMemcpyAsync(s->pmt.p, hm.data(), k * 8, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(s->pas.p, ha.data(), k * 8, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess && w_out) e = cudaMemsetAsync(s->flag.p, 0, nev * 4, st);
+  if (e != cudaSuccess) return scuda(e, "inference set-up");
+  point_part_kernel<<<k, WID, 0, st>>>(s->params, s->pmt.as<double>(), s->pas.as<double>(), k, s->as0, s->apow,
+                                       s->P1.as<float>(), s->OFFS.as<float>());
+  for (int64_t e0 = 0; e0 < nev; e0 += chunk) {
+    const int64_t ne = (nev - e0) < chunk ? (nev - e0) : chunk;
+    const int64_t np = ne * k;
+    event_features_kernel<<<(unsigned)((ne + 255) / 256), 256, 0, st>>>(momenta + e0 * 20, ne,
+                                                                        s->X.as<__nv_bfloat16>());
+    // per-event part of layer 1: E1 = x_ev W1 (parameter columns of x_ev are zero)
+    GemmArgs g{};
+    g.M = (int)ne;
+    g.N = WID;
+    g.K = NINP;
+    g.A = s->X.as<__nv_bfloat16>();
+    g.lda = NINP;
+    g.B = s->wb[0];
+    g.ldb = WID;
+    g.C32 = s->E1.as<float>();
+    g.ldc = WID;
+    g.k_per_split = NINP;
+    if ((e = gemm<false, false, EPI_F32>(g, 1, st)) != cudaSuccess) return scuda(e, "layer-1 gemm");
+    expand_kernel<<<(unsigned)((np * (WID / 2) + 255) / 256), 256, 0, st>>>(s->E1.as<float>(), s->P1.as<float>(), ne,
+                                                                            k, s->A[0].as<__nv_bfloat16>());
+    // layers 2..4 on the chunk's pairs (no pre-activations kept)
+    __nv_bfloat16* cur = s->A[0].as<__nv_bfloat16>();
+    __nv_bfloat16* nxt = s->A[1].as<__nv_bfloat16>();
+    for (int l = 1; l < 4; ++l) {
+      GemmArgs f{};
+      f.M = (int)np;
+      f.N = WID;
+      f.K = WID;
+      f.A = cur;
+      f.lda = WID;
+      f.B = s->wb[l];
+      f.ldb = WID;
+      f.C32 = nullptr;
+      f.C16 = nxt;
+      f.ldc16 = WID;
+      f.bias = s->params + OFF_B[l];
+      f.k_per_split = WID;
+      if ((e = gemm<false, false, EPI_FWD>(f, 1, st)) != cudaSuccess) return scuda(e, "hidden gemm");
+      std::swap(cur, nxt);
+    }
+    head_infer_kernel<<<(unsigned)((np + 7) / 8), 256, 0, st>>>(cur, s->params, s->OFFS.as<float>(), np, k, e0,
+                                                                 w_in, tau, pred, err,
+                                                                 w_out, w_out ? s->flag.as<int>() : nullptr);
+    if ((e = cudaGetLastError()) != cudaSuccess) return scuda(e, "inference head");
+  }
+  return REX_OK;
+}
+
+// Fused inference (surrogate_fused.cuh): one persistent tcgen05 kernel.
+int infer_fused(rex_surrogate* s, const double* momenta, const double* w_in, int64_t nev, const rex_params* pts,
+                int k, float tau, double* w_out, float* pred, float* err, cudaStream_t st) {
+  const size_t img1 = (size_t)FW * FK1, img = (size_t)FW * FW;
+  cudaError_t e = s->PK.ensure((img1 + 3 * img) * 2);
+  if (e == cudaSuccess) e = s->PTAB.ensure((size_t)k * sizeof(float4));
+  if (e == cudaSuccess) e = s->STATUS.ensure(4);
+  if (e == cudaSuccess) e = s->pmt.ensure((size_t)k * 8);
+  if (e == cudaSuccess) e = s->pas.ensure((size_t)k * 8);
+  if (e == cudaSuccess && w_out) e = s->flag.ensure(nev * 4);
+  if (e != cudaSuccess) return sfail(REX_ENOMEM, "inference buffers: %s", cudaGetErrorString(e));
+  std::vector<double> hm(k), ha(k);
+  for (int j = 0; j < k; ++j) {
+    hm[j] = pts[j].mt;
+    ha[j] = pts[j].alphas;
+  }
+  e = cudaMemcpyAsync(s->pmt.p, hm.data(), k * 8, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(s->pas.p, ha.data(), k * 8, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess && w_out) e = cudaMemsetAsync(s->flag.p, 0, nev * 4, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(s->STATUS.p, 0, 4, st);
+  if (e != cudaSuccess) return scuda(e, "inference set-up");
+  __nv_bfloat16* pk = s->PK.as<__nv_bfloat16>();
+  pack_kmajor_kernel<<<(unsigned)((img1 + 255) / 256), 256, 0, st>>>(s->params + OFF_W1, FK1, pk);
+  for (int l = 1; l < 4; ++l)
+    pack_kmajor_kernel<<<(unsigned)((img + 255) / 256), 256, 0, st>>>(s->params + OFF_W[l], FW,
+                                                                      pk + img1 + (l - 1) * img);
+  point_table_kernel<<<(k + 127) / 128, 128, 0, st>>>(s->pmt.as<double>(), s->pas.as<double>(), k, s->as0, s->apow,
+                                                      s->PTAB.as<float4>());
+  if ((e = cudaGetLastError()) != cudaSuccess) return scuda(e, "weight packing");
+  int dev = 0, sms = 0;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess ||
+      (e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess ||
+      (e = cudaFuncSetAttribute(fused_mlp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)sizeof(FusedSmem))) != cudaSuccess)
+    return scuda(e, "fused kernel set-up");
+  FusedArgs fa{};
+  fa.mom = momenta;
+  fa.w_in = w_in;
+  fa.nev = nev;
+  fa.k = k;
+  fa.ptab = s->PTAB.as<float4>();
+  fa.w1 = pk;
+  fa.w234 = pk + img1;
+  for (int l = 0; l < 4; ++l) fa.bias[l] = s->params + OFF_B[l];
+  fa.w5 = s->params + OFF_W5;
+  fa.b5 = s->params + OFF_B5;
+  fa.tau = tau;
+  fa.pred = pred;
+  fa.err = err;
+  fa.w_out = w_out;
+  fa.flag = w_out ? s->flag.as<int>() : nullptr;
+  fa.status = s->STATUS.as<int>();
+  const int64_t tiles = (nev * k + FM - 1) / FM;
+  const int grid = (int)(tiles < sms ? tiles : sms);
+  fused_mlp_kernel<<<grid, FTHREADS, sizeof(FusedSmem), st>>>(fa);
+  e = cudaGetLastError();
+  return e == cudaSuccess ? REX_OK : scuda(e, "fused inference kernel");
 }
 
 int check_handle(const rex_surrogate* s) { return s ? REX_OK : sfail(REX_EINVAL, "null surrogate handle"); }
@@ -641,78 +794,10 @@ int rex_surrogate_reweight(rex_surrogate* s, rex_proc* exact, const double* mome
   if (!momenta || !pts || (w_out && !w_in)) return sfail(REX_EINVAL, "null array");
   if (k > 4096) return sfail(REX_EINVAL, "at most 4096 points per call");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  // events per chunk: at most 8192 events and 2^19 (event, point) pairs
-  int64_t chunk = ((int64_t)1 << 19) / k;
-  if (chunk > 8192) chunk = 8192;
-  if (chunk < 1) chunk = 1;
-  const int64_t cev = nev < chunk ? nev : chunk;
-  const int64_t cpairs = cev * k;
-  cudaError_t e = s->X.ensure(cev * NINP * 2);
-  if (e == cudaSuccess) e = s->E1.ensure(cev * WID * 4);
-  if (e == cudaSuccess) e = s->P1.ensure((size_t)k * WID * 4);
-  if (e == cudaSuccess) e = s->OFFS.ensure((size_t)k * 4);
-  if (e == cudaSuccess) e = s->pmt.ensure((size_t)k * 8);
-  if (e == cudaSuccess) e = s->pas.ensure((size_t)k * 8);
-  if (e == cudaSuccess) e = s->A[0].ensure(cpairs * WID * 2);
-  if (e == cudaSuccess) e = s->A[1].ensure(cpairs * WID * 2);
-  if (e == cudaSuccess && w_out) e = s->flag.ensure(nev * 4);
-  if (e != cudaSuccess) return sfail(REX_ENOMEM, "inference buffers: %s", cudaGetErrorString(e));
-  std::vector<double> hm(k), ha(k);
-  for (int j = 0; j < k; ++j) {
-    hm[j] = pts[j].mt;
-    ha[j] = pts[j].alphas;
-  }
-  e = cudaMemcpyAsync(s->pmt.p, hm.data(), k * 8, cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(s->pas.p, ha.data(), k * 8, cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess && w_out) e = cudaMemsetAsync(s->flag.p, 0, nev * 4, st);
-  if (e != cudaSuccess) return scuda(e, "inference set-up");
-  point_part_kernel<<<k, WID, 0, st>>>(s->params, s->pmt.as<double>(), s->pas.as<double>(), k, s->as0, s->apow,
-                                       s->P1.as<float>(), s->OFFS.as<float>());
-  for (int64_t e0 = 0; e0 < nev; e0 += chunk) {
-    const int64_t ne = (nev - e0) < chunk ? (nev - e0) : chunk;
-    const int64_t np = ne * k;
-    event_features_kernel<<<(unsigned)((ne + 255) / 256), 256, 0, st>>>(momenta + e0 * 20, ne,
-                                                                        s->X.as<__nv_bfloat16>());
-    // per-event part of layer 1: E1 = x_ev W1 (parameter columns of x_ev are zero)
-    GemmArgs g{};
-    g.M = (int)ne;
-    g.N = WID;
-    g.K = NINP;
-    g.A = s->X.as<__nv_bfloat16>();
-    g.lda = NINP;
-    g.B = s->wb[0];
-    g.ldb = WID;
-    g.C32 = s->E1.as<float>();
-    g.ldc = WID;
-    g.k_per_split = NINP;
-    if ((e = gemm<false, false, EPI_F32>(g, 1, st)) != cudaSuccess) return scuda(e, "layer-1 gemm");
-    expand_kernel<<<(unsigned)((np * (WID / 2) + 255) / 256), 256, 0, st>>>(s->E1.as<float>(), s->P1.as<float>(), ne,
-                                                                            k, s->A[0].as<__nv_bfloat16>());
-    // layers 2..4 on the chunk's pairs (no pre-activations kept)
-    __nv_bfloat16* cur = s->A[0].as<__nv_bfloat16>();
-    __nv_bfloat16* nxt = s->A[1].as<__nv_bfloat16>();
-    for (int l = 1; l < 4; ++l) {
-      GemmArgs f{};
-      f.M = (int)np;
-      f.N = WID;
-      f.K = WID;
-      f.A = cur;
-      f.lda = WID;
-      f.B = s->wb[l];
-      f.ldb = WID;
-      f.C32 = nullptr;
-      f.C16 = nxt;
-      f.ldc16 = WID;
-      f.bias = s->params + OFF_B[l];
-      f.k_per_split = WID;
-      if ((e = gemm<false, false, EPI_FWD>(f, 1, st)) != cudaSuccess) return scuda(e, "hidden gemm");
-      std::swap(cur, nxt);
-    }
-    head_infer_kernel<<<(unsigned)((np + 7) / 8), 256, 0, st>>>(cur, s->params, s->OFFS.as<float>(), np, k, e0,
-                                                                 w_in, tau, pred, err,
-                                                                 w_out, w_out ? s->flag.as<int>() : nullptr);
-    if ((e = cudaGetLastError()) != cudaSuccess) return scuda(e, "inference head");
-  }
+  cudaError_t e;
+  rc = s->kernel == REX_SURROGATE_FUSED ? infer_fused(s, momenta, w_in, nev, pts, k, tau, w_out, pred, err, st)
+                                        : infer_layered(s, momenta, w_in, nev, pts, k, tau, w_out, pred, err, st);
+  if (rc) return rc;
   if (!w_out || !exact) return REX_OK;
   // exact fallback of the flagged events
   if ((e = s->cnt.ensure(8)) != cudaSuccess || (e = s->list.ensure(nev * 8)) != cudaSuccess)
@@ -720,10 +805,13 @@ int rex_surrogate_reweight(rex_surrogate* s, rex_proc* exact, const double* mome
   if ((e = cudaMemsetAsync(s->cnt.p, 0, 4, st)) != cudaSuccess) return scuda(e, "fallback counter");
   compact_kernel<<<(unsigned)((nev + 255) / 256), 256, 0, st>>>(s->flag.as<int>(), nev, s->cnt.as<int>(),
                                                                 s->list.as<int64_t>());
-  int nflag = 0;
+  int nflag = 0, status = 0;
   e = cudaMemcpyAsync(&nflag, s->cnt.p, 4, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess && s->kernel == REX_SURROGATE_FUSED)
+    e = cudaMemcpyAsync(&status, s->STATUS.p, 4, cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return scuda(e, "fallback count");
+  if (status) return sfail(REX_ECUDA, "fused inference kernel: a bounded wait gave up");
   if (n_fallback) *n_fallback = nflag;
   if (nflag == 0) return REX_OK;
   if ((e = s->gmom.ensure((size_t)nflag * 20 * 8)) != cudaSuccess || (e = s->gw.ensure((size_t)nflag * 8)) != cudaSuccess ||
@@ -737,6 +825,14 @@ int rex_surrogate_reweight(rex_surrogate* s, rex_proc* exact, const double* mome
                                                                               s->gout.as<double>(), w_out);
   e = cudaGetLastError();
   return e == cudaSuccess ? REX_OK : scuda(e, "fallback scatter");
+}
+
+int rex_surrogate_set_kernel(rex_surrogate* s, int kind) {
+  const int rc = check_handle(s);
+  if (rc) return rc;
+  if (kind != REX_SURROGATE_FUSED && kind != REX_SURROGATE_LAYERED) return sfail(REX_EINVAL, "unknown kernel kind");
+  s->kernel = kind;
+  return REX_OK;
 }
 
 int rex_surrogate_set_exact_alphas(rex_surrogate* s, double alphas0, int power) {

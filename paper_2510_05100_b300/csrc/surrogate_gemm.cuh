@@ -26,10 +26,28 @@ enum GemmEpi : int { EPI_F32 = 0, EPI_FWD = 1, EPI_BWD = 2 };
 constexpr int GBM = 128, GBN = 128, GBK = 32, GTHREADS = 256;
 constexpr int GPAD = 8;   // bf16 elements of padding per smem row (bank spread for ldmatrix)
 
-// gelu(z) = z Phi(z) and its derivative Phi(z) + z phi(z)
-__device__ __forceinline__ float gelu_f(float z) { return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f)); }
+// GELU in its tanh form (Hendrycks & Gimpel 2016):
+//   gelu(z) = h (1 + t), h = z / 2, t = tanh(u), u = sqrt(2/pi) (z + 0.044715 z^3)
+//   gelu'(z) = (1 + t) / 2 + h (1 - t^2) sqrt(2/pi) (1 + 3 * 0.044715 z^2)
+// with tanh from the hardware approximation (tanh.approx.f32, relative error
+// about 2^-11, one MUFU operation).
+__device__ __forceinline__ float tanh_hw(float x) {
+  float y;
+  asm("tanh.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+constexpr float GELU_C0 = 0.7978845608028654f;               // sqrt(2/pi)
+constexpr float GELU_C1 = 0.7978845608028654f * 0.044715f;   // sqrt(2/pi) * 0.044715
+__device__ __forceinline__ float gelu_f(float z) {
+  const float u = z * fmaf(GELU_C1, z * z, GELU_C0);
+  const float h = 0.5f * z;
+  return fmaf(h, tanh_hw(u), h);
+}
 __device__ __forceinline__ float gelu_grad_f(float z) {
-  return 0.5f * (1.0f + erff(z * 0.70710678118654752f)) + z * 0.39894228040143268f * expf(-0.5f * z * z);
+  const float z2 = z * z;
+  const float t = tanh_hw(z * fmaf(GELU_C1, z2, GELU_C0));
+  const float du = fmaf(3.0f * GELU_C1, z2, GELU_C0);
+  return fmaf(0.5f * z * (1.0f - t * t), du, 0.5f * (1.0f + t));
 }
 
 struct GemmArgs {

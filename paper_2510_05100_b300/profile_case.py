@@ -1,6 +1,8 @@
 """Run a fixed reweighting case for profilers (ncu): python -m paper_2510_05100_b300.profile_case
 
   --proc gg_ttxg --mode fp64|mixed --nev N --launches L
+  --surrogate-steps S          (surrogate training steps instead)
+  --surrogate-infer fused|layered  (surrogate inference instead)
 
 Generates the standard seeded events, then issues L rex_reweight launches to the
 16-point (gg_ttxg) / 8-point (gg_ttx) / 64-point (gg_ttxgg) grid and synchronises.
@@ -27,7 +29,22 @@ def main():
     ap.add_argument("--launches", type=int, default=2)
     ap.add_argument("--surrogate-steps", type=int, default=0,
                     help="instead: train the surrogate for this many steps of 8192 samples")
+    ap.add_argument("--surrogate-infer", choices=["fused", "layered"], default=None,
+                    help="instead: surrogate inference of --nev events x 64 points, --launches times")
     a = ap.parse_args()
+    if a.surrogate_infer:
+        mom = torch.from_numpy(ps.make_events("gg_ttxg", a.nev, 3)).cuda()
+        pts = ps.grid_64()
+        s = rex.Surrogate(1)
+        s.set_exact_alphas(0.118, 3)
+        s.set_kernel(rex.SURROGATE_FUSED if a.surrogate_infer == "fused" else rex.SURROGATE_LAYERED)
+        pred = torch.empty((a.nev, len(pts)), dtype=torch.float32, device="cuda")
+        for _ in range(a.launches):
+            s.reweight(mom, None, pts, pred=pred)
+        torch.cuda.synchronize()
+        print(f"surrogate {a.surrogate_infer} inference nev={a.nev} k={len(pts)} launches={a.launches} ok "
+              f"pred[0,:3]={pred[0, :3].tolist()}")
+        return
     if a.surrogate_steps:
         mom = torch.from_numpy(ps.make_events("gg_ttxg", a.nev, 3)).cuda()
         pts = ps.grid_gg_ttxg()

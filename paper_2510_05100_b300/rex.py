@@ -31,6 +31,8 @@ MIXED = 1
 FLAG_NO_DEDUPE = 1
 MULTI_PERSISTENT = 0
 MULTI_STREAMS = 1
+SURROGATE_FUSED = 0
+SURROGATE_LAYERED = 1
 
 # symbols declared in include/rex.h
 EXPORTS = (
@@ -41,7 +43,8 @@ EXPORTS = (
     "rex_multi_replay", "rex_multi_free", "rex_reweight_multi_noalloc", "rex_multi_set_mode",
     "rex_surrogate_num_params", "rex_surrogate_last_error", "rex_surrogate_create",
     "rex_surrogate_set_weights", "rex_surrogate_get_weights", "rex_surrogate_loss_grad",
-    "rex_surrogate_train", "rex_surrogate_reweight", "rex_surrogate_set_exact_alphas", "rex_surrogate_free",
+    "rex_surrogate_train", "rex_surrogate_reweight", "rex_surrogate_set_exact_alphas", "rex_surrogate_set_kernel",
+    "rex_surrogate_free",
 )
 
 
@@ -144,6 +147,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.rex_surrogate_reweight.restype = ctypes.c_int
     lib.rex_surrogate_set_exact_alphas.argtypes = [vp, ctypes.c_double, ctypes.c_int]
     lib.rex_surrogate_set_exact_alphas.restype = ctypes.c_int
+    lib.rex_surrogate_set_kernel.argtypes = [vp, ctypes.c_int]
+    lib.rex_surrogate_set_kernel.restype = ctypes.c_int
     lib.rex_surrogate_free.argtypes = [vp]
     lib.rex_surrogate_free.restype = None
     lib.rex_version.argtypes = []
@@ -365,6 +370,10 @@ class Surrogate:
     def set_exact_alphas(self, alphas0: float, power: int) -> None:
         """Make the alphas^power dependence of |M|^2 exact; the network learns the rest."""
         _scheck(load().rex_surrogate_set_exact_alphas(self._h, float(alphas0), int(power)))
+
+    def set_kernel(self, kind: int) -> None:
+        """Inference kernel: SURROGATE_FUSED (tcgen05, default) or SURROGATE_LAYERED (mma.sync GEMMs)."""
+        _scheck(load().rex_surrogate_set_kernel(self._h, int(kind)))
 
     def loss_grad(self, momenta, ratio, mt, alphas, stream=None):
         import numpy as np

@@ -140,8 +140,10 @@ def test_training_reduces_the_loss(rex, trained):
     assert losses[-20:].mean() < 0.2 * losses[:5].mean()
 
 
-def test_inference_matches_the_oracle_forward(rex, trained):
+@pytest.mark.parametrize("kernel", ["fused", "layered"])
+def test_inference_matches_the_oracle_forward(rex, trained, kernel):
     s, _, pts, _ = trained
+    s.set_kernel(rex.SURROGATE_FUSED if kernel == "fused" else rex.SURROGATE_LAYERED)
     n = 64
     mom = ps.make_events("gg_ttxg", n, 77)
     pred = torch.empty((n, len(pts)), dtype=torch.float32, device="cuda")
@@ -157,6 +159,38 @@ def test_inference_matches_the_oracle_forward(rex, trained):
     ref = out[:, 0].reshape(n, len(pts)) + mlp.coupling_part(al, 0.118, 3)[None, :]
     scale = np.abs(ref).max() + 1e-3
     assert np.max(np.abs(pred.cpu().numpy() - ref)) < 2e-2 * scale + 2e-3
+    s.set_kernel(rex.SURROGATE_FUSED)
+
+
+@pytest.mark.parametrize("n,k", [(1, 1), (37, 5), (300, 16), (20011, 16)])
+def test_fused_and_layered_kernels_agree(rex, trained, n, k):
+    """The tcgen05 kernel against the layer-by-layer one on ragged tile counts (n k
+    not a multiple of 128), a single partial tile, and more tiles than SMs.  Both
+    round activations to BF16, so a rounding flip of an activation may differ
+    between the two FP32 summation orders; the bound is a few BF16 ulps of the
+    output's scale."""
+    s, _, _, _ = trained
+    g = np.random.default_rng(n)
+    pts = [dict(mt=float(m), wt=0.0, alphas=float(a))
+           for m, a in zip(g.uniform(170.0, 176.0, k), g.uniform(0.110, 0.126, k))]
+    mom = torch.from_numpy(ps.make_events("gg_ttxg", n, 1000 + n)).cuda()
+    w = torch.from_numpy(g.uniform(0.5, 2.0, n)).cuda()
+    outs = {}
+    for kind in (rex.SURROGATE_FUSED, rex.SURROGATE_LAYERED):
+        s.set_kernel(kind)
+        pred = torch.full((n, k), float("nan"), dtype=torch.float32, device="cuda")
+        err = torch.full((n, k), float("nan"), dtype=torch.float32, device="cuda")
+        w_out = torch.full((n, k), float("nan"), dtype=torch.float64, device="cuda")
+        s.reweight(mom, w, pts, tau=float("inf"), w_out=w_out, pred=pred, err=err)
+        outs[kind] = (pred, err, w_out)
+    s.set_kernel(rex.SURROGATE_FUSED)
+    (pf, ef, wf), (pl, el, wl) = outs[rex.SURROGATE_FUSED], outs[rex.SURROGATE_LAYERED]
+    for a in (pf, ef, wf):
+        assert torch.isfinite(a).all()
+    scale = float(pl.abs().max()) + 1e-2
+    assert float((pf - pl).abs().max()) < 2e-2 * scale
+    assert float((ef - el).abs().max()) < 2e-2 * (float(el.abs().max()) + 1e-2)
+    assert torch.allclose(wf, w[:, None] * torch.exp(pf.double()), rtol=1e-12, atol=0)
 
 
 def test_fallback_extremes(rex, trained):
@@ -175,10 +209,12 @@ def test_fallback_extremes(rex, trained):
 
 
 def test_what_the_surrogate_gains_over_the_exact_path(rex, trained):
-    """Accuracy and speed of surrogate-with-fallback against the exact mixed kernel on
-    the same events and points.  On B300 the 4 x 256 network costs ~4e5 flops per
-    (event, point) against ~1e4 for the exact g g -> t t~ g amplitudes, so no speed gain is
-    expected; the test records both and checks the accuracy bookkeeping."""
+    """What the trained network buys against the method without it, on the same
+    events and points: the network alone (fused tcgen05 kernel) must beat the exact
+    FP64 kernel, and the fallback bookkeeping must hold (flagged events exact).
+    The exact mixed-precision kernel is timed beside them for the record: on B300
+    it stays faster than the 4 x 256 network (about 4e5 tensor flops per pair
+    against about 1e4 FP32 flops for the exact g g -> t t~ g amplitudes)."""
     s, exact, pts, _ = trained
     n = 1 << 15
     mom = torch.from_numpy(ps.make_events("gg_ttxg", n, 99)).cuda()
@@ -205,9 +241,11 @@ def test_what_the_surrogate_gains_over_the_exact_path(rex, trained):
         torch.cuda.synchronize()
         return (time.perf_counter() - t0) / 3
 
-    t_sur = clock(lambda: s.reweight(mom, w, pts, tau=float("inf"), w_out=out))
+    t_net = clock(lambda: s.reweight(mom, w, pts, tau=float("inf"), w_out=out))
+    t_fp64 = clock(lambda: exact.reweight(mom, w, pts, w_out=out))
+    t_fb = clock(lambda: s.reweight(mom, w, pts, tau=tau, exact=exact, w_out=out))
     t_mix = clock(lambda: mixed.reweight(mom, w, pts))
-    print(f"\nsurrogate: {t_sur * 1e3:.2f} ms, exact mixed: {t_mix * 1e3:.2f} ms, "
-          f"fallback {nfb}/{n} events, max rel err {float(rel.max()):.3e}, "
-          f"median {float(rel.median()):.3e}")
-    assert t_sur > 0 and t_mix > 0
+    print(f"\nnetwork only: {t_net * 1e3:.2f} ms, with fallback (tau {tau}): {t_fb * 1e3:.2f} ms, "
+          f"exact FP64: {t_fp64 * 1e3:.2f} ms, exact mixed: {t_mix * 1e3:.2f} ms; "
+          f"fallback {nfb}/{n} events, max rel err {float(rel.max()):.3e}, median {float(rel.median()):.3e}")
+    assert t_net < t_fp64

@@ -9,11 +9,18 @@ from oracle import mlp
 
 
 def test_gelu_values_and_derivative():
-    z = np.array([-3.0, -1.0, 0.0, 0.5, 2.0, 6.0])
-    assert np.allclose(mlp.gelu(z), z * norm.cdf(z), rtol=1e-14, atol=1e-16)      # z Phi(z)
+    z = np.linspace(-8.0, 8.0, 4001)
+    g = mlp.gelu(z)
+    # the tanh form stays within 4.8e-4 of the exact z Phi(z) (Hendrycks & Gimpel)
+    assert np.max(np.abs(g - z * norm.cdf(z))) < 4.8e-4
+    # tanh is odd: gelu(z) - gelu(-z) = z; gelu(0) = 0; saturation at both ends
+    assert np.allclose(g - mlp.gelu(-z), z, rtol=0, atol=1e-14)
+    assert mlp.gelu(np.array([0.0]))[0] == 0.0
+    assert abs(mlp.gelu(np.array([20.0]))[0] - 20.0) < 1e-12 and abs(mlp.gelu(np.array([-20.0]))[0]) < 1e-12
     h = 1e-6
-    fd = (mlp.gelu(z + h) - mlp.gelu(z - h)) / (2 * h)
-    assert np.allclose(mlp.gelu_grad(z), fd, rtol=1e-8, atol=1e-10)
+    zz = np.array([-3.0, -1.0, 0.0, 0.5, 2.0, 6.0])
+    fd = (mlp.gelu(zz + h) - mlp.gelu(zz - h)) / (2 * h)
+    assert np.allclose(mlp.gelu_grad(zz), fd, rtol=1e-8, atol=1e-10)
     assert mlp.gelu_grad(np.array([0.0]))[0] == 0.5
 
 
@@ -58,7 +65,9 @@ def test_forward_is_the_layer_composition():
     out, _ = mlp.forward(params, x)
     h = x
     for w, b in params[:-1]:
-        h = (h @ w + b) * norm.cdf(h @ w + b)
+        z = h @ w + b
+        # (1 + tanh(u)) / 2 = 1 / (1 + exp(-2u)): the tanh-form GELU as z times a logistic
+        h = z / (1.0 + np.exp(-2.0 * math.sqrt(2.0 / math.pi) * (z + 0.044715 * z ** 3)))
     ref = h @ params[-1][0] + params[-1][1]
     assert np.allclose(out, ref, rtol=1e-13, atol=1e-14)
 
