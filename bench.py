@@ -40,7 +40,7 @@ NEV = 1 << 20
 ORIGINAL = dict(mt=173.0, wt=0.0, alphas=0.118)
 SEED = 3
 # relative error of a new weight vs the FP64 oracle, per mode (tests/test_gpu_parity.py)
-STATED_ERROR = {"fp64": 1e-12, "mixed": 2e-3}
+STATED_ERROR = {"fp64": 1e-12, "mixed": 1e-3}
 
 # Peaks for an ALU-bound kernel, derived from unit counts and the maximum SM clock
 # (148 SMs, 2032 MHz): FP32 = 148 x 128 lanes x 2 flop x 2.032 GHz.  The FP64 figure
@@ -50,14 +50,24 @@ SM_MAX_MHZ = 2032.0
 FP32_PEAK = SM_COUNT * 128 * 2 * SM_MAX_MHZ * 1e6
 FP64_FMA_PER_SM_CLK = 2         # rex_probe_fma: 1.18 TFLOP/s at 2032 MHz on 148 SMs -> 1.96
 
+def _measured_peaks() -> dict:
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+PEAKS = _measured_peaks()
+
 # DRAM traffic per launch from one ncu capture (dram__bytes_read.sum +
 # dram__bytes_write.sum) of the dominant kernel, scaled to the full launch;
 # only reported while the kernel sources still hash to the captured version.
 TRAFFIC = {
     # ncu --set full of profile_case at 2^19 events (FP64, scaled x2 by events) and
     # 2^20 events (mixed); summaries of both captures are under profiles/
-    ("gg_ttxg", "fp64"): {"bytes_per_launch": 2 * (90.025216e6 + 35.550976e6), "source_hash": "01153260b7a38beb"},
-    ("gg_ttxg", "mixed"): {"bytes_per_launch": 176.805376e6 + 100.272128e6, "source_hash": "01153260b7a38beb"},
+    ("gg_ttxg", "fp64"): {"bytes_per_launch": 2 * (90.578688e6 + 35.637248e6), "source_hash": "aa45a6468ed07516"},
+    ("gg_ttxg", "mixed"): {"bytes_per_launch": 176.366336e6 + 100.289536e6, "source_hash": "aa45a6468ed07516"},
 }
 
 
@@ -276,10 +286,12 @@ def run_multi_leg(dev, stream, steps, world, barrier, max_over_ranks):
             "sequential_ms_per_step": ms_seq, "steps": steps}
 
 
-def run_surrogate_leg(dev, stream, world, max_over_ranks, steps=2000, tau=0.01):
+def run_surrogate_leg(dev, stream, world, max_over_ranks, tau=0.02):
     """Surrogate with exact fallback for g g -> t t~ g: train on 8M exact FP64 samples
-    (125k events x 64 random points), then reweight 4M events x 64 grid points; error
-    against the FP64 kernel (equal to the oracle to 1e-12 by the parity tests)."""
+    (125k events x 64 random points; 8000 Adam steps of 8192 with the learning rate
+    stepped down 1e-3 -> 3e-4 -> 1e-4; the alphas^3 part of the ratio exact), then
+    reweight 4M events x 64 grid points; error against the FP64 kernel (equal to the
+    oracle to 1e-12 by the parity tests)."""
     import torch
     from paper_2510_05100_b300 import rex
 
@@ -292,9 +304,12 @@ def run_surrogate_leg(dev, stream, world, max_over_ranks, steps=2000, tau=0.01):
     mom_tr = torch.from_numpy(ps.make_events(PROC, ntr, 51)).to(dev)
     ratio = exact64.reweight(mom_tr, torch.ones(ntr, dtype=torch.float64, device=dev), train_pts, stream=stream)
     sur = rex.Surrogate(5)
+    sur.set_exact_alphas(ORIGINAL["alphas"], 3)
+    phases = [(4000, 1e-3), (2000, 3e-4), (2000, 1e-4)]
     torch.cuda.synchronize(dev)
     t0 = time.perf_counter()
-    losses = sur.train(mom_tr, ratio, train_pts, steps=steps, batch=8192, lr=1e-3, seed=7, stream=stream)
+    losses = np.concatenate([sur.train(mom_tr, ratio, train_pts, steps=st, batch=8192, lr=lr, seed=7, stream=stream)
+                             for st, lr in phases])
     t_train = time.perf_counter() - t0
     del mom_tr, ratio
 
@@ -314,24 +329,40 @@ def run_surrogate_leg(dev, stream, world, max_over_ranks, steps=2000, tau=0.01):
 
     sur.reweight(mom[:8192], w[:8192], pts, tau=tau, exact=exact64, w_out=out[:8192], stream=stream)   # warm-up
     t_sur, nfb = timed(lambda: sur.reweight(mom, w, pts, tau=tau, exact=exact64, w_out=out, err=err, stream=stream))
+    # the network alone (fused tcgen05 kernel, no fallback), timed with CUDA events on the stream
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    tmp = torch.empty_like(out)
+    e0.record(stream)
+    sur.reweight(mom, w, pts, w_out=tmp, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    t_net = e0.elapsed_time(e1) * 1e-3
     ref = torch.empty_like(out)
     t_fp64, _ = timed(lambda: exact64.reweight(mom, w, pts, w_out=ref, stream=stream))
     mixed = rex.Process(PROC, rex.MIXED)
     mixed.set_params(ORIGINAL)
-    tmp = torch.empty_like(out)
     mixed.reweight(mom[:8192], w[:8192], pts, w_out=tmp[:8192], stream=stream)
     t_mix, _ = timed(lambda: mixed.reweight(mom, w, pts, w_out=tmp, stream=stream))
-    rel = (out / ref - 1.0).abs()
+    dlog = (out / ref).log().abs()
     flagged = (err > tau).any(dim=1)
-    kept = rel[~flagged]
-    sample = rel.flatten()[:: max(1, rel.numel() // 4_000_000)]
+    kept = dlog[~flagged]
+    sample = dlog.flatten()[:: max(1, dlog.numel() // 4_000_000)]
     units = nin * len(pts) * world
-    res = {"workload": f"{PROC}: train 8M exact samples (125k events x 64 random points, {steps} Adam steps "
-                       f"of 8192), reweight {nin} events x 64 grid points, fallback tau={tau}",
+    net_flops = nin * len(pts) * 2 * (32 * 256 + 3 * 256 * 256 + 256 * 2)
+    peak = PEAKS.get("bf16_tflops")
+    res = {"workload": f"{PROC}: train 8M exact samples (125k events x 64 random points, "
+                       f"{sum(p[0] for p in phases)} Adam steps of 8192), reweight {nin} events x 64 grid points, "
+                       f"fallback of every event with a predicted error above tau={tau}",
            "value": units / t_sur, "unit": UNIT, "fallback_rate": nfb / nin,
-           "rel_err_vs_fp64": {"max": float(rel.max()), "p99": float(torch.quantile(sample.float(), 0.99)),
-                               "median": float(sample.median())},
-           "escape_rate_1e-2": float((kept > 1e-2).float().mean()) if kept.numel() else 0.0,
+           "abs_err_log_weight": {"max": float(dlog.max()), "p99": float(torch.quantile(sample.float(), 0.99)),
+                                  "p999": float(torch.quantile(sample.float(), 0.999)),
+                                  "median": float(sample.median())},
+           "kept_pairs_above_1e-2": float((kept > 1e-2).float().mean()) if kept.numel() else 0.0,
+           "kept_pairs_above_3e-2": float((kept > 3e-2).float().mean()) if kept.numel() else 0.0,
+           "network_only": {"value": units / t_net, "unit": UNIT, "kernel": "fused tcgen05 (BF16, FP32 accumulation)",
+                            "tensor_tflops": net_flops / t_net / 1e12,
+                            "frac_of_bf16_peak": (net_flops / t_net / 1e12) / peak if peak else None,
+                            "peak_tflops": peak, "peak_source": "MEASURED_PEAKS bf16_tflops (burst, of measured)"},
            "exact_fp64_value": units / t_fp64, "exact_mixed_value": units / t_mix,
            "train_seconds": t_train, "final_loss": float(losses[-50:].mean()),
            "note": "surrogate-with-fallback vs the exact kernels on the same events and points"}
@@ -439,9 +470,19 @@ def run_ours(args, world, rank, local):
             if name == args.mode:
                 continue
             st = max(2, args.steps // 3)
-            tm, _, _ = time_mode(prec, fl, steps=st, warmup=1)
+            tm, per, _ = time_mode(prec, fl, steps=st, warmup=1)
+            # counted flops of one launch against the pipe that carries them
+            slots = (k + 1) if fl else 1 + len({p["mt"] for p in pts} - {ORIGINAL["mt"]})
+            cnt = flopmod.per_event(PROC, slots)
+            if prec == rex.FP64:
+                fpl, pk, pipe = cnt["total"] * args.nev, SM_COUNT * FP64_FMA_PER_SM_CLK * 2 * SM_MAX_MHZ * 1e6, "FP64 FMA"
+            else:
+                fpl, pk, pipe = cnt["amp"] * args.nev, FP32_PEAK, "FP32 FMA (amplitudes; FP64 invariants and sums not counted)"
+            ach = fpl / (statistics.mean(per) * 1e-3)
             extra[name] = {"value": args.nev * k * st * world / (tm * 1e-3), "unit": UNIT,
-                           "stated_rel_error": STATED_ERROR.get(name.split("_")[0])}
+                           "stated_rel_error": STATED_ERROR.get(name.split("_")[0]),
+                           "roofline": {"bound": "alu", "pipe": pipe, "achieved": ach / 1e12, "peak": pk / 1e12,
+                                        "unit": "TFLOP/s", "frac": ach / pk}}
 
     # ---- roofline of the dominant kernel (the fused gg_ttxg kernel; one launch per step)
     nmass = 1 + len({p["mt"] for p in pts} - {ORIGINAL["mt"]})

@@ -19,9 +19,12 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 FP64_TOL = 1e-12
-# max relative error of a new weight in mixed precision (FP32 amplitudes,
-# FP64 colour/helicity sums and ratio), measured over the parity samples
-MIXED_TOL = {"gg_ttx": 2e-4, "gg_ttxg": 2e-3, "gg_ttxgg": 2e-2}
+# Stated bound on the relative error of a new weight in mixed precision (FP32
+# currents and spinor chains, FP64 invariants, colour form in FP32 or on tensor
+# cores as FP16 hi+lo, FP64 helicity sum and ratio).  The largest errors seen
+# against the FP64 kernel over 2^20 (gg_ttx, gg_ttxg) and 2^16 (gg_ttxgg) events
+# are 7.4e-7, 1.4e-4 and 6.8e-5; the bounds keep a factor of 7 or more above them.
+MIXED_TOL = {"gg_ttx": 1e-5, "gg_ttxg": 1e-3, "gg_ttxgg": 1e-3}
 
 ORIG_QCD = dict(mt=173.0, wt=0.0, alphas=0.118)
 SIZES = {"ee_mumu": 300, "gg_ttx": 101, "gg_ttxg": 53, "gg_ttxgg": 19}
