@@ -193,7 +193,7 @@ def emit_process(name: str, ngluon: int) -> str:
     w(f"for (int k = l; k < {ninv}; k += nl) {{")
     w("switch (k) {", 2)
     for st, i in gidx.items():
-        w(f"case {i}: ev.fg[{i}] = R(-1.0 / ({inv_sq(sorted(st))})); break;", 3)
+        w(f"case {i}: ev.fg[{i}] = R(-1) / R({inv_sq(sorted(st))}); break;", 3)
     for st, i in sidx.items():
         w(f"case {ngs + i}: ev.q2[{i}] = {inv_sq(sorted(st) + [n])}; break;", 3)
     w("}", 2)

@@ -104,7 +104,7 @@ template <typename R>
 __device__ __forceinline__ void gg_ttx_event_phase2(gg_ttx_event<R>& ev, int l, int nl) {
   for (int k = l; k < 3; k += nl) {
     switch (k) {
-      case 0: ev.fg[0] = R(-1.0 / (ev.dd[0] + ev.dd[3] + 2.0 * ev.dd[1])); break;
+      case 0: ev.fg[0] = R(-1) / R(ev.dd[0] + ev.dd[3] + 2.0 * ev.dd[1]); break;
       case 1: ev.q2[0] = ev.dd[0] + ev.dd[5] + 2.0 * ev.dd[2]; break;
       case 2: ev.q2[1] = ev.dd[3] + ev.dd[5] + 2.0 * ev.dd[4]; break;
     }
@@ -339,10 +339,10 @@ template <typename R>
 __device__ __forceinline__ void gg_ttxg_event_phase2(gg_ttxg_event<R>& ev, int l, int nl) {
   for (int k = l; k < 10; k += nl) {
     switch (k) {
-      case 0: ev.fg[0] = R(-1.0 / (ev.dd[0] + ev.dd[4] + 2.0 * ev.dd[1])); break;
-      case 1: ev.fg[1] = R(-1.0 / (ev.dd[0] + ev.dd[7] + 2.0 * ev.dd[2])); break;
-      case 2: ev.fg[2] = R(-1.0 / (ev.dd[4] + ev.dd[7] + 2.0 * ev.dd[5])); break;
-      case 3: ev.fg[3] = R(-1.0 / (ev.dd[0] + ev.dd[4] + ev.dd[7] + 2.0 * ev.dd[1] + 2.0 * ev.dd[2] + 2.0 * ev.dd[5])); break;
+      case 0: ev.fg[0] = R(-1) / R(ev.dd[0] + ev.dd[4] + 2.0 * ev.dd[1]); break;
+      case 1: ev.fg[1] = R(-1) / R(ev.dd[0] + ev.dd[7] + 2.0 * ev.dd[2]); break;
+      case 2: ev.fg[2] = R(-1) / R(ev.dd[4] + ev.dd[7] + 2.0 * ev.dd[5]); break;
+      case 3: ev.fg[3] = R(-1) / R(ev.dd[0] + ev.dd[4] + ev.dd[7] + 2.0 * ev.dd[1] + 2.0 * ev.dd[2] + 2.0 * ev.dd[5]); break;
       case 4: ev.q2[0] = ev.dd[0] + ev.dd[9] + 2.0 * ev.dd[3]; break;
       case 5: ev.q2[1] = ev.dd[4] + ev.dd[9] + 2.0 * ev.dd[6]; break;
       case 6: ev.q2[2] = ev.dd[7] + ev.dd[9] + 2.0 * ev.dd[8]; break;
@@ -844,17 +844,17 @@ template <typename R>
 __device__ __forceinline__ void gg_ttxgg_event_phase2(gg_ttxgg_event<R>& ev, int l, int nl) {
   for (int k = l; k < 25; k += nl) {
     switch (k) {
-      case 0: ev.fg[0] = R(-1.0 / (ev.dd[0] + ev.dd[5] + 2.0 * ev.dd[1])); break;
-      case 1: ev.fg[1] = R(-1.0 / (ev.dd[0] + ev.dd[9] + 2.0 * ev.dd[2])); break;
-      case 2: ev.fg[2] = R(-1.0 / (ev.dd[0] + ev.dd[12] + 2.0 * ev.dd[3])); break;
-      case 3: ev.fg[3] = R(-1.0 / (ev.dd[5] + ev.dd[9] + 2.0 * ev.dd[6])); break;
-      case 4: ev.fg[4] = R(-1.0 / (ev.dd[5] + ev.dd[12] + 2.0 * ev.dd[7])); break;
-      case 5: ev.fg[5] = R(-1.0 / (ev.dd[9] + ev.dd[12] + 2.0 * ev.dd[10])); break;
-      case 6: ev.fg[6] = R(-1.0 / (ev.dd[0] + ev.dd[5] + ev.dd[9] + 2.0 * ev.dd[1] + 2.0 * ev.dd[2] + 2.0 * ev.dd[6])); break;
-      case 7: ev.fg[7] = R(-1.0 / (ev.dd[0] + ev.dd[5] + ev.dd[12] + 2.0 * ev.dd[1] + 2.0 * ev.dd[3] + 2.0 * ev.dd[7])); break;
-      case 8: ev.fg[8] = R(-1.0 / (ev.dd[0] + ev.dd[9] + ev.dd[12] + 2.0 * ev.dd[2] + 2.0 * ev.dd[3] + 2.0 * ev.dd[10])); break;
-      case 9: ev.fg[9] = R(-1.0 / (ev.dd[5] + ev.dd[9] + ev.dd[12] + 2.0 * ev.dd[6] + 2.0 * ev.dd[7] + 2.0 * ev.dd[10])); break;
-      case 10: ev.fg[10] = R(-1.0 / (ev.dd[0] + ev.dd[5] + ev.dd[9] + ev.dd[12] + 2.0 * ev.dd[1] + 2.0 * ev.dd[2] + 2.0 * ev.dd[3] + 2.0 * ev.dd[6] + 2.0 * ev.dd[7] + 2.0 * ev.dd[10])); break;
+      case 0: ev.fg[0] = R(-1) / R(ev.dd[0] + ev.dd[5] + 2.0 * ev.dd[1]); break;
+      case 1: ev.fg[1] = R(-1) / R(ev.dd[0] + ev.dd[9] + 2.0 * ev.dd[2]); break;
+      case 2: ev.fg[2] = R(-1) / R(ev.dd[0] + ev.dd[12] + 2.0 * ev.dd[3]); break;
+      case 3: ev.fg[3] = R(-1) / R(ev.dd[5] + ev.dd[9] + 2.0 * ev.dd[6]); break;
+      case 4: ev.fg[4] = R(-1) / R(ev.dd[5] + ev.dd[12] + 2.0 * ev.dd[7]); break;
+      case 5: ev.fg[5] = R(-1) / R(ev.dd[9] + ev.dd[12] + 2.0 * ev.dd[10]); break;
+      case 6: ev.fg[6] = R(-1) / R(ev.dd[0] + ev.dd[5] + ev.dd[9] + 2.0 * ev.dd[1] + 2.0 * ev.dd[2] + 2.0 * ev.dd[6]); break;
+      case 7: ev.fg[7] = R(-1) / R(ev.dd[0] + ev.dd[5] + ev.dd[12] + 2.0 * ev.dd[1] + 2.0 * ev.dd[3] + 2.0 * ev.dd[7]); break;
+      case 8: ev.fg[8] = R(-1) / R(ev.dd[0] + ev.dd[9] + ev.dd[12] + 2.0 * ev.dd[2] + 2.0 * ev.dd[3] + 2.0 * ev.dd[10]); break;
+      case 9: ev.fg[9] = R(-1) / R(ev.dd[5] + ev.dd[9] + ev.dd[12] + 2.0 * ev.dd[6] + 2.0 * ev.dd[7] + 2.0 * ev.dd[10]); break;
+      case 10: ev.fg[10] = R(-1) / R(ev.dd[0] + ev.dd[5] + ev.dd[9] + ev.dd[12] + 2.0 * ev.dd[1] + 2.0 * ev.dd[2] + 2.0 * ev.dd[3] + 2.0 * ev.dd[6] + 2.0 * ev.dd[7] + 2.0 * ev.dd[10]); break;
       case 11: ev.q2[0] = ev.dd[0] + ev.dd[14] + 2.0 * ev.dd[4]; break;
       case 12: ev.q2[1] = ev.dd[5] + ev.dd[14] + 2.0 * ev.dd[8]; break;
       case 13: ev.q2[2] = ev.dd[9] + ev.dd[14] + 2.0 * ev.dd[11]; break;

@@ -8,8 +8,9 @@
 //   a5  colour-flow amplitudes A(s) (jamps)
 //   a6  colour sum  sum_{s,s'} conj(A_s) C_ss' A_s'  with the exact integer matrix
 //   a7  helicity sum: top/antitop helicities inside the thread, gluon
-//       polarisations across the NGHEL lanes of the event (warp shuffles), FP64
-//   a8  ratio epilogue  w_out = w_in * |M_j|^2 / |M_0|^2  (0 if |M_0|^2 == 0)
+//       polarisations across the NGHEL lanes of the event (warp shuffles); FP64
+//       in the exact mode, FP32 in the mixed mode (non-negative terms)
+//   a8  ratio epilogue  w_out = w_in * |M_j|^2 / |M_0|^2  (0 if |M_0|^2 == 0), FP64
 //
 // Thread mapping (kernel variants, chosen per process and precision):
 //   SPLIT = 0: NGHEL = 2^n lanes per event, one gluon polarisation configuration
@@ -103,6 +104,7 @@ struct QcdTile {
 
   struct Smem {
     double me2s[EPB][MAX_MASS + 1];
+    double inv0[EPB];   // mixed mode: 1 / |M_0|^2 per event (0 if |M_0|^2 == 0)
     typename P::template event<R> evs[EPB];
     typename P::template mass<R> mss[EPB];
     alignas(16) __half tc[TC ? QCD_BLOCK / 32 : 1][TC ? ColourTc<NF>::WARP_HALVES : 1];
@@ -146,20 +148,22 @@ struct QcdTile {
     for (int m = 0; m < lp.nmass; ++m) {
       P::template mass_setup<R, WIDTH>(evd, lp.mass[m], lp.width[m], sm.mss[el], lane_ev, NH);
       __syncthreads();
-      double s = 0.0;
+      // a7: the helicity sum adds non-negative terms (no cancellation): FP64 in the
+      // exact mode, FP32 in the mixed mode (relative error <= 64 * 2^-24)
+      R s = R(0);
       if constexpr (TC) {
         // every lane takes part in the warp-wide MMA form; lane 8t of the warp
         // receives the colour sum of m16 tile t (part of its event), the others 0
         __half* tcs = sm.tc[tid >> 5];
         auto form = [&](const cx<float> (&A)[2][NF]) { return ColourTc<NF>::template form<NH>(A, tcs); };
-        s = P::template quark_line<R, double, WIDTH>(evd, sm.mss[el], J, hb_lo, hb_hi, form);
-        if (!valid) s = 0.0;
+        s = P::template quark_line<R, R, WIDTH>(evd, sm.mss[el], J, hb_lo, hb_hi, form);
+        if (!valid) s = R(0);
       } else {
-        if (valid) s = P::template quark_line<R, double, WIDTH>(evd, sm.mss[el], J, hb_lo, hb_hi);
+        if (valid) s = P::template quark_line<R, R, WIDTH>(evd, sm.mss[el], J, hb_lo, hb_hi);
       }
 #pragma unroll
       for (int off = NH / 2; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
-      if (leader) sm.me2s[el][m] = s;
+      if (leader) sm.me2s[el][m] = double(s);
       __syncthreads();
     }
 
@@ -167,13 +171,31 @@ struct QcdTile {
     const int nblk = (int)((nev - ev0) < EPB ? (nev - ev0) : EPB);
     if (lp.mode == OUT_RATIO) {
       const int k = lp.k;
-      for (int idx = tid; idx < nblk * k; idx += QCD_BLOCK) {
-        const int e = idx / k;
-        const int j = idx - e * k;
-        const double m0 = sm.me2s[e][0] * lp.factor0;
-        const double mj = sm.me2s[e][lp.slot[j]] * lp.factor[j];
-        const double w = w_in[ev0 + e];
-        out[(ev0 + e) * lp.out_stride + j] = (m0 == 0.0) ? 0.0 : w * (mj / m0);
+      if constexpr (std::is_same<R, double>::value) {
+        for (int idx = tid; idx < nblk * k; idx += QCD_BLOCK) {
+          const int e = idx / k;
+          const int j = idx - e * k;
+          const double m0 = sm.me2s[e][0] * lp.factor0;
+          const double mj = sm.me2s[e][lp.slot[j]] * lp.factor[j];
+          const double w = w_in[ev0 + e];
+          out[(ev0 + e) * lp.out_stride + j] = (m0 == 0.0) ? 0.0 : w * (mj / m0);
+        }
+      } else {
+        // mixed mode: one FP64 reciprocal per event instead of a division per point;
+        // a point whose |M|^2 equals the original's keeps its weight exactly
+        for (int e = tid; e < nblk; e += QCD_BLOCK) {
+          const double m0 = sm.me2s[e][0] * lp.factor0;
+          sm.inv0[e] = m0 == 0.0 ? 0.0 : 1.0 / m0;
+        }
+        __syncthreads();
+        for (int idx = tid; idx < nblk * k; idx += QCD_BLOCK) {
+          const int e = idx / k;
+          const int j = idx - e * k;
+          const double m0 = sm.me2s[e][0] * lp.factor0;
+          const double mj = sm.me2s[e][lp.slot[j]] * lp.factor[j];
+          const double w = w_in[ev0 + e];
+          out[(ev0 + e) * lp.out_stride + j] = (m0 == 0.0) ? 0.0 : (mj == m0 ? w : w * (mj * sm.inv0[e]));
+        }
       }
     } else {
       for (int e = tid; e < nblk; e += QCD_BLOCK) out[ev0 + e] = sm.me2s[e][0] * lp.factor0;
