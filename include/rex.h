@@ -267,7 +267,7 @@ int rex_surrogate_train(rex_surrogate *s, const double *momenta, const double *r
 /* Surrogate reweighting of nev events to k points (k <= 4096):
  * pred, err (device [nev][k] floats, may be NULL) receive the predicted log
  * ratio and error estimate; w_out (device [nev][k], may be NULL) receives
- * w_in * exp(pred), and then every event with some err > tau (or NaN) is
+ * w_in * exp(pred) (exp in FP32), and then every event with some err > tau (or NaN) is
  * recomputed exactly with the handle exact (rex_reweight on those events).
  * n_fallback (host, may be NULL) receives the number of such events.  With
  * w_out set the call synchronises stream (to size the fallback). */

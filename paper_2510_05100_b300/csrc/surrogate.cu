@@ -294,7 +294,7 @@ __global__ void __launch_bounds__(256) head_infer_kernel(const __nv_bfloat16* __
     e += P[OFF_B5 + 1];
     if (pred) pred[ev_base * k + pr] = y;
     if (err) err[ev_base * k + pr] = e;
-    if (w_out) w_out[ev_base * k + pr] = w_in[ev] * exp((double)y);
+    if (w_out) w_out[ev_base * k + pr] = w_in[ev] * (double)expf(y);
     if (flag && !(e <= tau)) flag[ev] = 1;   // NaN errors fall back too
   }
 }
@@ -586,6 +586,7 @@ int infer_fused(rex_surrogate* s, const double* momenta, const double* w_in, int
                 int k, float tau, double* w_out, float* pred, float* err, cudaStream_t st) {
   const size_t img1 = (size_t)FW * FK1, img = (size_t)FW * FW;
   cudaError_t e = s->PK.ensure((img1 + 3 * img) * 2);
+  if (e == cudaSuccess) e = s->X.ensure((size_t)nev * NINP * 2);
   if (e == cudaSuccess) e = s->PTAB.ensure((size_t)k * sizeof(float4));
   if (e == cudaSuccess) e = s->STATUS.ensure(4);
   if (e == cudaSuccess) e = s->pmt.ensure((size_t)k * 8);
@@ -609,6 +610,8 @@ int infer_fused(rex_surrogate* s, const double* momenta, const double* w_in, int
                                                                       pk + img1 + (l - 1) * img);
   point_table_kernel<<<(k + 127) / 128, 128, 0, st>>>(s->pmt.as<double>(), s->pas.as<double>(), k, s->as0, s->apow,
                                                       s->PTAB.as<float4>());
+  // per-event features (momenta in TeV, BF16), read by every pair of the event
+  event_features_kernel<<<(unsigned)((nev + 255) / 256), 256, 0, st>>>(momenta, nev, s->X.as<__nv_bfloat16>());
   if ((e = cudaGetLastError()) != cudaSuccess) return scuda(e, "weight packing");
   int dev = 0, sms = 0;
   if ((e = cudaGetDevice(&dev)) != cudaSuccess ||
@@ -617,7 +620,7 @@ int infer_fused(rex_surrogate* s, const double* momenta, const double* w_in, int
                                 (int)sizeof(FusedSmem))) != cudaSuccess)
     return scuda(e, "fused kernel set-up");
   FusedArgs fa{};
-  fa.mom = momenta;
+  fa.xev = s->X.as<__nv_bfloat16>();
   fa.w_in = w_in;
   fa.nev = nev;
   fa.k = k;

@@ -190,7 +190,7 @@ def test_fused_and_layered_kernels_agree(rex, trained, n, k):
     scale = float(pl.abs().max()) + 1e-2
     assert float((pf - pl).abs().max()) < 2e-2 * scale
     assert float((ef - el).abs().max()) < 2e-2 * (float(el.abs().max()) + 1e-2)
-    assert torch.allclose(wf, w[:, None] * torch.exp(pf.double()), rtol=1e-12, atol=0)
+    assert torch.allclose(wf, w[:, None] * torch.exp(pf.double()), rtol=1e-6, atol=0)   # exp in FP32
 
 
 def test_fallback_extremes(rex, trained):
@@ -205,7 +205,7 @@ def test_fallback_extremes(rex, trained):
     pred = torch.empty((n, len(pts)), dtype=torch.float32, device="cuda")
     nfb = s.reweight(mom, w, pts, tau=float("inf"), exact=exact, w_out=out, pred=pred)
     assert nfb == 0
-    assert torch.allclose(out, w[:, None] * torch.exp(pred.double()), rtol=1e-12, atol=0)
+    assert torch.allclose(out, w[:, None] * torch.exp(pred.double()), rtol=1e-6, atol=0)   # exp in FP32
 
 
 def test_what_the_surrogate_gains_over_the_exact_path(rex, trained):
