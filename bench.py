@@ -108,6 +108,17 @@ def oracle_throughput(mom_all: np.ndarray, pts, ntasks: int, chunk: int, cores: 
     return done * len(pts) / dt, done, dt
 
 
+def _cpu_model() -> str:
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
 def _start_pool(cores):
     import multiprocessing as mp
     os.environ.setdefault("OMP_NUM_THREADS", "1")
@@ -170,7 +181,7 @@ class ClockSampler:
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--mode", choices=["fp64", "mixed"], default="fp64")
@@ -179,6 +190,7 @@ def main():
     ap.add_argument("--no-extra-modes", action="store_true")
     ap.add_argument("--no-multi", action="store_true")
     ap.add_argument("--no-surrogate", action="store_true")
+    ap.add_argument("--no-xsec", action="store_true")
     args = ap.parse_args()
     world, rank, local = rdist.env()
     if args.impl == "reference":
@@ -509,6 +521,40 @@ def run_ours(args, world, rank, local):
                 "probe_fp64_tflops": probe64 / 1e12, "probe_fp32_tflops": probe32 / 1e12,
                 "algorithmic_bytes_per_launch": (args.nev * 5 * 4 * 8 + args.nev * 8 + args.nev * k * 8)}
 
+    # ---- reweighted cross sections (Sec. 3.1.2) on the headline's output
+    xsec = None
+    if not args.no_xsec:
+        proc = rex.Process(PROC, rex.FP64)
+        proc.set_params(ORIGINAL)
+        w_out = torch.empty((args.nev, k), dtype=torch.float64, device=dev)
+        proc.reweight(mom, w_in, pts, w_out=w_out, stream=stream)
+        proc.close()
+        xs = rex.XSec(k)
+        for _ in range(3):
+            xs.accumulate(w_in, w_out, stream=stream)
+        xs.reset(stream=stream)
+        reps = 20
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize(dev)
+        e0.record(stream)
+        for _ in range(reps):
+            xs.accumulate(w_in, w_out, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        t = e0.elapsed_time(e1) * 1e-3 / reps
+        sig, dsig, fb = xs.result(1.0, 0.01, stream=stream)
+        xs.close()
+        del w_out
+        flops = args.nev * k * 7                         # d, S, SS (fma), s1, r (fma) per weight
+        nbytes = args.nev * 8 + args.nev * k * 8         # w_in + w_out
+        p64 = SM_COUNT * FP64_FMA_PER_SM_CLK * 2 * SM_MAX_MHZ * 1e6
+        xsec = {"workload": f"sigma', dsigma' of {k} points over the headline's {args.nev} events",
+                "value": args.nev * k / t, "unit": UNIT, "ms_per_call": t * 1e3, "fallback_points": int(fb.sum()),
+                "roofline": {"bound": "alu", "pipe": "FP64", "achieved": flops / t / 1e12, "peak": p64 / 1e12,
+                             "unit": "TFLOP/s", "frac": flops / t / p64,
+                             "hbm_gbs": nbytes / t / 1e9, "hbm_frac": nbytes / t / 1e9 / PEAKS["hbm_gbs"]
+                             if PEAKS.get("hbm_gbs") else None}}
+
     multi = None if args.no_multi else run_multi_leg(dev, stream, max(3, args.steps // 2), world, barrier,
                                                      max_over_ranks)
     surrogate = None if args.no_surrogate else run_surrogate_leg(dev, stream, world, max_over_ranks)
@@ -519,8 +565,14 @@ def run_ours(args, world, rank, local):
         v, n, dt = oracle_throughput(sample_ev, pts, 4 * cores, 256, cores, cpu_pool)
         cpu_pool.close()
         cpu_pool.join()
+        # the same oracle on one core, in this process
+        t0 = time.perf_counter()
+        n1 = sum(_oracle_chunk((mom_np[i * 256:(i + 1) * 256].copy(), pts)) for i in range(2))
+        dt1 = time.perf_counter() - t0
         cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
-               "sample": f"{n} events of the workload x {k} points ({4 * cores} chunks of 256), {dt:.1f} s"}
+               "sample": f"{n} events of the workload x {k} points ({4 * cores} chunks of 256), {dt:.1f} s",
+               "one_core": {"value": n1 * k / dt1, "unit": UNIT, "sample": f"{n1} events x {k} points, {dt1:.1f} s"},
+               "cpu_model": _cpu_model()}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -531,7 +583,7 @@ def run_ours(args, world, rank, local):
                 "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                         "entry_point": "rex_reweight_host (pinned host buffers)"},
                 "gpu_launches": args.steps, "roofline": roofline, "cpu_baseline": cpu, "modes": extra,
-                "multi": multi, "surrogate": surrogate}
+                "multi": multi, "surrogate": surrogate, "xsec": xsec}
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist

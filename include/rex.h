@@ -219,6 +219,43 @@ int rex_reweight_multi_noalloc(const rex_batch *batches, int nbatch,
                                const rex_params *param_sets, int k,
                                int precision, void *stream);
 
+/* ---- Reweighted cross sections (Sec. 3.1.2) --------------------------------
+ * For a sample with cross section sigma, error dsigma, original weights w_i and
+ * reweighted weights w'_ij (i = events, j = points):
+ *   sigma'_j  = C sum_i w'_ij,  C = sigma / sum_i w_i (the sample's normalisation);
+ *   dsigma'_j = dsigma * mean_i(w'_ij / w_i) + sigma * std_i(w'_ij),
+ * with std the population standard deviation and the mean of w'/w taken over
+ * the events with w_i != 0.  When dsigma'_j is infinite, NaN or non-positive it
+ * is replaced by dsigma * max(sigma'_j / sigma, sigma / sigma'_j) and the
+ * point's fallback flag is set.
+ * The statistics accumulate in FP64 over any number of calls (a sample spread
+ * over several processes or batches) in a fixed order: results are bitwise
+ * reproducible.  Calls on one handle must be issued on one stream (or
+ * otherwise serialised).  Errors: REX_EINVAL, REX_ENOMEM, REX_ECUDA; the message
+ * is in rex_xsec_last_error(). */
+typedef struct rex_xsec rex_xsec; /* opaque, library-owned */
+
+const char *rex_xsec_last_error(void);
+
+/* Accumulator for k points (1 <= k <= 2^20), zeroed; device memory owned by the handle. */
+int rex_xsec_create(int k, rex_xsec **out);
+
+/* Zero the accumulator (enqueued on stream). */
+int rex_xsec_reset(rex_xsec *x, void *stream);
+
+/* Add nev events: w_in (device [nev]) and w_out (device [nev][k], e.g. the
+ * rex_reweight output).  Enqueued on stream; nev = 0 is a no-op.  Growing the
+ * internal partials buffer (a call with more events than any before)
+ * synchronises stream. */
+int rex_xsec_accumulate(rex_xsec *x, const double *w_in, const double *w_out, int64_t nev, void *stream);
+
+/* sigma'_j, dsigma'_j (host [k]) and fallback flags (host [k], may be NULL) of
+ * everything accumulated so far; synchronises stream. */
+int rex_xsec_result(rex_xsec *x, double sigma, double dsigma, double *sigma_out, double *dsigma_out,
+                    int *fallback, void *stream);
+
+void rex_xsec_free(rex_xsec *x);
+
 /* ---- Learned surrogate of the weight ratio ---------------------------------
  * The paper has no learned component.  An MLP (22 inputs -> 4 hidden layers of
  * 256 with GELU in its tanh form, z (1 + tanh(sqrt(2/pi) (z + 0.044715 z^3))) / 2

@@ -1,0 +1,277 @@
+// Reweighted cross sections and their errors on the GPU (sm_103a).
+//
+// Sec. 3.1.2:  sigma'_j = C sum_i w'_ij  (C = sigma / sum_i w_i),
+//              dsigma'_j = dsigma * mean_i(w'_ij / w_i) + sigma * std_i(w'_ij),
+// falling back to dsigma * max(sigma'_j / sigma, sigma / sigma'_j) when the
+// error is infinite, NaN or non-positive.  std is the population standard
+// deviation; the mean of w'/w runs over events with w_i != 0.
+//
+// The statistics are accumulated over any number of calls (a sample split over
+// several processes or batches) in FP64 and in a fixed order, so that the result
+// does not depend on how the GPU schedules the blocks:
+//   pass 1  block b of the grid reduces events [b E, (b+1) E): each thread keeps
+//           shifted sums (first value K: S = sum (x - K), SS = sum (x - K)^2) of
+//           its events for one point, turned into (n, mean, M2); the 8 threads of
+//           a point merge in a fixed order (Chan, Golub & LeVeque 1979);
+//   pass 2  one thread per point merges the blocks' partials in block order and
+//           then into the accumulator;
+//   result  sigma', dsigma' and the fallback flag per point.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "../../include/rex.h"
+
+namespace {
+
+constexpr int XS_TJ = 32;          // points per block (x)
+constexpr int XS_TE = 8;           // event rows per block (y)
+constexpr int XS_EB = 2048;        // events per block
+
+struct Moments {                   // count, mean, sum of squared deviations, plain sum, ratio sum
+  double n, mean, m2, s1, r;
+};
+
+__host__ __device__ inline Moments merge(const Moments& a, const Moments& b) {
+  if (b.n == 0.0) return a;
+  if (a.n == 0.0) return b;
+  Moments c;
+  c.n = a.n + b.n;
+  const double d = b.mean - a.mean;
+  c.mean = a.mean + d * (b.n / c.n);
+  c.m2 = a.m2 + b.m2 + d * d * (a.n * b.n / c.n);
+  c.s1 = a.s1 + b.s1;
+  c.r = a.r + b.r;
+  return c;
+}
+
+struct Scalars {                   // per block / accumulator: events, events with w != 0, sum of w
+  double n, nr, sw;
+};
+
+thread_local std::string g_xerr;
+int xfail(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_xerr = buf;
+  return code;
+}
+
+// pass 1: partial moments of events [bx E, bx E + E) for points 32 by + tj
+__global__ void __launch_bounds__(XS_TJ* XS_TE) xsec_partials_kernel(const double* __restrict__ w_in,
+                                                                     const double* __restrict__ w_out, int64_t nev,
+                                                                     int k, Moments* __restrict__ part,
+                                                                     Scalars* __restrict__ psc) {
+  __shared__ Moments sm[XS_TE][XS_TJ];
+  __shared__ Scalars ssc[XS_TE];
+  const int tj = threadIdx.x, te = threadIdx.y;
+  const int j = blockIdx.y * XS_TJ + tj;
+  const int64_t e_beg = (int64_t)blockIdx.x * XS_EB;
+  const int64_t e_end = (e_beg + XS_EB < nev) ? e_beg + XS_EB : nev;
+  double cnt = 0.0, K = 0.0, S = 0.0, SS = 0.0, s1 = 0.0, r = 0.0;
+  double nr = 0.0, sw = 0.0;
+  for (int64_t e = e_beg + te; e < e_end; e += XS_TE) {
+    const double w = w_in[e];
+    // one reciprocal per event and warp, shared by its 32 points
+    double inv = 0.0;
+    if (tj == 0 && w != 0.0) inv = 1.0 / w;
+    inv = __shfl_sync(0xffffffffu, inv, 0);
+    if (j < k) {
+      const double x = w_out[e * k + j];
+      if (cnt == 0.0) K = x;
+      const double d = x - K;
+      S += d;
+      SS = fma(d, d, SS);
+      s1 += x;
+      if (w != 0.0) r = fma(x, inv, r);
+      cnt += 1.0;
+    }
+    if (tj == 0) {
+      nr += (w != 0.0) ? 1.0 : 0.0;
+      sw += w;
+    }
+  }
+  Moments m;
+  m.n = cnt;
+  m.mean = cnt > 0.0 ? K + S / cnt : 0.0;
+  m.m2 = cnt > 0.0 ? SS - S * (S / cnt) : 0.0;
+  m.s1 = s1;
+  m.r = r;
+  sm[te][tj] = m;
+  if (tj == 0) ssc[te] = Scalars{0.0, nr, sw};
+  __syncthreads();
+  if (te == 0) {
+    Moments acc = sm[0][tj];
+    for (int t = 1; t < XS_TE; ++t) acc = merge(acc, sm[t][tj]);
+    if (j < k) part[(int64_t)blockIdx.x * k + j] = acc;
+    if (tj == 0 && blockIdx.y == 0) {
+      Scalars s{(double)(e_end - e_beg), 0.0, 0.0};
+      for (int t = 0; t < XS_TE; ++t) {
+        s.nr += ssc[t].nr;
+        s.sw += ssc[t].sw;
+      }
+      psc[blockIdx.x] = s;
+    }
+  }
+}
+
+// pass 2: merge the blocks' partials in block order, then into the accumulator
+__global__ void xsec_merge_kernel(const Moments* __restrict__ part, const Scalars* __restrict__ psc, int nblk, int k,
+                                  Moments* __restrict__ acc, Scalars* __restrict__ asc) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < k) {
+    Moments m = part[j];
+    for (int b = 1; b < nblk; ++b) m = merge(m, part[(int64_t)b * k + j]);
+    acc[j] = merge(acc[j], m);
+  }
+  if (j == 0) {
+    Scalars s = asc[0];
+    for (int b = 0; b < nblk; ++b) {
+      s.n += psc[b].n;
+      s.nr += psc[b].nr;
+      s.sw += psc[b].sw;
+    }
+    asc[0] = s;
+  }
+}
+
+__global__ void xsec_result_kernel(const Moments* __restrict__ acc, const Scalars* __restrict__ asc, int k,
+                                   double sigma, double dsigma, double* __restrict__ out) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= k) return;
+  const Moments m = acc[j];
+  const Scalars s = asc[0];
+  const double c = sigma / s.sw;
+  const double sig = c * m.s1;
+  const double mean_ratio = s.nr > 0.0 ? m.r / s.nr : NAN;
+  const double sd = sqrt(m.n > 0.0 ? (m.m2 > 0.0 ? m.m2 : 0.0) / m.n : NAN);
+  double ds = dsigma * mean_ratio + sigma * sd;
+  double fb = 0.0;
+  if (!isfinite(ds) || ds <= 0.0) {
+    const double r1 = sigma != 0.0 ? sig / sigma : INFINITY;
+    const double r2 = sig != 0.0 ? sigma / sig : INFINITY;
+    ds = dsigma * ((r2 > r1) ? r2 : r1);
+    fb = 1.0;
+  }
+  out[j] = sig;
+  out[k + j] = ds;
+  out[2 * k + j] = fb;
+}
+
+}  // namespace
+
+struct rex_xsec {
+  int k;
+  Moments* acc;        // [k]
+  Scalars* asc;        // [1]
+  Moments* part;       // [nblk][k], grown on demand
+  Scalars* psc;        // [nblk]
+  int64_t part_blocks;
+  double* res;         // [3][k]
+};
+
+extern "C" {
+
+const char* rex_xsec_last_error(void) { return g_xerr.c_str(); }
+
+int rex_xsec_create(int k, rex_xsec** out) {
+  if (!out) return xfail(REX_EINVAL, "null output handle pointer");
+  *out = nullptr;
+  if (k < 1 || k > (1 << 20)) return xfail(REX_EINVAL, "k must be in 1..2^20");
+  rex_xsec* x = new (std::nothrow) rex_xsec();
+  if (!x) return xfail(REX_ENOMEM, "out of host memory");
+  x->k = k;
+  cudaError_t e = cudaMalloc(&x->acc, sizeof(Moments) * k);
+  if (e == cudaSuccess) e = cudaMalloc(&x->asc, sizeof(Scalars));
+  if (e == cudaSuccess) e = cudaMalloc(&x->res, sizeof(double) * 3 * k);
+  if (e == cudaSuccess) e = cudaMemset(x->acc, 0, sizeof(Moments) * k);
+  if (e == cudaSuccess) e = cudaMemset(x->asc, 0, sizeof(Scalars));
+  if (e != cudaSuccess) {
+    cudaFree(x->acc);
+    cudaFree(x->asc);
+    cudaFree(x->res);
+    delete x;
+    return xfail(REX_ENOMEM, "accumulator allocation failed: %s", cudaGetErrorString(e));
+  }
+  *out = x;
+  return REX_OK;
+}
+
+int rex_xsec_reset(rex_xsec* x, void* stream) {
+  if (!x) return xfail(REX_EINVAL, "null handle");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaMemsetAsync(x->acc, 0, sizeof(Moments) * x->k, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(x->asc, 0, sizeof(Scalars), st);
+  return e == cudaSuccess ? REX_OK : xfail(REX_ECUDA, "reset: %s", cudaGetErrorString(e));
+}
+
+int rex_xsec_accumulate(rex_xsec* x, const double* w_in, const double* w_out, int64_t nev, void* stream) {
+  if (!x) return xfail(REX_EINVAL, "null handle");
+  if (nev < 0) return xfail(REX_EINVAL, "nev < 0");
+  if (nev == 0) return REX_OK;
+  if (!w_in || !w_out) return xfail(REX_EINVAL, "null array");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int64_t nblk = (nev + XS_EB - 1) / XS_EB;
+  if (nblk > 0x7fffffffLL) return xfail(REX_EINVAL, "too many events for one call");
+  if (nblk > x->part_blocks) {
+    // growing the partials buffer: earlier calls on this handle must have finished with it
+    cudaError_t e = cudaStreamSynchronize(st);
+    cudaFree(x->part);
+    cudaFree(x->psc);
+    x->part = nullptr;
+    x->psc = nullptr;
+    x->part_blocks = 0;
+    if (e == cudaSuccess) e = cudaMalloc(&x->part, sizeof(Moments) * x->k * nblk);
+    if (e == cudaSuccess) e = cudaMalloc(&x->psc, sizeof(Scalars) * nblk);
+    if (e != cudaSuccess) return xfail(REX_ENOMEM, "partials allocation failed: %s", cudaGetErrorString(e));
+    x->part_blocks = nblk;
+  }
+  const dim3 grid((unsigned)nblk, (unsigned)((x->k + XS_TJ - 1) / XS_TJ));
+  if (grid.y > 65535) return xfail(REX_EINVAL, "too many points");
+  xsec_partials_kernel<<<grid, dim3(XS_TJ, XS_TE), 0, st>>>(w_in, w_out, nev, x->k, x->part, x->psc);
+  xsec_merge_kernel<<<(x->k + 127) / 128, 128, 0, st>>>(x->part, x->psc, (int)nblk, x->k, x->acc, x->asc);
+  const cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? REX_OK : xfail(REX_ECUDA, "accumulate: %s", cudaGetErrorString(e));
+}
+
+int rex_xsec_result(rex_xsec* x, double sigma, double dsigma, double* sigma_out, double* dsigma_out, int* fallback,
+                    void* stream) {
+  if (!x) return xfail(REX_EINVAL, "null handle");
+  if (!sigma_out || !dsigma_out) return xfail(REX_EINVAL, "null output array");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int k = x->k;
+  xsec_result_kernel<<<(k + 127) / 128, 128, 0, st>>>(x->acc, x->asc, k, sigma, dsigma, x->res);
+  double* h = new (std::nothrow) double[3 * (size_t)k];
+  if (!h) return xfail(REX_ENOMEM, "out of host memory");
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h, x->res, sizeof(double) * 3 * k, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e == cudaSuccess) {
+    std::memcpy(sigma_out, h, sizeof(double) * k);
+    std::memcpy(dsigma_out, h + k, sizeof(double) * k);
+    if (fallback)
+      for (int j = 0; j < k; ++j) fallback[j] = h[2 * k + j] != 0.0;
+  }
+  delete[] h;
+  return e == cudaSuccess ? REX_OK : xfail(REX_ECUDA, "result: %s", cudaGetErrorString(e));
+}
+
+void rex_xsec_free(rex_xsec* x) {
+  if (!x) return;
+  cudaFree(x->acc);
+  cudaFree(x->asc);
+  cudaFree(x->part);
+  cudaFree(x->psc);
+  cudaFree(x->res);
+  delete x;
+}
+
+}  // extern "C"

@@ -45,6 +45,8 @@ EXPORTS = (
     "rex_surrogate_set_weights", "rex_surrogate_get_weights", "rex_surrogate_loss_grad",
     "rex_surrogate_train", "rex_surrogate_reweight", "rex_surrogate_set_exact_alphas", "rex_surrogate_set_kernel",
     "rex_surrogate_free",
+    "rex_xsec_last_error", "rex_xsec_create", "rex_xsec_reset", "rex_xsec_accumulate", "rex_xsec_result",
+    "rex_xsec_free",
 )
 
 
@@ -149,6 +151,18 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.rex_surrogate_set_exact_alphas.restype = ctypes.c_int
     lib.rex_surrogate_set_kernel.argtypes = [vp, ctypes.c_int]
     lib.rex_surrogate_set_kernel.restype = ctypes.c_int
+    lib.rex_xsec_last_error.argtypes = []
+    lib.rex_xsec_last_error.restype = ctypes.c_char_p
+    lib.rex_xsec_create.argtypes = [ctypes.c_int, ctypes.POINTER(vp)]
+    lib.rex_xsec_create.restype = ctypes.c_int
+    lib.rex_xsec_reset.argtypes = [vp, vp]
+    lib.rex_xsec_reset.restype = ctypes.c_int
+    lib.rex_xsec_accumulate.argtypes = [vp, vp, vp, i64, vp]
+    lib.rex_xsec_accumulate.restype = ctypes.c_int
+    lib.rex_xsec_result.argtypes = [vp, ctypes.c_double, ctypes.c_double, vp, vp, vp, vp]
+    lib.rex_xsec_result.restype = ctypes.c_int
+    lib.rex_xsec_free.argtypes = [vp]
+    lib.rex_xsec_free.restype = None
     lib.rex_surrogate_free.argtypes = [vp]
     lib.rex_surrogate_free.restype = None
     lib.rex_version.argtypes = []
@@ -400,6 +414,48 @@ class Surrogate:
                                               tau, _ptr(w_out), _ptr(pred), _ptr(err), ctypes.byref(nfb),
                                               _stream_ptr(stream)))
         return nfb.value
+
+
+def _xcheck(rc: int) -> None:
+    if rc != 0:
+        raise RexError(rc, load().rex_xsec_last_error().decode())
+
+
+class XSec:
+    """Reweighted cross sections and errors (rex_xsec_*), accumulated over calls."""
+
+    def __init__(self, k: int):
+        h = ctypes.c_void_p()
+        _xcheck(load().rex_xsec_create(int(k), ctypes.byref(h)))
+        self._h = h
+        self.k = int(k)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().rex_xsec_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def reset(self, stream=None) -> None:
+        _xcheck(load().rex_xsec_reset(self._h, _stream_ptr(stream)))
+
+    def accumulate(self, w_in, w_out, stream=None) -> None:
+        _xcheck(load().rex_xsec_accumulate(self._h, _ptr(w_in), _ptr(w_out), w_in.shape[0], _stream_ptr(stream)))
+
+    def result(self, sigma: float, dsigma: float, stream=None):
+        """(sigma' [k], dsigma' [k], fallback [k] bool) as numpy arrays."""
+        import numpy as np
+        s = np.empty(self.k)
+        ds = np.empty(self.k)
+        fb = np.empty(self.k, dtype=np.int32)
+        _xcheck(load().rex_xsec_result(self._h, float(sigma), float(dsigma), s.ctypes.data, ds.ctypes.data,
+                                       fb.ctypes.data, _stream_ptr(stream)))
+        return s, ds, fb.astype(bool)
 
 
 def probe_fma(fp64: bool, stream=None) -> float:
