@@ -545,7 +545,7 @@ def run_ours(args, world, rank, local):
         sig, dsig, fb = xs.result(1.0, 0.01, stream=stream)
         xs.close()
         del w_out
-        flops = args.nev * k * 7                         # d, S, SS (fma), s1, r (fma) per weight
+        flops = args.nev * k * 6                         # d, S, SS (fma), r (fma) per weight
         nbytes = args.nev * 8 + args.nev * k * 8         # w_in + w_out
         p64 = SM_COUNT * FP64_FMA_PER_SM_CLK * 2 * SM_MAX_MHZ * 1e6
         xsec = {"workload": f"sigma', dsigma' of {k} points over the headline's {args.nev} events",

@@ -375,3 +375,38 @@ def gauge_check(p: np.ndarray, mt: float, which: int, hel_g: tuple, lt: int, ltb
                          for t in terms], axis=1)
         res.append(np.real(np.einsum("ns,st,nt->n", amps.conj(), gmat, amps)))
     return res[0], res[1]
+
+
+def condition(p: np.ndarray, mt: float, wt: float, alphas: float) -> np.ndarray:
+    """Condition estimate of me2: kappa = sum_h sum_st |Re(A_s* G_st A_t)| / |M|^2 over
+    every helicity configuration h and every pair (s, t) of diagram terms, the same
+    terms me2 adds.  kappa >= 1; a result whose terms cancel has kappa >> 1, and a
+    relative rounding error up to ~ eps * kappa is then expected of any evaluation
+    order (a diagnostic for the tolerance rule, not a physical quantity)."""
+    p = np.asarray(p, dtype=np.float64)
+    nev, npart, _ = p.shape
+    ngl = npart - 2
+    g = math.sqrt(4.0 * math.pi * alphas)
+    terms = diagram_terms(ngl)
+    gmat = colour_matrix(ngl)
+    gl_rows = [0, 1] + list(range(4, npart))
+    p_out = [-p[:, 0], -p[:, 1]] + [p[:, r] for r in range(4, npart)]
+    p_t, p_tb = p[:, 2], p[:, 3]
+    total = np.zeros(nev)
+    absum = np.zeros(nev)
+    for hel_g in itertools.product((-1, 1), repeat=ngl):
+        eps = []
+        for k, (row, lam) in enumerate(zip(gl_rows, hel_g)):
+            e = polarisation(p[:, row], lam)
+            eps.append(e if k < 2 else e.conj())
+        kin = _Kinematics(p_out, eps, g)
+        for lt in (-1, 1):
+            ubar_t = bar(spinor_u(p_t, mt, lt))
+            for ltb in (-1, 1):
+                v_tb = spinor_v(p_tb, mt, ltb)
+                amps = np.stack([_line_amplitude(t, kin, ubar_t, v_tb, p_t, mt, wt)
+                                 for t in terms], axis=1)
+                pair = np.real(amps.conj()[:, :, None] * gmat[None, :, :] * amps[:, None, :])
+                total += pair.sum(axis=(1, 2))
+                absum += np.abs(pair).sum(axis=(1, 2))
+    return absum / np.abs(total)

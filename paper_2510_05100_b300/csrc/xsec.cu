@@ -11,10 +11,10 @@
 // does not depend on how the GPU schedules the blocks:
 //   pass 1  block b of the grid reduces events [b E, (b+1) E): each thread keeps
 //           shifted sums (first value K: S = sum (x - K), SS = sum (x - K)^2) of
-//           its events for one point, turned into (n, mean, M2); the 8 threads of
-//           a point merge in a fixed order (Chan, Golub & LeVeque 1979);
-//   pass 2  one thread per point merges the blocks' partials in block order and
-//           then into the accumulator;
+//           its events for one point, turned into (n, mean, M2, sum = n K + S);
+//           the threads of a point merge in a fixed order (Chan, Golub & LeVeque 1979);
+//   pass 2  one block per point merges the blocks' partials with a fixed-shape
+//           tree, then into the accumulator;
 //   result  sigma', dsigma' and the fallback flag per point.
 #include <cuda_runtime.h>
 
@@ -42,9 +42,9 @@ __host__ __device__ inline Moments merge(const Moments& a, const Moments& b) {
   if (a.n == 0.0) return b;
   Moments c;
   c.n = a.n + b.n;
-  const double d = b.mean - a.mean;
-  c.mean = a.mean + d * (b.n / c.n);
-  c.m2 = a.m2 + b.m2 + d * d * (a.n * b.n / c.n);
+  const double d = b.mean - a.mean, fb = b.n / c.n;
+  c.mean = a.mean + d * fb;
+  c.m2 = a.m2 + b.m2 + d * d * (a.n * fb);
   c.s1 = a.s1 + b.s1;
   c.r = a.r + b.r;
   return c;
@@ -65,81 +65,120 @@ int xfail(int code, const char* fmt, ...) {
   return code;
 }
 
-// pass 1: partial moments of events [bx E, bx E + E) for points 32 by + tj
+// pass 1: partial moments of events [bx E, bx E + E) for the points of column
+// group by.  A warp takes 32 events at a time: each lane loads one event's w and
+// forms its reciprocal (one warp-wide FP64 division per 32 events), then the
+// warp walks the 32 events G = 32 / kw at a time, lane L on event L / kw and
+// point by kw + L % kw (kw = lanes per event: the next power of two >= k, at
+// most 32), so that every lane has work when k < 32.
 __global__ void __launch_bounds__(XS_TJ* XS_TE) xsec_partials_kernel(const double* __restrict__ w_in,
                                                                      const double* __restrict__ w_out, int64_t nev,
-                                                                     int k, Moments* __restrict__ part,
+                                                                     int k, int kw, Moments* __restrict__ part,
                                                                      Scalars* __restrict__ psc) {
   __shared__ Moments sm[XS_TE][XS_TJ];
-  __shared__ Scalars ssc[XS_TE];
-  const int tj = threadIdx.x, te = threadIdx.y;
-  const int j = blockIdx.y * XS_TJ + tj;
+  __shared__ Scalars ssc[XS_TE][XS_TJ];
+  const int lane = threadIdx.x, te = threadIdx.y;
+  const int G = XS_TJ / kw;                      // events per warp step
+  const int sub = lane / kw, jl = lane - sub * kw;
+  const int j = blockIdx.y * kw + jl;
   const int64_t e_beg = (int64_t)blockIdx.x * XS_EB;
   const int64_t e_end = (e_beg + XS_EB < nev) ? e_beg + XS_EB : nev;
-  double cnt = 0.0, K = 0.0, S = 0.0, SS = 0.0, s1 = 0.0, r = 0.0;
+  int cnt = 0;                                   // integer count: keeps the FP64 pipe for the sums
+  double K = 0.0, S = 0.0, SS = 0.0, r = 0.0;
   double nr = 0.0, sw = 0.0;
-  for (int64_t e = e_beg + te; e < e_end; e += XS_TE) {
-    const double w = w_in[e];
-    // one reciprocal per event and warp, shared by its 32 points
-    double inv = 0.0;
-    if (tj == 0 && w != 0.0) inv = 1.0 / w;
-    inv = __shfl_sync(0xffffffffu, inv, 0);
-    if (j < k) {
-      const double x = w_out[e * k + j];
-      if (cnt == 0.0) K = x;
-      const double d = x - K;
-      S += d;
-      SS = fma(d, d, SS);
-      s1 += x;
-      if (w != 0.0) r = fma(x, inv, r);
-      cnt += 1.0;
+  for (int64_t g0 = e_beg + (int64_t)te * XS_TJ; g0 < e_end; g0 += (int64_t)XS_TE * XS_TJ) {
+    const int64_t el = g0 + lane;
+    const double wl = el < e_end ? w_in[el] : 0.0;
+    const double il = wl != 0.0 ? 1.0 / wl : 0.0;
+    if (blockIdx.y == 0 && el < e_end) {
+      nr += (wl != 0.0) ? 1.0 : 0.0;
+      sw += wl;
     }
-    if (tj == 0) {
-      nr += (w != 0.0) ? 1.0 : 0.0;
-      sw += w;
+    for (int s = 0; s < XS_TJ; s += G) {
+      const int src = s + sub;                     // event of this lane within the 32
+      const double w = __shfl_sync(0xffffffffu, wl, src);
+      const double inv = __shfl_sync(0xffffffffu, il, src);
+      const int64_t e = g0 + src;
+      if (e < e_end && j < k) {
+        const double x = w_out[e * k + j];
+        if (cnt == 0) K = x;
+        const double d = x - K;
+        S += d;
+        SS = fma(d, d, SS);
+        if (__double_as_longlong(w) << 1) r = fma(x, inv, r);   // w != 0 (either sign of zero)
+        ++cnt;
+      }
     }
   }
   Moments m;
-  m.n = cnt;
-  m.mean = cnt > 0.0 ? K + S / cnt : 0.0;
-  m.m2 = cnt > 0.0 ? SS - S * (S / cnt) : 0.0;
-  m.s1 = s1;
+  m.n = (double)cnt;
+  m.mean = cnt > 0 ? K + S / m.n : 0.0;
+  m.m2 = cnt > 0 ? SS - S * (S / m.n) : 0.0;
+  m.s1 = m.n * K + S;
   m.r = r;
-  sm[te][tj] = m;
-  if (tj == 0) ssc[te] = Scalars{0.0, nr, sw};
+  sm[te][lane] = m;
+  ssc[te][lane] = Scalars{0.0, nr, sw};
   __syncthreads();
-  if (te == 0) {
-    Moments acc = sm[0][tj];
-    for (int t = 1; t < XS_TE; ++t) acc = merge(acc, sm[t][tj]);
+  if (te == 0 && lane < kw) {
+    // the G lanes of point j in each of the 8 warps, in a fixed order
+    Moments acc = sm[0][lane];
+    for (int t = 0; t < XS_TE; ++t)
+      for (int g = 0; g < G; ++g)
+        if (t | g) acc = merge(acc, sm[t][g * kw + lane]);
     if (j < k) part[(int64_t)blockIdx.x * k + j] = acc;
-    if (tj == 0 && blockIdx.y == 0) {
-      Scalars s{(double)(e_end - e_beg), 0.0, 0.0};
-      for (int t = 0; t < XS_TE; ++t) {
-        s.nr += ssc[t].nr;
-        s.sw += ssc[t].sw;
+  }
+  if (te == 0 && lane == 0 && blockIdx.y == 0) {
+    Scalars sc{(double)(e_end - e_beg), 0.0, 0.0};
+    for (int t = 0; t < XS_TE; ++t)
+      for (int l = 0; l < XS_TJ; ++l) {
+        sc.nr += ssc[t][l].nr;
+        sc.sw += ssc[t][l].sw;
       }
-      psc[blockIdx.x] = s;
-    }
+    psc[blockIdx.x] = sc;
   }
 }
 
-// pass 2: merge the blocks' partials in block order, then into the accumulator
-__global__ void xsec_merge_kernel(const Moments* __restrict__ part, const Scalars* __restrict__ psc, int nblk, int k,
-                                  Moments* __restrict__ acc, Scalars* __restrict__ asc) {
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j < k) {
-    Moments m = part[j];
-    for (int b = 1; b < nblk; ++b) m = merge(m, part[(int64_t)b * k + j]);
-    acc[j] = merge(acc[j], m);
-  }
-  if (j == 0) {
-    Scalars s = asc[0];
-    for (int b = 0; b < nblk; ++b) {
-      s.n += psc[b].n;
-      s.nr += psc[b].nr;
-      s.sw += psc[b].sw;
+// pass 2: one block per point merges the blocks' partials with a fixed-shape
+// tree (thread t takes partials t, t + 256, ... in order, then a pairwise tree
+// over the 256 threads), then into the accumulator; block 0 also sums the scalars.
+constexpr int XS_MERGE = 256;
+__global__ void __launch_bounds__(XS_MERGE) xsec_merge_kernel(const Moments* __restrict__ part,
+                                                              const Scalars* __restrict__ psc, int nblk, int k,
+                                                              Moments* __restrict__ acc, Scalars* __restrict__ asc) {
+  __shared__ Moments sm[XS_MERGE];
+  __shared__ Scalars ss[XS_MERGE];
+  const int j = blockIdx.x, t = threadIdx.x;
+  Moments m{0.0, 0.0, 0.0, 0.0, 0.0};
+  Scalars sc{0.0, 0.0, 0.0};
+  for (int b = t; b < nblk; b += XS_MERGE) {
+    m = merge(m, part[(int64_t)b * k + j]);
+    if (j == 0) {
+      sc.n += psc[b].n;
+      sc.nr += psc[b].nr;
+      sc.sw += psc[b].sw;
     }
-    asc[0] = s;
+  }
+  sm[t] = m;
+  ss[t] = sc;
+  __syncthreads();
+  for (int stride = XS_MERGE / 2; stride > 0; stride >>= 1) {
+    if (t < stride) {
+      sm[t] = merge(sm[t], sm[t + stride]);
+      ss[t].n += ss[t + stride].n;
+      ss[t].nr += ss[t + stride].nr;
+      ss[t].sw += ss[t + stride].sw;
+    }
+    __syncthreads();
+  }
+  if (t == 0) {
+    acc[j] = merge(acc[j], sm[0]);
+    if (j == 0) {
+      Scalars a = asc[0];
+      a.n += ss[0].n;
+      a.nr += ss[0].nr;
+      a.sw += ss[0].sw;
+      asc[0] = a;
+    }
   }
 }
 
@@ -234,10 +273,12 @@ int rex_xsec_accumulate(rex_xsec* x, const double* w_in, const double* w_out, in
     if (e != cudaSuccess) return xfail(REX_ENOMEM, "partials allocation failed: %s", cudaGetErrorString(e));
     x->part_blocks = nblk;
   }
-  const dim3 grid((unsigned)nblk, (unsigned)((x->k + XS_TJ - 1) / XS_TJ));
+  int kw = 1;
+  while (kw < x->k && kw < XS_TJ) kw <<= 1;   // lanes per event
+  const dim3 grid((unsigned)nblk, (unsigned)((x->k + kw - 1) / kw));
   if (grid.y > 65535) return xfail(REX_EINVAL, "too many points");
-  xsec_partials_kernel<<<grid, dim3(XS_TJ, XS_TE), 0, st>>>(w_in, w_out, nev, x->k, x->part, x->psc);
-  xsec_merge_kernel<<<(x->k + 127) / 128, 128, 0, st>>>(x->part, x->psc, (int)nblk, x->k, x->acc, x->asc);
+  xsec_partials_kernel<<<grid, dim3(XS_TJ, XS_TE), 0, st>>>(w_in, w_out, nev, x->k, kw, x->part, x->psc);
+  xsec_merge_kernel<<<x->k, XS_MERGE, 0, st>>>(x->part, x->psc, (int)nblk, x->k, x->acc, x->asc);
   const cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? REX_OK : xfail(REX_ECUDA, "accumulate: %s", cudaGetErrorString(e));
 }
