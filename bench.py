@@ -191,6 +191,7 @@ def main():
     ap.add_argument("--no-multi", action="store_true")
     ap.add_argument("--no-surrogate", action="store_true")
     ap.add_argument("--no-xsec", action="store_true")
+    ap.add_argument("--no-lhe", action="store_true")
     args = ap.parse_args()
     world, rank, local = rdist.env()
     if args.impl == "reference":
@@ -382,6 +383,49 @@ def run_surrogate_leg(dev, stream, world, max_over_ranks, tau=0.02):
     return res
 
 
+def run_lhe_leg(dev, stream, pts, nev=100_000):
+    """The front-end around the path, file to file: read a synthetic LHE file of
+    g g -> t t~ g events (interleaved with other processes), extract the process,
+    reweight it to the points on the GPU (FP64, host buffers through the device),
+    append one weight per point and write the file."""
+    import tempfile
+    import torch
+    from paper_2510_05100_b300 import lhe_synth
+    from paper_2510_05100_b300 import rex
+
+    k = len(pts)
+    with tempfile.TemporaryDirectory() as tmp:
+        src, dst = os.path.join(tmp, "in.lhe"), os.path.join(tmp, "out.lhe")
+        lhe_synth.write_lhe(src, {PROC: nev, "gg_ttx": nev // 4}, seed=9)
+        size = os.path.getsize(src)
+        proc = rex.Process(PROC, rex.FP64)
+        proc.set_params(ORIGINAL)
+        pin, pout = lhe_synth.PROCESSES[PROC]
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        L = rex.Lhe(src)
+        t1 = time.perf_counter()
+        mom, w, idx = L.extract(pin, pout)
+        t2 = time.perf_counter()
+        w_out = proc.reweight(torch.from_numpy(mom).to(dev), torch.from_numpy(w).to(dev), pts,
+                              stream=stream).cpu().numpy()
+        t3 = time.perf_counter()
+        for j, pt in enumerate(pts):
+            L.set_weights("mt%.2f_as%.4f" % (pt["mt"], pt["alphas"]), idx, w_out[:, j])
+        L.write(dst)
+        t4 = time.perf_counter()
+        nfile = L.num_events
+        L.close()
+        proc.close()
+    n = mom.shape[0]
+    return {"workload": f"synthetic LHE v3 file of {nfile} events ({n} g g -> t t~ g, {nfile - n} g g -> t t~), "
+                        f"{size / 1e6:.0f} MB; {k} weights appended per g g -> t t~ g event",
+            "value": n * k / (t4 - t0), "unit": UNIT, "seconds": t4 - t0,
+            "read_events_per_s": nfile / (t1 - t0), "extract_events_per_s": nfile / (t2 - t1),
+            "reweight_seconds": t3 - t2, "write_events_per_s": nfile / (t4 - t3),
+            "threads": os.cpu_count(), "note": "file to file through the public API; read/extract/write on the host"}
+
+
 def run_ours(args, world, rank, local):
     cpu_pool = None
     cores = os.cpu_count() or 1
@@ -555,6 +599,8 @@ def run_ours(args, world, rank, local):
                              "hbm_gbs": nbytes / t / 1e9, "hbm_frac": nbytes / t / 1e9 / PEAKS["hbm_gbs"]
                              if PEAKS.get("hbm_gbs") else None}}
 
+    lhe_leg = None if args.no_lhe else run_lhe_leg(dev, stream, pts)
+
     multi = None if args.no_multi else run_multi_leg(dev, stream, max(3, args.steps // 2), world, barrier,
                                                      max_over_ranks)
     surrogate = None if args.no_surrogate else run_surrogate_leg(dev, stream, world, max_over_ranks)
@@ -583,7 +629,7 @@ def run_ours(args, world, rank, local):
                 "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                         "entry_point": "rex_reweight_host (pinned host buffers)"},
                 "gpu_launches": args.steps, "roofline": roofline, "cpu_baseline": cpu, "modes": extra,
-                "multi": multi, "surrogate": surrogate, "xsec": xsec}
+                "multi": multi, "surrogate": surrogate, "xsec": xsec, "lhe": lhe_leg}
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist

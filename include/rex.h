@@ -256,6 +256,45 @@ int rex_xsec_result(rex_xsec *x, double sigma, double dsigma, double *sigma_out,
 
 void rex_xsec_free(rex_xsec *x);
 
+/* ---- LHE front-end (host; Sec. 2 and Sec. 3.1) ------------------------------
+ * Reads an LHE v3 file, selects the events of one process by their external
+ * legs and hands their momenta to the reweighting calls in the process's parton
+ * order (the paper's eventBelongs sorting, parton reindexing and transposition
+ * to a structure of arrays), and writes the file back with new weights appended
+ * to every event (<rwgt><wgt id='ID'> %+.10e </wgt>) and declared in the header
+ * (<initrwgt><weightgroup name='rex_b300'><weight id='ID'>ID</weight>).  Nothing
+ * else of the file changes.  Host memory only; no GPU needed.  Errors:
+ * REX_EINVAL (unreadable or malformed file, bad argument), REX_ENOMEM; the
+ * message is in rex_lhe_last_error(). */
+typedef struct rex_lhe rex_lhe; /* opaque, library-owned */
+
+const char *rex_lhe_last_error(void);
+
+/* Parse path with nthreads threads (<= 0: all hardware threads). */
+int rex_lhe_read(const char *path, int nthreads, rex_lhe **out);
+
+int64_t rex_lhe_num_events(const rex_lhe *lhe);
+
+/* The events whose status -1 particles carry the PDG codes pdg_in[n_in] and whose
+ * status +1 particles carry pdg_out[n_out] (as multisets; other statuses are
+ * ignored), in file order.  Writes *nev; if momenta is not NULL, the momenta
+ * (E, px, py, pz) in the order pdg_in then pdg_out, identical codes in file order
+ * (host [nev][n_in + n_out][4]); if weights is not NULL, each event's xWgtUP
+ * (host [nev]); if index is not NULL, each event's position in the file (host
+ * [nev]).  Call with NULL arrays to size them. */
+int rex_lhe_extract(const rex_lhe *lhe, const int *pdg_in, int n_in, const int *pdg_out, int n_out,
+                    int64_t *nev, double *momenta, double *weights, int64_t *index);
+
+/* Set weight id (plain text, no quotes or markup) of the events at positions
+ * index[n] (host) to values[n] (host).  Ids are written in the order of their
+ * first call; an event without a value for an id gets no line for it. */
+int rex_lhe_set_weights(rex_lhe *lhe, const char *id, const int64_t *index, const double *values, int64_t n);
+
+/* Write the file with the weights inserted. */
+int rex_lhe_write(const rex_lhe *lhe, const char *path);
+
+void rex_lhe_free(rex_lhe *lhe);
+
 /* ---- Learned surrogate of the weight ratio ---------------------------------
  * The paper has no learned component.  An MLP (22 inputs -> 4 hidden layers of
  * 256 with GELU in its tanh form, z (1 + tanh(sqrt(2/pi) (z + 0.044715 z^3))) / 2

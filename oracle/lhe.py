@@ -40,7 +40,7 @@ def read(path: str) -> dict:
     with open(path, "r") as f:
         text = f.read()
     events = []
-    pos = 0
+    pos = _INIT.search(text).start()
     while True:
         m = _EVENT.search(text, pos)
         if not m:

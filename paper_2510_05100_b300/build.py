@@ -1,8 +1,9 @@
 """Build the sm_103a shared library librex_b300.so in-tree (python -m paper_2510_05100_b300.build).
 
-Steps: regenerate the amplitude header from the code generator, then one nvcc
-invocation compiling every .cu under csrc/ for sm_103a into a shared library
-next to this file.  nvcc cross-compiles, so this runs without a GPU.
+Steps: regenerate the amplitude header from the code generator, compile every
+.cu under csrc/ for sm_103a with nvcc and every host .cpp with the C++ compiler,
+then link one shared library next to this file.  nvcc cross-compiles, so this
+runs without a GPU.
 """
 from __future__ import annotations
 
@@ -27,10 +28,18 @@ def nvcc() -> str:
 
 
 def sources() -> list:
-    return sorted(glob.glob(os.path.join(CSRC, "*.cu")))
+    return sorted(glob.glob(os.path.join(CSRC, "*.cu")) + glob.glob(os.path.join(CSRC, "*.cpp")))
+
+
+def cxx() -> str:
+    return os.environ.get("CXX") or "g++"
 
 
 def _compile(src: str, obj: str, ptxas_info: bool):
+    if src.endswith(".cpp"):   # host-only C++ (the LHE front-end)
+        cmd = [cxx(), "-O2", "-std=c++17", "-fPIC", "-pthread", "-I", os.path.join(ROOT, "include"), "-c", "-o", obj,
+               src]
+        return cmd, subprocess.run(cmd, capture_output=True, text=True)
     cmd = [nvcc(), *ARCH, *FLAGS, "-c", "-o", obj, src]
     if ptxas_info:
         cmd.insert(1, "-Xptxas=-v")
@@ -47,7 +56,7 @@ def build(verbose: bool = False, ptxas_info: bool = False) -> str:
     objdir = os.path.join(ROOT, "_build", "obj")
     os.makedirs(objdir, exist_ok=True)
     srcs = sources()
-    objs = [os.path.join(objdir, os.path.basename(s)[:-3] + ".o") for s in srcs]
+    objs = [os.path.join(objdir, os.path.splitext(os.path.basename(s))[0] + ".o") for s in srcs]
     with ThreadPoolExecutor(max_workers=max(1, min(len(srcs), os.cpu_count() or 1))) as ex:
         results = list(ex.map(lambda so: _compile(so[0], so[1], ptxas_info), zip(srcs, objs)))
     for cmd, res in results:
@@ -57,7 +66,7 @@ def build(verbose: bool = False, ptxas_info: bool = False) -> str:
             raise RuntimeError(f"nvcc failed ({res.returncode}):\n{res.stdout}\n{res.stderr}")
         if ptxas_info or verbose:
             sys.stdout.write(res.stdout + res.stderr)
-    link = [nvcc(), *ARCH, "-shared", "-o", LIB, *objs]
+    link = [nvcc(), *ARCH, "-shared", "-o", LIB, *objs, "-lpthread"]
     res = subprocess.run(link, capture_output=True, text=True)
     if res.returncode != 0:
         raise RuntimeError(f"link failed ({res.returncode}):\n{res.stdout}\n{res.stderr}")

@@ -47,6 +47,8 @@ EXPORTS = (
     "rex_surrogate_free",
     "rex_xsec_last_error", "rex_xsec_create", "rex_xsec_reset", "rex_xsec_accumulate", "rex_xsec_result",
     "rex_xsec_free",
+    "rex_lhe_last_error", "rex_lhe_read", "rex_lhe_num_events", "rex_lhe_extract", "rex_lhe_set_weights",
+    "rex_lhe_write", "rex_lhe_free",
 )
 
 
@@ -161,6 +163,20 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.rex_xsec_accumulate.restype = ctypes.c_int
     lib.rex_xsec_result.argtypes = [vp, ctypes.c_double, ctypes.c_double, vp, vp, vp, vp]
     lib.rex_xsec_result.restype = ctypes.c_int
+    lib.rex_lhe_last_error.argtypes = []
+    lib.rex_lhe_last_error.restype = ctypes.c_char_p
+    lib.rex_lhe_read.argtypes = [ctypes.c_char_p, ctypes.c_int, ctypes.POINTER(vp)]
+    lib.rex_lhe_read.restype = ctypes.c_int
+    lib.rex_lhe_num_events.argtypes = [vp]
+    lib.rex_lhe_num_events.restype = i64
+    lib.rex_lhe_extract.argtypes = [vp, vp, ctypes.c_int, vp, ctypes.c_int, ctypes.POINTER(i64), vp, vp, vp]
+    lib.rex_lhe_extract.restype = ctypes.c_int
+    lib.rex_lhe_set_weights.argtypes = [vp, ctypes.c_char_p, vp, vp, i64]
+    lib.rex_lhe_set_weights.restype = ctypes.c_int
+    lib.rex_lhe_write.argtypes = [vp, ctypes.c_char_p]
+    lib.rex_lhe_write.restype = ctypes.c_int
+    lib.rex_lhe_free.argtypes = [vp]
+    lib.rex_lhe_free.restype = None
     lib.rex_xsec_free.argtypes = [vp]
     lib.rex_xsec_free.restype = None
     lib.rex_surrogate_free.argtypes = [vp]
@@ -456,6 +472,61 @@ class XSec:
         _xcheck(load().rex_xsec_result(self._h, float(sigma), float(dsigma), s.ctypes.data, ds.ctypes.data,
                                        fb.ctypes.data, _stream_ptr(stream)))
         return s, ds, fb.astype(bool)
+
+
+def _lcheck(rc: int) -> None:
+    if rc != 0:
+        raise RexError(rc, load().rex_lhe_last_error().decode())
+
+
+class Lhe:
+    """An LHE v3 file: process extraction and weight writing (rex_lhe_*; host only)."""
+
+    def __init__(self, path: str, nthreads: int = 0):
+        h = ctypes.c_void_p()
+        _lcheck(load().rex_lhe_read(os.fsencode(path), int(nthreads), ctypes.byref(h)))
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().rex_lhe_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def num_events(self) -> int:
+        return load().rex_lhe_num_events(self._h)
+
+    def extract(self, pdg_in, pdg_out):
+        """(momenta [n][npart][4] (E, px, py, pz), weights [n], file positions [n]) as numpy arrays."""
+        import numpy as np
+        a = np.ascontiguousarray(pdg_in, dtype=np.int32)
+        b = np.ascontiguousarray(pdg_out, dtype=np.int32)
+        n = ctypes.c_int64()
+        _lcheck(load().rex_lhe_extract(self._h, a.ctypes.data, a.size, b.ctypes.data, b.size, ctypes.byref(n),
+                                       None, None, None))
+        mom = np.empty((n.value, a.size + b.size, 4))
+        w = np.empty(n.value)
+        idx = np.empty(n.value, dtype=np.int64)
+        _lcheck(load().rex_lhe_extract(self._h, a.ctypes.data, a.size, b.ctypes.data, b.size, ctypes.byref(n),
+                                       mom.ctypes.data, w.ctypes.data, idx.ctypes.data))
+        return mom, w, idx
+
+    def set_weights(self, wid: str, index, values) -> None:
+        import numpy as np
+        i = np.ascontiguousarray(index, dtype=np.int64)
+        v = np.ascontiguousarray(values, dtype=np.float64)
+        if i.size != v.size:
+            raise ValueError("index and values differ in length")
+        _lcheck(load().rex_lhe_set_weights(self._h, wid.encode(), i.ctypes.data, v.ctypes.data, i.size))
+
+    def write(self, path: str) -> None:
+        _lcheck(load().rex_lhe_write(self._h, os.fsencode(path)))
 
 
 def probe_fma(fp64: bool, stream=None) -> float:

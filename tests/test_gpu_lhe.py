@@ -1,0 +1,68 @@
+"""From an LHE file to a reweighted LHE file (needs a B300): the front-end's
+extraction feeds the FP64 kernels, the new weights are written back, and the
+written file is read with the oracle's reader."""
+import re
+
+import numpy as np
+import pytest
+
+from rexlib import ensure_built
+from oracle import lhe as olhe
+from oracle import reweight as oracle_rw
+from paper_2510_05100_b300 import lhe_synth
+from paper_2510_05100_b300 import phase_space as ps
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+ORIG = dict(mt=173.0, wt=0.0, alphas=0.118)
+GRIDS = {"gg_ttx": ps.grid_gg_ttx(), "gg_ttxg": ps.grid_gg_ttxg()}
+
+
+@pytest.fixture(scope="module")
+def rex():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return ensure_built()
+
+
+def wid(pt):
+    return "mt%.2f_as%.4f" % (pt["mt"], pt["alphas"])
+
+
+def test_file_to_reweighted_file(rex, tmp_path):
+    src, dst = str(tmp_path / "in.lhe"), str(tmp_path / "out.lhe")
+    info = lhe_synth.write_lhe(src, {"gg_ttxg": 3000, "gg_ttx": 2000, "ee_mumu": 100}, seed=5)
+    L = rex.Lhe(src)
+    gpu = {}
+    for proc, pts in GRIDS.items():
+        pin, pout = lhe_synth.PROCESSES[proc]
+        mom, w, idx = L.extract(pin, pout)
+        assert mom.shape[0] == info[proc][0].shape[0]
+        p = rex.Process(proc, 0)
+        p.set_params(ORIG)
+        out = p.reweight(torch.from_numpy(mom).cuda(), torch.from_numpy(w).cuda(), pts).cpu().numpy()
+        ref = oracle_rw.reweight(proc, mom[:8], w[:8], ORIG, pts)
+        assert np.max(np.abs(out[:8] / ref - 1)) < 1e-12
+        for j, pt in enumerate(pts):
+            L.set_weights(wid(pt), idx, out[:, j])
+        gpu[proc] = (idx, out)
+    L.write(dst)
+    L.close()
+    doc = olhe.read(dst)
+    text = doc["text"]
+    ids = [wid(pt) for pts in GRIDS.values() for pt in pts]
+    for i in ids:
+        assert "<weight id='%s'>%s</weight>" % (i, i) in text
+    pat = re.compile(r"<wgt id='([^']+)'> ([^ ]+) </wgt>")
+    for proc, (idx, out) in gpu.items():
+        pts = GRIDS[proc]
+        for n in (0, 1, len(idx) // 2, len(idx) - 1):
+            ev = doc["events"][idx[n]]
+            found = dict(pat.findall(text[ev["start"]:ev["end"]]))
+            for j, pt in enumerate(pts):
+                assert float(found[wid(pt)]) == pytest.approx(out[n, j], rel=1e-10)   # %+.10e in the file
+    # events of other processes get no weight lines
+    _, _, eidx = olhe.extract(doc, *lhe_synth.PROCESSES["ee_mumu"])
+    ev = doc["events"][eidx[0]]
+    assert "<wgt" not in text[ev["start"]:ev["end"]]
