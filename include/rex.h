@@ -362,6 +362,13 @@ int rex_surrogate_reweight(rex_surrogate *s, rex_proc *exact, const double *mome
  * alphas.  Errors: REX_EINVAL for power outside 0..8 or alphas0 <= 0. */
 int rex_surrogate_set_exact_alphas(rex_surrogate *s, double alphas0, int power);
 
+/* Save the network (parameters, Adam state and step, the exact coupling setting)
+ * to a host file, or load one saved by this library (same parameter count).  Both
+ * synchronise the device.  Errors: REX_EINVAL (unreadable, unwritable or foreign
+ * file), REX_ECUDA. */
+int rex_surrogate_save(rex_surrogate *s, const char *path);
+int rex_surrogate_load(rex_surrogate *s, const char *path);
+
 /* Inference kernel of rex_surrogate_reweight.
  *   REX_SURROGATE_FUSED (default): one persistent kernel per call; each tile of
  *     128 (event, point) pairs runs all layers on the tcgen05 tensor cores with

@@ -830,6 +830,57 @@ int rex_surrogate_reweight(rex_surrogate* s, rex_proc* exact, const double* mome
   return e == cudaSuccess ? REX_OK : scuda(e, "fallback scatter");
 }
 
+// File format (native endianness): "REXSURR1", int64 parameter count, double
+// alphas0, int32 power, int32 step, then params, Adam m and v (FP32 each).
+int rex_surrogate_save(rex_surrogate* s, const char* path) {
+  int rc = check_handle(s);
+  if (rc) return rc;
+  if (!path) return sfail(REX_EINVAL, "null path");
+  std::vector<float> buf(3 * (size_t)NPARAM);
+  cudaError_t e = cudaMemcpy(buf.data(), s->params, NPARAM * 4, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(buf.data() + NPARAM, s->m, NPARAM * 4, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(buf.data() + 2 * NPARAM, s->v, NPARAM * 4, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return scuda(e, "save: copy parameters");
+  FILE* f = std::fopen(path, "wb");
+  if (!f) return sfail(REX_EINVAL, "cannot open %s for writing", path);
+  const int64_t n = NPARAM;
+  const int32_t pw = s->apow, st = s->step;
+  bool ok = std::fwrite("REXSURR1", 1, 8, f) == 8 && std::fwrite(&n, 8, 1, f) == 1 &&
+            std::fwrite(&s->as0, 8, 1, f) == 1 && std::fwrite(&pw, 4, 1, f) == 1 && std::fwrite(&st, 4, 1, f) == 1 &&
+            std::fwrite(buf.data(), 4, buf.size(), f) == buf.size();
+  ok = (std::fclose(f) == 0) && ok;
+  return ok ? REX_OK : sfail(REX_EINVAL, "short write to %s", path);
+}
+
+int rex_surrogate_load(rex_surrogate* s, const char* path) {
+  int rc = check_handle(s);
+  if (rc) return rc;
+  if (!path) return sfail(REX_EINVAL, "null path");
+  FILE* f = std::fopen(path, "rb");
+  if (!f) return sfail(REX_EINVAL, "cannot open %s", path);
+  char magic[8];
+  int64_t n = 0;
+  double as0 = 0.0;
+  int32_t pw = 0, st = 0;
+  std::vector<float> buf(3 * (size_t)NPARAM);
+  bool ok = std::fread(magic, 1, 8, f) == 8 && std::memcmp(magic, "REXSURR1", 8) == 0 && std::fread(&n, 8, 1, f) == 1 &&
+            n == NPARAM && std::fread(&as0, 8, 1, f) == 1 && std::fread(&pw, 4, 1, f) == 1 &&
+            std::fread(&st, 4, 1, f) == 1 && std::fread(buf.data(), 4, buf.size(), f) == buf.size();
+  std::fclose(f);
+  if (!ok || !(as0 > 0.0) || pw < 0 || pw > 8 || st < 0)
+    return sfail(REX_EINVAL, "%s is not a surrogate file of this network", path);
+  cudaError_t e = cudaMemcpy(s->params, buf.data(), NPARAM * 4, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(s->m, buf.data() + NPARAM, NPARAM * 4, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(s->v, buf.data() + 2 * NPARAM, NPARAM * 4, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = refresh_bf16(s, nullptr);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return scuda(e, "load: copy parameters");
+  s->as0 = as0;
+  s->apow = pw;
+  s->step = st;
+  return REX_OK;
+}
+
 int rex_surrogate_set_kernel(rex_surrogate* s, int kind) {
   const int rc = check_handle(s);
   if (rc) return rc;

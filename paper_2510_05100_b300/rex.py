@@ -44,6 +44,7 @@ EXPORTS = (
     "rex_surrogate_num_params", "rex_surrogate_last_error", "rex_surrogate_create",
     "rex_surrogate_set_weights", "rex_surrogate_get_weights", "rex_surrogate_loss_grad",
     "rex_surrogate_train", "rex_surrogate_reweight", "rex_surrogate_set_exact_alphas", "rex_surrogate_set_kernel",
+    "rex_surrogate_save", "rex_surrogate_load",
     "rex_surrogate_free",
     "rex_xsec_last_error", "rex_xsec_create", "rex_xsec_reset", "rex_xsec_accumulate", "rex_xsec_result",
     "rex_xsec_free",
@@ -151,6 +152,10 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.rex_surrogate_reweight.restype = ctypes.c_int
     lib.rex_surrogate_set_exact_alphas.argtypes = [vp, ctypes.c_double, ctypes.c_int]
     lib.rex_surrogate_set_exact_alphas.restype = ctypes.c_int
+    lib.rex_surrogate_save.argtypes = [vp, ctypes.c_char_p]
+    lib.rex_surrogate_save.restype = ctypes.c_int
+    lib.rex_surrogate_load.argtypes = [vp, ctypes.c_char_p]
+    lib.rex_surrogate_load.restype = ctypes.c_int
     lib.rex_surrogate_set_kernel.argtypes = [vp, ctypes.c_int]
     lib.rex_surrogate_set_kernel.restype = ctypes.c_int
     lib.rex_xsec_last_error.argtypes = []
@@ -400,6 +405,12 @@ class Surrogate:
     def set_exact_alphas(self, alphas0: float, power: int) -> None:
         """Make the alphas^power dependence of |M|^2 exact; the network learns the rest."""
         _scheck(load().rex_surrogate_set_exact_alphas(self._h, float(alphas0), int(power)))
+
+    def save(self, path: str) -> None:
+        _scheck(load().rex_surrogate_save(self._h, os.fsencode(path)))
+
+    def load(self, path: str) -> None:
+        _scheck(load().rex_surrogate_load(self._h, os.fsencode(path)))
 
     def set_kernel(self, kind: int) -> None:
         """Inference kernel: SURROGATE_FUSED (tcgen05, default) or SURROGATE_LAYERED (mma.sync GEMMs)."""

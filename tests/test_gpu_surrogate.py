@@ -249,3 +249,25 @@ def test_what_the_surrogate_gains_over_the_exact_path(rex, trained):
           f"exact FP64: {t_fp64 * 1e3:.2f} ms, exact mixed: {t_mix * 1e3:.2f} ms; "
           f"fallback {nfb}/{n} events, max rel err {float(rel.max()):.3e}, median {float(rel.median()):.3e}")
     assert t_net < t_fp64
+
+
+def test_save_and_load_round_trip(rex, trained, tmp_path):
+    """A saved network loads into a fresh handle with identical weights, coupling
+    setting and predictions; a foreign file is refused."""
+    s, _, pts, _ = trained
+    path = str(tmp_path / "net.bin")
+    s.save(path)
+    t = rex.Surrogate(99)
+    t.load(path)
+    assert np.array_equal(t.get_weights(), s.get_weights())
+    mom = torch.from_numpy(ps.make_events("gg_ttxg", 64, 5)).cuda()
+    a = torch.empty((64, len(pts)), dtype=torch.float32, device="cuda")
+    b = torch.empty_like(a)
+    s.reweight(mom, None, pts, pred=a)
+    t.reweight(mom, None, pts, pred=b)
+    assert torch.equal(a, b)
+    bad = str(tmp_path / "bad.bin")
+    open(bad, "wb").write(b"not a network")
+    with pytest.raises(rex.RexError):
+        t.load(bad)
+    t.close()
