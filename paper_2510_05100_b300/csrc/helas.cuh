@@ -191,6 +191,36 @@ __device__ __forceinline__ void slash_acc(R s, const R* a, const cx<R>* psi, cx<
   out[3].im = fma(am, psi[1].im, fma(a1, psi[0].im, fma(a2, psi[0].re, out[3].im)));
 }
 
+#if defined(__CUDACC__)
+// FP32: the same FMA chains on (re, im) pairs with packed FP32x2 FMAs (one
+// instruction per complex component); each lane rounds exactly as above.
+template <>
+__device__ __forceinline__ void slash_acc<float>(float s, const float* a, const cx<float>* psi, cx<float>* out) {
+  const float am = s * (a[0] - a[3]), ap = s * (a[0] + a[3]);
+  const float a1 = s * a[1], a2 = s * a[2];
+  auto P = [](const cx<float>& z) { return make_float2(z.re, z.im); };
+  auto X = [](const cx<float>& z) { return make_float2(z.im, z.re); };
+  auto B = [](float x) { return make_float2(x, x); };
+  float2 o;
+  o = __ffma2_rn(make_float2(-a2, a2), X(psi[3]), P(out[0]));
+  o = __ffma2_rn(B(-a1), P(psi[3]), o);
+  o = __ffma2_rn(B(am), P(psi[2]), o);
+  out[0] = cx<float>{o.x, o.y};
+  o = __ffma2_rn(make_float2(a2, -a2), X(psi[2]), P(out[1]));
+  o = __ffma2_rn(B(-a1), P(psi[2]), o);
+  o = __ffma2_rn(B(ap), P(psi[3]), o);
+  out[1] = cx<float>{o.x, o.y};
+  o = __ffma2_rn(make_float2(a2, -a2), X(psi[1]), P(out[2]));
+  o = __ffma2_rn(B(a1), P(psi[1]), o);
+  o = __ffma2_rn(B(ap), P(psi[0]), o);
+  out[2] = cx<float>{o.x, o.y};
+  o = __ffma2_rn(make_float2(-a2, a2), X(psi[0]), P(out[3]));
+  o = __ffma2_rn(B(a1), P(psi[0]), o);
+  o = __ffma2_rn(B(am), P(psi[1]), o);
+  out[3] = cx<float>{o.x, o.y};
+}
+#endif
+
 // out = (gamma . a) psi + c psi for real a and real c (FMA chains).
 template <typename R>
 __device__ __forceinline__ void slash_plus_scalar(const R* a, R c, const cx<R>* psi, cx<R>* out) {
@@ -198,6 +228,20 @@ __device__ __forceinline__ void slash_plus_scalar(const R* a, R c, const cx<R>* 
   for (int i = 0; i < 4; ++i) out[i] = cx<R>{c * psi[i].re, c * psi[i].im};
   slash_acc(R(1), a, psi, out);
 }
+
+#if defined(__CUDACC__)
+// FP32 with packed FP32x2 arithmetic (mixed mode): the scaling by c on (re, im) pairs
+template <>
+__device__ __forceinline__ void slash_plus_scalar<float>(const float* a, float c, const cx<float>* psi,
+                                                         cx<float>* out) {
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const float2 o = __fmul2_rn(make_float2(c, c), make_float2(psi[i].re, psi[i].im));
+    out[i] = cx<float>{o.x, o.y};
+  }
+  slash_acc(1.0f, a, psi, out);
+}
+#endif
 
 // Fermion propagator (FFV1_1 role) with the vertex and propagator factors i*i = -1:
 //   out = -(q-slash + m) in / (q^2 - m^2 + i m Gamma).
@@ -228,6 +272,22 @@ __device__ __forceinline__ cx<R> ubar_dot(const cx<R>* u, const cx<R>* x) {
 // ---------------------------------------------------------------------------
 // colour-ordered gluon vertices (VVV1P0_1 / VVVV roles), real currents
 // ---------------------------------------------------------------------------
+
+#if defined(__CUDACC__)
+// FP32: conj(u) . x summed as one chain of packed FP32x2 FMAs on (re, im)
+template <>
+__device__ __forceinline__ cx<float> ubar_dot<float>(const cx<float>* u, const cx<float>* x) {
+  float2 acc = make_float2(0.f, 0.f);
+  const int xi[4] = {2, 3, 0, 1};
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const cx<float> a = u[i], b = x[xi[i]];
+    acc = __ffma2_rn(make_float2(a.re, a.re), make_float2(b.re, b.im), acc);
+    acc = __ffma2_rn(make_float2(a.im, -a.im), make_float2(b.im, b.re), acc);
+  }
+  return cx<float>{acc.x, acc.y};
+}
+#endif
 
 // out += s * [ (X.Y)(PY - PX) - (X.(PX + 2 PY)) Y + (Y.(2 PX + PY)) X ]
 template <typename R>

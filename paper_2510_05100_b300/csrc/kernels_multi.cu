@@ -50,8 +50,11 @@ __global__ void __launch_bounds__(QCD_BLOCK, MINB)
 }
 
 // Lanes-per-event split of each QCD process in the multi kernel (the defaults of
-// the single-process kernels: FP64 no split; mixed: no split, and the tensor-core
-// colour form for gg_ttxgg).
+// the single-process kernels: no split, scalar colour form).  One register budget
+// serves every process: min blocks per SM follows g g -> t t~ g g, the heaviest.
+#ifndef REX_MULTI_MINB
+#define REX_MULTI_MINB 1
+#endif
 template <typename R>
 struct MultiSplit;
 template <>
@@ -61,8 +64,8 @@ struct MultiSplit<double> {
 };
 template <>
 struct MultiSplit<float> {
-  static constexpr int TTX = 0, TTXG = 0, TTXGG = 0, MINB = 3;
-  static constexpr bool TC_TTXGG = true;   // 24 colour flows: the tensor-core colour form
+  static constexpr int TTX = 0, TTXG = 0, TTXGG = 0, MINB = REX_MULTI_MINB;
+  static constexpr bool TC_TTXGG = false;
 };
 
 template <typename R, bool WIDTH>

@@ -10,7 +10,8 @@
 // then the events are parsed in parallel (std::thread, contiguous ranges) into
 // flat particle arrays (PDG code, status, E px py pz) with std::from_chars.
 // Writing: the original text is copied with the weight lines and the
-// <initrwgt> group inserted; nothing else changes.
+// <initrwgt> group inserted (events formatted in parallel, written in order);
+// nothing else changes.
 #include <algorithm>
 #include <charconv>
 #include <cmath>
@@ -295,11 +296,52 @@ int rex_lhe_set_weights(rex_lhe* L, const char* id, const int64_t* index, const 
   return REX_OK;
 }
 
+// One event's text with its weight lines inserted, appended to out.
+static void emit_event(const rex_lhe* L, size_t i, std::string& out, std::string& lines) {
+  const std::string& s = L->text;
+  const Event& e = L->ev[i];
+  char buf[64];
+  lines.clear();
+  for (size_t w = 0; w < L->wid.size(); ++w)
+    if (L->whas[w][i]) {
+      // " %+.10e " with std::to_chars (correctly rounded, as printf)
+      const double v = L->wval[w][i];
+      char* p = buf;
+      *p++ = ' ';
+      if (!std::signbit(v)) *p++ = '+';
+      p = std::to_chars(p, buf + sizeof buf - 2, v, std::chars_format::scientific, 10).ptr;
+      *p++ = ' ';
+      lines += "<wgt id='";
+      lines += L->wid[w];
+      lines += "'>";
+      lines.append(buf, (size_t)(p - buf));
+      lines += "</wgt>\n";
+    }
+  if (lines.empty()) {
+    out.append(s, (size_t)e.start, (size_t)(e.end - e.start));
+    return;
+  }
+  const size_t close = (size_t)e.end - 8;   // "</event>"
+  // the event's last </rwgt>, searched inside the event only
+  const std::string_view body(s.data() + e.start, close - (size_t)e.start);
+  const size_t rb = body.rfind("</rwgt>");
+  if (rb != std::string_view::npos) {
+    const size_t r = (size_t)e.start + rb;
+    out.append(s, (size_t)e.start, r - (size_t)e.start);
+    out += lines;
+    out.append(s, r, (size_t)e.end - r);
+  } else {
+    out.append(s, (size_t)e.start, close - (size_t)e.start);
+    out += "<rwgt>\n";
+    out += lines;
+    out += "</rwgt>\n";
+    out.append(s, close, 8);
+  }
+}
+
 int rex_lhe_write(const rex_lhe* L, const char* path) {
   if (!L || !path) return lfail(REX_EINVAL, "null argument");
   const std::string& s = L->text;
-  std::string out;
-  out.reserve(s.size() + L->ev.size() * (40 + 48 * L->wid.size()) + 1024);
   std::string header = s.substr(0, L->init_at);
   if (!L->wid.empty()) {
     std::string group = "<weightgroup name='rex_b300'>\n";
@@ -313,45 +355,38 @@ int rex_lhe_write(const rex_lhe* L, const char* path) {
     else
       header += "<header>\n<initrwgt>\n" + group + "</initrwgt>\n</header>\n";
   }
-  out += header;
-  size_t prev = L->init_at;
-  char buf[64];
-  std::string lines;
-  for (size_t i = 0; i < L->ev.size(); ++i) {
-    const Event& e = L->ev[i];
-    out.append(s, prev, (size_t)e.start - prev);
-    lines.clear();
-    for (size_t w = 0; w < L->wid.size(); ++w)
-      if (L->whas[w][i]) {
-        std::snprintf(buf, sizeof buf, " %+.10e ", L->wval[w][i]);
-        lines += "<wgt id='" + L->wid[w] + "'>" + buf + "</wgt>\n";
+  // events formatted in parallel, one text chunk per contiguous range (each range
+  // also carries the original text between its events), written in order
+  const int64_t nev = (int64_t)L->ev.size();
+  int nt = (int)std::thread::hardware_concurrency();
+  if (nt < 1) nt = 1;
+  if (nt > 64) nt = 64;
+  if (nev < 4096) nt = 1;
+  std::vector<std::string> chunk(nt);
+  std::vector<std::thread> th;
+  for (int t = 0; t < nt; ++t) {
+    const int64_t a = nev * t / nt, b = nev * (t + 1) / nt;
+    th.emplace_back([&, a, b, t]() {
+      std::string& out = chunk[t];
+      std::string lines;
+      if (b > a) out.reserve((size_t)(L->ev[b - 1].end - L->ev[a].start) + (size_t)(b - a) * (16 + 48 * L->wid.size()));
+      for (int64_t i = a; i < b; ++i) {
+        // the text between the previous event (or the <init> block) and this one
+        const size_t prev = i == 0 ? L->init_at : (size_t)L->ev[i - 1].end;
+        out.append(s, prev, (size_t)L->ev[i].start - prev);
+        emit_event(L, (size_t)i, out, lines);
       }
-    if (lines.empty()) {
-      out.append(s, (size_t)e.start, (size_t)(e.end - e.start));
-    } else {
-      const size_t close = (size_t)e.end - 8;   // "</event>"
-      // the event's last </rwgt>, searched inside the event only
-      const std::string_view body(s.data() + e.start, close - (size_t)e.start);
-      const size_t rb = body.rfind("</rwgt>");
-      if (rb != std::string_view::npos) {
-        const size_t r = (size_t)e.start + rb;
-        out.append(s, (size_t)e.start, r - (size_t)e.start);
-        out += lines;
-        out.append(s, r, (size_t)e.end - r);
-      } else {
-        out.append(s, (size_t)e.start, close - (size_t)e.start);
-        out += "<rwgt>\n" + lines + "</rwgt>\n";
-        out.append(s, close, 8);
-      }
-    }
-    prev = (size_t)e.end;
+    });
   }
-  out.append(s, prev, std::string::npos);
+  for (auto& x : th) x.join();
+  const size_t tail = nev ? (size_t)L->ev[nev - 1].end : L->init_at;
   FILE* f = std::fopen(path, "wb");
   if (!f) return lfail(REX_EINVAL, "cannot open %s for writing", path);
-  const size_t put = std::fwrite(out.data(), 1, out.size(), f);
-  const int rc = std::fclose(f);
-  return (put == out.size() && rc == 0) ? REX_OK : lfail(REX_EINVAL, "short write to %s", path);
+  bool ok = std::fwrite(header.data(), 1, header.size(), f) == header.size();
+  for (const auto& c : chunk) ok = ok && std::fwrite(c.data(), 1, c.size(), f) == c.size();
+  ok = ok && std::fwrite(s.data() + tail, 1, s.size() - tail, f) == s.size() - tail;
+  ok = (std::fclose(f) == 0) && ok;
+  return ok ? REX_OK : lfail(REX_EINVAL, "short write to %s", path);
 }
 
 void rex_lhe_free(rex_lhe* L) { delete L; }

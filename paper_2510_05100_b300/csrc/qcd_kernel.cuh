@@ -219,8 +219,8 @@ __global__ void __launch_bounds__(QCD_BLOCK, MINB)
 struct QcdVariant {
   int split, minb, tc;
 };
-constexpr QcdVariant kQcdVariants[QCD_NVARIANT] = {{0, 1, 0}, {1, 1, 0}, {0, 3, 0}, {1, 3, 0},
-                                                   {1, 4, 0}, {0, 3, 1}, {1, 3, 1}};
+constexpr QcdVariant kQcdVariants[QCD_NVARIANT] = {{0, 1, 0}, {1, 1, 0}, {0, 3, 0}, {1, 3, 0}, {1, 4, 0},
+                                                   {0, 3, 1}, {1, 3, 1}, {0, 1, 1}, {1, 1, 1}};
 
 template <int PROC, typename R, int V>
 static int launch_v(const double* mom, const double* w_in, int64_t nev, const QcdLaunch& lp,
@@ -253,6 +253,8 @@ static int launch_variant(int variant, const double* mom, const double* w_in, in
     case 4: return launch_v<PROC, R, 4>(mom, w_in, nev, lp, out, st);
     case 5: return launch_v<PROC, R, 5>(mom, w_in, nev, lp, out, st);
     case 6: return launch_v<PROC, R, 6>(mom, w_in, nev, lp, out, st);
+    case 7: return launch_v<PROC, R, 7>(mom, w_in, nev, lp, out, st);
+    case 8: return launch_v<PROC, R, 8>(mom, w_in, nev, lp, out, st);
     default: return (int)cudaErrorInvalidValue;
   }
 }

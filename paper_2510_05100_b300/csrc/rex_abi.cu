@@ -79,7 +79,7 @@ int default_variant(int kind, int precision) {
       {0, 0},   // ee_mumu (single variant)
       {0, 0},   // gg_ttx:   FP64 v0, mixed v0
       {0, 2},   // gg_ttxg:  FP64 v0, mixed v2 (min 3 blocks/SM)
-      {0, 5},   // gg_ttxgg: FP64 v0, mixed v5 (tensor-core colour form, min 3 blocks/SM)
+      {0, 0},   // gg_ttxgg: FP64 v0, mixed v0
   };
   return table[kind][precision == REX_MIXED ? 1 : 0];
 }

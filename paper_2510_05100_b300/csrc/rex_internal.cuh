@@ -91,7 +91,7 @@ int launch_multi(int mixed, int width, int blocks, const MultiLaunch& ml, unsign
                  void* stream);
 
 // Thread-mapping variants of the QCD kernels (see qcd_kernel.cuh).
-constexpr int QCD_NVARIANT = 7;
+constexpr int QCD_NVARIANT = 9;
 
 // Launchers (defined in the kernel translation units).  Return cudaError_t as int.
 int launch_gg_ttx(int mixed, int variant, const double* mom, const double* w_in, int64_t nev,

@@ -234,7 +234,7 @@ def test_every_kernel_variant(rex, proc, precision):
     ref = oracle_rw.reweight(proc, mom, w, ORIG_QCD, pts)
     p = make(proc, rex, precision)
     tol = FP64_TOL if precision == 0 else MIXED_TOL[proc]
-    assert p.num_variants == 7
+    assert p.num_variants == 9
     for v in range(p.num_variants):
         p.variant = v
         got = p.reweight(dev(mom), dev(w), pts).cpu().numpy()
@@ -250,10 +250,10 @@ def test_autotune_picks_the_fastest_variant(rex):
     out = torch.empty((n, 16), dtype=torch.float64, device="cuda")
     p = make("gg_ttxg", rex, 1)
     ms = p.autotune(mom, w, ps.grid_gg_ttxg(), out)
-    assert len(ms) == 7 and all(t > 0 for t in ms)
+    assert len(ms) == 9 and all(t > 0 for t in ms)
     assert p.variant == int(np.argmin(ms))
     with pytest.raises(rex.RexError):
-        p.variant = 7
+        p.variant = 9
 
 
 def test_fp64_tolerance_rule_on_ill_conditioned_events(rex):
