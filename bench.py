@@ -265,6 +265,8 @@ def run_multi_leg(dev, stream, steps, world, barrier, max_over_ranks):
                         torch.empty((n, len(pts)), dtype=torch.float64, device=dev)))
     m = rex.Multi(rex.MIXED)          # ee_mumu (FP64 only) joins the mixed launch
     m.capture(batches, pts)
+    ms_streams = rex.Multi(rex.MIXED, rex.MULTI_STREAMS)   # one launch per batch, forked streams
+    ms_streams.capture(batches, pts)
     units = sum(b[1].shape[0] for b in batches) * len(pts)
 
     def timed(fn):
@@ -291,12 +293,19 @@ def run_multi_leg(dev, stream, steps, world, barrier, max_over_ranks):
 
     ms_graph = timed(graph_step)
     ms_seq = timed(sequential_step)
+    ms_str = timed(lambda: ms_streams.replay(stream))
     m.close()
+    ms_streams.close()
     return {"workload": "10k ee_mumu (FP64) + 1M gg_ttx + 500k gg_ttxg + 100k gg_ttxgg (mixed) x 64 points",
             "value": rdist.job_throughput(units, world, ms_graph * 1e-3), "unit": UNIT,
             "ms_per_step": ms_graph, "graph_launches_per_step": 1, "kernel_launches_per_step": 1,
             "sequential_value": rdist.job_throughput(units, world, ms_seq * 1e-3),
-            "sequential_ms_per_step": ms_seq, "steps": steps}
+            "sequential_ms_per_step": ms_seq,
+            "streams_graph_value": rdist.job_throughput(units, world, ms_str * 1e-3),
+            "streams_graph_ms_per_step": ms_str,
+            "note": "value: the persistent kernel (one launch, one register budget for every process); "
+                    "streams_graph: one graph of per-process launches on forked streams",
+            "steps": steps}
 
 
 def run_surrogate_leg(dev, stream, world, max_over_ranks, tau=0.02):
