@@ -66,8 +66,8 @@ PEAKS = _measured_peaks()
 TRAFFIC = {
     # ncu --set full of profile_case at 2^19 events (FP64, scaled x2 by events) and
     # 2^20 events (mixed); summaries of both captures are under profiles/
-    ("gg_ttxg", "fp64"): {"bytes_per_launch": 2 * (89.822464e6 + 35.601664e6), "source_hash": "7ff84afe0cfae707"},
-    ("gg_ttxg", "mixed"): {"bytes_per_launch": 176.713728e6 + 100.014336e6, "source_hash": "7ff84afe0cfae707"},
+    ("gg_ttxg", "fp64"): {"bytes_per_launch": 2 * (89.659136e6 + 35.451904e6), "source_hash": "cc669a8b0247879f"},
+    ("gg_ttxg", "mixed"): {"bytes_per_launch": 177.336576e6 + 102.396416e6, "source_hash": "cc669a8b0247879f"},
 }
 
 
