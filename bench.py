@@ -595,6 +595,12 @@ def run_ours(args, world, rank, local):
         e1.record(stream)
         torch.cuda.synchronize(dev)
         t = e0.elapsed_time(e1) * 1e-3 / reps
+        # a sample spread over the ranks: gather and merge the states (the one exchange)
+        t0x = time.perf_counter()
+        merged = rdist.allgather_merge_xsec_state(xs.get_state(stream=stream), k, rex.xsec_merge_states,
+                                                  device=dev)
+        xs.set_state(merged, stream=stream)
+        t_exchange = time.perf_counter() - t0x
         sig, dsig, fb = xs.result(1.0, 0.01, stream=stream)
         xs.close()
         del w_out
@@ -603,6 +609,7 @@ def run_ours(args, world, rank, local):
         p64 = SM_COUNT * FP64_FMA_PER_SM_CLK * 2 * SM_MAX_MHZ * 1e6
         xsec = {"workload": f"sigma', dsigma' of {k} points over the headline's {args.nev} events",
                 "value": args.nev * k / t, "unit": UNIT, "ms_per_call": t * 1e3, "fallback_points": int(fb.sum()),
+                "state_exchange_ms": t_exchange * 1e3, "ranks_merged": world,
                 "roofline": {"bound": "alu", "pipe": "FP64", "achieved": flops / t / 1e12, "peak": p64 / 1e12,
                              "unit": "TFLOP/s", "frac": flops / t / p64,
                              "hbm_gbs": nbytes / t / 1e9, "hbm_frac": nbytes / t / 1e9 / PEAKS["hbm_gbs"]

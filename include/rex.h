@@ -254,6 +254,20 @@ int rex_xsec_accumulate(rex_xsec *x, const double *w_in, const double *w_out, in
 int rex_xsec_result(rex_xsec *x, double sigma, double dsigma, double *sigma_out, double *dsigma_out,
                     int *fallback, void *stream);
 
+/* The accumulator's statistics as 5k + 3 doubles: per point j, (n, mean of w',
+ * sum of squared deviations of w', sum of w', sum of w'/w), then (events, events
+ * with w != 0, sum of w).  get_state copies them to host and synchronises stream;
+ * set_state replaces them from host and synchronises stream.  Used to combine the
+ * accumulations of several GPUs (one process per GPU): every rank gathers all
+ * states and merges them in rank order with rex_xsec_merge_states. */
+int rex_xsec_get_state(rex_xsec *x, double *state, void *stream);
+int rex_xsec_set_state(rex_xsec *x, const double *state, void *stream);
+
+/* out = state a merged with state b (host arrays of 5k + 3 doubles; out may be a
+ * or b), with the pairwise update of Chan, Golub & LeVeque for the moments.  Host
+ * only: needs no GPU. */
+int rex_xsec_merge_states(const double *a, const double *b, int k, double *out);
+
 void rex_xsec_free(rex_xsec *x);
 
 /* ---- LHE front-end (host; Sec. 2 and Sec. 3.1) ------------------------------

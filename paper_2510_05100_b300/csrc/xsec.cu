@@ -305,6 +305,40 @@ int rex_xsec_result(rex_xsec* x, double sigma, double dsigma, double* sigma_out,
   return e == cudaSuccess ? REX_OK : xfail(REX_ECUDA, "result: %s", cudaGetErrorString(e));
 }
 
+int rex_xsec_get_state(rex_xsec* x, double* state, void* stream) {
+  if (!x || !state) return xfail(REX_EINVAL, "null argument");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  static_assert(sizeof(Moments) == 5 * sizeof(double) && sizeof(Scalars) == 3 * sizeof(double), "packed state");
+  cudaError_t e = cudaMemcpyAsync(state, x->acc, sizeof(Moments) * x->k, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(state + 5 * (size_t)x->k, x->asc, sizeof(Scalars), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  return e == cudaSuccess ? REX_OK : xfail(REX_ECUDA, "get_state: %s", cudaGetErrorString(e));
+}
+
+int rex_xsec_set_state(rex_xsec* x, const double* state, void* stream) {
+  if (!x || !state) return xfail(REX_EINVAL, "null argument");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaMemcpyAsync(x->acc, state, sizeof(Moments) * x->k, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(x->asc, state + 5 * (size_t)x->k, sizeof(Scalars), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  return e == cudaSuccess ? REX_OK : xfail(REX_ECUDA, "set_state: %s", cudaGetErrorString(e));
+}
+
+int rex_xsec_merge_states(const double* a, const double* b, int k, double* out) {
+  if (!a || !b || !out || k < 1) return xfail(REX_EINVAL, "bad arguments");
+  for (int j = 0; j < k; ++j) {
+    Moments ma, mb;
+    std::memcpy(&ma, a + 5 * (size_t)j, sizeof ma);
+    std::memcpy(&mb, b + 5 * (size_t)j, sizeof mb);
+    const Moments m = merge(ma, mb);
+    std::memcpy(out + 5 * (size_t)j, &m, sizeof m);
+  }
+  for (int i = 0; i < 3; ++i) out[5 * (size_t)k + i] = a[5 * (size_t)k + i] + b[5 * (size_t)k + i];
+  return REX_OK;
+}
+
 void rex_xsec_free(rex_xsec* x) {
   if (!x) return;
   cudaFree(x->acc);

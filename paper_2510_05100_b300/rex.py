@@ -47,7 +47,7 @@ EXPORTS = (
     "rex_surrogate_save", "rex_surrogate_load",
     "rex_surrogate_free",
     "rex_xsec_last_error", "rex_xsec_create", "rex_xsec_reset", "rex_xsec_accumulate", "rex_xsec_result",
-    "rex_xsec_free",
+    "rex_xsec_free", "rex_xsec_get_state", "rex_xsec_set_state", "rex_xsec_merge_states",
     "rex_lhe_last_error", "rex_lhe_read", "rex_lhe_num_events", "rex_lhe_extract", "rex_lhe_set_weights",
     "rex_lhe_write", "rex_lhe_free",
 )
@@ -182,6 +182,12 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.rex_lhe_write.restype = ctypes.c_int
     lib.rex_lhe_free.argtypes = [vp]
     lib.rex_lhe_free.restype = None
+    lib.rex_xsec_get_state.argtypes = [vp, vp, vp]
+    lib.rex_xsec_get_state.restype = ctypes.c_int
+    lib.rex_xsec_set_state.argtypes = [vp, vp, vp]
+    lib.rex_xsec_set_state.restype = ctypes.c_int
+    lib.rex_xsec_merge_states.argtypes = [vp, vp, ctypes.c_int, vp]
+    lib.rex_xsec_merge_states.restype = ctypes.c_int
     lib.rex_xsec_free.argtypes = [vp]
     lib.rex_xsec_free.restype = None
     lib.rex_surrogate_free.argtypes = [vp]
@@ -474,6 +480,20 @@ class XSec:
     def accumulate(self, w_in, w_out, stream=None) -> None:
         _xcheck(load().rex_xsec_accumulate(self._h, _ptr(w_in), _ptr(w_out), w_in.shape[0], _stream_ptr(stream)))
 
+    def get_state(self, stream=None):
+        """The accumulated statistics, 5k + 3 doubles (see rex_xsec_get_state)."""
+        import numpy as np
+        st = np.empty(5 * self.k + 3)
+        _xcheck(load().rex_xsec_get_state(self._h, st.ctypes.data, _stream_ptr(stream)))
+        return st
+
+    def set_state(self, state, stream=None) -> None:
+        import numpy as np
+        st = np.ascontiguousarray(state, dtype=np.float64)
+        if st.size != 5 * self.k + 3:
+            raise ValueError(f"state must hold {5 * self.k + 3} doubles")
+        _xcheck(load().rex_xsec_set_state(self._h, st.ctypes.data, _stream_ptr(stream)))
+
     def result(self, sigma: float, dsigma: float, stream=None):
         """(sigma' [k], dsigma' [k], fallback [k] bool) as numpy arrays."""
         import numpy as np
@@ -538,6 +558,16 @@ class Lhe:
 
     def write(self, path: str) -> None:
         _lcheck(load().rex_lhe_write(self._h, os.fsencode(path)))
+
+
+def xsec_merge_states(a, b, k: int):
+    """State a merged with state b (host only; rex_xsec_merge_states)."""
+    import numpy as np
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    out = np.empty_like(a)
+    _xcheck(load().rex_xsec_merge_states(a.ctypes.data, b.ctypes.data, int(k), out.ctypes.data))
+    return out
 
 
 def probe_fma(fp64: bool, stream=None) -> float:

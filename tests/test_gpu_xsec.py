@@ -120,3 +120,24 @@ def test_on_the_benchmark_weights(rex):
     rs, rds, rfb = oracle_xsec.reweighted_xsec(w.cpu().numpy(), wn.cpu().numpy(), 10.0, 0.3)
     assert np.array_equal(fb, rfb) and not fb.any()
     assert np.max(rel(s, rs)) < TOL and np.max(rel(ds, rds)) < TOL
+
+
+def test_state_round_trip_and_merge_of_two_accumulators(rex):
+    """Two accumulators over the halves of a sample (as two GPUs would hold them),
+    their states merged on the host and loaded into a third: the result of the whole
+    sample.  A state read and written back is unchanged, bit for bit."""
+    w, wn = sample(30001, 12, 21)
+    dw, dwn = torch.from_numpy(w).cuda(), torch.from_numpy(wn).cuda()
+    a, b, c = rex.XSec(12), rex.XSec(12), rex.XSec(12)
+    a.accumulate(dw[:14000], dwn[:14000])
+    b.accumulate(dw[14000:], dwn[14000:])
+    sa, sb = a.get_state(), b.get_state()
+    c.set_state(rex.xsec_merge_states(sa, sb, 12))
+    s, ds, fb = c.result(4.0, 0.2)
+    rs, rds, rfb = oracle_xsec.reweighted_xsec(w, wn, 4.0, 0.2)
+    assert np.array_equal(fb, rfb)
+    assert np.max(rel(s, rs)) < TOL and np.max(rel(ds, rds)) < TOL
+    a.set_state(sa)
+    assert np.array_equal(a.get_state(), sa)
+    for x in (a, b, c):
+        x.close()
