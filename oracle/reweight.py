@@ -9,7 +9,7 @@ from __future__ import annotations
 
 import numpy as np
 
-from . import ee, qcd
+from . import ee, qcd, qq
 
 QCD_PROCESSES = {"gg_ttx": 4, "gg_ttxg": 5, "gg_ttxgg": 6}
 
@@ -22,6 +22,8 @@ def me2(process: str, p: np.ndarray, point: dict) -> np.ndarray:
         if p.shape[1] != QCD_PROCESSES[process]:
             raise ValueError(f"{process} expects {QCD_PROCESSES[process]} particles")
         return qcd.me2(p, point["mt"], point.get("wt", 0.0), point["alphas"])
+    if process == "qq_ttx":
+        return qq.me2(p, point["mt"], point.get("wt", 0.0), point["alphas"])
     raise ValueError(f"unknown process {process!r}")
 
 

@@ -3,8 +3,10 @@
 * e+e- -> mu+mu- via photon + Z: textbook helicity amplitudes for massless
   fermions (Peskin & Schroeder Sec. 5.2; the Z adds a chiral coupling and a
   Breit-Wigner propagator).
-* g g -> Q Q~: the Combridge (1979) formula as printed in Ellis, Stirling &
-  Webber, "QCD and collider physics", Ch. 10 (spin and colour averaged).
+* g g -> Q Q~ and q q~ -> Q Q~: the Combridge (1979) formulas as printed in
+  Ellis, Stirling & Webber, "QCD and collider physics", Ch. 10 (spin and colour
+  averaged); for q q~ -> Q Q~ also the trace form of the same result, which
+  holds for any on-shell heavy-quark momenta (momentum conservation unused).
 * g g -> q q~ + n g, massless: colour-ordered Parke-Taylor amplitudes in the
   spinor-helicity formalism (Mangano & Parke, Phys. Rept. 200 (1991) 301;
   Dixon, TASI 1995 lectures, hep-ph/9601359) with the colour decomposition
@@ -66,6 +68,37 @@ def gg_qq_combridge(p, m, alphas):
     rho = 4.0 * m * m / s
     return gs2 * gs2 * (1.0 / (6.0 * t1 * t2) - 3.0 / 8.0) * (t1 * t1 + t2 * t2 + rho
                                                               - rho * rho / (4.0 * t1 * t2))
+
+
+def qq_qq_combridge(p, m, alphas):
+    """q q~ -> Q Q~: g_s^4 (4/9)(t1^2 + t2^2 + rho/2), t_i = 2 k_i.p_Q / s, rho = 4 m^2 / s."""
+    gs2 = 4.0 * math.pi * alphas
+    k1, k2, pq = p[:, 0], p[:, 1], p[:, 2]
+    s = mdot(k1 + k2, k1 + k2)
+    t1 = 2.0 * mdot(k1, pq) / s
+    t2 = 2.0 * mdot(k2, pq) / s
+    return gs2 * gs2 * 4.0 / 9.0 * (t1 * t1 + t2 * t2 + 2.0 * m * m / s)
+
+
+def qq_qq_trace(k1, k2, pq, pqb, m, alphas):
+    """The same |M|^2 from the Dirac traces, (1/36) g^4 * 2 * 32 [(k1.pq)(k2.pqb) +
+    (k1.pqb)(k2.pq) + m^2 k1.k2] / s^2, for massless k1, k2 and any pq, pqb of mass m."""
+    gs2 = 4.0 * math.pi * alphas
+    s = mdot(k1 + k2, k1 + k2)
+    tr = 32.0 * (mdot(k1, pq) * mdot(k2, pqb) + mdot(k1, pqb) * mdot(k2, pq) + m * m * mdot(k1, k2))
+    return gs2 * gs2 * 2.0 * tr / (36.0 * s * s)
+
+
+def light_cone_mass_shift(p, m):
+    """The momentum of mass m with the direction and the light-cone component E + |p| of p:
+    E' + |p'| = E + |p|, E' - |p'| = m^2 / (E + |p|)."""
+    a = np.linalg.norm(p[..., 1:], axis=-1)
+    plus = p[..., 0] + a
+    minus = m * m / plus
+    out = np.empty_like(p)
+    out[..., 0] = 0.5 * (plus + minus)
+    out[..., 1:] = p[..., 1:] * (0.5 * (plus - minus) / a)[..., None]
+    return out
 
 
 # ----------------------------------------------------------------------------
