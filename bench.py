@@ -192,6 +192,7 @@ def main():
     ap.add_argument("--no-surrogate", action="store_true")
     ap.add_argument("--no-xsec", action="store_true")
     ap.add_argument("--no-lhe", action="store_true")
+    ap.add_argument("--no-qq", action="store_true", help="skip the q q~ -> t t~ leg")
     args = ap.parse_args()
     world, rank, local = rdist.env()
     if args.impl == "reference":
@@ -435,6 +436,51 @@ def run_lhe_leg(dev, stream, pts, nev=100_000):
             "threads": os.cpu_count(), "note": "file to file through the public API; read/extract/write on the host"}
 
 
+def run_qq_leg(dev, stream, pts, steps, nev=NEV):
+    """q q~ -> t t~, the other leading-order channel of p p -> t t~, on the headline's
+    points: nev events per launch in FP64 and in mixed precision, each timed with CUDA
+    events on the launching stream, with its roofline (FP64 pipe / HBM)."""
+    import torch
+    from paper_2510_05100_b300 import flops as flopmod
+    from paper_2510_05100_b300 import rex
+    k = len(pts)
+    mom = torch.from_numpy(ps.make_events("qq_ttx", nev, SEED + 100)).to(dev)
+    w_in = torch.ones(nev, dtype=torch.float64, device=dev)
+    w_out = torch.empty((nev, k), dtype=torch.float64, device=dev)
+    amp = flopmod.per_event("qq_ttx", 1)["amp"]   # per-event constants (FP64 or FP32)
+    per_point = 7                                 # FP64 polynomial, coupling factor and ratio
+    nbytes = nev * (16 * 8 + 8 + 8 * k)           # momenta + w_in read, w_out written
+    p64 = SM_COUNT * FP64_FMA_PER_SM_CLK * 2 * SM_MAX_MHZ * 1e6
+    out = {"workload": f"q q~ -> t t~, {nev} events x {k} points (the headline's grid and original point); "
+                       "inputs + outputs exceed L2"}
+    for name, prec in (("fp64", rex.FP64), ("mixed", rex.MIXED)):
+        proc = rex.Process("qq_ttx", prec)
+        proc.set_params(ORIGINAL)
+        for _ in range(3):
+            proc.reweight(mom, w_in, pts, w_out=w_out, stream=stream)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        torch.cuda.synchronize(dev)
+        for a, b in ev:
+            a.record(stream)
+            proc.reweight(mom, w_in, pts, w_out=w_out, stream=stream)
+            b.record(stream)
+        torch.cuda.synchronize(dev)
+        proc.close()
+        t = statistics.mean(a.elapsed_time(b) for a, b in ev) * 1e-3
+        hbm = nbytes / t / 1e9
+        if prec == rex.FP64:
+            fl = (amp + per_point * k) * nev
+            roof = {"bound": "alu", "pipe": "FP64 FMA", "achieved": fl / t / 1e12, "peak": p64 / 1e12,
+                    "unit": "TFLOP/s", "frac": fl / t / p64, "flops_per_launch": fl}
+        else:
+            roof = {"bound": "hbm", "achieved": hbm, "peak": PEAKS.get("hbm_gbs"), "unit": "GB/s",
+                    "frac": hbm / PEAKS["hbm_gbs"] if PEAKS.get("hbm_gbs") else None,
+                    "fp32_flops_per_launch": amp * nev, "fp64_flops_per_launch": per_point * k * nev}
+        roof["algorithmic_bytes_per_launch"] = nbytes
+        out[name] = {"value": nev * k / t, "unit": UNIT, "ms_per_launch": t * 1e3, "roofline": roof}
+    return out
+
+
 def run_ours(args, world, rank, local):
     cpu_pool = None
     cores = os.cpu_count() or 1
@@ -616,6 +662,7 @@ def run_ours(args, world, rank, local):
                              if PEAKS.get("hbm_gbs") else None}}
 
     lhe_leg = None if args.no_lhe else run_lhe_leg(dev, stream, pts)
+    qq_leg = None if args.no_qq else run_qq_leg(dev, stream, pts, max(5, args.steps // 2))
 
     multi = None if args.no_multi else run_multi_leg(dev, stream, max(3, args.steps // 2), world, barrier,
                                                      max_over_ranks)
@@ -645,7 +692,7 @@ def run_ours(args, world, rank, local):
                 "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                         "entry_point": "rex_reweight_host (pinned host buffers)"},
                 "gpu_launches": args.steps, "roofline": roofline, "cpu_baseline": cpu, "modes": extra,
-                "multi": multi, "surrogate": surrogate, "xsec": xsec, "lhe": lhe_leg}
+                "multi": multi, "surrogate": surrogate, "xsec": xsec, "lhe": lhe_leg, "qq_ttx": qq_leg}
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist

@@ -63,10 +63,11 @@ extern "C" {
 typedef struct rex_proc rex_proc; /* opaque, library-owned */
 
 /* One parameter point.  Fields a process does not use are ignored.
- *   QCD processes (gg_ttx, gg_ttxg, gg_ttxgg): mt, wt (top mass and width,
- *     GeV), alphas (strong coupling, fixed; g_s = sqrt(4 pi alphas)).
+ *   QCD processes (gg_ttx, gg_ttxg, gg_ttxgg, qq_ttx): mt, wt (top mass and
+ *     width, GeV), alphas (strong coupling, fixed; g_s = sqrt(4 pi alphas)).
  *     mt enters the top propagators and the external top spinors; momenta
- *     are kept as given.
+ *     are kept as given.  qq_ttx has no top propagator: wt is checked and
+ *     ignored.
  *   ee_mumu: mz, wz (Z mass and width, GeV), sw2 (sin^2 theta_W),
  *     alpha (electromagnetic coupling); independent inputs, cW^2 = 1 - sW^2. */
 typedef struct {
@@ -78,7 +79,10 @@ typedef struct {
  * name: "ee_mumu"  e+(1) e-(2) -> mu+(3) mu-(4), photon + Z, massless leptons;
  *       "gg_ttx"   g(1) g(2) -> t(3) t~(4);
  *       "gg_ttxg"  g(1) g(2) -> t(3) t~(4) g(5);
- *       "gg_ttxgg" g(1) g(2) -> t(3) t~(4) g(5) g(6).
+ *       "gg_ttxgg" g(1) g(2) -> t(3) t~(4) g(5) g(6);
+ *       "qq_ttx"   q(1) q~(2) -> t(3) t~(4), massless light quark, one
+ *                  s-channel gluon (the other leading-order channel of
+ *                  p p -> t t~, Sec. 5).
  * precision: REX_FP64 or REX_MIXED.
  * On success *out receives a handle the caller releases with rex_free_process.
  * Errors: REX_EINVAL (null out, unknown name or precision). */
@@ -125,7 +129,7 @@ int rex_me2(rex_proc *proc, const double *momenta, int64_t nev,
             const rex_params *point, double *me2_out, void *stream);
 
 /* Kernel thread-mapping variants (QCD processes: lanes per event and
- * register budget; ee_mumu has one).  Every variant computes the same
+ * register budget; ee_mumu and qq_ttx have one).  Every variant computes the same
  * result; they differ only in speed.  rex_num_variants returns the count,
  * rex_get_variant / rex_set_variant read and select the handle's variant.
  * Errors: REX_EINVAL (bad handle or index). */

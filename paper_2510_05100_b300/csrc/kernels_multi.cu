@@ -2,18 +2,21 @@
 //
 // One launch reweights several subprocess batches of uneven size (e.g. 10k
 // e+e- -> mu+mu-, 1M g g -> t t~, 500k g g -> t t~ g, 100k g g -> t t~ g g) to the
-// same parameter points.  The paper runs subprocesses one after another and
+// same parameter points (q q~ -> t t~ batches too).  The paper runs subprocesses one after another and
 // finds multi-channel GPU runs latency bound (Sec. 4.2); here every (batch,
 // event tile) is a work item of a single persistent grid (one block per SM
 // slot), and blocks take items from a global atomic counter in
 // heaviest-process-first order so that the cheap tiles fill the tail.
-// The per-tile code is exactly the single-process kernels' (QcdTile, ee_tile).
+// The per-tile code is exactly the single-process kernels' (QcdTile, QqTile, ee_tile).
 #include <cuda_runtime.h>
 
 #include "ee_kernel.cuh"
 #include "qcd_kernel.cuh"
+#include "qq_kernel.cuh"
 
 namespace rex {
+
+static_assert(QQ_BLOCK == QCD_BLOCK, "every tile runs on the multi kernel's block size");
 
 template <typename R, bool WIDTH, int MINB, int S_TTX, int S_TTXG, int S_TTXGG, bool TC_TTXGG>
 __global__ void __launch_bounds__(QCD_BLOCK, MINB)
@@ -21,10 +24,12 @@ __global__ void __launch_bounds__(QCD_BLOCK, MINB)
   using T1 = QcdTile<PROC_GG_TTX, R, WIDTH, S_TTX>;
   using T2 = QcdTile<PROC_GG_TTXG, R, WIDTH, S_TTXG>;
   using T3 = QcdTile<PROC_GG_TTXGG, R, WIDTH, S_TTXGG, TC_TTXGG>;
+  using T4 = QqTile<R>;
   union Smem {
     typename T1::Smem a;
     typename T2::Smem b;
     typename T3::Smem c;
+    typename T4::Smem d;
   };
   __shared__ Smem sm;
   __shared__ unsigned long long item_s;
@@ -43,6 +48,7 @@ __global__ void __launch_bounds__(QCD_BLOCK, MINB)
       case PROC_GG_TTX: T1::run(sm.a, B.mom, B.w_in, B.nev, tile, B.t, B.out); break;
       case PROC_GG_TTXG: T2::run(sm.b, B.mom, B.w_in, B.nev, tile, B.t, B.out); break;
       case PROC_GG_TTXGG: T3::run(sm.c, B.mom, B.w_in, B.nev, tile, B.t, B.out); break;
+      case PROC_QQ_TTX: T4::run(sm.d, B.mom, B.w_in, B.nev, tile, B.t, B.out); break;
       default: break;
     }
     __syncthreads();
@@ -80,6 +86,7 @@ int multi_events_per_tile(int kind, int mixed) {
     case PROC_GG_TTX: return QCD_BLOCK / (4 << (mixed ? MultiSplit<float>::TTX : 0));
     case PROC_GG_TTXG: return QCD_BLOCK / (8 << (mixed ? MultiSplit<float>::TTXG : 0));
     case PROC_GG_TTXGG: return QCD_BLOCK / (16 << (mixed ? MultiSplit<float>::TTXGG : 0));
+    case PROC_QQ_TTX: return QqTile<float>::EPB;
     default: return 0;
   }
 }

@@ -67,19 +67,25 @@ const ProcInfo kProcs[] = {
     {"gg_ttx", PROC_GG_TTX, 4, gg_ttx_info::NGLUON, gg_ttx_info::COLOUR_DEN},
     {"gg_ttxg", PROC_GG_TTXG, 5, gg_ttxg_info::NGLUON, gg_ttxg_info::COLOUR_DEN},
     {"gg_ttxgg", PROC_GG_TTXGG, 6, gg_ttxgg_info::NGLUON, gg_ttxgg_info::COLOUR_DEN},
+    {"qq_ttx", PROC_QQ_TTX, 4, 0, 1},
 };
+static_assert(sizeof(kProcs) / sizeof(kProcs[0]) == PROC_LAST + 1, "one table row per process kind");
 
 const ProcInfo& info_of(int kind) { return kProcs[kind]; }
+
+// processes with one kernel (no thread-mapping variants to choose from)
+bool single_variant(int kind) { return kind == PROC_EE_MUMU || kind == PROC_QQ_TTX; }
 
 // Default thread-mapping variant per (process, precision), the fastest of every
 // variant timed on a B300 at 2^20 (gg_ttx, gg_ttxg) / 2^16 (gg_ttxgg) events;
 // rex_autotune picks again on the caller's device and data.
 int default_variant(int kind, int precision) {
-  static const int table[4][2] = {
+  static const int table[PROC_LAST + 1][2] = {
       {0, 0},   // ee_mumu (single variant)
       {0, 0},   // gg_ttx:   FP64 v0, mixed v0
       {0, 2},   // gg_ttxg:  FP64 v0, mixed v2 (min 3 blocks/SM)
       {0, 0},   // gg_ttxgg: FP64 v0, mixed v0
+      {0, 0},   // qq_ttx (single variant)
   };
   return table[kind][precision == REX_MIXED ? 1 : 0];
 }
@@ -91,6 +97,7 @@ int launch_qcd(const rex_proc* p, const double* mom, const double* w_in, int64_t
     case PROC_GG_TTX: return launch_gg_ttx(mixed, p->variant, mom, w_in, nev, lp, out, stream);
     case PROC_GG_TTXG: return launch_gg_ttxg(mixed, p->variant, mom, w_in, nev, lp, out, stream);
     case PROC_GG_TTXGG: return launch_gg_ttxgg(mixed, p->variant, mom, w_in, nev, lp, out, stream);
+    case PROC_QQ_TTX: return launch_qq_ttx(mixed, mom, w_in, nev, lp, out, stream);
     default: return (int)cudaErrorInvalidValue;
   }
 }
@@ -98,9 +105,11 @@ int launch_qcd(const rex_proc* p, const double* mom, const double* w_in, int64_t
 bool aligned8(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 7u) == 0; }
 bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
-// avg * (4 pi alphas)^n / colour_den for a pure-gluon tree amplitude with n gluons
+// avg * (4 pi alphas)^n / colour_den for a pure-gluon tree amplitude with n gluons;
+// q q~ -> t t~: (4 pi alphas)^2 * colour sum (N^2 - 1)/4 = 2 / (4 spins * 9 colours)
 double qcd_factor(const ProcInfo& pi, double alphas) {
   const double gs2 = 4.0 * M_PI * alphas;
+  if (pi.kind == PROC_QQ_TTX) return gs2 * gs2 * 2.0 / 36.0;
   double f = 1.0;
   for (int i = 0; i < pi.ngluon; ++i) f *= gs2;
   int nfinal = pi.ngluon - 2;
@@ -206,7 +215,7 @@ int run_ee_chunk(rex_proc* p, const double* mom, const double* w_in, int64_t nev
 
 int validate_proc(const rex_proc* p) {
   if (!p) return fail(REX_EINVAL, "null process handle");
-  if (p->kind < 0 || p->kind > PROC_GG_TTXGG) return fail(REX_EINVAL, "corrupt process handle");
+  if (p->kind < 0 || p->kind > PROC_LAST) return fail(REX_EINVAL, "corrupt process handle");
   return REX_OK;
 }
 
@@ -342,8 +351,8 @@ int multi_impl(rex_multi* m, const rex_batch* batches, int nbatch, const rex_par
   const int mixed_p = m->precision == REX_MIXED;
   double tile_cost[MULTI_MAX_BATCH];
   for (int i = 0; i < nbatch; ++i) {
-    static const double flops_per_event_slot[4] = {160.0, 5.0e3, 4.8e4, 5.7e5};   // per mass slot
-    static const double flops_per_event_fixed[4] = {6.4e3, 4.0e2, 6.6e3, 1.1e5};
+    static const double flops_per_event_slot[PROC_LAST + 1] = {160.0, 5.0e3, 4.8e4, 5.7e5, 3.0};   // per mass slot
+    static const double flops_per_event_fixed[PROC_LAST + 1] = {6.4e3, 4.0e2, 6.6e3, 1.1e5, 6.0e2};
     const int kind = batches[i].proc->kind;
     const double rate = (kind == PROC_EE_MUMU || !mixed_p) ? 1.0 : 64.0;
     const double slots = kind == PROC_EE_MUMU ? (k < MULTI_MAX_POINTS ? k : MULTI_MAX_POINTS) + 1.0 : 9.0;
@@ -690,19 +699,19 @@ int rex_me2(rex_proc* proc, const double* momenta, int64_t nev, const rex_params
 int rex_num_variants(const rex_proc* proc) {
   const int rc = validate_proc(proc);
   if (rc) return rc;
-  return proc->kind == PROC_EE_MUMU ? 1 : QCD_NVARIANT;
+  return single_variant(proc->kind) ? 1 : QCD_NVARIANT;
 }
 
 int rex_get_variant(const rex_proc* proc) {
   const int rc = validate_proc(proc);
   if (rc) return rc;
-  return proc->kind == PROC_EE_MUMU ? 0 : proc->variant;
+  return single_variant(proc->kind) ? 0 : proc->variant;
 }
 
 int rex_set_variant(rex_proc* proc, int variant) {
   const int rc = validate_proc(proc);
   if (rc) return rc;
-  const int n = proc->kind == PROC_EE_MUMU ? 1 : QCD_NVARIANT;
+  const int n = single_variant(proc->kind) ? 1 : QCD_NVARIANT;
   if (variant < 0 || variant >= n) return fail(REX_EINVAL, "variant %d out of range [0, %d)", variant, n);
   proc->variant = variant;
   return REX_OK;
@@ -712,7 +721,7 @@ int rex_autotune(rex_proc* proc, const double* momenta, const double* w_in, int6
                  const rex_params* param_sets, int k, double* w_out, void* stream, float* ms_out) {
   int rc = validate_proc(proc);
   if (rc) return rc;
-  if (proc->kind == PROC_EE_MUMU) return REX_OK;
+  if (single_variant(proc->kind)) return REX_OK;
   if (nev <= 0 || k <= 0) return fail(REX_EINVAL, "autotune needs nev > 0 and k > 0");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   cudaEvent_t e0, e1;

@@ -10,12 +10,14 @@ namespace rex {
 constexpr int MAX_MASS = 64;
 constexpr int MAX_POINTS = 256;
 
-enum ProcKind : int { PROC_EE_MUMU = 0, PROC_GG_TTX = 1, PROC_GG_TTXG = 2, PROC_GG_TTXGG = 3 };
+enum ProcKind : int { PROC_EE_MUMU = 0, PROC_GG_TTX = 1, PROC_GG_TTXG = 2, PROC_GG_TTXGG = 3, PROC_QQ_TTX = 4 };
+constexpr int PROC_LAST = PROC_QQ_TTX;
 enum OutMode : int { OUT_RATIO = 0, OUT_ME2 = 1 };
 
 // QCD processes: the amplitude is evaluated once per mass slot (slot 0 is the
 // original point) with unit coupling; point j then takes
-//   |M|^2_j = acc[slot[j]] * factor[j],  factor = avg * (4 pi alphas)^n / colour_den.
+//   |M|^2_j = acc[slot[j]] * factor[j],  factor = avg * (4 pi alphas)^n / colour_den
+// (q q~ -> t t~: avg * (4 pi alphas)^2 * colour sum 2).
 struct QcdLaunch {
   int nmass;
   int k;
@@ -100,6 +102,8 @@ int launch_gg_ttxg(int mixed, int variant, const double* mom, const double* w_in
                    const QcdLaunch& lp, double* out, void* stream);
 int launch_gg_ttxgg(int mixed, int variant, const double* mom, const double* w_in, int64_t nev,
                     const QcdLaunch& lp, double* out, void* stream);
+int launch_qq_ttx(int mixed, const double* mom, const double* w_in, int64_t nev, const QcdLaunch& lp,
+                  double* out, void* stream);
 int launch_ee(const double* mom, const double* w_in, int64_t nev, const EwLaunch& lp,
               double* out, void* stream);
 

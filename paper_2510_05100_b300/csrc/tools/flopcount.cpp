@@ -24,6 +24,7 @@ struct Cnt {
   Cnt(double x) : v(x) {}
   template <int U>
   explicit Cnt(Cnt<U> o) : v(o.v) {}   // R -> ACC conversion is free
+  explicit operator double() const { return v; }   // R -> FP64 conversion is free
 };
 template <int TAG>
 long long Cnt<TAG>::flops = 0;
@@ -64,6 +65,7 @@ using RC = Cnt<0>;    // amplitude arithmetic
 using AC = Cnt<1>;    // colour / helicity accumulation
 
 #include "../generated/qcd_amplitudes.cuh"
+#include "../qq_amplitude.cuh"
 
 using namespace rex;
 
@@ -122,7 +124,20 @@ int main() {
   std::printf("{\n");
   REX_COUNT(gg_ttx, 2, false);
   REX_COUNT(gg_ttxg, 3, false);
-  REX_COUNT(gg_ttxgg, 4, true);
+  REX_COUNT(gg_ttxgg, 4, false);
+  {
+    // q q~ -> t t~: the per-event constants (FP64 s and 1/s^2 not counted); every
+    // point then adds the FP64 polynomial and ratio, counted by the caller
+    double p[4][4];
+    for (int i = 0; i < 4; ++i)
+      for (int m = 0; m < 4; ++m) p[i][m] = 1.0 + i + 0.1 * m;
+    double c[3];
+    RC::flops = 0;
+    qq_ttx_coefficients<RC>(p, c);
+    std::printf("  \"qq_ttx\": {\"nghel\": 1, \"event_setup\": %lld, \"mass_setup\": 0, "
+                "\"polarisations\": 0, \"gluon_currents\": 0, \"quark_line_amp\": 0, "
+                "\"quark_line_acc\": 0}\n", RC::flops);
+  }
   std::printf("}\n");
   return 0;
 }

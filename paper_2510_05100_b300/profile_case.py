@@ -5,7 +5,7 @@
   --surrogate-infer fused|layered  (surrogate inference instead)
 
 Generates the standard seeded events, then issues L rex_reweight launches to the
-16-point (gg_ttxg) / 8-point (gg_ttx) / 64-point (gg_ttxgg) grid and synchronises.
+16-point (gg_ttxg, qq_ttx) / 8-point (gg_ttx) / 64-point (gg_ttxgg) grid and synchronises.
 """
 import argparse
 import os
@@ -18,7 +18,8 @@ import torch  # noqa: E402
 from paper_2510_05100_b300 import phase_space as ps  # noqa: E402
 from paper_2510_05100_b300 import rex  # noqa: E402
 
-GRIDS = {"gg_ttx": ps.grid_gg_ttx, "gg_ttxg": ps.grid_gg_ttxg, "gg_ttxgg": ps.grid_64}
+GRIDS = {"gg_ttx": ps.grid_gg_ttx, "gg_ttxg": ps.grid_gg_ttxg, "gg_ttxgg": ps.grid_64,
+         "qq_ttx": ps.grid_gg_ttxg}
 
 
 def main():

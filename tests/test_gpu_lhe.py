@@ -16,7 +16,8 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 ORIG = dict(mt=173.0, wt=0.0, alphas=0.118)
-GRIDS = {"gg_ttx": ps.grid_gg_ttx(), "gg_ttxg": ps.grid_gg_ttxg()}
+# the q q~ and g g channels of p p -> t t~ share their weight ids, as in one reweighting run
+GRIDS = {"gg_ttx": ps.grid_gg_ttx(), "qq_ttx": ps.grid_gg_ttx(), "gg_ttxg": ps.grid_gg_ttxg()}
 
 
 @pytest.fixture(scope="module")
@@ -32,7 +33,7 @@ def wid(pt):
 
 def test_file_to_reweighted_file(rex, tmp_path):
     src, dst = str(tmp_path / "in.lhe"), str(tmp_path / "out.lhe")
-    info = lhe_synth.write_lhe(src, {"gg_ttxg": 3000, "gg_ttx": 2000, "ee_mumu": 100}, seed=5)
+    info = lhe_synth.write_lhe(src, {"gg_ttxg": 3000, "gg_ttx": 2000, "qq_ttx": 700, "ee_mumu": 100}, seed=5)
     L = rex.Lhe(src)
     gpu = {}
     for proc, pts in GRIDS.items():

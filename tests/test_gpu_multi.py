@@ -11,7 +11,7 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 ORIG_QCD = dict(mt=173.0, wt=0.0, alphas=0.118)
-SIZES = {"ee_mumu": 150, "gg_ttx": 101, "gg_ttxg": 53, "gg_ttxgg": 19}
+SIZES = {"ee_mumu": 150, "gg_ttx": 101, "gg_ttxg": 53, "gg_ttxgg": 19, "qq_ttx": 300}
 
 
 @pytest.fixture(scope="module")

@@ -24,7 +24,8 @@ def rex():
 @pytest.fixture(scope="module")
 def synth(tmp_path_factory):
     path = str(tmp_path_factory.mktemp("lhe") / "synth.lhe")
-    info = lhe_synth.write_lhe(path, {"gg_ttxg": 6000, "gg_ttx": 3000, "ee_mumu": 700, "gg_ttxgg": 500}, seed=11,
+    info = lhe_synth.write_lhe(path, {"gg_ttxg": 6000, "gg_ttx": 3000, "ee_mumu": 700, "gg_ttxgg": 500,
+                                      "qq_ttx": 800}, seed=11,
                                with_initrwgt=True)
     return path, info
 
@@ -47,7 +48,7 @@ def test_synthetic_file_matches_the_oracle_and_the_generator(rex, synth, threads
     path, info = synth
     L = rex.Lhe(path, nthreads=threads)
     doc = olhe.read(path)
-    assert L.num_events == len(doc["events"]) == 10200
+    assert L.num_events == len(doc["events"]) == 11000
     for proc, (pin, pout) in lhe_synth.PROCESSES.items():
         got = L.extract(pin, pout)
         assert same(got, olhe.extract(doc, pin, pout)), proc

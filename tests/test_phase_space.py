@@ -12,6 +12,7 @@ def _mdot(a, b):
 @pytest.mark.parametrize("proc,masses", [
     ("ee_mumu", [0, 0, 0, 0]),
     ("gg_ttx", [0, 0, 173, 173]),
+    ("qq_ttx", [0, 0, 173, 173]),
     ("gg_ttxg", [0, 0, 173, 173, 0]),
     ("gg_ttxgg", [0, 0, 173, 173, 0, 0]),
 ])
