@@ -447,8 +447,11 @@ def run_qq_leg(dev, stream, pts, steps, nev=NEV):
     mom = torch.from_numpy(ps.make_events("qq_ttx", nev, SEED + 100)).to(dev)
     w_in = torch.ones(nev, dtype=torch.float64, device=dev)
     w_out = torch.empty((nev, k), dtype=torch.float64, device=dev)
-    amp = flopmod.per_event("qq_ttx", 1)["amp"]   # per-event constants (FP64 or FP32)
-    per_point = 7                                 # FP64 polynomial, coupling factor and ratio
+    # counted flops: the per-event constants, their normalisation by the original
+    # point (polynomial, reciprocal, three products) and per point the polynomial and
+    # the weight product; FP64 in the FP64 mode, FP32 in the mixed mode
+    amp = flopmod.per_event("qq_ttx", 1)["amp"] + 8
+    per_point = 6
     nbytes = nev * (16 * 8 + 8 + 8 * k)           # momenta + w_in read, w_out written
     p64 = SM_COUNT * FP64_FMA_PER_SM_CLK * 2 * SM_MAX_MHZ * 1e6
     out = {"workload": f"q q~ -> t t~, {nev} events x {k} points (the headline's grid and original point); "
@@ -468,14 +471,14 @@ def run_qq_leg(dev, stream, pts, steps, nev=NEV):
         proc.close()
         t = statistics.mean(a.elapsed_time(b) for a, b in ev) * 1e-3
         hbm = nbytes / t / 1e9
+        fl = (amp + per_point * k) * nev
         if prec == rex.FP64:
-            fl = (amp + per_point * k) * nev
             roof = {"bound": "alu", "pipe": "FP64 FMA", "achieved": fl / t / 1e12, "peak": p64 / 1e12,
                     "unit": "TFLOP/s", "frac": fl / t / p64, "flops_per_launch": fl}
         else:
             roof = {"bound": "hbm", "achieved": hbm, "peak": PEAKS.get("hbm_gbs"), "unit": "GB/s",
                     "frac": hbm / PEAKS["hbm_gbs"] if PEAKS.get("hbm_gbs") else None,
-                    "fp32_flops_per_launch": amp * nev, "fp64_flops_per_launch": per_point * k * nev}
+                    "fp32_flops_per_launch": fl, "fp32_tflops": fl / t / 1e12}
         roof["algorithmic_bytes_per_launch"] = nbytes
         out[name] = {"value": nev * k / t, "unit": UNIT, "ms_per_launch": t * 1e3, "roofline": roof}
     return out

@@ -29,14 +29,11 @@ __device__ __forceinline__ R chis(const R* p, cx<R>* chim, cx<R>* chip) {
   return p[0] + a;
 }
 
-// (C0, C2, C4) of one event, already divided by s^2, and s itself.
+// The helicity sum of one event as C0 + C2 m^2 + C4 m^4 (c[0..2]) times the
+// incoming scale w+(1)^2 w+(2)^2 (*e12) times g^4 colour / (avg s^2), which the
+// caller applies where it needs |M|^2 itself (the ratio does not).
 template <typename R>
-__device__ __forceinline__ void qq_ttx_coefficients(const double (&pd)[4][4], double* c) {
-  R p[4][4];
-#pragma unroll
-  for (int i = 0; i < 4; ++i)
-#pragma unroll
-    for (int m = 0; m < 4; ++m) p[i][m] = R(pd[i][m]);
+__device__ __forceinline__ void qq_ttx_coefficients(const R (&p)[4][4], R* c, R* e12) {
   cx<R> x1[2][2], x2[2][2], x3[2][2], x4[2][2];   // [0] = chi-, [1] = chi+
   const R e1 = chis(p[0], x1[0], x1[1]);
   const R e2 = chis(p[1], x2[0], x2[1]);
@@ -73,20 +70,14 @@ __device__ __forceinline__ void qq_ttx_coefficients(const double (&pd)[4][4], do
     prr[q] = rr;
     plr[q] = lr;
   }
-  const R w2 = e3 * e4;       // W^2
-  const R r2 = e4 / e3;       // r^2
-  const R c0 = w2 * (prr[1] + pll[2]);
-  const R c2 = r2 * (pll[0] + prr[3]) + (prr[0] + pll[3]) / r2 - R(2) * (plr[0] + plr[1] + plr[2] + plr[3]);
-  const R c4 = (pll[1] + prr[2]) / w2;
-  // incoming scale w+(1)^2 w+(2)^2 and 1/s^2, in FP64
-  double q[4];
-#pragma unroll
-  for (int m = 0; m < 4; ++m) q[m] = pd[0][m] + pd[1][m];
-  const double s = q[0] * q[0] - q[1] * q[1] - q[2] * q[2] - q[3] * q[3];
-  const double scale = double(e1) * double(e2) / (s * s);
-  c[0] = double(c0) * scale;
-  c[1] = double(c2) * scale;
-  c[2] = double(c4) * scale;
+  // W^2 = e3 e4, r^2 = e4 / e3, with one reciprocal
+  const R w2 = e3 * e4;
+  const R iw2 = R(1) / w2;
+  const R r2 = e4 * e4 * iw2, ir2 = e3 * e3 * iw2;
+  c[0] = w2 * (prr[1] + pll[2]);
+  c[1] = r2 * (pll[0] + prr[3]) + ir2 * (prr[0] + pll[3]) - R(2) * (plr[0] + plr[1] + plr[2] + plr[3]);
+  c[2] = iw2 * (pll[1] + prr[2]);
+  *e12 = e1 * e2;
 }
 
 }  // namespace rex

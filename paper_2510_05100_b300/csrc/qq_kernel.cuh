@@ -21,11 +21,20 @@
 //       (r = w+(4)/w+(3), W = w+(3) w+(4)) the helicity sum is exactly
 //           C0 + C2 m^2 + C4 m^4,
 //       three per-event constants: every parameter point then costs two FMAs;
-//   a8  ratio epilogue w_out = w_in |M_j|^2 / |M_0|^2 (0 if |M_0|^2 == 0), one
-//       FP64 reciprocal per event, consecutive threads writing consecutive outputs.
-// The top width enters no propagator of this diagram and is ignored.  FP64 in
-// the exact mode; in the mixed mode the per-event constants are built in FP32
-// from FP32 momenta, and s, the polynomial and the epilogue stay FP64.
+//   a8  ratio epilogue w_out = w_in |M_j|^2 / |M_0|^2 (0 if |M_0|^2 == 0): s, the
+//       incoming scale and the coupling factor of the original point cancel, so
+//       the event keeps q = C / P(m0^2) and point j, with a = f_j / f_0, gives
+//           w_out = w (q0 a + q2 a m_j^2 + q4 a m_j^4);
+//       points at the original top mass (any width or alpha_s) give w a exactly.
+//       Consecutive threads write consecutive outputs.
+// The top width enters no propagator of this diagram and is ignored.
+//
+// Precision.  FP64 mode: everything in FP64.  Mixed mode: B300 issues FP64 at 1/64
+// of the FP32 rate (2 FMA per SM per clock), so the mixed tile runs no FP64
+// instruction per output or per event: momenta and weights are converted
+// FP64 <-> FP32 on the integer ALUs (IEEE-754 bit fields, round to nearest even),
+// the constants, q and the per-point polynomial are FP32, and only points at the
+// original mass take the FP64 product w a.
 #pragma once
 #include <cuda_runtime.h>
 
@@ -38,18 +47,57 @@ namespace rex {
 
 constexpr int QQ_BLOCK = 128;
 
+// FP64 -> FP32 on integer ALUs: round to nearest even; magnitudes below the FP32
+// normal range become a signed zero, above it infinity; NaN stays NaN.
+__device__ __forceinline__ float f64_to_f32_alu(double x) {
+  const unsigned long long d = (unsigned long long)__double_as_longlong(x);
+  const unsigned hi = (unsigned)(d >> 32), lo = (unsigned)d;
+  const unsigned sign = hi & 0x80000000u, ahi = hi & 0x7fffffffu;
+  unsigned f;
+  if (ahi < (897u << 20)) {                 // biased exponent < 897: |x| < 2^-126
+    f = 0u;
+  } else if (ahi >= (1151u << 20)) {        // |x| >= 2^128, infinity or NaN
+    f = (ahi >= 0x7ff00000u && ((ahi & 0xfffffu) | lo)) ? 0x7fc00000u : 0x7f800000u;
+  } else {                                  // rebias the exponent by 1023 - 127 = 896
+    f = ((ahi - (896u << 20)) << 3) | (lo >> 29);
+    const unsigned rem = lo & 0x1fffffffu;  // the 29 dropped mantissa bits
+    f += (rem > 0x10000000u) | ((rem == 0x10000000u) & f);
+  }
+  return __uint_as_float(f | sign);
+}
+
+// FP32 -> FP64 on integer ALUs: exact for normal numbers, zeros, infinities and NaN
+// (FP32 subnormals, which the conversion above never produces, become zero).
+__device__ __forceinline__ double f32_to_f64_alu(float x) {
+  const unsigned b = __float_as_uint(x);
+  const unsigned sign = b & 0x80000000u, a = b & 0x7fffffffu;
+  unsigned hi, lo = a << 29;
+  if (a < 0x00800000u) {
+    hi = 0u;
+    lo = 0u;
+  } else if (a >= 0x7f800000u) {
+    hi = 0x7ff00000u | ((a & 0x7fffffu) >> 3);
+  } else {
+    hi = (a >> 3) + (896u << 20);
+  }
+  return __hiloint2double((int)(hi | sign), (int)lo);
+}
+
 template <typename R>
 struct QqTile {
   static constexpr int EPB = QQ_BLOCK;
   static constexpr int ROW = 17;   // padded row of 16 momenta (conflict-free row reads)
+  static constexpr bool MIXED = std::is_same<R, float>::value;
 
   struct Smem {
     double mom[EPB * ROW];
-    double c[3][EPB];
-    double m0[EPB];
-    double inv0[EPB];
-    double w[EPB];
-    double pt[MAX_POINTS][2];    // (m^2, factor) per point of the launch
+    R q[3][EPB];                 // C / P(m0^2) per event (0 if |M_0|^2 == 0)
+    double w[EPB];               // w_in (0 if |M_0|^2 == 0, NaN if it is NaN)
+    float wf[EPB];               // mixed mode: w in FP32
+    R pa[MAX_POINTS][3];         // a_j, a_j m_j^2, a_j m_j^4 with a_j = f_j / f_0
+    double r[MAX_POINTS];        // a_j in FP64
+    int same[MAX_POINTS];        // point j at the original top mass
+    R m0sq;
   };
 
   template <class TABLE>
@@ -67,39 +115,73 @@ struct QqTile {
       sm.mom[row * ROW + col] = v.x;
       sm.mom[row * ROW + col + 1] = v.y;
     }
-    // a2: the launch's points (m^2, factor)
+    // a2: the launch's points
     const int k = lp.mode == OUT_RATIO ? lp.k : 0;
     for (int j = tid; j < k; j += QQ_BLOCK) {
       const double m = lp.mass[lp.slot[j]];
-      sm.pt[j][0] = m * m;
-      sm.pt[j][1] = lp.factor[j];
+      const double a = lp.factor[j] / lp.factor0;
+      const double am2 = a * (m * m);
+      sm.pa[j][0] = R(a);
+      sm.pa[j][1] = R(am2);
+      sm.pa[j][2] = R(am2 * (m * m));
+      sm.r[j] = a;
+      sm.same[j] = m == lp.mass[0];
     }
+    if (tid == 0) sm.m0sq = R(lp.mass[0] * lp.mass[0]);
     __syncthreads();
     if (tid < nblk) {
-      double p[4][4];
+      R p[4][4];
 #pragma unroll
-      for (int i = 0; i < 16; ++i) p[i >> 2][i & 3] = sm.mom[tid * ROW + i];
-      double c[3];
-      qq_ttx_coefficients<R>(p, c);
-      const double m2 = lp.mass[0] * lp.mass[0];
-      const double m0 = ((c[2] * m2 + c[1]) * m2 + c[0]) * lp.factor0;
-      sm.c[0][tid] = c[0];
-      sm.c[1][tid] = c[1];
-      sm.c[2][tid] = c[2];
-      sm.m0[tid] = m0;
-      sm.inv0[tid] = m0 == 0.0 ? 0.0 : 1.0 / m0;
-      if (lp.mode == OUT_ME2) out[ev0 + tid] = m0;
-      else sm.w[tid] = w_in[ev0 + tid];
+      for (int i = 0; i < 16; ++i) {
+        const double v = sm.mom[tid * ROW + i];
+        if constexpr (MIXED) p[i >> 2][i & 3] = f64_to_f32_alu(v);
+        else p[i >> 2][i & 3] = v;
+      }
+      R c[3], e12;
+      qq_ttx_coefficients<R>(p, c, &e12);
+      const R m0sq = sm.m0sq;
+      const R p0 = (c[2] * m0sq + c[1]) * m0sq + c[0];
+      if (lp.mode == OUT_ME2) {
+        // |M|^2 itself: times the incoming scale, 1/s^2 and the coupling factor (FP64)
+        double q[4];
+#pragma unroll
+        for (int m = 0; m < 4; ++m) q[m] = sm.mom[tid * ROW + m] + sm.mom[tid * ROW + 4 + m];
+        const double s = q[0] * q[0] - q[1] * q[1] - q[2] * q[2] - q[3] * q[3];
+        out[ev0 + tid] = double(p0) * double(e12) / (s * s) * lp.factor0;
+        return;
+      }
+      const double w = w_in[ev0 + tid];
+      const bool zero = p0 == R(0), bad = !(p0 == p0);
+      const R inv = (zero || bad) ? R(0) : R(1) / p0;
+#pragma unroll
+      for (int i = 0; i < 3; ++i) sm.q[i][tid] = bad ? p0 : c[i] * inv;
+      const double wz = zero ? 0.0 : (bad ? __longlong_as_double(0x7ff8000000000000LL) : w);
+      sm.w[tid] = wz;
+      if constexpr (MIXED) sm.wf[tid] = f64_to_f32_alu(wz);
     }
-    if (lp.mode != OUT_RATIO) return;
+    if (lp.mode != OUT_RATIO || k == 0) return;
     __syncthreads();
+    // a8: output idx = e * k + j; (e, j) advance without an integer division per output
+    int e = tid / k, j = tid - (tid / k) * k;
+    const int de = QQ_BLOCK / k, dj = QQ_BLOCK - (QQ_BLOCK / k) * k;
     for (int idx = tid; idx < nblk * k; idx += QQ_BLOCK) {
-      const int e = idx / k;
-      const int j = idx - e * k;
-      const double m2 = sm.pt[j][0];
-      const double mj = ((sm.c[2][e] * m2 + sm.c[1][e]) * m2 + sm.c[0][e]) * sm.pt[j][1];
-      const double m0 = sm.m0[e], w = sm.w[e];
-      out[(ev0 + e) * lp.out_stride + j] = (m0 == 0.0) ? 0.0 : (mj == m0 ? w : w * (mj * sm.inv0[e]));
+      double o;
+      if (sm.same[j]) {
+        o = sm.w[e] * sm.r[j];
+      } else if constexpr (MIXED) {
+        const float rho = fmaf(sm.q[2][e], sm.pa[j][2], fmaf(sm.q[1][e], sm.pa[j][1], sm.q[0][e] * sm.pa[j][0]));
+        o = f32_to_f64_alu(sm.wf[e] * rho);
+      } else {
+        const double rho = fma(sm.q[2][e], sm.pa[j][2], fma(sm.q[1][e], sm.pa[j][1], sm.q[0][e] * sm.pa[j][0]));
+        o = sm.w[e] * rho;
+      }
+      out[(ev0 + e) * lp.out_stride + j] = o;
+      e += de;
+      j += dj;
+      if (j >= k) {
+        j -= k;
+        ++e;
+      }
     }
   }
 };

@@ -126,14 +126,15 @@ int main() {
   REX_COUNT(gg_ttxg, 3, false);
   REX_COUNT(gg_ttxgg, 4, false);
   {
-    // q q~ -> t t~: the per-event constants (FP64 s and 1/s^2 not counted); every
-    // point then adds the FP64 polynomial and ratio, counted by the caller
-    double p[4][4];
+    // q q~ -> t t~: the per-event constants; the caller adds the normalisation by
+    // the original point (a division and three products) and the per-point
+    // polynomial and weight product
+    RC p[4][4];
     for (int i = 0; i < 4; ++i)
-      for (int m = 0; m < 4; ++m) p[i][m] = 1.0 + i + 0.1 * m;
-    double c[3];
+      for (int m = 0; m < 4; ++m) p[i][m] = RC(1.0 + i + 0.1 * m);
+    RC c[3], e12;
     RC::flops = 0;
-    qq_ttx_coefficients<RC>(p, c);
+    qq_ttx_coefficients<RC>(p, c, &e12);
     std::printf("  \"qq_ttx\": {\"nghel\": 1, \"event_setup\": %lld, \"mass_setup\": 0, "
                 "\"polarisations\": 0, \"gluon_currents\": 0, \"quark_line_amp\": 0, "
                 "\"quark_line_acc\": 0}\n", RC::flops);

@@ -38,7 +38,7 @@ SURROGATE_LAYERED = 1
 EXPORTS = (
     "rex_init_process", "rex_process_npart", "rex_set_flags", "rex_set_params",
     "rex_reweight", "rex_reweight_host", "rex_me2", "rex_free_process",
-    "rex_last_error", "rex_version", "rex_probe_fma", "rex_num_variants", "rex_get_variant",
+    "rex_last_error", "rex_version", "rex_probe_fma", "rex_probe_convert", "rex_num_variants", "rex_get_variant",
     "rex_set_variant", "rex_autotune", "rex_multi_create", "rex_reweight_multi", "rex_multi_capture",
     "rex_multi_replay", "rex_multi_free", "rex_reweight_multi_noalloc", "rex_multi_set_mode",
     "rex_surrogate_num_params", "rex_surrogate_last_error", "rex_surrogate_create",
@@ -108,6 +108,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.rex_last_error.restype = ctypes.c_char_p
     lib.rex_probe_fma.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_double), vp]
     lib.rex_probe_fma.restype = ctypes.c_int
+    lib.rex_probe_convert.argtypes = [vp, i64, vp, vp, vp]
+    lib.rex_probe_convert.restype = ctypes.c_int
     lib.rex_num_variants.argtypes = [vp]
     lib.rex_num_variants.restype = ctypes.c_int
     lib.rex_get_variant.argtypes = [vp]
@@ -575,6 +577,16 @@ def probe_fma(fp64: bool, stream=None) -> float:
     out = ctypes.c_double()
     _check(load().rex_probe_fma(1 if fp64 else 0, ctypes.byref(out), _stream_ptr(stream)))
     return out.value
+
+
+def probe_convert(values, stream=None):
+    """The integer-ALU FP64 -> FP32 -> FP64 conversions of the mixed q q~ -> t t~ kernel on a
+    device FP64 tensor; returns (FP32 tensor, FP64 tensor)."""
+    import torch
+    f32 = torch.empty(values.shape, dtype=torch.float32, device=values.device)
+    f64 = torch.empty(values.shape, dtype=torch.float64, device=values.device)
+    _check(load().rex_probe_convert(_ptr(values), values.numel(), _ptr(f32), _ptr(f64), _stream_ptr(stream)))
+    return f32, f64
 
 
 def version() -> str:

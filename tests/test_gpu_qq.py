@@ -53,7 +53,7 @@ def points():
 
 def test_single_kernel_variant(rex):
     p = make(rex)
-    assert p.num_variants() == 1 and p.variant == 0
+    assert p.num_variants == 1 and p.variant == 0
     with pytest.raises(Exception):
         p.variant = 1
 
@@ -131,3 +131,28 @@ def test_full_size_workload_sampled(rex):
     assert np.max(rel(got[idx], ref)) < FP64_TOL
     mixed = make(rex, 1).reweight(dm, dw, pts).cpu().numpy()
     assert np.max(rel(mixed, got)) < MIXED_TOL
+
+
+def test_integer_alu_conversions_round_like_ieee(rex):
+    """The mixed tile's FP64 -> FP32 conversion (round to nearest even, flush below
+    2^-126) and the exact FP32 -> FP64 one, against numpy's IEEE casts."""
+    rng = np.random.default_rng(9)
+    x = np.concatenate([
+        rng.standard_normal(20000) * 10.0 ** rng.integers(-30, 30, 20000),
+        # ties: values exactly half-way between two FP32 numbers, both parities
+        (np.arange(1, 2001, dtype=np.float64) + 0.5) * 2.0 ** -23 + 1.0,
+        -(np.arange(1, 2001, dtype=np.float64) + 0.5) * 2.0 ** -23 - 1.0,
+        np.nextafter(np.float64(np.finfo(np.float32).max), np.inf) * np.array([1.0, -1.0]),
+        np.array([0.0, -0.0, 1.0, -2.5, 3.4e38, 3.5e38, -1e39, 1.2e-38, 1.1754943508222875e-38,
+                  1e-40, -1e-45, 1e-300, np.inf, -np.inf, np.nan, 173.0, 0.118]),
+    ])
+    f32, f64 = rex.probe_convert(torch.from_numpy(x).cuda())
+    f32, f64 = f32.cpu().numpy(), f64.cpu().numpy()
+    with np.errstate(over="ignore"):
+        ref = x.astype(np.float32)
+    tiny = np.abs(x) < 2.0 ** -126
+    ref[tiny] = np.copysign(np.float32(0.0), x[tiny]).astype(np.float32)
+    nan = np.isnan(x)
+    assert np.all(np.isnan(f32[nan])) and np.all(np.isnan(f64[nan]))
+    assert np.array_equal(f32[~nan].view(np.uint32), ref[~nan].view(np.uint32))
+    assert np.array_equal(f64[~nan].view(np.uint64), ref[~nan].astype(np.float64).view(np.uint64))
