@@ -47,39 +47,34 @@ namespace rex {
 
 constexpr int QQ_BLOCK = 128;
 
-// FP64 -> FP32 on integer ALUs: round to nearest even; magnitudes below the FP32
-// normal range become a signed zero, above it infinity; NaN stays NaN.
+// FP64 -> FP32 on integer ALUs (selects, no branches): round to nearest even;
+// magnitudes below the FP32 normal range become a signed zero, above it infinity;
+// NaN stays NaN.
 __device__ __forceinline__ float f64_to_f32_alu(double x) {
   const unsigned long long d = (unsigned long long)__double_as_longlong(x);
   const unsigned hi = (unsigned)(d >> 32), lo = (unsigned)d;
   const unsigned sign = hi & 0x80000000u, ahi = hi & 0x7fffffffu;
-  unsigned f;
-  if (ahi < (897u << 20)) {                 // biased exponent < 897: |x| < 2^-126
-    f = 0u;
-  } else if (ahi >= (1151u << 20)) {        // |x| >= 2^128, infinity or NaN
-    f = (ahi >= 0x7ff00000u && ((ahi & 0xfffffu) | lo)) ? 0x7fc00000u : 0x7f800000u;
-  } else {                                  // rebias the exponent by 1023 - 127 = 896
-    f = ((ahi - (896u << 20)) << 3) | (lo >> 29);
-    const unsigned rem = lo & 0x1fffffffu;  // the 29 dropped mantissa bits
-    f += (rem > 0x10000000u) | ((rem == 0x10000000u) & f);
-  }
+  // rebias the exponent by 1023 - 127 = 896 and keep 23 mantissa bits
+  unsigned f = ((ahi - (896u << 20)) << 3) | (lo >> 29);
+  const unsigned rem = lo & 0x1fffffffu;   // the 29 dropped mantissa bits
+  f += (rem > 0x10000000u) | ((rem == 0x10000000u) & f);
+  const unsigned big = (ahi > 0x7ff00000u || (ahi == 0x7ff00000u && lo != 0u)) ? 0x7fc00000u : 0x7f800000u;
+  f = ahi < (897u << 20) ? 0u : f;         // |x| < 2^-126
+  f = ahi >= (1151u << 20) ? big : f;      // |x| >= 2^128, infinity or NaN
   return __uint_as_float(f | sign);
 }
 
-// FP32 -> FP64 on integer ALUs: exact for normal numbers, zeros, infinities and NaN
-// (FP32 subnormals, which the conversion above never produces, become zero).
+// FP32 -> FP64 on integer ALUs (selects): exact for normal numbers, zeros,
+// infinities and NaN (FP32 subnormals, which the conversion above never
+// produces, become zero).
 __device__ __forceinline__ double f32_to_f64_alu(float x) {
   const unsigned b = __float_as_uint(x);
   const unsigned sign = b & 0x80000000u, a = b & 0x7fffffffu;
-  unsigned hi, lo = a << 29;
-  if (a < 0x00800000u) {
-    hi = 0u;
-    lo = 0u;
-  } else if (a >= 0x7f800000u) {
-    hi = 0x7ff00000u | ((a & 0x7fffffu) >> 3);
-  } else {
-    hi = (a >> 3) + (896u << 20);
-  }
+  const bool small = a < 0x00800000u, special = a >= 0x7f800000u;
+  unsigned hi = (a >> 3) + (896u << 20);
+  hi = special ? (0x7ff00000u | ((a & 0x7fffffu) >> 3)) : hi;
+  hi = small ? 0u : hi;
+  const unsigned lo = small ? 0u : a << 29;
   return __hiloint2double((int)(hi | sign), (int)lo);
 }
 
@@ -91,14 +86,58 @@ struct QqTile {
 
   struct Smem {
     double mom[EPB * ROW];
-    R q[3][EPB];                 // C / P(m0^2) per event (0 if |M_0|^2 == 0)
-    double w[EPB];               // w_in (0 if |M_0|^2 == 0, NaN if it is NaN)
-    float wf[EPB];               // mixed mode: w in FP32
+    alignas(16) R qw[EPB][4];    // C / P(m0^2) (0 if |M_0|^2 == 0) and w, per event
+    double w[EPB];               // w_in in FP64 (0 if |M_0|^2 == 0, NaN if it is NaN)
     R pa[MAX_POINTS][3];         // a_j, a_j m_j^2, a_j m_j^4 with a_j = f_j / f_0
     double r[MAX_POINTS];        // a_j in FP64
     int same[MAX_POINTS];        // point j at the original top mass
+    int any_same;
     R m0sq;
   };
+
+  // w_out of event e (tile row) at point j
+  template <bool SAME>
+  static __device__ __forceinline__ double weight(const Smem& sm, int e, R a0, R a2, R a4, bool same, double r) {
+    if (SAME && same) return sm.w[e] * r;
+    R q[4];
+    if constexpr (MIXED) {
+      const float4 v = *reinterpret_cast<const float4*>(sm.qw[e]);
+      q[0] = v.x; q[1] = v.y; q[2] = v.z; q[3] = v.w;
+    } else {
+#pragma unroll
+      for (int i = 0; i < 4; ++i) q[i] = sm.qw[e][i];
+    }
+    const R rho = fma(q[2], a4, fma(q[1], a2, q[0] * a0));
+    if constexpr (MIXED) return f32_to_f64_alu(q[3] * rho);
+    else return q[3] * rho;
+  }
+
+  // a8: every output of the tile; a thread keeps one point's constants in registers
+  // and walks events, so consecutive threads write consecutive outputs of a row
+  template <bool SAME>
+  static __device__ __forceinline__ void write_outputs(const Smem& sm, int nblk, int k, int64_t ev0,
+                                                       int64_t stride, double* __restrict__ out) {
+    const int tid = threadIdx.x;
+    if (k <= QQ_BLOCK) {
+      const int ne = QQ_BLOCK / k;             // events per pass
+      if (tid >= ne * k) return;
+      const int e0 = tid / k, j = tid - e0 * k;
+      const R a0 = sm.pa[j][0], a2 = sm.pa[j][1], a4 = sm.pa[j][2];
+      const bool same = SAME && sm.same[j];
+      const double r = SAME ? sm.r[j] : 0.0;
+      double* o = out + (ev0 + e0) * stride + j;
+      const int64_t step = (int64_t)ne * stride;
+      for (int e = e0; e < nblk; e += ne, o += step) *o = weight<SAME>(sm, e, a0, a2, a4, same, r);
+    } else {
+      for (int j = tid; j < k; j += QQ_BLOCK) {
+        const R a0 = sm.pa[j][0], a2 = sm.pa[j][1], a4 = sm.pa[j][2];
+        const bool same = SAME && sm.same[j];
+        const double r = SAME ? sm.r[j] : 0.0;
+        double* o = out + ev0 * stride + j;
+        for (int e = 0; e < nblk; ++e, o += stride) *o = weight<SAME>(sm, e, a0, a2, a4, same, r);
+      }
+    }
+  }
 
   template <class TABLE>
   static __device__ __forceinline__ void run(Smem& sm, const double* __restrict__ mom,
@@ -117,6 +156,11 @@ struct QqTile {
     }
     // a2: the launch's points
     const int k = lp.mode == OUT_RATIO ? lp.k : 0;
+    if (tid == 0) {
+      sm.m0sq = R(lp.mass[0] * lp.mass[0]);
+      sm.any_same = 0;
+    }
+    __syncthreads();
     for (int j = tid; j < k; j += QQ_BLOCK) {
       const double m = lp.mass[lp.slot[j]];
       const double a = lp.factor[j] / lp.factor0;
@@ -125,10 +169,10 @@ struct QqTile {
       sm.pa[j][1] = R(am2);
       sm.pa[j][2] = R(am2 * (m * m));
       sm.r[j] = a;
-      sm.same[j] = m == lp.mass[0];
+      const int same = m == lp.mass[0];
+      sm.same[j] = same;
+      if (same) sm.any_same = 1;
     }
-    if (tid == 0) sm.m0sq = R(lp.mass[0] * lp.mass[0]);
-    __syncthreads();
     if (tid < nblk) {
       R p[4][4];
 #pragma unroll
@@ -153,36 +197,17 @@ struct QqTile {
       const double w = w_in[ev0 + tid];
       const bool zero = p0 == R(0), bad = !(p0 == p0);
       const R inv = (zero || bad) ? R(0) : R(1) / p0;
-#pragma unroll
-      for (int i = 0; i < 3; ++i) sm.q[i][tid] = bad ? p0 : c[i] * inv;
       const double wz = zero ? 0.0 : (bad ? __longlong_as_double(0x7ff8000000000000LL) : w);
+#pragma unroll
+      for (int i = 0; i < 3; ++i) sm.qw[tid][i] = bad ? p0 : c[i] * inv;
+      if constexpr (MIXED) sm.qw[tid][3] = f64_to_f32_alu(wz);
+      else sm.qw[tid][3] = wz;
       sm.w[tid] = wz;
-      if constexpr (MIXED) sm.wf[tid] = f64_to_f32_alu(wz);
     }
     if (lp.mode != OUT_RATIO || k == 0) return;
     __syncthreads();
-    // a8: output idx = e * k + j; (e, j) advance without an integer division per output
-    int e = tid / k, j = tid - (tid / k) * k;
-    const int de = QQ_BLOCK / k, dj = QQ_BLOCK - (QQ_BLOCK / k) * k;
-    for (int idx = tid; idx < nblk * k; idx += QQ_BLOCK) {
-      double o;
-      if (sm.same[j]) {
-        o = sm.w[e] * sm.r[j];
-      } else if constexpr (MIXED) {
-        const float rho = fmaf(sm.q[2][e], sm.pa[j][2], fmaf(sm.q[1][e], sm.pa[j][1], sm.q[0][e] * sm.pa[j][0]));
-        o = f32_to_f64_alu(sm.wf[e] * rho);
-      } else {
-        const double rho = fma(sm.q[2][e], sm.pa[j][2], fma(sm.q[1][e], sm.pa[j][1], sm.q[0][e] * sm.pa[j][0]));
-        o = sm.w[e] * rho;
-      }
-      out[(ev0 + e) * lp.out_stride + j] = o;
-      e += de;
-      j += dj;
-      if (j >= k) {
-        j -= k;
-        ++e;
-      }
-    }
+    if (sm.any_same) write_outputs<true>(sm, nblk, k, ev0, lp.out_stride, out);
+    else write_outputs<false>(sm, nblk, k, ev0, lp.out_stride, out);
   }
 };
 
