@@ -421,10 +421,13 @@ int rex_probe_fma(int fp64, double *flops_per_second, void *stream);
  * kernel uses in place of FP64-pipe conversions (B300 issues FP64 at 1/64 of the
  * FP32 rate): f32_out[i] = FP64 -> FP32 of in[i] (round to nearest even;
  * magnitudes below 2^-126 give a signed zero, overflow gives infinity, NaN stays
- * NaN) and f64_out[i] = FP32 -> FP64 of f32_out[i] (exact).  All three arrays
- * are device arrays of n elements, 16-byte aligned is not required; enqueue only.
- * Errors: REX_EINVAL (n < 0, null array), REX_ECUDA. */
-int rex_probe_convert(const double *in, int64_t n, float *f32_out, double *f64_out, void *stream);
+ * NaN), f64_out[i] = FP32 -> FP64 of f32_out[i] (exact) and, if f32_finite_out
+ * is not null, f32_finite_out[i] = the kernel's FP64 -> FP32 conversion for
+ * momenta (the same rounding; finiteness is checked once per event instead, so
+ * its value is meaningful for finite in[i] below 2^128 only).  Device arrays of
+ * n elements; enqueue only.  Errors: REX_EINVAL (n < 0, null array), REX_ECUDA. */
+int rex_probe_convert(const double *in, int64_t n, float *f32_out, double *f64_out,
+                      float *f32_finite_out, void *stream);
 
 /* Library version string. */
 const char *rex_version(void);

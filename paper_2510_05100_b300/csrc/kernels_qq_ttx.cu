@@ -4,8 +4,10 @@
 
 namespace rex {
 
-template <typename R>
-__global__ void __launch_bounds__(QQ_BLOCK)
+// resident blocks per SM the register allocator must allow: FP64 4 (<= 128 registers),
+// mixed 8 (<= 64 registers)
+template <typename R, int MINB>
+__global__ void __launch_bounds__(QQ_BLOCK, MINB)
     qq_ttx_reweight_kernel(const double* __restrict__ mom, const double* __restrict__ w_in, int64_t nev,
                            const __grid_constant__ QcdLaunch lp, double* __restrict__ out) {
   __shared__ typename QqTile<R>::Smem sm;
@@ -18,30 +20,35 @@ int launch_qq_ttx(int mixed, const double* mom, const double* w_in, int64_t nev,
   if (blocks > 0x7fffffffLL) return (int)cudaErrorInvalidValue;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   if (mixed)
-    qq_ttx_reweight_kernel<float><<<(unsigned)blocks, QQ_BLOCK, 0, st>>>(mom, w_in, nev, lp, out);
+    qq_ttx_reweight_kernel<float, 8><<<(unsigned)blocks, QQ_BLOCK, 0, st>>>(mom, w_in, nev, lp, out);
   else
-    qq_ttx_reweight_kernel<double><<<(unsigned)blocks, QQ_BLOCK, 0, st>>>(mom, w_in, nev, lp, out);
+    qq_ttx_reweight_kernel<double, 4><<<(unsigned)blocks, QQ_BLOCK, 0, st>>>(mom, w_in, nev, lp, out);
   return (int)cudaGetLastError();
 }
 
 __global__ void convert_probe_kernel(const double* __restrict__ in, int64_t n, float* __restrict__ f32,
-                                     double* __restrict__ f64) {
+                                     double* __restrict__ f64, float* __restrict__ f32_finite) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const float f = f64_to_f32_alu(in[i]);
   f32[i] = f;
   f64[i] = f32_to_f64_alu(f);
+  if (f32_finite) {
+    unsigned ahi_max = 0u;
+    f32_finite[i] = f64_to_f32_alu_finite(in[i], ahi_max);
+  }
 }
 
 }  // namespace rex
 
-extern "C" int rex_probe_convert(const double* in, int64_t n, float* f32_out, double* f64_out, void* stream) {
+extern "C" int rex_probe_convert(const double* in, int64_t n, float* f32_out, double* f64_out,
+                                 float* f32_finite_out, void* stream) {
   if (n < 0) return REX_EINVAL;
   if (n == 0) return REX_OK;
   if (!in || !f32_out || !f64_out) return REX_EINVAL;
   const int64_t blocks = (n + 255) / 256;
   if (blocks > 0x7fffffffLL) return REX_EINVAL;
   rex::convert_probe_kernel<<<(unsigned)blocks, 256, 0, static_cast<cudaStream_t>(stream)>>>(in, n, f32_out,
-                                                                                           f64_out);
+                                                                                           f64_out, f32_finite_out);
   return cudaGetLastError() == cudaSuccess ? REX_OK : REX_ECUDA;
 }

@@ -78,6 +78,23 @@ __device__ __forceinline__ double f32_to_f64_alu(float x) {
   return __hiloint2double((int)(hi | sign), (int)lo);
 }
 
+// FP64 -> FP32 on integer ALUs for finite inputs, rounding to nearest even
+// (magnitudes below 2^-126 give a signed zero); the caller checks finiteness
+// once per event with the largest |x|'s high word, ahi_max (>= 1151 << 20:
+// infinite, NaN or beyond the FP32 range).
+__device__ __forceinline__ float f64_to_f32_alu_finite(double x, unsigned& ahi_max) {
+  const unsigned long long d = (unsigned long long)__double_as_longlong(x);
+  const unsigned hi = (unsigned)(d >> 32), lo = (unsigned)d;
+  const unsigned ahi = hi & 0x7fffffffu;
+  ahi_max = max(ahi_max, ahi);
+  unsigned f = __funnelshift_l(lo, ahi - (896u << 20), 3);
+  // round half to even on the 29 dropped bits: up if bit 28 is set and (bits 0..27
+  // are not all zero or the kept value is odd)
+  f += (lo >> 28) & 1u & ((lo & 0x0fffffffu) != 0u | f);
+  f = ahi < (897u << 20) ? 0u : f;
+  return __uint_as_float(f | (hi & 0x80000000u));
+}
+
 template <typename R>
 struct QqTile {
   static constexpr int EPB = QQ_BLOCK;
@@ -157,34 +174,65 @@ struct QqTile {
     // a2: the launch's points
     const int k = lp.mode == OUT_RATIO ? lp.k : 0;
     if (tid == 0) {
-      sm.m0sq = R(lp.mass[0] * lp.mass[0]);
+      if constexpr (MIXED) {
+        const float m0 = f64_to_f32_alu(lp.mass[0]);
+        sm.m0sq = m0 * m0;
+      } else {
+        sm.m0sq = lp.mass[0] * lp.mass[0];
+      }
       sm.any_same = 0;
     }
     __syncthreads();
     for (int j = tid; j < k; j += QQ_BLOCK) {
       const double m = lp.mass[lp.slot[j]];
-      const double a = lp.factor[j] / lp.factor0;
-      const double am2 = a * (m * m);
-      sm.pa[j][0] = R(a);
-      sm.pa[j][1] = R(am2);
-      sm.pa[j][2] = R(am2 * (m * m));
-      sm.r[j] = a;
-      const int same = m == lp.mass[0];
+      // the original mass (bitwise; masses are positive and finite)
+      const int same = __double_as_longlong(m) == __double_as_longlong(lp.mass[0]);
+      if constexpr (MIXED) {
+        // FP32 without FP64 instructions (FP64 issues at 1/64 of the FP32 rate)
+        const float mf = f64_to_f32_alu(m);
+        const float a = f64_to_f32_alu(lp.factor[j]) / f64_to_f32_alu(lp.factor0);
+        const float am2 = a * (mf * mf);
+        sm.pa[j][0] = a;
+        sm.pa[j][1] = am2;
+        sm.pa[j][2] = am2 * (mf * mf);
+        if (same) sm.r[j] = lp.factor[j] / lp.factor0;
+      } else {
+        const double a = lp.factor[j] / lp.factor0;
+        const double am2 = a * (m * m);
+        sm.pa[j][0] = a;
+        sm.pa[j][1] = am2;
+        sm.pa[j][2] = am2 * (m * m);
+        sm.r[j] = a;
+      }
       sm.same[j] = same;
       if (same) sm.any_same = 1;
     }
     if (tid < nblk) {
       R p[4][4];
+      unsigned ahi_max = 0u;   // mixed: largest |momentum| high word
+      double fin = 0.0;        // FP64: sum of 0 * momentum, NaN iff one is not finite
 #pragma unroll
       for (int i = 0; i < 16; ++i) {
         const double v = sm.mom[tid * ROW + i];
-        if constexpr (MIXED) p[i >> 2][i & 3] = f64_to_f32_alu(v);
-        else p[i >> 2][i & 3] = v;
+        if constexpr (MIXED) {
+          p[i >> 2][i & 3] = f64_to_f32_alu_finite(v, ahi_max);
+        } else {
+          p[i >> 2][i & 3] = v;
+          fin = fma(v, 0.0, fin);
+        }
       }
       R c[3], e12;
       qq_ttx_coefficients<R>(p, c, &e12);
       const R m0sq = sm.m0sq;
-      const R p0 = (c[2] * m0sq + c[1]) * m0sq + c[0];
+      R p0 = (c[2] * m0sq + c[1]) * m0sq + c[0];
+      // a non-finite momentum (in the mixed mode also one beyond the FP32 range) makes
+      // the event NaN; checked on the bit patterns (the energies of the massless
+      // quarks cancel from the ratio, so arithmetic alone would not always show it)
+      if constexpr (MIXED) {
+        if (ahi_max >= (1151u << 20)) p0 = __int_as_float(0x7fc00000);
+      } else {
+        p0 += fin;
+      }
       if (lp.mode == OUT_ME2) {
         // |M|^2 itself: times the incoming scale, 1/s^2 and the coupling factor (FP64)
         double q[4];

@@ -108,7 +108,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.rex_last_error.restype = ctypes.c_char_p
     lib.rex_probe_fma.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_double), vp]
     lib.rex_probe_fma.restype = ctypes.c_int
-    lib.rex_probe_convert.argtypes = [vp, i64, vp, vp, vp]
+    lib.rex_probe_convert.argtypes = [vp, i64, vp, vp, vp, vp]
     lib.rex_probe_convert.restype = ctypes.c_int
     lib.rex_num_variants.argtypes = [vp]
     lib.rex_num_variants.restype = ctypes.c_int
@@ -581,12 +581,14 @@ def probe_fma(fp64: bool, stream=None) -> float:
 
 def probe_convert(values, stream=None):
     """The integer-ALU FP64 -> FP32 -> FP64 conversions of the mixed q q~ -> t t~ kernel on a
-    device FP64 tensor; returns (FP32 tensor, FP64 tensor)."""
+    device FP64 tensor; returns (FP32, FP64 round trip, FP32 by the momentum conversion)."""
     import torch
     f32 = torch.empty(values.shape, dtype=torch.float32, device=values.device)
     f64 = torch.empty(values.shape, dtype=torch.float64, device=values.device)
-    _check(load().rex_probe_convert(_ptr(values), values.numel(), _ptr(f32), _ptr(f64), _stream_ptr(stream)))
-    return f32, f64
+    fin = torch.empty(values.shape, dtype=torch.float32, device=values.device)
+    _check(load().rex_probe_convert(_ptr(values), values.numel(), _ptr(f32), _ptr(f64), _ptr(fin),
+                                    _stream_ptr(stream)))
+    return f32, f64, fin
 
 
 def version() -> str:

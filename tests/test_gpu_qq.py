@@ -102,8 +102,9 @@ def test_ragged_tails(rex, n):
     assert np.max(rel(got, ref)) < FP64_TOL
 
 
-def test_empty_inputs_and_nonfinite_events(rex):
-    p = make(rex)
+@pytest.mark.parametrize("precision", [0, 1])
+def test_empty_inputs_and_nonfinite_events(rex, precision):
+    p = make(rex, precision)
     mom = ps.make_events(PROC, 40, 35)
     out = torch.full((40, 2), 7.0, dtype=torch.float64, device="cuda")
     p.reweight(dev(mom)[:0], dev(np.ones(40))[:0], ps.grid_gg_ttx()[:2], w_out=out[:0])
@@ -111,9 +112,11 @@ def test_empty_inputs_and_nonfinite_events(rex):
     torch.cuda.synchronize()
     assert torch.all(out == 7.0)
     mom[9, 2, 3] = np.nan
-    got = p.reweight(dev(mom), dev(np.ones(40)), ps.grid_gg_ttx()[:3]).cpu().numpy()
-    assert np.all(np.isnan(got[9]))
-    assert np.all(np.isfinite(np.delete(got, 9, axis=0)))
+    mom[17, 0, 0] = np.inf
+    pts = ps.grid_gg_ttx()[:3] + [ORIG, dict(mt=173.0, wt=0.0, alphas=0.121)]   # incl. same-mass points
+    got = p.reweight(dev(mom), dev(np.ones(40)), pts).cpu().numpy()
+    assert np.all(np.isnan(got[[9, 17]]))
+    assert np.all(np.isfinite(np.delete(got, [9, 17], axis=0)))
 
 
 def test_full_size_workload_sampled(rex):
@@ -146,8 +149,8 @@ def test_integer_alu_conversions_round_like_ieee(rex):
         np.array([0.0, -0.0, 1.0, -2.5, 3.4e38, 3.5e38, -1e39, 1.2e-38, 1.1754943508222875e-38,
                   1e-40, -1e-45, 1e-300, np.inf, -np.inf, np.nan, 173.0, 0.118]),
     ])
-    f32, f64 = rex.probe_convert(torch.from_numpy(x).cuda())
-    f32, f64 = f32.cpu().numpy(), f64.cpu().numpy()
+    f32, f64, fin = rex.probe_convert(torch.from_numpy(x).cuda())
+    f32, f64, fin = f32.cpu().numpy(), f64.cpu().numpy(), fin.cpu().numpy()
     with np.errstate(over="ignore"):
         ref = x.astype(np.float32)
     tiny = np.abs(x) < 2.0 ** -126
@@ -156,3 +159,6 @@ def test_integer_alu_conversions_round_like_ieee(rex):
     assert np.all(np.isnan(f32[nan])) and np.all(np.isnan(f64[nan]))
     assert np.array_equal(f32[~nan].view(np.uint32), ref[~nan].view(np.uint32))
     assert np.array_equal(f64[~nan].view(np.uint64), ref[~nan].astype(np.float64).view(np.uint64))
+    # the momentum conversion (finiteness checked per event) agrees wherever it is defined
+    ok = np.isfinite(x) & (np.abs(x) < 2.0 ** 128)
+    assert np.array_equal(fin[ok].view(np.uint32), ref[ok].view(np.uint32))
