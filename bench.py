@@ -64,10 +64,11 @@ PEAKS = _measured_peaks()
 # dram__bytes_write.sum) of the dominant kernel, scaled to the full launch;
 # only reported while the kernel sources still hash to the captured version.
 TRAFFIC = {
-    # ncu --set full of profile_case at 2^19 events (FP64, scaled x2 by events) and
-    # 2^20 events (mixed); summaries of both captures are under profiles/
-    ("gg_ttxg", "fp64"): {"bytes_per_launch": 2 * (89.659136e6 + 35.451904e6), "source_hash": "cc669a8b0247879f"},
-    ("gg_ttxg", "mixed"): {"bytes_per_launch": 177.336576e6 + 102.396416e6, "source_hash": "cc669a8b0247879f"},
+    # ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum of profile_case at 2^19
+    # events (FP64, scaled x2 by events) and 2^20 events (mixed); summaries of the
+    # captures are under profiles/
+    ("gg_ttxg", "fp64"): {"bytes_per_launch": 2 * (90.465024e6 + 35.403776e6), "source_hash": "61469b75d5115adb"},
+    ("gg_ttxg", "mixed"): {"bytes_per_launch": 176.333312e6 + 101.98784e6, "source_hash": "61469b75d5115adb"},
 }
 
 
