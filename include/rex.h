@@ -81,8 +81,9 @@ typedef struct {
  *       "gg_ttxg"  g(1) g(2) -> t(3) t~(4) g(5);
  *       "gg_ttxgg" g(1) g(2) -> t(3) t~(4) g(5) g(6);
  *       "qq_ttx"   q(1) q~(2) -> t(3) t~(4), massless light quark, one
- *                  s-channel gluon (the other leading-order channel of
- *                  p p -> t t~, Sec. 5).
+ *                  s-channel gluon (the quark-initiated leading-order
+ *                  channel of p p -> t t~; multi-channel samples with p any
+ *                  massless QCD parton are the paper's Sec. 4.2 workload).
  * precision: REX_FP64 or REX_MIXED.
  * On success *out receives a handle the caller releases with rex_free_process.
  * Errors: REX_EINVAL (null out, unknown name or precision). */

@@ -1,7 +1,9 @@
 """q q~ -> t t~ from its one Feynman diagram (oracle; test infrastructure only).
 
-The other leading-order channel of p p -> t t~ (Sec. 5, the top-pair and
-four-top workloads): a massless light quark q(1) and antiquark q~(2) annihilate
+The quark-initiated leading-order channel of p p -> t t~; with g g -> t t~ it
+forms a multi-channel sample of the kind the runtime comparison reweights
+(Sec. 4.2, where p may be any massless QCD parton): a massless light quark q(1)
+and antiquark q~(2) annihilate
 into an s-channel gluon that makes the top pair t(3) t~(4).  Feynman rules as
 in the g g -> t t~ (+ n g) oracle (Peskin & Schroeder Fig. 16.7, Feynman gauge):
 
