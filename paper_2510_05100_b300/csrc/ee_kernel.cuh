@@ -39,8 +39,14 @@ __device__ __forceinline__ cx<double> cmdot(const cx<double>* a, const cx<double
 // With d_a(h) = JeX(h).JmY(h) for the four chirality pairs a = (X, Y) and the
 // point's coefficients c_a, the helicity sum is a Hermitian form
 //     sum_h |sum_a c_a d_a(h)|^2 = c^dag H c,   H_ab = sum_h conj(d_a(h)) d_b(h),
-// so H (parameter independent) is built once per event from the 16 helicity
-// configurations and every point costs one 4x4 form.
+// so H (parameter independent) is built once per event and every point costs one
+// 4x4 form.
+//
+// Helicity filtering: the leptons are massless, so a vector or axial current of a
+// fermion-antifermion pair vanishes unless their helicities are opposite.  Of the
+// 16 configurations only (l1, l2, l3, l4) = (+,-,+,-), (-,+,+,-), (+,-,-,+), (-,+,-,+)
+// (h = 5, 6, 9, 10) reach H; the other 12 contribute exact zeros (their spinor halves
+// are w- chi with w- = 0/w+ = 0), so summing the 4 gives the same H bit for bit.
 template <class TABLE>
 __device__ __forceinline__ void ee_tile(const double* __restrict__ mom, const double* __restrict__ w_in,
                                         int64_t nev, int64_t tile, const TABLE& lp, double* __restrict__ out) {
@@ -63,7 +69,8 @@ __device__ __forceinline__ void ee_tile(const double* __restrict__ mom, const do
   double hd[4] = {0.0, 0.0, 0.0, 0.0};
   cx<double> ho[6] = {};
 #pragma unroll 1
-  for (int h = 0; h < 16; ++h) {
+  for (int hi = 0; hi < 4; ++hi) {
+    const int h = ((hi & 1) ? 6 : 5) + ((hi & 2) ? 4 : 0);   // 5, 6, 9, 10
     const int l1 = (h & 1) ? 1 : -1, l2 = (h & 2) ? 1 : -1;
     const int l3 = (h & 4) ? 1 : -1, l4 = (h & 8) ? 1 : -1;
     cx<double> v1[4], u2[4], v3[4], u4[4];

@@ -268,3 +268,26 @@ def test_top_width_enters_propagators():
     m1 = qcd.me2(p, MT, 1.5, AS)
     rel = np.abs(m1 / m0 - 1.0)
     assert np.all(rel > 0) and np.all(rel < 0.1)
+
+
+def test_massless_lepton_currents_vanish_for_equal_helicities():
+    """Helicity filtering of e+e- -> mu+mu- rests on this: a chiral current of a massless
+    fermion-antifermion pair vanishes unless their helicities are opposite, so only 4 of
+    the 16 configurations contribute."""
+    from oracle.lorentz import PL, PR
+    p = ps.make_events("ee_mumu", 16, 91)
+    scale = np.max(np.abs(p))
+    for proj in (PL, PR):
+        mats = np.einsum("mij,jk->mik", GAMMA, proj)
+        for l1 in (-1, 1):
+            for l2 in (-1, 1):
+                je = np.einsum("ni,mij,nj->nm", bar(spinor_v(p[:, 0], 0.0, l1)), mats, spinor_u(p[:, 1], 0.0, l2))
+                jm = np.einsum("ni,mij,nj->nm", bar(spinor_u(p[:, 3], 0.0, l2)), mats, spinor_v(p[:, 2], 0.0, l1))
+                if l1 == l2:
+                    assert np.max(np.abs(je)) < 1e-13 * scale and np.max(np.abs(jm)) < 1e-13 * scale
+    # and the surviving configurations carry all of |M|^2: both chiralities of opposite pairs
+    n_nonzero = 0
+    for l1, l2 in itertools.product((-1, 1), repeat=2):
+        j = np.einsum("ni,mij,nj->nm", bar(spinor_v(p[:, 0], 0.0, l1)), GAMMA, spinor_u(p[:, 1], 0.0, l2))
+        n_nonzero += int(np.max(np.abs(j)) > 1e-6 * scale)
+    assert n_nonzero == 2
