@@ -193,7 +193,7 @@ def main():
     ap.add_argument("--no-surrogate", action="store_true")
     ap.add_argument("--no-xsec", action="store_true")
     ap.add_argument("--no-lhe", action="store_true")
-    ap.add_argument("--no-qq", action="store_true", help="skip the q q~ -> t t~ leg")
+    ap.add_argument("--no-qq", action="store_true", help="skip the q q~ -> t t~ and p p -> t t~ legs")
     args = ap.parse_args()
     world, rank, local = rdist.env()
     if args.impl == "reference":
@@ -308,6 +308,63 @@ def run_multi_leg(dev, stream, steps, world, barrier, max_over_ranks):
             "note": "value: the persistent kernel (one launch, one register budget for every process); "
                     "streams_graph: one graph of per-process launches on forked streams",
             "steps": steps}
+
+
+# a two-channel p p -> t t~ sample: g g and q q~ initial states, 7 : 1, 2^20 events
+PP_TTX_BATCHES = (("gg_ttx", 917504, 11), ("qq_ttx", 131072, 12))
+
+
+def run_pp_ttx_leg(dev, stream, pts, steps, world, barrier, max_over_ranks):
+    """The p p -> t t~ channels (g g -> t t~ and q q~ -> t t~ batches of one sample)
+    reweighted to the headline's points: one graph-captured persistent multi-process
+    launch against one launch per channel, in FP64 and in mixed precision."""
+    import torch
+    from paper_2510_05100_b300 import rex
+
+    units = sum(n for _, n, _ in PP_TTX_BATCHES) * len(pts)
+
+    def timed(fn):
+        for _ in range(2):
+            fn()
+        torch.cuda.synchronize(dev)
+        barrier()
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        for _ in range(steps):
+            fn()
+        t1.record(stream)
+        torch.cuda.synchronize(dev)
+        barrier()
+        return max_over_ranks(t0.elapsed_time(t1)) / steps
+
+    out = {"workload": "p p -> t t~ sample of 2^20 events: 917504 g g -> t t~ + 131072 q q~ -> t t~, "
+                       f"{len(pts)} points", "unit": UNIT, "steps": steps}
+    for name, prec in (("fp64", rex.FP64), ("mixed", rex.MIXED)):
+        batches = []
+        for proc, n, seed in PP_TTX_BATCHES:
+            h = rex.Process(proc, prec)
+            h.set_params(ORIGINAL)
+            mom = torch.from_numpy(ps.make_events(proc, n, seed)).to(dev)
+            batches.append((h, mom, torch.ones(n, dtype=torch.float64, device=dev),
+                            torch.empty((n, len(pts)), dtype=torch.float64, device=dev)))
+        m = rex.Multi(prec)
+        m.capture(batches, pts)
+
+        def sequential():
+            for h, mom, w, wo in batches:
+                h.reweight(mom, w, pts, w_out=wo, stream=stream)
+
+        ms_multi = timed(lambda: m.replay(stream))
+        ms_seq = timed(sequential)
+        m.close()
+        for b in batches:
+            b[0].close()
+        out[name] = {"value": rdist.job_throughput(units, world, ms_multi * 1e-3), "ms_per_step": ms_multi,
+                     "kernel_launches_per_step": 1,
+                     "sequential_value": rdist.job_throughput(units, world, ms_seq * 1e-3),
+                     "sequential_ms_per_step": ms_seq}
+    return out
 
 
 def run_surrogate_leg(dev, stream, world, max_over_ranks, tau=0.02):
@@ -667,6 +724,8 @@ def run_ours(args, world, rank, local):
 
     lhe_leg = None if args.no_lhe else run_lhe_leg(dev, stream, pts)
     qq_leg = None if args.no_qq else run_qq_leg(dev, stream, pts, max(5, args.steps // 2))
+    pp_leg = None if args.no_qq else run_pp_ttx_leg(dev, stream, pts, max(3, args.steps // 4), world, barrier,
+                                                     max_over_ranks)
 
     multi = None if args.no_multi else run_multi_leg(dev, stream, max(3, args.steps // 2), world, barrier,
                                                      max_over_ranks)
@@ -696,7 +755,8 @@ def run_ours(args, world, rank, local):
                 "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                         "entry_point": "rex_reweight_host (pinned host buffers)"},
                 "gpu_launches": args.steps, "roofline": roofline, "cpu_baseline": cpu, "modes": extra,
-                "multi": multi, "surrogate": surrogate, "xsec": xsec, "lhe": lhe_leg, "qq_ttx": qq_leg}
+                "multi": multi, "surrogate": surrogate, "xsec": xsec, "lhe": lhe_leg, "qq_ttx": qq_leg,
+                "pp_ttx": pp_leg}
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist

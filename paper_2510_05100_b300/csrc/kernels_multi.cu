@@ -10,6 +10,8 @@
 // The per-tile code is exactly the single-process kernels' (QcdTile, QqTile, ee_tile).
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include "ee_kernel.cuh"
 #include "qcd_kernel.cuh"
 #include "qq_kernel.cuh"
@@ -18,7 +20,13 @@ namespace rex {
 
 static_assert(QQ_BLOCK == QCD_BLOCK, "every tile runs on the multi kernel's block size");
 
-template <typename R, bool WIDTH, int MINB, int S_TTX, int S_TTXG, int S_TTXGG, bool TC_TTXGG>
+// Register classes: the persistent kernel is compiled once per class with only
+// the tiles the class admits, so its register budget (and occupancy) follows the
+// heaviest process actually present in the launch:
+//   class 0: e+e- -> mu+mu-, g g -> t t~, q q~ -> t t~
+//   class 1: class 0 and g g -> t t~ g
+//   class 2: every process (g g -> t t~ g g sets the budget)
+template <typename R, bool WIDTH, int MINB, int CLASS, int S_TTX, int S_TTXG, int S_TTXGG, bool TC_TTXGG>
 __global__ void __launch_bounds__(QCD_BLOCK, MINB)
     multi_reweight_kernel(const __grid_constant__ MultiLaunch ml, unsigned long long* __restrict__ counter) {
   using T1 = QcdTile<PROC_GG_TTX, R, WIDTH, S_TTX>;
@@ -27,8 +35,8 @@ __global__ void __launch_bounds__(QCD_BLOCK, MINB)
   using T4 = QqTile<R>;
   union Smem {
     typename T1::Smem a;
-    typename T2::Smem b;
-    typename T3::Smem c;
+    typename std::conditional<(CLASS >= 1), typename T2::Smem, char>::type b;
+    typename std::conditional<(CLASS >= 2), typename T3::Smem, char>::type c;
     typename T4::Smem d;
   };
   __shared__ Smem sm;
@@ -46,8 +54,12 @@ __global__ void __launch_bounds__(QCD_BLOCK, MINB)
     switch (B.kind) {
       case PROC_EE_MUMU: ee_tile(B.mom, B.w_in, B.nev, tile, ml.ew, B.out); break;
       case PROC_GG_TTX: T1::run(sm.a, B.mom, B.w_in, B.nev, tile, B.t, B.out); break;
-      case PROC_GG_TTXG: T2::run(sm.b, B.mom, B.w_in, B.nev, tile, B.t, B.out); break;
-      case PROC_GG_TTXGG: T3::run(sm.c, B.mom, B.w_in, B.nev, tile, B.t, B.out); break;
+      case PROC_GG_TTXG:
+        if constexpr (CLASS >= 1) T2::run(sm.b, B.mom, B.w_in, B.nev, tile, B.t, B.out);
+        break;
+      case PROC_GG_TTXGG:
+        if constexpr (CLASS >= 2) T3::run(sm.c, B.mom, B.w_in, B.nev, tile, B.t, B.out);
+        break;
       case PROC_QQ_TTX: T4::run(sm.d, B.mom, B.w_in, B.nev, tile, B.t, B.out); break;
       default: break;
     }
@@ -55,75 +67,104 @@ __global__ void __launch_bounds__(QCD_BLOCK, MINB)
   }
 }
 
+int multi_class_of(int kind) {
+  return kind == PROC_GG_TTXGG ? 2 : (kind == PROC_GG_TTXG ? 1 : 0);
+}
+
 // Lanes-per-event split of each QCD process in the multi kernel (the defaults of
-// the single-process kernels: no split, scalar colour form).  One register budget
-// serves every process: min blocks per SM follows g g -> t t~ g g, the heaviest.
+// the single-process kernels: no split, scalar colour form) and the resident
+// blocks per SM the register allocator must allow, per register class: the
+// single-process kernels' best for the heaviest process of the class.
 #ifndef REX_MULTI_MINB
 #define REX_MULTI_MINB 1
 #endif
-template <typename R>
+template <typename R, int CLASS>
 struct MultiSplit;
-template <>
-struct MultiSplit<double> {
-  static constexpr int TTX = 0, TTXG = 0, TTXGG = 0, MINB = 1;
+template <int CLASS>
+struct MultiSplit<double, CLASS> {
+  static constexpr int TTX = 0, TTXG = 0, TTXGG = 0;
+  static constexpr int MINB = CLASS == 0 ? 3 : 1;
   static constexpr bool TC_TTXGG = false;
 };
-template <>
-struct MultiSplit<float> {
-  static constexpr int TTX = 0, TTXG = 0, TTXGG = 0, MINB = REX_MULTI_MINB;
+template <int CLASS>
+struct MultiSplit<float, CLASS> {
+  static constexpr int TTX = 0, TTXG = 0, TTXGG = 0;
+  static constexpr int MINB = CLASS == 0 ? 4 : (CLASS == 1 ? 3 : REX_MULTI_MINB);
   static constexpr bool TC_TTXGG = false;
 };
 
-template <typename R, bool WIDTH>
+template <typename R, bool WIDTH, int CLASS>
 static auto multi_kernel_ptr() {
-  using S = MultiSplit<R>;
-  return multi_reweight_kernel<R, WIDTH, S::MINB, S::TTX, S::TTXG, S::TTXGG, S::TC_TTXGG>;
+  using S = MultiSplit<R, CLASS>;
+  return multi_reweight_kernel<R, WIDTH, S::MINB, CLASS, S::TTX, S::TTXG, S::TTXGG, S::TC_TTXGG>;
 }
 
 int multi_events_per_tile(int kind, int mixed) {
+  (void)mixed;   // every class uses the unsplit mapping
   switch (kind) {
     case PROC_EE_MUMU: return 128;
-    case PROC_GG_TTX: return QCD_BLOCK / (4 << (mixed ? MultiSplit<float>::TTX : 0));
-    case PROC_GG_TTXG: return QCD_BLOCK / (8 << (mixed ? MultiSplit<float>::TTXG : 0));
-    case PROC_GG_TTXGG: return QCD_BLOCK / (16 << (mixed ? MultiSplit<float>::TTXGG : 0));
+    case PROC_GG_TTX: return QCD_BLOCK / 4;
+    case PROC_GG_TTXG: return QCD_BLOCK / 8;
+    case PROC_GG_TTXGG: return QCD_BLOCK / 16;
     case PROC_QQ_TTX: return QqTile<float>::EPB;
     default: return 0;
   }
 }
 
-int multi_grid_size(int mixed, int width, int* blocks) {
+template <typename R, bool WIDTH, int CLASS>
+static cudaError_t occupancy(int* per_sm) {
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, multi_kernel_ptr<R, WIDTH, CLASS>(), QCD_BLOCK, 0);
+}
+
+template <typename R, bool WIDTH>
+static cudaError_t occupancy_c(int cls, int* per_sm) {
+  switch (cls) {
+    case 0: return occupancy<R, WIDTH, 0>(per_sm);
+    case 1: return occupancy<R, WIDTH, 1>(per_sm);
+    default: return occupancy<R, WIDTH, 2>(per_sm);
+  }
+}
+
+int multi_grid_size(int mixed, int width, int cls, int* blocks) {
   int dev = 0, sms = 0, per_sm = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (e != cudaSuccess) return (int)e;
-  if (mixed)
-    e = width ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, multi_kernel_ptr<float, true>(), QCD_BLOCK, 0)
-              : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, multi_kernel_ptr<float, false>(), QCD_BLOCK, 0);
-  else
-    e = width ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, multi_kernel_ptr<double, true>(), QCD_BLOCK, 0)
-              : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, multi_kernel_ptr<double, false>(), QCD_BLOCK, 0);
+  if (mixed) e = width ? occupancy_c<float, true>(cls, &per_sm) : occupancy_c<float, false>(cls, &per_sm);
+  else e = width ? occupancy_c<double, true>(cls, &per_sm) : occupancy_c<double, false>(cls, &per_sm);
   if (e != cudaSuccess) return (int)e;
   *blocks = sms * (per_sm > 0 ? per_sm : 1);
   return 0;
 }
 
-template <typename R, bool WIDTH>
+template <typename R, bool WIDTH, int CLASS>
 static void launch_multi_t(int blocks, const MultiLaunch& ml, unsigned long long* counter, cudaStream_t st) {
-  using S = MultiSplit<R>;
-  multi_reweight_kernel<R, WIDTH, S::MINB, S::TTX, S::TTXG, S::TTXGG, S::TC_TTXGG><<<blocks, QCD_BLOCK, 0, st>>>(ml, counter);
+  using S = MultiSplit<R, CLASS>;
+  multi_reweight_kernel<R, WIDTH, S::MINB, CLASS, S::TTX, S::TTXG, S::TTXGG, S::TC_TTXGG>
+      <<<blocks, QCD_BLOCK, 0, st>>>(ml, counter);
 }
 
-int launch_multi(int mixed, int width, int blocks, const MultiLaunch& ml, unsigned long long* counter,
+template <typename R, bool WIDTH>
+static void launch_multi_c(int cls, int blocks, const MultiLaunch& ml, unsigned long long* counter,
+                           cudaStream_t st) {
+  switch (cls) {
+    case 0: launch_multi_t<R, WIDTH, 0>(blocks, ml, counter, st); break;
+    case 1: launch_multi_t<R, WIDTH, 1>(blocks, ml, counter, st); break;
+    default: launch_multi_t<R, WIDTH, 2>(blocks, ml, counter, st); break;
+  }
+}
+
+int launch_multi(int mixed, int width, int cls, int blocks, const MultiLaunch& ml, unsigned long long* counter,
                  void* stream) {
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(unsigned long long), st);
   if (e != cudaSuccess) return (int)e;
   if (mixed) {
-    if (width) launch_multi_t<float, true>(blocks, ml, counter, st);
-    else launch_multi_t<float, false>(blocks, ml, counter, st);
+    if (width) launch_multi_c<float, true>(cls, blocks, ml, counter, st);
+    else launch_multi_c<float, false>(cls, blocks, ml, counter, st);
   } else {
-    if (width) launch_multi_t<double, true>(blocks, ml, counter, st);
-    else launch_multi_t<double, false>(blocks, ml, counter, st);
+    if (width) launch_multi_c<double, true>(cls, blocks, ml, counter, st);
+    else launch_multi_c<double, false>(cls, blocks, ml, counter, st);
   }
   return (int)cudaGetLastError();
 }

@@ -6,6 +6,7 @@
 // computation: every |M|^2 and weight is produced by the kernels.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -291,7 +292,7 @@ struct rex_multi {
   cudaEvent_t fork, join[MULTI_MAX_BATCH];
   int device;
   unsigned long long* counter;   // device work counter (scratch), reset by every launch
-  int blocks[2];                 // persistent grid size without / with complex propagators
+  int blocks[MULTI_NCLASS][2];   // persistent grid size per register class, without / with complex propagators
   cudaStream_t cap_stream;
   cudaGraph_t graph;
   cudaGraphExec_t exec;
@@ -370,12 +371,13 @@ int multi_impl(rex_multi* m, const rex_batch* batches, int nbatch, const rex_par
     const int j1 = (k - j0) < MULTI_MAX_POINTS ? k : j0 + MULTI_MAX_POINTS;
     std::memset(&ml, 0, sizeof ml);
     int64_t total = 0;
-    int nb = 0, width = 0;
+    int nb = 0, width = 0, cls = 0;
     for (int oi = 0; oi < nbatch; ++oi) {
       const rex_batch& b = batches[order[oi]];
       if (b.nev == 0) continue;
       MultiBatch& B = ml.b[nb++];
       B.kind = b.proc->kind;
+      cls = std::max(cls, multi_class_of(B.kind));
       B.nev = b.nev;
       B.mom = b.momenta;
       B.w_in = b.w_in;
@@ -398,8 +400,8 @@ int multi_impl(rex_multi* m, const rex_batch* batches, int nbatch, const rex_par
     if (nb == 0) return REX_OK;
     ml.nbatch = nb;
     ml.total = total;
-    const int64_t grid = total < m->blocks[width] ? total : m->blocks[width];
-    const int err = launch_multi(mixed, width, (int)grid, ml, m->counter, stream);
+    const int64_t grid = total < m->blocks[cls][width] ? total : m->blocks[cls][width];
+    const int err = launch_multi(mixed, width, cls, (int)grid, ml, m->counter, stream);
     if (err != 0) return cuda_fail(err, "multi kernel launch");
   }
   return REX_OK;
@@ -423,14 +425,15 @@ int rex_multi_create(int precision, rex_multi** out) {
     delete m;
     return fail(REX_ENOMEM, "work-counter allocation failed: %s", cudaGetErrorString(e));
   }
-  for (int w = 0; w < 2; ++w) {
-    const int err = multi_grid_size(precision == REX_MIXED, w, &m->blocks[w]);
-    if (err != 0) {
-      cudaFree(m->counter);
-      delete m;
-      return cuda_fail(err, "occupancy query");
+  for (int c = 0; c < MULTI_NCLASS; ++c)
+    for (int w = 0; w < 2; ++w) {
+      const int err = multi_grid_size(precision == REX_MIXED, w, c, &m->blocks[c][w]);
+      if (err != 0) {
+        cudaFree(m->counter);
+        delete m;
+        return cuda_fail(err, "occupancy query");
+      }
     }
-  }
   e = cudaEventCreateWithFlags(&m->fork, cudaEventDisableTiming);
   for (int i = 0; i < MULTI_MAX_BATCH && e == cudaSuccess; ++i) {
     e = cudaStreamCreateWithFlags(&m->side[i], cudaStreamNonBlocking);
@@ -515,7 +518,7 @@ constexpr int NOALLOC_MAX_DEVICES = 64;
 struct NoallocDevice {
   bool ready;
   unsigned long long* counter;   // device address of g_noalloc_counter on this device
-  int blocks[2][2];              // persistent grid size [mixed][width]
+  int blocks[2][MULTI_NCLASS][2];   // persistent grid size [mixed][register class][width]
 };
 
 std::mutex g_noalloc_mutex;
@@ -535,10 +538,11 @@ int noalloc_setup(NoallocDevice** out) {
     e = cudaGetSymbolAddress(&ptr, g_noalloc_counter);
     if (e != cudaSuccess) return cuda_fail((int)e, "cudaGetSymbolAddress of the static work counter");
     for (int mixed = 0; mixed < 2; ++mixed)
-      for (int width = 0; width < 2; ++width) {
-        const int err = multi_grid_size(mixed, width, &d.blocks[mixed][width]);
-        if (err != 0) return cuda_fail(err, "occupancy query");
-      }
+      for (int c = 0; c < MULTI_NCLASS; ++c)
+        for (int width = 0; width < 2; ++width) {
+          const int err = multi_grid_size(mixed, width, c, &d.blocks[mixed][c][width]);
+          if (err != 0) return cuda_fail(err, "occupancy query");
+        }
     d.counter = static_cast<unsigned long long*>(ptr);
     d.ready = true;
   }
@@ -565,8 +569,7 @@ int rex_reweight_multi_noalloc(const rex_batch* batches, int nbatch, const rex_p
   std::memset(&tmp, 0, sizeof tmp);
   tmp.precision = precision;
   tmp.counter = d->counter;
-  tmp.blocks[0] = d->blocks[precision == REX_MIXED][0];
-  tmp.blocks[1] = d->blocks[precision == REX_MIXED][1];
+  std::memcpy(tmp.blocks, d->blocks[precision == REX_MIXED], sizeof tmp.blocks);
   return multi_impl(&tmp, batches, nbatch, param_sets, k, stream);
 }
 

@@ -87,9 +87,13 @@ struct MultiLaunch {
   EwTable ew;
 };
 
+// Register classes of the persistent kernel (kernels_multi.cu): the heaviest
+// process of a launch selects the instantiation and hence the register budget.
+constexpr int MULTI_NCLASS = 3;
+int multi_class_of(int kind);
 int multi_events_per_tile(int kind, int mixed);
-int multi_grid_size(int mixed, int width, int* blocks);
-int launch_multi(int mixed, int width, int blocks, const MultiLaunch& ml, unsigned long long* counter,
+int multi_grid_size(int mixed, int width, int cls, int* blocks);
+int launch_multi(int mixed, int width, int cls, int blocks, const MultiLaunch& ml, unsigned long long* counter,
                  void* stream);
 
 // Thread-mapping variants of the QCD kernels (see qcd_kernel.cuh).

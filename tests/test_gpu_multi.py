@@ -108,3 +108,25 @@ def test_multi_validation(rex):
         m.replay()                                    # nothing captured
     m.reweight([(p64, mom[:0], w[:0], wo[:0])], pts)  # empty batch: no-op
     m.reweight([(p64, mom, w, wo)], [])               # no points: no-op
+
+
+@pytest.mark.parametrize("subset", [("gg_ttx", "qq_ttx"), ("ee_mumu", "gg_ttx", "qq_ttx"),
+                                    ("gg_ttx", "gg_ttxg", "qq_ttx"), ("gg_ttxgg", "qq_ttx")])
+@pytest.mark.parametrize("precision", [0, 1])
+def test_register_classes(rex, subset, precision):
+    """The heaviest process of a launch picks the persistent kernel's register class
+    (light: e+e-, g g -> t t~, q q~ -> t t~; + g g -> t t~ g; + g g -> t t~ g g); every
+    class gives the single-process results."""
+    pts = points(16)
+    items = [it for it in setup(rex, precision, seed=31) if it[0] in subset]
+    m = rex.Multi(precision)
+    batches, single = [], []
+    for proc, p, mom, w in items:
+        dm, dw = dev(mom), dev(w)
+        batches.append((p, dm, dw, torch.zeros((mom.shape[0], len(pts)), dtype=torch.float64, device="cuda")))
+        single.append(p.reweight(dm, dw, pts).cpu().numpy())
+    m.reweight(batches, pts)
+    torch.cuda.synchronize()
+    for (proc, *_), b, ref in zip(items, batches, single):
+        assert np.max(np.abs(b[3].cpu().numpy() / ref - 1.0)) < 1e-13, proc
+    m.close()
