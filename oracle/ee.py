@@ -35,6 +35,41 @@ def _vector_current(left: np.ndarray, right: np.ndarray, cl: float, cr: float) -
     return np.einsum("ni,mij,nj->nm", left, mats, right)
 
 
+def me2_helicity(p: np.ndarray, mz: float, wz: float, sw2: float, alpha: float, hel: np.ndarray) -> np.ndarray:
+    """The term of the helicity sum (me2 = sum over configurations, same 1/4) of each
+    event's own configuration hel[N, 4] = (l1, l2, l3, l4), helicities +1/-1 of
+    e+, e-, mu+, mu- in the frame of the momenta."""
+    p = np.asarray(p, dtype=np.float64)
+    hel = np.asarray(hel)
+    out = np.zeros(p.shape[0])
+    for conf in itertools.product((-1, 1), repeat=4):
+        sel = np.all(hel == np.array(conf), axis=1)
+        if np.any(sel):
+            out[sel] = _config_me2(p[sel], mz, wz, sw2, alpha, conf)
+    return out
+
+
+def _config_me2(p, mz, wz, sw2, alpha, conf):
+    e = math.sqrt(4.0 * math.pi * alpha)
+    cw2 = 1.0 - sw2
+    gz = e / math.sqrt(sw2 * cw2)
+    gl = T3_LEPTON - Q_LEPTON * sw2
+    gr = -Q_LEPTON * sw2
+    p1, p2, p3, p4 = p[:, 0], p[:, 1], p[:, 2], p[:, 3]
+    q = p1 + p2
+    s = mdot(q, q)
+    l1, l2, l3, l4 = conf
+    vb1 = bar(spinor_v(p1, 0.0, l1))
+    u2 = spinor_u(p2, 0.0, l2)
+    v3 = spinor_v(p3, 0.0, l3)
+    ub4 = bar(spinor_u(p4, 0.0, l4))
+    amp = (-1j / s) * mdot(-1j * e * Q_LEPTON * _vector_current(vb1, u2, 1.0, 1.0),
+                           -1j * e * Q_LEPTON * _vector_current(ub4, v3, 1.0, 1.0))
+    amp = amp + (-1j / (s - mz * mz + 1j * mz * wz)) * mdot(-1j * gz * _vector_current(vb1, u2, gl, gr),
+                                                            -1j * gz * _vector_current(ub4, v3, gl, gr))
+    return np.abs(amp) ** 2 / 4.0
+
+
 def me2(p: np.ndarray, mz: float, wz: float, sw2: float, alpha: float) -> np.ndarray:
     p = np.asarray(p, dtype=np.float64)
     e = math.sqrt(4.0 * math.pi * alpha)

@@ -58,6 +58,24 @@ def amplitudes(p: np.ndarray, mt: float) -> np.ndarray:
     return np.stack(out, axis=1)
 
 
+def me2_helicity(p: np.ndarray, mt: float, wt: float, alphas: float, hel: np.ndarray) -> np.ndarray:
+    """The term of the helicity sum (me2 = sum over configurations) of each event's own
+    configuration hel[N, 4] = (l1, l2, l3, l4), helicities +1/-1 of q, q~, t, t~ in the
+    frame of the momenta (wt unused)."""
+    del wt
+    p = np.asarray(p, dtype=np.float64)
+    hel = np.asarray(hel)
+    g2 = 4.0 * math.pi * alphas
+    q = p[:, 0] + p[:, 1]
+    s = mdot(q, q)
+    amps = amplitudes(p, mt)   # [N, 16] in itertools.product((-1, 1), repeat=4) order
+    out = np.zeros(p.shape[0])
+    for i, conf in enumerate(itertools.product((-1, 1), repeat=4)):
+        sel = np.all(hel == np.array(conf), axis=1)
+        out[sel] = (g2 * g2 * colour_factor() * np.abs(amps[sel, i]) ** 2 / (s[sel] * s[sel]) / 36.0)
+    return out
+
+
 def me2(p: np.ndarray, mt: float, wt: float, alphas: float) -> np.ndarray:
     """Spin/colour summed and averaged |M|^2 for q q~ -> t t~, one point (wt unused)."""
     del wt

@@ -3,7 +3,9 @@
 w'_{e,j} = w_e |M(p_e; theta_j)|^2 / |M(p_e; theta_0)|^2  (paper Sec. 3, the
 weight factorisation), with the teaRex normaliser convention (Sec. 3.1.1):
 the normaliser is 1/|M|^2 with 1/0 mapped to 0, so an event whose original
-|M|^2 is zero gets new weights 0.
+|M|^2 is zero gets new weights 0.  Helicity-exclusive reweighting (the
+alternative to the helicity-summed default, Sec. 4.1.2) takes the same ratio of
+the event's own helicity configuration.
 """
 from __future__ import annotations
 
@@ -25,6 +27,36 @@ def me2(process: str, p: np.ndarray, point: dict) -> np.ndarray:
     if process == "qq_ttx":
         return qq.me2(p, point["mt"], point.get("wt", 0.0), point["alphas"])
     raise ValueError(f"unknown process {process!r}")
+
+
+# A configuration that vanishes identically (a massless fermion pair of equal
+# helicities in a vector current) comes out of the explicit spinors as a rounding
+# residue of about 1e-32 of the event's helicity sum; below this fraction a term is
+# taken as the exact zero it is (physical terms, helicity flips ~ m^2/s included,
+# are many orders above it).
+ZERO_TERM = 1e-24
+
+
+def me2_helicity(process: str, p: np.ndarray, point: dict, hel: np.ndarray) -> np.ndarray:
+    """The helicity-sum term of each event's own helicity configuration hel[N, npart]
+    (processes whose amplitudes are evaluated in a helicity basis)."""
+    if process == "ee_mumu":
+        m = ee.me2_helicity(p, point["mz"], point["wz"], point["sw2"], point["alpha"], hel)
+    elif process == "qq_ttx":
+        m = qq.me2_helicity(p, point["mt"], point.get("wt", 0.0), point["alphas"], hel)
+    else:
+        raise ValueError(f"no helicity-exclusive evaluation for {process!r}")
+    return np.where(m < ZERO_TERM * me2(process, p, point), 0.0, m)
+
+
+def reweight_helicity(process: str, p: np.ndarray, hel: np.ndarray, w_in: np.ndarray, original: dict,
+                      points: list[dict]) -> np.ndarray:
+    """Helicity-exclusive new weights [N, k]: w |M_h(theta_j)|^2 / |M_h(theta_0)|^2 with h
+    the event's own configuration, and 0 where |M_h(theta_0)|^2 == 0."""
+    m0 = me2_helicity(process, p, original, hel)
+    mk = (np.stack([me2_helicity(process, p, pt, hel) for pt in points]) if points
+          else np.zeros((0, p.shape[0])))
+    return ratio_epilogue(w_in, m0, mk)
 
 
 def ratio_epilogue(w_in: np.ndarray, me2_orig: np.ndarray, me2_new: np.ndarray) -> np.ndarray:

@@ -46,6 +46,51 @@ def ee_mumu_closed_form(p, mz, wz, sw2, alpha):
     return e2 * e2 / 4.0 * tot
 
 
+def ee_mumu_helicity_closed_form(p, hel, mz, wz, sw2, alpha):
+    """One helicity configuration (l1, l2, l3, l4) of e+ e- mu+ mu-, with the same 1/4:
+    (e^4/4) |Q^2 + g_X g_Y s/(sW^2 cW^2 (s - mZ^2 + i mZ GZ))|^2 (1 + eta cos)^2, X (Y) the
+    chirality of the e- (mu-): L for helicity -1; eta = +1 if X == Y; 0 unless the e+ and
+    the mu+ have the helicities opposite to the e- and the mu-."""
+    e2 = 4.0 * math.pi * alpha
+    cw2 = 1.0 - sw2
+    g = {-1: -0.5 + sw2, 1: sw2}
+    s = mdot(p[:, 0] + p[:, 1], p[:, 0] + p[:, 1])
+    n_e = p[:, 1, 1:] / np.linalg.norm(p[:, 1, 1:], axis=1)[:, None]
+    n_mu = p[:, 3, 1:] / np.linalg.norm(p[:, 3, 1:], axis=1)[:, None]
+    c = (n_e * n_mu).sum(1)
+    prop = s / (s - mz * mz + 1j * mz * wz)
+    out = np.zeros(p.shape[0])
+    for i, (l1, l2, l3, l4) in enumerate(hel):
+        if l1 != -l2 or l3 != -l4:
+            continue
+        eta = 1.0 if l2 == l4 else -1.0
+        out[i] = e2 * e2 / 4.0 * abs(1.0 + g[l2] * g[l4] / (sw2 * cw2) * prop[i]) ** 2 * (1.0 + eta * c[i]) ** 2
+    return out
+
+
+def qq_qq_helicity_cm(p, hel, m, alphas):
+    """q q~ -> Q Q~ per helicity configuration (l1, l2, l3, l4) in the centre-of-mass frame,
+    spin average 1/4 and colour included: g_s^4/18 (1 + l1 l3 cos)^2 when l3 = -l4 and
+    g_s^4/18 (1 - beta^2) sin^2 when l3 = l4; 0 unless l2 = -l1 (massless q, q~).  cos is
+    the angle between q and Q, beta the velocity of Q.  The 16 terms add up to the
+    Combridge form."""
+    gs2 = 4.0 * math.pi * alphas
+    nq = p[:, 0, 1:] / np.linalg.norm(p[:, 0, 1:], axis=1)[:, None]
+    pq = np.linalg.norm(p[:, 2, 1:], axis=1)
+    nQ = p[:, 2, 1:] / pq[:, None]
+    c = (nq * nQ).sum(1)
+    beta2 = (pq / p[:, 2, 0]) ** 2
+    out = np.zeros(p.shape[0])
+    for i, (l1, l2, l3, l4) in enumerate(hel):
+        if l2 != -l1:
+            continue
+        if l3 == -l4:
+            out[i] = gs2 * gs2 / 18.0 * (1.0 + l1 * l3 * c[i]) ** 2
+        else:
+            out[i] = gs2 * gs2 / 18.0 * (1.0 - beta2[i]) * (1.0 - c[i] * c[i])
+    return out
+
+
 def qed_limit_closed_form(p, alpha):
     """e^4 (1 + cos^2 theta): pure photon exchange (Peskin & Schroeder eq. 5.10)."""
     e2 = 4.0 * math.pi * alpha
