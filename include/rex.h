@@ -114,6 +114,26 @@ int rex_reweight(rex_proc *proc, const double *momenta, const double *w_in,
                  int64_t nev, const rex_params *param_sets, int k,
                  double *w_out, void *stream);
 
+/* Helicity-exclusive reweighting: the alternative to the helicity-summed default
+ * that MG5aMC reweighting offers (Sec. 4.1.2).  Each event keeps the helicity
+ * configuration it was generated with, and
+ *     w'_e = w_e |M_h(theta')|^2 / |M_h(theta_0)|^2,   h = the event's configuration,
+ * with |M_h|^2 colour-summed (and averaged) as in the helicity sum, so that summing
+ * it over configurations gives |M|^2.  A configuration whose |M_h(theta_0)|^2 is 0
+ * (in particular one that the chirality of a massless fermion pair forbids) gives 0
+ * (Sec. 3.1.1's 1/0 -> 0 rule).
+ *   helicities  device, [nev][npart] int8 in the process's particle order:
+ *               helicities in the frame of the momenta, +1 / -1 (a positive value
+ *               reads as +1, any other as -1); no alignment requirement
+ *   other arguments as rex_reweight.
+ * Processes: ee_mumu and qq_ttx, whose kernels evaluate helicity amplitudes; the
+ * g g processes sum real linear gluon polarisations and return REX_EUNSUPPORTED.
+ * Enqueue only.  Errors: REX_EUNSUPPORTED, REX_EINVAL (as rex_reweight, null
+ * helicities), REX_ENOTINIT, REX_ECUDA. */
+int rex_reweight_helicity(rex_proc *proc, const double *momenta, const signed char *helicities,
+                          const double *w_in, int64_t nev, const rex_params *param_sets, int k,
+                          double *w_out, void *stream);
+
 /* Same computation with HOST arrays: copies momenta and w_in to the device,
  * reweights, copies w_out back and synchronises stream before returning.
  * Page-locked host memory makes the copies asynchronous DMA.  Device

@@ -47,9 +47,14 @@ __device__ __forceinline__ cx<double> cmdot(const cx<double>* a, const cx<double
 // 16 configurations only (l1, l2, l3, l4) = (+,-,+,-), (-,+,+,-), (+,-,-,+), (-,+,-,+)
 // (h = 5, 6, 9, 10) reach H; the other 12 contribute exact zeros (their spinor halves
 // are w- chi with w- = 0/w+ = 0), so summing the 4 gives the same H bit for bit.
-template <class TABLE>
+//
+// Helicity-exclusive form (EXCL): H is built from the event's own configuration
+// hel[ev][0..3] = (l1, l2, l3, l4) (positive: +1, otherwise -1) alone; a configuration
+// the chirality rule forbids gives H = 0, hence |M_0|^2 = 0 and new weights 0.
+template <class TABLE, bool EXCL = false>
 __device__ __forceinline__ void ee_tile(const double* __restrict__ mom, const double* __restrict__ w_in,
-                                        int64_t nev, int64_t tile, const TABLE& lp, double* __restrict__ out) {
+                                        int64_t nev, int64_t tile, const TABLE& lp, double* __restrict__ out,
+                                        const signed char* __restrict__ hel = nullptr) {
   const int64_t ev = tile * 128 + threadIdx.x;
   if (ev >= nev) return;
   double p[4][4];
@@ -68,9 +73,14 @@ __device__ __forceinline__ void ee_tile(const double* __restrict__ mom, const do
   // H: diagonal (real) and upper triangle (complex) of the 4x4 Hermitian form
   double hd[4] = {0.0, 0.0, 0.0, 0.0};
   cx<double> ho[6] = {};
+  int hev = 0;
+  if constexpr (EXCL) {
+    const signed char* he = hel + ev * 4;
+    hev = (he[0] > 0 ? 1 : 0) | (he[1] > 0 ? 2 : 0) | (he[2] > 0 ? 4 : 0) | (he[3] > 0 ? 8 : 0);
+  }
 #pragma unroll 1
-  for (int hi = 0; hi < 4; ++hi) {
-    const int h = ((hi & 1) ? 6 : 5) + ((hi & 2) ? 4 : 0);   // 5, 6, 9, 10
+  for (int hi = 0; hi < (EXCL ? 1 : 4); ++hi) {
+    const int h = EXCL ? hev : ((hi & 1) ? 6 : 5) + ((hi & 2) ? 4 : 0);   // 5, 6, 9, 10
     const int l1 = (h & 1) ? 1 : -1, l2 = (h & 2) ? 1 : -1;
     const int l3 = (h & 4) ? 1 : -1, l4 = (h & 8) ? 1 : -1;
     cx<double> v1[4], u2[4], v3[4], u4[4];
@@ -137,10 +147,12 @@ __device__ __forceinline__ void ee_tile(const double* __restrict__ mom, const do
   }
 }
 
+template <bool EXCL>
 static __global__ void __launch_bounds__(128)
     ee_reweight_kernel(const double* __restrict__ mom, const double* __restrict__ w_in, int64_t nev,
-                       const __grid_constant__ EwLaunch lp, double* __restrict__ out) {
-  ee_tile(mom, w_in, nev, (int64_t)blockIdx.x, lp, out);
+                       const __grid_constant__ EwLaunch lp, double* __restrict__ out,
+                       const signed char* __restrict__ hel) {
+  ee_tile<EwLaunch, EXCL>(mom, w_in, nev, (int64_t)blockIdx.x, lp, out, hel);
 }
 
 }  // namespace rex

@@ -80,4 +80,52 @@ __device__ __forceinline__ void qq_ttx_coefficients(const R (&p)[4][4], R* c, R*
   *e12 = e1 * e2;
 }
 
+// Helicity-exclusive form: the term of one configuration (l1, l2, l3, l4) (positive:
+// +1, otherwise -1) as C0 + C2 m^2 + C4 m^4 in the same normalisation.  Equal q, q~
+// helicities give exact zeros (chirality).  For the top pair q = (l3, l4):
+//   (+,+): C2 = r^2 LL + RR / r^2 - 2 LR;   (-,-): C2 = LL / r^2 + r^2 RR - 2 LR;
+//   (+,-): C0 = W^2 RR, C2 = -2 LR, C4 = LL / W^2;   (-,+): C0 = W^2 LL, C2 = -2 LR, C4 = RR / W^2,
+// with LL = |DL|^2, RR = |DR|^2, LR = Re(DL* DR) of the one incoming current.
+template <typename R>
+__device__ __forceinline__ void qq_ttx_coefficients_h(const R (&p)[4][4], int l1, int l2, int l3, int l4, R* c,
+                                                      R* e12) {
+  cx<R> x1[2][2], x2[2][2], x3[2][2], x4[2][2];   // [0] = chi-, [1] = chi+
+  const R e1 = chis(p[0], x1[0], x1[1]);
+  const R e2 = chis(p[1], x2[0], x2[1]);
+  const R e3 = chis(p[2], x3[0], x3[1]);
+  const R e4 = chis(p[3], x4[0], x4[1]);
+  *e12 = e1 * e2;
+  c[0] = c[1] = c[2] = R(0);
+  if ((l1 > 0) == (l2 > 0)) return;
+  cx<R> J[4], S[4];
+  if (l1 > 0) {
+    sigma_bilinear(x2[1], x1[1], J);            // (+, -): sigma
+  } else {
+    sigma_bilinear(x2[0], x1[0], J);            // (-, +): sigmabar
+#pragma unroll
+    for (int m = 1; m < 4; ++m) J[m] = cx<R>{-J[m].re, -J[m].im};
+  }
+  sigma_bilinear(x3[l3 > 0 ? 1 : 0], x4[l4 > 0 ? 0 : 1], S);
+  const cx<R> t0 = J[0] * S[0];
+  const cx<R> t1 = J[1] * S[1] + J[2] * S[2] + J[3] * S[3];
+  const cx<R> dl = t0 + t1, dr = t0 - t1;
+  const R ll = dl.re * dl.re + dl.im * dl.im;
+  const R rr = dr.re * dr.re + dr.im * dr.im;
+  const R lr = dl.re * dr.re + dl.im * dr.im;
+  const R w2 = e3 * e4;
+  const R iw2 = R(1) / w2;
+  const R r2 = e4 * e4 * iw2, ir2 = e3 * e3 * iw2;
+  if ((l3 > 0) == (l4 > 0)) {
+    c[1] = (l3 > 0 ? r2 * ll + ir2 * rr : ir2 * ll + r2 * rr) - R(2) * lr;
+  } else if (l3 > 0) {
+    c[0] = w2 * rr;
+    c[1] = R(-2) * lr;
+    c[2] = iw2 * ll;
+  } else {
+    c[0] = w2 * ll;
+    c[1] = R(-2) * lr;
+    c[2] = iw2 * rr;
+  }
+}
+
 }  // namespace rex

@@ -156,10 +156,12 @@ struct QqTile {
     }
   }
 
-  template <class TABLE>
+  // EXCL: helicity-exclusive, hel[ev][0..3] = the event's (l1, l2, l3, l4)
+  template <bool EXCL = false, class TABLE>
   static __device__ __forceinline__ void run(Smem& sm, const double* __restrict__ mom,
                                              const double* __restrict__ w_in, int64_t nev, int64_t tile,
-                                             const TABLE& lp, double* __restrict__ out) {
+                                             const TABLE& lp, double* __restrict__ out,
+                                             const signed char* __restrict__ hel = nullptr) {
     const int tid = threadIdx.x;
     const int64_t ev0 = tile * EPB;
     const int nblk = (int)((nev - ev0) < EPB ? (nev - ev0) : EPB);
@@ -222,7 +224,12 @@ struct QqTile {
         }
       }
       R c[3], e12;
-      qq_ttx_coefficients<R>(p, c, &e12);
+      if constexpr (EXCL) {
+        const signed char* he = hel + (ev0 + tid) * 4;
+        qq_ttx_coefficients_h<R>(p, he[0], he[1], he[2], he[3], c, &e12);
+      } else {
+        qq_ttx_coefficients<R>(p, c, &e12);
+      }
       const R m0sq = sm.m0sq;
       R p0 = (c[2] * m0sq + c[1]) * m0sq + c[0];
       // a non-finite momentum (in the mixed mode also one beyond the FP32 range) makes

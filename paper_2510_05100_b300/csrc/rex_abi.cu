@@ -92,13 +92,13 @@ int default_variant(int kind, int precision) {
 }
 
 int launch_qcd(const rex_proc* p, const double* mom, const double* w_in, int64_t nev, const QcdLaunch& lp,
-               double* out, void* stream) {
+               double* out, void* stream, const signed char* hel) {
   const int mixed = p->precision == REX_MIXED;
   switch (p->kind) {
     case PROC_GG_TTX: return launch_gg_ttx(mixed, p->variant, mom, w_in, nev, lp, out, stream);
     case PROC_GG_TTXG: return launch_gg_ttxg(mixed, p->variant, mom, w_in, nev, lp, out, stream);
     case PROC_GG_TTXGG: return launch_gg_ttxgg(mixed, p->variant, mom, w_in, nev, lp, out, stream);
-    case PROC_QQ_TTX: return launch_qq_ttx(mixed, mom, w_in, nev, lp, out, stream);
+    case PROC_QQ_TTX: return launch_qq_ttx(mixed, mom, w_in, nev, lp, out, stream, hel);
     default: return (int)cudaErrorInvalidValue;
   }
 }
@@ -155,7 +155,7 @@ EwPoint ew_point(const rex_params& p) {
 // Enqueue one QCD launch for points [j0, j1) writing columns j0.. of rows with stride k.
 int run_qcd_chunk(rex_proc* p, const double* mom, const double* w_in, int64_t nev,
                   const rex_params* pts, int j0, int j1, int mode, double* out, int64_t stride,
-                  void* stream, int* next_j) {
+                  void* stream, int* next_j, const signed char* hel = nullptr) {
   const ProcInfo& pi = info_of(p->kind);
   QcdLaunch lp;
   std::memset(&lp, 0, sizeof lp);
@@ -191,14 +191,14 @@ int run_qcd_chunk(rex_proc* p, const double* mom, const double* w_in, int64_t ne
     if (lp.width[s] != 0.0) lp.has_width = 1;
   *next_j = j;
   double* o = (mode == OUT_RATIO) ? out + j0 : out;
-  const int err = launch_qcd(p, mom, w_in, nev, lp, o, stream);
+  const int err = launch_qcd(p, mom, w_in, nev, lp, o, stream, hel);
   if (err != 0) return cuda_fail(err, "kernel launch");
   return REX_OK;
 }
 
 int run_ee_chunk(rex_proc* p, const double* mom, const double* w_in, int64_t nev,
                  const rex_params* pts, int j0, int j1, int mode, double* out, int64_t stride,
-                 void* stream, int* next_j) {
+                 void* stream, int* next_j, const signed char* hel = nullptr) {
   EwLaunch lp;
   std::memset(&lp, 0, sizeof lp);
   lp.mode = mode;
@@ -209,7 +209,7 @@ int run_ee_chunk(rex_proc* p, const double* mom, const double* w_in, int64_t nev
   lp.k = j - j0;
   *next_j = j;
   double* o = (mode == OUT_RATIO) ? out + j0 : out;
-  const int err = launch_ee(mom, w_in, nev, lp, o, stream);
+  const int err = launch_ee(mom, w_in, nev, lp, o, stream, hel);
   if (err != 0) return cuda_fail(err, "kernel launch");
   return REX_OK;
 }
@@ -221,7 +221,8 @@ int validate_proc(const rex_proc* p) {
 }
 
 int reweight_impl(rex_proc* p, const double* momenta, const double* w_in, int64_t nev,
-                  const rex_params* param_sets, int k, double* w_out, void* stream) {
+                  const rex_params* param_sets, int k, double* w_out, void* stream,
+                  const signed char* hel = nullptr) {
   int rc = validate_proc(p);
   if (rc) return rc;
   if (nev < 0) return fail(REX_EINVAL, "nev < 0");
@@ -239,8 +240,8 @@ int reweight_impl(rex_proc* p, const double* momenta, const double* w_in, int64_
   while (j < k) {
     int next = j;
     rc = p->kind == PROC_EE_MUMU
-             ? run_ee_chunk(p, momenta, w_in, nev, param_sets, j, k, OUT_RATIO, w_out, k, stream, &next)
-             : run_qcd_chunk(p, momenta, w_in, nev, param_sets, j, k, OUT_RATIO, w_out, k, stream, &next);
+             ? run_ee_chunk(p, momenta, w_in, nev, param_sets, j, k, OUT_RATIO, w_out, k, stream, &next, hel)
+             : run_qcd_chunk(p, momenta, w_in, nev, param_sets, j, k, OUT_RATIO, w_out, k, stream, &next, hel);
     if (rc) return rc;
     j = next;
   }
@@ -637,6 +638,20 @@ int rex_set_params(rex_proc* proc, const rex_params* original) {
 int rex_reweight(rex_proc* proc, const double* momenta, const double* w_in, int64_t nev,
                  const rex_params* param_sets, int k, double* w_out, void* stream) {
   return reweight_impl(proc, momenta, w_in, nev, param_sets, k, w_out, stream);
+}
+
+int rex_reweight_helicity(rex_proc* proc, const double* momenta, const signed char* helicities,
+                          const double* w_in, int64_t nev, const rex_params* param_sets, int k, double* w_out,
+                          void* stream) {
+  const int rc = validate_proc(proc);
+  if (rc) return rc;
+  if (proc->kind != PROC_EE_MUMU && proc->kind != PROC_QQ_TTX)
+    return fail(REX_EUNSUPPORTED,
+                "helicity-exclusive reweighting needs helicity-basis amplitudes: ee_mumu and qq_ttx have them, "
+                "'%s' sums linear gluon polarisations",
+                info_of(proc->kind).name);
+  if (nev > 0 && k > 0 && !helicities) return fail(REX_EINVAL, "null helicity array");
+  return reweight_impl(proc, momenta, w_in, nev, param_sets, k, w_out, stream, helicities);
 }
 
 static int grow(double** buf, size_t* cap, size_t need) {

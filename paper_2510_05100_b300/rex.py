@@ -36,7 +36,7 @@ SURROGATE_LAYERED = 1
 
 # symbols declared in include/rex.h
 EXPORTS = (
-    "rex_init_process", "rex_process_npart", "rex_set_flags", "rex_set_params",
+    "rex_init_process", "rex_process_npart", "rex_set_flags", "rex_set_params", "rex_reweight_helicity",
     "rex_reweight", "rex_reweight_host", "rex_me2", "rex_free_process",
     "rex_last_error", "rex_version", "rex_probe_fma", "rex_probe_convert", "rex_num_variants", "rex_get_variant",
     "rex_set_variant", "rex_autotune", "rex_multi_create", "rex_reweight_multi", "rex_multi_capture",
@@ -98,6 +98,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.rex_set_params.restype = ctypes.c_int
     lib.rex_reweight.argtypes = [vp, vp, vp, i64, pp, ctypes.c_int, vp, vp]
     lib.rex_reweight.restype = ctypes.c_int
+    lib.rex_reweight_helicity.argtypes = [vp, vp, vp, vp, i64, pp, ctypes.c_int, vp, vp]
+    lib.rex_reweight_helicity.restype = ctypes.c_int
     lib.rex_reweight_host.argtypes = [vp, vp, vp, i64, pp, ctypes.c_int, vp, vp]
     lib.rex_reweight_host.restype = ctypes.c_int
     lib.rex_me2.argtypes = [vp, vp, i64, pp, vp, vp]
@@ -276,6 +278,21 @@ class Process:
         arr = _param_array(points)
         _check(load().rex_reweight(self._h, _ptr(momenta), _ptr(w_in), nev, arr, k,
                                    _ptr(w_out), _stream_ptr(stream)))
+        return w_out
+
+    def reweight_helicity(self, momenta, helicities, w_in, points: Sequence[dict], w_out=None, stream=None):
+        """Helicity-exclusive reweighting: helicities is a device int8 tensor [nev, npart] of
+        +1/-1 (the events' own configurations); otherwise as reweight."""
+        import torch
+        nev = momenta.shape[0]
+        k = len(points)
+        if helicities.dtype != torch.int8 or not helicities.is_contiguous():
+            raise ValueError("helicities must be a contiguous int8 tensor [nev, npart]")
+        if w_out is None:
+            w_out = torch.empty((nev, k), dtype=torch.float64, device=momenta.device)
+        arr = _param_array(points)
+        _check(load().rex_reweight_helicity(self._h, _ptr(momenta), _ptr(helicities), _ptr(w_in), nev, arr, k,
+                                            _ptr(w_out), _stream_ptr(stream)))
         return w_out
 
     def reweight_host(self, momenta, w_in, points: Sequence[dict], w_out, stream=None) -> None:

@@ -80,3 +80,21 @@ def test_ee_point_validation(rex):
         p.set_params(mz=91.1876, wz=2.4952, sw2=1.5, alpha=1 / 132.507)
     p.set_params(mz=91.1876, wz=2.4952, sw2=0.2312, alpha=1 / 132.507)
     p.close()
+
+
+def test_helicity_exclusive_validation_before_any_device_work(rex):
+    lib = rex.load()
+    pts = (rex.Params * 1)(rex.params(dict(mt=171.0, alphas=0.118)))
+    fake = ctypes.c_void_p(0x10000)     # never dereferenced: validation fails first
+    g = rex.Process("gg_ttxg")
+    g.set_params(mt=173.0, alphas=0.118)
+    assert lib.rex_reweight_helicity(g._h, fake, fake, fake, 10, pts, 1, fake, None) == rex.REX_EUNSUPPORTED
+    assert b"linear gluon polarisations" in lib.rex_last_error()
+    q = rex.Process("qq_ttx")
+    assert lib.rex_reweight_helicity(q._h, fake, fake, fake, 10, pts, 1, fake, None) == rex.REX_ENOTINIT
+    q.set_params(mt=173.0, alphas=0.118)
+    assert lib.rex_reweight_helicity(q._h, fake, None, fake, 10, pts, 1, fake, None) == rex.REX_EINVAL
+    assert lib.rex_reweight_helicity(q._h, None, None, None, 0, pts, 1, None, None) == rex.REX_OK
+    assert lib.rex_reweight_helicity(None, fake, fake, fake, 10, pts, 1, fake, None) == rex.REX_EINVAL
+    g.close()
+    q.close()

@@ -1,0 +1,81 @@
+"""Helicity-exclusive reweighting on the GPU vs the oracle, through the C ABI (needs a B300).
+
+Each event carries a random helicity configuration, forbidden ones included (they
+must give weight 0); tolerances as for the helicity sum: FP64 1e-12 relative,
+q q~ -> t t~ mixed 1e-5.
+"""
+import numpy as np
+import pytest
+
+from rexlib import ensure_built
+from oracle import reweight as oracle_rw
+from paper_2510_05100_b300 import phase_space as ps
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+QCD_ORIG = dict(mt=173.0, wt=0.0, alphas=0.118)
+
+
+@pytest.fixture(scope="module")
+def rex():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return ensure_built()
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def case(proc, n, seed):
+    mom = ps.make_events(proc, n, seed)
+    hel = np.random.default_rng(seed).choice(np.array([-1, 1], dtype=np.int8), size=(n, 4))
+    w = np.random.default_rng(seed + 1).uniform(-0.5, 2.0, n)
+    if proc == "ee_mumu":
+        return mom, hel, w, ps.EE_ORIGINAL, [ps.EE_NEW, dict(ps.EE_NEW, mz=91.5), ps.EE_ORIGINAL]
+    pts = ps.grid_gg_ttxg()[::3] + [QCD_ORIG, dict(mt=173.0, wt=0.0, alphas=0.124), dict(mt=168.0, wt=1.3, alphas=0.12)]
+    return mom, hel, w, QCD_ORIG, pts
+
+
+@pytest.mark.parametrize("proc,precision,tol", [("ee_mumu", 0, 1e-12), ("qq_ttx", 0, 1e-12), ("qq_ttx", 1, 1e-5)])
+def test_parity_with_forbidden_configurations(rex, proc, precision, tol):
+    n = 777   # several tiles, ragged tail
+    mom, hel, w, orig, pts = case(proc, n, 61)
+    p = rex.Process(proc, precision)
+    p.set_params(orig)
+    got = p.reweight_helicity(dev(mom), dev(hel), dev(w), pts).cpu().numpy()
+    ref = oracle_rw.reweight_helicity(proc, mom, hel, w, orig, pts)
+    zero = ref[:, 0] == 0.0
+    assert np.any(zero) and np.all(got[zero] == 0.0)
+    err = np.abs(got[~zero] - ref[~zero]) / np.abs(ref[~zero])
+    assert np.max(err) < tol
+    # an unchanged point keeps the weight exactly (0 for a forbidden configuration)
+    j = [i for i, pt in enumerate(pts) if pt == orig][0]
+    assert np.array_equal(got[~zero, j], w[~zero])
+
+
+def test_summing_configurations_gives_the_helicity_sum(rex):
+    """|M|^2 at a new point as the sum over the 16 configurations of
+    w_h' = |M_h'|^2 / |M_0|^2 ... checked through the weights: sum_h w'_h |M_h,0|^2 = w' |M_0|^2."""
+    n = 64
+    mom = ps.make_events("qq_ttx", n, 62)
+    idx = np.repeat(np.arange(n), 16)
+    confs = np.array(np.meshgrid(*[[-1, 1]] * 4, indexing="ij")).reshape(4, -1).T.astype(np.int8)
+    hel = np.tile(confs, (n, 1))
+    pts = [dict(mt=170.0, wt=0.0, alphas=0.118)]
+    p = rex.Process("qq_ttx", 0)
+    p.set_params(QCD_ORIG)
+    wh = p.reweight_helicity(dev(mom[idx]), dev(hel), dev(np.ones(16 * n)), pts).cpu().numpy()[:, 0]
+    m0h = oracle_rw.me2_helicity("qq_ttx", mom[idx], QCD_ORIG, hel)
+    summed = (wh * m0h).reshape(n, 16).sum(axis=1) / oracle_rw.me2("qq_ttx", mom, QCD_ORIG)
+    ws = p.reweight(dev(mom), dev(np.ones(n)), pts).cpu().numpy()[:, 0]
+    assert np.max(np.abs(summed / ws - 1.0)) < 1e-12
+
+
+def test_unsupported_processes_raise(rex):
+    p = rex.Process("gg_ttx", 0)
+    p.set_params(QCD_ORIG)
+    mom = dev(ps.make_events("gg_ttx", 4, 1))
+    with pytest.raises(rex.RexError):
+        p.reweight_helicity(mom, dev(np.ones((4, 4), dtype=np.int8)), dev(np.ones(4)), [QCD_ORIG])
