@@ -1,8 +1,11 @@
 """Helicity-exclusive reweighting on the GPU vs the oracle, through the C ABI (needs a B300).
 
 Each event carries a random helicity configuration, forbidden ones included (they
-must give weight 0); tolerances as for the helicity sum: FP64 1e-12 relative,
-q q~ -> t t~ mixed 1e-5.
+must give weight 0).  Tolerance: the helicity sum's (FP64 1e-12, q q~ -> t t~ mixed
+1e-5), or, for a term far below its event's helicity sum, the conditioning bound
+64 eps (sqrt(kappa_0) + sqrt(kappa_j)) with kappa = |M|^2 / |M_h|^2 at each point:
+the amplitude components are of the size of the whole sum's, so the absolute rounding
+of a small A_h is a relative error of about eps |A_typical| / |A_h| on |A_h|^2.
 """
 import numpy as np
 import pytest
@@ -28,6 +31,16 @@ def dev(a):
     return torch.from_numpy(np.ascontiguousarray(a)).cuda()
 
 
+def tolerance(proc, mom, hel, orig, pts, floor, eps):
+    """Per (event, point): max(floor, 64 eps (sqrt(kappa_0) + sqrt(kappa_j)))."""
+    def sqrt_kappa(pt):
+        mh = oracle_rw.me2_helicity(proc, mom, pt, hel)
+        return np.sqrt(oracle_rw.me2(proc, mom, pt) / np.where(mh > 0, mh, np.inf))
+    k0 = sqrt_kappa(orig)
+    kj = np.stack([sqrt_kappa(pt) for pt in pts], axis=1)
+    return np.maximum(floor, 64.0 * eps * (k0[:, None] + kj))
+
+
 def case(proc, n, seed):
     mom = ps.make_events(proc, n, seed)
     hel = np.random.default_rng(seed).choice(np.array([-1, 1], dtype=np.int8), size=(n, 4))
@@ -48,8 +61,12 @@ def test_parity_with_forbidden_configurations(rex, proc, precision, tol):
     ref = oracle_rw.reweight_helicity(proc, mom, hel, w, orig, pts)
     zero = ref[:, 0] == 0.0
     assert np.any(zero) and np.all(got[zero] == 0.0)
-    err = np.abs(got[~zero] - ref[~zero]) / np.abs(ref[~zero])
-    assert np.max(err) < tol
+    eps = np.finfo(np.float64 if precision == 0 else np.float32).eps / 2
+    bound = tolerance(proc, mom, hel, orig, pts, tol, eps)
+    err = np.abs(got - ref) / np.where(ref != 0.0, np.abs(ref), 1.0)
+    assert np.all(err[~zero] < bound[~zero])
+    # most terms meet the helicity sum's tolerance outright
+    assert np.mean(err[~zero] < tol) > 0.99
     # an unchanged point keeps the weight exactly (0 for a forbidden configuration)
     j = [i for i, pt in enumerate(pts) if pt == orig][0]
     assert np.array_equal(got[~zero, j], w[~zero])
