@@ -324,6 +324,14 @@ int64_t rex_lhe_num_events(const rex_lhe *lhe);
 int rex_lhe_extract(const rex_lhe *lhe, const int *pdg_in, int n_in, const int *pdg_out, int n_out,
                     int64_t *nev, double *momenta, double *weights, int64_t *index);
 
+/* The same events in the same order, with each particle's SPINUP (the LHE helicity
+ * column) rounded to an integer: host int8 [nev][n_in + n_out] in the order of
+ * rex_lhe_extract, the layout rex_reweight_helicity takes once copied to the
+ * device.  +1 / -1 are helicities; 9 means unknown (the LHE convention; also
+ * written for a particle line without the column).  Call with NULL to size. */
+int rex_lhe_extract_helicities(const rex_lhe *lhe, const int *pdg_in, int n_in, const int *pdg_out,
+                               int n_out, int64_t *nev, signed char *helicities);
+
 /* Set weight id (plain text, no quotes or markup) of the events at positions
  * index[n] (host) to values[n] (host).  Ids are written in the order of their
  * first call; an event without a value for an id gets no line for it. */

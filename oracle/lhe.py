@@ -16,6 +16,9 @@ extract(doc, in, out) the events whose status -1 particles carry the PDG codes
                       multisets; other statuses are ignored), with momenta
                       (E, px, py, pz) in the requested order (identical codes in
                       file order), the event weights xWgtUP and the event indices;
+extract_helicities(doc, in, out)
+                      the same events' SPINUP values rounded to integers, in the
+                      same particle order (9, unknown, where a line lacks it);
 write(doc, weights)   the file text with, for every weight id (in the order
                       given) and every event that has a value for it, a line
                       "<wgt id='ID'> %+.10e </wgt>" inside the event's last
@@ -85,6 +88,25 @@ def extract(doc: dict, pdg_in, pdg_out):
     n = len(pdg_in) + len(pdg_out)
     return (np.array(mom, dtype=np.float64).reshape(len(mom), n, 4), np.array(w, dtype=np.float64),
             np.array(idx, dtype=np.int64))
+
+
+def extract_helicities(doc: dict, pdg_in, pdg_out) -> np.ndarray:
+    pdg_in, pdg_out = list(pdg_in), list(pdg_out)
+    rows = []
+    for ev in doc["events"]:
+        ins = [p for p in ev["particles"] if p[1] == -1]
+        outs = [p for p in ev["particles"] if p[1] == 1]
+        if sorted(p[0] for p in ins) != sorted(pdg_in) or sorted(p[0] for p in outs) != sorted(pdg_out):
+            continue
+        row = []
+        for group, wanted in ((ins, pdg_in), (outs, pdg_out)):
+            used = [False] * len(group)
+            for code in wanted:
+                k = next(k for k, p in enumerate(group) if not used[k] and p[0] == code)
+                used[k] = True
+                row.append(int(round(group[k][12])) if len(group[k]) > 12 else 9)
+        rows.append(row)
+    return np.array(rows, dtype=np.int8).reshape(len(rows), len(pdg_in) + len(pdg_out))
 
 
 def write(doc: dict, weights: list) -> str:

@@ -8,7 +8,7 @@
 //
 // Reading: the whole file is loaded, the <event> spans are found by one scan,
 // then the events are parsed in parallel (std::thread, contiguous ranges) into
-// flat particle arrays (PDG code, status, E px py pz) with std::from_chars.
+// flat particle arrays (PDG code, status, E px py pz, SPINUP) with std::from_chars.
 // Writing: the original text is copied with the weight lines and the
 // <initrwgt> group inserted (events formatted in parallel, written in order);
 // nothing else changes.
@@ -70,6 +70,11 @@ struct Cursor {
     p = r.ptr;
     return v;
   }
+  // true when only blanks remain before the end of the line
+  bool at_eol() {
+    while (p < end && is_space(*p)) ++p;
+    return p >= end || *p == '\n';
+  }
   void next_line() {
     while (p < end && *p != '\n') ++p;
     if (p < end) ++p;
@@ -94,6 +99,7 @@ struct rex_lhe {
   std::vector<Event> ev;
   std::vector<int> pdg, status;
   std::vector<double> mom;   // [particles][4] E, px, py, pz
+  std::vector<signed char> spin;   // SPINUP rounded to an integer; 9 (unknown) when absent
   std::vector<std::string> wid;
   std::vector<std::vector<double>> wval;   // [id][event], NaN where unset
   std::vector<std::vector<char>> whas;
@@ -181,6 +187,7 @@ int rex_lhe_read(const char* path, int nthreads, rex_lhe** out) {
   L->pdg.resize(np);
   L->status.resize(np);
   L->mom.resize((size_t)np * 4);
+  L->spin.resize(np);
   // pass 2: the particle lines
   for_ranges([&](int64_t a, int64_t b) {
     for (int64_t i = a; i < b; ++i) {
@@ -200,6 +207,17 @@ int rex_lhe_read(const char* path, int nthreads, rex_lhe** out) {
         m[1] = px;
         m[2] = py;
         m[3] = pz;
+        // m, VTIMUP, SPINUP: optional trailing columns (SPINUP 9 = unknown when absent)
+        double sp = 9.0;
+        if (!c.at_eol()) {
+          c.num<double>();
+          if (!c.at_eol()) {
+            c.num<double>();
+            if (!c.at_eol()) sp = c.num<double>();
+          }
+        }
+        const double r = std::nearbyint(sp);
+        L->spin[q] = !(r == r) ? (signed char)9 : (signed char)(r > 127.0 ? 127 : (r < -127.0 ? -127 : r));
         c.next_line();
       }
       if (!c.ok) bad[i] = 1;
@@ -216,8 +234,12 @@ int rex_lhe_read(const char* path, int nthreads, rex_lhe** out) {
 
 int64_t rex_lhe_num_events(const rex_lhe* L) { return L ? (int64_t)L->ev.size() : REX_EINVAL; }
 
-int rex_lhe_extract(const rex_lhe* L, const int* pdg_in, int n_in, const int* pdg_out, int n_out, int64_t* nev,
-                    double* momenta, double* weights, int64_t* index) {
+}  // extern "C"
+
+// The events of one process (rex_lhe_extract, rex_lhe_extract_helicities): each
+// output is optional; rows follow the file order, particles the requested order.
+static int extract_impl(const rex_lhe* L, const int* pdg_in, int n_in, const int* pdg_out, int n_out, int64_t* nev,
+                        double* momenta, double* weights, int64_t* index, signed char* helicities) {
   if (!L || !nev || n_in < 0 || n_out < 0 || n_in + n_out < 1 || n_in + n_out > 64 ||
       (n_in && !pdg_in) || (n_out && !pdg_out))
     return lfail(REX_EINVAL, "bad arguments");
@@ -268,12 +290,40 @@ int rex_lhe_extract(const rex_lhe* L, const int* pdg_in, int n_in, const int* pd
         }
       }
     }
+    if (helicities) {
+      signed char* row = helicities + (size_t)n * npart;
+      int slot = 0;
+      for (int side = 0; side < 2; ++side) {
+        const std::vector<int>& want = side ? want_out : want_in;
+        const std::vector<int>& codes = side ? co : ci;
+        const std::vector<int64_t>& qs = side ? qo : qi;
+        used.assign(codes.size(), 0);
+        for (int code : want) {
+          size_t k = 0;
+          while (used[k] || codes[k] != code) ++k;
+          used[k] = 1;
+          row[slot++] = L->spin[(size_t)qs[k]];
+        }
+      }
+    }
     if (weights) weights[n] = e.xwgt;
     if (index) index[n] = i;
     ++n;
   }
   *nev = n;
   return REX_OK;
+}
+
+extern "C" {
+
+int rex_lhe_extract(const rex_lhe* L, const int* pdg_in, int n_in, const int* pdg_out, int n_out, int64_t* nev,
+                    double* momenta, double* weights, int64_t* index) {
+  return extract_impl(L, pdg_in, n_in, pdg_out, n_out, nev, momenta, weights, index, nullptr);
+}
+
+int rex_lhe_extract_helicities(const rex_lhe* L, const int* pdg_in, int n_in, const int* pdg_out, int n_out,
+                               int64_t* nev, signed char* helicities) {
+  return extract_impl(L, pdg_in, n_in, pdg_out, n_out, nev, nullptr, nullptr, nullptr, helicities);
 }
 
 int rex_lhe_set_weights(rex_lhe* L, const char* id, const int64_t* index, const double* values, int64_t n) {

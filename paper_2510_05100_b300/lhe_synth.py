@@ -7,7 +7,9 @@ random order between different PDG codes, identical codes keeping their
 generated order, so that a reader that reindexes to the process order recovers
 the generated arrays exactly.  Momenta and masses are written with 17
 significant digits (exact round trip).  Some events carry an extra status-2
-particle, a comment line, or an existing <rwgt> block.
+particle, a comment line, or an existing <rwgt> block.  With helicities=True every
+particle gets a seeded random helicity +1/-1 in the SPINUP column (9, unknown,
+otherwise).
 """
 from __future__ import annotations
 
@@ -40,11 +42,12 @@ def _order(codes: list, rng) -> list:
     return out
 
 
-def write_lhe(path: str, counts: dict, seed: int = 0, with_initrwgt: bool = False) -> dict:
+def write_lhe(path: str, counts: dict, seed: int = 0, with_initrwgt: bool = False, helicities: bool = False) -> dict:
     """Write a synthetic LHE file.  counts: {process name: number of events}.
 
     Returns {process: (momenta [n][npart][4], weights [n], file positions [n])},
-    the arrays in generation order with each event's position in the file."""
+    the arrays in generation order with each event's position in the file; with
+    helicities=True a fourth array, the int8 helicities [n][npart]."""
     rng = np.random.default_rng(seed)
     data = {}
     labels = []
@@ -52,7 +55,9 @@ def write_lhe(path: str, counts: dict, seed: int = 0, with_initrwgt: bool = Fals
         mom = ps.make_events(proc, n, seed * 100 + i + 1)
         w = rng.uniform(0.5, 1.5, n)
         w[rng.random(n) < 0.01] *= -1.0
-        data[proc] = (mom, w)
+        hel = (rng.choice(np.array([-1, 1], dtype=np.int8), size=mom.shape[:2]) if helicities
+               else np.full(mom.shape[:2], 9, dtype=np.int8))
+        data[proc] = (mom, w, hel)
         labels += [(proc, j) for j in range(n)]
     order = rng.permutation(len(labels))
     pos = {proc: np.empty(n, dtype=np.int64) for proc, n in counts.items()}
@@ -65,7 +70,7 @@ def write_lhe(path: str, counts: dict, seed: int = 0, with_initrwgt: bool = Fals
     for fpos, lab in enumerate(order):
         proc, j = labels[lab]
         pos[proc][j] = fpos
-        mom, w = data[proc]
+        mom, w, hel = data[proc]
         pin, pout = PROCESSES[proc]
         extra = proc == "gg_ttxg" and rng.random() < 0.1
         lines = []
@@ -77,8 +82,9 @@ def write_lhe(path: str, counts: dict, seed: int = 0, with_initrwgt: bool = Fals
         for code, st, r in rows:
             e, px, py, pz = mom[j, r]
             moth = (0, 0) if st == -1 else (1, 2)
-            lines.append(" %d %d %d %d %d %d %+.16e %+.16e %+.16e %.16e %.16e 0.0000e+00 9.0000e+00"
-                         % (code, st, moth[0], moth[1], 501 + r, 0, px, py, pz, e, _MASS.get(code, 0.0)))
+            lines.append(" %d %d %d %d %d %d %+.16e %+.16e %+.16e %.16e %.16e 0.0000e+00 %.4e"
+                         % (code, st, moth[0], moth[1], 501 + r, 0, px, py, pz, e, _MASS.get(code, 0.0),
+                            float(hel[j, r])))
         if extra:
             lines.append(" 25 2 1 2 0 0 +0.0 +0.0 +0.0 1.25e+02 1.25e+02 0.0000e+00 0.0000e+00")
         u = rng.random()
@@ -90,4 +96,6 @@ def write_lhe(path: str, counts: dict, seed: int = 0, with_initrwgt: bool = Fals
     out.append("</LesHouchesEvents>\n")
     with open(path, "w") as f:
         f.write("".join(out))
+    if helicities:
+        return {proc: (data[proc][0], data[proc][1], pos[proc], data[proc][2]) for proc in counts}
     return {proc: (data[proc][0], data[proc][1], pos[proc]) for proc in counts}

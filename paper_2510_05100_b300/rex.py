@@ -48,7 +48,7 @@ EXPORTS = (
     "rex_surrogate_free",
     "rex_xsec_last_error", "rex_xsec_create", "rex_xsec_reset", "rex_xsec_accumulate", "rex_xsec_result",
     "rex_xsec_free", "rex_xsec_get_state", "rex_xsec_set_state", "rex_xsec_merge_states",
-    "rex_lhe_last_error", "rex_lhe_read", "rex_lhe_num_events", "rex_lhe_extract", "rex_lhe_set_weights",
+    "rex_lhe_last_error", "rex_lhe_read", "rex_lhe_num_events", "rex_lhe_extract", "rex_lhe_extract_helicities", "rex_lhe_set_weights",
     "rex_lhe_write", "rex_lhe_free",
 )
 
@@ -180,6 +180,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.rex_lhe_num_events.restype = i64
     lib.rex_lhe_extract.argtypes = [vp, vp, ctypes.c_int, vp, ctypes.c_int, ctypes.POINTER(i64), vp, vp, vp]
     lib.rex_lhe_extract.restype = ctypes.c_int
+    lib.rex_lhe_extract_helicities.argtypes = [vp, vp, ctypes.c_int, vp, ctypes.c_int, ctypes.POINTER(i64), vp]
+    lib.rex_lhe_extract_helicities.restype = ctypes.c_int
     lib.rex_lhe_set_weights.argtypes = [vp, ctypes.c_char_p, vp, vp, i64]
     lib.rex_lhe_set_weights.restype = ctypes.c_int
     lib.rex_lhe_write.argtypes = [vp, ctypes.c_char_p]
@@ -566,6 +568,20 @@ class Lhe:
         _lcheck(load().rex_lhe_extract(self._h, a.ctypes.data, a.size, b.ctypes.data, b.size, ctypes.byref(n),
                                        mom.ctypes.data, w.ctypes.data, idx.ctypes.data))
         return mom, w, idx
+
+    def extract_helicities(self, pdg_in, pdg_out):
+        """The SPINUP values of the same events and particle order as extract, int8 [n][npart]
+        (+1 / -1 helicities, 9 unknown)."""
+        import numpy as np
+        a = np.ascontiguousarray(pdg_in, dtype=np.int32)
+        b = np.ascontiguousarray(pdg_out, dtype=np.int32)
+        n = ctypes.c_int64()
+        _lcheck(load().rex_lhe_extract_helicities(self._h, a.ctypes.data, a.size, b.ctypes.data, b.size,
+                                                  ctypes.byref(n), None))
+        hel = np.empty((n.value, a.size + b.size), dtype=np.int8)
+        _lcheck(load().rex_lhe_extract_helicities(self._h, a.ctypes.data, a.size, b.ctypes.data, b.size,
+                                                  ctypes.byref(n), hel.ctypes.data))
+        return hel
 
     def set_weights(self, wid: str, index, values) -> None:
         import numpy as np

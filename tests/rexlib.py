@@ -29,3 +29,18 @@ def cuda_available():
 
 
 gpu = pytest.mark.gpu
+
+
+def helicity_tolerance(proc, mom, hel, orig, pts, floor, eps):
+    """Per (event, point) bound on the relative error of a helicity-exclusive weight:
+    max(floor, 64 eps (sqrt(kappa_0) + sqrt(kappa_j))), kappa = |M|^2 / |M_h|^2 at
+    each point (the oracle's values)."""
+    import numpy as np
+    from oracle import reweight as oracle_rw
+
+    def sqrt_kappa(pt):
+        mh = oracle_rw.me2_helicity(proc, mom, pt, hel)
+        return np.sqrt(oracle_rw.me2(proc, mom, pt) / np.where(mh > 0, mh, np.inf))
+    k0 = sqrt_kappa(orig)
+    kj = np.stack([sqrt_kappa(pt) for pt in pts], axis=1)
+    return np.maximum(floor, 64.0 * eps * (k0[:, None] + kj))

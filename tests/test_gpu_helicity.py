@@ -10,7 +10,7 @@ of a small A_h is a relative error of about eps |A_typical| / |A_h| on |A_h|^2.
 import numpy as np
 import pytest
 
-from rexlib import ensure_built
+from rexlib import ensure_built, helicity_tolerance
 from oracle import reweight as oracle_rw
 from paper_2510_05100_b300 import phase_space as ps
 
@@ -29,16 +29,6 @@ def rex():
 
 def dev(a):
     return torch.from_numpy(np.ascontiguousarray(a)).cuda()
-
-
-def tolerance(proc, mom, hel, orig, pts, floor, eps):
-    """Per (event, point): max(floor, 64 eps (sqrt(kappa_0) + sqrt(kappa_j)))."""
-    def sqrt_kappa(pt):
-        mh = oracle_rw.me2_helicity(proc, mom, pt, hel)
-        return np.sqrt(oracle_rw.me2(proc, mom, pt) / np.where(mh > 0, mh, np.inf))
-    k0 = sqrt_kappa(orig)
-    kj = np.stack([sqrt_kappa(pt) for pt in pts], axis=1)
-    return np.maximum(floor, 64.0 * eps * (k0[:, None] + kj))
 
 
 def case(proc, n, seed):
@@ -62,7 +52,7 @@ def test_parity_with_forbidden_configurations(rex, proc, precision, tol):
     zero = ref[:, 0] == 0.0
     assert np.any(zero) and np.all(got[zero] == 0.0)
     eps = np.finfo(np.float64 if precision == 0 else np.float32).eps / 2
-    bound = tolerance(proc, mom, hel, orig, pts, tol, eps)
+    bound = helicity_tolerance(proc, mom, hel, orig, pts, tol, eps)
     err = np.abs(got - ref) / np.where(ref != 0.0, np.abs(ref), 1.0)
     assert np.all(err[~zero] < bound[~zero])
     # most terms meet the helicity sum's tolerance outright

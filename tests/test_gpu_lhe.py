@@ -67,3 +67,26 @@ def test_file_to_reweighted_file(rex, tmp_path):
     _, _, eidx = olhe.extract(doc, *lhe_synth.PROCESSES["ee_mumu"])
     ev = doc["events"][eidx[0]]
     assert "<wgt" not in text[ev["start"]:ev["end"]]
+
+
+def test_file_to_helicity_exclusive_weights(rex, tmp_path):
+    """SPINUP read from the file feeds helicity-exclusive reweighting of q q~ -> t t~."""
+    from rexlib import helicity_tolerance
+    src = str(tmp_path / "hel.lhe")
+    lhe_synth.write_lhe(src, {"qq_ttx": 600, "gg_ttx": 200}, seed=8, helicities=True)
+    L = rex.Lhe(src)
+    pin, pout = lhe_synth.PROCESSES["qq_ttx"]
+    mom, w, idx = L.extract(pin, pout)
+    hel = L.extract_helicities(pin, pout)
+    L.close()
+    p = rex.Process("qq_ttx", 0)
+    p.set_params(ORIG)
+    pts = GRIDS["qq_ttx"]
+    out = p.reweight_helicity(torch.from_numpy(mom).cuda(), torch.from_numpy(hel).cuda(),
+                              torch.from_numpy(w).cuda(), pts).cpu().numpy()
+    ref = oracle_rw.reweight_helicity("qq_ttx", mom, hel, w, ORIG, pts)
+    zero = ref[:, 0] == 0.0
+    assert np.any(zero) and np.all(out[zero] == 0.0)
+    bound = helicity_tolerance("qq_ttx", mom, hel, ORIG, pts, 1e-12, np.finfo(np.float64).eps / 2)
+    err = np.abs(out - ref) / np.where(ref != 0.0, np.abs(ref), 1.0)
+    assert np.all(err[~zero] < bound[~zero])

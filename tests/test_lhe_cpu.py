@@ -114,3 +114,32 @@ def test_errors(rex, tmp_path):
     with pytest.raises(rex.RexError):
         L.set_weights("it's", [0], [1.0])         # markup in the id
     L.close()
+
+
+def test_helicity_column(rex, tmp_path):
+    """SPINUP of the fixture (pinned by hand for its first event) and of a synthetic file with
+    random helicities: the native reader against the oracle reader and the generator."""
+    L = rex.Lhe(TINY)
+    doc = olhe.read(TINY)
+    for pin, pout in SIGS:
+        assert np.array_equal(L.extract_helicities(pin, pout), olhe.extract_helicities(doc, pin, pout))
+    # first event: g(+1) g(-1) -> t(+1) t~(-1) g(+1), in the order g g t t~ g
+    assert L.extract_helicities([21, 21], [6, -6, 21])[0].tolist() == [1, -1, 1, -1, 1]
+    L.close()
+    path = str(tmp_path / "hel.lhe")
+    info = lhe_synth.write_lhe(path, {"qq_ttx": 700, "ee_mumu": 300, "gg_ttxg": 500}, seed=13, helicities=True)
+    L = rex.Lhe(path)
+    doc = olhe.read(path)
+    for proc in info:
+        pin, pout = lhe_synth.PROCESSES[proc]
+        got = L.extract_helicities(pin, pout)
+        assert np.array_equal(got, olhe.extract_helicities(doc, pin, pout))
+        mom, w, pos, hel = info[proc]
+        assert np.array_equal(got, hel[np.argsort(pos)])
+    L.close()
+    # without the option every particle is written as unknown (9)
+    path2 = str(tmp_path / "nohel.lhe")
+    lhe_synth.write_lhe(path2, {"qq_ttx": 10}, seed=14)
+    L = rex.Lhe(path2)
+    assert np.all(L.extract_helicities([2, -2], [6, -6]) == 9)
+    L.close()
