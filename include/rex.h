@@ -8,8 +8,9 @@
  *     w_out[e][j] = w_in[e] * |M(p_e; theta_j)|^2 / |M(p_e; theta_0)|^2
  *                 = 0                       if |M(p_e; theta_0)|^2 == 0,
  *
- * where |M|^2 is the tree-level, helicity-summed (Sec. 4.1.2: only
- * helicity-summed reweighting) and colour-summed squared matrix element,
+ * where |M|^2 is the tree-level, helicity-summed (the paper's tool reweights
+ * helicity-summed only, Sec. 4.1.2; rex_reweight_helicity gives the
+ * helicity-exclusive alternative) and colour-summed squared matrix element,
  * averaged over initial spins and colours, theta_0 the parameter point set
  * with rex_set_params and theta_j the j-th entry of param_sets.
  *
@@ -23,8 +24,9 @@
  * Conventions for all calls:
  *  - return value 0 = success, negative = error (REX_E*); rex_last_error()
  *    returns a message for the calling thread's last failure;
- *  - device pointers must be 8-byte aligned device (or managed) memory of
- *    the current device; the caller owns every array passed in;
+ *  - device pointers must be device (or managed) memory of the current
+ *    device, 8-byte aligned (momenta 16-byte aligned); the caller owns every
+ *    array passed in;
  *  - stream is a cudaStream_t passed as void* (NULL = legacy default
  *    stream); calls taking a stream only enqueue work on it and return
  *    without synchronising; asynchronous kernel faults surface at the
@@ -46,13 +48,20 @@ extern "C" {
 #define REX_ENOTINIT (-2)    /* rex_reweight before rex_set_params */
 #define REX_ECUDA (-3)       /* a CUDA call failed; see rex_last_error() */
 #define REX_ENOMEM (-4)      /* a library-owned allocation failed */
-#define REX_EUNSUPPORTED (-5) /* precision mode not available for this process */
+#define REX_EUNSUPPORTED (-5) /* precision mode or helicity-exclusive reweighting not
+                                 available for this process */
 
-/* Precision modes (the paper's fptype option, Sec. 4.1.2, re-cut for B300):
+/* Precision modes (the paper's fptype option, Sec. 4.1.2, re-cut for B300,
+ * where FP64 issues at 1/64 of the FP32 rate):
  * REX_FP64: every step in FP64.
- * REX_MIXED: wavefunctions and amplitudes in FP32, colour sum on tensor
- *            cores (FP16 operands, FP32 accumulation), helicity sum and
- *            weight ratio in FP64. */
+ * REX_MIXED: wavefunctions, amplitudes, colour sum and helicity sum (whose
+ *            terms are non-negative) in FP32; Lorentz invariants and the
+ *            weight ratio in FP64 (q q~ -> t t~: FP32 after the momenta,
+ *            except the exact FP64 product for points at the original top
+ *            mass).  Kernel variants 5-8 of the g g processes put the colour
+ *            sum on tensor cores (FP16 hi/lo operands, FP32 accumulation).
+ *            The error against FP64 is bounded per process (gg_ttx 1e-5,
+ *            gg_ttxg and gg_ttxgg 1e-3, qq_ttx 1e-5, relative per weight). */
 #define REX_FP64 0
 #define REX_MIXED 1
 
@@ -150,8 +159,10 @@ int rex_me2(rex_proc *proc, const double *momenta, int64_t nev,
             const rex_params *point, double *me2_out, void *stream);
 
 /* Kernel thread-mapping variants (QCD processes: lanes per event and
- * register budget; ee_mumu and qq_ttx have one).  Every variant computes the same
- * result; they differ only in speed.  rex_num_variants returns the count,
+ * register budget, colour form; ee_mumu and qq_ttx have one).  Every variant
+ * computes the same quantity within its mode's tolerance (the summation order
+ * and, for the tensor-core variants 5-8 in REX_MIXED, the colour arithmetic
+ * differ); they differ in speed.  rex_num_variants returns the count,
  * rex_get_variant / rex_set_variant read and select the handle's variant.
  * Errors: REX_EINVAL (bad handle or index). */
 int rex_num_variants(const rex_proc *proc);
@@ -190,7 +201,10 @@ int rex_multi_create(int precision, rex_multi **out);
 
 /* Execution mode of a multi handle (rex_multi_set_mode; errors: REX_EINVAL):
  * REX_MULTI_PERSISTENT (default): one persistent kernel over every batch's
- *   event tiles, fed by the device work counter;
+ *   event tiles, fed by the device work counter; the heaviest process of the
+ *   launch selects the kernel's register class (e+e-, g g -> t t~ and
+ *   q q~ -> t t~ alone; with g g -> t t~ g; with g g -> t t~ g g), so light
+ *   batches keep the occupancy of their own kernels;
  * REX_MULTI_STREAMS: each batch's own tuned single-process kernel on a
  *   stream forked from (and joined back into) the caller's stream. */
 #define REX_MULTI_PERSISTENT 0
