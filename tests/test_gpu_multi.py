@@ -130,3 +130,38 @@ def test_register_classes(rex, subset, precision):
     for (proc, *_), b, ref in zip(items, batches, single):
         assert np.max(np.abs(b[3].cpu().numpy() / ref - 1.0)) < 1e-13, proc
     m.close()
+
+
+def test_config4_full_size_persistent_graph(rex):
+    """The multi-process workload at full size in the launch configuration the benchmark
+    times: 10k e+e- + 1M g g -> t t~ + 500k g g -> t t~ g + 100k g g -> t t~ g g, 64 points,
+    one captured persistent launch in mixed precision.  Every batch against its own
+    single-process launch at every event, sampled events against the oracle."""
+    mixed_tol = {"ee_mumu": 1e-12, "gg_ttx": 1e-5, "gg_ttxg": 1e-3, "gg_ttxgg": 1e-3}
+    pts = [dict(p, **ps.EE_NEW) for p in ps.grid_64()]
+    spec = (("ee_mumu", 10_000, 41), ("gg_ttx", 1_000_000, 42), ("gg_ttxg", 500_000, 43), ("gg_ttxgg", 100_000, 44))
+    batches, data = [], []
+    for proc, n, seed in spec:
+        p = rex.Process(proc, 0 if proc == "ee_mumu" else 1)
+        orig = ps.EE_ORIGINAL if proc == "ee_mumu" else ORIG_QCD
+        p.set_params(orig)
+        mom = ps.make_events(proc, n, seed)
+        dm, dw = dev(mom), torch.ones(n, dtype=torch.float64, device="cuda")
+        batches.append((p, dm, dw, torch.zeros((n, 64), dtype=torch.float64, device="cuda")))
+        data.append((proc, p, mom, orig, dm, dw))
+    m = rex.Multi(1)
+    m.capture(batches, pts)
+    m.replay()
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(9)
+    for (proc, p, mom, orig, dm, dw), b in zip(data, batches):
+        got = b[3].cpu().numpy()
+        single = p.reweight(dm, dw, pts).cpu().numpy()
+        assert np.max(np.abs(got / single - 1.0)) < 1e-13, proc
+        ns = 3 if proc == "gg_ttxgg" else 12
+        idx = rng.choice(mom.shape[0], ns, replace=False)
+        kp = pts if proc != "gg_ttxgg" else pts[::8]
+        cols = list(range(64)) if proc != "gg_ttxgg" else list(range(0, 64, 8))
+        ref = oracle_rw.reweight(proc, mom[idx], np.ones(ns), orig, kp)
+        assert np.max(np.abs(got[idx][:, cols] / ref - 1.0)) < mixed_tol[proc], proc
+    m.close()

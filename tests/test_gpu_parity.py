@@ -278,3 +278,43 @@ def test_fp64_tolerance_rule_on_ill_conditioned_events(rex):
         assert err[i, j] <= 64 * eps * (k0 + kj), (idx[i], j, err[i, j], k0, kj)
         worst = max(worst, err[i, j])
     assert np.all(err[2:] < FP64_TOL)          # the well-conditioned events meet 1e-12 outright
+
+
+def test_full_size_ee_every_event(rex):
+    """e+e- -> mu+mu-: the full 4096-event sample at the new electroweak point, every event
+    against the oracle."""
+    mom = ps.make_events("ee_mumu", 4096, 1)
+    w = np.ones(4096)
+    got = make("ee_mumu", rex).reweight(dev(mom), dev(w), [ps.EE_NEW]).cpu().numpy()
+    ref = oracle_rw.reweight("ee_mumu", mom, w, ps.EE_ORIGINAL, [ps.EE_NEW])
+    assert np.max(rel(got, ref)) < FP64_TOL
+
+
+def test_full_size_gg_ttx_sampled(rex):
+    """g g -> t t~ at 2^20 events x 8 points: the FP64 kernel on sampled events against the
+    oracle, the mixed kernel against the FP64 one at every event."""
+    n = 1 << 20
+    mom = ps.make_events("gg_ttx", n, 2)
+    w = np.ones(n)
+    pts = ps.grid_gg_ttx()
+    dm, dw = dev(mom), dev(w)
+    got = make("gg_ttx", rex).reweight(dm, dw, pts).cpu().numpy()
+    assert np.all(np.isfinite(got)) and np.all(got > 0)
+    idx = np.concatenate([np.random.default_rng(8).choice(n, 32, replace=False), [0, n - 1]])
+    ref = oracle_rw.reweight("gg_ttx", mom[idx], w[idx], ORIG_QCD, pts)
+    assert np.max(rel(got[idx], ref)) < FP64_TOL
+    mixed = make("gg_ttx", rex, precision=1).reweight(dm, dw, pts).cpu().numpy()
+    assert np.max(rel(mixed, got)) < MIXED_TOL["gg_ttx"]
+
+
+def test_full_size_gg_ttxg_mixed_every_event(rex):
+    """The headline workload (2^20 g g -> t t~ g events x 16 points) in mixed precision against
+    the FP64 kernel at every event (the FP64 kernel is checked against the oracle above)."""
+    n = 1 << 20
+    mom = ps.make_events("gg_ttxg", n, 3)
+    w = np.ones(n)
+    pts = ps.grid_gg_ttxg()
+    dm, dw = dev(mom), dev(w)
+    exact = make("gg_ttxg", rex).reweight(dm, dw, pts).cpu().numpy()
+    mixed = make("gg_ttxg", rex, precision=1).reweight(dm, dw, pts).cpu().numpy()
+    assert np.max(rel(mixed, exact)) < MIXED_TOL["gg_ttxg"]
