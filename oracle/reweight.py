@@ -11,7 +11,7 @@ from __future__ import annotations
 
 import numpy as np
 
-from . import ee, qcd, qq
+from . import ee, qcd, qq, qqg
 
 QCD_PROCESSES = {"gg_ttx": 4, "gg_ttxg": 5, "gg_ttxgg": 6}
 
@@ -26,6 +26,8 @@ def me2(process: str, p: np.ndarray, point: dict) -> np.ndarray:
         return qcd.me2(p, point["mt"], point.get("wt", 0.0), point["alphas"])
     if process == "qq_ttx":
         return qq.me2(p, point["mt"], point.get("wt", 0.0), point["alphas"])
+    if process == "qq_ttxg":
+        return qqg.me2(p, point["mt"], point.get("wt", 0.0), point["alphas"])
     raise ValueError(f"unknown process {process!r}")
 
 

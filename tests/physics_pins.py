@@ -286,3 +286,80 @@ def boost(p, beta):
     out[..., 0] = gam * (p[..., 0] + bp)
     out[..., 1:] = p[..., 1:] + ((gam - 1.0) * bp / b2)[..., None] * b + (gam * p[..., 0])[..., None] * b
     return out
+
+
+# ----------------------------------------------------------------------------
+# soft-gluon limit of q q~ -> Q Q~ g
+# ----------------------------------------------------------------------------
+def qq_qq_colour_correlators():
+    """C_ij = <B| T_i . T_j |B> / <B|B> for the Born colour tensor
+    B[i1, j2, i3, j4] = sum_b (t^b)_{j2 i1} (t^b)_{i3 j4} of q(1) q~(2) -> Q(3) Q~(4).
+    Insertions: an outgoing quark's index takes t^c from the left, an outgoing
+    antiquark's -t^c from the right; an incoming quark counts as an outgoing
+    antiquark and an incoming antiquark as an outgoing quark.  Returns C [4, 4] and
+    the colour-conservation residual max |sum_i T_i B|."""
+    t = _t_matrices()
+    born = np.einsum("bji,bkl->ijkl", t, t)
+    ins = [
+        lambda c: -np.einsum("xi,xjkl->ijkl", t[c], born),   # q in: index i1
+        lambda c: np.einsum("jx,ixkl->ijkl", t[c], born),    # q~ in: index j2
+        lambda c: np.einsum("kx,ijxl->ijkl", t[c], born),    # Q out: index i3
+        lambda c: -np.einsum("xl,ijkx->ijkl", t[c], born),   # Q~ out: index j4
+    ]
+    norm = np.real(np.sum(born.conj() * born))
+    corr = np.zeros((4, 4))
+    resid = 0.0
+    for c in range(8):
+        tb = [f(c) for f in ins]
+        resid = max(resid, float(np.max(np.abs(sum(tb)))))
+        for i in range(4):
+            for j in range(4):
+                corr[i, j] += np.real(np.sum(tb[i].conj() * tb[j])) / norm
+    return corr, resid
+
+
+def soft_eikonal(p, k, corr, alphas):
+    """-g^2 sum_{i,j} C_ij (p_i.p_j) / ((p_i.k)(p_j.k)) over the four hard legs (physical
+    momenta; the sign flips of incoming legs cancel in each term)."""
+    gs2 = 4.0 * math.pi * alphas
+    tot = 0.0
+    for i in range(4):
+        for j in range(4):
+            tot = tot + corr[i, j] * mdot(p[:, i], p[:, j]) / (mdot(p[:, i], k) * mdot(p[:, j], k))
+    return -gs2 * tot
+
+
+def soft_qq_ttg_events(n, seed, m, sqrt_s, omega_frac):
+    """q q~ -> Q Q~ g with a soft gluon of energy omega_frac * sqrt(s), exact momentum
+    conservation and on-shell Q: the Q Q~ pair recoils against the gluon and decays at
+    seeded angles in its rest frame.  Returns (events [n, 5, 4], Born events [n, 4, 4]
+    with the same angles at omega = 0)."""
+    rng = np.random.default_rng(seed)
+    e = sqrt_s / 2.0
+    p1 = np.array([e, 0.0, 0.0, e])
+    p2 = np.array([e, 0.0, 0.0, -e])
+    out, born = [], []
+    for _ in range(n):
+        ck, phk = rng.uniform(-0.9, 0.9), rng.uniform(0, 2 * math.pi)
+        nk = np.array([math.sqrt(1 - ck * ck) * math.cos(phk), math.sqrt(1 - ck * ck) * math.sin(phk), ck])
+        ct, pht = rng.uniform(-0.9, 0.9), rng.uniform(0, 2 * math.pi)
+        nt = np.array([math.sqrt(1 - ct * ct) * math.cos(pht), math.sqrt(1 - ct * ct) * math.sin(pht), ct])
+        rows = []
+        for om in (omega_frac * sqrt_s, 0.0):
+            k = np.concatenate([[om], om * nk])
+            pp = np.concatenate([[sqrt_s - om], -om * nk])
+            mm = math.sqrt(pp[0] ** 2 - pp[1:] @ pp[1:])
+            q = math.sqrt(mm * mm / 4.0 - m * m)
+            t_rest = np.concatenate([[mm / 2.0], q * nt])
+            tb_rest = np.concatenate([[mm / 2.0], -q * nt])
+            beta = pp[1:] / pp[0]
+            if om > 0.0:
+                t_lab = boost(t_rest[None], beta)[0]
+                tb_lab = boost(tb_rest[None], beta)[0]
+            else:
+                t_lab, tb_lab = t_rest, tb_rest
+            rows.append((k, t_lab, tb_lab))
+        (k, t_lab, tb_lab), (_, t0, tb0) = rows
+        out.append([p1, p2, t_lab, tb_lab, k])
+        born.append([p1, p2, t0, tb0])
+    return np.array(out), np.array(born)
