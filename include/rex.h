@@ -72,7 +72,7 @@ extern "C" {
 typedef struct rex_proc rex_proc; /* opaque, library-owned */
 
 /* One parameter point.  Fields a process does not use are ignored.
- *   QCD processes (gg_ttx, gg_ttxg, gg_ttxgg, qq_ttx): mt, wt (top mass and
+ *   QCD processes (gg_ttx, gg_ttxg, gg_ttxgg, qq_ttx, qq_ttxg): mt, wt (top mass and
  *     width, GeV), alphas (strong coupling, fixed; g_s = sqrt(4 pi alphas)).
  *     mt enters the top propagators and the external top spinors; momenta
  *     are kept as given.  qq_ttx has no top propagator: wt is checked and
@@ -89,6 +89,8 @@ typedef struct {
  *       "gg_ttx"   g(1) g(2) -> t(3) t~(4);
  *       "gg_ttxg"  g(1) g(2) -> t(3) t~(4) g(5);
  *       "gg_ttxgg" g(1) g(2) -> t(3) t~(4) g(5) g(6);
+ *       "qq_ttxg"  q(1) q~(2) -> t(3) t~(4) g(5), massless light quark,
+ *                  five diagrams;
  *       "qq_ttx"   q(1) q~(2) -> t(3) t~(4), massless light quark, one
  *                  s-channel gluon (the quark-initiated leading-order
  *                  channel of p p -> t t~; multi-channel samples with p any
@@ -159,7 +161,7 @@ int rex_me2(rex_proc *proc, const double *momenta, int64_t nev,
             const rex_params *point, double *me2_out, void *stream);
 
 /* Kernel thread-mapping variants (QCD processes: lanes per event and
- * register budget, colour form; ee_mumu and qq_ttx have one).  Every variant
+ * register budget, colour form; ee_mumu, qq_ttx and qq_ttxg have one).  Every variant
  * computes the same quantity within its mode's tolerance (the summation order
  * and, for the tensor-core variants 5-8 in REX_MIXED, the colour arithmetic
  * differ); they differ in speed.  rex_num_variants returns the count,
@@ -203,7 +205,8 @@ int rex_multi_create(int precision, rex_multi **out);
  * REX_MULTI_PERSISTENT (default): one persistent kernel over every batch's
  *   event tiles, fed by the device work counter; the heaviest process of the
  *   launch selects the kernel's register class (e+e-, g g -> t t~ and
- *   q q~ -> t t~ alone; with g g -> t t~ g; with g g -> t t~ g g), so light
+ *   q q~ -> t t~ alone; with g g -> t t~ g or q q~ -> t t~ g; with
+ *   g g -> t t~ g g), so light
  *   batches keep the occupancy of their own kernels;
  * REX_MULTI_STREAMS: each batch's own tuned single-process kernel on a
  *   stream forked from (and joined back into) the caller's stream. */

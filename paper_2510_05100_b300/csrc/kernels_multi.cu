@@ -15,16 +15,17 @@
 #include "ee_kernel.cuh"
 #include "qcd_kernel.cuh"
 #include "qq_kernel.cuh"
+#include "qqg_kernel.cuh"
 
 namespace rex {
 
-static_assert(QQ_BLOCK == QCD_BLOCK, "every tile runs on the multi kernel's block size");
+static_assert(QQ_BLOCK == QCD_BLOCK && QQG_BLOCK == QCD_BLOCK, "every tile runs on the multi kernel's block size");
 
 // Register classes: the persistent kernel is compiled once per class with only
 // the tiles the class admits, so its register budget (and occupancy) follows the
 // heaviest process actually present in the launch:
 //   class 0: e+e- -> mu+mu-, g g -> t t~, q q~ -> t t~
-//   class 1: class 0 and g g -> t t~ g
+//   class 1: class 0, g g -> t t~ g and q q~ -> t t~ g
 //   class 2: every process (g g -> t t~ g g sets the budget)
 template <typename R, bool WIDTH, int MINB, int CLASS, int S_TTX, int S_TTXG, int S_TTXGG, bool TC_TTXGG>
 __global__ void __launch_bounds__(QCD_BLOCK, MINB)
@@ -33,11 +34,13 @@ __global__ void __launch_bounds__(QCD_BLOCK, MINB)
   using T2 = QcdTile<PROC_GG_TTXG, R, WIDTH, S_TTXG>;
   using T3 = QcdTile<PROC_GG_TTXGG, R, WIDTH, S_TTXGG, TC_TTXGG>;
   using T4 = QqTile<R>;
+  using T5 = QqgTile<R>;
   union Smem {
     typename T1::Smem a;
     typename std::conditional<(CLASS >= 1), typename T2::Smem, char>::type b;
     typename std::conditional<(CLASS >= 2), typename T3::Smem, char>::type c;
     typename T4::Smem d;
+    typename std::conditional<(CLASS >= 1), typename T5::Smem, char>::type e;
   };
   __shared__ Smem sm;
   __shared__ unsigned long long item_s;
@@ -61,6 +64,9 @@ __global__ void __launch_bounds__(QCD_BLOCK, MINB)
         if constexpr (CLASS >= 2) T3::run(sm.c, B.mom, B.w_in, B.nev, tile, B.t, B.out);
         break;
       case PROC_QQ_TTX: T4::run(sm.d, B.mom, B.w_in, B.nev, tile, B.t, B.out); break;
+      case PROC_QQ_TTXG:
+        if constexpr (CLASS >= 1) T5::run(sm.e, B.mom, B.w_in, B.nev, tile, B.t, B.out);
+        break;
       default: break;
     }
     __syncthreads();
@@ -68,7 +74,7 @@ __global__ void __launch_bounds__(QCD_BLOCK, MINB)
 }
 
 int multi_class_of(int kind) {
-  return kind == PROC_GG_TTXGG ? 2 : (kind == PROC_GG_TTXG ? 1 : 0);
+  return kind == PROC_GG_TTXGG ? 2 : ((kind == PROC_GG_TTXG || kind == PROC_QQ_TTXG) ? 1 : 0);
 }
 
 // Lanes-per-event split of each QCD process in the multi kernel (the defaults of
@@ -107,6 +113,7 @@ int multi_events_per_tile(int kind, int mixed) {
     case PROC_GG_TTXG: return QCD_BLOCK / 8;
     case PROC_GG_TTXGG: return QCD_BLOCK / 16;
     case PROC_QQ_TTX: return QqTile<float>::EPB;
+    case PROC_QQ_TTXG: return QqgTile<float>::EPB;
     default: return 0;
   }
 }

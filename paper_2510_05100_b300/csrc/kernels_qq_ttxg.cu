@@ -1,0 +1,27 @@
+// Standalone launcher of the q q~ -> t t~ g reweighting kernel (sm_103a), FP64 and mixed.
+#include "qqg_kernel.cuh"
+
+namespace rex {
+
+template <typename R>
+__global__ void __launch_bounds__(QQG_BLOCK, 1)
+    qq_ttxg_reweight_kernel(const double* __restrict__ mom, const double* __restrict__ w_in, int64_t nev,
+                            const __grid_constant__ QcdLaunch lp, double* __restrict__ out) {
+  __shared__ typename QqgTile<R>::Smem sm;
+  QqgTile<R>::run(sm, mom, w_in, nev, (int64_t)blockIdx.x, lp, out);
+}
+
+int launch_qq_ttxg(int mixed, const double* mom, const double* w_in, int64_t nev, const QcdLaunch& lp,
+                   double* out, void* stream) {
+  constexpr int EPB = QqgTile<float>::EPB;
+  const int64_t blocks = (nev + EPB - 1) / EPB;
+  if (blocks > 0x7fffffffLL) return (int)cudaErrorInvalidValue;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (mixed)
+    qq_ttxg_reweight_kernel<float><<<(unsigned)blocks, QQG_BLOCK, 0, st>>>(mom, w_in, nev, lp, out);
+  else
+    qq_ttxg_reweight_kernel<double><<<(unsigned)blocks, QQG_BLOCK, 0, st>>>(mom, w_in, nev, lp, out);
+  return (int)cudaGetLastError();
+}
+
+}  // namespace rex

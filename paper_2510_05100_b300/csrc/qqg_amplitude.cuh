@@ -1,0 +1,227 @@
+// q(1) q~(2) -> t(3) t~(4) g(5): helicity amplitudes of one lane (device routines,
+// templated on the arithmetic type; the tile that runs them is in qqg_kernel.cuh).
+//
+// Diagrams (light line read from vbar(p2) to u(p1), top line from ubar(p3) to v(p4);
+// s = (p1 + p2)^2, s' = (p3 + p4)^2, k = p5, eps a real linear polarisation):
+//   a1 = C1 . J_out / s',   C1 = vbar2 gamma^mu (p1 - k)-slash eps-slash u1 / (p1 - k)^2
+//   a2 = C2 . J_out / s',   C2 = vbar2 eps-slash (k - p2)-slash gamma^mu u1 / (k - p2)^2
+//   a3 = ubar3 eps-slash ((p3 + k)-slash + m) J_in-slash v4 / (((p3 + k)^2 - m^2 + i m G) s)
+//   a4 = ubar3 J_in-slash ((-p4 - k)-slash + m) eps-slash v4 / (((p4 + k)^2 - m^2 + i m G) s)
+//   a5 = E . J_out / (s s'),  E = (J_in.eps)(q + k) + (J_in.(q' - k)) eps - (eps.(q' + q)) J_in
+// with J_in = vbar2 gamma u1, J_out = ubar3 gamma v4, q = p1 + p2, q' = p3 + p4 (the
+// three-gluon vertex with every momentum incoming).  The Feynman-rule factors are
+// -i g^3 for a1..a4 and g^3 for a5; the -i is moved into the colour matrix, which
+// then is the real symmetric N / 3 below, and g^6, 1/3 and the 1/36 average go into
+// the per-point factor.  N = 3 sum over colours of conj(K_d) K_d' for the colour
+// structures (t^b t^a)(t^b), (t^a t^b)(t^b), (t^b)(t^a t^b), (t^b)(t^b t^a) and
+// f^{bac}(t^b)(t^c), with the i of the last one's relative phase included; from
+// Tr(t^a t^b) = delta/2, sum_a t^a t^a = C_F = 4/3, sum_a t^a t^b t^a = -t^b / 6,
+// f^{acd} f^{bcd} = 3 delta: e.g. N_11 = 3 (N C_F^2 / 2) = 8, N_55 = 3 (C_A (N^2-1)/4) = 18.
+//
+// A lane holds one light-quark helicity pair (the two with equal helicities vanish
+// for massless quarks) and one gluon polarisation: 4 lanes per event.  Everything
+// the parameters do not touch (C1, C2, E, J_in) is built once per event; per mass
+// slot the lane builds the top spinors, the two top-line chains and the 5 amplitudes
+// of its 4 top-helicity pairs.
+#pragma once
+
+#include "helas.cuh"
+#include "qq_amplitude.cuh"
+
+namespace rex {
+
+// psibar gamma^mu chi of Dirac spinors (chiral basis):
+// psi_L^dag sigmabar^mu chi_L + psi_R^dag sigma^mu chi_R
+template <typename R>
+__device__ __forceinline__ void dirac_current(const cx<R>* psi, const cx<R>* chi, cx<R>* J) {
+  cx<R> sl[4], sr[4];
+  sigma_bilinear(psi, chi, sl);
+  sigma_bilinear(psi + 2, chi + 2, sr);
+  J[0] = sl[0] + sr[0];
+#pragma unroll
+  for (int m = 1; m < 4; ++m) J[m] = sr[m] - sl[m];
+}
+
+// out = J-slash psi for a complex 4-vector J
+template <typename R>
+__device__ __forceinline__ void cslash(const cx<R>* J, const cx<R>* psi, cx<R>* out) {
+  R jr[4], ji[4];
+#pragma unroll
+  for (int m = 0; m < 4; ++m) {
+    jr[m] = J[m].re;
+    ji[m] = J[m].im;
+  }
+  cx<R> t[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    out[i] = cx<R>{R(0), R(0)};
+    t[i] = cx<R>{R(0), R(0)};
+  }
+  slash_acc(R(1), jr, psi, out);
+  slash_acc(R(1), ji, psi, t);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) out[i] = out[i] + cx<R>{-t[i].im, t[i].re};
+}
+
+// Minkowski product of complex 4-vectors (no conjugation)
+template <typename R>
+__device__ __forceinline__ cx<R> cdotm(const cx<R>* a, const cx<R>* b) {
+  return a[0] * b[0] - a[1] * b[1] - a[2] * b[2] - a[3] * b[3];
+}
+
+// Minkowski product of a complex and a real 4-vector
+template <typename R>
+__device__ __forceinline__ cx<R> cdotr(const cx<R>* a, const R* b) {
+  return cx<R>{a[0].re * b[0] - a[1].re * b[1] - a[2].re * b[2] - a[3].re * b[3],
+               a[0].im * b[0] - a[1].im * b[1] - a[2].im * b[2] - a[3].im * b[3]};
+}
+
+// 3 x the colour matrix of a1..a5 (real symmetric; see the header comment)
+__device__ __forceinline__ constexpr int qqg_colour(int i, int j) {
+  constexpr int N[5][5] = {{8, -1, 7, -2, -9}, {-1, 8, -2, 7, 9}, {7, -2, 8, -1, -9},
+                           {-2, 7, -1, 8, 9}, {-9, 9, -9, 9, 18}};
+  return N[i][j];
+}
+
+template <typename R>
+struct QqgLane {
+  cx<R> jin[4], c1[4], c2[4], e[4];
+  R eps[4], a3[4], a4[4];
+  cx<R> chi3[2][2], chi4[2][2];   // [0] = chi-, [1] = chi+
+  R wp3, wp4;
+  R is, isp;                      // 1/s, 1/s'
+  double a3sq, a4sq;              // (p3 + k)^2, (p4 + k)^2 in FP64
+};
+
+// Lane set-up: light-quark helicities (l1, l2) = h12 ? (-, +) : (+, -), gluon
+// polarisation pol; pd: the event's FP64 momenta, p: the same in R.
+template <typename R>
+__device__ __forceinline__ void qqg_lane_setup(const double (&pd)[5][4], const R (&p)[5][4], int h12, int pol,
+                                               QqgLane<R>& L) {
+  const int l1 = h12 ? -1 : 1;
+  cx<R> u1[4], v2[4];
+  spinor_u(p[0], R(0), l1, u1);
+  spinor_v(p[1], R(0), -l1, v2);
+  pol_linear(p[4], pol, L.eps);
+  dirac_current(v2, u1, L.jin);
+  // FP64 invariants
+  double a1d[4], a2d[4], a3d[4], a4d[4], qd[4], qpd[4];
+#pragma unroll
+  for (int m = 0; m < 4; ++m) {
+    a1d[m] = pd[0][m] - pd[4][m];
+    a2d[m] = pd[4][m] - pd[1][m];
+    a3d[m] = pd[2][m] + pd[4][m];
+    a4d[m] = -pd[3][m] - pd[4][m];
+    qd[m] = pd[0][m] + pd[1][m];
+    qpd[m] = pd[2][m] + pd[3][m];
+  }
+  const double s = mdot(qd, qd), sp = mdot(qpd, qpd);
+  L.is = R(1.0 / s);
+  L.isp = R(1.0 / sp);
+  L.a3sq = mdot(a3d, a3d);
+  L.a4sq = mdot(a4d, a4d);
+  R a1[4], a2[4], q[4], qp[4];
+#pragma unroll
+  for (int m = 0; m < 4; ++m) {
+    a1[m] = R(a1d[m]);
+    a2[m] = R(a2d[m]);
+    L.a3[m] = R(a3d[m]);
+    L.a4[m] = R(a4d[m]);
+    q[m] = R(qd[m]);
+    qp[m] = R(qpd[m]);
+  }
+  // C1 = vbar2 gamma^mu a1-slash eps-slash u1 / a1^2
+  cx<R> t1[4], t2[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) t1[i] = cx<R>{R(0), R(0)};
+  slash_acc(R(1), L.eps, u1, t1);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) t2[i] = cx<R>{R(0), R(0)};
+  slash_acc(R(1), a1, t1, t2);
+  dirac_current(v2, t2, L.c1);
+  const R ia1 = R(1.0 / mdot(a1d, a1d));
+#pragma unroll
+  for (int m = 0; m < 4; ++m) L.c1[m] = ia1 * L.c1[m];
+  // C2 = vbar2 eps-slash a2-slash gamma^mu u1 / a2^2 = bar(a2-slash eps-slash v2) gamma^mu u1 / a2^2
+#pragma unroll
+  for (int i = 0; i < 4; ++i) t1[i] = cx<R>{R(0), R(0)};
+  slash_acc(R(1), L.eps, v2, t1);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) t2[i] = cx<R>{R(0), R(0)};
+  slash_acc(R(1), a2, t1, t2);
+  dirac_current(t2, u1, L.c2);
+  const R ia2 = R(1.0 / mdot(a2d, a2d));
+#pragma unroll
+  for (int m = 0; m < 4; ++m) L.c2[m] = ia2 * L.c2[m];
+  // E = (J_in.eps)(q + k) + (J_in.(q' - k)) eps - (eps.(q' + q)) J_in
+  R qk[4], qpk[4], qq2[4];
+#pragma unroll
+  for (int m = 0; m < 4; ++m) {
+    qk[m] = q[m] + p[4][m];
+    qpk[m] = qp[m] - p[4][m];
+    qq2[m] = qp[m] + q[m];
+  }
+  const cx<R> je = cdotr(L.jin, L.eps), jq = cdotr(L.jin, qpk);
+  const R eq = mdot(L.eps, qq2);
+#pragma unroll
+  for (int m = 0; m < 4; ++m) L.e[m] = qk[m] * je + L.eps[m] * jq - eq * L.jin[m];
+  // top helicity 2-spinors (mass independent)
+  L.wp3 = sqrt(chis(p[2], L.chi3[0], L.chi3[1]));
+  L.wp4 = sqrt(chis(p[3], L.chi4[0], L.chi4[1]));
+}
+
+// The lane's colour-summed |amplitude|^2 summed over the 4 top-helicity pairs, at top
+// mass m and width w (g, colour 1/3 and averaging not applied).
+template <typename R>
+__device__ __forceinline__ R qqg_slot(const QqgLane<R>& L, double m, double w) {
+  const R mr = R(m);
+  cx<R> u3[2][4], v4[2][4];
+  spinor_u_from(L.chi3, L.wp3, mr / L.wp3, u3);
+  spinor_v_from(L.chi4, L.wp4, mr / L.wp4, v4);
+  // 1 / (d + i m w) in FP64, then R
+  const double d3 = L.a3sq - m * m, d4 = L.a4sq - m * m, mw = m * w;
+  const double n3 = 1.0 / (d3 * d3 + mw * mw), n4 = 1.0 / (d4 * d4 + mw * mw);
+  const cx<R> i3 = cx<R>{R(d3 * n3), R(-mw * n3)} , i4 = cx<R>{R(d4 * n4), R(-mw * n4)};
+  const cx<R> f3 = L.is * i3, f4 = L.is * i4;
+  const R f5 = L.is * L.isp;
+  R sum = R(0);
+#pragma unroll
+  for (int l4 = 0; l4 < 2; ++l4) {
+    cx<R> t1[4], t2[4], t3[4], s1[4], s2[4], s3[4];
+    // eps-slash (a3-slash + m) J_in-slash v4
+    cslash(L.jin, v4[l4], t1);
+    slash_plus_scalar(L.a3, mr, t1, t2);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) t3[i] = cx<R>{R(0), R(0)};
+    slash_acc(R(1), L.eps, t2, t3);
+    // J_in-slash (a4-slash + m) eps-slash v4
+#pragma unroll
+    for (int i = 0; i < 4; ++i) s1[i] = cx<R>{R(0), R(0)};
+    slash_acc(R(1), L.eps, v4[l4], s1);
+    slash_plus_scalar(L.a4, mr, s1, s2);
+    cslash(L.jin, s2, s3);
+#pragma unroll
+    for (int l3 = 0; l3 < 2; ++l3) {
+      cx<R> jout[4];
+      dirac_current(u3[l3], v4[l4], jout);
+      cx<R> a[5];
+      a[0] = L.isp * cdotm(L.c1, jout);
+      a[1] = L.isp * cdotm(L.c2, jout);
+      a[2] = f3 * ubar_dot(u3[l3], t3);
+      a[3] = f4 * ubar_dot(u3[l3], s3);
+      a[4] = f5 * cdotm(L.e, jout);
+      R form = R(0);
+#pragma unroll
+      for (int d = 0; d < 5; ++d) {
+        form += R(qqg_colour(d, d)) * (a[d].re * a[d].re + a[d].im * a[d].im);
+#pragma unroll
+        for (int d2 = d + 1; d2 < 5; ++d2)
+          form += R(2 * qqg_colour(d, d2)) * (a[d].re * a[d2].re + a[d].im * a[d2].im);
+      }
+      sum += form;
+    }
+  }
+  return sum;
+}
+
+}  // namespace rex

@@ -69,13 +69,14 @@ const ProcInfo kProcs[] = {
     {"gg_ttxg", PROC_GG_TTXG, 5, gg_ttxg_info::NGLUON, gg_ttxg_info::COLOUR_DEN},
     {"gg_ttxgg", PROC_GG_TTXGG, 6, gg_ttxgg_info::NGLUON, gg_ttxgg_info::COLOUR_DEN},
     {"qq_ttx", PROC_QQ_TTX, 4, 0, 1},
+    {"qq_ttxg", PROC_QQ_TTXG, 5, 0, 1},
 };
 static_assert(sizeof(kProcs) / sizeof(kProcs[0]) == PROC_LAST + 1, "one table row per process kind");
 
 const ProcInfo& info_of(int kind) { return kProcs[kind]; }
 
 // processes with one kernel (no thread-mapping variants to choose from)
-bool single_variant(int kind) { return kind == PROC_EE_MUMU || kind == PROC_QQ_TTX; }
+bool single_variant(int kind) { return kind == PROC_EE_MUMU || kind == PROC_QQ_TTX || kind == PROC_QQ_TTXG; }
 
 // Default thread-mapping variant per (process, precision), the fastest of every
 // variant timed on a B300 at 2^20 (gg_ttx, gg_ttxg) / 2^16 (gg_ttxgg) events;
@@ -87,6 +88,7 @@ int default_variant(int kind, int precision) {
       {0, 2},   // gg_ttxg:  FP64 v0, mixed v2 (min 3 blocks/SM)
       {0, 0},   // gg_ttxgg: FP64 v0, mixed v0
       {0, 0},   // qq_ttx (single variant)
+      {0, 0},   // qq_ttxg (single variant)
   };
   return table[kind][precision == REX_MIXED ? 1 : 0];
 }
@@ -99,6 +101,7 @@ int launch_qcd(const rex_proc* p, const double* mom, const double* w_in, int64_t
     case PROC_GG_TTXG: return launch_gg_ttxg(mixed, p->variant, mom, w_in, nev, lp, out, stream);
     case PROC_GG_TTXGG: return launch_gg_ttxgg(mixed, p->variant, mom, w_in, nev, lp, out, stream);
     case PROC_QQ_TTX: return launch_qq_ttx(mixed, mom, w_in, nev, lp, out, stream, hel);
+    case PROC_QQ_TTXG: return launch_qq_ttxg(mixed, mom, w_in, nev, lp, out, stream);
     default: return (int)cudaErrorInvalidValue;
   }
 }
@@ -111,6 +114,8 @@ bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) ==
 double qcd_factor(const ProcInfo& pi, double alphas) {
   const double gs2 = 4.0 * M_PI * alphas;
   if (pi.kind == PROC_QQ_TTX) return gs2 * gs2 * 2.0 / 36.0;
+  // q q~ -> t t~ g: g^6, the integer colour matrix's 1/3, average 1/(4 spins * 9 colours)
+  if (pi.kind == PROC_QQ_TTXG) return gs2 * gs2 * gs2 / (3.0 * 36.0);
   double f = 1.0;
   for (int i = 0; i < pi.ngluon; ++i) f *= gs2;
   int nfinal = pi.ngluon - 2;
@@ -353,8 +358,8 @@ int multi_impl(rex_multi* m, const rex_batch* batches, int nbatch, const rex_par
   const int mixed_p = m->precision == REX_MIXED;
   double tile_cost[MULTI_MAX_BATCH];
   for (int i = 0; i < nbatch; ++i) {
-    static const double flops_per_event_slot[PROC_LAST + 1] = {160.0, 5.0e3, 4.8e4, 5.7e5, 3.0};   // per mass slot
-    static const double flops_per_event_fixed[PROC_LAST + 1] = {6.4e3, 4.0e2, 6.6e3, 1.1e5, 6.0e2};
+    static const double flops_per_event_slot[PROC_LAST + 1] = {160.0, 5.0e3, 4.8e4, 5.7e5, 3.0, 2.4e4};   // per mass slot
+    static const double flops_per_event_fixed[PROC_LAST + 1] = {6.4e3, 4.0e2, 6.6e3, 1.1e5, 6.0e2, 4.0e3};
     const int kind = batches[i].proc->kind;
     const double rate = (kind == PROC_EE_MUMU || !mixed_p) ? 1.0 : 64.0;
     const double slots = kind == PROC_EE_MUMU ? (k < MULTI_MAX_POINTS ? k : MULTI_MAX_POINTS) + 1.0 : 9.0;

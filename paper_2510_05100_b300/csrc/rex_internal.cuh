@@ -10,14 +10,16 @@ namespace rex {
 constexpr int MAX_MASS = 64;
 constexpr int MAX_POINTS = 256;
 
-enum ProcKind : int { PROC_EE_MUMU = 0, PROC_GG_TTX = 1, PROC_GG_TTXG = 2, PROC_GG_TTXGG = 3, PROC_QQ_TTX = 4 };
-constexpr int PROC_LAST = PROC_QQ_TTX;
+enum ProcKind : int {
+  PROC_EE_MUMU = 0, PROC_GG_TTX = 1, PROC_GG_TTXG = 2, PROC_GG_TTXGG = 3, PROC_QQ_TTX = 4, PROC_QQ_TTXG = 5
+};
+constexpr int PROC_LAST = PROC_QQ_TTXG;
 enum OutMode : int { OUT_RATIO = 0, OUT_ME2 = 1 };
 
 // QCD processes: the amplitude is evaluated once per mass slot (slot 0 is the
 // original point) with unit coupling; point j then takes
 //   |M|^2_j = acc[slot[j]] * factor[j],  factor = avg * (4 pi alphas)^n / colour_den
-// (q q~ -> t t~: avg * (4 pi alphas)^2 * colour sum 2).
+// (q q~ -> t t~: avg * (4 pi alphas)^2 * colour sum 2; q q~ -> t t~ g: (4 pi alphas)^3 / 108).
 struct QcdLaunch {
   int nmass;
   int k;
@@ -110,6 +112,8 @@ int launch_gg_ttxgg(int mixed, int variant, const double* mom, const double* w_i
 // [nev][npart] (int8, positive: +1, otherwise -1) for helicity-exclusive reweighting.
 int launch_qq_ttx(int mixed, const double* mom, const double* w_in, int64_t nev, const QcdLaunch& lp,
                   double* out, void* stream, const signed char* hel);
+int launch_qq_ttxg(int mixed, const double* mom, const double* w_in, int64_t nev, const QcdLaunch& lp,
+                   double* out, void* stream);
 int launch_ee(const double* mom, const double* w_in, int64_t nev, const EwLaunch& lp,
               double* out, void* stream, const signed char* hel);
 

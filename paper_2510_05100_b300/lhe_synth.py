@@ -25,6 +25,7 @@ PROCESSES = {
     "gg_ttxg": ([21, 21], [6, -6, 21]),
     "gg_ttxgg": ([21, 21], [6, -6, 21, 21]),
     "qq_ttx": ([2, -2], [6, -6]),
+    "qq_ttxg": ([2, -2], [6, -6, 21]),
 }
 _MASS = {6: 173.0, -6: 173.0}
 

@@ -40,7 +40,7 @@ def test_init_errors(rex):
     assert lib.rex_init_process(b"ee_mumu", rex.MIXED, ctypes.byref(h)) == rex.REX_EUNSUPPORTED
 
 
-@pytest.mark.parametrize("name,npart", [("ee_mumu", 4), ("gg_ttx", 4), ("gg_ttxg", 5), ("gg_ttxgg", 6), ("qq_ttx", 4)])
+@pytest.mark.parametrize("name,npart", [("ee_mumu", 4), ("gg_ttx", 4), ("gg_ttxg", 5), ("gg_ttxgg", 6), ("qq_ttx", 4), ("qq_ttxg", 5)])
 def test_handle_lifecycle(rex, name, npart):
     p = rex.Process(name)
     assert p.npart == npart

@@ -1,0 +1,115 @@
+"""q q~ -> t t~ g on the GPU vs the FP64 oracle, through the C ABI (needs a B300).
+
+Tolerances: FP64 1e-12 relative per weight; mixed precision (FP32 amplitudes,
+FP64 invariants, ratio and epilogue) 1e-4, a factor of 7 or more above the largest
+error measured against the FP64 kernel over 2^18 events.
+"""
+import numpy as np
+import pytest
+
+from rexlib import ensure_built
+from oracle import reweight as oracle_rw
+from paper_2510_05100_b300 import phase_space as ps
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+FP64_TOL = 1e-12
+MIXED_TOL = 1e-4
+ORIG = dict(mt=173.0, wt=0.0, alphas=0.118)
+PROC = "qq_ttxg"
+
+
+@pytest.fixture(scope="module")
+def rex():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return ensure_built()
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def make(rex, precision=0):
+    p = rex.Process(PROC, precision)
+    p.set_params(ORIG)
+    return p
+
+
+def rel(a, b):
+    return np.abs(a / b - 1.0)
+
+
+def points():
+    return ps.grid_gg_ttxg() + [dict(mt=172.0, wt=1.4, alphas=0.118), ORIG, dict(mt=173.0, wt=0.0, alphas=0.124)]
+
+
+@pytest.mark.parametrize("precision,tol", [(0, FP64_TOL), (1, MIXED_TOL)])
+def test_me2_parity(rex, precision, tol):
+    n = 75   # 3 tiles of 32, ragged tail
+    mom = ps.make_events(PROC, n, 71)
+    p = make(rex, precision)
+    for pt in (ORIG, dict(mt=169.0, wt=1.0, alphas=0.125)):
+        got = p.me2(dev(mom), pt).cpu().numpy()
+        ref = oracle_rw.me2(PROC, mom, pt)
+        assert np.max(rel(got, ref)) < tol
+
+
+@pytest.mark.parametrize("precision,tol", [(0, FP64_TOL), (1, MIXED_TOL)])
+def test_reweight_parity(rex, precision, tol):
+    n = 101
+    mom = ps.make_events(PROC, n, 72)
+    w = np.random.default_rng(7).uniform(-1.0, 2.0, n)
+    pts = points()
+    got = make(rex, precision).reweight(dev(mom), dev(w), pts).cpu().numpy()
+    ref = oracle_rw.reweight(PROC, mom, w, ORIG, pts)
+    assert np.max(np.abs(got - ref) / np.abs(ref)) < tol
+    j = pts.index(ORIG)
+    assert np.array_equal(got[:, j], w)
+    assert np.max(rel(got[:, j + 1], w * (0.124 / 0.118) ** 3)) < 1e-14
+
+
+@pytest.mark.parametrize("n", [1, 31, 32, 33])
+def test_ragged_tails(rex, n):
+    mom = ps.make_events(PROC, n, 73)
+    pts = ps.grid_gg_ttxg()[:6]
+    got = make(rex).reweight(dev(mom), dev(np.ones(n)), pts).cpu().numpy()
+    ref = oracle_rw.reweight(PROC, mom, np.ones(n), ORIG, pts)
+    assert np.max(rel(got, ref)) < FP64_TOL
+
+
+def test_mixed_against_fp64_at_scale(rex):
+    """2^18 events x 16 points: the mixed kernel against the FP64 kernel at every event,
+    and the FP64 kernel against the oracle on sampled events."""
+    n = 1 << 18
+    mom = ps.make_events(PROC, n, 74)
+    w = np.ones(n)
+    pts = ps.grid_gg_ttxg()
+    dm, dw = dev(mom), dev(w)
+    exact = make(rex).reweight(dm, dw, pts).cpu().numpy()
+    idx = np.concatenate([np.random.default_rng(9).choice(n, 12, replace=False), [0, n - 1]])
+    assert np.max(rel(exact[idx], oracle_rw.reweight(PROC, mom[idx], w[idx], ORIG, pts))) < FP64_TOL
+    mixed = make(rex, 1).reweight(dm, dw, pts).cpu().numpy()
+    err = float(np.max(rel(mixed, exact)))
+    print(f"q q~ -> t t~ g mixed vs FP64 max rel err {err:.3e}")
+    assert err < MIXED_TOL
+
+
+def test_in_the_persistent_multi_kernel(rex):
+    """g g -> t t~ g and q q~ -> t t~ g batches in one persistent launch (register class 1)."""
+    pts = ps.grid_gg_ttxg()
+    batches, single = [], []
+    for proc, n, seed in (("gg_ttxg", 90, 75), ("qq_ttxg", 70, 76)):
+        p = rex.Process(proc, 1)
+        p.set_params(ORIG)
+        dm = dev(ps.make_events(proc, n, seed))
+        dw = torch.ones(n, dtype=torch.float64, device="cuda")
+        batches.append((p, dm, dw, torch.zeros((n, len(pts)), dtype=torch.float64, device="cuda")))
+        single.append(p.reweight(dm, dw, pts).cpu().numpy())
+    m = rex.Multi(1)
+    m.reweight(batches, pts)
+    torch.cuda.synchronize()
+    for b, ref in zip(batches, single):
+        assert np.max(rel(b[3].cpu().numpy(), ref)) < 1e-13
+    m.close()

@@ -13,6 +13,7 @@ def _mdot(a, b):
     ("ee_mumu", [0, 0, 0, 0]),
     ("gg_ttx", [0, 0, 173, 173]),
     ("qq_ttx", [0, 0, 173, 173]),
+    ("qq_ttxg", [0, 0, 173, 173, 0]),
     ("gg_ttxg", [0, 0, 173, 173, 0]),
     ("gg_ttxgg", [0, 0, 173, 173, 0, 0]),
 ])
