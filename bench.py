@@ -193,7 +193,7 @@ def main():
     ap.add_argument("--no-surrogate", action="store_true")
     ap.add_argument("--no-xsec", action="store_true")
     ap.add_argument("--no-lhe", action="store_true")
-    ap.add_argument("--no-qq", action="store_true", help="skip the q q~ -> t t~ and p p -> t t~ legs")
+    ap.add_argument("--no-qq", action="store_true", help="skip the q q~ -> t t~ (g) and p p -> t t~ legs")
     args = ap.parse_args()
     world, rank, local = rdist.env()
     if args.impl == "reference":
@@ -308,6 +308,42 @@ def run_multi_leg(dev, stream, steps, world, barrier, max_over_ranks):
             "note": "value: the persistent kernel (one launch, one register budget for every process); "
                     "streams_graph: one graph of per-process launches on forked streams",
             "steps": steps}
+
+
+def run_qqg_leg(dev, stream, pts, steps, nev=NEV):
+    """q q~ -> t t~ g (the quark-initiated p p -> t t~ + jet channel) on the headline's
+    points: nev events per launch in FP64 and mixed precision, CUDA-event timed, with the
+    roofline of each kernel against its arithmetic pipe (counted flops)."""
+    import torch
+    from paper_2510_05100_b300 import flops as flopmod
+    from paper_2510_05100_b300 import rex
+    k = len(pts)
+    mom = torch.from_numpy(ps.make_events("qq_ttxg", nev, SEED + 200)).to(dev)
+    w_in = torch.ones(nev, dtype=torch.float64, device=dev)
+    w_out = torch.empty((nev, k), dtype=torch.float64, device=dev)
+    nmass = 1 + len({p["mt"] for p in pts} - {ORIGINAL["mt"]})
+    fl = flopmod.per_event("qq_ttxg", nmass)["amp"] * nev
+    p64 = SM_COUNT * FP64_FMA_PER_SM_CLK * 2 * SM_MAX_MHZ * 1e6
+    out = {"workload": f"q q~ -> t t~ g, {nev} events x {k} points ({nmass} mass slots), the headline's grid",
+           "flops_per_launch": fl}
+    for name, prec, peak, pipe in (("fp64", rex.FP64, p64, "FP64 FMA"), ("mixed", rex.MIXED, FP32_PEAK, "FP32 FMA")):
+        proc = rex.Process("qq_ttxg", prec)
+        proc.set_params(ORIGINAL)
+        for _ in range(3):
+            proc.reweight(mom, w_in, pts, w_out=w_out, stream=stream)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        torch.cuda.synchronize(dev)
+        for a, b in ev:
+            a.record(stream)
+            proc.reweight(mom, w_in, pts, w_out=w_out, stream=stream)
+            b.record(stream)
+        torch.cuda.synchronize(dev)
+        proc.close()
+        t = statistics.mean(a.elapsed_time(b) for a, b in ev) * 1e-3
+        out[name] = {"value": nev * k / t, "unit": UNIT, "ms_per_launch": t * 1e3,
+                     "roofline": {"bound": "alu", "pipe": pipe, "achieved": fl / t / 1e12, "peak": peak / 1e12,
+                                  "unit": "TFLOP/s", "frac": fl / t / peak}}
+    return out
 
 
 # a two-channel p p -> t t~ sample: g g and q q~ initial states, 7 : 1, 2^20 events
@@ -724,6 +760,7 @@ def run_ours(args, world, rank, local):
 
     lhe_leg = None if args.no_lhe else run_lhe_leg(dev, stream, pts)
     qq_leg = None if args.no_qq else run_qq_leg(dev, stream, pts, max(5, args.steps // 2))
+    qqg_leg = None if args.no_qq else run_qqg_leg(dev, stream, pts, max(3, args.steps // 4))
     pp_leg = None if args.no_qq else run_pp_ttx_leg(dev, stream, pts, max(3, args.steps // 4), world, barrier,
                                                      max_over_ranks)
 
@@ -756,7 +793,7 @@ def run_ours(args, world, rank, local):
                         "entry_point": "rex_reweight_host (pinned host buffers)"},
                 "gpu_launches": args.steps, "roofline": roofline, "cpu_baseline": cpu, "modes": extra,
                 "multi": multi, "surrogate": surrogate, "xsec": xsec, "lhe": lhe_leg, "qq_ttx": qq_leg,
-                "pp_ttx": pp_leg}
+                "qq_ttxg": qqg_leg, "pp_ttx": pp_leg}
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist

@@ -66,6 +66,7 @@ using AC = Cnt<1>;    // colour / helicity accumulation
 
 #include "../generated/qcd_amplitudes.cuh"
 #include "../qq_amplitude.cuh"
+#include "../qqg_amplitude.cuh"
 
 using namespace rex;
 
@@ -137,7 +138,28 @@ int main() {
     qq_ttx_coefficients<RC>(p, c, &e12);
     std::printf("  \"qq_ttx\": {\"nghel\": 1, \"event_setup\": %lld, \"mass_setup\": 0, "
                 "\"polarisations\": 0, \"gluon_currents\": 0, \"quark_line_amp\": 0, "
-                "\"quark_line_acc\": 0}\n", RC::flops);
+                "\"quark_line_acc\": 0},\n", RC::flops);
+  }
+  {
+    // q q~ -> t t~ g: 4 lanes per event; lane set-up once per event, the slot routine
+    // once per mass slot (FP64 invariants and denominators not counted)
+    double pd[5][4];
+    RC p[5][4];
+    for (int i = 0; i < 5; ++i)
+      for (int m = 0; m < 4; ++m) {
+        pd[i][m] = 1.0 + i + 0.1 * m;
+        p[i][m] = RC(pd[i][m]);
+      }
+    QqgLane<RC> L;
+    RC::flops = 0;
+    qqg_lane_setup<RC>(pd, p, 0, 0, L);
+    const long long f_setup = RC::flops;
+    RC::flops = 0;
+    qqg_slot<RC>(L, 173.0, 0.0);
+    const long long f_slot = RC::flops;
+    std::printf("  \"qq_ttxg\": {\"nghel\": 1, \"event_setup\": %lld, \"mass_setup\": %lld, "
+                "\"polarisations\": 0, \"gluon_currents\": 0, \"quark_line_amp\": 0, "
+                "\"quark_line_acc\": 0}\n", 4 * f_setup, 4 * f_slot);
   }
   std::printf("}\n");
   return 0;

@@ -27,7 +27,8 @@ def counts() -> dict:
     os.makedirs(BUILD, exist_ok=True)
     exe = os.path.join(BUILD, "flopcount")
     newest = max(os.path.getmtime(SRC), os.path.getmtime(GEN),
-                 os.path.getmtime(os.path.join(HERE, "csrc", "helas.cuh")))
+                 *(os.path.getmtime(os.path.join(HERE, "csrc", f))
+                   for f in ("helas.cuh", "qq_amplitude.cuh", "qqg_amplitude.cuh")))
     if not os.path.exists(exe) or os.path.getmtime(exe) < newest:
         subprocess.run(["g++", "-O0", "-std=c++17", "-o", exe, SRC], check=True)
     out = subprocess.run([exe], check=True, capture_output=True, text=True).stdout

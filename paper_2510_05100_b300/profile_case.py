@@ -19,7 +19,7 @@ from paper_2510_05100_b300 import phase_space as ps  # noqa: E402
 from paper_2510_05100_b300 import rex  # noqa: E402
 
 GRIDS = {"gg_ttx": ps.grid_gg_ttx, "gg_ttxg": ps.grid_gg_ttxg, "gg_ttxgg": ps.grid_64,
-         "qq_ttx": ps.grid_gg_ttxg}
+         "qq_ttx": ps.grid_gg_ttxg, "qq_ttxg": ps.grid_gg_ttxg}
 
 
 def main():
