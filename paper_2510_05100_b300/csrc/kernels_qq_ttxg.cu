@@ -3,8 +3,10 @@
 
 namespace rex {
 
-template <typename R>
-__global__ void __launch_bounds__(QQG_BLOCK, 1)
+// resident blocks per SM the register allocator must allow: FP64 1, mixed 3 (168
+// registers, no spill)
+template <typename R, int MINB>
+__global__ void __launch_bounds__(QQG_BLOCK, MINB)
     qq_ttxg_reweight_kernel(const double* __restrict__ mom, const double* __restrict__ w_in, int64_t nev,
                             const __grid_constant__ QcdLaunch lp, double* __restrict__ out) {
   __shared__ typename QqgTile<R>::Smem sm;
@@ -18,9 +20,9 @@ int launch_qq_ttxg(int mixed, const double* mom, const double* w_in, int64_t nev
   if (blocks > 0x7fffffffLL) return (int)cudaErrorInvalidValue;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   if (mixed)
-    qq_ttxg_reweight_kernel<float><<<(unsigned)blocks, QQG_BLOCK, 0, st>>>(mom, w_in, nev, lp, out);
+    qq_ttxg_reweight_kernel<float, 3><<<(unsigned)blocks, QQG_BLOCK, 0, st>>>(mom, w_in, nev, lp, out);
   else
-    qq_ttxg_reweight_kernel<double><<<(unsigned)blocks, QQG_BLOCK, 0, st>>>(mom, w_in, nev, lp, out);
+    qq_ttxg_reweight_kernel<double, 1><<<(unsigned)blocks, QQG_BLOCK, 0, st>>>(mom, w_in, nev, lp, out);
   return (int)cudaGetLastError();
 }
 

@@ -90,13 +90,21 @@ struct QqgLane {
   cx<R> chi3[2][2], chi4[2][2];   // [0] = chi-, [1] = chi+
   R wp3, wp4;
   R is, isp;                      // 1/s, 1/s'
-  double a3sq, a4sq;              // (p3 + k)^2, (p4 + k)^2 in FP64
+  R d3, d4;                       // (p3 + k)^2 - m0^2, (p4 + k)^2 - m0^2
+};
+
+// The event's invariants, taken in FP64 by the caller (once per event): 1/s, 1/s',
+// 1/(p1 - k)^2, 1/(k - p2)^2 and the top-propagator denominators at a reference mass
+// m0, (p3 + k)^2 - m0^2 and (p4 + k)^2 - m0^2; a slot at mass m adds m0^2 - m^2.
+template <typename R>
+struct QqgInvariants {
+  R is, isp, ia1, ia2, d3, d4;
 };
 
 // Lane set-up: light-quark helicities (l1, l2) = h12 ? (-, +) : (+, -), gluon
-// polarisation pol; pd: the event's FP64 momenta, p: the same in R.
+// polarisation pol; p: the event's momenta in R.
 template <typename R>
-__device__ __forceinline__ void qqg_lane_setup(const double (&pd)[5][4], const R (&p)[5][4], int h12, int pol,
+__device__ __forceinline__ void qqg_lane_setup(const R (&p)[5][4], const QqgInvariants<R>& inv, int h12, int pol,
                                                QqgLane<R>& L) {
   const int l1 = h12 ? -1 : 1;
   cx<R> u1[4], v2[4];
@@ -104,31 +112,21 @@ __device__ __forceinline__ void qqg_lane_setup(const double (&pd)[5][4], const R
   spinor_v(p[1], R(0), -l1, v2);
   pol_linear(p[4], pol, L.eps);
   dirac_current(v2, u1, L.jin);
-  // FP64 invariants
-  double a1d[4], a2d[4], a3d[4], a4d[4], qd[4], qpd[4];
+  L.is = inv.is;
+  L.isp = inv.isp;
+  L.d3 = inv.d3;
+  L.d4 = inv.d4;
+  R a1[4], a2[4], qk[4], qpk[4], qq2[4];
 #pragma unroll
   for (int m = 0; m < 4; ++m) {
-    a1d[m] = pd[0][m] - pd[4][m];
-    a2d[m] = pd[4][m] - pd[1][m];
-    a3d[m] = pd[2][m] + pd[4][m];
-    a4d[m] = -pd[3][m] - pd[4][m];
-    qd[m] = pd[0][m] + pd[1][m];
-    qpd[m] = pd[2][m] + pd[3][m];
-  }
-  const double s = mdot(qd, qd), sp = mdot(qpd, qpd);
-  L.is = R(1.0 / s);
-  L.isp = R(1.0 / sp);
-  L.a3sq = mdot(a3d, a3d);
-  L.a4sq = mdot(a4d, a4d);
-  R a1[4], a2[4], q[4], qp[4];
-#pragma unroll
-  for (int m = 0; m < 4; ++m) {
-    a1[m] = R(a1d[m]);
-    a2[m] = R(a2d[m]);
-    L.a3[m] = R(a3d[m]);
-    L.a4[m] = R(a4d[m]);
-    q[m] = R(qd[m]);
-    qp[m] = R(qpd[m]);
+    a1[m] = p[0][m] - p[4][m];
+    a2[m] = p[4][m] - p[1][m];
+    L.a3[m] = p[2][m] + p[4][m];
+    L.a4[m] = -p[3][m] - p[4][m];
+    const R q = p[0][m] + p[1][m], qp = p[2][m] + p[3][m];
+    qk[m] = q + p[4][m];
+    qpk[m] = qp - p[4][m];
+    qq2[m] = qp + q;
   }
   // C1 = vbar2 gamma^mu a1-slash eps-slash u1 / a1^2
   cx<R> t1[4], t2[4];
@@ -139,9 +137,8 @@ __device__ __forceinline__ void qqg_lane_setup(const double (&pd)[5][4], const R
   for (int i = 0; i < 4; ++i) t2[i] = cx<R>{R(0), R(0)};
   slash_acc(R(1), a1, t1, t2);
   dirac_current(v2, t2, L.c1);
-  const R ia1 = R(1.0 / mdot(a1d, a1d));
 #pragma unroll
-  for (int m = 0; m < 4; ++m) L.c1[m] = ia1 * L.c1[m];
+  for (int m = 0; m < 4; ++m) L.c1[m] = inv.ia1 * L.c1[m];
   // C2 = vbar2 eps-slash a2-slash gamma^mu u1 / a2^2 = bar(a2-slash eps-slash v2) gamma^mu u1 / a2^2
 #pragma unroll
   for (int i = 0; i < 4; ++i) t1[i] = cx<R>{R(0), R(0)};
@@ -150,17 +147,9 @@ __device__ __forceinline__ void qqg_lane_setup(const double (&pd)[5][4], const R
   for (int i = 0; i < 4; ++i) t2[i] = cx<R>{R(0), R(0)};
   slash_acc(R(1), a2, t1, t2);
   dirac_current(t2, u1, L.c2);
-  const R ia2 = R(1.0 / mdot(a2d, a2d));
 #pragma unroll
-  for (int m = 0; m < 4; ++m) L.c2[m] = ia2 * L.c2[m];
+  for (int m = 0; m < 4; ++m) L.c2[m] = inv.ia2 * L.c2[m];
   // E = (J_in.eps)(q + k) + (J_in.(q' - k)) eps - (eps.(q' + q)) J_in
-  R qk[4], qpk[4], qq2[4];
-#pragma unroll
-  for (int m = 0; m < 4; ++m) {
-    qk[m] = q[m] + p[4][m];
-    qpk[m] = qp[m] - p[4][m];
-    qq2[m] = qp[m] + q[m];
-  }
   const cx<R> je = cdotr(L.jin, L.eps), jq = cdotr(L.jin, qpk);
   const R eq = mdot(L.eps, qq2);
 #pragma unroll
@@ -170,19 +159,18 @@ __device__ __forceinline__ void qqg_lane_setup(const double (&pd)[5][4], const R
   L.wp4 = sqrt(chis(p[3], L.chi4[0], L.chi4[1]));
 }
 
-// The lane's colour-summed |amplitude|^2 summed over the 4 top-helicity pairs, at top
-// mass m and width w (g, colour 1/3 and averaging not applied).
+// The lane's colour-summed |amplitude|^2 summed over the 4 top-helicity pairs at top
+// mass mr, with dm2 = m0^2 - m^2 and mw = m Gamma (g, colour 1/3 and averaging not
+// applied).
 template <typename R>
-__device__ __forceinline__ R qqg_slot(const QqgLane<R>& L, double m, double w) {
-  const R mr = R(m);
+__device__ __forceinline__ R qqg_slot(const QqgLane<R>& L, R mr, R dm2, R mw) {
   cx<R> u3[2][4], v4[2][4];
   spinor_u_from(L.chi3, L.wp3, mr / L.wp3, u3);
   spinor_v_from(L.chi4, L.wp4, mr / L.wp4, v4);
-  // 1 / (d + i m w) in FP64, then R
-  const double d3 = L.a3sq - m * m, d4 = L.a4sq - m * m, mw = m * w;
-  const double n3 = 1.0 / (d3 * d3 + mw * mw), n4 = 1.0 / (d4 * d4 + mw * mw);
-  const cx<R> i3 = cx<R>{R(d3 * n3), R(-mw * n3)} , i4 = cx<R>{R(d4 * n4), R(-mw * n4)};
-  const cx<R> f3 = L.is * i3, f4 = L.is * i4;
+  // 1 / (d + i m Gamma)
+  const R d3 = L.d3 + dm2, d4 = L.d4 + dm2;
+  const R n3 = R(1) / (d3 * d3 + mw * mw), n4 = R(1) / (d4 * d4 + mw * mw);
+  const cx<R> f3 = L.is * cx<R>{d3 * n3, -mw * n3}, f4 = L.is * cx<R>{d4 * n4, -mw * n4};
   const R f5 = L.is * L.isp;
   R sum = R(0);
 #pragma unroll
@@ -222,6 +210,28 @@ __device__ __forceinline__ R qqg_slot(const QqgLane<R>& L, double m, double w) {
     }
   }
   return sum;
+}
+
+// The six FP64 invariants of an event: s, s', (p1 - k)^2, (k - p2)^2 and the top
+// denominators at the reference mass m0, (p3 + k)^2 - m0^2, (p4 + k)^2 - m0^2 (FP64
+// because (p1 - k)^2 and the top denominators cancel for collinear or soft gluons).
+__device__ __forceinline__ void qqg_invariants_fp64(const double (&pd)[5][4], double m0, double* v) {
+  double q[4], qp[4], a1[4], a2[4], a3[4], a4[4];
+#pragma unroll
+  for (int m = 0; m < 4; ++m) {
+    q[m] = pd[0][m] + pd[1][m];
+    qp[m] = pd[2][m] + pd[3][m];
+    a1[m] = pd[0][m] - pd[4][m];
+    a2[m] = pd[4][m] - pd[1][m];
+    a3[m] = pd[2][m] + pd[4][m];
+    a4[m] = pd[3][m] + pd[4][m];
+  }
+  v[0] = mdot(q, q);
+  v[1] = mdot(qp, qp);
+  v[2] = mdot(a1, a1);
+  v[3] = mdot(a2, a2);
+  v[4] = mdot(a3, a3) - m0 * m0;
+  v[5] = mdot(a4, a4) - m0 * m0;
 }
 
 }  // namespace rex

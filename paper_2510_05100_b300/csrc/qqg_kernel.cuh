@@ -3,7 +3,11 @@
 //
 // Blocks of 128 threads, 4 lanes per event (light-quark helicity pair x gluon
 // polarisation), 32 events per tile.
-//   a1     each lane loads its event's FP64 momenta (the 4 lanes read the same 160 B);
+//   a1     each lane loads its event's FP64 momenta (the 4 lanes read the same 160 B)
+//          and forms the six FP64 invariants; in the mixed mode these are the only
+//          FP64 instructions per event (B300 issues FP64 at 1/64 of the FP32 rate):
+//          momenta and invariants are converted on the integer ALUs, reciprocals and
+//          every per-slot quantity (m, m0^2 - m^2, m Gamma from a per-block table) are FP32;
 //   a3-a5  the lane builds its parameter-independent currents once
 //          (qqg_lane_setup), then per distinct (m_t, Gamma_t) slot its 4 top-helicity
 //          pairs' 5 amplitudes (qqg_slot);
@@ -17,6 +21,7 @@
 
 #include <type_traits>
 
+#include "fpconv.cuh"
 #include "qqg_amplitude.cuh"
 #include "rex_internal.cuh"
 
@@ -32,7 +37,13 @@ struct QqgTile {
   struct Smem {
     double me2s[EPB][MAX_MASS + 1];
     double inv0[EPB];
+    R mr[MAX_MASS], dm2[MAX_MASS], mw[MAX_MASS];   // per slot: m, m0^2 - m^2, m Gamma
   };
+
+  static __device__ __forceinline__ R to_r(double x) {
+    if constexpr (std::is_same<R, float>::value) return f64_to_f32_alu(x);
+    else return x;
+  }
 
   template <class TABLE>
   static __device__ __forceinline__ void run(Smem& sm, const double* __restrict__ mom,
@@ -44,6 +55,13 @@ struct QqgTile {
     const int64_t ev = ev0 + el;
     const bool valid = ev < nev;
     const int64_t evc = valid ? ev : nev - 1;
+    // per-slot table (slot 0 is the reference mass m0)
+    for (int s = tid; s < lp.nmass; s += QQG_BLOCK) {
+      const double m = lp.mass[s], m0 = lp.mass[0];
+      sm.mr[s] = to_r(m);
+      sm.dm2[s] = to_r((m0 - m) * (m0 + m));
+      sm.mw[s] = to_r(m * lp.width[s]);
+    }
     double pd[5][4];
     R p[5][4];
     const double2* src = reinterpret_cast<const double2*>(mom + evc * 20);
@@ -56,11 +74,21 @@ struct QqgTile {
 #pragma unroll
     for (int i = 0; i < 5; ++i)
 #pragma unroll
-      for (int m = 0; m < 4; ++m) p[i][m] = R(pd[i][m]);
+      for (int m = 0; m < 4; ++m) p[i][m] = to_r(pd[i][m]);
+    double v[6];
+    qqg_invariants_fp64(pd, lp.mass[0], v);
+    QqgInvariants<R> inv;
+    inv.is = R(1) / to_r(v[0]);
+    inv.isp = R(1) / to_r(v[1]);
+    inv.ia1 = R(1) / to_r(v[2]);
+    inv.ia2 = R(1) / to_r(v[3]);
+    inv.d3 = to_r(v[4]);
+    inv.d4 = to_r(v[5]);
     QqgLane<R> L;
-    qqg_lane_setup<R>(pd, p, lane & 1, lane >> 1, L);
+    qqg_lane_setup<R>(p, inv, lane & 1, lane >> 1, L);
+    __syncthreads();
     for (int s = 0; s < lp.nmass; ++s) {
-      R part = valid ? qqg_slot<R>(L, lp.mass[s], lp.width[s]) : R(0);
+      R part = valid ? qqg_slot<R>(L, sm.mr[s], sm.dm2[s], sm.mw[s]) : R(0);
       part += __shfl_xor_sync(0xffffffffu, part, 1);
       part += __shfl_xor_sync(0xffffffffu, part, 2);
       if (lane == 0) sm.me2s[el][s] = double(part);
