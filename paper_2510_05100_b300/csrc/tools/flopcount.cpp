@@ -142,7 +142,7 @@ int main() {
   }
   {
     // q q~ -> t t~ g: 4 lanes per event; lane set-up once per event, the slot routine
-    // once per mass slot (FP64 invariants and denominators not counted)
+    // once per mass slot (the six FP64 invariants and the reciprocals not counted)
     double pd[5][4];
     RC p[5][4];
     for (int i = 0; i < 5; ++i)
@@ -150,12 +150,13 @@ int main() {
         pd[i][m] = 1.0 + i + 0.1 * m;
         p[i][m] = RC(pd[i][m]);
       }
+    QqgInvariants<RC> inv{RC(1e-6), RC(1e-6), RC(-1e-4), RC(-1e-4), RC(100.0), RC(120.0)};
     QqgLane<RC> L;
     RC::flops = 0;
-    qqg_lane_setup<RC>(pd, p, 0, 0, L);
+    qqg_lane_setup<RC>(p, inv, 0, 0, L);
     const long long f_setup = RC::flops;
     RC::flops = 0;
-    qqg_slot<RC>(L, 173.0, 0.0);
+    qqg_slot<RC>(L, RC(171.0), RC(700.0), RC(0.0));
     const long long f_slot = RC::flops;
     std::printf("  \"qq_ttxg\": {\"nghel\": 1, \"event_setup\": %lld, \"mass_setup\": %lld, "
                 "\"polarisations\": 0, \"gluon_currents\": 0, \"quark_line_amp\": 0, "

@@ -98,3 +98,13 @@ def test_helicity_exclusive_validation_before_any_device_work(rex):
     assert lib.rex_reweight_helicity(None, fake, fake, fake, 10, pts, 1, fake, None) == rex.REX_EINVAL
     g.close()
     q.close()
+
+
+def test_flop_counter_builds_and_counts_every_process():
+    """The counting-scalar instantiation of the amplitude code (roofline flop counts)
+    compiles against the current device routines and covers every QCD process."""
+    from paper_2510_05100_b300 import flops
+    counts = flops.counts()
+    for proc in ("gg_ttx", "gg_ttxg", "gg_ttxgg", "qq_ttx", "qq_ttxg"):
+        assert flops.per_event(proc, 5)["amp"] > 0, proc
+    assert set(counts) >= {"gg_ttx", "gg_ttxg", "gg_ttxgg", "qq_ttx", "qq_ttxg"}
