@@ -102,20 +102,16 @@ struct QqgInvariants {
 };
 
 // Lane set-up: light-quark helicities (l1, l2) = h12 ? (-, +) : (+, -), gluon
-// polarisation pol; p: the event's momenta in R.
+// polarisation pol; p: the event's momenta in R.  C1 and C2 are left without their
+// propagator factors and the invariants unset: qqg_lane_scale applies them.
 template <typename R>
-__device__ __forceinline__ void qqg_lane_setup(const R (&p)[5][4], const QqgInvariants<R>& inv, int h12, int pol,
-                                               QqgLane<R>& L) {
+__device__ __forceinline__ void qqg_lane_setup(const R (&p)[5][4], int h12, int pol, QqgLane<R>& L) {
   const int l1 = h12 ? -1 : 1;
   cx<R> u1[4], v2[4];
   spinor_u(p[0], R(0), l1, u1);
   spinor_v(p[1], R(0), -l1, v2);
   pol_linear(p[4], pol, L.eps);
   dirac_current(v2, u1, L.jin);
-  L.is = inv.is;
-  L.isp = inv.isp;
-  L.d3 = inv.d3;
-  L.d4 = inv.d4;
   R a1[4], a2[4], qk[4], qpk[4], qq2[4];
 #pragma unroll
   for (int m = 0; m < 4; ++m) {
@@ -137,8 +133,6 @@ __device__ __forceinline__ void qqg_lane_setup(const R (&p)[5][4], const QqgInva
   for (int i = 0; i < 4; ++i) t2[i] = cx<R>{R(0), R(0)};
   slash_acc(R(1), a1, t1, t2);
   dirac_current(v2, t2, L.c1);
-#pragma unroll
-  for (int m = 0; m < 4; ++m) L.c1[m] = inv.ia1 * L.c1[m];
   // C2 = vbar2 eps-slash a2-slash gamma^mu u1 / a2^2 = bar(a2-slash eps-slash v2) gamma^mu u1 / a2^2
 #pragma unroll
   for (int i = 0; i < 4; ++i) t1[i] = cx<R>{R(0), R(0)};
@@ -147,8 +141,6 @@ __device__ __forceinline__ void qqg_lane_setup(const R (&p)[5][4], const QqgInva
   for (int i = 0; i < 4; ++i) t2[i] = cx<R>{R(0), R(0)};
   slash_acc(R(1), a2, t1, t2);
   dirac_current(t2, u1, L.c2);
-#pragma unroll
-  for (int m = 0; m < 4; ++m) L.c2[m] = inv.ia2 * L.c2[m];
   // E = (J_in.eps)(q + k) + (J_in.(q' - k)) eps - (eps.(q' + q)) J_in
   const cx<R> je = cdotr(L.jin, L.eps), jq = cdotr(L.jin, qpk);
   const R eq = mdot(L.eps, qq2);
@@ -157,6 +149,21 @@ __device__ __forceinline__ void qqg_lane_setup(const R (&p)[5][4], const QqgInva
   // top helicity 2-spinors (mass independent)
   L.wp3 = sqrt(chis(p[2], L.chi3[0], L.chi3[1]));
   L.wp4 = sqrt(chis(p[3], L.chi4[0], L.chi4[1]));
+}
+
+// The event's invariants into the lane: 1/s, 1/s', the top denominators and the
+// light-quark propagator factors of C1, C2.
+template <typename R>
+__device__ __forceinline__ void qqg_lane_scale(const QqgInvariants<R>& inv, QqgLane<R>& L) {
+  L.is = inv.is;
+  L.isp = inv.isp;
+  L.d3 = inv.d3;
+  L.d4 = inv.d4;
+#pragma unroll
+  for (int m = 0; m < 4; ++m) {
+    L.c1[m] = inv.ia1 * L.c1[m];
+    L.c2[m] = inv.ia2 * L.c2[m];
+  }
 }
 
 // The lane's colour-summed |amplitude|^2 summed over the 4 top-helicity pairs at top
@@ -212,9 +219,22 @@ __device__ __forceinline__ R qqg_slot(const QqgLane<R>& L, R mr, R dm2, R mw) {
   return sum;
 }
 
-// The six FP64 invariants of an event: s, s', (p1 - k)^2, (k - p2)^2 and the top
-// denominators at the reference mass m0, (p3 + k)^2 - m0^2, (p4 + k)^2 - m0^2 (FP64
-// because (p1 - k)^2 and the top denominators cancel for collinear or soft gluons).
+// Invariant t of an event (FP64 because (p1 - k)^2 and the top denominators cancel
+// for collinear or soft gluons): t = 0 s, 1 s', 2 (p1 - k)^2, 3 (k - p2)^2,
+// 4 (p3 + k)^2 - m0^2, 5 (p4 + k)^2 - m0^2; p: the event's [5][4] FP64 momenta.
+__device__ __forceinline__ double qqg_invariant_fp64(const double* __restrict__ p, int t, double m0) {
+  // the two momenta and the sign: t -> (a, b, sign) with x = p_a + sign p_b
+  const int a = t == 0 ? 0 : (t == 1 ? 2 : (t == 2 ? 0 : (t == 3 ? 4 : (t == 4 ? 2 : 3))));
+  const int b = t == 0 ? 1 : (t == 1 ? 3 : (t == 2 ? 4 : (t == 3 ? 1 : 4)));
+  const double sg = (t == 2 || t == 3) ? -1.0 : 1.0;
+  double x[4];
+#pragma unroll
+  for (int m = 0; m < 4; ++m) x[m] = p[4 * a + m] + sg * p[4 * b + m];
+  const double v = mdot(x, x);
+  return t >= 4 ? v - m0 * m0 : v;
+}
+
+// All six invariants of an event (reference form; the tile spreads them over its warps).
 __device__ __forceinline__ void qqg_invariants_fp64(const double (&pd)[5][4], double m0, double* v) {
   double q[4], qp[4], a1[4], a2[4], a3[4], a4[4];
 #pragma unroll

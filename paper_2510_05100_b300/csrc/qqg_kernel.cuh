@@ -3,11 +3,13 @@
 //
 // Blocks of 128 threads, 4 lanes per event (light-quark helicity pair x gluon
 // polarisation), 32 events per tile.
-//   a1     each lane loads its event's FP64 momenta (the 4 lanes read the same 160 B)
-//          and forms the six FP64 invariants; in the mixed mode these are the only
-//          FP64 instructions per event (B300 issues FP64 at 1/64 of the FP32 rate):
-//          momenta and invariants are converted on the integer ALUs, reciprocals and
-//          every per-slot quantity (m, m0^2 - m^2, m Gamma from a per-block table) are FP32;
+//   a1     each lane loads its event's FP64 momenta (the 4 lanes read the same 160 B);
+//          the six FP64 invariants of the tile's 32 events are computed once, warp w
+//          taking invariant w (warps 0, 1 also 4, 5) for every event, so no lane
+//          diverges; in the mixed mode these are the only FP64 instructions per
+//          event (B300 issues FP64 at 1/64 of the FP32 rate): momenta and invariants
+//          are converted on the integer ALUs, reciprocals and every per-slot
+//          quantity (m, m0^2 - m^2, m Gamma from a per-block table) are FP32;
 //   a3-a5  the lane builds its parameter-independent currents once
 //          (qqg_lane_setup), then per distinct (m_t, Gamma_t) slot its 4 top-helicity
 //          pairs' 5 amplitudes (qqg_slot);
@@ -38,6 +40,7 @@ struct QqgTile {
     double me2s[EPB][MAX_MASS + 1];
     double inv0[EPB];
     R mr[MAX_MASS], dm2[MAX_MASS], mw[MAX_MASS];   // per slot: m, m0^2 - m^2, m Gamma
+    R inv[6][EPB];                                 // per event: the six invariants (1/x for 0..3)
   };
 
   static __device__ __forceinline__ R to_r(double x) {
@@ -64,6 +67,7 @@ struct QqgTile {
     }
     double pd[5][4];
     R p[5][4];
+    static_assert(EPB == 32 && QQG_BLOCK == 128, "one warp per invariant type over the tile's 32 events");
     const double2* src = reinterpret_cast<const double2*>(mom + evc * 20);
 #pragma unroll
     for (int i = 0; i < 10; ++i) {
@@ -75,18 +79,29 @@ struct QqgTile {
     for (int i = 0; i < 5; ++i)
 #pragma unroll
       for (int m = 0; m < 4; ++m) p[i][m] = to_r(pd[i][m]);
-    double v[6];
-    qqg_invariants_fp64(pd, lp.mass[0], v);
-    QqgInvariants<R> inv;
-    inv.is = R(1) / to_r(v[0]);
-    inv.isp = R(1) / to_r(v[1]);
-    inv.ia1 = R(1) / to_r(v[2]);
-    inv.ia2 = R(1) / to_r(v[3]);
-    inv.d3 = to_r(v[4]);
-    inv.d4 = to_r(v[5]);
+    // the tile's invariants: warp w, lane e -> invariant w (and 4 + w for w < 2) of event e
+    {
+      const int w = tid >> 5, e = tid & 31;
+      const int64_t ei = ev0 + e < nev ? ev0 + e : nev - 1;
+      const double* pe = mom + ei * 20;
+      const double m0 = lp.mass[0];
+      const double v = qqg_invariant_fp64(pe, w, m0);
+      sm.inv[w][e] = R(1) / to_r(v);
+      if (w < 2) sm.inv[4 + w][e] = to_r(qqg_invariant_fp64(pe, 4 + w, m0));
+    }
     QqgLane<R> L;
-    qqg_lane_setup<R>(p, inv, lane & 1, lane >> 1, L);
+    qqg_lane_setup<R>(p, lane & 1, lane >> 1, L);
     __syncthreads();
+    {
+      QqgInvariants<R> inv;
+      inv.is = sm.inv[0][el];
+      inv.isp = sm.inv[1][el];
+      inv.ia1 = sm.inv[2][el];
+      inv.ia2 = sm.inv[3][el];
+      inv.d3 = sm.inv[4][el];
+      inv.d4 = sm.inv[5][el];
+      qqg_lane_scale(inv, L);
+    }
     for (int s = 0; s < lp.nmass; ++s) {
       R part = valid ? qqg_slot<R>(L, sm.mr[s], sm.dm2[s], sm.mw[s]) : R(0);
       part += __shfl_xor_sync(0xffffffffu, part, 1);

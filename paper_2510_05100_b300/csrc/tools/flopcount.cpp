@@ -153,7 +153,8 @@ int main() {
     QqgInvariants<RC> inv{RC(1e-6), RC(1e-6), RC(-1e-4), RC(-1e-4), RC(100.0), RC(120.0)};
     QqgLane<RC> L;
     RC::flops = 0;
-    qqg_lane_setup<RC>(p, inv, 0, 0, L);
+    qqg_lane_setup<RC>(p, 0, 0, L);
+    qqg_lane_scale<RC>(inv, L);
     const long long f_setup = RC::flops;
     RC::flops = 0;
     qqg_slot<RC>(L, RC(171.0), RC(700.0), RC(0.0));
