@@ -67,8 +67,8 @@ TRAFFIC = {
     # ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum of profile_case at 2^19
     # events (FP64, scaled x2 by events) and 2^20 events (mixed); summaries of the
     # captures are under profiles/
-    ("gg_ttxg", "fp64"): {"bytes_per_launch": 2 * (90.465024e6 + 35.403776e6), "source_hash": "61469b75d5115adb"},
-    ("gg_ttxg", "mixed"): {"bytes_per_launch": 176.333312e6 + 101.98784e6, "source_hash": "61469b75d5115adb"},
+    ("gg_ttxg", "fp64"): {"bytes_per_launch": 2 * (91.536384e6 + 35.176192e6), "source_hash": "f6c0fe1786b4abcd"},
+    ("gg_ttxg", "mixed"): {"bytes_per_launch": 176.872704e6 + 102.11328e6, "source_hash": "f6c0fe1786b4abcd"},
 }
 
 
