@@ -202,11 +202,10 @@ typedef struct {
 int rex_multi_create(int precision, rex_multi **out);
 
 /* Execution mode of a multi handle (rex_multi_set_mode; errors: REX_EINVAL):
- * REX_MULTI_PERSISTENT (default): one persistent kernel over every batch's
- *   event tiles, fed by the device work counter; the heaviest process of the
- *   launch selects the kernel's register class (e+e-, g g -> t t~ and
- *   q q~ -> t t~ alone; with g g -> t t~ g or q q~ -> t t~ g; with
- *   g g -> t t~ g g), so light
+ * REX_MULTI_PERSISTENT (default): persistent kernels over the batches' event
+ *   tiles, fed by the device work counter, one per register class present
+ *   (e+e-, g g -> t t~ and q q~ -> t t~; g g -> t t~ g and q q~ -> t t~ g;
+ *   g g -> t t~ g g), heaviest first, back to back on the stream, so light
  *   batches keep the occupancy of their own kernels;
  * REX_MULTI_STREAMS: each batch's own tuned single-process kernel on a
  *   stream forked from (and joined back into) the caller's stream. */
@@ -216,7 +215,8 @@ int rex_multi_set_mode(rex_multi *m, int mode);
 
 /* Reweight every batch to the same k points (host array, copied).  Each
  * batch's original point is its handle's.  Enqueues a counter reset and one
- * kernel per 64 points on stream; allocates nothing, so it can be captured.
+ * kernel per 64 points and register class present on stream; allocates
+ * nothing, so it can be captured.
  * At most one ee_mumu batch.  Errors: REX_EINVAL, REX_ENOTINIT, REX_ECUDA. */
 int rex_reweight_multi(rex_multi *m, const rex_batch *batches, int nbatch,
                        const rex_params *param_sets, int k, void *stream);

@@ -22,8 +22,8 @@ namespace rex {
 static_assert(QQ_BLOCK == QCD_BLOCK && QQG_BLOCK == QCD_BLOCK, "every tile runs on the multi kernel's block size");
 
 // Register classes: the persistent kernel is compiled once per class with only
-// the tiles the class admits, so its register budget (and occupancy) follows the
-// heaviest process actually present in the launch:
+// the tiles the class admits, and a multi-process call launches one kernel per
+// class present, so each process runs at the occupancy its class allows:
 //   class 0: e+e- -> mu+mu-, g g -> t t~, q q~ -> t t~
 //   class 1: class 0, g g -> t t~ g and q q~ -> t t~ g
 //   class 2: every process (g g -> t t~ g g sets the budget)

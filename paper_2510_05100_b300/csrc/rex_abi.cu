@@ -373,42 +373,46 @@ int multi_impl(rex_multi* m, const rex_batch* batches, int nbatch, const rex_par
       if (tile_cost[order[j]] > tile_cost[order[i]]) std::swap(order[i], order[j]);
   const int mixed = m->precision == REX_MIXED;
   static thread_local MultiLaunch ml;   // ~20 KB: kept off the stack
+  // one persistent launch per register class present, heaviest class first, back to
+  // back on the stream (one graph when captured): each class runs at the occupancy
+  // its own tiles allow instead of the heaviest process's
   for (int j0 = 0; j0 < k; j0 += MULTI_MAX_POINTS) {
     const int j1 = (k - j0) < MULTI_MAX_POINTS ? k : j0 + MULTI_MAX_POINTS;
-    std::memset(&ml, 0, sizeof ml);
-    int64_t total = 0;
-    int nb = 0, width = 0, cls = 0;
-    for (int oi = 0; oi < nbatch; ++oi) {
-      const rex_batch& b = batches[order[oi]];
-      if (b.nev == 0) continue;
-      MultiBatch& B = ml.b[nb++];
-      B.kind = b.proc->kind;
-      cls = std::max(cls, multi_class_of(B.kind));
-      B.nev = b.nev;
-      B.mom = b.momenta;
-      B.w_in = b.w_in;
-      B.out = b.w_out + j0;
-      const int epb = multi_events_per_tile(B.kind, mixed);
-      B.tile_begin = total;
-      total += (b.nev + epb - 1) / epb;
-      B.tile_end = total;
-      if (B.kind == PROC_EE_MUMU) {
-        ml.ew.k = j1 - j0;
-        ml.ew.mode = OUT_RATIO;
-        ml.ew.out_stride = k;
-        ml.ew.pt[0] = ew_point(b.proc->orig);
-        for (int j = j0; j < j1; ++j) ml.ew.pt[1 + j - j0] = ew_point(pts[j]);
-      } else {
-        fill_multi_table(b.proc, pts, j0, j1, k, B.t);
-        if (B.t.has_width) width = 1;
+    for (int cls = MULTI_NCLASS - 1; cls >= 0; --cls) {
+      std::memset(&ml, 0, sizeof ml);
+      int64_t total = 0;
+      int nb = 0, width = 0;
+      for (int oi = 0; oi < nbatch; ++oi) {
+        const rex_batch& b = batches[order[oi]];
+        if (b.nev == 0 || multi_class_of(b.proc->kind) != cls) continue;
+        MultiBatch& B = ml.b[nb++];
+        B.kind = b.proc->kind;
+        B.nev = b.nev;
+        B.mom = b.momenta;
+        B.w_in = b.w_in;
+        B.out = b.w_out + j0;
+        const int epb = multi_events_per_tile(B.kind, mixed);
+        B.tile_begin = total;
+        total += (b.nev + epb - 1) / epb;
+        B.tile_end = total;
+        if (B.kind == PROC_EE_MUMU) {
+          ml.ew.k = j1 - j0;
+          ml.ew.mode = OUT_RATIO;
+          ml.ew.out_stride = k;
+          ml.ew.pt[0] = ew_point(b.proc->orig);
+          for (int j = j0; j < j1; ++j) ml.ew.pt[1 + j - j0] = ew_point(pts[j]);
+        } else {
+          fill_multi_table(b.proc, pts, j0, j1, k, B.t);
+          if (B.t.has_width) width = 1;
+        }
       }
+      if (nb == 0) continue;
+      ml.nbatch = nb;
+      ml.total = total;
+      const int64_t grid = total < m->blocks[cls][width] ? total : m->blocks[cls][width];
+      const int err = launch_multi(mixed, width, cls, (int)grid, ml, m->counter, stream);
+      if (err != 0) return cuda_fail(err, "multi kernel launch");
     }
-    if (nb == 0) return REX_OK;
-    ml.nbatch = nb;
-    ml.total = total;
-    const int64_t grid = total < m->blocks[cls][width] ? total : m->blocks[cls][width];
-    const int err = launch_multi(mixed, width, cls, (int)grid, ml, m->counter, stream);
-    if (err != 0) return cuda_fail(err, "multi kernel launch");
   }
   return REX_OK;
 }
@@ -514,7 +518,7 @@ int rex_multi_replay(rex_multi* m, void* stream) {
 // Scratch of rex_reweight_multi_noalloc: the persistent kernel's 64-bit work
 // counter, held in this fixed device array instead of a handle's cudaMalloc'd
 // buffer.  Every GPU that loads the library holds these 256 bytes until exit.
-constexpr int NOALLOC_COUNTERS = 1;   // one launch per call
+constexpr int NOALLOC_COUNTERS = 1;   // one 64-point chunk per call; its per-class launches reuse it in stream order
 static __device__ __align__(256) unsigned long long g_noalloc_counter[NOALLOC_COUNTERS];
 
 namespace {
