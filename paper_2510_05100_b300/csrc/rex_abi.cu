@@ -373,9 +373,15 @@ int multi_impl(rex_multi* m, const rex_batch* batches, int nbatch, const rex_par
       if (tile_cost[order[j]] > tile_cost[order[i]]) std::swap(order[i], order[j]);
   const int mixed = m->precision == REX_MIXED;
   static thread_local MultiLaunch ml;   // ~20 KB: kept off the stack
-  // one persistent launch per register class present, heaviest class first, back to
-  // back on the stream (one graph when captured): each class runs at the occupancy
-  // its own tiles allow instead of the heaviest process's
+  bool forked = false;
+  // one persistent launch per register class present, heaviest class first (one graph
+  // when captured): each class runs at the occupancy its own tiles allow instead of
+  // the heaviest process's.  With side streams (a multi handle) the classes run on
+  // streams forked from the caller's, each with its own work counter, so a lighter
+  // class fills the SMs the heavier one's blocks leave at its tail; without them
+  // (the allocation-free entry point) they run back to back on one counter.
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const bool fork = m->side[0] != nullptr;
   for (int j0 = 0; j0 < k; j0 += MULTI_MAX_POINTS) {
     const int j1 = (k - j0) < MULTI_MAX_POINTS ? k : j0 + MULTI_MAX_POINTS;
     for (int cls = MULTI_NCLASS - 1; cls >= 0; --cls) {
@@ -410,9 +416,29 @@ int multi_impl(rex_multi* m, const rex_batch* batches, int nbatch, const rex_par
       ml.nbatch = nb;
       ml.total = total;
       const int64_t grid = total < m->blocks[cls][width] ? total : m->blocks[cls][width];
-      const int err = launch_multi(mixed, width, cls, (int)grid, ml, m->counter, stream);
+      void* ls = stream;
+      unsigned long long* counter = m->counter;
+      if (fork) {
+        cudaError_t e = cudaSuccess;
+        if (!forked) {
+          e = cudaEventRecord(m->fork, st);
+          forked = true;
+        }
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(m->side[cls], m->fork, 0);
+        if (e != cudaSuccess) return cuda_fail((int)e, "fork");
+        ls = m->side[cls];
+        counter = m->counter + cls;
+      }
+      const int err = launch_multi(mixed, width, cls, (int)grid, ml, counter, ls);
       if (err != 0) return cuda_fail(err, "multi kernel launch");
+      if (fork) {
+        cudaError_t e = cudaEventRecord(m->join[cls], m->side[cls]);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(st, m->join[cls], 0);
+        if (e != cudaSuccess) return cuda_fail((int)e, "join");
+      }
     }
+    // the next 64-point chunk re-forks after this one's joins
+    forked = false;
   }
   return REX_OK;
 }
