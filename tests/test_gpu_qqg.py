@@ -113,3 +113,20 @@ def test_in_the_persistent_multi_kernel(rex):
     for b, ref in zip(batches, single):
         assert np.max(rel(b[3].cpu().numpy(), ref)) < 1e-13
     m.close()
+
+
+@pytest.mark.parametrize("proc", ["qq_ttx", "qq_ttxg"])
+def test_point_lists_longer_than_one_launch(rex, proc):
+    """300 points with 100 distinct top masses: the entry point splits them into launches
+    of at most 256 points and 64 mass slots; every column against the oracle."""
+    n = 12
+    mom = ps.make_events(proc, n, 77)
+    w = np.random.default_rng(8).uniform(0.5, 2.0, n)
+    masses = np.linspace(168.0, 178.0, 100)
+    pts = [dict(mt=float(masses[j % 100]), wt=0.0, alphas=0.110 + 0.0001 * j) for j in range(300)]
+    p = rex.Process(proc, 0)
+    p.set_params(ORIG)
+    got = p.reweight(dev(mom), dev(w), pts).cpu().numpy()
+    cols = list(range(0, 300, 7)) + [255, 256, 299]
+    ref = oracle_rw.reweight(proc, mom, w, ORIG, [pts[j] for j in cols])
+    assert np.max(rel(got[:, cols], ref)) < FP64_TOL
