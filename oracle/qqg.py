@@ -130,6 +130,22 @@ def me2(p: np.ndarray, mt: float, wt: float, alphas: float) -> np.ndarray:
     return total / 36.0
 
 
+def me2_helicity(p: np.ndarray, mt: float, wt: float, alphas: float, hel: np.ndarray) -> np.ndarray:
+    """The term of the helicity sum (me2 = sum over configurations, same 1/36) of each
+    event's own configuration hel[N, 5] = (l1, l2, l3, l4, lg): helicities of q, q~, t,
+    t~ and the gluon in the frame of the momenta."""
+    p = np.asarray(p, dtype=np.float64)
+    hel = np.asarray(hel)
+    gm = colour_matrix()
+    out = np.zeros(p.shape[0])
+    for conf in itertools.product((-1, 1), repeat=5):
+        sel = np.all(hel == np.array(conf), axis=1)
+        if np.any(sel):
+            a = amplitudes(p[sel], mt, wt, alphas, conf)
+            out[sel] = np.real(np.einsum("ns,st,nt->n", a.conj(), gm, a)) / 36.0
+    return out
+
+
 def colour_amplitude(p: np.ndarray, mt: float, hel: tuple, eps_override=None, alphas: float = 0.118) -> np.ndarray:
     """sum_d K_d A_d: the colour-dressed amplitude [N, 8, 3, 3, 3, 3] of one configuration."""
     a = amplitudes(p, mt, 0.0, alphas, hel, eps_override)

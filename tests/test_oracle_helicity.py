@@ -85,3 +85,21 @@ def test_vanishing_configurations_are_exact_zeros(proc):
     assert np.all(terms[:, forbidden] == 0.0)
     rel = terms[:, ~forbidden] / reweight.me2(proc, p, orig)[:, None]
     assert np.min(rel) > 1e6 * reweight.ZERO_TERM
+
+
+def test_qq_ttxg_terms_sum_to_the_helicity_sum_and_zeros():
+    """q q~ -> t t~ g: the 32 configuration terms add up to the helicity sum, the
+    configurations with equal light-quark helicities are exact zeros after the residue
+    cut, and QCD's parity maps each term to its mirror."""
+    from oracle import qqg
+    p = ps.make_events("qq_ttxg", 6, 106)
+    orig = dict(mt=173.0, wt=0.0, alphas=0.118)
+    confs = np.array(list(itertools.product((-1, 1), repeat=5)))
+    idx = np.repeat(np.arange(6), 32)
+    hel = np.tile(confs, (6, 1))
+    terms = reweight.me2_helicity("qq_ttxg", p[idx], orig, hel).reshape(6, 32)
+    assert np.max(np.abs(terms.sum(axis=1) / qqg.me2(p, 173.0, 0.0, 0.118) - 1.0)) < 1e-13
+    forbidden = confs[:, 0] == confs[:, 1]
+    assert np.all(terms[:, forbidden] == 0.0) and np.all(terms[:, ~forbidden] > 0.0)
+    mirror = reweight.me2_helicity("qq_ttxg", p[idx], orig, -hel).reshape(6, 32)
+    assert np.max(np.abs(mirror - terms)) < 1e-12 * np.max(terms)
