@@ -137,8 +137,9 @@ int rex_reweight(rex_proc *proc, const double *momenta, const double *w_in,
  *               helicities in the frame of the momenta, +1 / -1 (a positive value
  *               reads as +1, any other as -1); no alignment requirement
  *   other arguments as rex_reweight.
- * Processes: ee_mumu and qq_ttx, whose kernels evaluate helicity amplitudes; the
- * g g processes sum real linear gluon polarisations and return REX_EUNSUPPORTED.
+ * Processes: ee_mumu, qq_ttx and qq_ttxg, whose kernels evaluate helicity
+ * amplitudes (the q q~ -> t t~ g gluon in the helicity basis); the g g processes
+ * sum real linear gluon polarisations and return REX_EUNSUPPORTED.
  * Enqueue only.  Errors: REX_EUNSUPPORTED, REX_EINVAL (as rex_reweight, null
  * helicities), REX_ENOTINIT, REX_ECUDA. */
 int rex_reweight_helicity(rex_proc *proc, const double *momenta, const signed char *helicities,

@@ -219,6 +219,122 @@ __device__ __forceinline__ R qqg_slot(const QqgLane<R>& L, R mr, R dm2, R mw) {
   return sum;
 }
 
+// ---- helicity-exclusive form: the event's own configuration (l1, l2, l3, l4, lg) ----
+// The gluon in the helicity basis, eps*(lg) = -(lg e_theta - i e_phi) / sqrt(2), with
+// e_theta, e_phi the two linear polarisations of pol_linear; the light-line and
+// top-line chains as above with a complex polarisation, and C2's adjoint taken with
+// conj(eps) (vbar eps-slash b-slash = bar(b-slash conj(eps)-slash v)).
+template <typename R>
+struct QqgLaneH {
+  cx<R> jin[4], c1[4], c2[4], e[4], eps[4];
+  R a3[4], a4[4];
+  cx<R> chi3[2][2], chi4[2][2];
+  R wp3, wp4;
+  R is, isp, d3, d4;
+  int i3, i4;      // top spinor index: 1 for helicity +, 0 for -
+  bool zero;       // equal light-quark helicities: the configuration vanishes
+};
+
+template <typename R>
+__device__ __forceinline__ void qqg_lane_setup_h(const R (&p)[5][4], const signed char* hel, QqgLaneH<R>& L) {
+  const int l1 = hel[0] > 0 ? 1 : -1, l2 = hel[1] > 0 ? 1 : -1, lg = hel[4] > 0 ? 1 : -1;
+  L.i3 = hel[2] > 0 ? 1 : 0;
+  L.i4 = hel[3] > 0 ? 1 : 0;
+  L.zero = l1 == l2;
+  cx<R> u1[4], v2[4];
+  spinor_u(p[0], R(0), l1, u1);
+  spinor_v(p[1], R(0), l2, v2);
+  R e1[4], e2[4];
+  pol_linear(p[4], 0, e1);
+  pol_linear(p[4], 1, e2);
+  const R r = R(0.70710678118654752440);
+  cx<R> epsc[4];
+#pragma unroll
+  for (int m = 0; m < 4; ++m) {
+    L.eps[m] = cx<R>{-R(lg) * e1[m] * r, e2[m] * r};
+    epsc[m] = cx<R>{L.eps[m].re, -L.eps[m].im};
+  }
+  dirac_current(v2, u1, L.jin);
+  R a1[4], a2[4], qk[4], qpk[4], qq2[4];
+#pragma unroll
+  for (int m = 0; m < 4; ++m) {
+    a1[m] = p[0][m] - p[4][m];
+    a2[m] = p[4][m] - p[1][m];
+    L.a3[m] = p[2][m] + p[4][m];
+    L.a4[m] = -p[3][m] - p[4][m];
+    const R q = p[0][m] + p[1][m], qp = p[2][m] + p[3][m];
+    qk[m] = q + p[4][m];
+    qpk[m] = qp - p[4][m];
+    qq2[m] = qp + q;
+  }
+  cx<R> t1[4], t2[4];
+  cslash(L.eps, u1, t1);                       // C1 = vbar2 gamma^mu a1-slash eps-slash u1
+#pragma unroll
+  for (int i = 0; i < 4; ++i) t2[i] = cx<R>{R(0), R(0)};
+  slash_acc(R(1), a1, t1, t2);
+  dirac_current(v2, t2, L.c1);
+  cslash(epsc, v2, t1);                        // C2 = bar(a2-slash conj(eps)-slash v2) gamma^mu u1
+#pragma unroll
+  for (int i = 0; i < 4; ++i) t2[i] = cx<R>{R(0), R(0)};
+  slash_acc(R(1), a2, t1, t2);
+  dirac_current(t2, u1, L.c2);
+  const cx<R> je = cdotm(L.jin, L.eps), jq = cdotr(L.jin, qpk), eq = cdotr(L.eps, qq2);
+#pragma unroll
+  for (int m = 0; m < 4; ++m) L.e[m] = qk[m] * je + L.eps[m] * jq - eq * L.jin[m];
+  L.wp3 = sqrt(chis(p[2], L.chi3[0], L.chi3[1]));
+  L.wp4 = sqrt(chis(p[3], L.chi4[0], L.chi4[1]));
+}
+
+template <typename R>
+__device__ __forceinline__ void qqg_lane_scale_h(const QqgInvariants<R>& inv, QqgLaneH<R>& L) {
+  L.is = inv.is;
+  L.isp = inv.isp;
+  L.d3 = inv.d3;
+  L.d4 = inv.d4;
+#pragma unroll
+  for (int m = 0; m < 4; ++m) {
+    L.c1[m] = inv.ia1 * L.c1[m];
+    L.c2[m] = inv.ia2 * L.c2[m];
+  }
+}
+
+// The colour-summed |amplitude|^2 of the lane's one configuration at top mass mr.
+template <typename R>
+__device__ __forceinline__ R qqg_slot_h(const QqgLaneH<R>& L, R mr, R dm2, R mw) {
+  if (L.zero) return R(0);
+  cx<R> u3[2][4], v4[2][4];
+  spinor_u_from(L.chi3, L.wp3, mr / L.wp3, u3);
+  spinor_v_from(L.chi4, L.wp4, mr / L.wp4, v4);
+  const cx<R>* u = u3[L.i3];
+  const cx<R>* v = v4[L.i4];
+  const R d3 = L.d3 + dm2, d4 = L.d4 + dm2;
+  const R n3 = R(1) / (d3 * d3 + mw * mw), n4 = R(1) / (d4 * d4 + mw * mw);
+  const cx<R> f3 = L.is * cx<R>{d3 * n3, -mw * n3}, f4 = L.is * cx<R>{d4 * n4, -mw * n4};
+  cx<R> t1[4], t2[4], t3[4], s1[4], s2[4], s3[4], jout[4];
+  cslash(L.jin, v, t1);                        // eps-slash (a3-slash + m) J_in-slash v4
+  slash_plus_scalar(L.a3, mr, t1, t2);
+  cslash(L.eps, t2, t3);
+  cslash(L.eps, v, s1);                        // J_in-slash (a4-slash + m) eps-slash v4
+  slash_plus_scalar(L.a4, mr, s1, s2);
+  cslash(L.jin, s2, s3);
+  dirac_current(u, v, jout);
+  cx<R> a[5];
+  a[0] = L.isp * cdotm(L.c1, jout);
+  a[1] = L.isp * cdotm(L.c2, jout);
+  a[2] = f3 * ubar_dot(u, t3);
+  a[3] = f4 * ubar_dot(u, s3);
+  a[4] = (L.is * L.isp) * cdotm(L.e, jout);
+  R form = R(0);
+#pragma unroll
+  for (int d = 0; d < 5; ++d) {
+    form += R(qqg_colour(d, d)) * (a[d].re * a[d].re + a[d].im * a[d].im);
+#pragma unroll
+    for (int d2 = d + 1; d2 < 5; ++d2)
+      form += R(2 * qqg_colour(d, d2)) * (a[d].re * a[d2].re + a[d].im * a[d2].im);
+  }
+  return form;
+}
+
 // Invariant t of an event (FP64 because (p1 - k)^2 and the top denominators cancel
 // for collinear or soft gluons): t = 0 s, 1 s', 2 (p1 - k)^2, 3 (k - p2)^2,
 // 4 (p3 + k)^2 - m0^2, 5 (p4 + k)^2 - m0^2; p: the event's [5][4] FP64 momenta.

@@ -48,10 +48,13 @@ struct QqgTile {
     else return x;
   }
 
-  template <class TABLE>
+  // EXCL: helicity-exclusive, hel[ev][0..4] = the event's (l1, l2, l3, l4, lg); the
+  // event's one configuration is evaluated by each of its 4 lanes for every 4th slot
+  template <bool EXCL = false, class TABLE>
   static __device__ __forceinline__ void run(Smem& sm, const double* __restrict__ mom,
                                              const double* __restrict__ w_in, int64_t nev, int64_t tile,
-                                             const TABLE& lp, double* __restrict__ out) {
+                                             const TABLE& lp, double* __restrict__ out,
+                                             const signed char* __restrict__ hel = nullptr) {
     const int tid = threadIdx.x;
     const int el = tid / QQG_LANES, lane = tid % QQG_LANES;
     const int64_t ev0 = tile * EPB;
@@ -89,10 +92,24 @@ struct QqgTile {
       sm.inv[w][e] = R(1) / to_r(v);
       if (w < 2) sm.inv[4 + w][e] = to_r(qqg_invariant_fp64(pe, 4 + w, m0));
     }
-    QqgLane<R> L;
-    qqg_lane_setup<R>(p, lane & 1, lane >> 1, L);
-    __syncthreads();
-    {
+    if constexpr (EXCL) {
+      QqgLaneH<R> L;
+      qqg_lane_setup_h<R>(p, hel + evc * 5, L);
+      __syncthreads();
+      QqgInvariants<R> inv;
+      inv.is = sm.inv[0][el];
+      inv.isp = sm.inv[1][el];
+      inv.ia1 = sm.inv[2][el];
+      inv.ia2 = sm.inv[3][el];
+      inv.d3 = sm.inv[4][el];
+      inv.d4 = sm.inv[5][el];
+      qqg_lane_scale_h(inv, L);
+      for (int s = lane; s < lp.nmass; s += QQG_LANES)
+        sm.me2s[el][s] = valid ? double(qqg_slot_h<R>(L, sm.mr[s], sm.dm2[s], sm.mw[s])) : 0.0;
+    } else {
+      QqgLane<R> L;
+      qqg_lane_setup<R>(p, lane & 1, lane >> 1, L);
+      __syncthreads();
       QqgInvariants<R> inv;
       inv.is = sm.inv[0][el];
       inv.isp = sm.inv[1][el];
@@ -101,12 +118,12 @@ struct QqgTile {
       inv.d3 = sm.inv[4][el];
       inv.d4 = sm.inv[5][el];
       qqg_lane_scale(inv, L);
-    }
-    for (int s = 0; s < lp.nmass; ++s) {
-      R part = valid ? qqg_slot<R>(L, sm.mr[s], sm.dm2[s], sm.mw[s]) : R(0);
-      part += __shfl_xor_sync(0xffffffffu, part, 1);
-      part += __shfl_xor_sync(0xffffffffu, part, 2);
-      if (lane == 0) sm.me2s[el][s] = double(part);
+      for (int s = 0; s < lp.nmass; ++s) {
+        R part = valid ? qqg_slot<R>(L, sm.mr[s], sm.dm2[s], sm.mw[s]) : R(0);
+        part += __shfl_xor_sync(0xffffffffu, part, 1);
+        part += __shfl_xor_sync(0xffffffffu, part, 2);
+        if (lane == 0) sm.me2s[el][s] = double(part);
+      }
     }
     __syncthreads();
     const int nblk = (int)((nev - ev0) < EPB ? (nev - ev0) : EPB);

@@ -101,7 +101,7 @@ int launch_qcd(const rex_proc* p, const double* mom, const double* w_in, int64_t
     case PROC_GG_TTXG: return launch_gg_ttxg(mixed, p->variant, mom, w_in, nev, lp, out, stream);
     case PROC_GG_TTXGG: return launch_gg_ttxgg(mixed, p->variant, mom, w_in, nev, lp, out, stream);
     case PROC_QQ_TTX: return launch_qq_ttx(mixed, mom, w_in, nev, lp, out, stream, hel);
-    case PROC_QQ_TTXG: return launch_qq_ttxg(mixed, mom, w_in, nev, lp, out, stream);
+    case PROC_QQ_TTXG: return launch_qq_ttxg(mixed, mom, w_in, nev, lp, out, stream, hel);
     default: return (int)cudaErrorInvalidValue;
   }
 }
@@ -680,10 +680,10 @@ int rex_reweight_helicity(rex_proc* proc, const double* momenta, const signed ch
                           void* stream) {
   const int rc = validate_proc(proc);
   if (rc) return rc;
-  if (proc->kind != PROC_EE_MUMU && proc->kind != PROC_QQ_TTX)
+  if (proc->kind != PROC_EE_MUMU && proc->kind != PROC_QQ_TTX && proc->kind != PROC_QQ_TTXG)
     return fail(REX_EUNSUPPORTED,
-                "helicity-exclusive reweighting needs helicity-basis amplitudes: ee_mumu and qq_ttx have them, "
-                "'%s' sums linear gluon polarisations",
+                "helicity-exclusive reweighting needs helicity-basis amplitudes: ee_mumu, qq_ttx and qq_ttxg "
+                "have them, '%s' sums linear gluon polarisations",
                 info_of(proc->kind).name);
   if (nev > 0 && k > 0 && !helicities) return fail(REX_EINVAL, "null helicity array");
   return reweight_impl(proc, momenta, w_in, nev, param_sets, k, w_out, stream, helicities);

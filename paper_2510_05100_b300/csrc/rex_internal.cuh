@@ -113,7 +113,7 @@ int launch_gg_ttxgg(int mixed, int variant, const double* mom, const double* w_i
 int launch_qq_ttx(int mixed, const double* mom, const double* w_in, int64_t nev, const QcdLaunch& lp,
                   double* out, void* stream, const signed char* hel);
 int launch_qq_ttxg(int mixed, const double* mom, const double* w_in, int64_t nev, const QcdLaunch& lp,
-                   double* out, void* stream);
+                   double* out, void* stream, const signed char* hel);
 int launch_ee(const double* mom, const double* w_in, int64_t nev, const EwLaunch& lp,
               double* out, void* stream, const signed char* hel);
 

@@ -86,3 +86,24 @@ def test_unsupported_processes_raise(rex):
     mom = dev(ps.make_events("gg_ttx", 4, 1))
     with pytest.raises(rex.RexError):
         p.reweight_helicity(mom, dev(np.ones((4, 4), dtype=np.int8)), dev(np.ones(4)), [QCD_ORIG])
+
+
+@pytest.mark.parametrize("precision,tol", [(0, 1e-12), (1, 1e-4)])
+def test_qq_ttxg_exclusive_parity(rex, precision, tol):
+    """q q~ -> t t~ g, each event with a random configuration of its 5 helicities (the
+    gluon's in the helicity basis), against the oracle's per-configuration terms."""
+    n = 150
+    mom = ps.make_events("qq_ttxg", n, 63)
+    hel = np.random.default_rng(63).choice(np.array([-1, 1], dtype=np.int8), size=(n, 5))
+    w = np.random.default_rng(64).uniform(0.5, 2.0, n)
+    pts = ps.grid_gg_ttxg()[::3] + [QCD_ORIG, dict(mt=172.0, wt=1.2, alphas=0.121)]
+    p = rex.Process("qq_ttxg", precision)
+    p.set_params(QCD_ORIG)
+    got = p.reweight_helicity(dev(mom), dev(hel), dev(w), pts).cpu().numpy()
+    ref = oracle_rw.reweight_helicity("qq_ttxg", mom, hel, w, QCD_ORIG, pts)
+    zero = ref[:, 0] == 0.0
+    assert np.any(zero) and np.all(got[zero] == 0.0)
+    eps = np.finfo(np.float64 if precision == 0 else np.float32).eps / 2
+    bound = helicity_tolerance("qq_ttxg", mom, hel, QCD_ORIG, pts, tol, eps)
+    err = np.abs(got - ref) / np.where(ref != 0.0, np.abs(ref), 1.0)
+    assert np.all(err[~zero] < bound[~zero])
