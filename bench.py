@@ -355,18 +355,19 @@ def run_qqg_leg(dev, stream, pts, steps, nev=NEV):
     return out
 
 
-# a two-channel p p -> t t~ sample: g g and q q~ initial states, 7 : 1, 2^20 events
+# two-channel p p -> t t~ (+ jet) samples: g g and q q~ initial states, 7 : 1, 2^20 events
 PP_TTX_BATCHES = (("gg_ttx", 917504, 11), ("qq_ttx", 131072, 12))
+PP_TTXJ_BATCHES = (("gg_ttxg", 917504, 13), ("qq_ttxg", 131072, 14))
 
 
-def run_pp_ttx_leg(dev, stream, pts, steps, world, barrier, max_over_ranks):
-    """The p p -> t t~ channels (g g -> t t~ and q q~ -> t t~ batches of one sample)
-    reweighted to the headline's points: one graph-captured persistent multi-process
-    launch against one launch per channel, in FP64 and in mixed precision."""
+def run_pp_ttx_leg(dev, stream, pts, steps, world, barrier, max_over_ranks, spec=PP_TTX_BATCHES):
+    """The p p -> t t~ (+ jet) channels (g g and q q~ batches of one sample) reweighted to
+    the headline's points: one graph-captured persistent multi-process launch against one
+    launch per channel, in FP64 and in mixed precision."""
     import torch
     from paper_2510_05100_b300 import rex
 
-    units = sum(n for _, n, _ in PP_TTX_BATCHES) * len(pts)
+    units = sum(n for _, n, _ in spec) * len(pts)
 
     def timed(fn):
         for _ in range(2):
@@ -383,11 +384,11 @@ def run_pp_ttx_leg(dev, stream, pts, steps, world, barrier, max_over_ranks):
         barrier()
         return max_over_ranks(t0.elapsed_time(t1)) / steps
 
-    out = {"workload": "p p -> t t~ sample of 2^20 events: 917504 g g -> t t~ + 131072 q q~ -> t t~, "
-                       f"{len(pts)} points", "unit": UNIT, "steps": steps}
+    desc = " + ".join(f"{n} {proc}" for proc, n, _ in spec)
+    out = {"workload": f"two-channel sample of 2^20 events: {desc}, {len(pts)} points", "unit": UNIT, "steps": steps}
     for name, prec in (("fp64", rex.FP64), ("mixed", rex.MIXED)):
         batches = []
-        for proc, n, seed in PP_TTX_BATCHES:
+        for proc, n, seed in spec:
             h = rex.Process(proc, prec)
             h.set_params(ORIGINAL)
             mom = torch.from_numpy(ps.make_events(proc, n, seed)).to(dev)
@@ -772,6 +773,8 @@ def run_ours(args, world, rank, local):
     qqg_leg = None if args.no_qq else run_qqg_leg(dev, stream, pts, max(3, args.steps // 4))
     pp_leg = None if args.no_qq else run_pp_ttx_leg(dev, stream, pts, max(3, args.steps // 4), world, barrier,
                                                      max_over_ranks)
+    ppj_leg = None if args.no_qq else run_pp_ttx_leg(dev, stream, pts, 3, world, barrier, max_over_ranks,
+                                                      spec=PP_TTXJ_BATCHES)
 
     multi = None if args.no_multi else run_multi_leg(dev, stream, max(3, args.steps // 2), world, barrier,
                                                      max_over_ranks)
@@ -802,7 +805,7 @@ def run_ours(args, world, rank, local):
                         "entry_point": "rex_reweight_host (pinned host buffers)"},
                 "gpu_launches": args.steps, "roofline": roofline, "cpu_baseline": cpu, "modes": extra,
                 "multi": multi, "surrogate": surrogate, "xsec": xsec, "lhe": lhe_leg, "qq_ttx": qq_leg,
-                "qq_ttxg": qqg_leg, "pp_ttx": pp_leg}
+                "qq_ttxg": qqg_leg, "pp_ttx": pp_leg, "pp_ttxj": ppj_leg}
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist
