@@ -104,7 +104,8 @@ struct QcdTile {
 
   struct Smem {
     double me2s[EPB][MAX_MASS + 1];
-    double inv0[EPB];   // mixed mode: 1 / |M_0|^2 per event (0 if |M_0|^2 == 0)
+    double mult[MAX_POINTS];   // mixed mode: per point, f_j / f_0 (slot 0) or f_j
+    int slotj[MAX_POINTS];     // mixed mode: per point, its mass slot
     typename P::template event<R> evs[EPB];
     typename P::template mass<R> mss[EPB];
     alignas(16) __half tc[TC ? QCD_BLOCK / 32 : 1][TC ? ColourTc<NF>::WARP_HALVES : 1];
@@ -181,20 +182,35 @@ struct QcdTile {
           out[(ev0 + e) * lp.out_stride + j] = (m0 == 0.0) ? 0.0 : w * (mj / m0);
         }
       } else {
-        // mixed mode: one FP64 reciprocal per event instead of a division per point;
-        // a point whose |M|^2 equals the original's keeps its weight exactly
+        // mixed mode (B300 issues FP64 at 1/64 of the FP32 rate): per event the slot
+        // sums become w |M_s|^2 / |M_0|^2 with one division, slot 0 holds w itself (0
+        // if |M_0|^2 == 0, NaN if it is NaN), and each output is one FP64 product with
+        // the point's multiplier, f_j / f_0 on the original slot (an unchanged point
+        // keeps its weight exactly) and f_j elsewhere
+        for (int j = tid; j < k; j += QCD_BLOCK) {
+          sm.slotj[j] = lp.slot[j];
+          sm.mult[j] = lp.slot[j] == 0 ? lp.factor[j] / lp.factor0 : lp.factor[j];
+        }
         for (int e = tid; e < nblk; e += QCD_BLOCK) {
           const double m0 = sm.me2s[e][0] * lp.factor0;
-          sm.inv0[e] = m0 == 0.0 ? 0.0 : 1.0 / m0;
+          const double w = w_in[ev0 + e];
+          const double wi = m0 == 0.0 ? 0.0 : w / m0;
+          for (int sl = 1; sl < lp.nmass; ++sl) sm.me2s[e][sl] *= wi;
+          sm.me2s[e][0] = m0 == 0.0 ? 0.0 : (m0 == m0 ? w : m0);
         }
         __syncthreads();
+        // output idx = e * k + j; (e, j) advance without an integer division per output
+        const int kk = k > 0 ? k : 1;
+        int e = tid / kk, j = tid - (tid / kk) * kk;
+        const int de = QCD_BLOCK / kk, dj = QCD_BLOCK - (QCD_BLOCK / kk) * kk;
         for (int idx = tid; idx < nblk * k; idx += QCD_BLOCK) {
-          const int e = idx / k;
-          const int j = idx - e * k;
-          const double m0 = sm.me2s[e][0] * lp.factor0;
-          const double mj = sm.me2s[e][lp.slot[j]] * lp.factor[j];
-          const double w = w_in[ev0 + e];
-          out[(ev0 + e) * lp.out_stride + j] = (m0 == 0.0) ? 0.0 : (mj == m0 ? w : w * (mj * sm.inv0[e]));
+          out[(ev0 + e) * lp.out_stride + j] = sm.me2s[e][sm.slotj[j]] * sm.mult[j];
+          e += de;
+          j += dj;
+          if (j >= k) {
+            j -= k;
+            ++e;
+          }
         }
       }
     } else {
