@@ -38,7 +38,8 @@ struct QqgTile {
 
   struct Smem {
     double me2s[EPB][MAX_MASS + 1];
-    double inv0[EPB];
+    double mult[MAX_POINTS];   // mixed mode: per point, f_j / f_0 (slot 0) or f_j
+    int slotj[MAX_POINTS];     // mixed mode: per point, its mass slot
     R mr[MAX_MASS], dm2[MAX_MASS], mw[MAX_MASS];   // per slot: m, m0^2 - m^2, m Gamma
     R inv[6][EPB];                                 // per event: the six invariants (1/x for 0..3)
   };
@@ -139,18 +140,33 @@ struct QqgTile {
           out[(ev0 + e) * lp.out_stride + j] = (m0 == 0.0) ? 0.0 : w * (mj / m0);
         }
       } else {
+        // mixed mode: per event the slot sums become w |M_s|^2 / |M_0|^2 with one FP64
+        // division and slot 0 holds w itself (0 if |M_0|^2 == 0, NaN if it is NaN); each
+        // output is one FP64 product with the point's multiplier (f_j / f_0 on the
+        // original slot, so an unchanged point keeps its weight exactly, f_j elsewhere)
+        for (int j = tid; j < k; j += QQG_BLOCK) {
+          sm.slotj[j] = lp.slot[j];
+          sm.mult[j] = lp.slot[j] == 0 ? lp.factor[j] / lp.factor0 : lp.factor[j];
+        }
         for (int e = tid; e < nblk; e += QQG_BLOCK) {
           const double m0 = sm.me2s[e][0] * lp.factor0;
-          sm.inv0[e] = m0 == 0.0 ? 0.0 : 1.0 / m0;
+          const double w = w_in[ev0 + e];
+          const double wi = m0 == 0.0 ? 0.0 : w / m0;
+          for (int sl = 1; sl < lp.nmass; ++sl) sm.me2s[e][sl] *= wi;
+          sm.me2s[e][0] = m0 == 0.0 ? 0.0 : (m0 == m0 ? w : m0);
         }
         __syncthreads();
+        const int kk = k > 0 ? k : 1;
+        int e = tid / kk, j = tid - (tid / kk) * kk;
+        const int de = QQG_BLOCK / kk, dj = QQG_BLOCK - (QQG_BLOCK / kk) * kk;
         for (int idx = tid; idx < nblk * k; idx += QQG_BLOCK) {
-          const int e = idx / k;
-          const int j = idx - e * k;
-          const double m0 = sm.me2s[e][0] * lp.factor0;
-          const double mj = sm.me2s[e][lp.slot[j]] * lp.factor[j];
-          const double w = w_in[ev0 + e];
-          out[(ev0 + e) * lp.out_stride + j] = (m0 == 0.0) ? 0.0 : (mj == m0 ? w : w * (mj * sm.inv0[e]));
+          out[(ev0 + e) * lp.out_stride + j] = sm.me2s[e][sm.slotj[j]] * sm.mult[j];
+          e += de;
+          j += dj;
+          if (j >= k) {
+            j -= k;
+            ++e;
+          }
         }
       }
     } else {
