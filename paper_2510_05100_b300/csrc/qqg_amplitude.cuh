@@ -350,24 +350,4 @@ __device__ __forceinline__ double qqg_invariant_fp64(const double* __restrict__ 
   return t >= 4 ? v - m0 * m0 : v;
 }
 
-// All six invariants of an event (reference form; the tile spreads them over its warps).
-__device__ __forceinline__ void qqg_invariants_fp64(const double (&pd)[5][4], double m0, double* v) {
-  double q[4], qp[4], a1[4], a2[4], a3[4], a4[4];
-#pragma unroll
-  for (int m = 0; m < 4; ++m) {
-    q[m] = pd[0][m] + pd[1][m];
-    qp[m] = pd[2][m] + pd[3][m];
-    a1[m] = pd[0][m] - pd[4][m];
-    a2[m] = pd[4][m] - pd[1][m];
-    a3[m] = pd[2][m] + pd[4][m];
-    a4[m] = pd[3][m] + pd[4][m];
-  }
-  v[0] = mdot(q, q);
-  v[1] = mdot(qp, qp);
-  v[2] = mdot(a1, a1);
-  v[3] = mdot(a2, a2);
-  v[4] = mdot(a3, a3) - m0 * m0;
-  v[5] = mdot(a4, a4) - m0 * m0;
-}
-
 }  // namespace rex
