@@ -22,6 +22,12 @@ sum_{d,d'} conj(A_d) G_dd' A_d' with G = conj(K) K^T over every index.  Summed o
 the 32 helicity configurations, averaged by 1/4 (spins) and 1/9 (quark colours).
 Top spinors follow the Lorentz module's mass convention; the width enters the top
 propagators as q^2 - m^2 + i m Gamma.
+
+The crossed channels with one light quark line (q g -> t t~ q, q~ g -> t t~ q~, the
+beam-swapped g q, g q~ and q~ q) are the same five diagrams with each external
+state's own wavefunction and the momenta along the fermion-number flow
+(CROSSINGS, amplitudes_crossed); the colour sum is the same, the average 1/96 for
+q g (1/4 spins, 1/3 quark and 1/8 gluon colours).
 """
 from __future__ import annotations
 
@@ -72,31 +78,25 @@ def _vector_chain(left: np.ndarray, before: list, after: list, right: np.ndarray
     return out
 
 
-def amplitudes(p: np.ndarray, mt: float, wt: float, alphas: float, hel: tuple, eps_override=None) -> np.ndarray:
-    """The five diagram amplitudes [N, 5] of one helicity configuration
-    hel = (l1, l2, l3, l4, lg); eps_override replaces the gluon's eps* (gauge checks)."""
-    p = np.asarray(p, dtype=np.float64)
-    n = p.shape[0]
+def _diagrams(q1, q2, p3, p4, k, left, right, ub3, v4, eps, mt, wt, alphas) -> np.ndarray:
+    """The five diagram amplitudes [N, 5] of one light line read from the row spinor
+    left to the column spinor right, momenta along the fermion-number flow: q1 enters
+    the line at right, q2 at left, and the gluon leaves it with momentum k and vector
+    eps (eps* of an outgoing gluon, eps of an incoming one with k = -its momentum)."""
     g = math.sqrt(4.0 * math.pi * alphas)
-    l1, l2, l3, l4, lg = hel
-    p1, p2, p3, p4, k = p[:, 0], p[:, 1], p[:, 2], p[:, 3], p[:, 4]
-    u1 = spinor_u(p1, 0.0, l1)
-    vb2 = bar(spinor_v(p2, 0.0, l2))
-    ub3 = bar(spinor_u(p3, mt, l3))
-    v4 = spinor_v(p4, mt, l4)
-    eps = polarisation(k, lg).conj() if eps_override is None else eps_override.astype(complex)
+    n = left.shape[0]
     es = slash(eps)
-    q = p1 + p2
+    q = q1 + q2
     qp = p3 + p4
     s, sp = mdot(q, q), mdot(qp, qp)
     m1 = np.eye(4) * mt
-    j_in = _vector_chain(vb2, [], [], u1)
+    j_in = _vector_chain(left, [], [], right)
     j_out = _vector_chain(ub3, [], [], v4)
     # D1, D2: emission from the light line (massless propagators)
-    a1 = p1 - k
-    c1 = _vector_chain(vb2, [], [slash(a1), es], u1) / mdot(a1, a1)[:, None]
-    a2 = k - p2
-    c2 = _vector_chain(vb2, [es, slash(a2)], [], u1) / mdot(a2, a2)[:, None]
+    a1 = q1 - k
+    c1 = _vector_chain(left, [], [slash(a1), es], right) / mdot(a1, a1)[:, None]
+    a2 = k - q2
+    c2 = _vector_chain(left, [es, slash(a2)], [], right) / mdot(a2, a2)[:, None]
     # D3, D4: emission from the top line
     a3 = p3 + k
     d3 = mdot(a3, a3) - mt * mt + 1j * mt * wt
@@ -115,6 +115,74 @@ def amplitudes(p: np.ndarray, mt: float, wt: float, alphas: float, hel: tuple, e
          - mdot(j_in, j_out) * mdot(eps, qp + q))
     amp[:, 4] = g ** 3 * v / (s * sp)
     return amp
+
+
+def amplitudes(p: np.ndarray, mt: float, wt: float, alphas: float, hel: tuple, eps_override=None) -> np.ndarray:
+    """The five diagram amplitudes [N, 5] of one helicity configuration
+    hel = (l1, l2, l3, l4, lg); eps_override replaces the gluon's eps* (gauge checks)."""
+    p = np.asarray(p, dtype=np.float64)
+    l1, l2, l3, l4, lg = hel
+    p1, p2, p3, p4, k = p[:, 0], p[:, 1], p[:, 2], p[:, 3], p[:, 4]
+    eps = polarisation(k, lg).conj() if eps_override is None else eps_override.astype(complex)
+    return _diagrams(p1, p2, p3, p4, k, bar(spinor_v(p2, 0.0, l2)), spinor_u(p1, 0.0, l1),
+                     bar(spinor_u(p3, mt, l3)), spinor_v(p4, mt, l4), eps, mt, wt, alphas)
+
+
+# The crossings of q q~ -> t t~ g into the other p p -> t t~ + jet channels with a
+# light quark line.  Record order: the two incoming partons, t, t~, the outgoing
+# parton.  Each entry: (indices of the incoming quark, incoming antiquark, outgoing
+# quark, outgoing antiquark, incoming gluon, outgoing gluon; None where absent) and
+# the spin-colour average (1/4 for the spins, 1/9 for a q q~ pair, 1/24 for q g).
+CROSSINGS = {
+    "qq_ttxg": ((0, 1, None, None, None, 4), 36.0),
+    "qxq_ttxg": ((1, 0, None, None, None, 4), 36.0),
+    "qg_ttxq": ((0, None, 4, None, 1, None), 96.0),
+    "gq_ttxq": ((1, None, 4, None, 0, None), 96.0),
+    "qxg_ttxqx": ((None, 0, None, 4, 1, None), 96.0),
+    "gqx_ttxqx": ((None, 1, None, 4, 0, None), 96.0),
+}
+
+
+def amplitudes_crossed(process: str, p: np.ndarray, mt: float, wt: float, alphas: float, hel: tuple,
+                       eps_override=None) -> np.ndarray:
+    """The five diagram amplitudes [N, 5] of one channel of CROSSINGS from the Feynman
+    rules of its own external states (Peskin & Schroeder Sec. 4.7): an incoming
+    quark gives u, an outgoing quark ubar, an incoming antiquark vbar, an outgoing
+    antiquark v, an outgoing gluon eps*, an incoming gluon eps.  hel: the helicities
+    of the record's particles in record order.  The light line runs along the
+    fermion-number flow from the quark entering the diagram (an incoming quark or
+    an outgoing antiquark, momentum q1) to the one leaving it (momentum -q2)."""
+    p = np.asarray(p, dtype=np.float64)
+    (iq, iqb, oq, oqb, ig, og), _ = CROSSINGS[process]
+    if iq is not None:
+        right, q1 = spinor_u(p[:, iq], 0.0, hel[iq]), p[:, iq]
+    else:
+        right, q1 = spinor_v(p[:, oqb], 0.0, hel[oqb]), -p[:, oqb]
+    if iqb is not None:
+        left, q2 = bar(spinor_v(p[:, iqb], 0.0, hel[iqb])), p[:, iqb]
+    else:
+        left, q2 = bar(spinor_u(p[:, oq], 0.0, hel[oq])), -p[:, oq]
+    if og is not None:
+        k, eps = p[:, og], polarisation(p[:, og], hel[og]).conj()
+    else:
+        k, eps = -p[:, ig], polarisation(p[:, ig], hel[ig])
+    if eps_override is not None:
+        eps = eps_override.astype(complex)
+    return _diagrams(q1, q2, p[:, 2], p[:, 3], k, left, right, bar(spinor_u(p[:, 2], mt, hel[2])),
+                     spinor_v(p[:, 3], mt, hel[3]), eps, mt, wt, alphas)
+
+
+def me2_crossed(process: str, p: np.ndarray, mt: float, wt: float, alphas: float) -> np.ndarray:
+    """Spin/colour summed and averaged |M|^2 of one channel of CROSSINGS, one point."""
+    p = np.asarray(p, dtype=np.float64)
+    if p.ndim != 3 or p.shape[1] != 5:
+        raise ValueError(f"{process} expects momenta [N, 5, 4]")
+    gm = colour_matrix()
+    total = np.zeros(p.shape[0])
+    for hel in itertools.product((-1, 1), repeat=5):
+        a = amplitudes_crossed(process, p, mt, wt, alphas, hel)
+        total += np.real(np.einsum("ns,st,nt->n", a.conj(), gm, a))
+    return total / CROSSINGS[process][1]
 
 
 def me2(p: np.ndarray, mt: float, wt: float, alphas: float) -> np.ndarray:
@@ -146,7 +214,12 @@ def me2_helicity(p: np.ndarray, mt: float, wt: float, alphas: float, hel: np.nda
     return out
 
 
-def colour_amplitude(p: np.ndarray, mt: float, hel: tuple, eps_override=None, alphas: float = 0.118) -> np.ndarray:
-    """sum_d K_d A_d: the colour-dressed amplitude [N, 8, 3, 3, 3, 3] of one configuration."""
-    a = amplitudes(p, mt, 0.0, alphas, hel, eps_override)
+def colour_amplitude(p: np.ndarray, mt: float, hel: tuple, eps_override=None, alphas: float = 0.118,
+                     process: str = "qq_ttxg") -> np.ndarray:
+    """sum_d K_d A_d: the colour-dressed amplitude [N, 8, 3, 3, 3, 3] of one configuration
+    (hel in record order) of q q~ -> t t~ g or one of its CROSSINGS."""
+    if process == "qq_ttxg":
+        a = amplitudes(p, mt, 0.0, alphas, hel, eps_override)
+    else:
+        a = amplitudes_crossed(process, p, mt, 0.0, alphas, hel, eps_override)
     return np.einsum("nd,dajklm->najklm", a, colour_tensors())

@@ -28,6 +28,8 @@ def me2(process: str, p: np.ndarray, point: dict) -> np.ndarray:
         return qq.me2(p, point["mt"], point.get("wt", 0.0), point["alphas"])
     if process == "qq_ttxg":
         return qqg.me2(p, point["mt"], point.get("wt", 0.0), point["alphas"])
+    if process in qqg.CROSSINGS:
+        return qqg.me2_crossed(process, p, point["mt"], point.get("wt", 0.0), point["alphas"])
     raise ValueError(f"unknown process {process!r}")
 
 

@@ -14,7 +14,10 @@ Workloads (all in the partonic centre-of-mass frame, no cuts):
 * ``gg_ttx``: g(1) g(2) -> t(3) t~(4); sqrt(s_hat) log-uniform, isotropic top.
 * ``qq_ttx``: q(1) q~(2) -> t(3) t~(4), massless light quarks; the same
   two-body kinematics as ``gg_ttx``.
-* ``qq_ttxg``: q(1) q~(2) -> t(3) t~(4) g(5); the ``gg_ttxg`` kinematics.
+* ``qq_ttxg``: q(1) q~(2) -> t(3) t~(4) g(5); the ``gg_ttxg`` kinematics.  Its
+  crossed channels ``qxq_ttxg``, ``qg_ttxq``, ``gq_ttxq``, ``qxg_ttxqx`` and
+  ``gqx_ttxqx`` (the two incoming partons, t, t~, the outgoing light parton) take
+  the same kinematics: every external light parton is massless.
 * ``gg_ttxg`` / ``gg_ttxgg``: g g -> t t~ g (g): massive RAMBO (Kleiss, Stirling,
   Ellis, Comput. Phys. Commun. 40 (1986) 359) at log-uniform sqrt(s_hat).
 
@@ -34,7 +37,9 @@ ALPHAS_DEFAULT = 0.118
 EE_ORIGINAL = dict(mz=91.1876, wz=2.4952, sw2=0.2312, alpha=1.0 / 132.507)
 EE_NEW = dict(mz=91.0, wz=2.6, sw2=0.2300, alpha=1.0 / 132.507)
 
-PROCESS_NPART = {"ee_mumu": 4, "gg_ttx": 4, "qq_ttx": 4, "gg_ttxg": 5, "qq_ttxg": 5, "gg_ttxgg": 6}
+QQ_TTXG_CROSSINGS = ("qq_ttxg", "qxq_ttxg", "qg_ttxq", "gq_ttxq", "qxg_ttxqx", "gqx_ttxqx")
+PROCESS_NPART = {"ee_mumu": 4, "gg_ttx": 4, "qq_ttx": 4, "gg_ttxg": 5, "gg_ttxgg": 6,
+                 **{name: 5 for name in QQ_TTXG_CROSSINGS}}
 
 
 def _rng(seed: int) -> np.random.Generator:
@@ -182,7 +187,7 @@ def make_events(process: str, nev: int, seed: int, mt: float = MT_DEFAULT) -> np
         return ee_mumu_events(nev, seed)
     if process in ("gg_ttx", "qq_ttx"):
         return two_body_events(nev, seed, mt, mt, 2.0 * mt + 1.0, 3000.0)
-    if process in ("gg_ttxg", "qq_ttxg"):
+    if process == "gg_ttxg" or process in QQ_TTXG_CROSSINGS:
         return gg_tt_jets_events(nev, seed, 1, 400.0, 4000.0, mt)
     if process == "gg_ttxgg":
         return gg_tt_jets_events(nev, seed, 2, 500.0, 5000.0, mt)

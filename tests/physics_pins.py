@@ -363,3 +363,38 @@ def soft_qq_ttg_events(n, seed, m, sqrt_s, omega_frac):
         out.append([p1, p2, t_lab, tb_lab, k])
         born.append([p1, p2, t0, tb0])
     return np.array(out), np.array(born)
+
+
+# ----------------------------------------------------------------------------
+# initial-state collinear limit of q g -> Q Q~ q (g -> q q~ splitting)
+# ----------------------------------------------------------------------------
+def collinear_initial_events(n, seed, m, sqrt_s, x, theta):
+    """a(pa) g(pb) -> Q Q~ c(pc) in the centre-of-mass frame, pa along +z, pb along -z,
+    the outgoing light parton c of energy (1 - x) E_b at angle theta to pb (seeded
+    azimuth), the Q Q~ pair recoiling and decaying at seeded angles in its rest frame.
+    Returns events [n, 5, 4] in the order (pa, pb, Q, Q~, pc)."""
+    rng = np.random.default_rng(seed)
+    e = sqrt_s / 2.0
+    pa = np.array([e, 0.0, 0.0, e])
+    pb = np.array([e, 0.0, 0.0, -e])
+    out = []
+    for _ in range(n):
+        phi = rng.uniform(0, 2 * math.pi)
+        ec = (1.0 - x) * e
+        pc = ec * np.array([1.0, math.sin(theta) * math.cos(phi), math.sin(theta) * math.sin(phi), -math.cos(theta)])
+        qq = pa + pb - pc
+        mm = math.sqrt(qq[0] ** 2 - qq[1:] @ qq[1:])
+        q = math.sqrt(mm * mm / 4.0 - m * m)
+        ct, pht = rng.uniform(-0.9, 0.9), rng.uniform(0, 2 * math.pi)
+        nt = np.array([math.sqrt(1 - ct * ct) * math.cos(pht), math.sqrt(1 - ct * ct) * math.sin(pht), ct])
+        t_rest = np.concatenate([[mm / 2.0], q * nt])
+        tb_rest = np.concatenate([[mm / 2.0], -q * nt])
+        beta = qq[1:] / qq[0]
+        out.append([pa, pb, boost(t_rest[None], beta)[0], boost(tb_rest[None], beta)[0], pc])
+    return np.array(out)
+
+
+def splitting_g_to_qq(x):
+    """The spin- and colour-averaged g -> q q~ splitting function T_R (x^2 + (1 - x)^2),
+    T_R = 1/2 (Altarelli & Parisi, Nucl. Phys. B126 (1977) 298)."""
+    return 0.5 * (x * x + (1.0 - x) ** 2)
