@@ -355,14 +355,16 @@ def run_qqg_leg(dev, stream, pts, steps, nev=NEV):
     return out
 
 
-# two-channel p p -> t t~ (+ jet) samples: g g and q q~ initial states, 7 : 1, 2^20 events
+# multi-channel p p -> t t~ (+ jet) samples of 2^20 events: g g and q q~ initial states
+# 7 : 1 for t t~; g g, q g, q~ g and q q~ 12 : 2 : 1 : 1 for t t~ + jet
 PP_TTX_BATCHES = (("gg_ttx", 917504, 11), ("qq_ttx", 131072, 12))
-PP_TTXJ_BATCHES = (("gg_ttxg", 917504, 13), ("qq_ttxg", 131072, 14))
+PP_TTXJ_BATCHES = (("gg_ttxg", 786432, 13), ("qg_ttxq", 131072, 15), ("qxg_ttxqx", 65536, 16),
+                   ("qq_ttxg", 65536, 14))
 
 
 def run_pp_ttx_leg(dev, stream, pts, steps, world, barrier, max_over_ranks, spec=PP_TTX_BATCHES):
-    """The p p -> t t~ (+ jet) channels (g g and q q~ batches of one sample) reweighted to
-    the headline's points: one graph-captured persistent multi-process launch against one
+    """The p p -> t t~ (+ jet) channels (one batch per initial state of one sample)
+    reweighted to the headline's points: one graph-captured persistent multi-process launch against one
     launch per channel, in FP64 and in mixed precision."""
     import torch
     from paper_2510_05100_b300 import rex
@@ -385,7 +387,8 @@ def run_pp_ttx_leg(dev, stream, pts, steps, world, barrier, max_over_ranks, spec
         return max_over_ranks(t0.elapsed_time(t1)) / steps
 
     desc = " + ".join(f"{n} {proc}" for proc, n, _ in spec)
-    out = {"workload": f"two-channel sample of 2^20 events: {desc}, {len(pts)} points", "unit": UNIT, "steps": steps}
+    out = {"workload": f"{len(spec)}-channel sample of 2^20 events: {desc}, {len(pts)} points", "unit": UNIT,
+           "steps": steps}
     for name, prec in (("fp64", rex.FP64), ("mixed", rex.MIXED)):
         batches = []
         for proc, n, seed in spec:

@@ -72,7 +72,7 @@ extern "C" {
 typedef struct rex_proc rex_proc; /* opaque, library-owned */
 
 /* One parameter point.  Fields a process does not use are ignored.
- *   QCD processes (gg_ttx, gg_ttxg, gg_ttxgg, qq_ttx, qq_ttxg): mt, wt (top mass and
+ *   QCD processes (gg_ttx, gg_ttxg, gg_ttxgg, qq_ttx, qq_ttxg and its crossings): mt, wt (top mass and
  *     width, GeV), alphas (strong coupling, fixed; g_s = sqrt(4 pi alphas)).
  *     mt enters the top propagators and the external top spinors; momenta
  *     are kept as given.  qq_ttx has no top propagator: wt is checked and
@@ -91,6 +91,13 @@ typedef struct {
  *       "gg_ttxgg" g(1) g(2) -> t(3) t~(4) g(5) g(6);
  *       "qq_ttxg"  q(1) q~(2) -> t(3) t~(4) g(5), massless light quark,
  *                  five diagrams;
+ *       "qxq_ttxg" q~(1) q(2) -> t(3) t~(4) g(5);
+ *       "qg_ttxq"  q(1) g(2) -> t(3) t~(4) q(5);   "gq_ttxq"   g(1) q(2) -> t(3) t~(4) q(5);
+ *       "qxg_ttxqx" q~(1) g(2) -> t(3) t~(4) q~(5); "gqx_ttxqx" g(1) q~(2) -> t(3) t~(4) q~(5):
+ *                  the crossings of qq_ttxg that complete p p -> t t~ + jet with a
+ *                  light-quark line, evaluated by its kernels with the event's
+ *                  partons read into its slots (spin-colour average 1/96 for the
+ *                  q g channels, 1/36 for q q~); helicity-summed only;
  *       "qq_ttx"   q(1) q~(2) -> t(3) t~(4), massless light quark, one
  *                  s-channel gluon (the quark-initiated leading-order
  *                  channel of p p -> t t~; multi-channel samples with p any
@@ -139,7 +146,8 @@ int rex_reweight(rex_proc *proc, const double *momenta, const double *w_in,
  *   other arguments as rex_reweight.
  * Processes: ee_mumu, qq_ttx and qq_ttxg, whose kernels evaluate helicity
  * amplitudes (the q q~ -> t t~ g gluon in the helicity basis); the g g processes
- * sum real linear gluon polarisations and return REX_EUNSUPPORTED.
+ * sum real linear gluon polarisations and the crossings of qq_ttxg use the
+ * helicity sum's freedom in their wavefunctions: both return REX_EUNSUPPORTED.
  * Enqueue only.  Errors: REX_EUNSUPPORTED, REX_EINVAL (as rex_reweight, null
  * helicities), REX_ENOTINIT, REX_ECUDA. */
 int rex_reweight_helicity(rex_proc *proc, const double *momenta, const signed char *helicities,

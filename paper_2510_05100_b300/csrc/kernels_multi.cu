@@ -65,7 +65,7 @@ __global__ void __launch_bounds__(QCD_BLOCK, MINB)
         break;
       case PROC_QQ_TTX: T4::run(sm.d, B.mom, B.w_in, B.nev, tile, B.t, B.out); break;
       case PROC_QQ_TTXG:
-        if constexpr (CLASS >= 1) T5::run(sm.e, B.mom, B.w_in, B.nev, tile, B.t, B.out);
+        if constexpr (CLASS >= 1) T5::run(sm.e, B.mom, B.w_in, B.nev, tile, B.t, B.out, nullptr, B.cross);
         break;
       default: break;
     }

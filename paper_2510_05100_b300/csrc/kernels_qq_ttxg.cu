@@ -9,22 +9,22 @@ template <typename R, int MINB, bool EXCL>
 __global__ void __launch_bounds__(QQG_BLOCK, MINB)
     qq_ttxg_reweight_kernel(const double* __restrict__ mom, const double* __restrict__ w_in, int64_t nev,
                             const __grid_constant__ QcdLaunch lp, double* __restrict__ out,
-                            const signed char* __restrict__ hel) {
+                            const signed char* __restrict__ hel, const __grid_constant__ QqgCrossing cross) {
   __shared__ typename QqgTile<R>::Smem sm;
-  QqgTile<R>::template run<EXCL>(sm, mom, w_in, nev, (int64_t)blockIdx.x, lp, out, hel);
+  QqgTile<R>::template run<EXCL>(sm, mom, w_in, nev, (int64_t)blockIdx.x, lp, out, hel, cross);
 }
 
 int launch_qq_ttxg(int mixed, const double* mom, const double* w_in, int64_t nev, const QcdLaunch& lp,
-                   double* out, void* stream, const signed char* hel) {
+                   double* out, void* stream, const signed char* hel, const QqgCrossing& cross) {
   constexpr int EPB = QqgTile<float>::EPB;
   const int64_t blocks = (nev + EPB - 1) / EPB;
   if (blocks > 0x7fffffffLL) return (int)cudaErrorInvalidValue;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const unsigned g = (unsigned)blocks;
-  if (mixed && hel) qq_ttxg_reweight_kernel<float, 3, true><<<g, QQG_BLOCK, 0, st>>>(mom, w_in, nev, lp, out, hel);
-  else if (mixed) qq_ttxg_reweight_kernel<float, 3, false><<<g, QQG_BLOCK, 0, st>>>(mom, w_in, nev, lp, out, nullptr);
-  else if (hel) qq_ttxg_reweight_kernel<double, 1, true><<<g, QQG_BLOCK, 0, st>>>(mom, w_in, nev, lp, out, hel);
-  else qq_ttxg_reweight_kernel<double, 1, false><<<g, QQG_BLOCK, 0, st>>>(mom, w_in, nev, lp, out, nullptr);
+  if (mixed && hel) qq_ttxg_reweight_kernel<float, 3, true><<<g, QQG_BLOCK, 0, st>>>(mom, w_in, nev, lp, out, hel, cross);
+  else if (mixed) qq_ttxg_reweight_kernel<float, 3, false><<<g, QQG_BLOCK, 0, st>>>(mom, w_in, nev, lp, out, nullptr, cross);
+  else if (hel) qq_ttxg_reweight_kernel<double, 1, true><<<g, QQG_BLOCK, 0, st>>>(mom, w_in, nev, lp, out, hel, cross);
+  else qq_ttxg_reweight_kernel<double, 1, false><<<g, QQG_BLOCK, 0, st>>>(mom, w_in, nev, lp, out, nullptr, cross);
   return (int)cudaGetLastError();
 }
 

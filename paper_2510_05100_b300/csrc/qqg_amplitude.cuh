@@ -102,15 +102,32 @@ struct QqgInvariants {
 };
 
 // Lane set-up: light-quark helicities (l1, l2) = h12 ? (-, +) : (+, -), gluon
-// polarisation pol; p: the event's momenta in R.  C1 and C2 are left without their
-// propagator factors and the invariants unset: qqg_lane_scale applies them.
+// polarisation pol; p: the event's momenta in R along the fermion-number flow of
+// the q q~ -> t t~ g slots.  C1 and C2 are left without their propagator factors
+// and the invariants unset: qqg_lane_scale applies them.
+//
+// Crossed channels: bit 0, 1, 2 of neg marks slot 0, 1, 4 as holding a negated
+// physical momentum (an outgoing antiquark, an outgoing quark, an incoming gluon).
+// Their wavefunctions are built from the physical momentum with the direct
+// channel's functions: summed over helicities only sum_h psi psibar enters, and for
+// a massless momentum that is p-slash for u and for v alike, while the two real
+// linear polarisations of a gluon sum to the same transverse projector whether it
+// is incoming or outgoing.  (The helicity-exclusive form has no such freedom and
+// takes the direct channel only.)
 template <typename R>
-__device__ __forceinline__ void qqg_lane_setup(const R (&p)[5][4], int h12, int pol, QqgLane<R>& L) {
+__device__ __forceinline__ void qqg_lane_setup(const R (&p)[5][4], int h12, int pol, QqgLane<R>& L, int neg = 0) {
   const int l1 = h12 ? -1 : 1;
+  R k0[4], k1[4], k4[4];   // physical momenta of the light partons
+#pragma unroll
+  for (int m = 0; m < 4; ++m) {
+    k0[m] = (neg & 1) ? -p[0][m] : p[0][m];
+    k1[m] = (neg & 2) ? -p[1][m] : p[1][m];
+    k4[m] = (neg & 4) ? -p[4][m] : p[4][m];
+  }
   cx<R> u1[4], v2[4];
-  spinor_u(p[0], R(0), l1, u1);
-  spinor_v(p[1], R(0), -l1, v2);
-  pol_linear(p[4], pol, L.eps);
+  spinor_u(k0, R(0), l1, u1);
+  spinor_v(k1, R(0), -l1, v2);
+  pol_linear(k4, pol, L.eps);
   dirac_current(v2, u1, L.jin);
   R a1[4], a2[4], qk[4], qpk[4], qq2[4];
 #pragma unroll
@@ -333,21 +350,6 @@ __device__ __forceinline__ R qqg_slot_h(const QqgLaneH<R>& L, R mr, R dm2, R mw)
       form += R(2 * qqg_colour(d, d2)) * (a[d].re * a[d2].re + a[d].im * a[d2].im);
   }
   return form;
-}
-
-// Invariant t of an event (FP64 because (p1 - k)^2 and the top denominators cancel
-// for collinear or soft gluons): t = 0 s, 1 s', 2 (p1 - k)^2, 3 (k - p2)^2,
-// 4 (p3 + k)^2 - m0^2, 5 (p4 + k)^2 - m0^2; p: the event's [5][4] FP64 momenta.
-__device__ __forceinline__ double qqg_invariant_fp64(const double* __restrict__ p, int t, double m0) {
-  // the two momenta and the sign: t -> (a, b, sign) with x = p_a + sign p_b
-  const int a = t == 0 ? 0 : (t == 1 ? 2 : (t == 2 ? 0 : (t == 3 ? 4 : (t == 4 ? 2 : 3))));
-  const int b = t == 0 ? 1 : (t == 1 ? 3 : (t == 2 ? 4 : (t == 3 ? 1 : 4)));
-  const double sg = (t == 2 || t == 3) ? -1.0 : 1.0;
-  double x[4];
-#pragma unroll
-  for (int m = 0; m < 4; ++m) x[m] = p[4 * a + m] + sg * p[4 * b + m];
-  const double v = mdot(x, x);
-  return t >= 4 ? v - m0 * m0 : v;
 }
 
 }  // namespace rex

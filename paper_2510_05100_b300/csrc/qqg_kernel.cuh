@@ -32,6 +32,33 @@ namespace rex {
 constexpr int QQG_BLOCK = 128;
 constexpr int QQG_LANES = 4;
 
+constexpr QqgCrossing kQqgDirect = {{0, 1, 2, 3, 4}, {0, 0, 0, 0, 0}};
+
+// x with its sign flipped where neg (an integer XOR on the high word: no FP64 issue)
+__device__ __forceinline__ double qqg_flip(double x, bool neg) {
+  return __hiloint2double(__double2hiint(x) ^ (neg ? (int)0x80000000 : 0), __double2loint(x));
+}
+
+// Invariant t of an event (FP64 because (p1 - k)^2 and the top denominators cancel
+// for collinear or soft gluons), over the slot momenta of the channel cr:
+// t = 0 s, 1 s', 2 (p1 - k)^2, 3 (k - p2)^2, 4 (p3 + k)^2 - m0^2, 5 (p4 + k)^2 - m0^2;
+// p: the event's [5][4] FP64 record.
+__device__ __forceinline__ double qqg_invariant_fp64(const double* __restrict__ p, int t, double m0,
+                                                     const QqgCrossing& cr) {
+  // the two slots and the sign: t -> (a, b, minus) with x = p_a -/+ p_b
+  const int a = t == 0 ? 0 : (t == 1 ? 2 : (t == 2 ? 0 : (t == 3 ? 4 : (t == 4 ? 2 : 3))));
+  const int b = t == 0 ? 1 : (t == 1 ? 3 : (t == 2 ? 4 : (t == 3 ? 1 : 4)));
+  const bool minus = t == 2 || t == 3;
+  const double* pa = p + 4 * cr.src[a];
+  const double* pb = p + 4 * cr.src[b];
+  const bool na = cr.neg[a] != 0, nb = (cr.neg[b] != 0) != minus;
+  double x[4];
+#pragma unroll
+  for (int m = 0; m < 4; ++m) x[m] = qqg_flip(pa[m], na) + qqg_flip(pb[m], nb);
+  const double v = mdot(x, x);
+  return t >= 4 ? v - m0 * m0 : v;
+}
+
 template <typename R>
 struct QqgTile {
   static constexpr int EPB = QQG_BLOCK / QQG_LANES;
@@ -50,12 +77,14 @@ struct QqgTile {
   }
 
   // EXCL: helicity-exclusive, hel[ev][0..4] = the event's (l1, l2, l3, l4, lg); the
-  // event's one configuration is evaluated by each of its 4 lanes for every 4th slot
+  // event's one configuration is evaluated by each of its 4 lanes for every 4th slot.
+  // cr: the channel (the direct one for EXCL).
   template <bool EXCL = false, class TABLE>
   static __device__ __forceinline__ void run(Smem& sm, const double* __restrict__ mom,
                                              const double* __restrict__ w_in, int64_t nev, int64_t tile,
                                              const TABLE& lp, double* __restrict__ out,
-                                             const signed char* __restrict__ hel = nullptr) {
+                                             const signed char* __restrict__ hel = nullptr,
+                                             const QqgCrossing& cr = kQqgDirect) {
     const int tid = threadIdx.x;
     const int el = tid / QQG_LANES, lane = tid % QQG_LANES;
     const int64_t ev0 = tile * EPB;
@@ -72,12 +101,17 @@ struct QqgTile {
     double pd[5][4];
     R p[5][4];
     static_assert(EPB == 32 && QQG_BLOCK == 128, "one warp per invariant type over the tile's 32 events");
+    // slot i <- the channel's particle cr.src[i], its sign flipped where crossed
     const double2* src = reinterpret_cast<const double2*>(mom + evc * 20);
 #pragma unroll
-    for (int i = 0; i < 10; ++i) {
-      const double2 v = __ldg(src + i);
-      pd[(2 * i) >> 2][(2 * i) & 3] = v.x;
-      pd[(2 * i + 1) >> 2][(2 * i + 1) & 3] = v.y;
+    for (int i = 0; i < 5; ++i) {
+      const double2* q = src + 2 * cr.src[i];
+      const double2 v0 = __ldg(q), v1 = __ldg(q + 1);
+      const bool ng = cr.neg[i] != 0;
+      pd[i][0] = qqg_flip(v0.x, ng);
+      pd[i][1] = qqg_flip(v0.y, ng);
+      pd[i][2] = qqg_flip(v1.x, ng);
+      pd[i][3] = qqg_flip(v1.y, ng);
     }
 #pragma unroll
     for (int i = 0; i < 5; ++i)
@@ -89,9 +123,9 @@ struct QqgTile {
       const int64_t ei = ev0 + e < nev ? ev0 + e : nev - 1;
       const double* pe = mom + ei * 20;
       const double m0 = lp.mass[0];
-      const double v = qqg_invariant_fp64(pe, w, m0);
+      const double v = qqg_invariant_fp64(pe, w, m0, cr);
       sm.inv[w][e] = R(1) / to_r(v);
-      if (w < 2) sm.inv[4 + w][e] = to_r(qqg_invariant_fp64(pe, 4 + w, m0));
+      if (w < 2) sm.inv[4 + w][e] = to_r(qqg_invariant_fp64(pe, 4 + w, m0, cr));
     }
     if constexpr (EXCL) {
       QqgLaneH<R> L;
@@ -109,7 +143,7 @@ struct QqgTile {
         sm.me2s[el][s] = valid ? double(qqg_slot_h<R>(L, sm.mr[s], sm.dm2[s], sm.mw[s])) : 0.0;
     } else {
       QqgLane<R> L;
-      qqg_lane_setup<R>(p, lane & 1, lane >> 1, L);
+      qqg_lane_setup<R>(p, lane & 1, lane >> 1, L, (cr.neg[0] ? 1 : 0) | (cr.neg[1] ? 2 : 0) | (cr.neg[4] ? 4 : 0));
       __syncthreads();
       QqgInvariants<R> inv;
       inv.is = sm.inv[0][el];

@@ -30,6 +30,8 @@ struct rex_proc {
   int variant;        // QCD thread-mapping variant (qcd_kernel.cuh)
   int has_orig;
   rex_params orig;
+  QqgCrossing cross;  // q q~ -> t t~ g channels: how the kernel reads an event
+  double avg;         // q q~ -> t t~ g channels: the spin-colour average's denominator
   // rex_reweight_host buffers (device), grown on demand
   double* d_mom;
   double* d_win;
@@ -73,6 +75,29 @@ const ProcInfo kProcs[] = {
 };
 static_assert(sizeof(kProcs) / sizeof(kProcs[0]) == PROC_LAST + 1, "one table row per process kind");
 
+// The crossed channels of q q~ -> t t~ g with one light-quark line (record order: the
+// two incoming partons, t, t~, the outgoing parton), run by the q q~ -> t t~ g
+// kernels; avg: 4 spins x 9 colours for q q~, x 24 for q g.
+struct QqgChannel {
+  const char* name;
+  QqgCrossing cross;
+  double avg;
+};
+const QqgChannel kQqgChannels[] = {
+    {"qq_ttxg", {{0, 1, 2, 3, 4}, {0, 0, 0, 0, 0}}, 36.0},
+    {"qxq_ttxg", {{1, 0, 2, 3, 4}, {0, 0, 0, 0, 0}}, 36.0},
+    {"qg_ttxq", {{0, 4, 2, 3, 1}, {0, 1, 0, 0, 1}}, 96.0},
+    {"gq_ttxq", {{1, 4, 2, 3, 0}, {0, 1, 0, 0, 1}}, 96.0},
+    {"qxg_ttxqx", {{4, 0, 2, 3, 1}, {1, 0, 0, 0, 1}}, 96.0},
+    {"gqx_ttxqx", {{4, 1, 2, 3, 0}, {1, 0, 0, 0, 1}}, 96.0},
+};
+
+bool is_direct(const QqgCrossing& c) {
+  for (int i = 0; i < 5; ++i)
+    if (c.src[i] != i || c.neg[i] != 0) return false;
+  return true;
+}
+
 const ProcInfo& info_of(int kind) { return kProcs[kind]; }
 
 // processes with one kernel (no thread-mapping variants to choose from)
@@ -101,7 +126,7 @@ int launch_qcd(const rex_proc* p, const double* mom, const double* w_in, int64_t
     case PROC_GG_TTXG: return launch_gg_ttxg(mixed, p->variant, mom, w_in, nev, lp, out, stream);
     case PROC_GG_TTXGG: return launch_gg_ttxgg(mixed, p->variant, mom, w_in, nev, lp, out, stream);
     case PROC_QQ_TTX: return launch_qq_ttx(mixed, mom, w_in, nev, lp, out, stream, hel);
-    case PROC_QQ_TTXG: return launch_qq_ttxg(mixed, mom, w_in, nev, lp, out, stream, hel);
+    case PROC_QQ_TTXG: return launch_qq_ttxg(mixed, mom, w_in, nev, lp, out, stream, hel, p->cross);
     default: return (int)cudaErrorInvalidValue;
   }
 }
@@ -111,11 +136,13 @@ bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) ==
 
 // avg * (4 pi alphas)^n / colour_den for a pure-gluon tree amplitude with n gluons;
 // q q~ -> t t~: (4 pi alphas)^2 * colour sum (N^2 - 1)/4 = 2 / (4 spins * 9 colours)
-double qcd_factor(const ProcInfo& pi, double alphas) {
+double qcd_factor(const rex_proc* p, double alphas) {
+  const ProcInfo& pi = info_of(p->kind);
   const double gs2 = 4.0 * M_PI * alphas;
   if (pi.kind == PROC_QQ_TTX) return gs2 * gs2 * 2.0 / 36.0;
-  // q q~ -> t t~ g: g^6, the integer colour matrix's 1/3, average 1/(4 spins * 9 colours)
-  if (pi.kind == PROC_QQ_TTXG) return gs2 * gs2 * gs2 / (3.0 * 36.0);
+  // q q~ -> t t~ g and its crossings: g^6, the integer colour matrix's 1/3, and the
+  // channel's average (1/(4 spins * 9 colours) for q q~, 1/(4 * 24) for q g)
+  if (pi.kind == PROC_QQ_TTXG) return gs2 * gs2 * gs2 / (3.0 * p->avg);
   double f = 1.0;
   for (int i = 0; i < pi.ngluon; ++i) f *= gs2;
   int nfinal = pi.ngluon - 2;
@@ -161,7 +188,6 @@ EwPoint ew_point(const rex_params& p) {
 int run_qcd_chunk(rex_proc* p, const double* mom, const double* w_in, int64_t nev,
                   const rex_params* pts, int j0, int j1, int mode, double* out, int64_t stride,
                   void* stream, int* next_j, const signed char* hel = nullptr) {
-  const ProcInfo& pi = info_of(p->kind);
   QcdLaunch lp;
   std::memset(&lp, 0, sizeof lp);
   lp.mode = mode;
@@ -169,7 +195,7 @@ int run_qcd_chunk(rex_proc* p, const double* mom, const double* w_in, int64_t ne
   lp.nmass = 1;
   lp.mass[0] = p->orig.mt;
   lp.width[0] = p->orig.wt;
-  lp.factor0 = qcd_factor(pi, p->orig.alphas);
+  lp.factor0 = qcd_factor(p, p->orig.alphas);
   const bool dedupe = !(p->flags & REX_FLAG_NO_DEDUPE);
   int j = j0;
   for (; j < j1 && j - j0 < MAX_POINTS; ++j) {
@@ -189,7 +215,7 @@ int run_qcd_chunk(rex_proc* p, const double* mom, const double* w_in, int64_t ne
       lp.width[slot] = q.wt;
     }
     lp.slot[j - j0] = slot;
-    lp.factor[j - j0] = qcd_factor(pi, q.alphas);
+    lp.factor[j - j0] = qcd_factor(p, q.alphas);
   }
   lp.k = j - j0;
   for (int s = 0; s < lp.nmass; ++s)
@@ -257,14 +283,13 @@ int reweight_impl(rex_proc* p, const double* momenta, const double* w_in, int64_
 // persistent multi-process launch
 // ---------------------------------------------------------------------------
 int fill_multi_table(const rex_proc* p, const rex_params* pts, int j0, int j1, int64_t stride, MultiTable& t) {
-  const ProcInfo& pi = info_of(p->kind);
   std::memset(&t, 0, sizeof t);
   t.mode = OUT_RATIO;
   t.out_stride = stride;
   t.nmass = 1;
   t.mass[0] = p->orig.mt;
   t.width[0] = p->orig.wt;
-  t.factor0 = qcd_factor(pi, p->orig.alphas);
+  t.factor0 = qcd_factor(p, p->orig.alphas);
   const bool dedupe = !(p->flags & REX_FLAG_NO_DEDUPE);
   for (int j = j0; j < j1; ++j) {
     const rex_params& q = pts[j];
@@ -281,7 +306,7 @@ int fill_multi_table(const rex_proc* p, const rex_params* pts, int j0, int j1, i
       t.width[slot] = q.wt;
     }
     t.slot[j - j0] = slot;
-    t.factor[j - j0] = qcd_factor(pi, q.alphas);
+    t.factor[j - j0] = qcd_factor(p, q.alphas);
   }
   t.k = j1 - j0;
   for (int s = 0; s < t.nmass; ++s)
@@ -393,6 +418,7 @@ int multi_impl(rex_multi* m, const rex_batch* batches, int nbatch, const rex_par
         if (b.nev == 0 || multi_class_of(b.proc->kind) != cls) continue;
         MultiBatch& B = ml.b[nb++];
         B.kind = b.proc->kind;
+        B.cross = b.proc->cross;
         B.nev = b.nev;
         B.mom = b.momenta;
         B.w_in = b.w_in;
@@ -632,6 +658,12 @@ int rex_init_process(const char* name, int precision, rex_proc** out) {
   int kind = -1;
   for (const ProcInfo& pi : kProcs)
     if (std::strcmp(pi.name, name) == 0) kind = pi.kind;
+  const QqgChannel* channel = nullptr;
+  for (const QqgChannel& c : kQqgChannels)
+    if (std::strcmp(c.name, name) == 0) {
+      kind = PROC_QQ_TTXG;
+      channel = &c;
+    }
   if (kind < 0) return fail(REX_EINVAL, "unknown process '%s'", name);
   if (kind == PROC_EE_MUMU && precision != REX_FP64)
     return fail(REX_EUNSUPPORTED, "ee_mumu is implemented in FP64 only");
@@ -641,6 +673,10 @@ int rex_init_process(const char* name, int precision, rex_proc** out) {
   p->kind = kind;
   p->precision = precision;
   p->variant = default_variant(kind, precision);
+  if (channel) {
+    p->cross = channel->cross;
+    p->avg = channel->avg;
+  }
   *out = p;
   return REX_OK;
 }
@@ -685,6 +721,10 @@ int rex_reweight_helicity(rex_proc* proc, const double* momenta, const signed ch
                 "helicity-exclusive reweighting needs helicity-basis amplitudes: ee_mumu, qq_ttx and qq_ttxg "
                 "have them, '%s' sums linear gluon polarisations",
                 info_of(proc->kind).name);
+  if (proc->kind == PROC_QQ_TTXG && !is_direct(proc->cross))
+    return fail(REX_EUNSUPPORTED,
+                "helicity-exclusive reweighting of q q~ -> t t~ g is built for the direct channel only; its "
+                "crossings evaluate the helicity sum");
   if (nev > 0 && k > 0 && !helicities) return fail(REX_EINVAL, "null helicity array");
   return reweight_impl(proc, momenta, w_in, nev, param_sets, k, w_out, stream, helicities);
 }

@@ -52,6 +52,16 @@ struct EwLaunch {
   EwPoint pt[MAX_EW_POINTS + 1];
 };
 
+// A channel of q q~ -> t t~ g as its kernel reads an event: slot s of the
+// q q~ -> t t~ g record (q in, q~ in, t, t~, g out) takes the event's particle
+// src[s], with its momentum negated where neg[s] (a crossed parton: an outgoing
+// quark in the q~ slot, an outgoing antiquark in the q slot, an incoming gluon in
+// the g slot).  The direct channel is {{0, 1, 2, 3, 4}, {0, 0, 0, 0, 0}}.
+struct QqgCrossing {
+  signed char src[5];
+  signed char neg[5];
+};
+
 // Persistent multi-process launch (kernels_multi.cu): up to MULTI_MAX_BATCH
 // subprocess batches, up to MULTI_MAX_POINTS points per launch.
 constexpr int MULTI_MAX_BATCH = 8;
@@ -69,6 +79,7 @@ struct MultiTable {     // QCD batch: the QcdLaunch fields a tile reads
 
 struct MultiBatch {
   int kind;
+  QqgCrossing cross;    // q q~ -> t t~ g channels only
   int64_t nev, tile_begin, tile_end;   // work items [tile_begin, tile_end) of the launch
   const double* mom;
   const double* w_in;
@@ -113,7 +124,7 @@ int launch_gg_ttxgg(int mixed, int variant, const double* mom, const double* w_i
 int launch_qq_ttx(int mixed, const double* mom, const double* w_in, int64_t nev, const QcdLaunch& lp,
                   double* out, void* stream, const signed char* hel);
 int launch_qq_ttxg(int mixed, const double* mom, const double* w_in, int64_t nev, const QcdLaunch& lp,
-                   double* out, void* stream, const signed char* hel);
+                   double* out, void* stream, const signed char* hel, const QqgCrossing& cross);
 int launch_ee(const double* mom, const double* w_in, int64_t nev, const EwLaunch& lp,
               double* out, void* stream, const signed char* hel);
 

@@ -40,7 +40,9 @@ def test_init_errors(rex):
     assert lib.rex_init_process(b"ee_mumu", rex.MIXED, ctypes.byref(h)) == rex.REX_EUNSUPPORTED
 
 
-@pytest.mark.parametrize("name,npart", [("ee_mumu", 4), ("gg_ttx", 4), ("gg_ttxg", 5), ("gg_ttxgg", 6), ("qq_ttx", 4), ("qq_ttxg", 5)])
+@pytest.mark.parametrize("name,npart", [("ee_mumu", 4), ("gg_ttx", 4), ("gg_ttxg", 5), ("gg_ttxgg", 6), ("qq_ttx", 4), ("qq_ttxg", 5),
+                                        ("qxq_ttxg", 5), ("qg_ttxq", 5), ("gq_ttxq", 5), ("qxg_ttxqx", 5),
+                                        ("gqx_ttxqx", 5)])
 def test_handle_lifecycle(rex, name, npart):
     p = rex.Process(name)
     assert p.npart == npart
@@ -96,6 +98,11 @@ def test_helicity_exclusive_validation_before_any_device_work(rex):
     assert lib.rex_reweight_helicity(q._h, fake, None, fake, 10, pts, 1, fake, None) == rex.REX_EINVAL
     assert lib.rex_reweight_helicity(q._h, None, None, None, 0, pts, 1, None, None) == rex.REX_OK
     assert lib.rex_reweight_helicity(None, fake, fake, fake, 10, pts, 1, fake, None) == rex.REX_EINVAL
+    x = rex.Process("qg_ttxq")       # a crossing evaluates the helicity sum only
+    x.set_params(mt=173.0, alphas=0.118)
+    assert lib.rex_reweight_helicity(x._h, fake, fake, fake, 10, pts, 1, fake, None) == rex.REX_EUNSUPPORTED
+    assert b"direct channel only" in lib.rex_last_error()
+    x.close()
     g.close()
     q.close()
 
