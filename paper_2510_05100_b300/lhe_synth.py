@@ -26,6 +26,8 @@ PROCESSES = {
     "gg_ttxgg": ([21, 21], [6, -6, 21, 21]),
     "qq_ttx": ([2, -2], [6, -6]),
     "qq_ttxg": ([2, -2], [6, -6, 21]),
+    "qg_ttxq": ([2, 21], [6, -6, 2]),
+    "qxg_ttxqx": ([-2, 21], [6, -6, -2]),
 }
 _MASS = {6: 173.0, -6: 173.0}
 

@@ -90,3 +90,28 @@ def test_file_to_helicity_exclusive_weights(rex, tmp_path):
     bound = helicity_tolerance("qq_ttx", mom, hel, ORIG, pts, 1e-12, np.finfo(np.float64).eps / 2)
     err = np.abs(out - ref) / np.where(ref != 0.0, np.abs(ref), 1.0)
     assert np.all(err[~zero] < bound[~zero])
+
+
+def test_pp_ttxj_file_every_channel(rex, tmp_path):
+    """A p p -> t t~ + jet file with g g, q q~, q g and q~ g events in random beam order:
+    each channel extracted by its PDG codes (incoming parton order as listed) and
+    reweighted by its own process against the oracle."""
+    src = str(tmp_path / "ppj.lhe")
+    counts = {"gg_ttxg": 300, "qq_ttxg": 90, "qg_ttxq": 150, "qxg_ttxqx": 70}
+    info = lhe_synth.write_lhe(src, counts, seed=6)
+    pts = GRIDS["gg_ttxg"]
+    L = rex.Lhe(src)
+    for proc in counts:
+        pin, pout = lhe_synth.PROCESSES[proc]
+        mom, w, idx = L.extract(pin, pout)
+        assert mom.shape[0] == counts[proc]
+        gen, wgen, pos = info[proc]
+        order = np.argsort(pos)
+        assert np.array_equal(mom, gen[order]) and np.array_equal(w, wgen[order])
+        p = rex.Process(proc, 0)
+        p.set_params(ORIG)
+        out = p.reweight(torch.from_numpy(mom).cuda(), torch.from_numpy(w).cuda(), pts).cpu().numpy()
+        ref = oracle_rw.reweight(proc, mom[:8], w[:8], ORIG, pts)
+        assert np.max(np.abs(out[:8] / ref - 1)) < 1e-12, proc
+        p.close()
+    L.close()

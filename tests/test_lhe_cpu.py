@@ -25,7 +25,7 @@ def rex():
 def synth(tmp_path_factory):
     path = str(tmp_path_factory.mktemp("lhe") / "synth.lhe")
     info = lhe_synth.write_lhe(path, {"gg_ttxg": 6000, "gg_ttx": 3000, "ee_mumu": 700, "gg_ttxgg": 500,
-                                      "qq_ttx": 800, "qq_ttxg": 400}, seed=11,
+                                      "qq_ttx": 800, "qq_ttxg": 400, "qg_ttxq": 300, "qxg_ttxqx": 200}, seed=11,
                                with_initrwgt=True)
     return path, info
 
@@ -48,7 +48,7 @@ def test_synthetic_file_matches_the_oracle_and_the_generator(rex, synth, threads
     path, info = synth
     L = rex.Lhe(path, nthreads=threads)
     doc = olhe.read(path)
-    assert L.num_events == len(doc["events"]) == 11400
+    assert L.num_events == len(doc["events"]) == 11900
     for proc, (pin, pout) in lhe_synth.PROCESSES.items():
         got = L.extract(pin, pout)
         assert same(got, olhe.extract(doc, pin, pout)), proc
