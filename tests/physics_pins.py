@@ -398,3 +398,36 @@ def splitting_g_to_qq(x):
     """The spin- and colour-averaged g -> q q~ splitting function T_R (x^2 + (1 - x)^2),
     T_R = 1/2 (Altarelli & Parisi, Nucl. Phys. B126 (1977) 298)."""
     return 0.5 * (x * x + (1.0 - x) ** 2)
+
+
+def forward_quark_events(nphi, seed, m, sqrt_s, x, theta):
+    """q(pa) g(pb) -> Q Q~ q(pc) with the outgoing quark of energy (1 - x) E_a at angle
+    theta to pa (along +z), at nphi equally spaced azimuths around pa (which averages
+    out the cos(2 phi) spin correlation of a gluon entering the hard process); the Q Q~
+    pair recoils and decays at one seeded rest-frame direction for all azimuths.
+    Returns events [nphi, 5, 4] in the order (pa, pb, Q, Q~, pc)."""
+    rng = np.random.default_rng(seed)
+    e = sqrt_s / 2.0
+    pa = np.array([e, 0.0, 0.0, e])
+    pb = np.array([e, 0.0, 0.0, -e])
+    ct, pht = rng.uniform(-0.9, 0.9), rng.uniform(0, 2 * math.pi)
+    nt = np.array([math.sqrt(1 - ct * ct) * math.cos(pht), math.sqrt(1 - ct * ct) * math.sin(pht), ct])
+    out = []
+    for k in range(nphi):
+        phi = 2.0 * math.pi * k / nphi + 0.3
+        ec = (1.0 - x) * e
+        pc = ec * np.array([1.0, math.sin(theta) * math.cos(phi), math.sin(theta) * math.sin(phi), math.cos(theta)])
+        qq = pa + pb - pc
+        mm = math.sqrt(qq[0] ** 2 - qq[1:] @ qq[1:])
+        q = math.sqrt(mm * mm / 4.0 - m * m)
+        t_rest = np.concatenate([[mm / 2.0], q * nt])
+        tb_rest = np.concatenate([[mm / 2.0], -q * nt])
+        beta = qq[1:] / qq[0]
+        out.append([pa, pb, boost(t_rest[None], beta)[0], boost(tb_rest[None], beta)[0], pc])
+    return np.array(out)
+
+
+def splitting_q_to_g(x):
+    """The q -> g splitting function C_F (1 + (1 - x)^2) / x, x the gluon's momentum
+    fraction (Altarelli & Parisi, Nucl. Phys. B126 (1977) 298)."""
+    return (4.0 / 3.0) * (1.0 + (1.0 - x) ** 2) / x

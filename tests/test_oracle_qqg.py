@@ -135,3 +135,19 @@ def test_crossed_lorentz_invariance_and_scaling(process):
     q = pp.boost(pp.rotate(p, pp.random_rotation(5)), [-0.2, 0.35, 0.3])
     assert np.max(np.abs(qqg.me2_crossed(process, q, MT, 0.0, AS) / m - 1.0)) < 1e-12
     assert np.allclose(qqg.me2_crossed(process, p, MT, 0.0, 0.124) / m, (0.124 / AS) ** 3, rtol=1e-13)
+
+
+@pytest.mark.parametrize("x", [0.4, 0.75])
+def test_forward_quark_limit(x):
+    """The outgoing quark collinear to the incoming one (q -> q g*, the gluon with x p_q
+    entering g g -> t t~): averaged over the quark's azimuth, |M|^2 -> 8 pi alpha_s
+    P_gq(x) / (x 2 p_q.p_q') |M(g g -> t t~)|^2 with the Combridge closed form.  This
+    pins the t-channel gluon of the crossed light line, three-gluon vertex included;
+    before the average the azimuthal spin correlation of the gluon is visible."""
+    ev = pp.forward_quark_events(8, 36, MT, 1500.0, x, 1e-3)
+    got = qqg.me2_crossed("qg_ttxq", ev, MT, 0.0, AS)
+    t = 2.0 * pp.mdot(ev[:, 0], ev[:, 4])
+    born = pp.gg_qq_combridge(np.stack([x * ev[:, 0], ev[:, 1], ev[:, 2], ev[:, 3]], axis=1), MT, AS)
+    ratio = got / (8.0 * np.pi * AS * pp.splitting_q_to_g(x) / (x * t) * born)
+    assert abs(np.mean(ratio) - 1.0) < 2e-6     # measured 4e-8 .. 2e-7 at theta = 1e-3
+    assert np.std(ratio) > 1e-2                  # the cos(2 phi) correlation
