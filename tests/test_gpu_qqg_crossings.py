@@ -118,3 +118,32 @@ def test_every_channel_in_one_persistent_launch(rex, precision):
     for b, ref in zip(batches, single):
         assert np.max(rel(b[3].cpu().numpy(), ref)) < 1e-13
     m.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_full_size_pp_ttxj_sample(rex, precision):
+    """The benchmark's four-channel p p -> t t~ + jet sample (2^20 events, 16 points) in
+    one persistent launch, as it is timed: FP64 against the oracle on sampled events of
+    every channel; mixed against each channel's own single-process launch."""
+    spec = (("gg_ttxg", 786432, 13), ("qg_ttxq", 131072, 15), ("qxg_ttxqx", 65536, 16), ("qq_ttxg", 65536, 14))
+    pts = ps.grid_gg_ttxg()
+    batches, moms = [], []
+    for proc, n, seed in spec:
+        p = make(rex, proc, precision)
+        mom = ps.make_events(proc, n, seed)
+        moms.append(mom)
+        batches.append((p, dev(mom), torch.ones(n, dtype=torch.float64, device="cuda"),
+                        torch.zeros((n, len(pts)), dtype=torch.float64, device="cuda")))
+    m = rex.Multi(precision)
+    m.reweight(batches, pts)
+    torch.cuda.synchronize()
+    for (proc, n, _), mom, b in zip(spec, moms, batches):
+        got = b[3].cpu().numpy()
+        if precision == 0:
+            idx = np.concatenate([np.random.default_rng(13).choice(n, 5, replace=False), [0, n - 1]])
+            ref = oracle_rw.reweight(proc, mom[idx], np.ones(len(idx)), ORIG, pts)
+            assert np.max(rel(got[idx], ref)) < FP64_TOL, proc
+        else:
+            single = b[0].reweight(b[1], b[2], pts).cpu().numpy()
+            assert np.max(rel(got, single)) < 1e-13, proc
+    m.close()
