@@ -389,6 +389,7 @@ def run_pp_ttx_leg(dev, stream, pts, steps, world, barrier, max_over_ranks, spec
     desc = " + ".join(f"{n} {proc}" for proc, n, _ in spec)
     out = {"workload": f"{len(spec)}-channel sample of 2^20 events: {desc}, {len(pts)} points", "unit": UNIT,
            "steps": steps}
+    results = {}
     for name, prec in (("fp64", rex.FP64), ("mixed", rex.MIXED)):
         batches = []
         for proc, n, seed in spec:
@@ -406,6 +407,9 @@ def run_pp_ttx_leg(dev, stream, pts, steps, world, barrier, max_over_ranks, spec
 
         ms_multi = timed(lambda: m.replay(stream))
         ms_seq = timed(sequential)
+        m.replay(stream)
+        torch.cuda.synchronize(dev)
+        results[name] = [b[3].clone() for b in batches]
         m.close()
         for b in batches:
             b[0].close()
@@ -413,6 +417,12 @@ def run_pp_ttx_leg(dev, stream, pts, steps, world, barrier, max_over_ranks, spec
                      "kernel_launches_per_step": 1,
                      "sequential_value": rdist.job_throughput(units, world, ms_seq * 1e-3),
                      "sequential_ms_per_step": ms_seq}
+    # accuracy of the mixed mode on this sample: per channel, against the FP64 weights
+    acc = {}
+    for (proc, _, _), wm, wd in zip(spec, results["mixed"], results["fp64"]):
+        err = ((wm / wd) - 1.0).abs().amax(dim=1)
+        acc[proc] = {"max_rel_err": float(err.max()), "frac_events_above_1e-4": float((err > 1e-4).double().mean())}
+    out["mixed"]["vs_fp64"] = acc
     return out
 
 
