@@ -283,6 +283,14 @@ def _line_amplitude(term, kin, ubar_t, v_tb, p_t, mt, wt):
     return np.einsum("ni,ni->n", ubar_t, psi)
 
 
+def _real(p) -> np.ndarray:
+    """Momenta as a real array: FP64, unless they are given in extended precision
+    (np.longdouble), which is then kept through every step.  The extended path only
+    measures the FP64 evaluation's own rounding error (pins of the condition estimate)."""
+    p = np.asarray(p)
+    return p if p.dtype == np.longdouble else p.astype(np.float64)
+
+
 def me2_helicity(p: np.ndarray, mt: float, wt: float, alphas: float,
                  hel_g: tuple, lt: int, ltb: int) -> np.ndarray:
     """Colour-summed |M|^2 (not averaged) for one physical helicity configuration.
@@ -290,7 +298,7 @@ def me2_helicity(p: np.ndarray, mt: float, wt: float, alphas: float,
     hel_g: helicities of the gluons in row order (g1, g2, g5, ...); lt, ltb:
     helicities of the outgoing top and antitop.
     """
-    p = np.asarray(p, dtype=np.float64)
+    p = _real(p)
     npart = p.shape[1]
     ngl = npart - 2
     g = math.sqrt(4.0 * math.pi * alphas)
@@ -315,7 +323,7 @@ def me2(p: np.ndarray, mt: float, wt: float, alphas: float) -> np.ndarray:
 
     p: [N, 4+n, 4] physical momenta (E, px, py, pz); rows g g t t~ g...
     """
-    p = np.asarray(p, dtype=np.float64)
+    p = _real(p)
     nev, npart, _ = p.shape
     ngl = npart - 2
     nfinal_g = ngl - 2
@@ -325,7 +333,7 @@ def me2(p: np.ndarray, mt: float, wt: float, alphas: float) -> np.ndarray:
     gl_rows = [0, 1] + list(range(4, npart))
     p_out = [-p[:, 0], -p[:, 1]] + [p[:, r] for r in range(4, npart)]
     p_t, p_tb = p[:, 2], p[:, 3]
-    total = np.zeros(nev)
+    total = np.zeros(nev, dtype=p.dtype)
     for hel_g in itertools.product((-1, 1), repeat=ngl):
         eps = []
         for k, (row, lam) in enumerate(zip(gl_rows, hel_g)):
@@ -350,7 +358,7 @@ def gauge_check(p: np.ndarray, mt: float, which: int, hel_g: tuple, lt: int, ltb
 
     Returns (sum over events of the gauge-replaced value, sum of the physical one).
     """
-    p = np.asarray(p, dtype=np.float64)
+    p = _real(p)
     npart = p.shape[1]
     ngl = npart - 2
     g = math.sqrt(4.0 * math.pi * alphas)
@@ -383,7 +391,7 @@ def condition(p: np.ndarray, mt: float, wt: float, alphas: float) -> np.ndarray:
     terms me2 adds.  kappa >= 1; a result whose terms cancel has kappa >> 1, and a
     relative rounding error up to ~ eps * kappa is then expected of any evaluation
     order (a diagnostic for the tolerance rule, not a physical quantity)."""
-    p = np.asarray(p, dtype=np.float64)
+    p = _real(p)
     nev, npart, _ = p.shape
     ngl = npart - 2
     g = math.sqrt(4.0 * math.pi * alphas)
@@ -392,8 +400,8 @@ def condition(p: np.ndarray, mt: float, wt: float, alphas: float) -> np.ndarray:
     gl_rows = [0, 1] + list(range(4, npart))
     p_out = [-p[:, 0], -p[:, 1]] + [p[:, r] for r in range(4, npart)]
     p_t, p_tb = p[:, 2], p[:, 3]
-    total = np.zeros(nev)
-    absum = np.zeros(nev)
+    total = np.zeros(nev, dtype=p.dtype)
+    absum = np.zeros(nev, dtype=p.dtype)
     for hel_g in itertools.product((-1, 1), repeat=ngl):
         eps = []
         for k, (row, lam) in enumerate(zip(gl_rows, hel_g)):

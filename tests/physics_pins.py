@@ -431,3 +431,92 @@ def splitting_q_to_g(x):
     """The q -> g splitting function C_F (1 + (1 - x)^2) / x, x the gluon's momentum
     fraction (Altarelli & Parisi, Nucl. Phys. B126 (1977) 298)."""
     return (4.0 / 3.0) * (1.0 + (1.0 - x) ** 2) / x
+
+
+# ----------------------------------------------------------------------------
+# g g -> Q Q~ diagram by diagram, for the condition estimate
+# ----------------------------------------------------------------------------
+def _dirac_rep_gammas():
+    """gamma^mu in the Dirac (standard) representation: gamma^0 = diag(1, 1, -1, -1),
+    gamma^i = [[0, sigma_i], [-sigma_i, 0]] (a different basis from the oracle's chiral one)."""
+    sig = [np.array([[0, 1], [1, 0]], complex), np.array([[0, -1j], [1j, 0]], complex),
+           np.array([[1, 0], [0, -1]], complex)]
+    g = np.zeros((4, 4, 4), complex)
+    g[0] = np.diag([1, 1, -1, -1]).astype(complex)
+    for i in range(3):
+        g[i + 1, :2, 2:] = sig[i]
+        g[i + 1, 2:, :2] = -sig[i]
+    return g, sig
+
+
+def _helicity_two_spinors(n, sig):
+    """Eigenvectors of n.sigma for eigenvalues +1 and -1, from a numerical eigensolver
+    (their phases are arbitrary; the quantities built from them do not depend on phases)."""
+    m = n[0] * sig[0] + n[1] * sig[1] + n[2] * sig[2]
+    val, vec = np.linalg.eigh(m)
+    return {+1: vec[:, 1], -1: vec[:, 0]}
+
+
+def _circular_polarisations(k):
+    """(e1 + i lam e2)/sqrt(2) with e1, e2, k-hat right-handed and orthonormal; zero time
+    component.  Any such e1 gives the helicity vectors up to a phase."""
+    n = k[1:] / np.linalg.norm(k[1:])
+    ref = np.array([1.0, 0.0, 0.0]) if abs(n[0]) < 0.9 else np.array([0.0, 1.0, 0.0])
+    e1 = ref - (ref @ n) * n
+    e1 /= np.linalg.norm(e1)
+    e2 = np.cross(n, e1)
+    return {lam: np.concatenate([[0.0], (e1 + 1j * lam * e2) / math.sqrt(2.0)]) for lam in (1, -1)}
+
+
+def gg_qq_pair_terms(p, m, alphas):
+    """For one event g(k1) g(k2) -> Q(p1) Q~(p2) with on-shell heavy quarks: the terms
+    x[h, s, t] = Re(conj(A_s) G_st A_t) of the colour- and helicity-summed |M|^2, for the
+    three diagrams (t-channel colour t^a t^b, u-channel t^b t^a, s-channel f^abc t^c) and
+    the 16 helicity configurations h.  Written from the Feynman rules (quark-gluon vertex
+    i g gamma^mu t^a, gluon propagator -i g_{mu nu}/q^2, three-gluon vertex g f^abc [...],
+    all momenta incoming) in the Dirac representation, with helicity spinors
+    u = (sqrt(E+m) chi, lam sqrt(E-m) chi), v = (-lam sqrt(E-m) eta, sqrt(E+m) eta),
+    eta = chi_{-lam}, and G_st = sum over colours of conj(K_s) K_t."""
+    gam, sig = _dirac_rep_gammas()
+    metric = np.array([1.0, -1.0, -1.0, -1.0])
+    g = math.sqrt(4.0 * math.pi * alphas)
+    k1, k2, p1, p2 = p[0], p[1], p[2], p[3]
+
+    def slash_(a):
+        return np.einsum("m,mij->ij", (a * metric).astype(complex), gam)
+
+    def dot(a, b):
+        return a[0] * b[0] - a[1] * b[1] - a[2] * b[2] - a[3] * b[3]
+
+    def u_spinor(q, lam):
+        e, a = q[0], np.linalg.norm(q[1:])
+        chi = _helicity_two_spinors(q[1:] / a, sig)[lam]
+        return np.concatenate([math.sqrt(e + m) * chi, lam * math.sqrt(e - m) * chi])
+
+    def v_spinor(q, lam):
+        e, a = q[0], np.linalg.norm(q[1:])
+        eta = _helicity_two_spinors(q[1:] / a, sig)[-lam]
+        return np.concatenate([-lam * math.sqrt(e - m) * eta, math.sqrt(e + m) * eta])
+
+    def prop(q):
+        return (slash_(q) + m * np.eye(4)) / (dot(q, q) - m * m)
+
+    t = _t_matrices()
+    f = np.real(-2j * np.einsum("aij,bjk,cki->abc", t, t, t) + 2j * np.einsum("bij,ajk,cki->abc", t, t, t))
+    kcol = [np.einsum("aik,bkj->abij", t, t), np.einsum("bik,akj->abij", t, t),
+            np.einsum("abc,cij->abij", f, t)]
+    gmat = np.array([[np.sum(np.conj(ks) * kt) for kt in kcol] for ks in kcol])
+    eps1, eps2 = _circular_polarisations(k1), _circular_polarisations(k2)
+    s = dot(k1 + k2, k1 + k2)
+    out = []
+    for l1, l2, lq, lqb in itertools.product((1, -1), repeat=4):
+        e1, e2 = eps1[l1], eps2[l2]
+        ubar = np.conj(u_spinor(p1, lq)) @ gam[0]
+        v = v_spinor(p2, lqb)
+        a_t = -1j * g * g * ubar @ slash_(e1) @ prop(p1 - k1) @ slash_(e2) @ v
+        a_u = -1j * g * g * ubar @ slash_(e2) @ prop(p1 - k2) @ slash_(e1) @ v
+        vert = dot(e1, e2) * (k1 - k2) + 2.0 * dot(e1, k2) * e2 - 2.0 * dot(e2, k1) * e1
+        a_s = g * g * (ubar @ slash_(vert) @ v) / s
+        amp = np.array([a_t, a_u, a_s])
+        out.append(np.real(np.conj(amp)[:, None] * gmat * amp[None, :]))
+    return np.array(out)

@@ -280,6 +280,28 @@ def test_fp64_tolerance_rule_on_ill_conditioned_events(rex):
     assert np.all(err[2:] < FP64_TOL)          # the well-conditioned events meet 1e-12 outright
 
 
+def test_fp64_ill_conditioned_events_against_extended_precision(rex):
+    """The same eight events against the oracle's diagrams evaluated in extended precision
+    (np.longdouble), which removes the FP64 oracle's own rounding (6.3e-12 on event 75):
+    the kernel's error is then its own, and it stays within 64 eps (kappa_0 + kappa_j)."""
+    from oracle import qcd
+    mom = ps.make_events("gg_ttxgg", 512, 3)
+    grid = ps.grid_64()
+    idx = np.array([75, 146, 0, 100, 200, 300, 400, 511])
+    pts = [grid[13], grid[51]]
+    got = make("gg_ttxgg", rex).reweight(dev(mom[idx]), dev(np.ones(len(idx))), pts).cpu().numpy()
+    ext = mom[idx].astype(np.longdouble)
+    m0 = qcd.me2(ext, ORIG_QCD["mt"], 0.0, ORIG_QCD["alphas"])
+    eps = np.finfo(float).eps
+    k0 = qcd.condition(mom[idx], ORIG_QCD["mt"], 0.0, ORIG_QCD["alphas"])
+    for j, pt in enumerate(pts):
+        ref = (qcd.me2(ext, pt["mt"], 0.0, pt["alphas"]) / m0).astype(np.float64)
+        kj = qcd.condition(mom[idx], pt["mt"], 0.0, pt["alphas"])
+        err = np.abs(got[:, j] / ref - 1.0)
+        assert np.all(err <= 64 * eps * (k0 + kj)), (j, err, k0, kj)
+        assert np.all(err[2:] < FP64_TOL)
+
+
 def test_full_size_ee_every_event(rex):
     """e+e- -> mu+mu-: the full 4096-event sample at the new electroweak point, every event
     against the oracle."""
