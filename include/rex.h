@@ -46,7 +46,12 @@ extern "C" {
 #define REX_OK 0
 #define REX_EINVAL (-1)      /* bad handle, name, size, null or misaligned pointer */
 #define REX_ENOTINIT (-2)    /* rex_reweight before rex_set_params */
-#define REX_ECUDA (-3)       /* a CUDA call failed; see rex_last_error() */
+#define REX_ECUDA (-3)       /* a CUDA call failed; see rex_last_error().  The
+                              * reweighting entry points also return it, before
+                              * enqueueing anything, when a CUDA error from earlier
+                              * work is already pending on the calling thread
+                              * (cudaPeekAtLastError); the message says so and the
+                              * error is left pending for its owner. */
 #define REX_ENOMEM (-4)      /* a library-owned allocation failed */
 #define REX_EUNSUPPORTED (-5) /* precision mode or helicity-exclusive reweighting not
                                  available for this process */
@@ -250,11 +255,10 @@ void rex_multi_free(rex_multi *m);
 /* Allocation-free form of rex_reweight_multi.  The paper has no counterpart:
  * this entry point exists for callers that cannot call cudaMalloc, and so
  * cannot create the rex_multi handle (whose creation allocates its device
- * work counter).  Two kinds of caller are in that position: code that
- * records its work into a CUDA graph with global stream capture, where a
- * device allocation is an illegal call inside the captured region; and
- * applications whose device memory belongs to a framework's caching
- * allocator or to a fixed budget, which forbid allocations made outside it.
+ * work counter).  Such callers are applications whose device memory belongs
+ * to a framework's caching allocator or to a fixed budget (a serving process
+ * that sizes its memory once at start-up, a plug-in inside a host program that
+ * owns the device), which forbid allocations made outside it.
  *
  * Same computation and arguments as rex_reweight_multi, with the precision
  * given here instead of by a handle.  The caller still owns and passes every
@@ -423,13 +427,41 @@ int rex_surrogate_train(rex_surrogate *s, const double *momenta, const double *r
  * pred, err (device [nev][k] floats, may be NULL) receive the predicted log
  * ratio and error estimate; w_out (device [nev][k], may be NULL) receives
  * w_in * exp(pred) (exp in FP32), and then every event with some err > tau (or NaN) is
- * recomputed exactly with the handle exact (rex_reweight on those events).
+ * recomputed exactly with the handle exact (rex_reweight on those events), as is
+ * every event outside the guard (rex_surrogate_set_guard).
  * n_fallback (host, may be NULL) receives the number of such events.  With
  * w_out set the call synchronises stream (to size the fallback). */
 int rex_surrogate_reweight(rex_surrogate *s, rex_proc *exact, const double *momenta,
                            const double *w_in, int64_t nev, const rex_params *param_sets, int k,
                            float tau, double *w_out, float *pred, float *err,
                            int64_t *n_fallback, void *stream);
+
+/* Input-domain guard of the fallback: with y_min > 0, rex_surrogate_reweight also
+ * recomputes exactly every event whose final-gluon invariant
+ *     y = min over i in {1, 2, t, t~} of 2 k.p_i / s_hat   (k the final gluon,
+ *     s_hat = (p_1 + p_2)^2)
+ * is below y_min (or NaN).  Small y is the soft and collinear region, where |M|^2
+ * is singular and the weight ratio varies fastest with the top mass: the network's
+ * largest errors sit there and its error head does not see them.  y_min = 0 (the
+ * default) turns the guard off.  Not saved by rex_surrogate_save.
+ * Errors: REX_EINVAL (y_min outside [0, 1)). */
+int rex_surrogate_set_guard(rex_surrogate *s, double y_min);
+
+/* Choose the fallback threshold tau and the guard for a stated error bound, on a
+ * held-out set of nev events (device momenta [nev][5][4]) at k points: with the
+ * exact handle's ratios r (rex_reweight, unit weights) as truth, a kept pair
+ * "escapes" when |pred - log r| > bound.  Among the candidate guards (off, and the
+ * y quantiles 0.25 % .. 50 %) and every threshold, the call picks the pair that
+ * keeps the most events while the kept pairs' escape share stays <= max_escape,
+ * sets that guard on the handle and returns tau (pass it to rex_surrogate_reweight),
+ * the guard, and the fallback share and escape share on this set (host outputs;
+ * fallback_out, escape_out may be NULL).  If no event can be kept, tau is -inf
+ * (every event falls back).  Allocates work buffers of about 16 nev k bytes and
+ * synchronises stream.  Errors: REX_EINVAL, REX_ENOMEM, REX_ECUDA. */
+int rex_surrogate_calibrate(rex_surrogate *s, rex_proc *exact, const double *momenta, int64_t nev,
+                            const rex_params *param_sets, int k, double bound, double max_escape,
+                            float *tau_out, double *guard_out, double *fallback_out, double *escape_out,
+                            void *stream);
 
 /* Exact coupling part of the target.  At tree level |M|^2 is proportional to
  * alphas^power (power = 3 for g g -> t t~ g: one factor g_s^2 per QCD vertex
@@ -470,25 +502,6 @@ void rex_free_process(rex_proc *proc);
 
 /* Message of the calling thread's most recent error ("" if none). */
 const char *rex_last_error(void);
-
-/* Measurement tooling (the paper has no counterpart): issue-rate probe of
- * the FP64 (fp64 != 0) or FP32 fused multiply-add pipe of the current device.
- * Runs a few tens of milliseconds of independent FMA chains on every SM,
- * synchronises stream, and writes the best observed rate in flop/s
- * (an FMA counts two flops).  Errors: REX_EINVAL (null output), REX_ECUDA. */
-int rex_probe_fma(int fp64, double *flops_per_second, void *stream);
-
-/* Check of the integer-ALU float conversions the mixed-precision q q~ -> t t~
- * kernel uses in place of FP64-pipe conversions (B300 issues FP64 at 1/64 of the
- * FP32 rate): f32_out[i] = FP64 -> FP32 of in[i] (round to nearest even;
- * magnitudes below 2^-126 give a signed zero, overflow gives infinity, NaN stays
- * NaN), f64_out[i] = FP32 -> FP64 of f32_out[i] (exact) and, if f32_finite_out
- * is not null, f32_finite_out[i] = the kernel's FP64 -> FP32 conversion for
- * momenta (the same rounding; finiteness is checked once per event instead, so
- * its value is meaningful for finite in[i] below 2^128 only).  Device arrays of
- * n elements; enqueue only.  Errors: REX_EINVAL (n < 0, null array), REX_ECUDA. */
-int rex_probe_convert(const double *in, int64_t n, float *f32_out, double *f64_out,
-                      float *f32_finite_out, void *stream);
 
 /* Library version string. */
 const char *rex_version(void);

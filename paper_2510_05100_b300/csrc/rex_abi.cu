@@ -57,6 +57,17 @@ int cuda_fail(int err, const char* what) {
   return fail(REX_ECUDA, "%s: %s", what, cudaGetErrorString(static_cast<cudaError_t>(err)));
 }
 
+// A CUDA error left by earlier work on this thread (another library's failed launch,
+// an asynchronous fault) would otherwise be picked up by the launch check after this
+// call's own kernel and reported as that kernel's.  Report it before enqueueing
+// anything, under its own message, without clearing it.
+int pending_error() {
+  const cudaError_t e = cudaPeekAtLastError();
+  if (e == cudaSuccess) return REX_OK;
+  return fail(REX_ECUDA, "CUDA error pending from earlier work, before this call enqueued anything: %s",
+              cudaGetErrorString(e));
+}
+
 struct ProcInfo {
   const char* name;
   int kind;
@@ -267,6 +278,7 @@ int reweight_impl(rex_proc* p, const double* momenta, const double* w_in, int64_
     rc = p->kind == PROC_EE_MUMU ? check_ew_point(param_sets[j]) : check_qcd_point(param_sets[j]);
     if (rc) return rc;
   }
+  if ((rc = pending_error())) return rc;
   int j = 0;
   while (j < k) {
     int next = j;
@@ -337,6 +349,7 @@ int multi_impl(rex_multi* m, const rex_batch* batches, int nbatch, const rex_par
     return fail(REX_EINVAL, "nbatch must be in [1, %d] (got %d)", MULTI_MAX_BATCH, nbatch);
   if (!batches) return fail(REX_EINVAL, "null batch array");
   if (k < 0) return fail(REX_EINVAL, "k < 0");
+  if (k > 0 && !pts) return fail(REX_EINVAL, "null parameter array");
   int nee = 0;
   for (int i = 0; i < nbatch; ++i) {
     const rex_batch& b = batches[i];
@@ -358,7 +371,7 @@ int multi_impl(rex_multi* m, const rex_batch* batches, int nbatch, const rex_par
   }
   if (nee > 1) return fail(REX_EINVAL, "at most one ee_mumu batch per multi launch");
   if (k == 0) return REX_OK;
-  if (!pts) return fail(REX_EINVAL, "null parameter array");
+  if (const int pe = pending_error()) return pe;
   if (m->mode == REX_MULTI_STREAMS) {
     // fork: every batch's own tuned single-process kernel on its side stream; join
     cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -779,6 +792,7 @@ int rex_me2(rex_proc* proc, const double* momenta, int64_t nev, const rex_params
   if (nev == 0) return REX_OK;
   if (!momenta || !me2_out) return fail(REX_EINVAL, "null array pointer");
   if (!aligned16(momenta) || !aligned8(me2_out)) return fail(REX_EINVAL, "misaligned array pointer");
+  if ((rc = pending_error())) return rc;
   // evaluate with the point as the original: slot 0 only
   rex_proc tmp = *proc;
   tmp.orig = *point;

@@ -13,6 +13,7 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -328,6 +329,57 @@ __global__ void scatter_kernel(const int64_t* __restrict__ list, int n, int k, c
   w_out[list[i] * k + j] = src[t];
 }
 
+// Input-domain guard of the fallback.  For g g -> t t~ g the network's largest
+// errors sit where the final gluon is soft or collinear: there |M|^2 is singular and
+// the ratio varies fastest with the top mass.  y = min over the other four partons i
+// of 2 k.p_i / s_hat (k the final gluon, s_hat = (p_1 + p_2)^2) measures both
+// limits; events with y below the guard (or a NaN y) fall back.
+__device__ __forceinline__ double soft_collinear_y(const double* __restrict__ p) {
+  auto dot = [&](int a, int b) {
+    return p[4 * a] * p[4 * b] - p[4 * a + 1] * p[4 * b + 1] - p[4 * a + 2] * p[4 * b + 2] - p[4 * a + 3] * p[4 * b + 3];
+  };
+  const double shat = dot(0, 0) + 2.0 * dot(0, 1) + dot(1, 1);
+  double y = dot(4, 0);
+#pragma unroll
+  for (int i = 1; i < 4; ++i) y = fmin(y, dot(4, i));
+  return 2.0 * y / shat;
+}
+
+__global__ void guard_kernel(const double* __restrict__ mom, int64_t nev, double y0, int* __restrict__ flag) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nev) return;
+  const double y = soft_collinear_y(mom + i * 20);
+  if (!(y >= y0)) flag[i] = 1;
+}
+
+// Per-event calibration statistics over k points: the largest predicted error
+// (+inf if any is NaN), the number of points whose |pred - log(ratio)| exceeds the
+// bound (a non-positive or NaN ratio counts as exceeding it), and y.
+__global__ void calib_stats_kernel(const double* __restrict__ mom, const float* __restrict__ pred,
+                                   const float* __restrict__ err, const double* __restrict__ ratio, int64_t nev,
+                                   int k, double bound, float* __restrict__ emax, int* __restrict__ nbad,
+                                   double* __restrict__ yout) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nev) return;
+  float em = -INFINITY;
+  int bad = 0;
+  for (int j = 0; j < k; ++j) {
+    const float e = err[i * k + j];
+    em = (e == e) ? fmaxf(em, e) : INFINITY;
+    const double r = ratio[i * k + j];
+    const double d = r > 0.0 ? fabs((double)pred[i * k + j] - log(r)) : INFINITY;
+    bad += !(d <= bound);
+  }
+  emax[i] = em;
+  nbad[i] = bad;
+  yout[i] = soft_collinear_y(mom + i * 20);
+}
+
+__global__ void fill_kernel(double* __restrict__ x, int64_t n, double v) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) x[i] = v;
+}
+
 // ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
@@ -370,9 +422,11 @@ struct rex_surrogate {
   double as0 = 0.118;   // exact coupling part: apow * log(alphas / as0)
   int apow = 0;
   int kernel = REX_SURROGATE_FUSED;   // inference kernel
+  double guard_y = 0.0;   // events with soft_collinear_y < guard_y fall back (0: off)
   // work buffers, grown on demand
   DevBuf X, T, Z[4], A[4], dZa, dZb, part, pmt, pas, E1, P1, OFFS, flag, cnt, list, gmom, gw, gout;
   DevBuf PK, PTAB, STATUS;   // fused inference: packed weight images, point table, wait status
+  DevBuf CP, CE, CR, CW, CS1, CS2, CS3;   // calibration: pred, err, exact ratio, unit weights, per-event stats
 };
 
 namespace {
@@ -384,7 +438,8 @@ void release(rex_surrogate* s) {
   cudaFree(s->v);
   for (auto& w : s->wb) cudaFree(w);
   for (DevBuf* b : {&s->X, &s->T, &s->dZa, &s->dZb, &s->part, &s->pmt, &s->pas, &s->E1, &s->P1, &s->OFFS, &s->flag, &s->cnt,
-                    &s->list, &s->gmom, &s->gw, &s->gout, &s->PK, &s->PTAB, &s->STATUS})
+                    &s->list, &s->gmom, &s->gw, &s->gout, &s->PK, &s->PTAB, &s->STATUS, &s->CP, &s->CE, &s->CR,
+                    &s->CW, &s->CS1, &s->CS2, &s->CS3})
     b->release();
   for (int l = 0; l < 4; ++l) {
     s->Z[l].release();
@@ -802,9 +857,13 @@ int rex_surrogate_reweight(rex_surrogate* s, rex_proc* exact, const double* mome
                                         : infer_layered(s, momenta, w_in, nev, pts, k, tau, w_out, pred, err, st);
   if (rc) return rc;
   if (!w_out || !exact) return REX_OK;
-  // exact fallback of the flagged events
+  // exact fallback of the flagged events (predicted error above tau, or outside the guard)
   if ((e = s->cnt.ensure(8)) != cudaSuccess || (e = s->list.ensure(nev * 8)) != cudaSuccess)
     return sfail(REX_ENOMEM, "fallback buffers");
+  if (s->guard_y > 0.0) {
+    guard_kernel<<<(unsigned)((nev + 255) / 256), 256, 0, st>>>(momenta, nev, s->guard_y, s->flag.as<int>());
+    if ((e = cudaGetLastError()) != cudaSuccess) return scuda(e, "fallback guard");
+  }
   if ((e = cudaMemsetAsync(s->cnt.p, 0, 4, st)) != cudaSuccess) return scuda(e, "fallback counter");
   compact_kernel<<<(unsigned)((nev + 255) / 256), 256, 0, st>>>(s->flag.as<int>(), nev, s->cnt.as<int>(),
                                                                 s->list.as<int64_t>());
@@ -828,6 +887,102 @@ int rex_surrogate_reweight(rex_surrogate* s, rex_proc* exact, const double* mome
                                                                               s->gout.as<double>(), w_out);
   e = cudaGetLastError();
   return e == cudaSuccess ? REX_OK : scuda(e, "fallback scatter");
+}
+
+int rex_surrogate_set_guard(rex_surrogate* s, double y_min) {
+  const int rc = check_handle(s);
+  if (rc) return rc;
+  if (!(y_min >= 0.0 && y_min < 1.0)) return sfail(REX_EINVAL, "guard y_min must be in [0, 1) (got %g)", y_min);
+  s->guard_y = y_min;
+  return REX_OK;
+}
+
+int rex_surrogate_calibrate(rex_surrogate* s, rex_proc* exact, const double* momenta, int64_t nev,
+                            const rex_params* pts, int k, double bound, double max_escape, float* tau_out,
+                            double* guard_out, double* fallback_out, double* escape_out, void* stream) {
+  int rc = check_handle(s);
+  if (rc) return rc;
+  if (!exact || !momenta || !pts || !tau_out || !guard_out) return sfail(REX_EINVAL, "null argument");
+  if (nev < 1 || k < 1 || k > 4096) return sfail(REX_EINVAL, "need nev >= 1 and 1 <= k <= 4096");
+  if (!(bound > 0.0) || !(max_escape >= 0.0 && max_escape < 1.0))
+    return sfail(REX_EINVAL, "bound must be > 0 and max_escape in [0, 1)");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const size_t pairs = (size_t)nev * k;
+  cudaError_t e = s->CP.ensure(pairs * 4);
+  if (e == cudaSuccess) e = s->CE.ensure(pairs * 4);
+  if (e == cudaSuccess) e = s->CR.ensure(pairs * 8);
+  if (e == cudaSuccess) e = s->CW.ensure((size_t)nev * 8);
+  if (e == cudaSuccess) e = s->CS1.ensure((size_t)nev * 4);
+  if (e == cudaSuccess) e = s->CS2.ensure((size_t)nev * 4);
+  if (e == cudaSuccess) e = s->CS3.ensure((size_t)nev * 8);
+  if (e != cudaSuccess) return sfail(REX_ENOMEM, "calibration buffers: %s", cudaGetErrorString(e));
+  // the network's prediction and error estimate, and the exact ratio (unit weights)
+  rc = s->kernel == REX_SURROGATE_FUSED
+           ? infer_fused(s, momenta, nullptr, nev, pts, k, 0.f, nullptr, s->CP.as<float>(), s->CE.as<float>(), st)
+           : infer_layered(s, momenta, nullptr, nev, pts, k, 0.f, nullptr, s->CP.as<float>(), s->CE.as<float>(), st);
+  if (rc) return rc;
+  fill_kernel<<<(unsigned)((nev + 255) / 256), 256, 0, st>>>(s->CW.as<double>(), nev, 1.0);
+  rc = rex_reweight(exact, momenta, s->CW.as<double>(), nev, pts, k, s->CR.as<double>(), stream);
+  if (rc) return sfail(rc, "exact ratios: %s", rex_last_error());
+  calib_stats_kernel<<<(unsigned)((nev + 255) / 256), 256, 0, st>>>(
+      momenta, s->CP.as<float>(), s->CE.as<float>(), s->CR.as<double>(), nev, k, bound, s->CS1.as<float>(),
+      s->CS2.as<int>(), s->CS3.as<double>());
+  if ((e = cudaGetLastError()) != cudaSuccess) return scuda(e, "calibration statistics");
+  std::vector<float> emax(nev);
+  std::vector<int> nbad(nev);
+  std::vector<double> y(nev);
+  int status = 0;
+  e = cudaMemcpyAsync(emax.data(), s->CS1.p, nev * 4, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(nbad.data(), s->CS2.p, nev * 4, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(y.data(), s->CS3.p, nev * 8, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess && s->kernel == REX_SURROGATE_FUSED)
+    e = cudaMemcpyAsync(&status, s->STATUS.p, 4, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return scuda(e, "calibration copy");
+  if (status) return sfail(REX_ECUDA, "fused inference kernel: a bounded wait gave up");
+  // candidate guards: off, and the y below which a given share of the events lies
+  std::vector<double> ys;
+  for (double v : y)
+    if (v == v) ys.push_back(v);
+  std::sort(ys.begin(), ys.end());
+  std::vector<double> guards{0.0};
+  for (double q : {0.0025, 0.005, 0.01, 0.02, 0.03, 0.05, 0.075, 0.1, 0.15, 0.2, 0.25, 0.3, 0.4, 0.5})
+    if (!ys.empty()) guards.push_back(ys[(size_t)(q * (ys.size() - 1))]);
+  // for each guard: keep the events inside it in order of their largest predicted
+  // error, as far as the kept pairs' share above the bound stays within max_escape
+  double best_fb = 2.0, best_guard = 0.0, best_esc = 0.0;
+  float best_tau = -INFINITY;
+  std::vector<int64_t> order;
+  for (double g : guards) {
+    order.clear();
+    for (int64_t i = 0; i < nev; ++i)
+      if (g == 0.0 || y[i] >= g) order.push_back(i);
+    std::sort(order.begin(), order.end(), [&](int64_t a, int64_t b) { return emax[a] < emax[b]; });
+    int64_t bad = 0, keep = 0, cbad = 0;
+    for (size_t r = 0; r < order.size(); ++r) {
+      const float t = emax[order[r]];
+      if (!(t < INFINITY)) break;
+      cbad += nbad[order[r]];
+      // a threshold keeps every event with the same largest error: decide at the last of a tie
+      if (r + 1 < order.size() && emax[order[r + 1]] == t) continue;
+      if ((double)cbad > max_escape * (double)(r + 1) * k) continue;
+      keep = (int64_t)r + 1;
+      bad = cbad;
+    }
+    const double fb = 1.0 - (double)keep / (double)nev;
+    if (fb < best_fb) {
+      best_fb = fb;
+      best_guard = g;
+      best_tau = keep ? emax[order[keep - 1]] : -INFINITY;
+      best_esc = keep ? (double)bad / ((double)keep * k) : 0.0;
+    }
+  }
+  s->guard_y = best_guard;
+  *tau_out = best_tau;
+  *guard_out = best_guard;
+  if (fallback_out) *fallback_out = best_fb;
+  if (escape_out) *escape_out = best_esc;
+  return REX_OK;
 }
 
 // File format (native endianness): "REXSURR1", int64 parameter count, double

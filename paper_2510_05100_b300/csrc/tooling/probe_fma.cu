@@ -1,10 +1,10 @@
-// FMA-pipe throughput probe (measurement tooling for the roofline, not part of
-// the reweighting method).  Every thread runs NCHAIN independent dependent
+// FMA-pipe throughput probe (measurement tooling for the roofline, built into the
+// tooling library, not part of the reweighting ABI).  Every thread runs NCHAIN independent dependent
 // chains of fused multiply-adds; the grid covers every SM several times, so the
 // issue rate of the FP64 or FP32 FMA pipe is the only limit.
 #include <cuda_runtime.h>
 
-#include "../../include/rex.h"
+#include "../../../include/rex_tooling.h"
 
 namespace {
 
@@ -26,11 +26,11 @@ __global__ void __launch_bounds__(256) fma_chains(T* sink, int iters, T a, T b) 
 }  // namespace
 
 extern "C" int rex_probe_fma(int fp64, double* flops_per_second, void* stream) {
-  if (!flops_per_second) return REX_EINVAL;
+  if (!flops_per_second) return REX_TOOLING_EINVAL;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   int dev = 0, sms = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess) return REX_ECUDA;
-  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return REX_ECUDA;
+  if (cudaGetDevice(&dev) != cudaSuccess) return REX_TOOLING_ECUDA;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return REX_TOOLING_ECUDA;
   const int blocks = sms * 8, threads = 256;
   constexpr int NCHAIN = 8;
   const int iters = fp64 ? 512 : 16384;
@@ -48,7 +48,7 @@ extern "C" int rex_probe_fma(int fp64, double* flops_per_second, void* stream) {
     if (cudaEventSynchronize(e1) != cudaSuccess) {
       cudaEventDestroy(e0);
       cudaEventDestroy(e1);
-      return REX_ECUDA;
+      return REX_TOOLING_ECUDA;
     }
     float ms = 0.f;
     cudaEventElapsedTime(&ms, e0, e1);
@@ -58,5 +58,5 @@ extern "C" int rex_probe_fma(int fp64, double* flops_per_second, void* stream) {
   cudaEventDestroy(e1);
   const double flops = 2.0 * NCHAIN * (double)iters * blocks * threads;
   *flops_per_second = flops / (best * 1e-3);
-  return cudaGetLastError() == cudaSuccess ? REX_OK : REX_ECUDA;
+  return cudaGetLastError() == cudaSuccess ? REX_TOOLING_OK : REX_TOOLING_ECUDA;
 }

@@ -19,6 +19,8 @@ from typing import Iterable, Sequence
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "librex_b300.so")
+TOOLING_LIB_PATH = os.path.join(HERE, "librex_tooling_b300.so")
+TOOLING_EXPORTS = ("rex_probe_fma", "rex_probe_convert")
 
 REX_OK = 0
 REX_EINVAL = -1
@@ -38,12 +40,13 @@ SURROGATE_LAYERED = 1
 EXPORTS = (
     "rex_init_process", "rex_process_npart", "rex_set_flags", "rex_set_params", "rex_reweight_helicity",
     "rex_reweight", "rex_reweight_host", "rex_me2", "rex_free_process",
-    "rex_last_error", "rex_version", "rex_probe_fma", "rex_probe_convert", "rex_num_variants", "rex_get_variant",
+    "rex_last_error", "rex_version", "rex_num_variants", "rex_get_variant",
     "rex_set_variant", "rex_autotune", "rex_multi_create", "rex_reweight_multi", "rex_multi_capture",
     "rex_multi_replay", "rex_multi_free", "rex_reweight_multi_noalloc", "rex_multi_set_mode",
     "rex_surrogate_num_params", "rex_surrogate_last_error", "rex_surrogate_create",
     "rex_surrogate_set_weights", "rex_surrogate_get_weights", "rex_surrogate_loss_grad",
     "rex_surrogate_train", "rex_surrogate_reweight", "rex_surrogate_set_exact_alphas", "rex_surrogate_set_kernel",
+    "rex_surrogate_set_guard", "rex_surrogate_calibrate",
     "rex_surrogate_save", "rex_surrogate_load",
     "rex_surrogate_free",
     "rex_xsec_last_error", "rex_xsec_create", "rex_xsec_reset", "rex_xsec_accumulate", "rex_xsec_result",
@@ -108,10 +111,6 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.rex_free_process.restype = None
     lib.rex_last_error.argtypes = []
     lib.rex_last_error.restype = ctypes.c_char_p
-    lib.rex_probe_fma.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_double), vp]
-    lib.rex_probe_fma.restype = ctypes.c_int
-    lib.rex_probe_convert.argtypes = [vp, i64, vp, vp, vp, vp]
-    lib.rex_probe_convert.restype = ctypes.c_int
     lib.rex_num_variants.argtypes = [vp]
     lib.rex_num_variants.restype = ctypes.c_int
     lib.rex_get_variant.argtypes = [vp]
@@ -162,6 +161,11 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.rex_surrogate_load.restype = ctypes.c_int
     lib.rex_surrogate_set_kernel.argtypes = [vp, ctypes.c_int]
     lib.rex_surrogate_set_kernel.restype = ctypes.c_int
+    lib.rex_surrogate_set_guard.argtypes = [vp, ctypes.c_double]
+    lib.rex_surrogate_set_guard.restype = ctypes.c_int
+    lib.rex_surrogate_calibrate.argtypes = [vp, vp, vp, i64, pp, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                            fp, dp, dp, dp, vp]
+    lib.rex_surrogate_calibrate.restype = ctypes.c_int
     lib.rex_xsec_last_error.argtypes = []
     lib.rex_xsec_last_error.restype = ctypes.c_char_p
     lib.rex_xsec_create.argtypes = [ctypes.c_int, ctypes.POINTER(vp)]
@@ -433,6 +437,24 @@ class Surrogate:
         """Make the alphas^power dependence of |M|^2 exact; the network learns the rest."""
         _scheck(load().rex_surrogate_set_exact_alphas(self._h, float(alphas0), int(power)))
 
+    def set_guard(self, y_min: float) -> None:
+        """Always recompute exactly the events whose final-gluon invariant
+        min_i 2 k.p_i / s_hat is below y_min (0 turns the guard off)."""
+        _scheck(load().rex_surrogate_set_guard(self._h, float(y_min)))
+
+    def calibrate(self, exact: "Process", momenta, points: Sequence[dict], bound: float, max_escape: float,
+                  stream=None) -> dict:
+        """rex_surrogate_calibrate on held-out device momenta: picks tau and the guard that keep
+        the most events with at most max_escape of the kept pairs off by more than bound in
+        log weight; sets the guard and returns {tau, guard, fallback_rate, escape_rate}."""
+        tau = ctypes.c_float()
+        guard, fb, esc = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        _scheck(load().rex_surrogate_calibrate(self._h, exact._h, _ptr(momenta), momenta.shape[0],
+                                               _param_array(points), len(points), float(bound), float(max_escape),
+                                               ctypes.byref(tau), ctypes.byref(guard), ctypes.byref(fb),
+                                               ctypes.byref(esc), _stream_ptr(stream)))
+        return {"tau": tau.value, "guard": guard.value, "fallback_rate": fb.value, "escape_rate": esc.value}
+
     def save(self, path: str) -> None:
         _scheck(load().rex_surrogate_save(self._h, os.fsencode(path)))
 
@@ -605,10 +627,35 @@ def xsec_merge_states(a, b, k: int):
     return out
 
 
+_tooling = None
+
+
+def load_tooling(path: str = TOOLING_LIB_PATH) -> ctypes.CDLL:
+    """Load librex_tooling_b300.so, the measurement and test probes (include/rex_tooling.h)."""
+    global _tooling
+    if _tooling is not None:
+        return _tooling
+    if not os.path.exists(path):
+        raise ImportError(f"{path} is missing: build it with `python -m paper_2510_05100_b300.build`")
+    lib = ctypes.CDLL(path)
+    vp, i64 = ctypes.c_void_p, ctypes.c_int64
+    lib.rex_probe_fma.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_double), vp]
+    lib.rex_probe_fma.restype = ctypes.c_int
+    lib.rex_probe_convert.argtypes = [vp, i64, vp, vp, vp, vp]
+    lib.rex_probe_convert.restype = ctypes.c_int
+    _tooling = lib
+    return lib
+
+
+def _tcheck(rc: int, what: str) -> None:
+    if rc != 0:
+        raise RexError(rc, f"{what} failed")
+
+
 def probe_fma(fp64: bool, stream=None) -> float:
     """Measured FMA-pipe rate of the current device in flop/s (FP64 or FP32)."""
     out = ctypes.c_double()
-    _check(load().rex_probe_fma(1 if fp64 else 0, ctypes.byref(out), _stream_ptr(stream)))
+    _tcheck(load_tooling().rex_probe_fma(1 if fp64 else 0, ctypes.byref(out), _stream_ptr(stream)), "rex_probe_fma")
     return out.value
 
 
@@ -619,8 +666,8 @@ def probe_convert(values, stream=None):
     f32 = torch.empty(values.shape, dtype=torch.float32, device=values.device)
     f64 = torch.empty(values.shape, dtype=torch.float64, device=values.device)
     fin = torch.empty(values.shape, dtype=torch.float32, device=values.device)
-    _check(load().rex_probe_convert(_ptr(values), values.numel(), _ptr(f32), _ptr(f64), _ptr(fin),
-                                    _stream_ptr(stream)))
+    _tcheck(load_tooling().rex_probe_convert(_ptr(values), values.numel(), _ptr(f32), _ptr(f64), _ptr(fin),
+                                             _stream_ptr(stream)), "rex_probe_convert")
     return f32, f64, fin
 
 

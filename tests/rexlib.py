@@ -6,6 +6,7 @@ import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 HEADER = os.path.join(ROOT, "include", "rex.h")
+TOOLING_HEADER = os.path.join(ROOT, "include", "rex_tooling.h")
 
 
 def ensure_built():
@@ -15,8 +16,8 @@ def ensure_built():
     return rex
 
 
-def declared_symbols():
-    text = open(HEADER).read()
+def declared_symbols(header=HEADER):
+    text = open(header).read()
     return sorted(set(re.findall(r"^(?:int64_t|int|void|const char \*)\s*\*?\s*(rex_\w+)\s*\(", text, re.M)))
 
 

@@ -29,6 +29,18 @@ def test_library_exports_every_declared_symbol(rex):
     assert "sm_103a" in rex.version()
 
 
+def test_tooling_library_exports_its_header():
+    """The measurement and test probes live in their own library, outside the reweighting ABI."""
+    from rexlib import TOOLING_HEADER
+    rex = ensure_built()
+    lib = rex.load_tooling()
+    syms = declared_symbols(TOOLING_HEADER)
+    assert set(syms) == set(rex.TOOLING_EXPORTS)
+    for s in syms:
+        assert hasattr(lib, s), s
+        assert s not in declared_symbols()
+
+
 def test_init_errors(rex):
     lib = rex.load()
     h = ctypes.c_void_p()

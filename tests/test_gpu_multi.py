@@ -108,6 +108,15 @@ def test_multi_validation(rex):
         m.replay()                                    # nothing captured
     m.reweight([(p64, mom[:0], w[:0], wo[:0])], pts)  # empty batch: no-op
     m.reweight([(p64, mom, w, wo)], [])               # no points: no-op
+    # a NULL parameter array with k = 1 is rejected before any point is read
+    import ctypes
+    lib = rex.load()
+    barr = (rex.Batch * 1)(rex.Batch(p64._h.value, mom.data_ptr(), w.data_ptr(), 4, wo.data_ptr()))
+    assert lib.rex_reweight_multi(m._h, barr, 1, None, 1, None) == rex.REX_EINVAL
+    assert b"null parameter array" in lib.rex_last_error()
+    assert lib.rex_multi_capture(m._h, barr, 1, None, 1) == rex.REX_EINVAL
+    assert lib.rex_reweight_multi_noalloc(barr, 1, None, 1, 0, None) == rex.REX_EINVAL
+    assert b"null parameter array" in lib.rex_last_error()
 
 
 @pytest.mark.parametrize("subset", [("gg_ttx", "qq_ttx"), ("ee_mumu", "gg_ttx", "qq_ttx"),

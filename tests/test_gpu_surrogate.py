@@ -251,6 +251,54 @@ def test_what_the_surrogate_gains_over_the_exact_path(rex, trained):
     assert t_net < t_fp64
 
 
+def soft_collinear_y(mom):
+    """The guard variable, written out here: min over i in {1, 2, t, t~} of 2 k.p_i / s_hat."""
+    def dot(a, b):
+        return a[..., 0] * b[..., 0] - (a[..., 1:] * b[..., 1:]).sum(-1)
+    shat = dot(mom[:, 0] + mom[:, 1], mom[:, 0] + mom[:, 1])
+    return 2.0 * np.min(np.stack([dot(mom[:, 4], mom[:, i]) for i in range(4)]), axis=0) / shat
+
+
+def test_calibrated_fallback_holds_the_stated_bound_on_held_out_events(rex, trained):
+    """The stated error bound of the surrogate: calibrated on one held-out set (tau on the
+    error head and the soft/collinear guard, at most 5e-4 of the kept pairs off by more
+    than the bound in |log w|), it keeps the escape rate of the pairs it does not send
+    back to the exact path at or below 1e-3 on an independent held-out seed, measured
+    against the FP64 kernel; every fallback row is exact."""
+    s, exact, pts, _ = trained
+    bound = 5e-2
+    n = 1 << 15
+    mom_cal = torch.from_numpy(ps.make_events("gg_ttxg", n, 4141)).cuda()
+    cal = s.calibrate(exact, mom_cal, pts, bound, 5e-4)
+    assert cal["escape_rate"] <= 5e-4 and 0.0 <= cal["fallback_rate"] < 1.0, cal
+    mom_np = ps.make_events("gg_ttxg", n, 4242)
+    mom = torch.from_numpy(mom_np).cuda()
+    w = torch.from_numpy(np.random.default_rng(3).uniform(0.5, 2.0, n)).cuda()
+    ref = exact.reweight(mom, w, pts)
+    out = torch.empty_like(ref)
+    errp = torch.empty((n, len(pts)), dtype=torch.float32, device="cuda")
+    nfb = s.reweight(mom, w, pts, tau=cal["tau"], exact=exact, w_out=out, err=errp)
+    flagged = (errp > cal["tau"]).any(dim=1).cpu().numpy() | ~(soft_collinear_y(mom_np) >= cal["guard"])
+    assert nfb == int(flagged.sum())
+    dlog = (out / ref).log().abs().cpu().numpy()
+    assert np.all(dlog[flagged] == 0.0)                       # fallback rows are the exact ones
+    kept = dlog[~flagged]
+    escape = float((kept > bound).mean())
+    print(f"\ncalibration: tau {cal['tau']:.4g}, guard {cal['guard']:.4g}, fallback {cal['fallback_rate']:.3f}; "
+          f"held-out: fallback {nfb / n:.3f}, escape {escape:.2e}, max kept {kept.max():.3g}")
+    assert kept.size > 0 and escape <= 1e-3
+    s.set_guard(0.0)
+
+
+def test_guard_validation(rex, trained):
+    s = trained[0]
+    with pytest.raises(rex.RexError):
+        s.set_guard(-0.1)
+    with pytest.raises(rex.RexError):
+        s.set_guard(1.0)
+    s.set_guard(0.0)
+
+
 def test_save_and_load_round_trip(rex, trained, tmp_path):
     """A saved network loads into a fresh handle with identical weights, coupling
     setting and predictions; a foreign file is refused."""

@@ -1,11 +1,14 @@
 """rex_reweight_multi_noalloc, the allocation-free multi-process entry point.
 
-Callers that cannot allocate device memory (graph capture in global mode,
-framework-owned memory budgets) use this entry point instead of a rex_multi
-handle.  The test calls it twice in a row through the C ABI and checks every
-output against the single-process entry point rex_reweight.  It lives in its
-own file, collected last, and sets everything up itself, so it passes both
-alone in a fresh process and after the other tests.
+Callers whose device memory belongs to a framework's allocator or to a fixed
+budget cannot allocate device memory themselves, and use this entry point instead
+of a rex_multi handle (whose creation allocates).  The test calls it twice in a
+row through the C ABI, over every process class including the q q~ and q g
+channels, checks every output against the single-process entry point
+rex_reweight, and checks that the device's free memory does not change across a
+call; one more call goes through the Python binding.  It lives in its own file,
+collected last, and sets everything up itself, so it passes both alone in a fresh
+process and after the other tests.
 """
 import ctypes
 
@@ -36,7 +39,8 @@ def test_noalloc_matches_single_process_entry_point_twice(rex):
     parr = (rex.Params * len(pts))(*[rex.params(p) for p in pts])
     for precision in (0, 1):
         items = []
-        for proc, n, seed in (("ee_mumu", 130, 1), ("gg_ttx", 97, 2), ("gg_ttxg", 45, 3), ("gg_ttxgg", 13, 4)):
+        for proc, n, seed in (("ee_mumu", 130, 1), ("gg_ttx", 97, 2), ("gg_ttxg", 45, 3), ("gg_ttxgg", 13, 4),
+                              ("qq_ttx", 77, 5), ("qq_ttxg", 41, 6), ("qg_ttxq", 39, 7)):
             h = rex.Process(proc, 0 if proc == "ee_mumu" else precision)
             h.set_params(ps.EE_ORIGINAL if proc == "ee_mumu" else ORIG_QCD)
             mom = torch.from_numpy(ps.make_events(proc, n, seed)).cuda()
@@ -50,13 +54,22 @@ def test_noalloc_matches_single_process_entry_point_twice(rex):
             for i, ((h, mom, w, _), o) in enumerate(zip(items, outs)):
                 barr[i] = rex.Batch(h._h.value, mom.data_ptr(), w.data_ptr(), mom.shape[0], o.data_ptr())
             stream = torch.cuda.current_stream().cuda_stream
+            torch.cuda.synchronize()
+            free0 = torch.cuda.mem_get_info()[0]
             rc = lib.rex_reweight_multi_noalloc(barr, len(items), parr, len(pts), precision,
                                                 ctypes.c_void_p(stream))
             assert rc == 0, lib.rex_last_error()
             torch.cuda.synchronize()
+            assert torch.cuda.mem_get_info()[0] == free0, "device memory changed across the call"
             for (h, _, _, ref), o in zip(items, outs):
                 got = o.cpu().numpy()
                 assert np.max(np.abs(got / ref - 1.0)) < TOL, (h.name, precision, call)
+        # the same launch through the Python binding
+        outs = [torch.full((it[1].shape[0], len(pts)), -1.0, dtype=torch.float64, device="cuda") for it in items]
+        rex.reweight_multi_noalloc([(h, mom, w, o) for (h, mom, w, _), o in zip(items, outs)], pts, precision)
+        torch.cuda.synchronize()
+        for (h, _, _, ref), o in zip(items, outs):
+            assert np.max(np.abs(o.cpu().numpy() / ref - 1.0)) < TOL, (h.name, precision, "binding")
 
 
 def test_noalloc_rejects_more_points_than_its_counter_covers(rex):
