@@ -319,6 +319,85 @@ def run_multi_leg(dev, stream, steps, world, barrier, max_over_ranks):
             "steps": steps}
 
 
+# many channels of small event counts: the regime where one launch per subprocess leaves
+# the GPU latency bound (paper Sec. 4.2); crossed channels use the q q~ -> t t~ g events
+SMALL_MULTI_BATCHES = (("gg_ttx", 8000, 71, "gg_ttx"), ("gg_ttxg", 4000, 72, "gg_ttxg"),
+                       ("gg_ttxgg", 1000, 73, "gg_ttxgg"), ("qq_ttx", 8000, 74, "qq_ttx"),
+                       ("qq_ttxg", 3000, 75, "qq_ttxg"), ("qg_ttxq", 2000, 76, "qq_ttxg"),
+                       ("gq_ttxq", 2000, 77, "qq_ttxg"), ("qxg_ttxqx", 1000, 78, "qq_ttxg"))
+
+
+def run_small_multi_leg(dev, stream, steps, world, barrier, max_over_ranks):
+    """Eight subprocess batches of 10^3 - 10^4 events x 64 points (mixed precision): one
+    graph of persistent kernels (one per register class present) against a graph of one
+    single-process launch per batch (captured with the same stream), the streams mode's
+    graph of per-process launches on forked streams, and plain sequential launches."""
+    import torch
+    from paper_2510_05100_b300 import rex
+
+    pts = ps.grid_64()
+    batches = []
+    for proc, n, seed, gen in SMALL_MULTI_BATCHES:
+        h = rex.Process(proc, rex.MIXED)
+        h.set_params(ORIGINAL)
+        mom = torch.from_numpy(ps.make_events(gen, n, seed)).to(dev)
+        batches.append((h, mom, torch.ones(n, dtype=torch.float64, device=dev),
+                        torch.empty((n, len(pts)), dtype=torch.float64, device=dev)))
+    units = sum(b[1].shape[0] for b in batches) * len(pts)
+    m = rex.Multi(rex.MIXED)
+    m.capture(batches, pts)
+    ms_streams = rex.Multi(rex.MIXED, rex.MULTI_STREAMS)
+    ms_streams.capture(batches, pts)
+
+    def sequential_step(st=stream):
+        for h, mom, w, wo in batches:
+            h.reweight(mom, w, pts, w_out=wo, stream=st)
+
+    # the same per-batch launches captured into one CUDA graph
+    cap = torch.cuda.Stream(dev)
+    cap.wait_stream(torch.cuda.current_stream(dev))
+    sequential_step(cap)
+    torch.cuda.synchronize(dev)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=cap):
+        sequential_step(cap)
+
+    def timed(fn):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize(dev)
+        barrier()
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        for _ in range(steps):
+            fn()
+        t1.record(stream)
+        torch.cuda.synchronize(dev)
+        barrier()
+        return max_over_ranks(t0.elapsed_time(t1)) / steps
+
+    ms_persistent = timed(lambda: m.replay(stream))
+    ms_seq_graph = timed(lambda: g.replay())
+    ms_streams_graph = timed(lambda: ms_streams.replay(stream))
+    ms_seq = timed(sequential_step)
+    m.close()
+    ms_streams.close()
+    for b in batches:
+        b[0].close()
+    desc = " + ".join(f"{n} {proc}" for proc, n, _, _ in SMALL_MULTI_BATCHES)
+    val = lambda ms: rdist.job_throughput(units, world, ms * 1e-3)   # noqa: E731
+    return {"workload": f"{desc}, 64 points each, mixed precision", "unit": UNIT, "steps": steps,
+            "persistent_graph": {"value": val(ms_persistent), "ms_per_step": ms_persistent},
+            "per_process_graph": {"value": val(ms_seq_graph), "ms_per_step": ms_seq_graph},
+            "streams_graph": {"value": val(ms_streams_graph), "ms_per_step": ms_streams_graph},
+            "sequential_launches": {"value": val(ms_seq), "ms_per_step": ms_seq},
+            "note": "persistent_graph: one graph of persistent kernels, one per register class present; "
+                    "per_process_graph: one single-process launch per batch, captured; streams_graph: "
+                    "per-process launches on forked streams, captured; sequential_launches: per-process "
+                    "launches from the host"}
+
+
 def run_qqg_leg(dev, stream, pts, steps, nev=NEV):
     """q q~ -> t t~ g (the quark-initiated p p -> t t~ + jet channel) on the headline's
     points: nev events per launch in FP64 and mixed precision, CUDA-event timed, with the
@@ -673,10 +752,30 @@ def run_small_configs_leg(dev, stream, steps):
     proc = rex.Process("ee_mumu", rex.FP64)
     proc.set_params(ps.EE_ORIGINAL)
     t = time_launches(proc, mom, w_in, [ps.EE_NEW], w_out, 200)
+    # the same launches replayed from a CUDA graph: device time without the host's call overhead
+    cap = torch.cuda.Stream(dev)
+    cap.wait_stream(torch.cuda.current_stream(dev))
+    proc.reweight(mom, w_in, [ps.EE_NEW], w_out=w_out, stream=cap)
+    torch.cuda.synchronize(dev)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=cap):
+        for _ in range(50):
+            proc.reweight(mom, w_in, [ps.EE_NEW], w_out=w_out, stream=cap)
+    graph.replay()
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(4):
+        graph.replay()
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    t_graph = e0.elapsed_time(e1) * 1e-3 / 200
     proc.close()
     out["ee_mumu"] = {"workload": "e+ e- -> mu+ mu- (gamma + Z), sqrt(s) = 500 GeV, 4096 events x 1 point "
                                   "(mZ 91.1876 -> 91.0, wZ 2.4952 -> 2.6, sin2thetaW 0.2312 -> 0.2300), FP64",
                       "value": nee / t, "unit": UNIT, "us_per_launch": t * 1e6, "launches_timed": 200,
+                      "graph_replay": {"value": nee / t_graph, "us_per_launch": t_graph * 1e6,
+                                       "note": "50 launches captured in one CUDA graph, replayed 4 times"},
                       "stated_rel_error": 1e-12,
                       "roofline": {"bound": "latency", "note": "28 events per SM: one launch is its fixed cost "
                                    "(launch, one block wave, the epilogue), no pipe is the limit"}}
@@ -913,6 +1012,8 @@ def run_ours(args, world, rank, local):
 
     multi = None if args.no_multi else run_multi_leg(dev, stream, max(3, args.steps // 2), world, barrier,
                                                      max_over_ranks)
+    small_multi = None if args.no_multi else run_small_multi_leg(dev, stream, max(5, args.steps), world, barrier,
+                                                                 max_over_ranks)
     surrogate = None if args.no_surrogate else run_surrogate_leg(dev, stream, world, max_over_ranks)
 
     cpu = None
@@ -940,7 +1041,8 @@ def run_ours(args, world, rank, local):
                         "entry_point": "rex_reweight_host (pinned host buffers)"},
                 "gpu_launches": args.steps, "roofline": roofline, "cpu_baseline": cpu, "modes": extra,
                 "multi": multi, "surrogate": surrogate, "xsec": xsec, "lhe": lhe_leg, "qq_ttx": qq_leg,
-                "qq_ttxg": qqg_leg, "pp_ttx": pp_leg, "pp_ttxj": ppj_leg, "configs_1_2": small}
+                "qq_ttxg": qqg_leg, "pp_ttx": pp_leg, "pp_ttxj": ppj_leg, "configs_1_2": small,
+                "multi_small_batches": small_multi}
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist

@@ -155,10 +155,14 @@ int rex_reweight(rex_proc *proc, const double *momenta, const double *w_in,
  *               helicities in the frame of the momenta, +1 / -1 (a positive value
  *               reads as +1, any other as -1); no alignment requirement
  *   other arguments as rex_reweight.
- * Processes: ee_mumu, qq_ttx and qq_ttxg, whose kernels evaluate helicity
- * amplitudes (the q q~ -> t t~ g gluon in the helicity basis); the g g processes
- * sum real linear gluon polarisations and the crossings of qq_ttxg use the
- * helicity sum's freedom in their wavefunctions: both return REX_EUNSUPPORTED.
+ * Processes: ee_mumu, qq_ttx and qq_ttxg evaluate helicity amplitudes directly
+ * (the q q~ -> t t~ g gluon in the helicity basis).  gg_ttx, gg_ttxg and gg_ttxgg
+ * evaluate the jamps of every real linear polarisation configuration of the
+ * gluons (one lane each) and combine them into the event's helicity amplitude,
+ * e_lambda = (e1 - i lambda e2)/sqrt(2) up to a phase, before the colour sum; only
+ * the event's own top and antitop helicities are evaluated.  The crossings of
+ * qq_ttxg use the helicity sum's freedom in their wavefunctions and return
+ * REX_EUNSUPPORTED.
  * Enqueue only.  Errors: REX_EUNSUPPORTED, REX_EINVAL (as rex_reweight, null
  * helicities), REX_ENOTINIT, REX_ECUDA. */
 int rex_reweight_helicity(rex_proc *proc, const double *momenta, const signed char *helicities,

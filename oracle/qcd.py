@@ -318,6 +318,24 @@ def me2_helicity(p: np.ndarray, mt: float, wt: float, alphas: float,
     return np.real(np.einsum("ns,st,nt->n", amps.conj(), gmat, amps))
 
 
+def me2_helicity_per_event(p: np.ndarray, mt: float, wt: float, alphas: float, hel: np.ndarray) -> np.ndarray:
+    """Each event's own helicity term of me2, averaged as me2 is (so that the sum over
+    every configuration gives me2): hel[N, npart] in particle order g g t t~ g.., +1 / -1
+    (a positive entry reads as +1).  Events are grouped by configuration and each group
+    evaluated with me2_helicity."""
+    p = _real(p)
+    hel = np.where(np.asarray(hel) > 0, 1, -1)
+    nev, npart, _ = p.shape
+    ngl = npart - 2
+    gl_rows = [0, 1] + list(range(4, npart))
+    out = np.zeros(nev, dtype=p.dtype)
+    configs, inverse = np.unique(hel, axis=0, return_inverse=True)
+    for c, h in enumerate(configs):
+        idx = np.nonzero(inverse.reshape(-1) == c)[0]
+        out[idx] = me2_helicity(p[idx], mt, wt, alphas, tuple(int(h[r]) for r in gl_rows), int(h[2]), int(h[3]))
+    return out / (4.0 * 64.0 * math.factorial(ngl - 2))
+
+
 def me2(p: np.ndarray, mt: float, wt: float, alphas: float) -> np.ndarray:
     """Spin/colour summed and averaged |M|^2 for g g -> t t~ + n g, one point.
 

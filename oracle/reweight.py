@@ -50,6 +50,8 @@ def me2_helicity(process: str, p: np.ndarray, point: dict, hel: np.ndarray) -> n
         m = qq.me2_helicity(p, point["mt"], point.get("wt", 0.0), point["alphas"], hel)
     elif process == "qq_ttxg":
         m = qqg.me2_helicity(p, point["mt"], point.get("wt", 0.0), point["alphas"], hel)
+    elif process in QCD_PROCESSES:
+        m = qcd.me2_helicity_per_event(p, point["mt"], point.get("wt", 0.0), point["alphas"], hel)
     else:
         raise ValueError(f"no helicity-exclusive evaluation for {process!r}")
     return np.where(m < ZERO_TERM * me2(process, p, point), 0.0, m)

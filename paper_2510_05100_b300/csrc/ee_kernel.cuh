@@ -51,11 +51,11 @@ __device__ __forceinline__ cx<double> cmdot(const cx<double>* a, const cx<double
 // Helicity-exclusive form (EXCL): H is built from the event's own configuration
 // hel[ev][0..3] = (l1, l2, l3, l4) (positive: +1, otherwise -1) alone; a configuration
 // the chirality rule forbids gives H = 0, hence |M_0|^2 = 0 and new weights 0.
-template <class TABLE, bool EXCL = false>
+template <class TABLE, bool EXCL = false, int TPB = 128>
 __device__ __forceinline__ void ee_tile(const double* __restrict__ mom, const double* __restrict__ w_in,
                                         int64_t nev, int64_t tile, const TABLE& lp, double* __restrict__ out,
                                         const signed char* __restrict__ hel = nullptr) {
-  const int64_t ev = tile * 128 + threadIdx.x;
+  const int64_t ev = tile * TPB + threadIdx.x;
   if (ev >= nev) return;
   double p[4][4];
   const double2* src = reinterpret_cast<const double2*>(mom + ev * 16);
@@ -78,21 +78,36 @@ __device__ __forceinline__ void ee_tile(const double* __restrict__ mom, const do
     const signed char* he = hel + ev * 4;
     hev = (he[0] > 0 ? 1 : 0) | (he[1] > 0 ? 2 : 0) | (he[2] > 0 ? 4 : 0) | (he[3] > 0 ? 8 : 0);
   }
+  // both helicity spinors of every lepton from one helicity basis and one omega_+
+  // per lepton (massless: omega_- = 0); index 0: helicity -, 1: +.  FP64 square roots
+  // are the expensive part of this thread's work on B300, so they are not repeated
+  // per configuration.
+  cx<double> v1[2][4], u2[2][4], v3[2][4], u4[2][4];
+  {
+    cx<double> chi[2][2];
+    double pabs, wp, wm;
+    omegas(p[0], 0.0, &pabs, &wp, &wm);
+    chi_pair(p[0], pabs, chi[1], chi[0]);
+    spinor_v_from(chi, wp, wm, v1);
+    omegas(p[1], 0.0, &pabs, &wp, &wm);
+    chi_pair(p[1], pabs, chi[1], chi[0]);
+    spinor_u_from(chi, wp, wm, u2);
+    omegas(p[2], 0.0, &pabs, &wp, &wm);
+    chi_pair(p[2], pabs, chi[1], chi[0]);
+    spinor_v_from(chi, wp, wm, v3);
+    omegas(p[3], 0.0, &pabs, &wp, &wm);
+    chi_pair(p[3], pabs, chi[1], chi[0]);
+    spinor_u_from(chi, wp, wm, u4);
+  }
 #pragma unroll 1
   for (int hi = 0; hi < (EXCL ? 1 : 4); ++hi) {
     const int h = EXCL ? hev : ((hi & 1) ? 6 : 5) + ((hi & 2) ? 4 : 0);   // 5, 6, 9, 10
-    const int l1 = (h & 1) ? 1 : -1, l2 = (h & 2) ? 1 : -1;
-    const int l3 = (h & 4) ? 1 : -1, l4 = (h & 8) ? 1 : -1;
-    cx<double> v1[4], u2[4], v3[4], u4[4];
-    spinor_v(p[0], 0.0, l1, v1);
-    spinor_u(p[1], 0.0, l2, u2);
-    spinor_v(p[2], 0.0, l3, v3);
-    spinor_u(p[3], 0.0, l4, u4);
+    const int i1 = h & 1, i2 = (h >> 1) & 1, i3 = (h >> 2) & 1, i4 = (h >> 3) & 1;
     cx<double> je[2][4], jm[2][4];
-    chiral_current(v1, u2, -1.0, je[0]);          // vbar1 gamma P_L u2
-    chiral_current(v1 + 2, u2 + 2, 1.0, je[1]);   // vbar1 gamma P_R u2
-    chiral_current(u4, v3, -1.0, jm[0]);          // ubar4 gamma P_L v3
-    chiral_current(u4 + 2, v3 + 2, 1.0, jm[1]);   // ubar4 gamma P_R v3
+    chiral_current(v1[i1], u2[i2], -1.0, je[0]);          // vbar1 gamma P_L u2
+    chiral_current(v1[i1] + 2, u2[i2] + 2, 1.0, je[1]);   // vbar1 gamma P_R u2
+    chiral_current(u4[i4], v3[i3], -1.0, jm[0]);          // ubar4 gamma P_L v3
+    chiral_current(u4[i4] + 2, v3[i3] + 2, 1.0, jm[1]);   // ubar4 gamma P_R v3
     cx<double> d[4];
 #pragma unroll
     for (int x = 0; x < 2; ++x)
@@ -147,12 +162,12 @@ __device__ __forceinline__ void ee_tile(const double* __restrict__ mom, const do
   }
 }
 
-template <bool EXCL>
-static __global__ void __launch_bounds__(128)
+template <bool EXCL, int TPB>
+static __global__ void __launch_bounds__(TPB)
     ee_reweight_kernel(const double* __restrict__ mom, const double* __restrict__ w_in, int64_t nev,
                        const __grid_constant__ EwLaunch lp, double* __restrict__ out,
                        const signed char* __restrict__ hel) {
-  ee_tile<EwLaunch, EXCL>(mom, w_in, nev, (int64_t)blockIdx.x, lp, out, hel);
+  ee_tile<EwLaunch, EXCL, TPB>(mom, w_in, nev, (int64_t)blockIdx.x, lp, out, hel);
 }
 
 }  // namespace rex

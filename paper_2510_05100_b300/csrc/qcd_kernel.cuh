@@ -88,7 +88,65 @@ constexpr int QCD_BLOCK = 128;
 // TABLE is the launch's parameter table (QcdLaunch, or a batch table of the
 // persistent multi-process kernel): nmass, mass[], width[], k, mode,
 // out_stride, slot[], factor[], factor0.
-template <int PROC, typename R, bool WIDTH, int SPLIT, bool TC_REQ = false>
+// Helicity-exclusive colour form: each lane holds the jamps of one real linear
+// polarisation configuration of the gluons (its bits gh); an amplitude is linear in
+// every polarisation vector, so the jamps of the event's helicity configuration are
+// J_h = sum over the event's lanes of c_lane * A_lane with
+//     c_lane = prod over gluons with bit 1 of (-i lambda_g sigma_g),
+// where e_lambda ~ (e1 - i lambda sigma e2)/sqrt(2) (incoming: eps, outgoing: eps*)
+// and sigma_g = -1 only where the linear basis is left-handed about the vector it
+// was built from (a momentum exactly along -z).  The event's lanes add their terms
+// with warp shuffles; lane 0 of the event returns
+//     2^-NG sum_{f,f'} Cint_{ff'} Re(conj(J_f) J_f'),
+// the others 0, so the lane sum of the helicity loop is |M_h|^2 (times COLOUR_DEN).
+// A configuration that a selection rule forbids (angular momentum in on-shell
+// g g -> t t~, four of the sixteen) is zero only to the rounding of its inputs: on
+// momenta rounded to FP64 it comes out at or below 1e-14 of the sum over the gluon
+// configurations at the same top helicities (the lanes' own colour forms, basis
+// independent).  A term below ZERO_TERM of that sum is returned as 0, so that its
+// weight follows the 1/0 -> 0 rule instead of a ratio of rounding residues: 1e-13 in
+// FP64, 1e-11 in FP32; the smallest physical term seen is 1.2e-11 of it (g g -> t t~ g).
+template <typename R, int NF, int NGH, int NG>
+struct ExclusiveColourForm {
+  static constexpr double ZERO_TERM = std::is_same<R, double>::value ? 1e-13 : 1e-11;
+  cx<R> c;        // this lane's coefficient
+  int ht;         // the event's top helicity (0: -, 1: +)
+  bool lead;      // lane 0 of the event
+  const int (*col)[NF];
+  __device__ __forceinline__ R operator()(const cx<R> (&A)[2][NF]) const {
+    cx<R> J[NF];
+#pragma unroll
+    for (int f = 0; f < NF; ++f) J[f] = A[ht][f];
+    R scale = form(J);   // this lane's own linear configuration
+#pragma unroll
+    for (int f = 0; f < NF; ++f) J[f] = c * J[f];
+#pragma unroll
+    for (int off = 1; off < NGH; off <<= 1) {
+      scale += __shfl_xor_sync(0xffffffffu, scale, off);
+#pragma unroll
+      for (int f = 0; f < NF; ++f) {
+        J[f].re += __shfl_xor_sync(0xffffffffu, J[f].re, off);
+        J[f].im += __shfl_xor_sync(0xffffffffu, J[f].im, off);
+      }
+    }
+    const R s = form(J) * (R(1) / R(1 << NG));
+    return (lead && !(s < R(ZERO_TERM) * scale)) ? s : R(0);
+  }
+  // sum_{f,f'} Cint_{ff'} Re(conj(J_f) J_f')
+  __device__ __forceinline__ R form(const cx<R> (&J)[NF]) const {
+    R s = R(0);
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+      R t = R(col[f][f]) * (J[f].re * J[f].re + J[f].im * J[f].im);
+#pragma unroll
+      for (int g = f + 1; g < NF; ++g) t += R(2 * col[f][g]) * (J[f].re * J[g].re + J[f].im * J[g].im);
+      s += t;
+    }
+    return s;
+  }
+};
+
+template <int PROC, typename R, bool WIDTH, int SPLIT, bool TC_REQ = false, bool EXCL = false>
 struct QcdTile {
   using P = QcdProc<PROC>;
   static constexpr int NG = P::info::NGLUON;
@@ -101,6 +159,7 @@ struct QcdTile {
   static constexpr bool TC = TC_REQ && std::is_same<R, float>::value && NH >= 8;
   static_assert(32 % NH == 0 || NH % 32 == 0, "gluon-polarisation lanes must tile a warp");
   static_assert(NH <= 32, "one event per warp at most");
+  static_assert(!EXCL || (SPLIT == 0 && !TC), "helicity-exclusive tiles: one lane per gluon configuration");
 
   struct Smem {
     double me2s[EPB][MAX_MASS + 1];
@@ -114,7 +173,8 @@ struct QcdTile {
   template <class TABLE>
   static __device__ __forceinline__ void run(Smem& sm, const double* __restrict__ mom,
                                              const double* __restrict__ w_in, int64_t nev, int64_t tile,
-                                             const TABLE& lp, double* __restrict__ out) {
+                                             const TABLE& lp, double* __restrict__ out,
+                                             const signed char* __restrict__ hel = nullptr) {
     const int tid = threadIdx.x;
     const int el = tid / NH;
     const int lane_ev = tid - el * NH;
@@ -145,6 +205,27 @@ struct QcdTile {
     // a6 on tensor cores: the colour matrix as MMA B fragments in this warp's smem
     if constexpr (TC) ColourTc<NF>::load(P::colour(), sm.tc[tid >> 5]);
 
+    // helicity-exclusive: the event's configuration (process order g g t t~ g..) and
+    // this lane's coefficient in its amplitude
+    ExclusiveColourForm<R, NF, NGH, NG> xform{cx<R>{R(1), R(0)}, 0, gh == 0, P::colour()};
+    int hb_x = 0;
+    if constexpr (EXCL) {
+      const signed char* h = hel + evc * NPART;
+      xform.ht = h[2] > 0 ? 1 : 0;
+      hb_x = h[3] > 0 ? 1 : 0;
+#pragma unroll
+      for (int g = 0; g < NG; ++g) {
+        if (!((gh >> g) & 1)) continue;
+        const int lam = h[g < 2 ? g : g + 2] > 0 ? 1 : -1;
+        const R* d = evd.pg[g];
+        // the same test as pol_linear's branch: the fixed (x, y) basis is left-handed
+        // about a vector along -z
+        const bool left = !(d[1] * d[1] + d[2] * d[2] > R(0)) && d[3] < R(0);
+        const R f = R(left ? lam : -lam);   // factor -i lambda sigma = i f
+        xform.c = cx<R>{-f * xform.c.im, f * xform.c.re};
+      }
+    }
+
     // a3-a7 per distinct mass slot
     for (int m = 0; m < lp.nmass; ++m) {
       P::template mass_setup<R, WIDTH>(evd, lp.mass[m], lp.width[m], sm.mss[el], lane_ev, NH);
@@ -152,7 +233,12 @@ struct QcdTile {
       // a7: the helicity sum adds non-negative terms (no cancellation): FP64 in the
       // exact mode, FP32 in the mixed mode (relative error <= 64 * 2^-24)
       R s = R(0);
-      if constexpr (TC) {
+      if constexpr (EXCL) {
+        // every lane takes part in the event's shuffles; only the event's own antitop
+        // helicity is evaluated
+        s = P::template quark_line<R, R, WIDTH>(evd, sm.mss[el], J, hb_x, hb_x + 1, xform);
+        if (!valid) s = R(0);
+      } else if constexpr (TC) {
         // every lane takes part in the warp-wide MMA form; lane 8t of the warp
         // receives the colour sum of m16 tile t (part of its event), the others 0
         __half* tcs = sm.tc[tid >> 5];
@@ -274,6 +360,38 @@ static int launch_variant(int variant, const double* mom, const double* w_in, in
     default: return (int)cudaErrorInvalidValue;
   }
 }
+
+template <int PROC, typename R, bool WIDTH>
+__global__ void __launch_bounds__(QCD_BLOCK, 1)
+    qcd_exclusive_kernel(const double* __restrict__ mom, const double* __restrict__ w_in, int64_t nev,
+                         const __grid_constant__ QcdLaunch lp, double* __restrict__ out,
+                         const signed char* __restrict__ hel) {
+  using T = QcdTile<PROC, R, WIDTH, 0, false, true>;
+  __shared__ typename T::Smem sm;
+  T::run(sm, mom, w_in, nev, (int64_t)blockIdx.x, lp, out, hel);
+}
+
+template <int PROC, typename R>
+static int launch_exclusive(const double* mom, const double* w_in, int64_t nev, const QcdLaunch& lp, double* out,
+                            const signed char* hel, cudaStream_t st) {
+  constexpr int EPB = QCD_BLOCK / QcdProc<PROC>::info::NGHEL;
+  const int64_t blocks = (nev + EPB - 1) / EPB;
+  if (blocks > 0x7fffffffLL) return (int)cudaErrorInvalidValue;
+  if (lp.has_width)
+    qcd_exclusive_kernel<PROC, R, true><<<(unsigned)blocks, QCD_BLOCK, 0, st>>>(mom, w_in, nev, lp, out, hel);
+  else
+    qcd_exclusive_kernel<PROC, R, false><<<(unsigned)blocks, QCD_BLOCK, 0, st>>>(mom, w_in, nev, lp, out, hel);
+  return (int)cudaGetLastError();
+}
+
+// helicity-exclusive launcher of one g g process (rex_reweight_helicity)
+#define REX_DEFINE_QCD_EXCLUSIVE_LAUNCHER(KIND, NAME)                                                  \
+  int launch_##NAME##_exclusive(int mixed, const double* mom, const double* w_in, int64_t nev,          \
+                                const QcdLaunch& lp, double* out, void* stream, const signed char* hel) { \
+    cudaStream_t st = static_cast<cudaStream_t>(stream);                                                \
+    return mixed ? launch_exclusive<KIND, float>(mom, w_in, nev, lp, out, hel, st)                      \
+                 : launch_exclusive<KIND, double>(mom, w_in, nev, lp, out, hel, st);                    \
+  }
 
 #define REX_DEFINE_QCD_LAUNCHER(KIND, NAME)                                                          \
   int launch_##NAME(int mixed, int variant, const double* mom, const double* w_in, int64_t nev,     \

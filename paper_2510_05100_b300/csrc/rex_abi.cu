@@ -133,9 +133,15 @@ int launch_qcd(const rex_proc* p, const double* mom, const double* w_in, int64_t
                double* out, void* stream, const signed char* hel) {
   const int mixed = p->precision == REX_MIXED;
   switch (p->kind) {
-    case PROC_GG_TTX: return launch_gg_ttx(mixed, p->variant, mom, w_in, nev, lp, out, stream);
-    case PROC_GG_TTXG: return launch_gg_ttxg(mixed, p->variant, mom, w_in, nev, lp, out, stream);
-    case PROC_GG_TTXGG: return launch_gg_ttxgg(mixed, p->variant, mom, w_in, nev, lp, out, stream);
+    case PROC_GG_TTX:
+      return hel ? launch_gg_ttx_exclusive(mixed, mom, w_in, nev, lp, out, stream, hel)
+                 : launch_gg_ttx(mixed, p->variant, mom, w_in, nev, lp, out, stream);
+    case PROC_GG_TTXG:
+      return hel ? launch_gg_ttxg_exclusive(mixed, mom, w_in, nev, lp, out, stream, hel)
+                 : launch_gg_ttxg(mixed, p->variant, mom, w_in, nev, lp, out, stream);
+    case PROC_GG_TTXGG:
+      return hel ? launch_gg_ttxgg_exclusive(mixed, mom, w_in, nev, lp, out, stream, hel)
+                 : launch_gg_ttxgg(mixed, p->variant, mom, w_in, nev, lp, out, stream);
     case PROC_QQ_TTX: return launch_qq_ttx(mixed, mom, w_in, nev, lp, out, stream, hel);
     case PROC_QQ_TTXG: return launch_qq_ttxg(mixed, mom, w_in, nev, lp, out, stream, hel, p->cross);
     default: return (int)cudaErrorInvalidValue;
@@ -729,11 +735,6 @@ int rex_reweight_helicity(rex_proc* proc, const double* momenta, const signed ch
                           void* stream) {
   const int rc = validate_proc(proc);
   if (rc) return rc;
-  if (proc->kind != PROC_EE_MUMU && proc->kind != PROC_QQ_TTX && proc->kind != PROC_QQ_TTXG)
-    return fail(REX_EUNSUPPORTED,
-                "helicity-exclusive reweighting needs helicity-basis amplitudes: ee_mumu, qq_ttx and qq_ttxg "
-                "have them, '%s' sums linear gluon polarisations",
-                info_of(proc->kind).name);
   if (proc->kind == PROC_QQ_TTXG && !is_direct(proc->cross))
     return fail(REX_EUNSUPPORTED,
                 "helicity-exclusive reweighting of q q~ -> t t~ g is built for the direct channel only; its "

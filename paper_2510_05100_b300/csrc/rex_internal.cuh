@@ -119,6 +119,14 @@ int launch_gg_ttxg(int mixed, int variant, const double* mom, const double* w_in
                    const QcdLaunch& lp, double* out, void* stream);
 int launch_gg_ttxgg(int mixed, int variant, const double* mom, const double* w_in, int64_t nev,
                     const QcdLaunch& lp, double* out, void* stream);
+// Helicity-exclusive reweighting of the g g processes (the events' helicity
+// configurations hel [nev][npart], int8, positive: +1, otherwise -1).
+int launch_gg_ttx_exclusive(int mixed, const double* mom, const double* w_in, int64_t nev, const QcdLaunch& lp,
+                            double* out, void* stream, const signed char* hel);
+int launch_gg_ttxg_exclusive(int mixed, const double* mom, const double* w_in, int64_t nev, const QcdLaunch& lp,
+                             double* out, void* stream, const signed char* hel);
+int launch_gg_ttxgg_exclusive(int mixed, const double* mom, const double* w_in, int64_t nev, const QcdLaunch& lp,
+                              double* out, void* stream, const signed char* hel);
 // hel: null for the helicity sum, else the events' helicity configurations
 // [nev][npart] (int8, positive: +1, otherwise -1) for helicity-exclusive reweighting.
 int launch_qq_ttx(int mixed, const double* mom, const double* w_in, int64_t nev, const QcdLaunch& lp,

@@ -1,6 +1,6 @@
 """Run a fixed reweighting case for profilers (ncu): python -m paper_2510_05100_b300.profile_case
 
-  --proc gg_ttxg --mode fp64|mixed --nev N --launches L
+  --proc gg_ttxg --mode fp64|mixed --nev N --launches L [--variant V]
   --surrogate-steps S          (surrogate training steps instead)
   --surrogate-infer fused|layered  (surrogate inference instead)
 
@@ -28,6 +28,7 @@ def main():
     ap.add_argument("--mode", choices=["fp64", "mixed"], default="fp64")
     ap.add_argument("--nev", type=int, default=1 << 19)
     ap.add_argument("--launches", type=int, default=2)
+    ap.add_argument("--variant", type=int, default=None, help="kernel thread-mapping variant (g g processes)")
     ap.add_argument("--surrogate-steps", type=int, default=0,
                     help="instead: train the surrogate for this many steps of 8192 samples")
     ap.add_argument("--surrogate-infer", choices=["fused", "layered"], default=None,
@@ -62,11 +63,13 @@ def main():
     pts = GRIDS[a.proc]()
     p = rex.Process(a.proc, rex.FP64 if a.mode == "fp64" else rex.MIXED)
     p.set_params(mt=173.0, wt=0.0, alphas=0.118)
+    if a.variant is not None:
+        p.variant = a.variant
     out = torch.empty((a.nev, len(pts)), dtype=torch.float64, device="cuda")
     for _ in range(a.launches):
         p.reweight(mom, w, pts, w_out=out)
     torch.cuda.synchronize()
-    print(f"{a.proc} {a.mode} nev={a.nev} k={len(pts)} launches={a.launches} ok "
+    print(f"{a.proc} {a.mode} variant={p.variant} nev={a.nev} k={len(pts)} launches={a.launches} ok "
           f"w_out[0,:3]={out[0, :3].tolist()}")
 
 

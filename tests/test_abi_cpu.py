@@ -101,9 +101,10 @@ def test_helicity_exclusive_validation_before_any_device_work(rex):
     pts = (rex.Params * 1)(rex.params(dict(mt=171.0, alphas=0.118)))
     fake = ctypes.c_void_p(0x10000)     # never dereferenced: validation fails first
     g = rex.Process("gg_ttxg")
+    assert lib.rex_reweight_helicity(g._h, fake, fake, fake, 10, pts, 1, fake, None) == rex.REX_ENOTINIT
     g.set_params(mt=173.0, alphas=0.118)
-    assert lib.rex_reweight_helicity(g._h, fake, fake, fake, 10, pts, 1, fake, None) == rex.REX_EUNSUPPORTED
-    assert b"linear gluon polarisations" in lib.rex_last_error()
+    assert lib.rex_reweight_helicity(g._h, fake, None, fake, 10, pts, 1, fake, None) == rex.REX_EINVAL
+    assert b"null helicity array" in lib.rex_last_error()
     q = rex.Process("qq_ttx")
     assert lib.rex_reweight_helicity(q._h, fake, fake, fake, 10, pts, 1, fake, None) == rex.REX_ENOTINIT
     q.set_params(mt=173.0, alphas=0.118)

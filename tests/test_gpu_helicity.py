@@ -81,11 +81,82 @@ def test_summing_configurations_gives_the_helicity_sum(rex):
 
 
 def test_unsupported_processes_raise(rex):
-    p = rex.Process("gg_ttx", 0)
+    """The crossings of q q~ -> t t~ g evaluate only the helicity sum."""
+    p = rex.Process("qg_ttxq", 0)
     p.set_params(QCD_ORIG)
-    mom = dev(ps.make_events("gg_ttx", 4, 1))
+    mom = dev(ps.make_events("qq_ttxg", 4, 1))
     with pytest.raises(rex.RexError):
-        p.reweight_helicity(mom, dev(np.ones((4, 4), dtype=np.int8)), dev(np.ones(4)), [QCD_ORIG])
+        p.reweight_helicity(mom, dev(np.ones((4, 5), dtype=np.int8)), dev(np.ones(4)), [QCD_ORIG])
+
+
+GG_NPART = {"gg_ttx": 4, "gg_ttxg": 5, "gg_ttxgg": 6}
+
+
+def extended_reference(proc, mom, hel, w, pts):
+    """The oracle's exclusive weights evaluated in extended precision (np.longdouble): a
+    small helicity term carries the FP64 rounding of its diagrams' sum, relative error up
+    to ~ eps sum_d |A_d| / |A_h| (7e-10 on one g g -> t t~ g term here), beyond what the
+    small-term bound allows; the extended evaluation removes it from the reference."""
+    ref = oracle_rw.reweight_helicity(proc, mom.astype(np.longdouble), hel, w, QCD_ORIG, pts)
+    return np.asarray(ref, dtype=np.float64)
+
+
+@pytest.mark.parametrize("proc,precision,tol,n", [("gg_ttx", 0, 1e-12, 300), ("gg_ttx", 1, 1e-5, 300),
+                                                  ("gg_ttxg", 0, 1e-12, 97), ("gg_ttxg", 1, 1e-3, 97),
+                                                  ("gg_ttxgg", 0, 1e-12, 13), ("gg_ttxgg", 1, 1e-3, 13)])
+def test_gg_exclusive_parity(rex, proc, precision, tol, n):
+    """g g -> t t~ (+ g, + g g): each event with a random configuration of all its
+    helicities.  The kernels sum real linear gluon polarisations; the exclusive tile
+    combines its lanes' jamps into the helicity amplitude of the event's configuration
+    (e_lambda ~ e1 -/+ i lambda e2).  Against the oracle's per-configuration terms,
+    with the helicity sum's tolerance or the small-term conditioning bound."""
+    npart = GG_NPART[proc]
+    mom = ps.make_events(proc, n, 65)
+    hel = np.random.default_rng(65).choice(np.array([-1, 1], dtype=np.int8), size=(n, npart))
+    w = np.random.default_rng(66).uniform(0.5, 2.0, n)
+    pts = ps.grid_gg_ttxg()[::3] + [QCD_ORIG, dict(mt=172.0, wt=1.2, alphas=0.121)]
+    p = rex.Process(proc, precision)
+    p.set_params(QCD_ORIG)
+    got = p.reweight_helicity(dev(mom), dev(hel), dev(w), pts).cpu().numpy()
+    ref = extended_reference(proc, mom, hel, w, pts)
+    # g g -> t t~: four of the sixteen configurations are forbidden by angular momentum in
+    # the on-shell 2 -> 2 kinematics; on FP64 momenta they are zero to ~1e-17 of the sum,
+    # and the kernel reports them as 0 (the 1/0 -> 0 rule) at every point
+    zero = np.zeros(n, dtype=bool)
+    if proc == "gg_ttx":
+        ext = mom.astype(np.longdouble)
+        frac = oracle_rw.me2_helicity(proc, ext, QCD_ORIG, hel) / oracle_rw.me2(proc, ext, QCD_ORIG)
+        zero = np.asarray(frac, dtype=np.float64) < 1e-12
+        assert np.any(zero)
+    assert np.all(got[zero] == 0.0)
+    eps = np.finfo(np.float64 if precision == 0 else np.float32).eps / 2
+    bound = helicity_tolerance(proc, mom, hel, QCD_ORIG, pts, tol, eps)
+    err = np.abs(got[~zero] / ref[~zero] - 1.0)
+    assert np.all(err < bound[~zero]), (np.max(err), np.max(err / bound[~zero]))
+    assert np.mean(err < tol) > 0.9
+    j = pts.index(QCD_ORIG)
+    kept = ~zero & (got[:, j] != 0.0)         # FP32 returns a term below 1e-11 of its scale as 0
+    assert np.mean(kept[~zero]) > 0.95
+    assert np.array_equal(got[kept, j], w[kept])   # an unchanged point keeps the weight exactly
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_gg_ttxg_configurations_sum_to_the_helicity_sum(rex, precision):
+    """sum_h w'_h |M_h,0|^2 = w' |M_0|^2 over the 32 configurations of each event, with
+    the GPU's exclusive and helicity-summed weights."""
+    n = 24
+    mom = ps.make_events("gg_ttxg", n, 67)
+    confs = np.array(np.meshgrid(*[[-1, 1]] * 5, indexing="ij")).reshape(5, -1).T.astype(np.int8)
+    idx = np.repeat(np.arange(n), 32)
+    hel = np.tile(confs, (n, 1))
+    pts = [dict(mt=170.0, wt=0.0, alphas=0.118)]
+    p = rex.Process("gg_ttxg", precision)
+    p.set_params(QCD_ORIG)
+    wh = p.reweight_helicity(dev(mom[idx]), dev(hel), dev(np.ones(32 * n)), pts).cpu().numpy()[:, 0]
+    m0h = oracle_rw.me2_helicity("gg_ttxg", mom[idx], QCD_ORIG, hel)
+    summed = (wh * m0h).reshape(n, 32).sum(axis=1) / oracle_rw.me2("gg_ttxg", mom, QCD_ORIG)
+    ws = p.reweight(dev(mom), dev(np.ones(n)), pts).cpu().numpy()[:, 0]
+    assert np.max(np.abs(summed / ws - 1.0)) < (1e-12 if precision == 0 else 1e-4)
 
 
 @pytest.mark.parametrize("precision,tol", [(0, 1e-12), (1, 1e-4)])

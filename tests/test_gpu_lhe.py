@@ -115,3 +115,27 @@ def test_pp_ttxj_file_every_channel(rex, tmp_path):
         assert np.max(np.abs(out[:8] / ref - 1)) < 1e-12, proc
         p.close()
     L.close()
+
+
+def test_file_to_helicity_exclusive_weights_gg_ttxg(rex, tmp_path):
+    """SPINUP read from the file feeds helicity-exclusive reweighting of g g -> t t~ g."""
+    from rexlib import helicity_tolerance
+    src = str(tmp_path / "hel_gg.lhe")
+    lhe_synth.write_lhe(src, {"gg_ttxg": 120, "qq_ttx": 40}, seed=9, helicities=True)
+    L = rex.Lhe(src)
+    pin, pout = lhe_synth.PROCESSES["gg_ttxg"]
+    mom, w, idx = L.extract(pin, pout)
+    hel = L.extract_helicities(pin, pout)
+    L.close()
+    p = rex.Process("gg_ttxg", 0)
+    p.set_params(ORIG)
+    pts = GRIDS["gg_ttxg"]
+    out = p.reweight_helicity(torch.from_numpy(mom).cuda(), torch.from_numpy(hel).cuda(),
+                              torch.from_numpy(w).cuda(), pts).cpu().numpy()
+    # the reference in extended precision: the oracle's own FP64 rounding of small helicity
+    # terms exceeds their bound (see test_gpu_helicity.extended_reference)
+    ref = np.asarray(oracle_rw.reweight_helicity("gg_ttxg", mom.astype(np.longdouble), hel, w, ORIG, pts),
+                     dtype=np.float64)
+    bound = helicity_tolerance("gg_ttxg", mom, hel, ORIG, pts, 1e-12, np.finfo(np.float64).eps / 2)
+    err = np.abs(out - ref) / np.abs(ref)
+    assert np.all(err < bound)

@@ -103,3 +103,20 @@ def test_qq_ttxg_terms_sum_to_the_helicity_sum_and_zeros():
     assert np.all(terms[:, forbidden] == 0.0) and np.all(terms[:, ~forbidden] > 0.0)
     mirror = reweight.me2_helicity("qq_ttxg", p[idx], orig, -hel).reshape(6, 32)
     assert np.max(np.abs(mirror - terms)) < 1e-12 * np.max(terms)
+
+
+@pytest.mark.parametrize("proc,npart,n", [("gg_ttx", 4, 6), ("gg_ttxg", 5, 4), ("gg_ttxgg", 6, 2)])
+def test_gg_terms_sum_to_the_helicity_sum_and_parity(proc, npart, n):
+    """The g g processes' per-event helicity terms: over every configuration they add up to
+    the helicity sum, and parity (every 3-momentum reversed, every helicity flipped) maps
+    each term onto its mirror; at a shifted top mass (the spinors' light-cone convention)."""
+    p = ps.make_events(proc, n, 105)
+    pt = dict(mt=171.0, wt=0.0, alphas=0.118)
+    cfg = np.array(list(itertools.product((-1, 1), repeat=npart)), dtype=np.int8)
+    idx, hel = np.repeat(np.arange(n), len(cfg)), np.tile(cfg, (n, 1))
+    terms = reweight.me2_helicity(proc, p[idx], pt, hel).reshape(n, -1)
+    assert np.max(np.abs(terms.sum(axis=1) / reweight.me2(proc, p, pt) - 1.0)) < 1e-13
+    mirror = p.copy()
+    mirror[..., 1:] *= -1.0
+    flipped = reweight.me2_helicity(proc, mirror[idx], pt, -hel).reshape(n, -1)
+    assert np.max(np.abs(flipped - terms)) < 1e-13 * np.max(terms)
