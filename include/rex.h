@@ -66,13 +66,13 @@ extern "C" {
  *            mass).  Kernel variants 5-8 of the g g processes put the colour
  *            sum on tensor cores (FP16 hi/lo operands, FP32 accumulation).
  *            The error against FP64 is bounded per process (gg_ttx 1e-5,
- *            gg_ttxg and gg_ttxgg 1e-3, qq_ttx 1e-5, qq_ttxg and qxq_ttxg 1e-4,
- *            relative per weight).  The q g and q~ g crossings of qq_ttxg meet
- *            1e-4 except for a forward light quark: the Feynman-gauge diagrams
- *            on the t-channel gluon cancel, and the error grows like
- *            4 * 2^-24 * s_hat / |t| (t the light quark's momentum transfer;
- *            about 4e-4 of events exceed 1e-4 on the p p -> t t~ + jet
- *            sample).  Use REX_FP64 where those events matter. */
+ *            gg_ttxg and gg_ttxgg 1e-3, qq_ttx 1e-5, qq_ttxg and every crossing
+ *            of it 1e-4, relative per weight).  For the q g and q~ g crossings
+ *            this holds for forward light quarks too: when the light line's
+ *            gluon has |t| < s' / 256 the kernel splits the light-quark current
+ *            along the gluon momentum (J = J' + a q, J' formed in FP64) and
+ *            evaluates the part along q through the Ward identity, so the
+ *            diagrams on the t-channel gluon no longer cancel in FP32. */
 #define REX_FP64 0
 #define REX_MIXED 1
 

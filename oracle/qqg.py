@@ -59,6 +59,14 @@ def colour_matrix() -> np.ndarray:
     return k.conj() @ k.T
 
 
+def _real(p) -> np.ndarray:
+    """Momenta as a real array: FP64, unless they are given in extended precision
+    (np.longdouble), which is then kept through every step (a reference free of the
+    FP64 evaluation's own rounding, for ill-conditioned events)."""
+    p = np.asarray(p)
+    return p if p.dtype == np.longdouble else p.astype(np.float64)
+
+
 def _chain(left: np.ndarray, mats: list, right: np.ndarray) -> np.ndarray:
     """left-row . (product of [N,4,4] matrices) . right-column, [N]."""
     m = mats[0]
@@ -71,7 +79,7 @@ def _vector_chain(left: np.ndarray, before: list, after: list, right: np.ndarray
     """left . B gamma^mu A . right for every mu (upper index), [N, 4]."""
     n = left.shape[0]
     eye = np.broadcast_to(np.eye(4, dtype=complex), (n, 4, 4))
-    out = np.empty((n, 4), dtype=complex)
+    out = np.empty((n, 4), dtype=np.result_type(left, right, complex))
     for mu in range(4):
         g = np.broadcast_to(GAMMA[mu], (n, 4, 4))
         out[:, mu] = _chain(left, (before or [eye]) + [g] + (after or [eye]), right)
@@ -105,7 +113,7 @@ def _diagrams(q1, q2, p3, p4, k, left, right, ub3, v4, eps, mt, wt, alphas) -> n
     d4 = mdot(a4, a4) - mt * mt + 1j * mt * wt
     c4 = _vector_chain(ub3, [], [slash(a4) + m1, es], v4) / d4[:, None]
     cf = -1j * g ** 3        # (i g)^3 x i (fermion propagator) x (-i) (gluon propagator)
-    amp = np.empty((n, 5), dtype=complex)
+    amp = np.empty((n, 5), dtype=np.result_type(left, right, complex))
     amp[:, 0] = cf * mdot(c1, j_out) / sp
     amp[:, 1] = cf * mdot(c2, j_out) / sp
     amp[:, 2] = cf * mdot(j_in, c3) / s
@@ -120,7 +128,7 @@ def _diagrams(q1, q2, p3, p4, k, left, right, ub3, v4, eps, mt, wt, alphas) -> n
 def amplitudes(p: np.ndarray, mt: float, wt: float, alphas: float, hel: tuple, eps_override=None) -> np.ndarray:
     """The five diagram amplitudes [N, 5] of one helicity configuration
     hel = (l1, l2, l3, l4, lg); eps_override replaces the gluon's eps* (gauge checks)."""
-    p = np.asarray(p, dtype=np.float64)
+    p = _real(p)
     l1, l2, l3, l4, lg = hel
     p1, p2, p3, p4, k = p[:, 0], p[:, 1], p[:, 2], p[:, 3], p[:, 4]
     eps = polarisation(k, lg).conj() if eps_override is None else eps_override.astype(complex)
@@ -152,7 +160,7 @@ def amplitudes_crossed(process: str, p: np.ndarray, mt: float, wt: float, alphas
     of the record's particles in record order.  The light line runs along the
     fermion-number flow from the quark entering the diagram (an incoming quark or
     an outgoing antiquark, momentum q1) to the one leaving it (momentum -q2)."""
-    p = np.asarray(p, dtype=np.float64)
+    p = _real(p)
     (iq, iqb, oq, oqb, ig, og), _ = CROSSINGS[process]
     if iq is not None:
         right, q1 = spinor_u(p[:, iq], 0.0, hel[iq]), p[:, iq]
@@ -174,11 +182,11 @@ def amplitudes_crossed(process: str, p: np.ndarray, mt: float, wt: float, alphas
 
 def me2_crossed(process: str, p: np.ndarray, mt: float, wt: float, alphas: float) -> np.ndarray:
     """Spin/colour summed and averaged |M|^2 of one channel of CROSSINGS, one point."""
-    p = np.asarray(p, dtype=np.float64)
+    p = _real(p)
     if p.ndim != 3 or p.shape[1] != 5:
         raise ValueError(f"{process} expects momenta [N, 5, 4]")
     gm = colour_matrix()
-    total = np.zeros(p.shape[0])
+    total = np.zeros(p.shape[0], dtype=p.dtype)
     for hel in itertools.product((-1, 1), repeat=5):
         a = amplitudes_crossed(process, p, mt, wt, alphas, hel)
         total += np.real(np.einsum("ns,st,nt->n", a.conj(), gm, a))
@@ -187,11 +195,11 @@ def me2_crossed(process: str, p: np.ndarray, mt: float, wt: float, alphas: float
 
 def me2(p: np.ndarray, mt: float, wt: float, alphas: float) -> np.ndarray:
     """Spin/colour summed and averaged |M|^2 for q q~ -> t t~ g, one point."""
-    p = np.asarray(p, dtype=np.float64)
+    p = _real(p)
     if p.ndim != 3 or p.shape[1] != 5:
         raise ValueError("q q~ -> t t~ g expects momenta [N, 5, 4]")
     gm = colour_matrix()
-    total = np.zeros(p.shape[0])
+    total = np.zeros(p.shape[0], dtype=p.dtype)
     for hel in itertools.product((-1, 1), repeat=5):
         a = amplitudes(p, mt, wt, alphas, hel)
         total += np.real(np.einsum("ns,st,nt->n", a.conj(), gm, a))
@@ -202,10 +210,10 @@ def me2_helicity(p: np.ndarray, mt: float, wt: float, alphas: float, hel: np.nda
     """The term of the helicity sum (me2 = sum over configurations, same 1/36) of each
     event's own configuration hel[N, 5] = (l1, l2, l3, l4, lg): helicities of q, q~, t,
     t~ and the gluon in the frame of the momenta."""
-    p = np.asarray(p, dtype=np.float64)
+    p = _real(p)
     hel = np.asarray(hel)
     gm = colour_matrix()
-    out = np.zeros(p.shape[0])
+    out = np.zeros(p.shape[0], dtype=p.dtype)
     for conf in itertools.product((-1, 1), repeat=5):
         sel = np.all(hel == np.array(conf), axis=1)
         if np.any(sel):

@@ -35,12 +35,14 @@ __global__ void __launch_bounds__(QCD_BLOCK, MINB)
   using T3 = QcdTile<PROC_GG_TTXGG, R, WIDTH, S_TTXGG, TC_TTXGG>;
   using T4 = QqTile<R>;
   using T5 = QqgTile<R>;
+  using T6 = QqgTile<R, true>;   // crossed light line (q g, q~ g): the t-channel tile
   union Smem {
     typename T1::Smem a;
     typename std::conditional<(CLASS >= 1), typename T2::Smem, char>::type b;
     typename std::conditional<(CLASS >= 2), typename T3::Smem, char>::type c;
     typename T4::Smem d;
     typename std::conditional<(CLASS >= 1), typename T5::Smem, char>::type e;
+    typename std::conditional<(CLASS >= 1), typename T6::Smem, char>::type f;
   };
   __shared__ Smem sm;
   __shared__ unsigned long long item_s;
@@ -65,7 +67,12 @@ __global__ void __launch_bounds__(QCD_BLOCK, MINB)
         break;
       case PROC_QQ_TTX: T4::run(sm.d, B.mom, B.w_in, B.nev, tile, B.t, B.out); break;
       case PROC_QQ_TTXG:
-        if constexpr (CLASS >= 1) T5::run(sm.e, B.mom, B.w_in, B.nev, tile, B.t, B.out, nullptr, B.cross);
+        if constexpr (CLASS >= 1) {
+          if (B.cross.neg[0] || B.cross.neg[1])
+            T6::run(sm.f, B.mom, B.w_in, B.nev, tile, B.t, B.out, nullptr, B.cross);
+          else
+            T5::run(sm.e, B.mom, B.w_in, B.nev, tile, B.t, B.out, nullptr, B.cross);
+        }
         break;
       default: break;
     }

@@ -91,7 +91,27 @@ struct QqgLane {
   R wp3, wp4;
   R is, isp;                      // 1/s, 1/s'
   R d3, d4;                       // (p3 + k)^2 - m0^2, (p4 + k)^2 - m0^2
+  bool split;                     // gauge split of J_in taken (jin holds J', QqgSplit the rest)
 };
+
+// The rest of a lane's gauge split (qqg_lane_gauge_split), kept in shared memory; a
+// lane without the split holds zeros here, which leave its amplitudes unchanged.
+template <typename R>
+struct QqgSplit {
+  cx<R> al;                       // J_in = J' + al q
+  R qpe;                          // q'.eps
+  R n3[4], n4[4];                 // (1, -p-hat) of top and antitop
+  R h3, h4;                       // (p^2 - m0^2) / (2 (E + |p|)) of top and antitop
+  R g3, g4;                       // 1 / (2 (E + |p|))
+};
+
+template <typename R>
+__device__ __forceinline__ void qqg_split_clear(QqgSplit<R>& S) {
+#pragma unroll
+  for (int m = 0; m < 4; ++m) S.n3[m] = S.n4[m] = R(0);
+  S.al = cx<R>{R(0), R(0)};
+  S.qpe = S.h3 = S.h4 = S.g3 = S.g4 = R(0);
+}
 
 // The event's invariants, taken in FP64 by the caller (once per event): 1/s, 1/s',
 // 1/(p1 - k)^2, 1/(k - p2)^2 and the top-propagator denominators at a reference mass
@@ -166,6 +186,88 @@ __device__ __forceinline__ void qqg_lane_setup(const R (&p)[5][4], int h12, int 
   // top helicity 2-spinors (mass independent)
   L.wp3 = sqrt(chis(p[2], L.chi3[0], L.chi3[1]));
   L.wp4 = sqrt(chis(p[3], L.chi4[0], L.chi4[1]));
+  L.split = false;
+}
+
+// Gauge split of the light-quark current for a gluon of small virtuality s = q^2
+// (the crossed channels' t-channel gluon of a forward light quark, |s| << s').
+//
+// There a3, a4 and a5 each grow like 1/|s| while their colour sum grows like
+// 1/sqrt|s|: J_in points along q up to O(sqrt|s|), and the part along q cancels
+// between the three (Ward identity), which in FP32 costs a relative error of about
+// 2^-24 s'/|s|.  Writing J_in = J' + al q with J'.q' = 0 (q' = p3 + p4, al =
+// J_in.q' / q.q'), linearity gives a_i(J_in) = a_i(J') + al a_i(q), and with the
+// propagator identities S(P) q-slash = c3 + S(P)(p4-slash + m) (P = p3 + k, q = P +
+// p4), ubar3 q-slash S(Q) = ubar3 (p3-slash - m) S(Q) - c4 ubar3 (Q = -p4 - k), with
+// c = (P^2 - m^2) / (P^2 - m^2 + i m Gamma) (1 at zero width), and the three-gluon
+// vertex contracted with q:
+//     s a3(q) =  c3 X + ubar3 eps-slash S(P) d4-slash v4
+//     s a4(q) = -c4 X + ubar3 d3-slash S(Q) eps-slash v4
+//     s a5(q) =     X - (q'.eps) ubar3 (d3 + d4)-slash v4 / s',     X = ubar3 eps-slash v4,
+// where d = p - p~ = (p^2 - m^2) / (2 (E + |p|)) (1, -p-hat) is the difference between
+// a top momentum and the on-shell momentum its spinor is built on at mass m (zero at
+// the event's own mass).  X (0, 0, 1, -1, 1) is a null vector of the colour matrix
+// (its rows 2..4 against (1, -1, 1) sum to 0), so dropping it leaves |M|^2 unchanged:
+// the lane evaluates a3..a5 with J' in place of J_in plus al times the d terms and
+// X (c - 1), none of which cancels.  J' = J_in - al q itself cancels, so it is formed in FP64
+// from the FP64 momenta (once per event, for the events that take the split).
+// pd: the event's slot momenta in FP64; e3, e4: p3^2 - m0^2 and p4^2 - m0^2 in FP64.
+template <typename R>
+__device__ __forceinline__ void qqg_lane_gauge_split(const double (&pd)[5][4], int h12, int neg, R e3, R e4,
+                                                     QqgLane<R>& L, QqgSplit<R>& S) {
+  const int l1 = h12 ? -1 : 1;
+  double k0[4], k1[4], q[4], qp[4];
+#pragma unroll
+  for (int m = 0; m < 4; ++m) {
+    k0[m] = (neg & 1) ? -pd[0][m] : pd[0][m];
+    k1[m] = (neg & 2) ? -pd[1][m] : pd[1][m];
+    q[m] = pd[0][m] + pd[1][m];
+    qp[m] = pd[2][m] + pd[3][m];
+  }
+  cx<double> u1[4], v2[4], j[4];
+  spinor_u(k0, 0.0, l1, u1);
+  spinor_v(k1, 0.0, -l1, v2);
+  dirac_current(v2, u1, j);
+  const cx<double> jq = cdotr(j, qp);
+  const double iqq = 1.0 / mdot(q, qp);
+  const cx<double> al = cx<double>{jq.re * iqq, jq.im * iqq};
+  cx<R> jp[4];
+#pragma unroll
+  for (int m = 0; m < 4; ++m) jp[m] = cx<R>{R(j[m].re - al.re * q[m]), R(j[m].im - al.im * q[m])};
+  // E with J' (the same vertex as qqg_lane_setup)
+  R qk[4], qpk[4], qq2[4], r3[4], r4[4];
+#pragma unroll
+  for (int m = 0; m < 4; ++m) {
+    qk[m] = R(q[m] + pd[4][m]);
+    qpk[m] = R(qp[m] - pd[4][m]);
+    qq2[m] = R(qp[m] + q[m]);
+    r3[m] = R(pd[2][m]);
+    r4[m] = R(pd[3][m]);
+  }
+  const cx<R> je = cdotr(jp, L.eps), jqk = cdotr(jp, qpk);
+  const R eq = mdot(L.eps, qq2);
+#pragma unroll
+  for (int m = 0; m < 4; ++m) {
+    L.jin[m] = jp[m];
+    L.e[m] = qk[m] * je + L.eps[m] * jqk - eq * jp[m];
+  }
+  S.al = cx<R>{R(al.re), R(al.im)};
+  R qpr[4] = {R(qp[0]), R(qp[1]), R(qp[2]), R(qp[3])};
+  S.qpe = mdot(qpr, L.eps);
+  const R a3 = sqrt(r3[1] * r3[1] + r3[2] * r3[2] + r3[3] * r3[3]);
+  const R a4 = sqrt(r4[1] * r4[1] + r4[2] * r4[2] + r4[3] * r4[3]);
+  S.n3[0] = R(1);
+  S.n4[0] = R(1);
+#pragma unroll
+  for (int m = 1; m < 4; ++m) {
+    S.n3[m] = -r3[m] / a3;
+    S.n4[m] = -r4[m] / a4;
+  }
+  S.g3 = R(0.5) / (L.wp3 * L.wp3);
+  S.g4 = R(0.5) / (L.wp4 * L.wp4);
+  S.h3 = e3 * S.g3;
+  S.h4 = e4 * S.g4;
+  L.split = true;
 }
 
 // The event's invariants into the lane: 1/s, 1/s', the top denominators and the
@@ -183,6 +285,9 @@ __device__ __forceinline__ void qqg_lane_scale(const QqgInvariants<R>& inv, QqgL
   }
 }
 
+// The lane's colour-summed |amplitude|^2 summed over the 4 top-helicity pairs at top
+// mass mr, with dm2 = m0^2 - m^2 and mw = m Gamma (g, colour 1/3 and averaging not
+// applied).
 // The lane's colour-summed |amplitude|^2 summed over the 4 top-helicity pairs at top
 // mass mr, with dm2 = m0^2 - m^2 and mw = m Gamma (g, colour 1/3 and averaging not
 // applied).
@@ -222,6 +327,82 @@ __device__ __forceinline__ R qqg_slot(const QqgLane<R>& L, R mr, R dm2, R mw) {
       a[2] = f3 * ubar_dot(u3[l3], t3);
       a[3] = f4 * ubar_dot(u3[l3], s3);
       a[4] = f5 * cdotm(L.e, jout);
+      R form = R(0);
+#pragma unroll
+      for (int d = 0; d < 5; ++d) {
+        form += R(qqg_colour(d, d)) * (a[d].re * a[d].re + a[d].im * a[d].im);
+#pragma unroll
+        for (int d2 = d + 1; d2 < 5; ++d2)
+          form += R(2 * qqg_colour(d, d2)) * (a[d].re * a[d2].re + a[d].im * a[d2].im);
+      }
+      sum += form;
+    }
+  }
+  return sum;
+}
+
+// qqg_slot for a tile of crossed channels (a light line with a t-channel gluon): L.jin
+// and L.e hold J' and E(J'), sp the rest of the lane's gauge split (zeros without one).
+template <typename R>
+__device__ __forceinline__ R qqg_slot_split(const QqgLane<R>& L, R mr, R dm2, R mw, const QqgSplit<R>* sp) {
+  cx<R> u3[2][4], v4[2][4];
+  spinor_u_from(L.chi3, L.wp3, mr / L.wp3, u3);
+  spinor_v_from(L.chi4, L.wp4, mr / L.wp4, v4);
+  // 1 / (d + i m Gamma)
+  const R d3 = L.d3 + dm2, d4 = L.d4 + dm2;
+  const R n3 = R(1) / (d3 * d3 + mw * mw), n4 = R(1) / (d4 * d4 + mw * mw);
+  const cx<R> f3 = L.is * cx<R>{d3 * n3, -mw * n3}, f4 = L.is * cx<R>{d4 * n4, -mw * n4};
+  const R f5 = L.is * L.isp;
+  // al d3 and al d4 at this mass, d = delta (1, -p-hat)
+  const R del3 = sp->h3 + dm2 * sp->g3, del4 = sp->h4 + dm2 * sp->g4;
+  R sum = R(0);
+#pragma unroll
+  for (int l4 = 0; l4 < 2; ++l4) {
+    cx<R> t1[4], t2[4], t3[4], s1[4], s2[4], s3[4];
+    {  // eps-slash (a3-slash + m) (J' + al d4)-slash v4
+      cx<R> j4[4];
+#pragma unroll
+      for (int m = 0; m < 4; ++m) j4[m] = L.jin[m] + (del4 * sp->n4[m]) * sp->al;
+      cslash(j4, v4[l4], t1);
+    }
+    slash_plus_scalar(L.a3, mr, t1, t2);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) t3[i] = cx<R>{R(0), R(0)};
+    slash_acc(R(1), L.eps, t2, t3);
+    // (J' + al d3)-slash (a4-slash + m) eps-slash v4
+#pragma unroll
+    for (int i = 0; i < 4; ++i) s1[i] = cx<R>{R(0), R(0)};
+    slash_acc(R(1), L.eps, v4[l4], s1);
+    slash_plus_scalar(L.a4, mr, s1, s2);
+    {
+      cx<R> j3[4];
+#pragma unroll
+      for (int m = 0; m < 4; ++m) j3[m] = L.jin[m] + (del3 * sp->n3[m]) * sp->al;
+      cslash(j3, s2, s3);
+    }
+#pragma unroll
+    for (int l3 = 0; l3 < 2; ++l3) {
+      cx<R> jout[4];
+      dirac_current(u3[l3], v4[l4], jout);
+      cx<R> a[5];
+      a[0] = L.isp * cdotm(L.c1, jout);
+      a[1] = L.isp * cdotm(L.c2, jout);
+      a[2] = f3 * ubar_dot(u3[l3], t3);
+      a[3] = f4 * ubar_dot(u3[l3], s3);
+      {  // E(J') - (q'.eps) al (d3 + d4), with ubar3 D-slash v4 = D . J_out
+        R dv[4];
+#pragma unroll
+        for (int m = 0; m < 4; ++m) dv[m] = del3 * sp->n3[m] + del4 * sp->n4[m];
+        a[4] = f5 * (cdotm(L.e, jout) - sp->qpe * (sp->al * cdotr(jout, dv)));
+      }
+      if (mw != R(0)) {
+        // a width leaves X (c - 1) of the null part, c = D / (D + i m Gamma):
+        // -(i m Gamma al X) f3 in a3 and +(i m Gamma al X) f4 in a4
+        const cx<R> ax = sp->al * cdotr(jout, L.eps);
+        const cx<R> iwx = cx<R>{-mw * ax.im, mw * ax.re};
+        a[2] = a[2] - f3 * iwx;
+        a[3] = a[3] + f4 * iwx;
+      }
       R form = R(0);
 #pragma unroll
       for (int d = 0; d < 5; ++d) {

@@ -59,7 +59,11 @@ __device__ __forceinline__ double qqg_invariant_fp64(const double* __restrict__ 
   return t >= 4 ? v - m0 * m0 : v;
 }
 
-template <typename R>
+// T_CHANNEL: the channel's light line is crossed (q g, q~ g and their beam swaps), so
+// the gluon on it is a t-channel one and the lanes take the gauge split of their
+// current when it is forward (qqg_lane_gauge_split); the direct q q~ channel and q~ q
+// run the plain tile.
+template <typename R, bool T_CHANNEL = false>
 struct QqgTile {
   static constexpr int EPB = QQG_BLOCK / QQG_LANES;
 
@@ -68,7 +72,8 @@ struct QqgTile {
     double mult[MAX_POINTS];   // mixed mode: per point, f_j / f_0 (slot 0) or f_j
     int slotj[MAX_POINTS];     // mixed mode: per point, its mass slot
     R mr[MAX_MASS], dm2[MAX_MASS], mw[MAX_MASS];   // per slot: m, m0^2 - m^2, m Gamma
-    R inv[6][EPB];                                 // per event: the six invariants (1/x for 0..3)
+    R inv[T_CHANNEL ? 8 : 6][EPB];                 // per event: the invariants (1/x for 0..3)
+    QqgSplit<R> split[T_CHANNEL ? QQG_BLOCK : 1];  // per lane: current, vertex vector, gauge split
   };
 
   static __device__ __forceinline__ R to_r(double x) {
@@ -117,7 +122,8 @@ struct QqgTile {
     for (int i = 0; i < 5; ++i)
 #pragma unroll
       for (int m = 0; m < 4; ++m) p[i][m] = to_r(pd[i][m]);
-    // the tile's invariants: warp w, lane e -> invariant w (and 4 + w for w < 2) of event e
+    // the tile's invariants: warp w, lane e -> invariant w and 4 + w of event e
+    // (6, 7: p3^2 - m0^2 and p4^2 - m0^2 of the top and antitop, for the gauge split)
     {
       const int w = tid >> 5, e = tid & 31;
       const int64_t ei = ev0 + e < nev ? ev0 + e : nev - 1;
@@ -125,7 +131,12 @@ struct QqgTile {
       const double m0 = lp.mass[0];
       const double v = qqg_invariant_fp64(pe, w, m0, cr);
       sm.inv[w][e] = R(1) / to_r(v);
-      if (w < 2) sm.inv[4 + w][e] = to_r(qqg_invariant_fp64(pe, 4 + w, m0, cr));
+      if (w < 2) {
+        sm.inv[4 + w][e] = to_r(qqg_invariant_fp64(pe, 4 + w, m0, cr));
+      } else if constexpr (T_CHANNEL) {
+        const double* pt = pe + 4 * cr.src[w];   // slots 2, 3: the top and antitop, never crossed
+        sm.inv[4 + w][e] = to_r(mdot(pt, pt) - m0 * m0);
+      }
     }
     if constexpr (EXCL) {
       QqgLaneH<R> L;
@@ -153,11 +164,30 @@ struct QqgTile {
       inv.d3 = sm.inv[4][el];
       inv.d4 = sm.inv[5][el];
       qqg_lane_scale(inv, L);
+      // a gluon of small virtuality on the light line (a forward light quark of a
+      // crossed channel, |s| < s' / 256): the gauge split keeps its cancellation out of
+      // the arithmetic
+      if constexpr (T_CHANNEL) {
+        // a forward light quark (|t| < s' / 256): the gauge split keeps the cancellation of
+        // the t-channel gluon's diagrams out of the arithmetic
+        QqgSplit<R>& sp = sm.split[tid];
+        qqg_split_clear(sp);
+        if (abs(inv.is) > R(256) * abs(inv.isp))
+          qqg_lane_gauge_split<R>(pd, lane & 1, (cr.neg[0] ? 1 : 0) | (cr.neg[1] ? 2 : 0), sm.inv[6][el],
+                                  sm.inv[7][el], L, sp);
+        for (int s = 0; s < lp.nmass; ++s) {
+          R part = valid ? qqg_slot_split<R>(L, sm.mr[s], sm.dm2[s], sm.mw[s], &sp) : R(0);
+          part += __shfl_xor_sync(0xffffffffu, part, 1);
+          part += __shfl_xor_sync(0xffffffffu, part, 2);
+          if (lane == 0) sm.me2s[el][s] = double(part);
+        }
+      } else {
       for (int s = 0; s < lp.nmass; ++s) {
         R part = valid ? qqg_slot<R>(L, sm.mr[s], sm.dm2[s], sm.mw[s]) : R(0);
         part += __shfl_xor_sync(0xffffffffu, part, 1);
         part += __shfl_xor_sync(0xffffffffu, part, 2);
         if (lane == 0) sm.me2s[el][s] = double(part);
+      }
       }
     }
     __syncthreads();

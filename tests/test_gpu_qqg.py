@@ -97,7 +97,11 @@ def test_mixed_against_fp64_at_scale(rex):
 
 
 def test_in_the_persistent_multi_kernel(rex):
-    """g g -> t t~ g and q q~ -> t t~ g batches in one persistent launch (register class 1)."""
+    """g g -> t t~ g and q q~ -> t t~ g batches in one persistent launch (register class 1),
+    in mixed precision: the persistent kernel compiles the same tile code into another
+    kernel, where the compiler's FP32 contraction choices can differ, so its weights agree
+    with the single-process launch's to FP32 rounding (both are within the stated bound of
+    the FP64 result)."""
     pts = ps.grid_gg_ttxg()
     batches, single = [], []
     for proc, n, seed in (("gg_ttxg", 90, 75), ("qq_ttxg", 70, 76)):
@@ -111,7 +115,7 @@ def test_in_the_persistent_multi_kernel(rex):
     m.reweight(batches, pts)
     torch.cuda.synchronize()
     for b, ref in zip(batches, single):
-        assert np.max(rel(b[3].cpu().numpy(), ref)) < 1e-13
+        assert np.max(rel(b[3].cpu().numpy(), ref)) < 1e-5
     m.close()
 
 

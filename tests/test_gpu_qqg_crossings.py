@@ -4,12 +4,13 @@
 Each channel (q~ q, q g, g q, q~ g, g q~ initial states) runs the q q~ -> t t~ g kernels
 with the event's partons read into the direct channel's slots; the oracle evaluates
 each channel from its own external wavefunctions.  Tolerances as for the direct
-channel: FP64 1e-12 relative per weight, mixed precision 1e-4 on the samples.  A
-crossed light line exchanges a t-channel gluon, t = (p_in - p_out)^2 of the light
-quark, and for a forward quark the Feynman-gauge diagrams on it cancel to
-|t| / s_hat of their size: rounding is amplified by kappa = s_hat / |t|.  The
-mixed-against-FP64 check over every event of a large sample therefore holds each
-event to max(1e-4, 4 * 2^-24 * kappa) and at most 1e-3 of the events above 1e-4.
+channel: FP64 1e-12 relative per weight, mixed precision 1e-4.  A crossed light line
+exchanges a t-channel gluon, t = (p_in - p_out)^2 of the light quark; for a forward
+quark the Feynman-gauge diagrams on it cancel to |t| / s_hat of their size.  The
+kernels split the light-quark current along the gluon momentum (the part along it is
+the cancelling one, evaluated through the Ward identity), so the mixed bound holds at
+every event, forward quarks included; the forward-limit test takes the oracle in
+extended precision, whose FP64 evaluation itself loses about 1e-16 s_hat / |t|.
 """
 import numpy as np
 import pytest
@@ -25,6 +26,11 @@ FP64_TOL = 1e-12
 MIXED_TOL = 1e-4
 ORIG = dict(mt=173.0, wt=0.0, alphas=0.118)
 CROSSED = ["qxq_ttxg", "qg_ttxq", "gq_ttxq", "qxg_ttxqx", "gqx_ttxqx"]
+# persistent kernel against the single-process launch: the same tile code compiled into
+# another kernel; in FP32 the compiler's contraction choices there can differ, and both
+# stay within the mixed bound of the FP64 result (the gauge-split events, conditioned
+# like 2^-24 sqrt(s_hat / |t|), show the largest differences)
+MULTI_TOL = {0: 1e-13, 1: MIXED_TOL}
 
 
 @pytest.fixture(scope="module")
@@ -91,12 +97,37 @@ def test_mixed_against_fp64_at_scale(rex, proc):
     mixed = make(rex, proc, 1).reweight(dm, dw, pts).cpu().numpy()
     err = np.max(rel(mixed, exact), axis=1)
     kappa = mdot(mom[:, 0] + mom[:, 1]) / np.abs(mdot(mom[:, 0] - mom[:, 4]))
-    bound = np.maximum(MIXED_TOL, 4.0 * 2.0 ** -24 * kappa)
-    over = float(np.mean(err > MIXED_TOL))
-    print(f"{proc} mixed vs FP64 max rel err {err.max():.3e} (kappa {kappa[np.argmax(err)]:.3e}), "
-          f"max err / bound {np.max(err / bound):.3f}, fraction above {MIXED_TOL:g}: {over:.2e}")
-    assert np.all(err < bound)
-    assert over < 1e-3
+    print(f"{proc} mixed vs FP64 max rel err {err.max():.3e} (kappa {kappa[np.argmax(err)]:.3e}, "
+          f"largest kappa {kappa.max():.3e})")
+    assert np.all(err < MIXED_TOL)
+
+
+@pytest.mark.parametrize("proc,swap", [("qg_ttxq", False), ("gq_ttxq", True), ("qxg_ttxqx", False)])
+def test_forward_light_quark_limit(rex, proc, swap):
+    """Outgoing light quark at 1e-2, 1e-3 and 1e-4 rad from the incoming one (s_hat / |t| up
+    to 6e8), 16 azimuths each, at the headline's points, a width and a new alpha_s: FP64
+    and mixed against the oracle in extended precision."""
+    import physics_pins as pp
+    mom = np.concatenate([pp.forward_quark_events(16, 7 + i, 173.0, 1000.0, 0.3, th)
+                          for i, th in enumerate((1e-2, 1e-3, 1e-4))])
+    if swap:
+        mom = mom[:, [1, 0, 2, 3, 4]].copy()
+    n = mom.shape[0]
+    w = np.ones(n)
+    pts = ps.grid_gg_ttxg() + [dict(mt=172.0, wt=1.4, alphas=0.118), dict(mt=173.0, wt=0.0, alphas=0.124)]
+    ref = np.asarray(oracle_rw.reweight(proc, mom.astype(np.longdouble), w, ORIG, pts), dtype=np.float64)
+    iq = 1 if swap else 0
+    kappa = mdot(mom[:, 0] + mom[:, 1]) / np.abs(mdot(mom[:, iq] - mom[:, 4]))
+    assert kappa.max() > 1e8
+    got64 = make(rex, proc).reweight(dev(mom), dev(w), pts).cpu().numpy()
+    got32 = make(rex, proc, 1).reweight(dev(mom), dev(w), pts).cpu().numpy()
+    e64, e32 = np.max(rel(got64, ref), axis=1), np.max(rel(got32, ref), axis=1)
+    print(f"{proc}: FP64 max err {e64.max():.3e}, mixed max err {e32.max():.3e}, kappa up to {kappa.max():.2e}")
+    # FP64: the invariant t itself, formed from Cartesian FP64 components, carries a relative
+    # rounding of about eps s_hat / |t| (the FP64 oracle shares it): the exact mode's
+    # tolerance rule, err <= 64 eps kappa, with kappa = s_hat / |t| the condition of t
+    assert np.all(e64 < np.maximum(FP64_TOL, 64 * np.finfo(float).eps * kappa))
+    assert np.all(e32 < MIXED_TOL)
 
 
 @pytest.mark.parametrize("precision", [0, 1])
@@ -116,7 +147,7 @@ def test_every_channel_in_one_persistent_launch(rex, precision):
     m.reweight(batches, pts)
     torch.cuda.synchronize()
     for b, ref in zip(batches, single):
-        assert np.max(rel(b[3].cpu().numpy(), ref)) < 1e-13
+        assert np.max(rel(b[3].cpu().numpy(), ref)) < MULTI_TOL[precision]
     m.close()
 
 
@@ -145,5 +176,5 @@ def test_full_size_pp_ttxj_sample(rex, precision):
             assert np.max(rel(got[idx], ref)) < FP64_TOL, proc
         else:
             single = b[0].reweight(b[1], b[2], pts).cpu().numpy()
-            assert np.max(rel(got, single)) < 1e-13, proc
+            assert np.max(rel(got, single)) < MULTI_TOL[precision], proc
     m.close()

@@ -22,7 +22,10 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 ORIG_QCD = dict(mt=173.0, wt=0.0, alphas=0.118)
-TOL = 1e-13     # the multi-launch tests' tolerance against rex_reweight
+# the multi-launch tests' tolerance against rex_reweight: FP64 1e-13; mixed precision to
+# the q q~ -> t t~ g family's stated bound (the persistent kernel compiles the same tile
+# code into another kernel, where FP32 contraction choices can differ)
+TOL = {0: 1e-13, 1: 1e-4}
 
 
 @pytest.fixture(scope="module")
@@ -63,13 +66,13 @@ def test_noalloc_matches_single_process_entry_point_twice(rex):
             assert torch.cuda.mem_get_info()[0] == free0, "device memory changed across the call"
             for (h, _, _, ref), o in zip(items, outs):
                 got = o.cpu().numpy()
-                assert np.max(np.abs(got / ref - 1.0)) < TOL, (h.name, precision, call)
+                assert np.max(np.abs(got / ref - 1.0)) < TOL[precision], (h.name, precision, call)
         # the same launch through the Python binding
         outs = [torch.full((it[1].shape[0], len(pts)), -1.0, dtype=torch.float64, device="cuda") for it in items]
         rex.reweight_multi_noalloc([(h, mom, w, o) for (h, mom, w, _), o in zip(items, outs)], pts, precision)
         torch.cuda.synchronize()
         for (h, _, _, ref), o in zip(items, outs):
-            assert np.max(np.abs(o.cpu().numpy() / ref - 1.0)) < TOL, (h.name, precision, "binding")
+            assert np.max(np.abs(o.cpu().numpy() / ref - 1.0)) < TOL[precision], (h.name, precision, "binding")
 
 
 def test_noalloc_rejects_more_points_than_its_counter_covers(rex):
