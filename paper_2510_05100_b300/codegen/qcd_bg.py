@@ -136,7 +136,8 @@ def emit_process(name: str, ngluon: int) -> str:
     w(f"R ps[{ngs}][4];        // momentum sum of each gluon set")
     w(f"R fg[{ngs}];           // -1 / P^2 of each gluon set (P^2 in FP64)")
     w(f"R q[{nsuf}][4];        // -(p_tbar + P) of each suffix set")
-    w(f"double q2[{nsuf}];     // q^2 in FP64 (the mass slot subtracts m^2 in FP64)")
+    w(f"double q2[{nsuf}];     // q^2 in FP64 (the exact mode's mass slot subtracts m^2 in FP64)")
+    w(f"R qm[{nsuf}];          // q^2 - m0^2 (FP64, then R): the mixed mode's slot adds m0^2 - m^2 in R")
     w("cx<R> cht[2][2], chb[2][2];   // helicity 2-spinors chi-, chi+ of top / antitop")
     w("R wpt, iwpt, wptb, iwptb;     // omega_+ and 1/omega_+ of top / antitop")
     w("};", 0)
@@ -166,7 +167,7 @@ def emit_process(name: str, ngluon: int) -> str:
     w("template <typename R>", 0)
     w(f"__device__ __forceinline__ void {name}_event_phase1(const double* __restrict__ p, "
       f"{name}_event<R>& ev, int l, int nl) {{", 0)
-    w(f"for (int i = l; i < {npart * 4}; i += nl) ev.praw[i] = R(__ldg(p + i));")
+    w(f"for (int i = l; i < {npart * 4}; i += nl) ev.praw[i] = to_r<R>(__ldg(p + i));")
     w(f"for (int k = l; k < {len(dots)}; k += nl) {{")
     w("int a = 0, b = 0;", 2)
     w("switch (k) {", 2)
@@ -185,17 +186,18 @@ def emit_process(name: str, ngluon: int) -> str:
     w("", 0)
 
     # event setup, phase 2
-    w("// Event setup, phase 2 (after a barrier): lanes form the FP64 invariants; lane 0", 0)
-    w("// builds the R-typed vectors and the top/antitop spinor bases.", 0)
+    w("// Event setup, phase 2 (after a barrier): lanes form the FP64 invariants (q^2 also", 0)
+    w("// less m02, the square of the launch's reference mass); lane 0 builds the R-typed", 0)
+    w("// vectors and the top/antitop spinor bases.", 0)
     w("template <typename R>", 0)
-    w(f"__device__ __forceinline__ void {name}_event_phase2({name}_event<R>& ev, int l, int nl) {{", 0)
+    w(f"__device__ __forceinline__ void {name}_event_phase2({name}_event<R>& ev, double m02, int l, int nl) {{", 0)
     ninv = ngs + nsuf
     w(f"for (int k = l; k < {ninv}; k += nl) {{")
     w("switch (k) {", 2)
     for st, i in gidx.items():
-        w(f"case {i}: ev.fg[{i}] = R(-1) / R({inv_sq(sorted(st))}); break;", 3)
+        w(f"case {i}: ev.fg[{i}] = R(-1) / to_r<R>({inv_sq(sorted(st))}); break;", 3)
     for st, i in sidx.items():
-        w(f"case {ngs + i}: ev.q2[{i}] = {inv_sq(sorted(st) + [n])}; break;", 3)
+        w(f"case {ngs + i}: ev.q2[{i}] = {inv_sq(sorted(st) + [n])}; ev.qm[{i}] = to_r<R>(ev.q2[{i}] - m02); break;", 3)
     w("}", 2)
     w("}")
     w("if (l == 0) {")
@@ -228,20 +230,24 @@ def emit_process(name: str, ngluon: int) -> str:
     w("", 0)
 
     # mass setup
-    w("// Per (event, mass), run by every lane l of nl: inverse propagator denominators", 0)
-    w("// (q^2 - m^2 in FP64, the reciprocal in R); lane 0 builds the top spinors.", 0)
+    w("// Per (event, mass), run by every lane l of nl: inverse propagator denominators,", 0)
+    w("// q^2 - m^2 in FP64 in the exact mode; in the mixed mode (R = float) (q^2 - m0^2) +", 0)
+    w("// (m0^2 - m^2) in R with dm2 = m0^2 - m^2 from the launch's slot table, so the slot", 0)
+    w("// loop issues no FP64 instruction (exact at the reference mass, where dm2 = 0, and", 0)
+    w("// free of cancellation elsewhere); lane 0 builds the top spinors.", 0)
     w("template <typename R, bool WIDTH>", 0)
-    w(f"__device__ __forceinline__ void {name}_mass_setup(const {name}_event<R>& ev, double mt, double wt, "
+    w(f"__device__ __forceinline__ void {name}_mass_setup(const {name}_event<R>& ev, double mt, double wt, R dm2, "
       f"{name}_mass<R>& mm, int l, int nl) {{", 0)
+    w("constexpr bool F32 = std::is_same<R, float>::value;")
     w("const double m2 = mt * mt;")
-    w("const R mw = R(mt * wt);")
+    w("const R mw = F32 ? to_r<R>(mt) * to_r<R>(wt) : R(mt * wt);")
     w(f"for (int i = l; i < {nsuf}; i += nl) {{")
-    w("const R d = R(ev.q2[i] - m2);", 2)
+    w("const R d = F32 ? ev.qm[i] + dm2 : R(ev.q2[i] - m2);", 2)
     w("if (WIDTH) { const R nn = R(1) / (d * d + mw * mw); mm.idr[i] = d * nn; mm.idi[i] = -mw * nn; }", 2)
     w("else { mm.idr[i] = R(1) / d; mm.idi[i] = R(0); }", 2)
     w("}")
     w("if (l == 0) {")
-    w("const R mr = R(mt);", 2)
+    w("const R mr = to_r<R>(mt);", 2)
     w("mm.m = mr;", 2)
     w("spinor_u_from(ev.cht, ev.wpt, mr * ev.iwpt, mm.ut);", 2)
     w("spinor_v_from(ev.chb, ev.wptb, mr * ev.iwptb, mm.v);", 2)

@@ -52,7 +52,8 @@ struct gg_ttx_event {
   R ps[1][4];        // momentum sum of each gluon set
   R fg[1];           // -1 / P^2 of each gluon set (P^2 in FP64)
   R q[2][4];        // -(p_tbar + P) of each suffix set
-  double q2[2];     // q^2 in FP64 (the mass slot subtracts m^2 in FP64)
+  double q2[2];     // q^2 in FP64 (the exact mode's mass slot subtracts m^2 in FP64)
+  R qm[2];          // q^2 - m0^2 (FP64, then R): the mixed mode's slot adds m0^2 - m^2 in R
   cx<R> cht[2][2], chb[2][2];   // helicity 2-spinors chi-, chi+ of top / antitop
   R wpt, iwpt, wptb, iwptb;     // omega_+ and 1/omega_+ of top / antitop
 };
@@ -78,7 +79,7 @@ struct gg_ttx_gluons {   // colour-ordered gluon currents of one polarisation co
 // soft or collinear gluons are built from these FP64 products.
 template <typename R>
 __device__ __forceinline__ void gg_ttx_event_phase1(const double* __restrict__ p, gg_ttx_event<R>& ev, int l, int nl) {
-  for (int i = l; i < 16; i += nl) ev.praw[i] = R(__ldg(p + i));
+  for (int i = l; i < 16; i += nl) ev.praw[i] = to_r<R>(__ldg(p + i));
   for (int k = l; k < 6; k += nl) {
     int a = 0, b = 0;
     switch (k) {
@@ -98,15 +99,16 @@ __device__ __forceinline__ void gg_ttx_event_phase1(const double* __restrict__ p
   }
 }
 
-// Event setup, phase 2 (after a barrier): lanes form the FP64 invariants; lane 0
-// builds the R-typed vectors and the top/antitop spinor bases.
+// Event setup, phase 2 (after a barrier): lanes form the FP64 invariants (q^2 also
+// less m02, the square of the launch's reference mass); lane 0 builds the R-typed
+// vectors and the top/antitop spinor bases.
 template <typename R>
-__device__ __forceinline__ void gg_ttx_event_phase2(gg_ttx_event<R>& ev, int l, int nl) {
+__device__ __forceinline__ void gg_ttx_event_phase2(gg_ttx_event<R>& ev, double m02, int l, int nl) {
   for (int k = l; k < 3; k += nl) {
     switch (k) {
-      case 0: ev.fg[0] = R(-1) / R(ev.dd[0] + ev.dd[3] + 2.0 * ev.dd[1]); break;
-      case 1: ev.q2[0] = ev.dd[0] + ev.dd[5] + 2.0 * ev.dd[2]; break;
-      case 2: ev.q2[1] = ev.dd[3] + ev.dd[5] + 2.0 * ev.dd[4]; break;
+      case 0: ev.fg[0] = R(-1) / to_r<R>(ev.dd[0] + ev.dd[3] + 2.0 * ev.dd[1]); break;
+      case 1: ev.q2[0] = ev.dd[0] + ev.dd[5] + 2.0 * ev.dd[2]; ev.qm[0] = to_r<R>(ev.q2[0] - m02); break;
+      case 2: ev.q2[1] = ev.dd[3] + ev.dd[5] + 2.0 * ev.dd[4]; ev.qm[1] = to_r<R>(ev.q2[1] - m02); break;
     }
   }
   if (l == 0) {
@@ -133,19 +135,23 @@ __device__ __forceinline__ void gg_ttx_event_phase2(gg_ttx_event<R>& ev, int l, 
   }
 }
 
-// Per (event, mass), run by every lane l of nl: inverse propagator denominators
-// (q^2 - m^2 in FP64, the reciprocal in R); lane 0 builds the top spinors.
+// Per (event, mass), run by every lane l of nl: inverse propagator denominators,
+// q^2 - m^2 in FP64 in the exact mode; in the mixed mode (R = float) (q^2 - m0^2) +
+// (m0^2 - m^2) in R with dm2 = m0^2 - m^2 from the launch's slot table, so the slot
+// loop issues no FP64 instruction (exact at the reference mass, where dm2 = 0, and
+// free of cancellation elsewhere); lane 0 builds the top spinors.
 template <typename R, bool WIDTH>
-__device__ __forceinline__ void gg_ttx_mass_setup(const gg_ttx_event<R>& ev, double mt, double wt, gg_ttx_mass<R>& mm, int l, int nl) {
+__device__ __forceinline__ void gg_ttx_mass_setup(const gg_ttx_event<R>& ev, double mt, double wt, R dm2, gg_ttx_mass<R>& mm, int l, int nl) {
+  constexpr bool F32 = std::is_same<R, float>::value;
   const double m2 = mt * mt;
-  const R mw = R(mt * wt);
+  const R mw = F32 ? to_r<R>(mt) * to_r<R>(wt) : R(mt * wt);
   for (int i = l; i < 2; i += nl) {
-    const R d = R(ev.q2[i] - m2);
+    const R d = F32 ? ev.qm[i] + dm2 : R(ev.q2[i] - m2);
     if (WIDTH) { const R nn = R(1) / (d * d + mw * mw); mm.idr[i] = d * nn; mm.idi[i] = -mw * nn; }
     else { mm.idr[i] = R(1) / d; mm.idi[i] = R(0); }
   }
   if (l == 0) {
-    const R mr = R(mt);
+    const R mr = to_r<R>(mt);
     mm.m = mr;
     spinor_u_from(ev.cht, ev.wpt, mr * ev.iwpt, mm.ut);
     spinor_v_from(ev.chb, ev.wptb, mr * ev.iwptb, mm.v);
@@ -277,7 +283,8 @@ struct gg_ttxg_event {
   R ps[4][4];        // momentum sum of each gluon set
   R fg[4];           // -1 / P^2 of each gluon set (P^2 in FP64)
   R q[6][4];        // -(p_tbar + P) of each suffix set
-  double q2[6];     // q^2 in FP64 (the mass slot subtracts m^2 in FP64)
+  double q2[6];     // q^2 in FP64 (the exact mode's mass slot subtracts m^2 in FP64)
+  R qm[6];          // q^2 - m0^2 (FP64, then R): the mixed mode's slot adds m0^2 - m^2 in R
   cx<R> cht[2][2], chb[2][2];   // helicity 2-spinors chi-, chi+ of top / antitop
   R wpt, iwpt, wptb, iwptb;     // omega_+ and 1/omega_+ of top / antitop
 };
@@ -309,7 +316,7 @@ struct gg_ttxg_gluons {   // colour-ordered gluon currents of one polarisation c
 // soft or collinear gluons are built from these FP64 products.
 template <typename R>
 __device__ __forceinline__ void gg_ttxg_event_phase1(const double* __restrict__ p, gg_ttxg_event<R>& ev, int l, int nl) {
-  for (int i = l; i < 20; i += nl) ev.praw[i] = R(__ldg(p + i));
+  for (int i = l; i < 20; i += nl) ev.praw[i] = to_r<R>(__ldg(p + i));
   for (int k = l; k < 10; k += nl) {
     int a = 0, b = 0;
     switch (k) {
@@ -333,22 +340,23 @@ __device__ __forceinline__ void gg_ttxg_event_phase1(const double* __restrict__ 
   }
 }
 
-// Event setup, phase 2 (after a barrier): lanes form the FP64 invariants; lane 0
-// builds the R-typed vectors and the top/antitop spinor bases.
+// Event setup, phase 2 (after a barrier): lanes form the FP64 invariants (q^2 also
+// less m02, the square of the launch's reference mass); lane 0 builds the R-typed
+// vectors and the top/antitop spinor bases.
 template <typename R>
-__device__ __forceinline__ void gg_ttxg_event_phase2(gg_ttxg_event<R>& ev, int l, int nl) {
+__device__ __forceinline__ void gg_ttxg_event_phase2(gg_ttxg_event<R>& ev, double m02, int l, int nl) {
   for (int k = l; k < 10; k += nl) {
     switch (k) {
-      case 0: ev.fg[0] = R(-1) / R(ev.dd[0] + ev.dd[4] + 2.0 * ev.dd[1]); break;
-      case 1: ev.fg[1] = R(-1) / R(ev.dd[0] + ev.dd[7] + 2.0 * ev.dd[2]); break;
-      case 2: ev.fg[2] = R(-1) / R(ev.dd[4] + ev.dd[7] + 2.0 * ev.dd[5]); break;
-      case 3: ev.fg[3] = R(-1) / R(ev.dd[0] + ev.dd[4] + ev.dd[7] + 2.0 * ev.dd[1] + 2.0 * ev.dd[2] + 2.0 * ev.dd[5]); break;
-      case 4: ev.q2[0] = ev.dd[0] + ev.dd[9] + 2.0 * ev.dd[3]; break;
-      case 5: ev.q2[1] = ev.dd[4] + ev.dd[9] + 2.0 * ev.dd[6]; break;
-      case 6: ev.q2[2] = ev.dd[7] + ev.dd[9] + 2.0 * ev.dd[8]; break;
-      case 7: ev.q2[3] = ev.dd[0] + ev.dd[4] + ev.dd[9] + 2.0 * ev.dd[1] + 2.0 * ev.dd[3] + 2.0 * ev.dd[6]; break;
-      case 8: ev.q2[4] = ev.dd[0] + ev.dd[7] + ev.dd[9] + 2.0 * ev.dd[2] + 2.0 * ev.dd[3] + 2.0 * ev.dd[8]; break;
-      case 9: ev.q2[5] = ev.dd[4] + ev.dd[7] + ev.dd[9] + 2.0 * ev.dd[5] + 2.0 * ev.dd[6] + 2.0 * ev.dd[8]; break;
+      case 0: ev.fg[0] = R(-1) / to_r<R>(ev.dd[0] + ev.dd[4] + 2.0 * ev.dd[1]); break;
+      case 1: ev.fg[1] = R(-1) / to_r<R>(ev.dd[0] + ev.dd[7] + 2.0 * ev.dd[2]); break;
+      case 2: ev.fg[2] = R(-1) / to_r<R>(ev.dd[4] + ev.dd[7] + 2.0 * ev.dd[5]); break;
+      case 3: ev.fg[3] = R(-1) / to_r<R>(ev.dd[0] + ev.dd[4] + ev.dd[7] + 2.0 * ev.dd[1] + 2.0 * ev.dd[2] + 2.0 * ev.dd[5]); break;
+      case 4: ev.q2[0] = ev.dd[0] + ev.dd[9] + 2.0 * ev.dd[3]; ev.qm[0] = to_r<R>(ev.q2[0] - m02); break;
+      case 5: ev.q2[1] = ev.dd[4] + ev.dd[9] + 2.0 * ev.dd[6]; ev.qm[1] = to_r<R>(ev.q2[1] - m02); break;
+      case 6: ev.q2[2] = ev.dd[7] + ev.dd[9] + 2.0 * ev.dd[8]; ev.qm[2] = to_r<R>(ev.q2[2] - m02); break;
+      case 7: ev.q2[3] = ev.dd[0] + ev.dd[4] + ev.dd[9] + 2.0 * ev.dd[1] + 2.0 * ev.dd[3] + 2.0 * ev.dd[6]; ev.qm[3] = to_r<R>(ev.q2[3] - m02); break;
+      case 8: ev.q2[4] = ev.dd[0] + ev.dd[7] + ev.dd[9] + 2.0 * ev.dd[2] + 2.0 * ev.dd[3] + 2.0 * ev.dd[8]; ev.qm[4] = to_r<R>(ev.q2[4] - m02); break;
+      case 9: ev.q2[5] = ev.dd[4] + ev.dd[7] + ev.dd[9] + 2.0 * ev.dd[5] + 2.0 * ev.dd[6] + 2.0 * ev.dd[8]; ev.qm[5] = to_r<R>(ev.q2[5] - m02); break;
     }
   }
   if (l == 0) {
@@ -390,19 +398,23 @@ __device__ __forceinline__ void gg_ttxg_event_phase2(gg_ttxg_event<R>& ev, int l
   }
 }
 
-// Per (event, mass), run by every lane l of nl: inverse propagator denominators
-// (q^2 - m^2 in FP64, the reciprocal in R); lane 0 builds the top spinors.
+// Per (event, mass), run by every lane l of nl: inverse propagator denominators,
+// q^2 - m^2 in FP64 in the exact mode; in the mixed mode (R = float) (q^2 - m0^2) +
+// (m0^2 - m^2) in R with dm2 = m0^2 - m^2 from the launch's slot table, so the slot
+// loop issues no FP64 instruction (exact at the reference mass, where dm2 = 0, and
+// free of cancellation elsewhere); lane 0 builds the top spinors.
 template <typename R, bool WIDTH>
-__device__ __forceinline__ void gg_ttxg_mass_setup(const gg_ttxg_event<R>& ev, double mt, double wt, gg_ttxg_mass<R>& mm, int l, int nl) {
+__device__ __forceinline__ void gg_ttxg_mass_setup(const gg_ttxg_event<R>& ev, double mt, double wt, R dm2, gg_ttxg_mass<R>& mm, int l, int nl) {
+  constexpr bool F32 = std::is_same<R, float>::value;
   const double m2 = mt * mt;
-  const R mw = R(mt * wt);
+  const R mw = F32 ? to_r<R>(mt) * to_r<R>(wt) : R(mt * wt);
   for (int i = l; i < 6; i += nl) {
-    const R d = R(ev.q2[i] - m2);
+    const R d = F32 ? ev.qm[i] + dm2 : R(ev.q2[i] - m2);
     if (WIDTH) { const R nn = R(1) / (d * d + mw * mw); mm.idr[i] = d * nn; mm.idi[i] = -mw * nn; }
     else { mm.idr[i] = R(1) / d; mm.idi[i] = R(0); }
   }
   if (l == 0) {
-    const R mr = R(mt);
+    const R mr = to_r<R>(mt);
     mm.m = mr;
     spinor_u_from(ev.cht, ev.wpt, mr * ev.iwpt, mm.ut);
     spinor_v_from(ev.chb, ev.wptb, mr * ev.iwptb, mm.v);
@@ -752,7 +764,8 @@ struct gg_ttxgg_event {
   R ps[11][4];        // momentum sum of each gluon set
   R fg[11];           // -1 / P^2 of each gluon set (P^2 in FP64)
   R q[14][4];        // -(p_tbar + P) of each suffix set
-  double q2[14];     // q^2 in FP64 (the mass slot subtracts m^2 in FP64)
+  double q2[14];     // q^2 in FP64 (the exact mode's mass slot subtracts m^2 in FP64)
+  R qm[14];          // q^2 - m0^2 (FP64, then R): the mixed mode's slot adds m0^2 - m^2 in R
   cx<R> cht[2][2], chb[2][2];   // helicity 2-spinors chi-, chi+ of top / antitop
   R wpt, iwpt, wptb, iwptb;     // omega_+ and 1/omega_+ of top / antitop
 };
@@ -809,7 +822,7 @@ struct gg_ttxgg_gluons {   // colour-ordered gluon currents of one polarisation 
 // soft or collinear gluons are built from these FP64 products.
 template <typename R>
 __device__ __forceinline__ void gg_ttxgg_event_phase1(const double* __restrict__ p, gg_ttxgg_event<R>& ev, int l, int nl) {
-  for (int i = l; i < 24; i += nl) ev.praw[i] = R(__ldg(p + i));
+  for (int i = l; i < 24; i += nl) ev.praw[i] = to_r<R>(__ldg(p + i));
   for (int k = l; k < 15; k += nl) {
     int a = 0, b = 0;
     switch (k) {
@@ -838,37 +851,38 @@ __device__ __forceinline__ void gg_ttxgg_event_phase1(const double* __restrict__
   }
 }
 
-// Event setup, phase 2 (after a barrier): lanes form the FP64 invariants; lane 0
-// builds the R-typed vectors and the top/antitop spinor bases.
+// Event setup, phase 2 (after a barrier): lanes form the FP64 invariants (q^2 also
+// less m02, the square of the launch's reference mass); lane 0 builds the R-typed
+// vectors and the top/antitop spinor bases.
 template <typename R>
-__device__ __forceinline__ void gg_ttxgg_event_phase2(gg_ttxgg_event<R>& ev, int l, int nl) {
+__device__ __forceinline__ void gg_ttxgg_event_phase2(gg_ttxgg_event<R>& ev, double m02, int l, int nl) {
   for (int k = l; k < 25; k += nl) {
     switch (k) {
-      case 0: ev.fg[0] = R(-1) / R(ev.dd[0] + ev.dd[5] + 2.0 * ev.dd[1]); break;
-      case 1: ev.fg[1] = R(-1) / R(ev.dd[0] + ev.dd[9] + 2.0 * ev.dd[2]); break;
-      case 2: ev.fg[2] = R(-1) / R(ev.dd[0] + ev.dd[12] + 2.0 * ev.dd[3]); break;
-      case 3: ev.fg[3] = R(-1) / R(ev.dd[5] + ev.dd[9] + 2.0 * ev.dd[6]); break;
-      case 4: ev.fg[4] = R(-1) / R(ev.dd[5] + ev.dd[12] + 2.0 * ev.dd[7]); break;
-      case 5: ev.fg[5] = R(-1) / R(ev.dd[9] + ev.dd[12] + 2.0 * ev.dd[10]); break;
-      case 6: ev.fg[6] = R(-1) / R(ev.dd[0] + ev.dd[5] + ev.dd[9] + 2.0 * ev.dd[1] + 2.0 * ev.dd[2] + 2.0 * ev.dd[6]); break;
-      case 7: ev.fg[7] = R(-1) / R(ev.dd[0] + ev.dd[5] + ev.dd[12] + 2.0 * ev.dd[1] + 2.0 * ev.dd[3] + 2.0 * ev.dd[7]); break;
-      case 8: ev.fg[8] = R(-1) / R(ev.dd[0] + ev.dd[9] + ev.dd[12] + 2.0 * ev.dd[2] + 2.0 * ev.dd[3] + 2.0 * ev.dd[10]); break;
-      case 9: ev.fg[9] = R(-1) / R(ev.dd[5] + ev.dd[9] + ev.dd[12] + 2.0 * ev.dd[6] + 2.0 * ev.dd[7] + 2.0 * ev.dd[10]); break;
-      case 10: ev.fg[10] = R(-1) / R(ev.dd[0] + ev.dd[5] + ev.dd[9] + ev.dd[12] + 2.0 * ev.dd[1] + 2.0 * ev.dd[2] + 2.0 * ev.dd[3] + 2.0 * ev.dd[6] + 2.0 * ev.dd[7] + 2.0 * ev.dd[10]); break;
-      case 11: ev.q2[0] = ev.dd[0] + ev.dd[14] + 2.0 * ev.dd[4]; break;
-      case 12: ev.q2[1] = ev.dd[5] + ev.dd[14] + 2.0 * ev.dd[8]; break;
-      case 13: ev.q2[2] = ev.dd[9] + ev.dd[14] + 2.0 * ev.dd[11]; break;
-      case 14: ev.q2[3] = ev.dd[12] + ev.dd[14] + 2.0 * ev.dd[13]; break;
-      case 15: ev.q2[4] = ev.dd[0] + ev.dd[5] + ev.dd[14] + 2.0 * ev.dd[1] + 2.0 * ev.dd[4] + 2.0 * ev.dd[8]; break;
-      case 16: ev.q2[5] = ev.dd[0] + ev.dd[9] + ev.dd[14] + 2.0 * ev.dd[2] + 2.0 * ev.dd[4] + 2.0 * ev.dd[11]; break;
-      case 17: ev.q2[6] = ev.dd[0] + ev.dd[12] + ev.dd[14] + 2.0 * ev.dd[3] + 2.0 * ev.dd[4] + 2.0 * ev.dd[13]; break;
-      case 18: ev.q2[7] = ev.dd[5] + ev.dd[9] + ev.dd[14] + 2.0 * ev.dd[6] + 2.0 * ev.dd[8] + 2.0 * ev.dd[11]; break;
-      case 19: ev.q2[8] = ev.dd[5] + ev.dd[12] + ev.dd[14] + 2.0 * ev.dd[7] + 2.0 * ev.dd[8] + 2.0 * ev.dd[13]; break;
-      case 20: ev.q2[9] = ev.dd[9] + ev.dd[12] + ev.dd[14] + 2.0 * ev.dd[10] + 2.0 * ev.dd[11] + 2.0 * ev.dd[13]; break;
-      case 21: ev.q2[10] = ev.dd[0] + ev.dd[5] + ev.dd[9] + ev.dd[14] + 2.0 * ev.dd[1] + 2.0 * ev.dd[2] + 2.0 * ev.dd[4] + 2.0 * ev.dd[6] + 2.0 * ev.dd[8] + 2.0 * ev.dd[11]; break;
-      case 22: ev.q2[11] = ev.dd[0] + ev.dd[5] + ev.dd[12] + ev.dd[14] + 2.0 * ev.dd[1] + 2.0 * ev.dd[3] + 2.0 * ev.dd[4] + 2.0 * ev.dd[7] + 2.0 * ev.dd[8] + 2.0 * ev.dd[13]; break;
-      case 23: ev.q2[12] = ev.dd[0] + ev.dd[9] + ev.dd[12] + ev.dd[14] + 2.0 * ev.dd[2] + 2.0 * ev.dd[3] + 2.0 * ev.dd[4] + 2.0 * ev.dd[10] + 2.0 * ev.dd[11] + 2.0 * ev.dd[13]; break;
-      case 24: ev.q2[13] = ev.dd[5] + ev.dd[9] + ev.dd[12] + ev.dd[14] + 2.0 * ev.dd[6] + 2.0 * ev.dd[7] + 2.0 * ev.dd[8] + 2.0 * ev.dd[10] + 2.0 * ev.dd[11] + 2.0 * ev.dd[13]; break;
+      case 0: ev.fg[0] = R(-1) / to_r<R>(ev.dd[0] + ev.dd[5] + 2.0 * ev.dd[1]); break;
+      case 1: ev.fg[1] = R(-1) / to_r<R>(ev.dd[0] + ev.dd[9] + 2.0 * ev.dd[2]); break;
+      case 2: ev.fg[2] = R(-1) / to_r<R>(ev.dd[0] + ev.dd[12] + 2.0 * ev.dd[3]); break;
+      case 3: ev.fg[3] = R(-1) / to_r<R>(ev.dd[5] + ev.dd[9] + 2.0 * ev.dd[6]); break;
+      case 4: ev.fg[4] = R(-1) / to_r<R>(ev.dd[5] + ev.dd[12] + 2.0 * ev.dd[7]); break;
+      case 5: ev.fg[5] = R(-1) / to_r<R>(ev.dd[9] + ev.dd[12] + 2.0 * ev.dd[10]); break;
+      case 6: ev.fg[6] = R(-1) / to_r<R>(ev.dd[0] + ev.dd[5] + ev.dd[9] + 2.0 * ev.dd[1] + 2.0 * ev.dd[2] + 2.0 * ev.dd[6]); break;
+      case 7: ev.fg[7] = R(-1) / to_r<R>(ev.dd[0] + ev.dd[5] + ev.dd[12] + 2.0 * ev.dd[1] + 2.0 * ev.dd[3] + 2.0 * ev.dd[7]); break;
+      case 8: ev.fg[8] = R(-1) / to_r<R>(ev.dd[0] + ev.dd[9] + ev.dd[12] + 2.0 * ev.dd[2] + 2.0 * ev.dd[3] + 2.0 * ev.dd[10]); break;
+      case 9: ev.fg[9] = R(-1) / to_r<R>(ev.dd[5] + ev.dd[9] + ev.dd[12] + 2.0 * ev.dd[6] + 2.0 * ev.dd[7] + 2.0 * ev.dd[10]); break;
+      case 10: ev.fg[10] = R(-1) / to_r<R>(ev.dd[0] + ev.dd[5] + ev.dd[9] + ev.dd[12] + 2.0 * ev.dd[1] + 2.0 * ev.dd[2] + 2.0 * ev.dd[3] + 2.0 * ev.dd[6] + 2.0 * ev.dd[7] + 2.0 * ev.dd[10]); break;
+      case 11: ev.q2[0] = ev.dd[0] + ev.dd[14] + 2.0 * ev.dd[4]; ev.qm[0] = to_r<R>(ev.q2[0] - m02); break;
+      case 12: ev.q2[1] = ev.dd[5] + ev.dd[14] + 2.0 * ev.dd[8]; ev.qm[1] = to_r<R>(ev.q2[1] - m02); break;
+      case 13: ev.q2[2] = ev.dd[9] + ev.dd[14] + 2.0 * ev.dd[11]; ev.qm[2] = to_r<R>(ev.q2[2] - m02); break;
+      case 14: ev.q2[3] = ev.dd[12] + ev.dd[14] + 2.0 * ev.dd[13]; ev.qm[3] = to_r<R>(ev.q2[3] - m02); break;
+      case 15: ev.q2[4] = ev.dd[0] + ev.dd[5] + ev.dd[14] + 2.0 * ev.dd[1] + 2.0 * ev.dd[4] + 2.0 * ev.dd[8]; ev.qm[4] = to_r<R>(ev.q2[4] - m02); break;
+      case 16: ev.q2[5] = ev.dd[0] + ev.dd[9] + ev.dd[14] + 2.0 * ev.dd[2] + 2.0 * ev.dd[4] + 2.0 * ev.dd[11]; ev.qm[5] = to_r<R>(ev.q2[5] - m02); break;
+      case 17: ev.q2[6] = ev.dd[0] + ev.dd[12] + ev.dd[14] + 2.0 * ev.dd[3] + 2.0 * ev.dd[4] + 2.0 * ev.dd[13]; ev.qm[6] = to_r<R>(ev.q2[6] - m02); break;
+      case 18: ev.q2[7] = ev.dd[5] + ev.dd[9] + ev.dd[14] + 2.0 * ev.dd[6] + 2.0 * ev.dd[8] + 2.0 * ev.dd[11]; ev.qm[7] = to_r<R>(ev.q2[7] - m02); break;
+      case 19: ev.q2[8] = ev.dd[5] + ev.dd[12] + ev.dd[14] + 2.0 * ev.dd[7] + 2.0 * ev.dd[8] + 2.0 * ev.dd[13]; ev.qm[8] = to_r<R>(ev.q2[8] - m02); break;
+      case 20: ev.q2[9] = ev.dd[9] + ev.dd[12] + ev.dd[14] + 2.0 * ev.dd[10] + 2.0 * ev.dd[11] + 2.0 * ev.dd[13]; ev.qm[9] = to_r<R>(ev.q2[9] - m02); break;
+      case 21: ev.q2[10] = ev.dd[0] + ev.dd[5] + ev.dd[9] + ev.dd[14] + 2.0 * ev.dd[1] + 2.0 * ev.dd[2] + 2.0 * ev.dd[4] + 2.0 * ev.dd[6] + 2.0 * ev.dd[8] + 2.0 * ev.dd[11]; ev.qm[10] = to_r<R>(ev.q2[10] - m02); break;
+      case 22: ev.q2[11] = ev.dd[0] + ev.dd[5] + ev.dd[12] + ev.dd[14] + 2.0 * ev.dd[1] + 2.0 * ev.dd[3] + 2.0 * ev.dd[4] + 2.0 * ev.dd[7] + 2.0 * ev.dd[8] + 2.0 * ev.dd[13]; ev.qm[11] = to_r<R>(ev.q2[11] - m02); break;
+      case 23: ev.q2[12] = ev.dd[0] + ev.dd[9] + ev.dd[12] + ev.dd[14] + 2.0 * ev.dd[2] + 2.0 * ev.dd[3] + 2.0 * ev.dd[4] + 2.0 * ev.dd[10] + 2.0 * ev.dd[11] + 2.0 * ev.dd[13]; ev.qm[12] = to_r<R>(ev.q2[12] - m02); break;
+      case 24: ev.q2[13] = ev.dd[5] + ev.dd[9] + ev.dd[12] + ev.dd[14] + 2.0 * ev.dd[6] + 2.0 * ev.dd[7] + 2.0 * ev.dd[8] + 2.0 * ev.dd[10] + 2.0 * ev.dd[11] + 2.0 * ev.dd[13]; ev.qm[13] = to_r<R>(ev.q2[13] - m02); break;
     }
   }
   if (l == 0) {
@@ -941,19 +955,23 @@ __device__ __forceinline__ void gg_ttxgg_event_phase2(gg_ttxgg_event<R>& ev, int
   }
 }
 
-// Per (event, mass), run by every lane l of nl: inverse propagator denominators
-// (q^2 - m^2 in FP64, the reciprocal in R); lane 0 builds the top spinors.
+// Per (event, mass), run by every lane l of nl: inverse propagator denominators,
+// q^2 - m^2 in FP64 in the exact mode; in the mixed mode (R = float) (q^2 - m0^2) +
+// (m0^2 - m^2) in R with dm2 = m0^2 - m^2 from the launch's slot table, so the slot
+// loop issues no FP64 instruction (exact at the reference mass, where dm2 = 0, and
+// free of cancellation elsewhere); lane 0 builds the top spinors.
 template <typename R, bool WIDTH>
-__device__ __forceinline__ void gg_ttxgg_mass_setup(const gg_ttxgg_event<R>& ev, double mt, double wt, gg_ttxgg_mass<R>& mm, int l, int nl) {
+__device__ __forceinline__ void gg_ttxgg_mass_setup(const gg_ttxgg_event<R>& ev, double mt, double wt, R dm2, gg_ttxgg_mass<R>& mm, int l, int nl) {
+  constexpr bool F32 = std::is_same<R, float>::value;
   const double m2 = mt * mt;
-  const R mw = R(mt * wt);
+  const R mw = F32 ? to_r<R>(mt) * to_r<R>(wt) : R(mt * wt);
   for (int i = l; i < 14; i += nl) {
-    const R d = R(ev.q2[i] - m2);
+    const R d = F32 ? ev.qm[i] + dm2 : R(ev.q2[i] - m2);
     if (WIDTH) { const R nn = R(1) / (d * d + mw * mw); mm.idr[i] = d * nn; mm.idi[i] = -mw * nn; }
     else { mm.idr[i] = R(1) / d; mm.idi[i] = R(0); }
   }
   if (l == 0) {
-    const R mr = R(mt);
+    const R mr = to_r<R>(mt);
     mm.m = mr;
     spinor_u_from(ev.cht, ev.wpt, mr * ev.iwpt, mm.ut);
     spinor_v_from(ev.chb, ev.wptb, mr * ev.iwptb, mm.v);

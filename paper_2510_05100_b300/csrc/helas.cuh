@@ -20,9 +20,21 @@
 #pragma once
 #if defined(__CUDACC__)
 #include <cuda_runtime.h>
+
+#include "fpconv.cuh"
 #endif
 
 namespace rex {
+
+// FP64 -> R.  In device code R = float converts on the integer ALUs (fpconv.cuh:
+// round to nearest even, B300 issues FP64-pipe conversions at 1/64 of the FP32 rate);
+// any other R is a plain conversion.
+template <typename R>
+__device__ __forceinline__ R to_r(double x) { return R(x); }
+#if defined(__CUDACC__)
+template <>
+__device__ __forceinline__ float to_r<float>(double x) { return f64_to_f32_alu(x); }
+#endif
 
 template <typename R>
 struct cx {

@@ -52,13 +52,14 @@ struct QcdProc;
       NAME##_event_phase1(p, ev, l, nl);                                                      \
     }                                                                                         \
     template <typename R>                                                                     \
-    static __device__ __forceinline__ void event_phase2(event<R>& ev, int l, int nl) {        \
-      NAME##_event_phase2(ev, l, nl);                                                         \
+    static __device__ __forceinline__ void event_phase2(event<R>& ev, double m02, int l,      \
+                                                        int nl) {                             \
+      NAME##_event_phase2(ev, m02, l, nl);                                                    \
     }                                                                                         \
     template <typename R, bool W>                                                             \
     static __device__ __forceinline__ void mass_setup(const event<R>& ev, double m, double w, \
-                                                      mass<R>& mm, int l, int nl) {           \
-      NAME##_mass_setup<R, W>(ev, m, w, mm, l, nl);                                           \
+                                                      R dm2, mass<R>& mm, int l, int nl) {    \
+      NAME##_mass_setup<R, W>(ev, m, w, dm2, mm, l, nl);                                      \
     }                                                                                         \
     template <typename R>                                                                     \
     static __device__ __forceinline__ void gluon_currents(const event<R>& ev,                 \
@@ -161,10 +162,14 @@ struct QcdTile {
   static_assert(NH <= 32, "one event per warp at most");
   static_assert(!EXCL || (SPLIT == 0 && !TC), "helicity-exclusive tiles: one lane per gluon configuration");
 
+  static constexpr bool F32 = std::is_same<R, float>::value;
   struct Smem {
-    double me2s[EPB][MAX_MASS + 1];
-    double mult[MAX_POINTS];   // mixed mode: per point, f_j / f_0 (slot 0) or f_j
+    double me2s[EPB][F32 ? 1 : MAX_MASS + 1];   // exact mode: the slot sums; mixed mode: w
+    float me2f[F32 ? EPB : 1][MAX_MASS + 1];   // mixed mode: the FP32 slot sums
+    double mult[MAX_POINTS];   // mixed mode: per point, f_j / f_0
+    float multf[MAX_POINTS];   // mixed mode: the same in FP32
     int slotj[MAX_POINTS];     // mixed mode: per point, its mass slot
+    R dm2[MAX_MASS];           // per slot: m0^2 - m^2 (the mixed mode's propagators)
     typename P::template event<R> evs[EPB];
     typename P::template mass<R> mss[EPB];
     alignas(16) __half tc[TC ? QCD_BLOCK / 32 : 1][TC ? ColourTc<NF>::WARP_HALVES : 1];
@@ -188,10 +193,13 @@ struct QcdTile {
     const int64_t evc = valid ? ev : nev - 1;
 
     // a1/a2: the event's lanes load its FP64 momenta, convert them and form the
-    // FP64 invariants cooperatively (two phases, block barriers between them)
+    // FP64 invariants cooperatively (two phases, block barriers between them); the
+    // slot table of m0^2 - m^2 (m0 = slot 0's mass) for the mixed mode's propagators
+    const double m0 = lp.mass[0];
+    for (int m = tid; m < lp.nmass; m += QCD_BLOCK) sm.dm2[m] = to_r<R>((m0 - lp.mass[m]) * (m0 + lp.mass[m]));
     P::event_phase1(mom + evc * (NPART * 4), sm.evs[el], lane_ev, NH);
     __syncthreads();
-    P::event_phase2(sm.evs[el], lane_ev, NH);
+    P::event_phase2(sm.evs[el], m0 * m0, lane_ev, NH);
     __syncthreads();
     const auto& evd = sm.evs[el];
 
@@ -228,7 +236,7 @@ struct QcdTile {
 
     // a3-a7 per distinct mass slot
     for (int m = 0; m < lp.nmass; ++m) {
-      P::template mass_setup<R, WIDTH>(evd, lp.mass[m], lp.width[m], sm.mss[el], lane_ev, NH);
+      P::template mass_setup<R, WIDTH>(evd, lp.mass[m], lp.width[m], sm.dm2[m], sm.mss[el], lane_ev, NH);
       __syncthreads();
       // a7: the helicity sum adds non-negative terms (no cancellation): FP64 in the
       // exact mode, FP32 in the mixed mode (relative error <= 64 * 2^-24)
@@ -250,7 +258,10 @@ struct QcdTile {
       }
 #pragma unroll
       for (int off = NH / 2; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
-      if (leader) sm.me2s[el][m] = double(s);
+      if (leader) {
+        if constexpr (F32) sm.me2f[el][m] = s;
+        else sm.me2s[el][m] = double(s);
+      }
       __syncthreads();
     }
 
@@ -268,21 +279,23 @@ struct QcdTile {
           out[(ev0 + e) * lp.out_stride + j] = (m0 == 0.0) ? 0.0 : w * (mj / m0);
         }
       } else {
-        // mixed mode (B300 issues FP64 at 1/64 of the FP32 rate): per event the slot
-        // sums become w |M_s|^2 / |M_0|^2 with one division, slot 0 holds w itself (0
-        // if |M_0|^2 == 0, NaN if it is NaN), and each output is one FP64 product with
-        // the point's multiplier, f_j / f_0 on the original slot (an unchanged point
-        // keeps its weight exactly) and f_j elsewhere
+        // mixed mode (B300 issues FP64 at 1/64 of the FP32 rate): the ratio in FP32.
+        // Per event the FP32 slot sums become w |M_s|^2 / |M_0|^2 (one FP32 division),
+        // and an output at slot s > 0 is that times f_j / f_0 in FP32, converted to FP64
+        // on the integer ALUs.  An output at the original slot is w (f_j / f_0) in FP64,
+        // so an unchanged point keeps its weight exactly; slot 0 holds w (0 if
+        // |M_0|^2 == 0, NaN if it is NaN).
         for (int j = tid; j < k; j += QCD_BLOCK) {
           sm.slotj[j] = lp.slot[j];
-          sm.mult[j] = lp.slot[j] == 0 ? lp.factor[j] / lp.factor0 : lp.factor[j];
+          sm.mult[j] = lp.factor[j] / lp.factor0;
+          sm.multf[j] = to_r<float>(sm.mult[j]);
         }
         for (int e = tid; e < nblk; e += QCD_BLOCK) {
-          const double m0 = sm.me2s[e][0] * lp.factor0;
+          const float m0 = sm.me2f[e][0];
           const double w = w_in[ev0 + e];
-          const double wi = m0 == 0.0 ? 0.0 : w / m0;
-          for (int sl = 1; sl < lp.nmass; ++sl) sm.me2s[e][sl] *= wi;
-          sm.me2s[e][0] = m0 == 0.0 ? 0.0 : (m0 == m0 ? w : m0);
+          const float wi = m0 == 0.f ? 0.f : to_r<float>(w) / m0;
+          for (int sl = 1; sl < lp.nmass; ++sl) sm.me2f[e][sl] *= wi;
+          sm.me2s[e][0] = m0 == 0.f ? 0.0 : (m0 == m0 ? w : (double)m0);
         }
         __syncthreads();
         // output idx = e * k + j; (e, j) advance without an integer division per output
@@ -290,7 +303,9 @@ struct QcdTile {
         int e = tid / kk, j = tid - (tid / kk) * kk;
         const int de = QCD_BLOCK / kk, dj = QCD_BLOCK - (QCD_BLOCK / kk) * kk;
         for (int idx = tid; idx < nblk * k; idx += QCD_BLOCK) {
-          out[(ev0 + e) * lp.out_stride + j] = sm.me2s[e][sm.slotj[j]] * sm.mult[j];
+          const int sl = sm.slotj[j];
+          out[(ev0 + e) * lp.out_stride + j] =
+              sl == 0 ? sm.me2s[e][0] * sm.mult[j] : f32_to_f64_alu(sm.me2f[e][sl] * sm.multf[j]);
           e += de;
           j += dj;
           if (j >= k) {
@@ -300,7 +315,8 @@ struct QcdTile {
         }
       }
     } else {
-      for (int e = tid; e < nblk; e += QCD_BLOCK) out[ev0 + e] = sm.me2s[e][0] * lp.factor0;
+      for (int e = tid; e < nblk; e += QCD_BLOCK)
+        out[ev0 + e] = (F32 ? (double)sm.me2f[e][0] : sm.me2s[e][0]) * lp.factor0;
     }
   }
 };

@@ -116,8 +116,8 @@ void count(const char* name, int nghel, ES es, MSF msf, GC gc, QL ql, bool last)
 #define REX_COUNT(NAME, NG, LAST)                                                                   \
   count<NG, NAME##_event<RC>, NAME##_mass<RC>, NAME##_gluons<RC>>(                                  \
       #NAME, 1 << NG,                                                                               \
-      [](const double* p, auto& ev) { NAME##_event_phase1(p, ev, 0, 1); NAME##_event_phase2(ev, 0, 1); }, \
-      [](auto& ev, double m, double w, auto& mm) { NAME##_mass_setup<RC, false>(ev, m, w, mm, 0, 1); }, \
+      [](const double* p, auto& ev) { NAME##_event_phase1(p, ev, 0, 1); NAME##_event_phase2(ev, 173.0 * 173.0, 0, 1); }, \
+      [](auto& ev, double m, double w, auto& mm) { NAME##_mass_setup<RC, false>(ev, m, w, RC(0.0), mm, 0, 1); }, \
       [](auto& ev, auto& eps, auto& J) { NAME##_gluon_currents(ev, eps, J); },                       \
       [](auto& ev, auto& mm, auto& J) { return NAME##_quark_line<RC, AC, false, RC>(ev, mm, J); }, LAST)
 
