@@ -273,6 +273,7 @@ def run_multi_leg(dev, stream, steps, world, barrier, max_over_ranks):
         batches.append((h, mom, torch.ones(n, dtype=torch.float64, device=dev),
                         torch.empty((n, len(pts)), dtype=torch.float64, device=dev)))
     m = rex.Multi(rex.MIXED)          # ee_mumu (FP64 only) joins the mixed launch
+    tune = m.autotune(batches, pts, stream=stream)   # slot groups by measurement
     m.capture(batches, pts)
     ms_streams = rex.Multi(rex.MIXED, rex.MULTI_STREAMS)   # one launch per batch, forked streams
     ms_streams.capture(batches, pts)
@@ -303,11 +304,13 @@ def run_multi_leg(dev, stream, steps, world, barrier, max_over_ranks):
     ms_graph = timed(graph_step)
     ms_seq = timed(sequential_step)
     ms_str = timed(lambda: ms_streams.replay(stream))
+    m_groups = m.slot_groups
     m.close()
     ms_streams.close()
     return {"workload": "10k ee_mumu (FP64) + 1M gg_ttx + 500k gg_ttxg + 100k gg_ttxgg (mixed) x 64 points",
             "value": rdist.job_throughput(units, world, ms_graph * 1e-3), "unit": UNIT,
-            "ms_per_step": ms_graph, "graph_launches_per_step": 1,
+            "ms_per_step": ms_graph, "graph_launches_per_step": 1, "slot_groups": m_groups,
+            "autotune_ms_per_launch": dict(zip((1, 2, 3, 4, 6, 8), tune)),
             "kernel_launches_per_step": 3,   # one persistent kernel per register class present
             "sequential_value": rdist.job_throughput(units, world, ms_seq * 1e-3),
             "sequential_ms_per_step": ms_seq,
@@ -345,6 +348,7 @@ def run_small_multi_leg(dev, stream, steps, world, barrier, max_over_ranks):
                         torch.empty((n, len(pts)), dtype=torch.float64, device=dev)))
     units = sum(b[1].shape[0] for b in batches) * len(pts)
     m = rex.Multi(rex.MIXED)
+    tune = m.autotune(batches, pts, stream=stream)   # slot groups by measurement
     m.capture(batches, pts)
     ms_streams = rex.Multi(rex.MIXED, rex.MULTI_STREAMS)
     ms_streams.capture(batches, pts)
@@ -378,6 +382,10 @@ def run_small_multi_leg(dev, stream, steps, world, barrier, max_over_ranks):
         return max_over_ranks(t0.elapsed_time(t1)) / steps
 
     ms_persistent = timed(lambda: m.replay(stream))
+    groups = m.slot_groups
+    m.slot_groups = 1
+    m.capture(batches, pts)
+    ms_persistent1 = timed(lambda: m.replay(stream))
     ms_seq_graph = timed(lambda: g.replay())
     ms_streams_graph = timed(lambda: ms_streams.replay(stream))
     ms_seq = timed(sequential_step)
@@ -388,7 +396,9 @@ def run_small_multi_leg(dev, stream, steps, world, barrier, max_over_ranks):
     desc = " + ".join(f"{n} {proc}" for proc, n, _, _ in SMALL_MULTI_BATCHES)
     val = lambda ms: rdist.job_throughput(units, world, ms * 1e-3)   # noqa: E731
     return {"workload": f"{desc}, 64 points each, mixed precision", "unit": UNIT, "steps": steps,
-            "persistent_graph": {"value": val(ms_persistent), "ms_per_step": ms_persistent},
+            "persistent_graph": {"value": val(ms_persistent), "ms_per_step": ms_persistent,
+                                 "slot_groups": groups, "autotune_ms_per_launch": dict(zip((1, 2, 3, 4, 6, 8), tune)),
+                                 "without_slot_groups_ms_per_step": ms_persistent1},
             "per_process_graph": {"value": val(ms_seq_graph), "ms_per_step": ms_seq_graph},
             "streams_graph": {"value": val(ms_streams_graph), "ms_per_step": ms_streams_graph},
             "sequential_launches": {"value": val(ms_seq), "ms_per_step": ms_seq},

@@ -245,6 +245,29 @@ int rex_multi_set_mode(rex_multi *m, int mode);
 int rex_reweight_multi(rex_multi *m, const rex_batch *batches, int nbatch,
                        const rex_params *param_sets, int k, void *stream);
 
+/* Slot groups of the persistent mode (the paper's observation that small
+ * subprocess batches leave a GPU latency bound, Sec. 4.2): each g g tile's
+ * distinct top-mass slots (beyond the original one) are split over `groups` work
+ * items, each of which evaluates the original slot and its share and writes the
+ * weights at those slots.  A batch of few tiles then spreads over more SMs, at
+ * the cost of re-evaluating the original slot once per group; large batches lose
+ * by it.  groups in [1, REX_MULTI_MAX_SLOT_GROUPS] (default 1; at most one slot
+ * per group is used).  Errors: REX_EINVAL.  rex_multi_get_slot_groups returns the
+ * setting (or REX_EINVAL). */
+#define REX_MULTI_MAX_SLOT_GROUPS 16
+int rex_multi_set_slot_groups(rex_multi *m, int groups);
+int rex_multi_get_slot_groups(const rex_multi *m);
+
+/* Pick the slot groups by measurement: runs rex_reweight_multi with these
+ * arguments for each of 1, 2, 3, 4, 6 and 8 groups (a warm-up and three timed
+ * launches each, CUDA events on stream), keeps the fastest in the handle and
+ * writes the mean times (ms, REX_MULTI_TUNE_CANDIDATES floats) to ms_out (host,
+ * may be NULL).  Overwrites the batches' w_out; synchronises stream.
+ * Errors: as rex_reweight_multi. */
+#define REX_MULTI_TUNE_CANDIDATES 6
+int rex_multi_autotune(rex_multi *m, const rex_batch *batches, int nbatch,
+                       const rex_params *param_sets, int k, void *stream, float *ms_out);
+
 /* Capture one rex_reweight_multi call (same arguments) into a CUDA graph kept
  * in the handle, replacing any earlier capture; rex_multi_replay launches it
  * on stream.  The graph reads the batch pointers given at capture time.

@@ -55,15 +55,21 @@ __global__ void __launch_bounds__(QCD_BLOCK, MINB)
     int b = 0;
     while (b + 1 < ml.nbatch && item >= ml.b[b].tile_end) ++b;
     const MultiBatch& B = ml.b[b];
-    const int64_t tile = item - B.tile_begin;
+    // a g g batch's item: (tile, slot group); slots 1 .. nmass-1 split evenly over the
+    // groups, slot 0 evaluated by each and its outputs written by group 0
+    const int64_t local = item - B.tile_begin;
+    const int64_t tile = local / B.ngroup;
+    const int grp = (int)(local - tile * B.ngroup);
+    const int nm1 = B.t.nmass - 1;
+    const int s_lo = 1 + (nm1 * grp) / B.ngroup, s_hi = 1 + (nm1 * (grp + 1)) / B.ngroup;
     switch (B.kind) {
       case PROC_EE_MUMU: ee_tile(B.mom, B.w_in, B.nev, tile, ml.ew, B.out); break;
-      case PROC_GG_TTX: T1::run(sm.a, B.mom, B.w_in, B.nev, tile, B.t, B.out); break;
+      case PROC_GG_TTX: T1::run(sm.a, B.mom, B.w_in, B.nev, tile, B.t, B.out, nullptr, s_lo, s_hi, grp == 0); break;
       case PROC_GG_TTXG:
-        if constexpr (CLASS >= 1) T2::run(sm.b, B.mom, B.w_in, B.nev, tile, B.t, B.out);
+        if constexpr (CLASS >= 1) T2::run(sm.b, B.mom, B.w_in, B.nev, tile, B.t, B.out, nullptr, s_lo, s_hi, grp == 0);
         break;
       case PROC_GG_TTXGG:
-        if constexpr (CLASS >= 2) T3::run(sm.c, B.mom, B.w_in, B.nev, tile, B.t, B.out);
+        if constexpr (CLASS >= 2) T3::run(sm.c, B.mom, B.w_in, B.nev, tile, B.t, B.out, nullptr, s_lo, s_hi, grp == 0);
         break;
       case PROC_QQ_TTX: T4::run(sm.d, B.mom, B.w_in, B.nev, tile, B.t, B.out); break;
       case PROC_QQ_TTXG:

@@ -175,11 +175,17 @@ struct QcdTile {
     alignas(16) __half tc[TC ? QCD_BLOCK / 32 : 1][TC ? ColourTc<NF>::WARP_HALVES : 1];
   };
 
+  // Slot group [s_lo, s_hi) (the persistent kernel's split of a tile's mass slots over
+  // several work items, for batches too small to fill the GPU): the tile evaluates slot
+  // 0 (the original point, every ratio's denominator) and the slots of its group, and
+  // writes the outputs at those slots, the ones at slot 0 only if own0.  The defaults
+  // take every slot.
   template <class TABLE>
   static __device__ __forceinline__ void run(Smem& sm, const double* __restrict__ mom,
                                              const double* __restrict__ w_in, int64_t nev, int64_t tile,
                                              const TABLE& lp, double* __restrict__ out,
-                                             const signed char* __restrict__ hel = nullptr) {
+                                             const signed char* __restrict__ hel = nullptr, int s_lo = 1,
+                                             int s_hi = MAX_MASS + 1, bool own0 = true) {
     const int tid = threadIdx.x;
     const int el = tid / NH;
     const int lane_ev = tid - el * NH;
@@ -234,8 +240,9 @@ struct QcdTile {
       }
     }
 
-    // a3-a7 per distinct mass slot
+    // a3-a7 per distinct mass slot (of the group)
     for (int m = 0; m < lp.nmass; ++m) {
+      if (m != 0 && (m < s_lo || m >= s_hi)) continue;
       P::template mass_setup<R, WIDTH>(evd, lp.mass[m], lp.width[m], sm.dm2[m], sm.mss[el], lane_ev, NH);
       __syncthreads();
       // a7: the helicity sum adds non-negative terms (no cancellation): FP64 in the
@@ -273,8 +280,10 @@ struct QcdTile {
         for (int idx = tid; idx < nblk * k; idx += QCD_BLOCK) {
           const int e = idx / k;
           const int j = idx - e * k;
+          const int sl = lp.slot[j];
+          if (sl == 0 ? !own0 : (sl < s_lo || sl >= s_hi)) continue;
           const double m0 = sm.me2s[e][0] * lp.factor0;
-          const double mj = sm.me2s[e][lp.slot[j]] * lp.factor[j];
+          const double mj = sm.me2s[e][sl] * lp.factor[j];
           const double w = w_in[ev0 + e];
           out[(ev0 + e) * lp.out_stride + j] = (m0 == 0.0) ? 0.0 : w * (mj / m0);
         }
@@ -294,7 +303,8 @@ struct QcdTile {
           const float m0 = sm.me2f[e][0];
           const double w = w_in[ev0 + e];
           const float wi = m0 == 0.f ? 0.f : to_r<float>(w) / m0;
-          for (int sl = 1; sl < lp.nmass; ++sl) sm.me2f[e][sl] *= wi;
+          const int lo = s_lo > 1 ? s_lo : 1, hi = s_hi < lp.nmass ? s_hi : lp.nmass;
+          for (int sl = lo; sl < hi; ++sl) sm.me2f[e][sl] *= wi;
           sm.me2s[e][0] = m0 == 0.f ? 0.0 : (m0 == m0 ? w : (double)m0);
         }
         __syncthreads();
@@ -304,8 +314,9 @@ struct QcdTile {
         const int de = QCD_BLOCK / kk, dj = QCD_BLOCK - (QCD_BLOCK / kk) * kk;
         for (int idx = tid; idx < nblk * k; idx += QCD_BLOCK) {
           const int sl = sm.slotj[j];
-          out[(ev0 + e) * lp.out_stride + j] =
-              sl == 0 ? sm.me2s[e][0] * sm.mult[j] : f32_to_f64_alu(sm.me2f[e][sl] * sm.multf[j]);
+          if (sl == 0 ? own0 : (sl >= s_lo && sl < s_hi))
+            out[(ev0 + e) * lp.out_stride + j] =
+                sl == 0 ? sm.me2s[e][0] * sm.mult[j] : f32_to_f64_alu(sm.me2f[e][sl] * sm.multf[j]);
           e += de;
           j += dj;
           if (j >= k) {
@@ -315,8 +326,9 @@ struct QcdTile {
         }
       }
     } else {
-      for (int e = tid; e < nblk; e += QCD_BLOCK)
-        out[ev0 + e] = (F32 ? (double)sm.me2f[e][0] : sm.me2s[e][0]) * lp.factor0;
+      if (own0)
+        for (int e = tid; e < nblk; e += QCD_BLOCK)
+          out[ev0 + e] = (F32 ? (double)sm.me2f[e][0] : sm.me2s[e][0]) * lp.factor0;
     }
   }
 };

@@ -345,6 +345,7 @@ struct rex_multi {
   cudaStream_t cap_stream;
   cudaGraph_t graph;
   cudaGraphExec_t exec;
+  int slot_groups;               // work items per g g tile (rex_multi_set_slot_groups / rex_multi_autotune)
 };
 
 namespace {
@@ -443,9 +444,7 @@ int multi_impl(rex_multi* m, const rex_batch* batches, int nbatch, const rex_par
         B.w_in = b.w_in;
         B.out = b.w_out + j0;
         const int epb = multi_events_per_tile(B.kind, mixed);
-        B.tile_begin = total;
-        total += (b.nev + epb - 1) / epb;
-        B.tile_end = total;
+        B.ngroup = 1;
         if (B.kind == PROC_EE_MUMU) {
           ml.ew.k = j1 - j0;
           ml.ew.mode = OUT_RATIO;
@@ -455,7 +454,14 @@ int multi_impl(rex_multi* m, const rex_batch* batches, int nbatch, const rex_par
         } else {
           fill_multi_table(b.proc, pts, j0, j1, k, B.t);
           if (B.t.has_width) width = 1;
+          // g g batches: the handle's slot groups per tile, at most one slot each
+          const bool gg = B.kind == PROC_GG_TTX || B.kind == PROC_GG_TTXG || B.kind == PROC_GG_TTXGG;
+          if (gg && m->slot_groups > 1 && B.t.nmass > 2)
+            B.ngroup = m->slot_groups < B.t.nmass - 1 ? m->slot_groups : B.t.nmass - 1;
         }
+        B.tile_begin = total;
+        total += (b.nev + epb - 1) / epb * B.ngroup;
+        B.tile_end = total;
       }
       if (nb == 0) continue;
       ml.nbatch = nb;
@@ -538,6 +544,61 @@ int rex_multi_set_mode(rex_multi* m, int mode) {
 int rex_reweight_multi(rex_multi* m, const rex_batch* batches, int nbatch, const rex_params* param_sets, int k,
                        void* stream) {
   return multi_impl(m, batches, nbatch, param_sets, k, stream);
+}
+
+int rex_multi_set_slot_groups(rex_multi* m, int groups) {
+  if (!m) return fail(REX_EINVAL, "null multi handle");
+  if (groups < 1 || groups > REX_MULTI_MAX_SLOT_GROUPS)
+    return fail(REX_EINVAL, "slot groups must be in [1, %d] (got %d)", REX_MULTI_MAX_SLOT_GROUPS, groups);
+  m->slot_groups = groups;
+  return REX_OK;
+}
+
+int rex_multi_get_slot_groups(const rex_multi* m) {
+  if (!m) return fail(REX_EINVAL, "null multi handle");
+  return m->slot_groups > 1 ? m->slot_groups : 1;
+}
+
+int rex_multi_autotune(rex_multi* m, const rex_batch* batches, int nbatch, const rex_params* param_sets, int k,
+                       void* stream, float* ms_out) {
+  if (!m) return fail(REX_EINVAL, "null multi handle");
+  static const int cand[REX_MULTI_TUNE_CANDIDATES] = {1, 2, 3, 4, 6, 8};
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  if (e != cudaSuccess) {
+    if (e0) cudaEventDestroy(e0);
+    return cuda_fail((int)e, "autotune events");
+  }
+  const int keep = m->slot_groups;
+  int best = 1, rc = REX_OK;
+  float best_ms = 0.f;
+  for (int c = 0; c < REX_MULTI_TUNE_CANDIDATES && rc == REX_OK; ++c) {
+    m->slot_groups = cand[c];
+    rc = multi_impl(m, batches, nbatch, param_sets, k, stream);   // warm-up
+    if (rc) break;
+    e = cudaEventRecord(e0, st);
+    for (int r = 0; r < 3 && rc == REX_OK && e == cudaSuccess; ++r) rc = multi_impl(m, batches, nbatch, param_sets, k, stream);
+    if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (e != cudaSuccess) {
+      rc = cuda_fail((int)e, "autotune timing");
+      break;
+    }
+    ms /= 3.f;
+    if (ms_out) ms_out[c] = ms;
+    if (c == 0 || ms < best_ms) {
+      best_ms = ms;
+      best = cand[c];
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  m->slot_groups = rc == REX_OK ? best : keep;
+  return rc;
 }
 
 int rex_multi_capture(rex_multi* m, const rex_batch* batches, int nbatch, const rex_params* param_sets, int k) {

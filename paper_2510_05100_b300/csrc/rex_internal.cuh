@@ -80,6 +80,7 @@ struct MultiTable {     // QCD batch: the QcdLaunch fields a tile reads
 struct MultiBatch {
   int kind;
   QqgCrossing cross;    // q q~ -> t t~ g channels only
+  int ngroup;           // g g batches: slot groups per tile (work items per tile); 1 otherwise
   int64_t nev, tile_begin, tile_end;   // work items [tile_begin, tile_end) of the launch
   const double* mom;
   const double* w_in;

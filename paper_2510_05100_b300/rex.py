@@ -43,6 +43,7 @@ EXPORTS = (
     "rex_last_error", "rex_version", "rex_num_variants", "rex_get_variant",
     "rex_set_variant", "rex_autotune", "rex_multi_create", "rex_reweight_multi", "rex_multi_capture",
     "rex_multi_replay", "rex_multi_free", "rex_reweight_multi_noalloc", "rex_multi_set_mode",
+    "rex_multi_set_slot_groups", "rex_multi_get_slot_groups", "rex_multi_autotune",
     "rex_surrogate_num_params", "rex_surrogate_last_error", "rex_surrogate_create",
     "rex_surrogate_set_weights", "rex_surrogate_get_weights", "rex_surrogate_loss_grad",
     "rex_surrogate_train", "rex_surrogate_reweight", "rex_surrogate_set_exact_alphas", "rex_surrogate_set_kernel",
@@ -134,6 +135,12 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.rex_multi_set_mode.restype = ctypes.c_int
     lib.rex_reweight_multi_noalloc.argtypes = [bp, ctypes.c_int, pp, ctypes.c_int, ctypes.c_int, vp]
     lib.rex_reweight_multi_noalloc.restype = ctypes.c_int
+    lib.rex_multi_set_slot_groups.argtypes = [vp, ctypes.c_int]
+    lib.rex_multi_set_slot_groups.restype = ctypes.c_int
+    lib.rex_multi_get_slot_groups.argtypes = [vp]
+    lib.rex_multi_get_slot_groups.restype = ctypes.c_int
+    lib.rex_multi_autotune.argtypes = [vp, bp, ctypes.c_int, pp, ctypes.c_int, vp, ctypes.POINTER(ctypes.c_float)]
+    lib.rex_multi_autotune.restype = ctypes.c_int
     fp = ctypes.POINTER(ctypes.c_float)
     lib.rex_surrogate_num_params.argtypes = []
     lib.rex_surrogate_num_params.restype = ctypes.c_int64
@@ -352,6 +359,23 @@ class Multi:
 
     def set_mode(self, mode: int) -> None:
         _check(load().rex_multi_set_mode(self._h, mode))
+
+    @property
+    def slot_groups(self) -> int:
+        return load().rex_multi_get_slot_groups(self._h)
+
+    @slot_groups.setter
+    def slot_groups(self, groups: int) -> None:
+        _check(load().rex_multi_set_slot_groups(self._h, int(groups)))
+
+    def autotune(self, batches, points: Sequence[dict], stream=None) -> list:
+        """rex_multi_autotune: time 1, 2, 3, 4, 6, 8 slot groups on these batches, keep the
+        fastest; returns the mean ms per launch of each."""
+        arr = self._batches(batches)
+        ms = (ctypes.c_float * 6)()
+        _check(load().rex_multi_autotune(self._h, arr, len(batches), _param_array(points), len(points),
+                                         _stream_ptr(stream), ms))
+        return list(ms)
 
     def close(self):
         if getattr(self, "_h", None):

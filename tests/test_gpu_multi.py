@@ -174,3 +174,36 @@ def test_config4_full_size_persistent_graph(rex):
         ref = oracle_rw.reweight(proc, mom[idx], np.ones(ns), orig, kp)
         assert np.max(np.abs(got[idx][:, cols] / ref - 1.0)) < mixed_tol[proc], proc
     m.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_slot_groups_and_autotune(rex, precision):
+    """Slot groups split each g g tile's mass slots over several work items (1, 3 and 8
+    groups of the 16-mass point list, a ragged split included): every weight equals the
+    single-process launch's; the autotuner times its six candidates and keeps one."""
+    g = ps.grid_64()
+    pts = [dict(g[j], **ps.EE_NEW) for j in range(0, 64, 4)]     # 8 masses x 2 alphas
+    items = setup(rex, precision, seed=41)
+    batches, single = [], []
+    for proc, p, mom, w in items:
+        dm, dw = dev(mom), dev(w)
+        batches.append((p, dm, dw, torch.zeros((mom.shape[0], len(pts)), dtype=torch.float64, device="cuda")))
+        single.append(p.reweight(dm, dw, pts).cpu().numpy())
+    m = rex.Multi(precision)
+    assert m.slot_groups == 1
+    for groups in (3, 8, 1):
+        m.slot_groups = groups
+        for b in batches:
+            b[3].zero_()
+        m.reweight(batches, pts)
+        torch.cuda.synchronize()
+        for (proc, *_), b, ref in zip(items, batches, single):
+            assert np.max(np.abs(b[3].cpu().numpy() / ref - 1.0)) < 1e-13, (proc, groups)
+    with pytest.raises(rex.RexError):
+        m.slot_groups = 0
+    with pytest.raises(rex.RexError):
+        m.slot_groups = 17
+    ms = m.autotune(batches, pts)
+    assert len(ms) == 6 and all(t > 0 for t in ms)
+    assert m.slot_groups == (1, 2, 3, 4, 6, 8)[int(np.argmin(ms))]
+    m.close()
