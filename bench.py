@@ -802,13 +802,17 @@ def run_small_configs_leg(dev, stream, steps):
     gg = {"workload": f"g g -> t t~, {n} events x {k} points (mt in linspace(171,175,4) x alphas in "
                       "{0.112, 0.124}); inputs + outputs exceed L2", "unit": UNIT}
     ref = None
-    for name, prec, variants in (("fp64", rex.FP64, [None]), ("mixed_scalar_colour", rex.MIXED, [None]),
+    for name, prec, variants in (("fp64", rex.FP64, ["tuned"]), ("mixed_scalar_colour", rex.MIXED, ["tuned"]),
                                  ("mixed_tensor_core_colour", rex.MIXED, [6, 8])):
         best = None
         for v in variants:
             proc = rex.Process("gg_ttx", prec)
             proc.set_params(ORIGINAL)
-            if v is not None:
+            if v == "tuned":   # rex_autotune: every variant timed on these events, the fastest kept
+                tuned_ms = proc.autotune(mom, w_in, pts, w_out)
+                if prec == rex.MIXED and proc.variant >= 5:   # the scalar colour form's best
+                    proc.variant = int(np.argmin(tuned_ms[:5]))
+            else:
                 proc.variant = v
             t = time_launches(proc, mom, w_in, pts, w_out, steps)
             variant = proc.variant

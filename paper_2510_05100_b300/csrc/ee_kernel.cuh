@@ -162,6 +162,136 @@ __device__ __forceinline__ void ee_tile(const double* __restrict__ mom, const do
   }
 }
 
+// The helicity sum with four lanes per event (standalone kernel, blocks of 128 =
+// 32 events): lane q evaluates configuration h = 5, 6, 9, 10 for q = 0..3.  Lane q
+// builds lepton q's helicity basis and omega_+ (the FP64 square roots, once per
+// lepton), the lanes exchange the parts their configuration needs, each forms its d_a
+// and H contribution, and a butterfly over the four lanes sums H.  Every lane then
+// evaluates the original point and every fourth new point.  B300 issues FP64 at 2
+// FMA per clock per SM, so for a sample of a few thousand events the chain a thread
+// carries, not the pipe, sets the time: a quarter of the thread-per-event chain.
+template <class TABLE>
+__device__ __forceinline__ void ee_tile_split(const double* __restrict__ mom, const double* __restrict__ w_in,
+                                              int64_t nev, int64_t tile, const TABLE& lp, double* __restrict__ out) {
+  const int q = threadIdx.x & 3;
+  const int64_t ev = tile * 32 + (threadIdx.x >> 2);
+  const bool valid = ev < nev;
+  const int64_t evc = valid ? ev : nev - 1;
+  double p[4][4];
+  const double2* src = reinterpret_cast<const double2*>(mom + evc * 16);
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const double2 v = __ldg(src + i);
+    p[i / 2][(i % 2) * 2] = v.x;
+    p[i / 2][(i % 2) * 2 + 1] = v.y;
+  }
+  double qs[4];
+#pragma unroll
+  for (int m = 0; m < 4; ++m) qs[m] = p[0][m] + p[1][m];
+  const double s = mdot(qs, qs);
+  // lepton q: helicity 2-spinors chi-, chi+ and omega_+ (massless: omega_- = 0)
+  cx<double> chi[2][2];
+  double wp;
+  {
+    double pabs, wm;
+    const double* pq = q == 0 ? p[0] : (q == 1 ? p[1] : (q == 2 ? p[2] : p[3]));
+    omegas(pq, 0.0, &pabs, &wp, &wm);
+    chi_pair(pq, pabs, chi[1], chi[0]);
+  }
+  // this lane's configuration: helicity index (0: -, 1: +) of each lepton
+  const int h = (q & 1 ? 6 : 5) + (q & 2 ? 4 : 0);
+  const int base = threadIdx.x & 28;   // lane 0 of the event within the warp
+  cx<double> sp[4][4];                 // v1, u2, v3, u4 of the configuration
+#pragma unroll
+  for (int t = 0; t < 4; ++t) {
+    // lepton t's 2-spinor for this lane's helicity, and its omega_+, from lane t
+    const int it = (h >> t) & 1;
+    const unsigned src_lane = (unsigned)(base + t);
+    cx<double> c[2][2];
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+      for (int b = 0; b < 2; ++b) {
+        c[a][b].re = __shfl_sync(0xffffffffu, chi[a][b].re, src_lane);
+        c[a][b].im = __shfl_sync(0xffffffffu, chi[a][b].im, src_lane);
+      }
+    const double w = __shfl_sync(0xffffffffu, wp, src_lane);
+    cx<double> both[2][4];
+    if (t == 0 || t == 2) spinor_v_from(c, w, 0.0, both);
+    else spinor_u_from(c, w, 0.0, both);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) sp[t][i] = both[it][i];
+  }
+  cx<double> je[2][4], jm[2][4];
+  chiral_current(sp[0], sp[1], -1.0, je[0]);          // vbar1 gamma P_L u2
+  chiral_current(sp[0] + 2, sp[1] + 2, 1.0, je[1]);   // vbar1 gamma P_R u2
+  chiral_current(sp[3], sp[2], -1.0, jm[0]);          // ubar4 gamma P_L v3
+  chiral_current(sp[3] + 2, sp[2] + 2, 1.0, jm[1]);   // ubar4 gamma P_R v3
+  cx<double> d[4];
+#pragma unroll
+  for (int x = 0; x < 2; ++x)
+#pragma unroll
+    for (int y = 0; y < 2; ++y) d[2 * x + y] = cmdot(je[x], jm[y]);
+  double hd[4];
+  cx<double> ho[6];
+  {
+    int o = 0;
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      hd[a] = d[a].re * d[a].re + d[a].im * d[a].im;
+#pragma unroll
+      for (int b2 = a + 1; b2 < 4; ++b2) ho[o++] = cdot1(d[a], d[b2]);   // conj(d_a) d_b
+    }
+  }
+#pragma unroll
+  for (int off = 1; off < 4; off <<= 1) {
+#pragma unroll
+    for (int a = 0; a < 4; ++a) hd[a] += __shfl_xor_sync(0xffffffffu, hd[a], off);
+#pragma unroll
+    for (int o = 0; o < 6; ++o) {
+      ho[o].re += __shfl_xor_sync(0xffffffffu, ho[o].re, off);
+      ho[o].im += __shfl_xor_sync(0xffffffffu, ho[o].im, off);
+    }
+  }
+  if (!valid) return;
+  auto me2_at = [&](const EwPoint& c) {
+    const double den_re = s - c.mz2, den_im = c.mzwz;
+    const double nn = 1.0 / (den_re * den_re + den_im * den_im);
+    const cx<double> dz = cx<double>{den_re * nn, -den_im * nn};   // 1/(s - mZ^2 + i mZ GZ)
+    const double ca = c.e2qq / s;
+    cx<double> coef[4];
+#pragma unroll
+    for (int xy = 0; xy < 4; ++xy) coef[xy] = cx<double>{ca, 0.0} + c.gzz[xy] * dz;
+    double sum = 0.0;
+    int o = 0;
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      sum += (coef[a].re * coef[a].re + coef[a].im * coef[a].im) * hd[a];
+#pragma unroll
+      for (int b2 = a + 1; b2 < 4; ++b2) {
+        const cx<double> t = cdot1(coef[a], coef[b2]) * ho[o++];
+        sum += 2.0 * t.re;
+      }
+    }
+    return sum * c.avg;
+  };
+  const double me2_0 = me2_at(lp.pt[0]);
+  if (lp.mode == OUT_ME2) {
+    if (q == 0) out[ev] = me2_0;
+    return;
+  }
+  for (int j = 1 + q; j <= lp.k; j += 4) {
+    const double me2 = me2_at(lp.pt[j]);
+    out[ev * lp.out_stride + (j - 1)] = (me2_0 == 0.0) ? 0.0 : w_in[ev] * (me2 / me2_0);
+  }
+}
+
+static __global__ void __launch_bounds__(128)
+    ee_reweight_split_kernel(const double* __restrict__ mom, const double* __restrict__ w_in, int64_t nev,
+                             const __grid_constant__ EwLaunch lp, double* __restrict__ out) {
+  ee_tile_split<EwLaunch>(mom, w_in, nev, (int64_t)blockIdx.x, lp, out);
+}
+
 template <bool EXCL, int TPB>
 static __global__ void __launch_bounds__(TPB)
     ee_reweight_kernel(const double* __restrict__ mom, const double* __restrict__ w_in, int64_t nev,

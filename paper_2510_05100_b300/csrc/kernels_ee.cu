@@ -19,6 +19,12 @@ static int launch_ee_t(const double* mom, const double* w_in, int64_t nev, const
 int launch_ee(const double* mom, const double* w_in, int64_t nev, const EwLaunch& lp, double* out,
               void* stream, const signed char* hel) {
   cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (!hel) {   // the helicity sum: four lanes per event (ee_tile_split)
+    const int64_t blocks = (nev + 31) / 32;
+    if (blocks > 0x7fffffffLL) return (int)cudaErrorInvalidValue;
+    ee_reweight_split_kernel<<<(unsigned)blocks, 128, 0, st>>>(mom, w_in, nev, lp, out);
+    return (int)cudaGetLastError();
+  }
   return nev < 148 * 128 * 4 ? launch_ee_t<32>(mom, w_in, nev, lp, out, st, hel)
                              : launch_ee_t<128>(mom, w_in, nev, lp, out, st, hel);
 }
