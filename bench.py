@@ -80,7 +80,7 @@ def kernel_source_hash() -> str:
     h = hashlib.sha256()
     for rel in ("paper_2510_05100_b300/csrc/qcd_kernel.cuh", "paper_2510_05100_b300/csrc/kernels_gg_ttxg.cu",
                 "paper_2510_05100_b300/csrc/helas.cuh", "paper_2510_05100_b300/csrc/colour_tc.cuh",
-                "paper_2510_05100_b300/csrc/generated/qcd_amplitudes.cuh"):
+                "paper_2510_05100_b300/csrc/fpconv.cuh", "paper_2510_05100_b300/csrc/generated/qcd_amplitudes.cuh"):
         with open(os.path.join(ROOT, rel), "rb") as f:
             h.update(f.read())
     with open(os.path.join(ROOT, "paper_2510_05100_b300/csrc/rex_internal.cuh")) as f:
@@ -257,6 +257,28 @@ MULTI_BATCHES = (("ee_mumu", 10_000, 41), ("gg_ttx", 1_000_000, 42), ("gg_ttxg",
                  ("gg_ttxgg", 100_000, 44))
 
 
+def multi_amp_flops(spec, pts):
+    """Counted FP32 amplitude flops of one mixed multi-process step (SURVEY's time-weighted
+    fraction of a batch: all its processes' flops over one time and the FP32 peak).
+    spec: (process, events); crossed q q~ -> t t~ g channels count as q q~ -> t t~ g; the
+    e+e- batch runs in FP64 and is left out."""
+    from paper_2510_05100_b300 import flops as flopmod
+    nmass = 1 + len({p["mt"] for p in pts} - {ORIGINAL["mt"]})
+    total = 0
+    for proc, n in spec:
+        kind = "qq_ttxg" if proc in ("qxq_ttxg", "qg_ttxq", "gq_ttxq", "qxg_ttxqx", "gqx_ttxqx") else proc
+        if kind == "ee_mumu":
+            continue
+        total += n * flopmod.per_event(kind, 1 if kind == "qq_ttx" else nmass)["amp"]
+    return total
+
+
+def time_weighted(fl, ms):
+    return {"bound": "alu", "pipe": "FP32 FMA (counted amplitude flops of every batch over the step)",
+            "achieved": fl / (ms * 1e-3) / 1e12, "peak": FP32_PEAK / 1e12, "unit": "TFLOP/s",
+            "frac": fl / (ms * 1e-3) / FP32_PEAK}
+
+
 def run_multi_leg(dev, stream, steps, world, barrier, max_over_ranks):
     """Mixed batch of four subprocesses x 64 points in one persistent, graph-captured launch
     (mixed precision), against the same work as four sequential single-process launches."""
@@ -306,6 +328,7 @@ def run_multi_leg(dev, stream, steps, world, barrier, max_over_ranks):
     ms_str = timed(lambda: ms_streams.replay(stream))
     m_groups = m.slot_groups
     m.close()
+    fl = multi_amp_flops([(proc, n) for proc, n, _ in MULTI_BATCHES], pts)
     ms_streams.close()
     return {"workload": "10k ee_mumu (FP64) + 1M gg_ttx + 500k gg_ttxg + 100k gg_ttxgg (mixed) x 64 points",
             "value": rdist.job_throughput(units, world, ms_graph * 1e-3), "unit": UNIT,
@@ -316,6 +339,9 @@ def run_multi_leg(dev, stream, steps, world, barrier, max_over_ranks):
             "sequential_ms_per_step": ms_seq,
             "streams_graph_value": rdist.job_throughput(units, world, ms_str * 1e-3),
             "streams_graph_ms_per_step": ms_str,
+            "roofline": time_weighted(fl, ms_graph),
+            "sequential_roofline_frac": time_weighted(fl, ms_seq)["frac"],
+            "streams_graph_roofline_frac": time_weighted(fl, ms_str)["frac"],
             "note": "value: one captured graph of persistent kernels, one per register class present; "
                     "sequential: one single-process launch per batch; streams_graph: one graph of "
                     "per-process launches on forked streams",
@@ -395,7 +421,12 @@ def run_small_multi_leg(dev, stream, steps, world, barrier, max_over_ranks):
         b[0].close()
     desc = " + ".join(f"{n} {proc}" for proc, n, _, _ in SMALL_MULTI_BATCHES)
     val = lambda ms: rdist.job_throughput(units, world, ms * 1e-3)   # noqa: E731
+    fl = multi_amp_flops([(proc, n) for proc, n, _, _ in SMALL_MULTI_BATCHES], pts)
+    frac = lambda ms: time_weighted(fl, ms)["frac"]   # noqa: E731
     return {"workload": f"{desc}, 64 points each, mixed precision", "unit": UNIT, "steps": steps,
+            "roofline": time_weighted(fl, ms_persistent),
+            "fracs": {"persistent_graph": frac(ms_persistent), "per_process_graph": frac(ms_seq_graph),
+                      "streams_graph": frac(ms_streams_graph), "sequential_launches": frac(ms_seq)},
             "persistent_graph": {"value": val(ms_persistent), "ms_per_step": ms_persistent,
                                  "slot_groups": groups, "autotune_ms_per_launch": dict(zip((1, 2, 3, 4, 6, 8), tune)),
                                  "without_slot_groups_ms_per_step": ms_persistent1},
