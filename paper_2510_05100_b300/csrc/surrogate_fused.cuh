@@ -7,13 +7,13 @@
 //   [tcgen05.mma, K = 256] x 3 with +b, GELU epilogues -> output head
 //   (two FP32 dot products over the 256 BF16 activations) -> pred, err, w_out.
 //
-// Warp roles (544 threads):
-//   warps 0-15 epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 (its tile
-//              rows) and the 64 columns of group g = w / 4; it turns the FP32
+// Warp roles (288 threads):
+//   warps 0-7  epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 (its tile
+//              rows) and the 128 columns of group g = w / 4; it turns the FP32
 //              accumulator into BF16 activations (bias + GELU, packed FP32x2
 //              arithmetic, one hardware tanh per element) written to shared
 //              memory in 32-column chunks, and computes the output head;
-//   warp 16    MMA issue (one lane): the layer MMAs and the weight copies.
+//   warp 8     MMA issue (one lane): the layer MMAs and the weight copies.
 // Overlap: the accumulator is double-buffered in TMEM (2 x 256 columns; the
 // layers of a tile alternate between them), and each 32-column chunk of
 // activations is handed to the MMA warp through an mbarrier as soon as it is
