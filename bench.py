@@ -258,7 +258,7 @@ MULTI_BATCHES = (("ee_mumu", 10_000, 41), ("gg_ttx", 1_000_000, 42), ("gg_ttxg",
 
 
 def multi_amp_flops(spec, pts):
-    """Counted FP32 amplitude flops of one mixed multi-process step (SURVEY's time-weighted
+    """Counted FP32 amplitude flops of one mixed multi-process step (for the time-weighted
     fraction of a batch: all its processes' flops over one time and the FP32 peak).
     spec: (process, events); crossed q q~ -> t t~ g channels count as q q~ -> t t~ g; the
     e+e- batch runs in FP64 and is left out."""
