@@ -659,9 +659,9 @@ int infer_fused(rex_surrogate* s, const double* momenta, const double* w_in, int
   if (e == cudaSuccess) e = cudaMemsetAsync(s->STATUS.p, 0, 4, st);
   if (e != cudaSuccess) return scuda(e, "inference set-up");
   __nv_bfloat16* pk = s->PK.as<__nv_bfloat16>();
-  pack_kmajor_kernel<<<(unsigned)((img1 + 255) / 256), 256, 0, st>>>(s->params + OFF_W1, FK1, pk);
+  pack_kmajor_kernel<<<(unsigned)((img1 + 255) / 256), 256, 0, st>>>(s->params + OFF_W1, FK1, 1.0f, pk);
   for (int l = 1; l < 4; ++l)
-    pack_kmajor_kernel<<<(unsigned)((img + 255) / 256), 256, 0, st>>>(s->params + OFF_W[l], FW,
+    pack_kmajor_kernel<<<(unsigned)((img + 255) / 256), 256, 0, st>>>(s->params + OFF_W[l], FW, FWSCALE,
                                                                       pk + img1 + (l - 1) * img);
   point_table_kernel<<<(k + 127) / 128, 128, 0, st>>>(s->pmt.as<double>(), s->pas.as<double>(), k, s->as0, s->apow,
                                                       s->PTAB.as<float4>());
@@ -691,8 +691,9 @@ int infer_fused(rex_surrogate* s, const double* momenta, const double* w_in, int
   fa.w_out = w_out;
   fa.flag = w_out ? s->flag.as<int>() : nullptr;
   fa.status = s->STATUS.as<int>();
-  const int64_t tiles = (nev * k + FM - 1) / FM;
-  const int grid = (int)(tiles < sms ? tiles : sms);
+  // two tiles per CTA at a time: no more CTAs than tile pairs
+  const int64_t pairs = ((nev * k + FM - 1) / FM + 1) / 2;
+  const int grid = (int)(pairs < sms ? pairs : sms);
   fused_mlp_kernel<<<grid, FTHREADS, sizeof(FusedSmem), st>>>(fa);
   e = cudaGetLastError();
   return e == cudaSuccess ? REX_OK : scuda(e, "fused inference kernel");
