@@ -15,7 +15,7 @@
 //              arithmetic, one hardware tanh per element) written to shared
 //              memory in 32-column chunks, and computes the output head;
 //   warp 16    MMA issue (one lane);
-//   warp 17    weight producer (one lane per ring slot).
+//   warp 17    weight producer (the copy for ring slot r issued by lane r).
 // Ping-pong: each tile slot has its own accumulator (TMEM columns 256 s ..
 // 256 s + 255) and its own activation buffer, and the MMAs alternate between
 // the slots layer by layer, slot 1 two layers behind slot 0 (step k: slot 0
@@ -29,10 +29,11 @@
 // every MMA of a layer accumulates onto its bias and the epilogue adds nothing.
 // Weights: BF16 images of W^T cut into 8 K-chunks of 32 (16 KB each) stream
 // from L2 through a ring of FNSLOT slots, in the order the MMAs read them (each
-// chunk once per tile); lane r of the producer owns ring slot r and refills it
-// as soon as the MMAs reading it have completed (bulk copies issued by one
-// thread complete one after another, copies of different threads overlap).  W1
-// stays resident.  The images of W2, W3, W4 and the head weights are scaled by
+// chunk once per tile); the producer warp refills a slot as soon as the MMAs
+// reading it have completed, the copy issued by the slot's own lane (bulk copies
+// issued by one thread complete one after another, copies of different threads
+// overlap) while the warp stays converged (lanes spinning on different barriers
+// in one warp delayed the refills).  W1 stays resident.  The images of W2, W3, W4 and the head weights are scaled by
 // 1/2 (exact in BF16 and FP32) and the epilogues produce 2 gelu(z) = z (1 + tanh
 // u), which saves the multiplication by 1/2: the products entering every
 // accumulation are the same as with unscaled weights and gelu(z).
@@ -277,36 +278,41 @@ __global__ void __launch_bounds__(FTHREADS, 1) fused_mlp_kernel(const __grid_con
 
   if (warp == FPROD_WARP) {
     // ========================= weight producer =========================
-    // Lane r < FNSLOT owns ring slot r: fills r, r + FNSLOT, ...
-    if (lane < FNSLOT) {
-      const int r = lane;
+    // The warp walks the ring uses in the MMAs' order (per step and slot with a
+    // layer >= 2, its 8 chunks); use f goes to ring slot r = f % FNSLOT and its copy
+    // is issued by lane r (bulk copies issued by one thread complete one after
+    // another, copies of different threads overlap), after the whole warp has seen
+    // the slot's previous chunk read by its MMAs.
+    {
       bool ok = true;
-      uint32_t n = 0;   // fills of slot r issued
-      if (r == 0) {
+      uint32_t f = 0;
+      if (lane == 0) {
         tc05::mbar_expect_tx(&sm.w1_full, FCHUNK * 2);
         tc05::bulk_g2s(sm.w1, a.w1, FCHUNK * 2, &sm.w1_full);
       }
-      // the MMAs' order of ring uses: per step and slot with a layer >= 2, its 8 chunks
-      uint32_t f = 0;
       for (int64_t k = 0; ok && k < nsteps; ++k)
         for (int ts = 0; ok && ts < 2; ++ts) {
           int l;
           int64_t t;
           if (!step_work(k, ts, per_slot, l, t) || l == 0) continue;
           for (int i = 0; i < FNCH; ++i, ++f) {
-            if (f % FNSLOT != (uint32_t)r) continue;
-            // the slot's previous chunk must have been read by its MMAs
-            if (n > 0 && !(ok = wait_bar(sm, &sm.w_empty[r], (n - 1) & 1u))) break;
-            tc05::mbar_expect_tx(&sm.w_full[r], FCHUNK * 2);
-            tc05::bulk_g2s(sm.wring[r], a.w234 + ((size_t)(l - 1) * FNCH + chunk_at(i)) * FCHUNK, FCHUNK * 2,
-                           &sm.w_full[r]);
-            ++n;
+            const uint32_t r = f % FNSLOT, use = f / FNSLOT;
+            if (use > 0 && !(ok = wait_bar(sm, &sm.w_empty[r], (use - 1) & 1u))) break;
+            if (lane == (int)r) {
+              tc05::mbar_expect_tx(&sm.w_full[r], FCHUNK * 2);
+              tc05::bulk_g2s(sm.wring[r], a.w234 + ((size_t)(l - 1) * FNCH + chunk_at(i)) * FCHUNK, FCHUNK * 2,
+                             &sm.w_full[r]);
+            }
+            __syncwarp();
           }
         }
-      if (!ok) sm.abort = 1;
+      if (!ok && lane == 0) sm.abort = 1;
       // drain: every copy issued has landed (normally consumed already)
-      if (r == 0 && !tc05::mbar_wait(&sm.w1_full, 0, kTimeoutNs)) sm.abort = 1;
-      if (n > 0 && !tc05::mbar_wait(&sm.w_full[r], (n - 1) & 1u, kTimeoutNs)) sm.abort = 1;
+      if (lane == 0 && !tc05::mbar_wait(&sm.w1_full, 0, kTimeoutNs)) sm.abort = 1;
+      if (lane < FNSLOT && (uint32_t)lane < f) {
+        const uint32_t last = (f - 1 - (uint32_t)lane) / FNSLOT;   // the slot's last use
+        if (!tc05::mbar_wait(&sm.w_full[lane], last & 1u, kTimeoutNs)) sm.abort = 1;
+      }
     }
     __syncwarp();
   } else if (warp == FMMA_WARP) {
