@@ -402,7 +402,11 @@ __global__ void __launch_bounds__(FTHREADS, 1) fused_mlp_kernel(const __grid_con
         arrive(&sm.x_ready[1]);
       }
     }
-    uint4 xnext[2] = {make_uint4(0u, 0u, 0u, 0u), make_uint4(0u, 0u, 0u, 0u)};
+    // the next features of a slot live from its layer-3 epilogue to its head, and the
+    // two slots' intervals never overlap (slot 1 trails by two layers): one register
+    // group holds them (an array indexed by the slot would live in local memory, and
+    // its store would wait for the global load)
+    uint4 xnext = make_uint4(0u, 0u, 0u, 0u);
     for (int64_t k = 0; ok && k < nsteps; ++k)
       for (int s = 0; s < 2; ++s) {
         int l;
@@ -442,11 +446,11 @@ __global__ void __launch_bounds__(FTHREADS, 1) fused_mlp_kernel(const __grid_con
           __syncwarp();
           if (lane == 0) arrive(&sm.acc_ready[s]);
           // the slot's next features, loaded early, are written at its head
-          if (l == 2 && more) xnext[s] = load_x(a, tile_of(t + 1, s), npairs, tid);
+          if (l == 2 && more) xnext = load_x(a, tile_of(t + 1, s), npairs, tid);
         } else {
           // layer 4 has finished reading this slot's activations: its next features
           if (more) {
-            store_x(sm.act[s], xnext[s], tid);
+            store_x(sm.act[s], xnext, tid);
             tc05::fence_proxy_async();
             __syncwarp();
             if (lane == 0) arrive(&sm.x_ready[s]);
