@@ -322,13 +322,13 @@ __global__ void __launch_bounds__(FTHREADS, 1) fused_mlp_kernel(const __grid_con
       constexpr uint64_t DACT = tc05::smem_desc_bits(128, (FW / 8) * 128);   // act: 256 columns
       constexpr uint64_t DCH = tc05::smem_desc_bits(128, (FCH / 8) * 128);   // weight chunk: 32 columns
       uint32_t f = 0;                                   // ring uses so far
-      uint32_t ph_acc[2] = {0, 0}, ph_x[2] = {0, 0};
+      uint32_t ph_acc = 0, ph_x = 0;   // phase parities, bit s for tile slot s (registers, not arrays)
       // descriptor of element 0 of each operand buffer; advancing by 16 bytes adds 1
-      const uint64_t dact[2] = {tc05::smem_desc(sm.act[0], DACT), tc05::smem_desc(sm.act[1], DACT)};
+      const uint64_t dact0 = tc05::smem_desc(sm.act[0], DACT);
+      constexpr uint64_t DACT_SLOT = sizeof(sm.act[0]) / 16;      // descriptor step between the slots' buffers
       const uint64_t dw1 = tc05::smem_desc(sm.w1, DCH);
-      uint64_t dring[FNSLOT];
-#pragma unroll
-      for (int r = 0; r < FNSLOT; ++r) dring[r] = tc05::smem_desc(sm.wring[r], DCH);
+      const uint64_t dring0 = tc05::smem_desc(sm.wring[0], DCH);
+      constexpr uint64_t DRING_SLOT = sizeof(sm.wring[0]) / 16;   // descriptor step between ring slots
       bool ok = wait_bar(sm, &sm.w1_full, 0);
       for (int64_t k = 0; ok && k < nsteps; ++k)
         for (int s = 0; ok && s < 2; ++s) {
@@ -338,18 +338,19 @@ __global__ void __launch_bounds__(FTHREADS, 1) fused_mlp_kernel(const __grid_con
           const uint32_t dst = tmem + (uint32_t)(s * FW);
           if (l == 0) {
             // layer 1: x -> accumulator (holding b1)
-            if (!(ok = wait_bar(sm, &sm.acc_ready[s], ph_acc[s]) && wait_bar(sm, &sm.x_ready[s], ph_x[s]))) break;
-            ph_acc[s] ^= 1;
-            ph_x[s] ^= 1;
+            if (!(ok = wait_bar(sm, &sm.acc_ready[s], (ph_acc >> s) & 1u) && wait_bar(sm, &sm.x_ready[s], (ph_x >> s) & 1u)))
+              break;
+            ph_acc ^= 1u << s;
+            ph_x ^= 1u << s;
             tc05::fence_after_sync();
             for (int kk = 0; kk < FK1 / 16; ++kk)   // 128 elements = 256 bytes per K step of 16
-              tc05::mma_bf16(dst, dact[s] + 16 * kk, dw1 + 16 * kk, IDESC, 1u);
+              tc05::mma_bf16(dst, dact0 + DACT_SLOT * s + 16 * kk, dw1 + 16 * kk, IDESC, 1u);
             tc05::mma_commit(&sm.acc_full[s]);
           } else {
             // the slot's epilogue has written every activation chunk, read the
             // accumulator and stored the bias
-            if (!(ok = wait_bar(sm, &sm.acc_ready[s], ph_acc[s]))) break;
-            ph_acc[s] ^= 1;
+            if (!(ok = wait_bar(sm, &sm.acc_ready[s], (ph_acc >> s) & 1u))) break;
+            ph_acc ^= 1u << s;
             tc05::fence_after_sync();
             for (int i = 0; i < FNCH; ++i, ++f) {
               const int c = chunk_at(i);
@@ -357,7 +358,8 @@ __global__ void __launch_bounds__(FTHREADS, 1) fused_mlp_kernel(const __grid_con
               if (!(ok = wait_bar(sm, &sm.w_full[r], (f / FNSLOT) & 1u))) break;
 #pragma unroll
               for (int j = 0; j < FCH / 16; ++j)
-                tc05::mma_bf16(dst, dact[s] + (uint64_t)(16 * (2 * c + j)), dring[r] + (uint64_t)(16 * j), IDESC, 1u);
+                tc05::mma_bf16(dst, dact0 + DACT_SLOT * s + (uint64_t)(16 * (2 * c + j)),
+                               dring0 + DRING_SLOT * r + (uint64_t)(16 * j), IDESC, 1u);
               tc05::mma_commit(&sm.w_empty[r]);   // the producer may refill ring slot r
             }
             if (!ok) break;
@@ -375,7 +377,7 @@ __global__ void __launch_bounds__(FTHREADS, 1) fused_mlp_kernel(const __grid_con
     const int q = warp & 3, g = warp >> 2;
     const int row = q * 32 + lane;   // tile row = TMEM lane
     const uint32_t trow = tmem + ((uint32_t)(q * 32) << 16);
-    uint32_t ph_full[2] = {0, 0}, ph_head[2] = {0, 0};
+    uint32_t ph_full = 0, ph_head = 0;   // phase parities, bit s for tile slot s
     bool ok = true;
     // both accumulators start holding b1; both slots' first features
 #pragma unroll
@@ -414,8 +416,8 @@ __global__ void __launch_bounds__(FTHREADS, 1) fused_mlp_kernel(const __grid_con
         if (!step_work(k, s, per_slot, l, t)) continue;
         const int64_t tile = tile_of(t, s);
         const bool more = t + 1 < per_slot;   // the slot has a next tile
-        if (!(ok = wait_bar(sm, &sm.acc_full[s], ph_full[s]))) break;
-        ph_full[s] ^= 1;
+        if (!(ok = wait_bar(sm, &sm.acc_full[s], (ph_full >> s) & 1u))) break;
+        ph_full ^= 1u << s;
         tc05::fence_after_sync();
         const uint32_t tacc = trow + (uint32_t)(s * FW);
         const int nl = (l + 1) & 3;      // the layer that accumulates here next
@@ -496,8 +498,8 @@ __global__ void __launch_bounds__(FTHREADS, 1) fused_mlp_kernel(const __grid_con
             __syncwarp();
             if (lane == 0) arrive(&sm.head_ready[s]);
           } else {
-            if (!(ok = wait_bar(sm, &sm.head_ready[s], ph_head[s]))) break;
-            ph_head[s] ^= 1;
+            if (!(ok = wait_bar(sm, &sm.head_ready[s], (ph_head >> s) & 1u))) break;
+            ph_head ^= 1u << s;
             if (out) {
               float y = ye.x, er = ye.y;
 #pragma unroll
