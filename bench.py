@@ -67,8 +67,8 @@ TRAFFIC = {
     # ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum of profile_case at 2^19
     # events (FP64, scaled x2 by events) and 2^20 events (mixed); summaries of the
     # captures are under profiles/
-    ("gg_ttxg", "fp64"): {"bytes_per_launch": 2 * (91.294464e6 + 34.751232e6), "source_hash": "26e19290907aadc9"},
-    ("gg_ttxg", "mixed"): {"bytes_per_launch": 176.315648e6 + 101.576192e6, "source_hash": "26e19290907aadc9"},
+    ("gg_ttxg", "fp64"): {"bytes_per_launch": 2 * (91.502848e6 + 35.003648e6), "source_hash": "3595a4023fc99614"},
+    ("gg_ttxg", "mixed"): {"bytes_per_launch": 176.351488e6 + 104.789760e6, "source_hash": "3595a4023fc99614"},
 }
 
 

@@ -349,7 +349,7 @@ __global__ void __launch_bounds__(QCD_BLOCK, MINB)
 struct QcdVariant {
   int split, minb, tc;
 };
-constexpr QcdVariant kQcdVariants[QCD_NVARIANT] = {{0, 1, 0}, {1, 1, 0}, {0, 3, 0}, {1, 3, 0}, {1, 4, 0},
+constexpr QcdVariant kQcdVariants[QCD_NVARIANT] = {{0, 1, 0}, {1, 1, 0}, {0, 3, 0}, {1, 3, 0}, {0, 4, 0},
                                                    {0, 3, 1}, {1, 3, 1}, {0, 1, 1}, {1, 1, 1}};
 
 template <int PROC, typename R, int V>

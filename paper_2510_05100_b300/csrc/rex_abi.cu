@@ -121,7 +121,7 @@ int default_variant(int kind, int precision) {
   static const int table[PROC_LAST + 1][2] = {
       {0, 0},   // ee_mumu (single variant)
       {0, 0},   // gg_ttx:   FP64 v0, mixed v0
-      {0, 2},   // gg_ttxg:  FP64 v0, mixed v2 (min 3 blocks/SM)
+      {0, 4},   // gg_ttxg:  FP64 v0, mixed v4 (min 4 blocks/SM: 16 warps, 128 registers)
       {0, 0},   // gg_ttxgg: FP64 v0, mixed v0
       {0, 0},   // qq_ttx (single variant)
       {0, 0},   // qq_ttxg (single variant)
