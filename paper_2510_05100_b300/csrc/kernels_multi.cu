@@ -108,7 +108,7 @@ struct MultiSplit<double, CLASS> {
 template <int CLASS>
 struct MultiSplit<float, CLASS> {
   static constexpr int TTX = 0, TTXG = 0, TTXGG = 0;
-  static constexpr int MINB = CLASS == 0 ? 4 : (CLASS == 1 ? 3 : REX_MULTI_MINB);
+  static constexpr int MINB = CLASS == 0 ? 4 : (CLASS == 1 ? 4 : REX_MULTI_MINB);
   static constexpr bool TC_TTXGG = false;
 };
 
