@@ -52,7 +52,14 @@ extern "C" {
                               * work is already pending on the calling thread
                               * (cudaPeekAtLastError); the message says so and the
                               * error is left pending for its owner. */
-#define REX_ENOMEM (-4)      /* a library-owned allocation failed */
+#define REX_ENOMEM (-4)      /* a library-owned allocation failed; what was
+                              * allocated before the failure is released.  For
+                              * tests: while the environment variable
+                              * REX_FAIL_DEVICE_ALLOC holds n >= 1, the n-th
+                              * library-owned device allocation counted from when
+                              * it took that value, and every later one while it
+                              * keeps it, fails as out of memory without touching
+                              * the device. */
 #define REX_EUNSUPPORTED (-5) /* precision mode or helicity-exclusive reweighting not
                                  available for this process */
 

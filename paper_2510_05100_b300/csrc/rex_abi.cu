@@ -10,6 +10,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <new>
@@ -18,10 +19,38 @@
 #include <vector>
 
 #include "../../include/rex.h"
+#include "dev_alloc.h"
 #include "generated/qcd_amplitudes.cuh"
 #include "rex_internal.cuh"
 
 using namespace rex;
+
+namespace rex {
+
+cudaError_t dev_malloc(void** p, size_t bytes) {
+  static std::mutex mu;
+  static std::string armed;     // the value the countdown belongs to
+  static long made = 0;         // allocations since it took that value
+  *p = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    const char* v = std::getenv("REX_FAIL_DEVICE_ALLOC");
+    char* end = nullptr;
+    const long n = (v && *v) ? std::strtol(v, &end, 10) : 0;
+    if (n >= 1 && end && *end == '\0') {
+      if (armed != v) {
+        armed = v;
+        made = 0;
+      }
+      if (++made >= n) return cudaErrorMemoryAllocation;
+    } else {
+      armed.clear();
+    }
+  }
+  return cudaMalloc(p, bytes);
+}
+
+}  // namespace rex
 
 struct rex_proc {
   int kind;
@@ -507,7 +536,7 @@ int rex_multi_create(int precision, rex_multi** out) {
   std::memset(m, 0, sizeof *m);
   m->precision = precision;
   cudaError_t e = cudaGetDevice(&m->device);
-  if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&m->counter), 256);
+  if (e == cudaSuccess) e = dev_malloc(&m->counter, 256);
   if (e != cudaSuccess) {
     delete m;
     return fail(REX_ENOMEM, "work-counter allocation failed: %s", cudaGetErrorString(e));
@@ -809,7 +838,7 @@ static int grow(double** buf, size_t* cap, size_t need) {
   if (*buf) cudaFree(*buf);
   *buf = nullptr;
   *cap = 0;
-  const cudaError_t e = cudaMalloc(reinterpret_cast<void**>(buf), need * sizeof(double));
+  const cudaError_t e = dev_malloc(buf, need * sizeof(double));
   if (e != cudaSuccess) {
     *buf = nullptr;
     return fail(REX_ENOMEM, "device allocation of %zu doubles failed: %s", need, cudaGetErrorString(e));

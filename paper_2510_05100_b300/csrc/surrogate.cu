@@ -24,6 +24,7 @@
 #include <vector>
 
 #include "../../include/rex.h"
+#include "dev_alloc.h"
 #include "surrogate_fused.cuh"
 #include "surrogate_gemm.cuh"
 
@@ -398,7 +399,7 @@ struct DevBuf {
     if (p) cudaFree(p);
     p = nullptr;
     cap = 0;
-    const cudaError_t e = cudaMalloc(&p, bytes);
+    const cudaError_t e = rex::dev_malloc(&p, bytes);
     if (e == cudaSuccess) cap = bytes;
     return e;
   }
@@ -714,11 +715,11 @@ int rex_surrogate_create(unsigned long long seed, rex_surrogate** out) {
   *out = nullptr;
   rex_surrogate* s = new (std::nothrow) rex_surrogate();
   if (!s) return sfail(REX_ENOMEM, "out of host memory");
-  cudaError_t e = cudaMalloc(&s->params, NPARAM * 4);
-  if (e == cudaSuccess) e = cudaMalloc(&s->grads, NPARAM * 4);
-  if (e == cudaSuccess) e = cudaMalloc(&s->m, NPARAM * 4);
-  if (e == cudaSuccess) e = cudaMalloc(&s->v, NPARAM * 4);
-  for (int l = 0; l < 4 && e == cudaSuccess; ++l) e = cudaMalloc(&s->wb[l], (size_t)KIN[l] * WID * 2);
+  cudaError_t e = rex::dev_malloc(&s->params, NPARAM * 4);
+  if (e == cudaSuccess) e = rex::dev_malloc(&s->grads, NPARAM * 4);
+  if (e == cudaSuccess) e = rex::dev_malloc(&s->m, NPARAM * 4);
+  if (e == cudaSuccess) e = rex::dev_malloc(&s->v, NPARAM * 4);
+  for (int l = 0; l < 4 && e == cudaSuccess; ++l) e = rex::dev_malloc(&s->wb[l], (size_t)KIN[l] * WID * 2);
   if (e != cudaSuccess) {
     release(s);
     delete s;

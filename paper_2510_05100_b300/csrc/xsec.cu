@@ -26,6 +26,7 @@
 #include <string>
 
 #include "../../include/rex.h"
+#include "dev_alloc.h"
 
 namespace {
 
@@ -228,9 +229,9 @@ int rex_xsec_create(int k, rex_xsec** out) {
   rex_xsec* x = new (std::nothrow) rex_xsec();
   if (!x) return xfail(REX_ENOMEM, "out of host memory");
   x->k = k;
-  cudaError_t e = cudaMalloc(&x->acc, sizeof(Moments) * k);
-  if (e == cudaSuccess) e = cudaMalloc(&x->asc, sizeof(Scalars));
-  if (e == cudaSuccess) e = cudaMalloc(&x->res, sizeof(double) * 3 * k);
+  cudaError_t e = rex::dev_malloc(&x->acc, sizeof(Moments) * k);
+  if (e == cudaSuccess) e = rex::dev_malloc(&x->asc, sizeof(Scalars));
+  if (e == cudaSuccess) e = rex::dev_malloc(&x->res, sizeof(double) * 3 * k);
   if (e == cudaSuccess) e = cudaMemset(x->acc, 0, sizeof(Moments) * k);
   if (e == cudaSuccess) e = cudaMemset(x->asc, 0, sizeof(Scalars));
   if (e != cudaSuccess) {
@@ -268,9 +269,15 @@ int rex_xsec_accumulate(rex_xsec* x, const double* w_in, const double* w_out, in
     x->part = nullptr;
     x->psc = nullptr;
     x->part_blocks = 0;
-    if (e == cudaSuccess) e = cudaMalloc(&x->part, sizeof(Moments) * x->k * nblk);
-    if (e == cudaSuccess) e = cudaMalloc(&x->psc, sizeof(Scalars) * nblk);
-    if (e != cudaSuccess) return xfail(REX_ENOMEM, "partials allocation failed: %s", cudaGetErrorString(e));
+    if (e == cudaSuccess) e = rex::dev_malloc(&x->part, sizeof(Moments) * x->k * nblk);
+    if (e == cudaSuccess) e = rex::dev_malloc(&x->psc, sizeof(Scalars) * nblk);
+    if (e != cudaSuccess) {
+      cudaFree(x->part);
+      cudaFree(x->psc);
+      x->part = nullptr;
+      x->psc = nullptr;
+      return xfail(REX_ENOMEM, "partials allocation failed: %s", cudaGetErrorString(e));
+    }
     x->part_blocks = nblk;
   }
   int kw = 1;

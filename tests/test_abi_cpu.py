@@ -128,3 +128,18 @@ def test_flop_counter_builds_and_counts_every_process():
     for proc in ("gg_ttx", "gg_ttxg", "gg_ttxgg", "qq_ttx", "qq_ttxg"):
         assert flops.per_event(proc, 5)["amp"] > 0, proc
     assert set(counts) >= {"gg_ttx", "gg_ttxg", "gg_ttxgg", "qq_ttx", "qq_ttxg"}
+
+
+def test_injected_device_allocation_failure_is_reported(rex, monkeypatch):
+    """The allocation-failure hook (REX_FAIL_DEVICE_ALLOC): the first library-owned
+    device allocation of a handle fails as out of memory before any device is touched,
+    and the call returns REX_ENOMEM with the cause in its message."""
+    lib = rex.load()
+    monkeypatch.setenv("REX_FAIL_DEVICE_ALLOC", "1")
+    h = ctypes.c_void_p()
+    assert lib.rex_xsec_create(4, ctypes.byref(h)) == rex.REX_ENOMEM
+    assert not h.value
+    assert b"out of memory" in lib.rex_xsec_last_error()
+    assert lib.rex_surrogate_create(1, ctypes.byref(h)) == rex.REX_ENOMEM
+    assert not h.value
+    assert b"out of memory" in lib.rex_surrogate_last_error()
