@@ -265,11 +265,30 @@ int rex_reweight_multi(rex_multi *m, const rex_batch *batches, int nbatch,
 int rex_multi_set_slot_groups(rex_multi *m, int groups);
 int rex_multi_get_slot_groups(const rex_multi *m);
 
-/* Pick the slot groups by measurement: runs rex_reweight_multi with these
- * arguments for each of 1, 2, 3, 4, 6 and 8 groups (a warm-up and three timed
- * launches each, CUDA events on stream), keeps the fastest in the handle and
- * writes the mean times (ms, REX_MULTI_TUNE_CANDIDATES floats) to ms_out (host,
- * may be NULL).  Overwrites the batches' w_out; synchronises stream.
+/* Tile costs of the persistent mode.  Its work items are handed out longest
+ * tiles first, so that short ones fill the tail.  The cost is one value per tile
+ * kind: one per process, plus one for the q q~ -> t t~ g channels whose light
+ * line is crossed (q g, q~ g and their beam swaps run on a tile of their own).
+ * A launch orders its batches by the measured costs when every batch with events
+ * has one; otherwise by an estimate from counted flops per event and the issue
+ * rate of the pipe each tile runs on.
+ * rex_multi_get_tile_cost writes the cost of proc's tile kind to *us (host; 0 if
+ * not measured).  rex_multi_set_tile_cost sets it (us finite and >= 0; 0 clears
+ * it), e.g. from a stored tuning.  Costs are in microseconds of one block and
+ * depend on the point list they were measured with.  Errors: REX_EINVAL. */
+int rex_multi_get_tile_cost(const rex_multi *m, const rex_proc *proc, double *us);
+int rex_multi_set_tile_cost(rex_multi *m, const rex_proc *proc, double us);
+
+/* Tune the persistent mode by measurement, in two steps.
+ * 1. Tile costs: the first batch of each tile kind runs alone in its persistent
+ *    launch (a warm-up and two timed launches).  Its time, times the blocks its
+ *    tiles occupied, divided by its tiles, is stored as that kind's cost.
+ * 2. Slot groups: rex_reweight_multi runs with these arguments for each of 1, 2,
+ *    3, 4, 6 and 8 groups (a warm-up and three timed launches each).  The fastest
+ *    is kept in the handle, and the mean times (ms, REX_MULTI_TUNE_CANDIDATES
+ *    floats) go to ms_out (host, may be NULL).
+ * Timing uses CUDA events on stream.  Overwrites the batches' w_out and
+ * synchronises stream.  On an error the handle keeps its earlier settings.
  * Errors: as rex_reweight_multi. */
 #define REX_MULTI_TUNE_CANDIDATES 6
 int rex_multi_autotune(rex_multi *m, const rex_batch *batches, int nbatch,

@@ -375,9 +375,42 @@ struct rex_multi {
   cudaGraph_t graph;
   cudaGraphExec_t exec;
   int slot_groups;               // work items per g g tile (rex_multi_set_slot_groups / rex_multi_autotune)
+  double tile_us[PROC_LAST + 2]; // measured time of one tile per tile kind (tile_kind), 0 when not measured
 };
 
 namespace {
+
+// The tile a process's batch runs on in the persistent kernel: one per process, and a
+// second one for the q q~ -> t t~ g channels whose light line is crossed (q g, q~ g and
+// their beam swaps: the t-channel tile).
+int tile_kind(const rex_proc* p) {
+  return (p->kind == PROC_QQ_TTXG && (p->cross.neg[0] || p->cross.neg[1])) ? PROC_LAST + 1 : p->kind;
+}
+
+// Cost of one tile of each batch; items are handed out longest tiles first, so that
+// short ones fill the tail.  The measured times (rex_multi_autotune,
+// rex_multi_set_tile_cost) when every batch with events has one (returns true);
+// otherwise an estimate: events per tile x flops per event / issue rate of the pipe
+// the tile runs on (FP64 is 1/64 of FP32 on B300; e+e- tiles always run in FP64).
+bool tile_costs(const rex_multi* m, const rex_batch* batches, int nbatch, int k, double* cost) {
+  bool measured = true;
+  for (int i = 0; i < nbatch; ++i) {
+    cost[i] = batches[i].nev > 0 ? m->tile_us[tile_kind(batches[i].proc)] : 0.0;
+    if (batches[i].nev > 0 && !(cost[i] > 0.0)) measured = false;
+  }
+  if (measured) return true;
+  const int mixed_p = m->precision == REX_MIXED;
+  for (int i = 0; i < nbatch; ++i) {
+    static const double flops_per_event_slot[PROC_LAST + 1] = {160.0, 5.0e3, 4.8e4, 5.7e5, 3.0, 2.4e4};   // per mass slot
+    static const double flops_per_event_fixed[PROC_LAST + 1] = {6.4e3, 4.0e2, 6.6e3, 1.1e5, 6.0e2, 4.0e3};
+    const int kind = batches[i].proc->kind;
+    const double rate = (kind == PROC_EE_MUMU || !mixed_p) ? 1.0 : 64.0;
+    const double slots = kind == PROC_EE_MUMU ? (k < MULTI_MAX_POINTS ? k : MULTI_MAX_POINTS) + 1.0 : 9.0;
+    cost[i] = multi_events_per_tile(kind, mixed_p) *
+              (flops_per_event_fixed[kind] + slots * flops_per_event_slot[kind]) / rate;
+  }
+  return false;
+}
 
 int multi_impl(rex_multi* m, const rex_batch* batches, int nbatch, const rex_params* pts, int k, void* stream) {
   if (!m) return fail(REX_EINVAL, "null multi handle");
@@ -426,20 +459,9 @@ int multi_impl(rex_multi* m, const rex_batch* batches, int nbatch, const rex_par
     }
     return REX_OK;
   }
-  // longest tiles first: items are handed out in this order.  Estimated time of
-  // one tile = events per tile x flops per event / issue rate of the pipe it runs
-  // on (FP64 is 1/64 of FP32 on B300); e+e- tiles always run in FP64.
-  const int mixed_p = m->precision == REX_MIXED;
+  // longest tiles first: items are handed out in this order
   double tile_cost[MULTI_MAX_BATCH];
-  for (int i = 0; i < nbatch; ++i) {
-    static const double flops_per_event_slot[PROC_LAST + 1] = {160.0, 5.0e3, 4.8e4, 5.7e5, 3.0, 2.4e4};   // per mass slot
-    static const double flops_per_event_fixed[PROC_LAST + 1] = {6.4e3, 4.0e2, 6.6e3, 1.1e5, 6.0e2, 4.0e3};
-    const int kind = batches[i].proc->kind;
-    const double rate = (kind == PROC_EE_MUMU || !mixed_p) ? 1.0 : 64.0;
-    const double slots = kind == PROC_EE_MUMU ? (k < MULTI_MAX_POINTS ? k : MULTI_MAX_POINTS) + 1.0 : 9.0;
-    tile_cost[i] = multi_events_per_tile(kind, mixed_p) *
-                   (flops_per_event_fixed[kind] + slots * flops_per_event_slot[kind]) / rate;
-  }
+  tile_costs(m, batches, nbatch, k, tile_cost);
   int order[MULTI_MAX_BATCH];
   for (int i = 0; i < nbatch; ++i) order[i] = i;
   for (int i = 0; i < nbatch; ++i)
@@ -588,6 +610,24 @@ int rex_multi_get_slot_groups(const rex_multi* m) {
   return m->slot_groups > 1 ? m->slot_groups : 1;
 }
 
+int rex_multi_get_tile_cost(const rex_multi* m, const rex_proc* proc, double* us) {
+  if (!m) return fail(REX_EINVAL, "null multi handle");
+  if (!us) return fail(REX_EINVAL, "null output pointer");
+  const int rc = validate_proc(proc);
+  if (rc) return rc;
+  *us = m->tile_us[tile_kind(proc)];
+  return REX_OK;
+}
+
+int rex_multi_set_tile_cost(rex_multi* m, const rex_proc* proc, double us) {
+  if (!m) return fail(REX_EINVAL, "null multi handle");
+  const int rc = validate_proc(proc);
+  if (rc) return rc;
+  if (!(us >= 0.0) || !std::isfinite(us)) return fail(REX_EINVAL, "tile cost must be finite and >= 0 (got %g)", us);
+  m->tile_us[tile_kind(proc)] = us;
+  return REX_OK;
+}
+
 int rex_multi_autotune(rex_multi* m, const rex_batch* batches, int nbatch, const rex_params* param_sets, int k,
                        void* stream, float* ms_out) {
   if (!m) return fail(REX_EINVAL, "null multi handle");
@@ -601,23 +641,57 @@ int rex_multi_autotune(rex_multi* m, const rex_batch* batches, int nbatch, const
     return cuda_fail((int)e, "autotune events");
   }
   const int keep = m->slot_groups;
-  int best = 1, rc = REX_OK;
+  double keep_us[PROC_LAST + 2];
+  std::memcpy(keep_us, m->tile_us, sizeof keep_us);
+  // mean ms per call of `reps` calls on these batches, after a warm-up call
+  auto timed = [&](const rex_batch* b, int nb, int reps, float* ms) -> int {
+    int r = multi_impl(m, b, nb, param_sets, k, stream);
+    if (r) return r;
+    cudaError_t ce = cudaEventRecord(e0, st);
+    for (int i = 0; i < reps && r == REX_OK && ce == cudaSuccess; ++i) r = multi_impl(m, b, nb, param_sets, k, stream);
+    if (r) return r;
+    if (ce == cudaSuccess) ce = cudaEventRecord(e1, st);
+    if (ce == cudaSuccess) ce = cudaEventSynchronize(e1);
+    float t = 0.f;
+    if (ce == cudaSuccess) ce = cudaEventElapsedTime(&t, e0, e1);
+    if (ce != cudaSuccess) return cuda_fail((int)ce, "autotune timing");
+    *ms = t / reps;
+    return REX_OK;
+  };
+  m->slot_groups = 1;
+  int rc = multi_impl(m, batches, nbatch, param_sets, k, stream);   // validates the arguments
+  // one tile's time per tile kind, from the first batch of that kind run alone in its
+  // persistent launch: with fewer tiles than blocks each tile has a block of its own
+  // and the launch lasts one tile, otherwise the blocks share out the tiles
+  bool seen[PROC_LAST + 2] = {};
+  for (int i = 0; i < nbatch && rc == REX_OK && k > 0; ++i) {
+    const rex_batch& b = batches[i];
+    const int key = tile_kind(b.proc);
+    if (b.nev == 0 || seen[key]) continue;
+    seen[key] = true;
+    float ms = 0.f;
+    rc = timed(&b, 1, 2, &ms);
+    if (rc) break;
+    const int epb = multi_events_per_tile(b.proc->kind, m->precision == REX_MIXED);
+    const double tiles = (double)((b.nev + epb - 1) / epb);
+    const int launches = (k + MULTI_MAX_POINTS - 1) / MULTI_MAX_POINTS;
+    int width = 0;
+    if (b.proc->kind != PROC_EE_MUMU) {
+      width = b.proc->orig.wt != 0.0;
+      for (int j = 0; j < k; ++j)
+        if (param_sets[j].wt != 0.0) width = 1;
+    }
+    const double grid = m->blocks[multi_class_of(b.proc->kind)][width];
+    const double us = 1e3 * ms / launches * (tiles < grid ? tiles : grid) / tiles;
+    m->tile_us[key] = us > 0.0 ? us : 1e-3;
+  }
+  int best = 1;
   float best_ms = 0.f;
   for (int c = 0; c < REX_MULTI_TUNE_CANDIDATES && rc == REX_OK; ++c) {
     m->slot_groups = cand[c];
-    rc = multi_impl(m, batches, nbatch, param_sets, k, stream);   // warm-up
-    if (rc) break;
-    e = cudaEventRecord(e0, st);
-    for (int r = 0; r < 3 && rc == REX_OK && e == cudaSuccess; ++r) rc = multi_impl(m, batches, nbatch, param_sets, k, stream);
-    if (e == cudaSuccess) e = cudaEventRecord(e1, st);
-    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
     float ms = 0.f;
-    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
-    if (e != cudaSuccess) {
-      rc = cuda_fail((int)e, "autotune timing");
-      break;
-    }
-    ms /= 3.f;
+    rc = timed(batches, nbatch, 3, &ms);
+    if (rc) break;
     if (ms_out) ms_out[c] = ms;
     if (c == 0 || ms < best_ms) {
       best_ms = ms;
@@ -627,6 +701,7 @@ int rex_multi_autotune(rex_multi* m, const rex_batch* batches, int nbatch, const
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   m->slot_groups = rc == REX_OK ? best : keep;
+  if (rc != REX_OK) std::memcpy(m->tile_us, keep_us, sizeof keep_us);
   return rc;
 }
 

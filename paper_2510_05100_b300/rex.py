@@ -44,6 +44,7 @@ EXPORTS = (
     "rex_set_variant", "rex_autotune", "rex_multi_create", "rex_reweight_multi", "rex_multi_capture",
     "rex_multi_replay", "rex_multi_free", "rex_reweight_multi_noalloc", "rex_multi_set_mode",
     "rex_multi_set_slot_groups", "rex_multi_get_slot_groups", "rex_multi_autotune",
+    "rex_multi_get_tile_cost", "rex_multi_set_tile_cost",
     "rex_surrogate_num_params", "rex_surrogate_last_error", "rex_surrogate_create",
     "rex_surrogate_set_weights", "rex_surrogate_get_weights", "rex_surrogate_loss_grad",
     "rex_surrogate_train", "rex_surrogate_reweight", "rex_surrogate_set_exact_alphas", "rex_surrogate_set_kernel",
@@ -141,6 +142,10 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.rex_multi_get_slot_groups.restype = ctypes.c_int
     lib.rex_multi_autotune.argtypes = [vp, bp, ctypes.c_int, pp, ctypes.c_int, vp, ctypes.POINTER(ctypes.c_float)]
     lib.rex_multi_autotune.restype = ctypes.c_int
+    lib.rex_multi_get_tile_cost.argtypes = [vp, vp, ctypes.POINTER(ctypes.c_double)]
+    lib.rex_multi_get_tile_cost.restype = ctypes.c_int
+    lib.rex_multi_set_tile_cost.argtypes = [vp, vp, ctypes.c_double]
+    lib.rex_multi_set_tile_cost.restype = ctypes.c_int
     fp = ctypes.POINTER(ctypes.c_float)
     lib.rex_surrogate_num_params.argtypes = []
     lib.rex_surrogate_num_params.restype = ctypes.c_int64
@@ -368,9 +373,20 @@ class Multi:
     def slot_groups(self, groups: int) -> None:
         _check(load().rex_multi_set_slot_groups(self._h, int(groups)))
 
+    def tile_cost(self, proc) -> float:
+        """rex_multi_get_tile_cost: measured microseconds of one tile of proc's kind (0: none)."""
+        us = ctypes.c_double()
+        _check(load().rex_multi_get_tile_cost(self._h, proc._h, ctypes.byref(us)))
+        return us.value
+
+    def set_tile_cost(self, proc, us: float) -> None:
+        """rex_multi_set_tile_cost (0 clears the measured cost)."""
+        _check(load().rex_multi_set_tile_cost(self._h, proc._h, float(us)))
+
     def autotune(self, batches, points: Sequence[dict], stream=None) -> list:
-        """rex_multi_autotune: time 1, 2, 3, 4, 6, 8 slot groups on these batches, keep the
-        fastest; returns the mean ms per launch of each."""
+        """rex_multi_autotune: measure each tile kind's cost, then time 1, 2, 3, 4, 6, 8
+        slot groups on these batches and keep the fastest; returns the mean ms per
+        launch of each."""
         arr = self._batches(batches)
         ms = (ctypes.c_float * 6)()
         _check(load().rex_multi_autotune(self._h, arr, len(batches), _param_array(points), len(points),

@@ -143,3 +143,13 @@ def test_injected_device_allocation_failure_is_reported(rex, monkeypatch):
     assert lib.rex_surrogate_create(1, ctypes.byref(h)) == rex.REX_ENOMEM
     assert not h.value
     assert b"out of memory" in lib.rex_surrogate_last_error()
+
+
+def test_tile_cost_calls_validate_their_handles(rex):
+    lib = rex.load()
+    p = rex.Process("gg_ttxg")
+    us = ctypes.c_double(-1.0)
+    assert lib.rex_multi_get_tile_cost(None, p._h, ctypes.byref(us)) == rex.REX_EINVAL
+    assert lib.rex_multi_set_tile_cost(None, p._h, 1.0) == rex.REX_EINVAL
+    assert us.value == -1.0
+    p.close()

@@ -207,3 +207,62 @@ def test_slot_groups_and_autotune(rex, precision):
     assert len(ms) == 6 and all(t > 0 for t in ms)
     assert m.slot_groups == (1, 2, 3, 4, 6, 8)[int(np.argmin(ms))]
     m.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_measured_tile_costs_order_the_launch(rex, precision, tmp_path):
+    """rex_multi_autotune measures one tile's time per tile kind (seven batches, six
+    kinds: the crossed q g channel has a tile of its own) and the persistent launch
+    then hands out its items by those costs.  The order changes no weight: estimated,
+    measured and reversed costs give bitwise the same outputs.  The tuning cache
+    stores the costs and restores them into a new handle without timing."""
+    from paper_2510_05100_b300 import tune_cache
+    pts = points(16)
+    items = setup(rex, precision, seed=23)
+    for proc, n in (("qq_ttxg", 77), ("qg_ttxq", 45)):
+        p = rex.Process(proc, precision)
+        p.set_params(ORIG_QCD)
+        items.append((proc, p, ps.make_events(proc, n, 300 + n), np.random.default_rng(n).uniform(0.5, 2.0, n)))
+    batches = [(p, dev(mom), dev(w), torch.zeros((mom.shape[0], len(pts)), dtype=torch.float64, device="cuda"))
+               for _, p, mom, w in items]
+    m = rex.Multi(precision)
+    assert all(m.tile_cost(b[0]) == 0.0 for b in batches)
+
+    def run(handle):
+        for b in batches:
+            b[3].zero_()
+        handle.reweight(batches, pts)
+        torch.cuda.synchronize()
+        return [b[3].cpu().numpy().copy() for b in batches]
+
+    estimated = run(m)
+    m.autotune(batches, pts)
+    cost = {name: m.tile_cost(b[0]) for (name, *_), b in zip(items, batches)}
+    assert all(c > 0 for c in cost.values()), cost
+    assert cost["gg_ttxgg"] > cost["gg_ttxg"] > cost["gg_ttx"], cost
+    m.slot_groups = 1
+    measured = run(m)
+    for (name, *_), b in zip(items, batches):
+        m.set_tile_cost(b[0], 1.0 / cost[name])          # the opposite order
+    reversed_ = run(m)
+    for a, b, c in zip(estimated, measured, reversed_):
+        assert np.array_equal(a, b) and np.array_equal(a, c)
+    m.set_tile_cost(batches[0][0], 0.0)
+    assert m.tile_cost(batches[0][0]) == 0.0
+    for bad in (-1.0, float("nan"), float("inf")):
+        with pytest.raises(rex.RexError):
+            m.set_tile_cost(batches[0][0], bad)
+    m.close()
+
+    path = str(tmp_path / "tune.json")
+    m1 = rex.Multi(precision)
+    e1 = tune_cache.autotune_multi(m1, batches, pts, path)
+    m2 = rex.Multi(precision)
+    e2 = tune_cache.autotune_multi(m2, batches, pts, path)
+    assert not e1["cached"] and e2["cached"] and m2.slot_groups == m1.slot_groups
+    for b in batches:
+        assert m2.tile_cost(b[0]) == m1.tile_cost(b[0]) > 0
+    m1.close()
+    m2.close()
+    for _, p, *_ in items:
+        p.close()

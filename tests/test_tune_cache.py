@@ -1,5 +1,5 @@
 """The JSON cache of tuning choices (host logic, no GPU): a miss tunes and stores, a hit
-applies the stored choice without timing, keys separate GPU, process, precision, k and
+applies the stored choice (and the multi handle's tile costs) without timing, keys separate GPU, process, precision, k and
 batch composition, and an unreadable file counts as empty."""
 import json
 
@@ -25,11 +25,20 @@ class FakeBatch:
 class FakeMulti:
     def __init__(self, precision=1, best=2):
         self.precision, self.slot_groups, self.best, self.tuned = precision, 1, best, 0
+        self.costs = {}
 
     def autotune(self, batches, points, stream=None):
         self.tuned += 1
         self.slot_groups = self.best
+        for i, b in enumerate(batches):
+            self.costs[b[0].name] = 10.0 * (i + 1) + self.best
         return [3.0, 2.0, 2.5]
+
+    def tile_cost(self, proc):
+        return self.costs.get(proc.name, 0.0)
+
+    def set_tile_cost(self, proc, us):
+        self.costs[proc.name] = us
 
 
 def test_miss_tunes_and_stores_then_hit_applies_without_timing(tmp_path):
@@ -63,9 +72,11 @@ def test_slot_groups_keyed_by_batch_composition(tmp_path):
     batches = [(FakeProcess("gg_ttx"), FakeBatch(8000), None, None), (FakeProcess("qq_ttx"), FakeBatch(3000), None, None)]
     m = FakeMulti(best=2)
     assert tune_cache.autotune_multi(m, batches, [{}] * 64, path, gpu="B300")["choice"] == 2
+    assert m.costs == {"gg_ttx": 12.0, "qq_ttx": 22.0}
     m2 = FakeMulti(best=6)
     e = tune_cache.autotune_multi(m2, batches, [{}] * 64, path, gpu="B300")
     assert e["cached"] and m2.slot_groups == 2 and m2.tuned == 0
+    assert m2.costs == {"gg_ttx": 12.0, "qq_ttx": 22.0}     # the stored tile costs, restored
     other = [(FakeProcess("gg_ttx"), FakeBatch(8001), None, None)] + batches[1:]
     m3 = FakeMulti(best=3)
     assert not tune_cache.autotune_multi(m3, other, [{}] * 64, path, gpu="B300")["cached"]
