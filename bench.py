@@ -201,6 +201,7 @@ def main():
     ap.add_argument("--no-xsec", action="store_true")
     ap.add_argument("--no-lhe", action="store_true")
     ap.add_argument("--no-qq", action="store_true", help="skip the q q~ -> t t~ (g) and p p -> t t~ legs")
+    ap.add_argument("--no-helicity", action="store_true", help="skip the helicity-exclusive leg")
     args = ap.parse_args()
     world, rank, local = rdist.env()
     if args.impl == "reference":
@@ -327,6 +328,7 @@ def run_multi_leg(dev, stream, steps, world, barrier, max_over_ranks):
     ms_seq = timed(sequential_step)
     ms_str = timed(lambda: ms_streams.replay(stream))
     m_groups = m.slot_groups
+    tile_us = {proc: m.tile_cost(b[0]) for (proc, _, _), b in zip(MULTI_BATCHES, batches)}
     m.close()
     fl = multi_amp_flops([(proc, n) for proc, n, _ in MULTI_BATCHES], pts)
     ms_streams.close()
@@ -334,6 +336,7 @@ def run_multi_leg(dev, stream, steps, world, barrier, max_over_ranks):
             "value": rdist.job_throughput(units, world, ms_graph * 1e-3), "unit": UNIT,
             "ms_per_step": ms_graph, "graph_launches_per_step": 1, "slot_groups": m_groups,
             "autotune_ms_per_launch": dict(zip((1, 2, 3, 4, 6, 8), tune)),
+            "measured_tile_us": tile_us,   # one block's time per tile: the order of the work items
             "kernel_launches_per_step": 3,   # one persistent kernel per register class present
             "sequential_value": rdist.job_throughput(units, world, ms_seq * 1e-3),
             "sequential_ms_per_step": ms_seq,
@@ -415,6 +418,7 @@ def run_small_multi_leg(dev, stream, steps, world, barrier, max_over_ranks):
     ms_seq_graph = timed(lambda: g.replay())
     ms_streams_graph = timed(lambda: ms_streams.replay(stream))
     ms_seq = timed(sequential_step)
+    tile_us = {proc: m.tile_cost(b[0]) for (proc, _, _, _), b in zip(SMALL_MULTI_BATCHES, batches)}
     m.close()
     ms_streams.close()
     for b in batches:
@@ -429,7 +433,7 @@ def run_small_multi_leg(dev, stream, steps, world, barrier, max_over_ranks):
                       "streams_graph": frac(ms_streams_graph), "sequential_launches": frac(ms_seq)},
             "persistent_graph": {"value": val(ms_persistent), "ms_per_step": ms_persistent,
                                  "slot_groups": groups, "autotune_ms_per_launch": dict(zip((1, 2, 3, 4, 6, 8), tune)),
-                                 "without_slot_groups_ms_per_step": ms_persistent1},
+                                 "without_slot_groups_ms_per_step": ms_persistent1, "measured_tile_us": tile_us},
             "per_process_graph": {"value": val(ms_seq_graph), "ms_per_step": ms_seq_graph},
             "streams_graph": {"value": val(ms_streams_graph), "ms_per_step": ms_streams_graph},
             "sequential_launches": {"value": val(ms_seq), "ms_per_step": ms_seq},
@@ -756,6 +760,68 @@ def run_qq_leg(dev, stream, pts, steps, nev=NEV):
     return out
 
 
+HEL_SEED = SEED + 200   # helicity configurations of the exclusive leg's events
+
+
+def helicity_inputs(nev=NEV):
+    """The exclusive leg's events: the headline sample, each with a random configuration
+    of its five helicities (+1/-1, int8 [nev][5])."""
+    mom = ps.make_events(PROC, nev, SEED)
+    hel = np.random.default_rng(HEL_SEED).choice(np.array([-1, 1], dtype=np.int8), size=(nev, 5))
+    return mom, hel
+
+
+def run_helicity_leg(dev, stream, pts, steps, nev=NEV):
+    """Helicity-exclusive reweighting (rex_reweight_helicity) of the headline workload:
+    each event reweighted with its own helicity configuration, FP64 and mixed, beside the
+    helicity-summed launch on the same events.  Counted flops: the exclusive tile's
+    amplitude arithmetic (its lanes evaluate the quark line for the event's antitop
+    helicity only)."""
+    import torch
+    from paper_2510_05100_b300 import flops as flopmod
+    from paper_2510_05100_b300 import rex
+    k = len(pts)
+    mom_np, hel_np = helicity_inputs(nev)
+    mom = torch.from_numpy(mom_np).to(dev)
+    hel = torch.from_numpy(hel_np).to(dev)
+    w_in = torch.ones(nev, dtype=torch.float64, device=dev)
+    w_out = torch.empty((nev, k), dtype=torch.float64, device=dev)
+    nmass = 1 + len({p["mt"] for p in pts} - {ORIGINAL["mt"]})
+    p64 = SM_COUNT * FP64_FMA_PER_SM_CLK * 2 * SM_MAX_MHZ * 1e6
+    out = {"workload": f"{PROC}, {nev} events x {k} points, each event with a random helicity configuration "
+                       "(the headline's sample and grid)",
+           "stated_rel_error": {"fp64": 1e-12, "mixed": 1e-3}}
+
+    def timed(fn):
+        for _ in range(2):
+            fn()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        torch.cuda.synchronize(dev)
+        for a, b in ev:
+            a.record(stream)
+            fn()
+            b.record(stream)
+        torch.cuda.synchronize(dev)
+        return statistics.mean(a.elapsed_time(b) for a, b in ev) * 1e-3
+
+    for name, prec in (("fp64", rex.FP64), ("mixed", rex.MIXED)):
+        proc = rex.Process(PROC, prec)
+        proc.set_params(ORIGINAL)
+        t = timed(lambda: proc.reweight_helicity(mom, hel, w_in, pts, w_out=w_out, stream=stream))
+        t_sum = timed(lambda: proc.reweight(mom, w_in, pts, w_out=w_out, stream=stream))
+        proc.close()
+        cnt = flopmod.per_event(PROC, nmass, exclusive=True)
+        if prec == rex.FP64:
+            fl, pk, pipe = cnt["total"] * nev, p64, "FP64 FMA"
+        else:
+            fl, pk, pipe = cnt["amp"] * nev, FP32_PEAK, "FP32 FMA (amplitudes; FP64 invariants not counted)"
+        out[name] = {"value": nev * k / t, "unit": UNIT, "ms_per_launch": t * 1e3,
+                     "helicity_summed_ms_per_launch": t_sum * 1e3, "exclusive_over_summed_time": t / t_sum,
+                     "roofline": {"bound": "alu", "pipe": pipe, "achieved": fl / t / 1e12, "peak": pk / 1e12,
+                                  "unit": "TFLOP/s", "frac": fl / t / pk, "flops_per_launch": fl}}
+    return out
+
+
 def run_small_configs_leg(dev, stream, steps):
     """The two single-process workloads beside the headline.
 
@@ -1050,6 +1116,7 @@ def run_ours(args, world, rank, local):
     lhe_leg = None if args.no_lhe else run_lhe_leg(dev, stream, pts)
     qq_leg = None if args.no_qq else run_qq_leg(dev, stream, pts, max(5, args.steps // 2))
     qqg_leg = None if args.no_qq else run_qqg_leg(dev, stream, pts, max(3, args.steps // 4))
+    hel_leg = None if args.no_helicity else run_helicity_leg(dev, stream, pts, max(3, args.steps // 4))
     pp_leg = None if args.no_qq else run_pp_ttx_leg(dev, stream, pts, max(3, args.steps // 4), world, barrier,
                                                      max_over_ranks)
     ppj_leg = None if args.no_qq else run_pp_ttx_leg(dev, stream, pts, 3, world, barrier, max_over_ranks,
@@ -1087,7 +1154,7 @@ def run_ours(args, world, rank, local):
                 "gpu_launches": args.steps, "roofline": roofline, "cpu_baseline": cpu, "modes": extra,
                 "multi": multi, "surrogate": surrogate, "xsec": xsec, "lhe": lhe_leg, "qq_ttx": qq_leg,
                 "qq_ttxg": qqg_leg, "pp_ttx": pp_leg, "pp_ttxj": ppj_leg, "configs_1_2": small,
-                "multi_small_batches": small_multi}
+                "multi_small_batches": small_multi, "helicity_exclusive": hel_leg}
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist

@@ -170,6 +170,12 @@ int rex_reweight(rex_proc *proc, const double *momenta, const double *w_in,
  * the event's own top and antitop helicities are evaluated.  The crossings of
  * qq_ttxg use the helicity sum's freedom in their wavefunctions and return
  * REX_EUNSUPPORTED.
+ * Error against FP64 per weight: the helicity sum's bound of the mode (1e-12 in
+ * REX_FP64, the process's REX_MIXED bound), or, for a term far below its event's
+ * helicity sum, up to 64 eps (sqrt(kappa_0) + sqrt(kappa_j)) with eps the mode's
+ * unit roundoff and kappa = |M|^2 / |M_h|^2 at the original point and at point j:
+ * the amplitudes that cancel into a small |M_h| are of the size of the whole sum's
+ * and leave their rounding on it.
  * Enqueue only.  Errors: REX_EUNSUPPORTED, REX_EINVAL (as rex_reweight, null
  * helicities), REX_ENOTINIT, REX_ECUDA. */
 int rex_reweight_helicity(rex_proc *proc, const double *momenta, const signed char *helicities,

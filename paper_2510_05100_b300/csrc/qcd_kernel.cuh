@@ -389,8 +389,17 @@ static int launch_variant(int variant, const double* mom, const double* w_in, in
   }
 }
 
+// resident blocks per SM the register allocator must allow in the helicity-exclusive
+// kernels: 4 in mixed precision (16 warps per SM; g g -> t t~ g 2^20 x 16 in 3.73 ms
+// against 4.79 ms at the 245 registers of 1 block), except g g -> t t~ g g, whose
+// lanes would spill 3 KB at 128 registers; 1 in FP64
+template <int PROC, typename R>
+constexpr int exclusive_minb() {
+  return (std::is_same<R, float>::value && PROC != PROC_GG_TTXGG) ? 4 : 1;
+}
+
 template <int PROC, typename R, bool WIDTH>
-__global__ void __launch_bounds__(QCD_BLOCK, 1)
+__global__ void __launch_bounds__(QCD_BLOCK, exclusive_minb<PROC, R>())
     qcd_exclusive_kernel(const double* __restrict__ mom, const double* __restrict__ w_in, int64_t nev,
                          const __grid_constant__ QcdLaunch lp, double* __restrict__ out,
                          const signed char* __restrict__ hel) {

@@ -75,9 +75,10 @@ using namespace rex;
 // Counts per call: event setup (once per event), mass setup (once per event and
 // mass slot), gluon currents (once per event and polarisation configuration),
 // polarisation vectors (idem), quark line (once per event, polarisation
-// configuration and mass slot).
-template <int NG, class EV, class MS, class GL, class ES, class MSF, class GC, class QL>
-void count(const char* name, int nghel, ES es, MSF msf, GC gc, QL ql, bool last) {
+// configuration and mass slot; and its amplitude arithmetic for one antitop
+// helicity, what a helicity-exclusive tile evaluates).
+template <int NG, class EV, class MS, class GL, class ES, class MSF, class GC, class QL, class QLX>
+void count(const char* name, int nghel, ES es, MSF msf, GC gc, QL ql, QLX qlx, bool last) {
   double p[NG + 2][4];
   RC eps[NG][4], pr[NG + 2][4];
   for (int i = 0; i < NG + 2; ++i)
@@ -107,10 +108,13 @@ void count(const char* name, int nghel, ES es, MSF msf, GC gc, QL ql, bool last)
   AC::flops = 0;
   ql(ev, mm, J);
   const long long f_line_r = RC::flops, f_line_a = AC::flops;
+  RC::flops = 0;
+  qlx(ev, mm, J);
+  const long long f_line_x = RC::flops;
   std::printf("  \"%s\": {\"nghel\": %d, \"event_setup\": %lld, \"mass_setup\": %lld, "
               "\"polarisations\": %lld, \"gluon_currents\": %lld, \"quark_line_amp\": %lld, "
-              "\"quark_line_acc\": %lld}%s\n",
-              name, nghel, f_event, f_mass, f_pol, f_gluon, f_line_r, f_line_a, last ? "" : ",");
+              "\"quark_line_acc\": %lld, \"quark_line_amp_one_antitop\": %lld}%s\n",
+              name, nghel, f_event, f_mass, f_pol, f_gluon, f_line_r, f_line_a, f_line_x, last ? "" : ",");
 }
 
 #define REX_COUNT(NAME, NG, LAST)                                                                   \
@@ -119,7 +123,8 @@ void count(const char* name, int nghel, ES es, MSF msf, GC gc, QL ql, bool last)
       [](const double* p, auto& ev) { NAME##_event_phase1(p, ev, 0, 1); NAME##_event_phase2(ev, 173.0 * 173.0, 0, 1); }, \
       [](auto& ev, double m, double w, auto& mm) { NAME##_mass_setup<RC, false>(ev, m, w, RC(0.0), mm, 0, 1); }, \
       [](auto& ev, auto& eps, auto& J) { NAME##_gluon_currents(ev, eps, J); },                       \
-      [](auto& ev, auto& mm, auto& J) { return NAME##_quark_line<RC, AC, false, RC>(ev, mm, J); }, LAST)
+      [](auto& ev, auto& mm, auto& J) { return NAME##_quark_line<RC, AC, false, RC>(ev, mm, J); },      \
+      [](auto& ev, auto& mm, auto& J) { return NAME##_quark_line<RC, AC, false, RC>(ev, mm, J, 0, 1); }, LAST)
 
 int main() {
   std::printf("{\n");

@@ -35,15 +35,19 @@ def counts() -> dict:
     return json.loads(out)
 
 
-def per_event(proc: str, nmass: int) -> dict:
+def per_event(proc: str, nmass: int, exclusive: bool = False) -> dict:
     """Flops of one event evaluated at ``nmass`` distinct mass slots.
 
     'amp': amplitude arithmetic (FP64 in REX_FP64, FP32 in REX_MIXED);
     'acc': colour/helicity accumulation (FP64 in both modes).
+    exclusive: the helicity-exclusive g g tile, whose lanes evaluate the quark line
+    for the event's own antitop helicity only (its colour form counted as the summed
+    tile's; the warp shuffles that combine the lanes' jamps are not counted).
     """
     c = counts()[proc]
     nh = c["nghel"]
+    line = c["quark_line_amp_one_antitop"] if exclusive else c["quark_line_amp"]
     amp = (c["event_setup"] + nmass * c["mass_setup"]
-           + nh * (c["gluon_currents"] + c["polarisations"] + nmass * c["quark_line_amp"]))
+           + nh * (c["gluon_currents"] + c["polarisations"] + nmass * line))
     acc = nh * nmass * c["quark_line_acc"]
     return {"amp": amp, "acc": acc, "total": amp + acc}

@@ -178,3 +178,49 @@ def test_qq_ttxg_exclusive_parity(rex, precision, tol):
     bound = helicity_tolerance("qq_ttxg", mom, hel, QCD_ORIG, pts, tol, eps)
     err = np.abs(got - ref) / np.where(ref != 0.0, np.abs(ref), 1.0)
     assert np.all(err[~zero] < bound[~zero])
+
+
+def test_full_size_exclusive_headline_workload(rex):
+    """The helicity-exclusive leg of bench.py at its full size and in its launch: 2^20
+    g g -> t t~ g events (the headline sample, seed 3) x the 16 headline points, each
+    event with a random configuration (seed 203).  FP64 against the extended-precision
+    oracle on sampled events; mixed against FP64 at every event, within
+    max(1e-3, 64 eps32 (sqrt(kappa_0) + sqrt(kappa_j))).  kappa_0 = |M_0|^2 / |M_h,0|^2
+    comes from the oracle for the events beyond 1e-3, and kappa_j = kappa_0 w'_j / w'_h,j
+    from the FP64 summed and exclusive weights (the ratio of the two reweightings is
+    kappa_j / kappa_0)."""
+    n = 1 << 20
+    mom = ps.make_events("gg_ttxg", n, 3)
+    hel = np.random.default_rng(203).choice(np.array([-1, 1], dtype=np.int8), size=(n, 5))
+    w = np.ones(n)
+    pts = ps.grid_gg_ttxg()
+    dm, dh, dw = dev(mom), dev(hel), dev(w)
+    exact = rex.Process("gg_ttxg", 0)
+    exact.set_params(QCD_ORIG)
+    fp64 = exact.reweight_helicity(dm, dh, dw, pts).cpu().numpy()
+    mixed_p = rex.Process("gg_ttxg", 1)
+    mixed_p.set_params(QCD_ORIG)
+    mixed = mixed_p.reweight_helicity(dm, dh, dw, pts).cpu().numpy()
+
+    rng = np.random.default_rng(7)
+    idx = np.concatenate([rng.choice(n, 22, replace=False), [0, n - 1]])
+    ref = extended_reference("gg_ttxg", mom[idx], hel[idx], w[idx], pts)
+    bound = helicity_tolerance("gg_ttxg", mom[idx], hel[idx], QCD_ORIG, pts, 1e-12, np.finfo(np.float64).eps / 2)
+    assert np.all(np.abs(fp64[idx] / ref - 1.0) < bound)
+
+    both = (fp64 != 0.0) & (mixed != 0.0)
+    assert np.all((fp64 == 0.0) == (mixed == 0.0)) or np.mean(both) > 0.999
+    err = np.where(both, np.abs(mixed / np.where(both, fp64, 1.0) - 1.0), 0.0)
+    far = np.nonzero(np.any(err > 1e-3, axis=1))[0]
+    assert len(far) <= n // 100, len(far)           # small terms only (1.5e-3 of the events here)
+    if len(far):
+        summed = exact.reweight(dev(mom[far]), dev(w[far]), pts).cpu().numpy()
+        m0 = oracle_rw.me2("gg_ttxg", mom[far], QCD_ORIG)
+        m0h = oracle_rw.me2_helicity("gg_ttxg", mom[far], QCD_ORIG, hel[far])
+        k0 = m0 / m0h
+        nz = fp64[far] != 0.0
+        kj = np.where(nz, k0[:, None] * summed / np.where(nz, fp64[far], 1.0), np.inf)
+        bound = np.maximum(1e-3, 64.0 * (np.finfo(np.float32).eps / 2) * (np.sqrt(k0)[:, None] + np.sqrt(kj)))
+        assert np.all(err[far] < bound), np.max(err[far] / bound)
+    exact.close()
+    mixed_p.close()
