@@ -67,8 +67,8 @@ TRAFFIC = {
     # ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum of profile_case at 2^19
     # events (FP64, scaled x2 by events) and 2^20 events (mixed); summaries of the
     # captures are under profiles/
-    ("gg_ttxg", "fp64"): {"bytes_per_launch": 2 * (91.502848e6 + 35.003648e6), "source_hash": "3595a4023fc99614"},
-    ("gg_ttxg", "mixed"): {"bytes_per_launch": 176.351488e6 + 104.789760e6, "source_hash": "3595a4023fc99614"},
+    ("gg_ttxg", "fp64"): {"bytes_per_launch": 2 * (91.620864e6 + 34.870784e6), "source_hash": "5a809526a53ffab1"},
+    ("gg_ttxg", "mixed"): {"bytes_per_launch": 176.351744e6 + 104.733184e6, "source_hash": "5a809526a53ffab1"},
 }
 
 
