@@ -184,9 +184,14 @@ int rex_reweight_helicity(rex_proc *proc, const double *momenta, const signed ch
 
 /* Same computation with HOST arrays: copies momenta and w_in to the device,
  * reweights, copies w_out back and synchronises stream before returning.
- * Page-locked host memory makes the copies asynchronous DMA.  Device
- * buffers are library-owned, grown on demand and kept until rex_free_process.
- * Errors: as rex_reweight, plus REX_ENOMEM. */
+ * The events go in chunks (at least 2^16 events, at most 8 chunks) on two
+ * streams of the handle, forked from stream after the work already on it and
+ * joined back into it: a chunk's kernel runs while the next chunk's inputs are
+ * copied in and the previous chunk's weights copied out.  Page-locked host
+ * memory makes the copies asynchronous DMA, which this overlap needs.  Device
+ * buffers and the two streams are library-owned, made on first use and kept
+ * until rex_free_process.  On an error the call still waits for every copy it
+ * had enqueued.  Errors: as rex_reweight, plus REX_ENOMEM. */
 int rex_reweight_host(rex_proc *proc, const double *momenta, const double *w_in,
                       int64_t nev, const rex_params *param_sets, int k,
                       double *w_out, void *stream);

@@ -66,6 +66,9 @@ struct rex_proc {
   double* d_win;
   double* d_wout;
   size_t cap_mom, cap_win, cap_wout;
+  // rex_reweight_host pipeline: two streams forked from the caller's, created on first use
+  cudaStream_t hs[2];
+  cudaEvent_t hfork, hjoin[2];
 };
 
 namespace {
@@ -545,6 +548,25 @@ int multi_impl(rex_multi* m, const rex_batch* batches, int nbatch, const rex_par
   return REX_OK;
 }
 
+int ensure_host_pipeline(rex_proc* p) {
+  if (p->hs[0]) return REX_OK;
+  cudaError_t e = cudaEventCreateWithFlags(&p->hfork, cudaEventDisableTiming);
+  for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
+    e = cudaStreamCreateWithFlags(&p->hs[i], cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->hjoin[i], cudaEventDisableTiming);
+  }
+  if (e == cudaSuccess) return REX_OK;
+  for (int i = 0; i < 2; ++i) {
+    if (p->hs[i]) cudaStreamDestroy(p->hs[i]);
+    if (p->hjoin[i]) cudaEventDestroy(p->hjoin[i]);
+    p->hs[i] = nullptr;
+    p->hjoin[i] = nullptr;
+  }
+  if (p->hfork) cudaEventDestroy(p->hfork);
+  p->hfork = nullptr;
+  return cuda_fail((int)e, "host-copy pipeline streams");
+}
+
 }  // namespace
 
 extern "C" {
@@ -935,14 +957,48 @@ int rex_reweight_host(rex_proc* proc, const double* momenta, const double* w_in,
   if ((rc = grow(&proc->d_mom, &proc->cap_mom, nm))) return rc;
   if ((rc = grow(&proc->d_win, &proc->cap_win, nw))) return rc;
   if ((rc = grow(&proc->d_wout, &proc->cap_wout, no))) return rc;
+  if ((rc = ensure_host_pipeline(proc))) return rc;
+  // Chunks of events alternate between two streams forked from the caller's: while one
+  // chunk's kernel runs, the next chunk's inputs come in and the previous chunk's weights
+  // go out (the copy engines of each direction work beside the SMs).  At least 2^16
+  // events per chunk, so that a launch still fills the GPU; the two streams' kernels
+  // overlap at the chunk boundaries.
+  const int64_t chunk = std::max<int64_t>(int64_t(1) << 16, (nev + 7) / 8);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  cudaError_t e = cudaMemcpyAsync(proc->d_mom, momenta, nm * sizeof(double), cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(proc->d_win, w_in, nw * sizeof(double), cudaMemcpyHostToDevice, st);
-  if (e != cudaSuccess) return cuda_fail((int)e, "host-to-device copy");
-  rc = reweight_impl(proc, proc->d_mom, proc->d_win, nev, param_sets, k, proc->d_wout, stream);
-  if (rc) return rc;
-  e = cudaMemcpyAsync(w_out, proc->d_wout, no * sizeof(double), cudaMemcpyDeviceToHost, st);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaError_t e = cudaEventRecord(proc->hfork, st);
+  for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = cudaStreamWaitEvent(proc->hs[i], proc->hfork, 0);
+  if (e != cudaSuccess) return cuda_fail((int)e, "host-copy pipeline fork");
+  int c = 0;
+  for (int64_t e0 = 0; e0 < nev && rc == REX_OK; e0 += chunk, ++c) {
+    const int64_t n = std::min(chunk, nev - e0);
+    cudaStream_t cs = proc->hs[c & 1];
+    const size_t om = (size_t)e0 * npart * 4, oo = (size_t)e0 * (size_t)k;
+    e = cudaMemcpyAsync(proc->d_mom + om, momenta + om, (size_t)n * npart * 4 * sizeof(double),
+                        cudaMemcpyHostToDevice, cs);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(proc->d_win + e0, w_in + e0, (size_t)n * sizeof(double), cudaMemcpyHostToDevice, cs);
+    if (e != cudaSuccess) {
+      rc = cuda_fail((int)e, "host-to-device copy");
+      break;
+    }
+    rc = reweight_impl(proc, proc->d_mom + om, proc->d_win + e0, n, param_sets, k, proc->d_wout + oo, cs);
+    if (rc) break;
+    e = cudaMemcpyAsync(w_out + oo, proc->d_wout + oo, (size_t)n * (size_t)k * sizeof(double),
+                        cudaMemcpyDeviceToHost, cs);
+    if (e != cudaSuccess) rc = cuda_fail((int)e, "device-to-host copy");
+  }
+  // join back into the caller's stream (also after an error, so that no copy into the
+  // caller's arrays is still in flight when the call returns)
+  for (int i = 0; i < 2; ++i) {
+    cudaError_t ej = cudaEventRecord(proc->hjoin[i], proc->hs[i]);
+    if (ej == cudaSuccess) ej = cudaStreamWaitEvent(st, proc->hjoin[i], 0);
+    if (ej != cudaSuccess) {
+      cudaStreamSynchronize(proc->hs[i]);
+      if (rc == REX_OK) rc = cuda_fail((int)ej, "host-copy pipeline join");
+    }
+  }
+  e = cudaStreamSynchronize(st);
+  if (rc != REX_OK) return rc;
   if (e != cudaSuccess) return cuda_fail((int)e, "device-to-host copy");
   return REX_OK;
 }
@@ -1037,6 +1093,11 @@ void rex_free_process(rex_proc* proc) {
   if (proc->d_mom) cudaFree(proc->d_mom);
   if (proc->d_win) cudaFree(proc->d_win);
   if (proc->d_wout) cudaFree(proc->d_wout);
+  for (int i = 0; i < 2; ++i) {
+    if (proc->hs[i]) cudaStreamDestroy(proc->hs[i]);
+    if (proc->hjoin[i]) cudaEventDestroy(proc->hjoin[i]);
+  }
+  if (proc->hfork) cudaEventDestroy(proc->hfork);
   delete proc;
 }
 

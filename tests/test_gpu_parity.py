@@ -194,6 +194,31 @@ def test_host_entry_point_matches_device_entry_point(rex):
     assert np.array_equal(dev_out, host_out)
 
 
+@pytest.mark.parametrize("proc,precision", [("gg_ttx", 1), ("qq_ttx", 0), ("ee_mumu", 0)])
+def test_host_entry_point_pipelines_chunks(rex, proc, precision):
+    """rex_reweight_host in chunks of 2^16 events on two streams: 4 chunks and a ragged
+    tail, from page-locked and from pageable host arrays, bitwise equal to one device
+    launch; then a smaller call on the same handle (buffers already grown)."""
+    n = 3 * (1 << 16) + 4321
+    mom = ps.make_events(proc, n, 112)
+    w = np.random.default_rng(6).uniform(0.5, 2.0, n)
+    pts = ps.grid_gg_ttx()[:5] if proc != "ee_mumu" else [ps.EE_NEW, ps.EE_ORIGINAL]
+    p = rex.Process(proc, precision)
+    p.set_params(ps.EE_ORIGINAL if proc == "ee_mumu" else ORIG_QCD)
+    ref = p.reweight(dev(mom), dev(w), pts).cpu().numpy()
+    pinned = [torch.from_numpy(a).pin_memory() for a in (mom, w)]
+    out_pinned = torch.zeros((n, len(pts)), dtype=torch.float64).pin_memory()
+    p.reweight_host(pinned[0], pinned[1], pts, out_pinned)
+    assert np.array_equal(out_pinned.numpy(), ref)
+    out = np.zeros((n, len(pts)))
+    p.reweight_host(mom, w, pts, out)
+    assert np.array_equal(out, ref)
+    small = np.zeros((1000, len(pts)))
+    p.reweight_host(mom[:1000], w[:1000], pts, small)
+    assert np.array_equal(small, ref[:1000])
+    p.close()
+
+
 @pytest.mark.parametrize("proc", ["gg_ttx", "gg_ttxg", "gg_ttxgg"])
 def test_mixed_precision_error_bound(rex, proc):
     n = SIZES[proc] * 2
