@@ -28,10 +28,17 @@
 #include <type_traits>
 
 #include "colour_tc.cuh"
+#include "df64.cuh"
 #include "generated/qcd_amplitudes.cuh"
 #include "rex_internal.cuh"
 
 namespace rex {
+
+// lane exchange of a warp (df64.cuh overloads it for double-float values)
+template <typename T>
+__device__ __forceinline__ T shfl_xor(T v, int off) {
+  return __shfl_xor_sync(0xffffffffu, v, off);
+}
 
 template <int PROC>
 struct QcdProc;
@@ -264,7 +271,7 @@ struct QcdTile {
         if (valid) s = P::template quark_line<R, R, WIDTH>(evd, sm.mss[el], J, hb_lo, hb_hi);
       }
 #pragma unroll
-      for (int off = NH / 2; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+      for (int off = NH / 2; off > 0; off >>= 1) s += shfl_xor(s, off);
       if (leader) {
         if constexpr (F32) sm.me2f[el][m] = s;
         else sm.me2s[el][m] = double(s);
@@ -276,7 +283,7 @@ struct QcdTile {
     const int nblk = (int)((nev - ev0) < EPB ? (nev - ev0) : EPB);
     if (lp.mode == OUT_RATIO) {
       const int k = lp.k;
-      if constexpr (std::is_same<R, double>::value) {
+      if constexpr (!F32) {   // FP64 and double-float: the FP64 slot sums and ratio
         for (int idx = tid; idx < nblk * k; idx += QCD_BLOCK) {
           const int e = idx / k;
           const int j = idx - e * k;
@@ -428,6 +435,36 @@ static int launch_exclusive(const double* mom, const double* w_in, int64_t nev, 
     cudaStream_t st = static_cast<cudaStream_t>(stream);                                                \
     return mixed ? launch_exclusive<KIND, float>(mom, w_in, nev, lp, out, hel, st)                      \
                  : launch_exclusive<KIND, double>(mom, w_in, nev, lp, out, hel, st);                    \
+  }
+
+// double-float amplitudes (REX_DF64, df64.cuh): one mapping per process at the
+// register allocator's own occupancy (255 registers, 8 warps per SM).  g g -> t t~ g
+// splits the antitop helicity over two lanes (half the live state: 488 B of spill
+// against 956 B; 162.7 against 167.3 ms for 2^20 x 16; 3 blocks per SM, at 168
+// registers, spill 1.8 KB and took 184 ms).
+template <int PROC>
+constexpr int df64_split() {
+  return PROC == PROC_GG_TTXG ? 1 : 0;
+}
+
+template <int PROC>
+static int launch_df64_t(const double* mom, const double* w_in, int64_t nev, const QcdLaunch& lp, double* out,
+                         cudaStream_t st) {
+  constexpr int SPLIT = df64_split<PROC>();
+  constexpr int EPB = QCD_BLOCK / (QcdProc<PROC>::info::NGHEL << SPLIT);
+  const int64_t blocks = (nev + EPB - 1) / EPB;
+  if (blocks > 0x7fffffffLL) return (int)cudaErrorInvalidValue;
+  if (lp.has_width)
+    qcd_reweight_kernel<PROC, df64, true, SPLIT, 1><<<(unsigned)blocks, QCD_BLOCK, 0, st>>>(mom, w_in, nev, lp, out);
+  else
+    qcd_reweight_kernel<PROC, df64, false, SPLIT, 1><<<(unsigned)blocks, QCD_BLOCK, 0, st>>>(mom, w_in, nev, lp, out);
+  return (int)cudaGetLastError();
+}
+
+#define REX_DEFINE_QCD_DF64_LAUNCHER(KIND, NAME)                                                       \
+  int launch_##NAME##_df64(const double* mom, const double* w_in, int64_t nev, const QcdLaunch& lp,   \
+                           double* out, void* stream) {                                               \
+    return launch_df64_t<KIND>(mom, w_in, nev, lp, out, static_cast<cudaStream_t>(stream));          \
   }
 
 #define REX_DEFINE_QCD_LAUNCHER(KIND, NAME)                                                          \

@@ -144,7 +144,9 @@ bool is_direct(const QqgCrossing& c) {
 const ProcInfo& info_of(int kind) { return kProcs[kind]; }
 
 // processes with one kernel (no thread-mapping variants to choose from)
-bool single_variant(int kind) { return kind == PROC_EE_MUMU || kind == PROC_QQ_TTX || kind == PROC_QQ_TTXG; }
+bool single_variant(const rex_proc* p) {
+  return p->precision == REX_DF64 || p->kind == PROC_EE_MUMU || p->kind == PROC_QQ_TTX || p->kind == PROC_QQ_TTXG;
+}
 
 // Default thread-mapping variant per (process, precision), the fastest of every
 // variant timed on a B300 at 2^20 (gg_ttx, gg_ttxg) / 2^16 (gg_ttxgg) events;
@@ -164,6 +166,11 @@ int default_variant(int kind, int precision) {
 int launch_qcd(const rex_proc* p, const double* mom, const double* w_in, int64_t nev, const QcdLaunch& lp,
                double* out, void* stream, const signed char* hel) {
   const int mixed = p->precision == REX_MIXED;
+  if (p->precision == REX_DF64) {   // gg_ttx and gg_ttxg only (rex_init_process), never exclusive
+    if (hel) return (int)cudaErrorInvalidValue;
+    return p->kind == PROC_GG_TTX ? launch_gg_ttx_df64(mom, w_in, nev, lp, out, stream)
+                                  : launch_gg_ttxg_df64(mom, w_in, nev, lp, out, stream);
+  }
   switch (p->kind) {
     case PROC_GG_TTX:
       return hel ? launch_gg_ttx_exclusive(mixed, mom, w_in, nev, lp, out, stream, hel)
@@ -574,6 +581,8 @@ extern "C" {
 int rex_multi_create(int precision, rex_multi** out) {
   if (!out) return fail(REX_EINVAL, "null output handle pointer");
   *out = nullptr;
+  if (precision == REX_DF64)
+    return fail(REX_EUNSUPPORTED, "the persistent multi-process kernels are built in FP64 and mixed precision");
   if (precision != REX_FP64 && precision != REX_MIXED) return fail(REX_EINVAL, "unknown precision %d", precision);
   rex_multi* m = new (std::nothrow) rex_multi;
   if (!m) return fail(REX_ENOMEM, "out of host memory");
@@ -824,6 +833,8 @@ extern "C" {
 
 int rex_reweight_multi_noalloc(const rex_batch* batches, int nbatch, const rex_params* param_sets, int k,
                                int precision, void* stream) {
+  if (precision == REX_DF64)
+    return fail(REX_EUNSUPPORTED, "the persistent multi-process kernels are built in FP64 and mixed precision");
   if (precision != REX_FP64 && precision != REX_MIXED) return fail(REX_EINVAL, "unknown precision %d", precision);
   if (k > MULTI_MAX_POINTS * NOALLOC_COUNTERS)
     return fail(REX_EINVAL,
@@ -860,7 +871,8 @@ int rex_init_process(const char* name, int precision, rex_proc** out) {
   if (!out) return fail(REX_EINVAL, "null output handle pointer");
   *out = nullptr;
   if (!name) return fail(REX_EINVAL, "null process name");
-  if (precision != REX_FP64 && precision != REX_MIXED) return fail(REX_EINVAL, "unknown precision %d", precision);
+  if (precision != REX_FP64 && precision != REX_MIXED && precision != REX_DF64)
+    return fail(REX_EINVAL, "unknown precision %d", precision);
   int kind = -1;
   for (const ProcInfo& pi : kProcs)
     if (std::strcmp(pi.name, name) == 0) kind = pi.kind;
@@ -873,6 +885,8 @@ int rex_init_process(const char* name, int precision, rex_proc** out) {
   if (kind < 0) return fail(REX_EINVAL, "unknown process '%s'", name);
   if (kind == PROC_EE_MUMU && precision != REX_FP64)
     return fail(REX_EUNSUPPORTED, "ee_mumu is implemented in FP64 only");
+  if (precision == REX_DF64 && kind != PROC_GG_TTX && kind != PROC_GG_TTXG)
+    return fail(REX_EUNSUPPORTED, "REX_DF64 is built for gg_ttx and gg_ttxg");
   rex_proc* p = new (std::nothrow) rex_proc;
   if (!p) return fail(REX_ENOMEM, "out of host memory");
   std::memset(p, 0, sizeof *p);
@@ -922,6 +936,8 @@ int rex_reweight_helicity(rex_proc* proc, const double* momenta, const signed ch
                           void* stream) {
   const int rc = validate_proc(proc);
   if (rc) return rc;
+  if (proc->precision == REX_DF64)
+    return fail(REX_EUNSUPPORTED, "helicity-exclusive reweighting is built in FP64 and mixed precision");
   if (proc->kind == PROC_QQ_TTXG && !is_direct(proc->cross))
     return fail(REX_EUNSUPPORTED,
                 "helicity-exclusive reweighting of q q~ -> t t~ g is built for the direct channel only; its "
@@ -1028,19 +1044,19 @@ int rex_me2(rex_proc* proc, const double* momenta, int64_t nev, const rex_params
 int rex_num_variants(const rex_proc* proc) {
   const int rc = validate_proc(proc);
   if (rc) return rc;
-  return single_variant(proc->kind) ? 1 : QCD_NVARIANT;
+  return single_variant(proc) ? 1 : QCD_NVARIANT;
 }
 
 int rex_get_variant(const rex_proc* proc) {
   const int rc = validate_proc(proc);
   if (rc) return rc;
-  return single_variant(proc->kind) ? 0 : proc->variant;
+  return single_variant(proc) ? 0 : proc->variant;
 }
 
 int rex_set_variant(rex_proc* proc, int variant) {
   const int rc = validate_proc(proc);
   if (rc) return rc;
-  const int n = single_variant(proc->kind) ? 1 : QCD_NVARIANT;
+  const int n = single_variant(proc) ? 1 : QCD_NVARIANT;
   if (variant < 0 || variant >= n) return fail(REX_EINVAL, "variant %d out of range [0, %d)", variant, n);
   proc->variant = variant;
   return REX_OK;
@@ -1050,7 +1066,7 @@ int rex_autotune(rex_proc* proc, const double* momenta, const double* w_in, int6
                  const rex_params* param_sets, int k, double* w_out, void* stream, float* ms_out) {
   int rc = validate_proc(proc);
   if (rc) return rc;
-  if (single_variant(proc->kind)) return REX_OK;
+  if (single_variant(proc)) return REX_OK;
   if (nev <= 0 || k <= 0) return fail(REX_EINVAL, "autotune needs nev > 0 and k > 0");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   cudaEvent_t e0, e1;

@@ -122,6 +122,11 @@ int launch_gg_ttxgg(int mixed, int variant, const double* mom, const double* w_i
                     const QcdLaunch& lp, double* out, void* stream);
 // Helicity-exclusive reweighting of the g g processes (the events' helicity
 // configurations hel [nev][npart], int8, positive: +1, otherwise -1).
+// double-float amplitudes (REX_DF64)
+int launch_gg_ttx_df64(const double* mom, const double* w_in, int64_t nev, const QcdLaunch& lp, double* out,
+                       void* stream);
+int launch_gg_ttxg_df64(const double* mom, const double* w_in, int64_t nev, const QcdLaunch& lp, double* out,
+                        void* stream);
 int launch_gg_ttx_exclusive(int mixed, const double* mom, const double* w_in, int64_t nev, const QcdLaunch& lp,
                             double* out, void* stream, const signed char* hel);
 int launch_gg_ttxg_exclusive(int mixed, const double* mom, const double* w_in, int64_t nev, const QcdLaunch& lp,

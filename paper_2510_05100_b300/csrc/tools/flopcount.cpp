@@ -64,6 +64,33 @@ inline Cnt<T> rsqrt(Cnt<T> a) { ++Cnt<T>::flops; return Cnt<T>(1.0 / std::sqrt(a
 using RC = Cnt<0>;    // amplitude arithmetic
 using AC = Cnt<1>;    // colour / helicity accumulation
 
+// Double-float (REX_DF64) cost of each operation in FP32 flops as df64.cuh performs
+// them (an FMA counts two, a division or square root one): sum 10, product 10,
+// fused multiply-add 18, quotient 25, square root 12, reciprocal square root 37;
+// sign flips, comparisons and FP64 -> double-float conversions cost none.
+struct DC {
+  static long long flops;
+  double v;
+  DC() : v(0) {}
+  DC(double x) : v(x) {}
+  explicit operator double() const { return v; }
+};
+long long DC::flops = 0;
+inline DC operator+(DC a, DC b) { DC::flops += 10; return DC(a.v + b.v); }
+inline DC operator-(DC a, DC b) { DC::flops += 10; return DC(a.v - b.v); }
+inline DC operator*(DC a, DC b) { DC::flops += 10; return DC(a.v * b.v); }
+inline DC operator/(DC a, DC b) { DC::flops += 25; return DC(a.v / b.v); }
+inline DC& operator+=(DC& a, DC b) { a = a + b; return a; }
+inline DC& operator-=(DC& a, DC b) { a = a - b; return a; }
+inline DC& operator*=(DC& a, DC b) { a = a * b; return a; }
+inline DC operator-(DC a) { return DC(-a.v); }
+inline bool operator>(DC a, DC b) { return a.v > b.v; }
+inline bool operator>=(DC a, DC b) { return a.v >= b.v; }
+inline bool operator<=(DC a, DC b) { return a.v <= b.v; }
+inline DC fma(DC a, DC b, DC c) { DC::flops += 18; return DC(a.v * b.v + c.v); }
+inline DC sqrt(DC a) { DC::flops += 12; return DC(std::sqrt(a.v)); }
+inline DC rsqrt(DC a) { DC::flops += 37; return DC(1.0 / std::sqrt(a.v)); }
+
 #include "../generated/qcd_amplitudes.cuh"
 #include "../qq_amplitude.cuh"
 #include "../qqg_amplitude.cuh"
@@ -126,8 +153,56 @@ void count(const char* name, int nghel, ES es, MSF msf, GC gc, QL ql, QLX qlx, b
       [](auto& ev, auto& mm, auto& J) { return NAME##_quark_line<RC, AC, false, RC>(ev, mm, J); },      \
       [](auto& ev, auto& mm, auto& J) { return NAME##_quark_line<RC, AC, false, RC>(ev, mm, J, 0, 1); }, LAST)
 
+// The same routines in double-float: FP32 flops per call (split 0 accounting: both
+// antitop helicities per quark-line call).
+template <int NG, class EV, class MS, class GL, class ES, class MSF, class GC, class QL>
+void count_df(const char* name, int nghel, ES es, MSF msf, GC gc, QL ql) {
+  double p[NG + 2][4];
+  DC eps[NG][4], pr[NG + 2][4];
+  for (int i = 0; i < NG + 2; ++i)
+    for (int m = 0; m < 4; ++m) {
+      p[i][m] = 1.0 + i + 0.1 * m;
+      pr[i][m] = DC(p[i][m]);
+    }
+  for (int i = 0; i < NG; ++i)
+    for (int m = 0; m < 4; ++m) eps[i][m] = DC(0.5);
+  EV ev;
+  MS mm;
+  GL J;
+  DC::flops = 0;
+  es(&p[0][0], ev);
+  const long long f_event = DC::flops;
+  DC::flops = 0;
+  msf(ev, 173.0, 0.0, mm);
+  const long long f_mass = DC::flops;
+  DC::flops = 0;
+  DC e[4];
+  for (int g = 0; g < NG; ++g) pol_linear(pr[g], 0, e);
+  const long long f_pol = DC::flops;
+  DC::flops = 0;
+  gc(ev, eps, J);
+  const long long f_gluon = DC::flops;
+  DC::flops = 0;
+  ql(ev, mm, J);
+  const long long f_line = DC::flops;
+  std::printf("  \"%s_df64\": {\"nghel\": %d, \"event_setup\": %lld, \"mass_setup\": %lld, "
+              "\"polarisations\": %lld, \"gluon_currents\": %lld, \"quark_line_amp\": %lld, "
+              "\"quark_line_acc\": 0, \"quark_line_amp_one_antitop\": 0},\n",
+              name, nghel, f_event, f_mass, f_pol, f_gluon, f_line);
+}
+
+#define REX_COUNT_DF(NAME, NG)                                                                      \
+  count_df<NG, NAME##_event<DC>, NAME##_mass<DC>, NAME##_gluons<DC>>(                                \
+      #NAME, 1 << NG,                                                                               \
+      [](const double* p, auto& ev) { NAME##_event_phase1(p, ev, 0, 1); NAME##_event_phase2(ev, 173.0 * 173.0, 0, 1); }, \
+      [](auto& ev, double m, double w, auto& mm) { NAME##_mass_setup<DC, false>(ev, m, w, DC(0.0), mm, 0, 1); }, \
+      [](auto& ev, auto& eps, auto& J) { NAME##_gluon_currents(ev, eps, J); },                       \
+      [](auto& ev, auto& mm, auto& J) { return NAME##_quark_line<DC, DC, false, DC>(ev, mm, J); })
+
 int main() {
   std::printf("{\n");
+  REX_COUNT_DF(gg_ttx, 2);
+  REX_COUNT_DF(gg_ttxg, 3);
   REX_COUNT(gg_ttx, 2, false);
   REX_COUNT(gg_ttxg, 3, false);
   REX_COUNT(gg_ttxgg, 4, false);

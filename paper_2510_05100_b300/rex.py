@@ -30,6 +30,7 @@ REX_ENOMEM = -4
 REX_EUNSUPPORTED = -5
 FP64 = 0
 MIXED = 1
+DF64 = 2          # double-float amplitudes (gg_ttx, gg_ttxg)
 FLAG_NO_DEDUPE = 1
 MULTI_PERSISTENT = 0
 MULTI_STREAMS = 1

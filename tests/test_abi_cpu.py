@@ -50,6 +50,12 @@ def test_init_errors(rex):
     assert lib.rex_init_process(None, 0, ctypes.byref(h)) == rex.REX_EINVAL
     assert lib.rex_init_process(b"gg_ttxg", 0, None) == rex.REX_EINVAL
     assert lib.rex_init_process(b"ee_mumu", rex.MIXED, ctypes.byref(h)) == rex.REX_EUNSUPPORTED
+    for name in (b"gg_ttxgg", b"qq_ttx", b"qq_ttxg", b"qg_ttxq", b"ee_mumu"):   # double-float: g g -> t t~ (g)
+        assert lib.rex_init_process(name, rex.DF64, ctypes.byref(h)) == rex.REX_EUNSUPPORTED
+    for name in ("gg_ttx", "gg_ttxg"):
+        p = rex.Process(name, rex.DF64)
+        assert p.num_variants == 1 and p.variant == 0
+        p.close()
 
 
 @pytest.mark.parametrize("name,npart", [("ee_mumu", 4), ("gg_ttx", 4), ("gg_ttxg", 5), ("gg_ttxgg", 6), ("qq_ttx", 4), ("qq_ttxg", 5),

@@ -1,0 +1,123 @@
+"""REX_DF64 (double-float amplitudes on the FP32 pipe) against the FP64 oracle, through
+the C ABI (needs a B300).
+
+Tolerance: the exact mode's, 1e-12 relative per weight, with the exact mode's rule for
+an ill-conditioned (event, point): err <= 64 eps_df (kappa_0 + kappa_j), eps_df = 2^-48
+the double-float unit roundoff and kappa the oracle's condition estimate.
+"""
+import numpy as np
+import pytest
+
+from rexlib import ensure_built
+from oracle import reweight as oracle_rw
+from paper_2510_05100_b300 import phase_space as ps
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-12
+EPS_DF = 2.0 ** -48
+ORIG = dict(mt=173.0, wt=0.0, alphas=0.118)
+SIZES = {"gg_ttx": 101, "gg_ttxg": 53}        # several tiles and a ragged tail
+NGLUON = {"gg_ttx": 2, "gg_ttxg": 3}
+
+
+@pytest.fixture(scope="module")
+def rex():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return ensure_built()
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def make(rex, proc, precision=2):
+    p = rex.Process(proc, precision)
+    p.set_params(ORIG)
+    return p
+
+
+def rel(a, b):
+    return np.abs(a / b - 1.0)
+
+
+def points(proc):
+    grid = ps.grid_gg_ttx() if proc == "gg_ttx" else ps.grid_gg_ttxg()
+    return grid + [dict(mt=172.0, wt=1.4, alphas=0.121)]      # a width: the complex-propagator kernel
+
+
+@pytest.mark.parametrize("proc", ["gg_ttx", "gg_ttxg"])
+def test_me2_and_reweight_parity(rex, proc):
+    n = SIZES[proc]
+    mom = ps.make_events(proc, n, 601)
+    w = np.random.default_rng(9).uniform(0.5, 2.0, n)
+    p = make(rex, proc)
+    assert p.num_variants == 1 and p.variant == 0
+    for pt in (ORIG, points(proc)[3], points(proc)[-1]):
+        got = p.me2(dev(mom), pt).cpu().numpy()
+        assert np.max(rel(got, oracle_rw.me2(proc, mom, pt))) < TOL, pt
+    pts = points(proc)
+    got = p.reweight(dev(mom), dev(w), pts).cpu().numpy()
+    ref = oracle_rw.reweight(proc, mom, w, ORIG, pts)
+    assert np.max(rel(got, ref)) < TOL
+    p.close()
+
+
+@pytest.mark.parametrize("proc", ["gg_ttx", "gg_ttxg"])
+def test_unchanged_point_and_alphas_scaling(rex, proc):
+    """An unchanged point returns the input weight bit for bit; a point that changes
+    alpha_s alone scales by (alpha_s'/alpha_s)^n."""
+    n = SIZES[proc]
+    mom = ps.make_events(proc, n, 602)
+    w = np.random.default_rng(10).uniform(0.5, 2.0, n)
+    p = make(rex, proc)
+    got = p.reweight(dev(mom), dev(w), [ORIG, dict(mt=173.0, wt=0.0, alphas=0.124)]).cpu().numpy()
+    assert np.array_equal(got[:, 0], w)
+    assert np.allclose(got[:, 1] / w, (0.124 / 0.118) ** NGLUON[proc], rtol=1e-14, atol=0)
+    p.close()
+
+
+def test_full_size_headline_against_fp64(rex):
+    """The headline workload (2^20 g g -> t t~ g events x 16 points, seed 3) in REX_DF64
+    against the FP64 kernel at every event and the oracle on sampled events.  An
+    (event, point) beyond 1e-12 of the FP64 kernel must meet the conditioning rule with
+    the oracle's kappa; at most 1e-4 of the events may need it."""
+    from oracle import qcd
+    n = 1 << 20
+    mom = ps.make_events("gg_ttxg", n, 3)
+    w = np.ones(n)
+    pts = ps.grid_gg_ttxg()
+    dm, dw = dev(mom), dev(w)
+    df = make(rex, "gg_ttxg").reweight(dm, dw, pts).cpu().numpy()
+    fp = make(rex, "gg_ttxg", 0).reweight(dm, dw, pts).cpu().numpy()
+    assert np.all(np.isfinite(df)) and np.all(df > 0)
+    idx = np.concatenate([np.random.default_rng(11).choice(n, 22, replace=False), [0, n - 1]])
+    ref = oracle_rw.reweight("gg_ttxg", mom[idx], w[idx], ORIG, pts)
+    assert np.max(rel(df[idx], ref)) < TOL
+    err = rel(df, fp)
+    far = np.nonzero(np.any(err > TOL, axis=1))[0]
+    assert len(far) <= n // 10000, len(far)
+    for i in far:
+        k0 = qcd.condition(mom[i:i + 1], ORIG["mt"], 0.0, ORIG["alphas"])[0]
+        for j in np.nonzero(err[i] > TOL)[0]:
+            kj = qcd.condition(mom[i:i + 1], pts[j]["mt"], 0.0, pts[j]["alphas"])[0]
+            assert err[i, j] <= 64 * EPS_DF * (k0 + kj), (i, j, err[i, j], k0, kj)
+
+
+def test_df64_scope(rex):
+    """Built for gg_ttx and gg_ttxg, helicity-summed, outside the persistent kernels."""
+    for proc in ("gg_ttxgg", "qq_ttx", "qq_ttxg", "ee_mumu"):
+        with pytest.raises(rex.RexError) as err:
+            rex.Process(proc, rex.DF64)
+        assert err.value.code == rex.REX_EUNSUPPORTED
+    p = make(rex, "gg_ttxg")
+    mom = dev(ps.make_events("gg_ttxg", 4, 1))
+    with pytest.raises(rex.RexError) as err:
+        p.reweight_helicity(mom, dev(np.ones((4, 5), dtype=np.int8)), dev(np.ones(4)), [ORIG])
+    assert err.value.code == rex.REX_EUNSUPPORTED
+    with pytest.raises(rex.RexError) as err:
+        rex.Multi(rex.DF64)
+    assert err.value.code == rex.REX_EUNSUPPORTED
+    p.close()
