@@ -25,7 +25,7 @@ GRIDS = {"gg_ttx": ps.grid_gg_ttx, "gg_ttxg": ps.grid_gg_ttxg, "gg_ttxgg": ps.gr
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--proc", default="gg_ttxg")
-    ap.add_argument("--mode", choices=["fp64", "mixed"], default="fp64")
+    ap.add_argument("--mode", choices=["fp64", "mixed", "df64"], default="fp64")
     ap.add_argument("--nev", type=int, default=1 << 19)
     ap.add_argument("--launches", type=int, default=2)
     ap.add_argument("--variant", type=int, default=None, help="kernel thread-mapping variant (g g processes)")
@@ -61,7 +61,7 @@ def main():
     mom = torch.from_numpy(ps.make_events(a.proc, a.nev, 3)).cuda()
     w = torch.ones(a.nev, dtype=torch.float64, device="cuda")
     pts = GRIDS[a.proc]()
-    p = rex.Process(a.proc, rex.FP64 if a.mode == "fp64" else rex.MIXED)
+    p = rex.Process(a.proc, {"fp64": rex.FP64, "mixed": rex.MIXED, "df64": rex.DF64}[a.mode])
     p.set_params(mt=173.0, wt=0.0, alphas=0.118)
     if a.variant is not None:
         p.variant = a.variant
