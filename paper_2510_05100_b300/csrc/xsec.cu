@@ -7,11 +7,12 @@
 // deviation; the mean of w'/w runs over events with w_i != 0.
 //
 // The statistics are accumulated over any number of calls (a sample split over
-// several processes or batches) in FP64 and in a fixed order, so that the result
-// does not depend on how the GPU schedules the blocks:
+// several processes or batches) in a fixed order, so that the result does not
+// depend on how the GPU schedules the blocks:
 //   pass 1  block b of the grid reduces events [b E, (b+1) E): each thread keeps
 //           shifted sums (first value K: S = sum (x - K), SS = sum (x - K)^2) of
-//           its events for one point, turned into (n, mean, M2, sum = n K + S);
+//           its events for one point, in double-float (FP64 for a block whose values
+//           leave its range), turned into (n, mean, M2, sum = n K + S) in FP64;
 //           the threads of a point merge in a fixed order (Chan, Golub & LeVeque 1979);
 //   pass 2  one block per point merges the blocks' partials with a fixed-shape
 //           tree, then into the accumulator;
@@ -27,6 +28,8 @@
 
 #include "../../include/rex.h"
 #include "dev_alloc.h"
+#include "df64.cuh"
+#include "fpconv.cuh"
 
 namespace {
 
@@ -66,51 +69,181 @@ int xfail(int code, const char* fmt, ...) {
   return code;
 }
 
-// pass 1: partial moments of events [bx E, bx E + E) for the points of column
-// group by.  A warp takes 32 events at a time: each lane loads one event's w and
-// forms its reciprocal (one warp-wide FP64 division per 32 events), then the
-// warp walks the 32 events G = 32 / kw at a time, lane L on event L / kw and
-// point by kw + L % kw (kw = lanes per event: the next power of two >= k, at
-// most 32), so that every lane has work when k < 32.
-__global__ void __launch_bounds__(XS_TJ* XS_TE) xsec_partials_kernel(const double* __restrict__ w_in,
+// Per-thread sums of pass 1 for point j: the count, the first value K, S = sum (x - K),
+// SS = sum (x - K)^2 and r = sum x / w over the events with w != 0; the block's
+// scalars (events with w != 0, sum of w) come from the threads of column group 0.
+struct ThreadSums {
+  int cnt;
+  bool wide;   // a value outside the double-float range (DF only)
+  double K, S, SS, r, nr, sw;
+};
+
+// Bit-field helpers on the two 32-bit halves of an FP64 value (32-bit integer
+// instructions only).
+// The biased exponent (0 for zero and subnormals).
+__device__ __forceinline__ int exponent_of(double x) { return (__double2hiint(x) >> 20) & 0x7ff; }
+
+__device__ __forceinline__ bool is_zero(double x) {
+  return (((unsigned)__double2hiint(x) << 1) | (unsigned)__double2loint(x)) == 0u;
+}
+
+// x / 2^e for a normal x whose result stays normal: the exponent field minus e.
+__device__ __forceinline__ double scale_down(double x, int e) {
+  return __hiloint2double(__double2hiint(x) - (e << 20), __double2loint(x));
+}
+
+// An integer |n| < 2^22 as FP32 without a conversion instruction (B300 runs those at
+// the FP64 rate): n added to the bit pattern of 2^23 + 2^22, then that offset removed.
+__device__ __forceinline__ float small_int_to_float(int n) {
+  return __fsub_rn(__int_as_float(0x4B400000 + n), 12582912.0f);
+}
+
+// FP64 -> double-float without an FP64 or conversion instruction, for a normal x with a
+// binary exponent in [-60, 60]: hi keeps the 24 leading significand bits (rounded half
+// up), lo the remaining 29 as a signed integer, assembled in FP32 from its upper 22 and
+// lower 7 bits and scaled by powers of two; hi + lo equals x to 2^-53 |x|.
+__device__ __forceinline__ rex::df64 split_df(double x) {
+  const unsigned h = (unsigned)__double2hiint(x), l = (unsigned)__double2loint(x);
+  const unsigned sign = h & 0x80000000u;
+  const int e = (int)((h >> 20) & 0x7ffu) - 1023;
+  unsigned top = (((h & 0xfffffu) | 0x100000u) << 3) | (l >> 29);   // 2^23 <= top < 2^24
+  int rem = (int)(l & 0x1fffffffu);                                  // the 29 bits below
+  if (rem >= (1 << 28)) {
+    ++top;
+    rem -= 1 << 29;
+  }
+  const int eh = top == (1u << 24) ? e + 1 : e;        // rounding carried into the exponent
+  const float hi = __uint_as_float(sign | ((unsigned)(eh + 127) << 23) | (top & 0x7fffffu));
+  const float lo = __fmaf_rn(small_int_to_float(rem >> 7), __uint_as_float((unsigned)(e - 45 + 127) << 23),
+                             __fmul_rn(small_int_to_float(rem & 127), __uint_as_float((unsigned)(e - 52 + 127) << 23)));
+  return rex::df64_make(hi, sign ? -lo : lo);
+}
+
+__device__ __forceinline__ double df_to_double(rex::df64 v) {
+  return rex::f32_to_f64_alu(v.hi) + rex::f32_to_f64_alu(v.lo);
+}
+
+// pass 1 of one thread.  A warp takes 32 events at a time: each lane loads one event's
+// w and forms its reciprocal (one per event), then the warp walks the 32 events
+// G = 32 / kw at a time, lane L on event L / kw and point by kw + L % kw (kw = lanes per
+// event: the next power of two >= k, at most 32), so that every lane has work when
+// k < 32.
+// DF: the sums and the reciprocal in double-float on the FP32 pipe (B300 issues FP64,
+// conversions included, at 1/64 of the FP32 rate), each value first scaled by 2^-e0
+// (e0: the exponent of the thread's first value; an exact power-of-two scaling undone
+// at the end) and split into two FP32 numbers with integer instructions.  A value
+// further than 2^40 from that scale, a w outside [2^-60, 2^60], a subnormal, an
+// infinity or a NaN is beyond what the FP32 exponent range carries for the sums and
+// squares: the result is then flagged (wide), and the caller recomputes the whole block
+// in FP64 (in the same order, so the result stays bitwise reproducible).
+template <bool DF>
+__device__ __forceinline__ ThreadSums thread_sums(const double* __restrict__ w_in, const double* __restrict__ w_out,
+                                                  int64_t e_beg, int64_t e_end, int k, int kw, int j) {
+  const int lane = threadIdx.x, te = threadIdx.y;
+  const int G = XS_TJ / kw;                      // events per warp step
+  const int sub = lane / kw;
+  int cnt = 0;                                   // integer count: keeps the FP64 pipe for the sums
+  double K = 0.0, S = 0.0, SS = 0.0, r = 0.0;
+  int nnz = 0;                                   // events with w != 0 (column group 0)
+  double sw = 0.0;
+  rex::df64 Kd = rex::df64_make(0.f, 0.f), Sd = Kd, SSd = Kd, rd = Kd;
+  int e0 = 0;                                    // DF: the scale exponent (unbiased)
+  bool out_of_range = false;
+  if constexpr (DF) {
+    // the thread's first value (event e_beg + 32 te + sub): K, its scale and its split
+    const int64_t e_first = e_beg + (int64_t)te * XS_TJ + sub;
+    if (e_first < e_end && j < k) {
+      K = w_out[e_first * k + j];
+      const int ek = exponent_of(K);
+      if (ek == 0x7ff || (ek == 0 && !is_zero(K))) out_of_range = true;
+      else if (!is_zero(K)) {
+        e0 = ek - 1023;
+        Kd = split_df(scale_down(K, e0));
+      }
+    }
+  }
+  for (int64_t g0 = e_beg + (int64_t)te * XS_TJ; g0 < e_end; g0 += (int64_t)XS_TE * XS_TJ) {
+    const int64_t el = g0 + lane;
+    const double wl = el < e_end ? w_in[el] : 0.0;
+    double il = 0.0;
+    if constexpr (!DF) il = wl != 0.0 ? 1.0 / wl : 0.0;
+    if (blockIdx.y == 0 && el < e_end) {
+      nnz += is_zero(wl) ? 0 : 1;
+      sw += wl;
+    }
+    rex::df64 ild = rex::df64_make(0.f, 0.f);
+    if constexpr (DF) {
+      // 1 / w in double-float (no FP64 division): w within [2^-60, 2^60] or zero
+      const int ew = exponent_of(wl);
+      if (!is_zero(wl)) {
+        if (ew < 1023 - 60 || ew >= 1023 + 60) out_of_range = true;
+        else ild = rex::df64(1) / split_df(wl);
+      }
+    }
+    for (int s = 0; s < XS_TJ; s += G) {
+      const int src = s + sub;                     // event of this lane within the 32
+      const double w = __shfl_sync(0xffffffffu, wl, src);
+      const int64_t e = g0 + src;
+      if constexpr (DF) {
+        const rex::df64 inv = rex::df64_make(__shfl_sync(0xffffffffu, ild.hi, src),
+                                             __shfl_sync(0xffffffffu, ild.lo, src));
+        if (e < e_end && j < k) {
+          const double x = w_out[e * k + j];
+          const int ex = exponent_of(x);
+          rex::df64 xd = rex::df64_make(0.f, 0.f);
+          if (!is_zero(x)) {
+            if (ex == 0 || ex == 0x7ff || ex - 1023 - e0 < -40 || ex - 1023 - e0 >= 40) out_of_range = true;
+            else xd = split_df(scale_down(x, e0));
+          }
+          const rex::df64 d = xd - Kd;
+          Sd = Sd + d;
+          SSd = fma(d, d, SSd);
+          if (!is_zero(w)) rd = fma(xd, inv, rd);      // w != 0 (either sign of zero)
+          ++cnt;
+        }
+      } else {
+        const double inv = __shfl_sync(0xffffffffu, il, src);
+        if (e < e_end && j < k) {
+          const double x = w_out[e * k + j];
+          if (cnt == 0) K = x;
+          const double d = x - K;
+          S += d;
+          SS = fma(d, d, SS);
+          if (__double_as_longlong(w) << 1) r = fma(x, inv, r);
+          ++cnt;
+        }
+      }
+    }
+  }
+  if constexpr (DF) {
+    const double p2 = __longlong_as_double((long long)(e0 + 1023) << 52);   // 2^e0, e0 of a normal K
+    S = df_to_double(Sd) * p2;
+    SS = df_to_double(SSd) * p2 * p2;
+    r = df_to_double(rd) * p2;
+  }
+  return ThreadSums{cnt, out_of_range, K, S, SS, r, (double)nnz, sw};
+}
+
+// pass 1: partial moments of events [bx E, bx E + E) for the points of column group
+// by, from the threads' sums in double-float, or in FP64 for a block with a value
+// outside the double-float range (see thread_sums).  The Chan-Golub-LeVeque merges of
+// the threads' moments and everything after them stay FP64.
+__global__ void __launch_bounds__(XS_TJ* XS_TE, 2) xsec_partials_kernel(const double* __restrict__ w_in,
                                                                      const double* __restrict__ w_out, int64_t nev,
                                                                      int k, int kw, Moments* __restrict__ part,
                                                                      Scalars* __restrict__ psc) {
   __shared__ Moments sm[XS_TE][XS_TJ];
   __shared__ Scalars ssc[XS_TE][XS_TJ];
   const int lane = threadIdx.x, te = threadIdx.y;
-  const int G = XS_TJ / kw;                      // events per warp step
+  const int G = XS_TJ / kw;
   const int sub = lane / kw, jl = lane - sub * kw;
   const int j = blockIdx.y * kw + jl;
   const int64_t e_beg = (int64_t)blockIdx.x * XS_EB;
   const int64_t e_end = (e_beg + XS_EB < nev) ? e_beg + XS_EB : nev;
-  int cnt = 0;                                   // integer count: keeps the FP64 pipe for the sums
-  double K = 0.0, S = 0.0, SS = 0.0, r = 0.0;
-  double nr = 0.0, sw = 0.0;
-  for (int64_t g0 = e_beg + (int64_t)te * XS_TJ; g0 < e_end; g0 += (int64_t)XS_TE * XS_TJ) {
-    const int64_t el = g0 + lane;
-    const double wl = el < e_end ? w_in[el] : 0.0;
-    const double il = wl != 0.0 ? 1.0 / wl : 0.0;
-    if (blockIdx.y == 0 && el < e_end) {
-      nr += (wl != 0.0) ? 1.0 : 0.0;
-      sw += wl;
-    }
-    for (int s = 0; s < XS_TJ; s += G) {
-      const int src = s + sub;                     // event of this lane within the 32
-      const double w = __shfl_sync(0xffffffffu, wl, src);
-      const double inv = __shfl_sync(0xffffffffu, il, src);
-      const int64_t e = g0 + src;
-      if (e < e_end && j < k) {
-        const double x = w_out[e * k + j];
-        if (cnt == 0) K = x;
-        const double d = x - K;
-        S += d;
-        SS = fma(d, d, SS);
-        if (__double_as_longlong(w) << 1) r = fma(x, inv, r);   // w != 0 (either sign of zero)
-        ++cnt;
-      }
-    }
-  }
+  ThreadSums ts = thread_sums<true>(w_in, w_out, e_beg, e_end, k, kw, j);
+  if (__syncthreads_or(ts.wide)) ts = thread_sums<false>(w_in, w_out, e_beg, e_end, k, kw, j);
+  const int cnt = ts.cnt;
+  const double K = ts.K, S = ts.S, SS = ts.SS, r = ts.r, nr = ts.nr, sw = ts.sw;
   Moments m;
   m.n = (double)cnt;
   m.mean = cnt > 0 ? K + S / m.n : 0.0;

@@ -141,3 +141,29 @@ def test_state_round_trip_and_merge_of_two_accumulators(rex):
     assert np.array_equal(a.get_state(), sa)
     for x in (a, b, c):
         x.close()
+
+
+@pytest.mark.parametrize("scale", [1e-250, 1e-30, 1e30, 1e250])
+def test_uniformly_scaled_weights(rex, scale):
+    """The double-float sums scale each thread's values by a power of two near its first
+    value, so weights of any common magnitude keep the exact mode's tolerance."""
+    w, wn = sample(20000, 8, 12)
+    s, ds, fb = run(rex, w, wn * scale, 1.0, 0.1)
+    rs, rds, rfb = oracle_xsec.reweighted_xsec(w, wn * scale, 1.0, 0.1)
+    assert np.array_equal(fb, rfb)
+    assert np.max(rel(s, rs)) < TOL and np.max(rel(ds, rds)) < TOL
+
+
+def test_values_beyond_the_double_float_range_take_the_fp64_path(rex):
+    """Blocks holding a value further than 2^40 from its thread's scale, a subnormal or
+    a tiny input weight are summed in FP64 instead (same tolerance); the others stay in
+    double-float."""
+    w, wn = sample(9000, 6, 13, zeros=False)
+    wn[5, 2] *= 1e20               # 2^66 above its neighbours
+    wn[2100, 0] = 1e-310           # subnormal
+    w[4500] = 1e-30                # reciprocal beyond 2^60
+    wn[4500] *= 1e-30
+    s, ds, fb = run(rex, w, wn, 1.0, 0.1)
+    rs, rds, rfb = oracle_xsec.reweighted_xsec(w, wn, 1.0, 0.1)
+    assert np.array_equal(fb, rfb)
+    assert np.max(rel(s, rs)) < TOL and np.max(rel(ds, rds)) < TOL
