@@ -66,8 +66,9 @@ using AC = Cnt<1>;    // colour / helicity accumulation
 
 // Double-float (REX_DF64) cost of each operation in FP32 flops as df64.cuh performs
 // them (an FMA counts two, a division or square root one): sum 10, product 10,
-// fused multiply-add 18, quotient 25, square root 12, reciprocal square root 37;
-// sign flips, comparisons and FP64 -> double-float conversions cost none.
+// fused multiply-add 18, quotient 25, square root 12, reciprocal square root 37, and
+// slash_acc 404, ubar_dot 246, vvv_acc 501 and vvvv_acc 381 (below); sign flips, comparisons and
+// FP64 -> double-float conversions cost none.
 struct DC {
   static long long flops;
   double v;
@@ -90,6 +91,54 @@ inline bool operator<=(DC a, DC b) { return a.v <= b.v; }
 inline DC fma(DC a, DC b, DC c) { DC::flops += 18; return DC(a.v * b.v + c.v); }
 inline DC sqrt(DC a) { DC::flops += 12; return DC(std::sqrt(a.v)); }
 inline DC rsqrt(DC a) { DC::flops += 37; return DC(1.0 / std::sqrt(a.v)); }
+
+#include "../helas.cuh"
+
+// df64.cuh's slash_acc for double-float values (s = +-1 as a sign, three products per
+// output component each added with one TwoSum, one renormalisation per component):
+// two double-float sums (20) + 24 products x 15 + 8 renormalisations x 3 = 404 FP32 flops
+inline void slash_acc(DC s, const DC* a, const rex::cx<DC>* psi, rex::cx<DC>* out) {
+  const long long keep = DC::flops;
+  const double am = s.v * (a[0].v - a[3].v), ap = s.v * (a[0].v + a[3].v), a1 = s.v * a[1].v, a2 = s.v * a[2].v;
+  out[0].re.v += am * psi[2].re.v - a1 * psi[3].re.v - a2 * psi[3].im.v;
+  out[0].im.v += am * psi[2].im.v - a1 * psi[3].im.v + a2 * psi[3].re.v;
+  out[1].re.v += ap * psi[3].re.v - a1 * psi[2].re.v + a2 * psi[2].im.v;
+  out[1].im.v += ap * psi[3].im.v - a1 * psi[2].im.v - a2 * psi[2].re.v;
+  out[2].re.v += ap * psi[0].re.v + a1 * psi[1].re.v + a2 * psi[1].im.v;
+  out[2].im.v += ap * psi[0].im.v + a1 * psi[1].im.v - a2 * psi[1].re.v;
+  out[3].re.v += am * psi[1].re.v + a1 * psi[0].re.v - a2 * psi[0].im.v;
+  out[3].im.v += am * psi[1].im.v + a1 * psi[0].im.v + a2 * psi[0].re.v;
+  DC::flops = keep + 404;
+}
+
+// df64.cuh's closure and vertex helpers for double-float values (products summed with
+// one TwoSum each and one renormalisation per sum; s = +-1 as a sign; 2x exact):
+// ubar_dot two eight-product sums = 246; vvv_acc 8 sums (80) + 3 Minkowski products
+// (3 x 63) + 4 differences (40) + 4 three-product accumulations (4 x 48) = 501;
+// vvvv_acc 3 x 63 + 4 x 48 = 381.
+inline rex::cx<DC> ubar_dot(const rex::cx<DC>* u, const rex::cx<DC>* x) {
+  const long long keep = DC::flops;
+  const rex::cx<DC> r = rex::cdot1(u[0], x[2]) + rex::cdot1(u[1], x[3]) + rex::cdot1(u[2], x[0]) + rex::cdot1(u[3], x[1]);
+  DC::flops = keep + 246;
+  return r;
+}
+inline void vvv_acc(DC s, const DC* jx, const DC* px, const DC* jy, const DC* py, DC* out) {
+  const long long keep = DC::flops;
+  DC a[4], b[4];
+  for (int m = 0; m < 4; ++m) {
+    a[m] = px[m] + DC(2.0) * py[m];
+    b[m] = DC(2.0) * px[m] + py[m];
+  }
+  const DC xy = s * rex::mdot(jx, jy), xa = s * rex::mdot(jx, a), yb = s * rex::mdot(jy, b);
+  for (int m = 0; m < 4; ++m) out[m] = out[m] + xy * (py[m] - px[m]) - xa * jy[m] + yb * jx[m];
+  DC::flops = keep + 501;
+}
+inline void vvvv_acc(DC s, const DC* jx, const DC* jy, const DC* jz, DC* out) {
+  const long long keep = DC::flops;
+  const DC xy = s * rex::mdot(jx, jy), yz = s * rex::mdot(jy, jz), xz2 = DC(-2.0) * s * rex::mdot(jx, jz);
+  for (int m = 0; m < 4; ++m) out[m] = out[m] + xy * jz[m] + yz * jx[m] + xz2 * jy[m];
+  DC::flops = keep + 381;
+}
 
 #include "../generated/qcd_amplitudes.cuh"
 #include "../qq_amplitude.cuh"
