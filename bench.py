@@ -445,8 +445,8 @@ def run_small_multi_leg(dev, stream, steps, world, barrier, max_over_ranks):
 
 def run_qqg_leg(dev, stream, pts, steps, nev=NEV):
     """q q~ -> t t~ g (the quark-initiated p p -> t t~ + jet channel) on the headline's
-    points: nev events per launch in FP64 and mixed precision, CUDA-event timed, with the
-    roofline of each kernel against its arithmetic pipe (counted flops)."""
+    points: nev events per launch in FP64, mixed precision and double-float, CUDA-event
+    timed, with the roofline of each kernel against its arithmetic pipe (counted flops)."""
     import torch
     from paper_2510_05100_b300 import flops as flopmod
     from paper_2510_05100_b300 import rex
@@ -459,7 +459,9 @@ def run_qqg_leg(dev, stream, pts, steps, nev=NEV):
     p64 = SM_COUNT * FP64_FMA_PER_SM_CLK * 2 * SM_MAX_MHZ * 1e6
     out = {"workload": f"q q~ -> t t~ g, {nev} events x {k} points ({nmass} mass slots), the headline's grid",
            "flops_per_launch": fl}
-    for name, prec, peak, pipe in (("fp64", rex.FP64, p64, "FP64 FMA"), ("mixed", rex.MIXED, FP32_PEAK, "FP32 FMA")):
+    fl_df = flopmod.per_event("qq_ttxg_df64", nmass)["amp"] * nev   # FP32 flops of the double-float code
+    for name, prec, peak, pipe in (("fp64", rex.FP64, p64, "FP64 FMA"), ("mixed", rex.MIXED, FP32_PEAK, "FP32 FMA"),
+                                   ("double_float", rex.DF64, FP32_PEAK, "FP32 FMA (double-float operations)")):
         proc = rex.Process("qq_ttxg", prec)
         proc.set_params(ORIGINAL)
         for _ in range(3):
@@ -473,9 +475,10 @@ def run_qqg_leg(dev, stream, pts, steps, nev=NEV):
         torch.cuda.synchronize(dev)
         proc.close()
         t = statistics.mean(a.elapsed_time(b) for a, b in ev) * 1e-3
+        f = fl_df if prec == rex.DF64 else fl
         out[name] = {"value": nev * k / t, "unit": UNIT, "ms_per_launch": t * 1e3,
-                     "roofline": {"bound": "alu", "pipe": pipe, "achieved": fl / t / 1e12, "peak": peak / 1e12,
-                                  "unit": "TFLOP/s", "frac": fl / t / peak}}
+                     "roofline": {"bound": "alu", "pipe": pipe, "achieved": f / t / 1e12, "peak": peak / 1e12,
+                                  "unit": "TFLOP/s", "frac": f / t / peak}}
     return out
 
 

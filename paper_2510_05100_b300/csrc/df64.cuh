@@ -29,6 +29,7 @@
 namespace rex {
 
 // the FP32 and FP64 overloads stay visible beside the double-float ones below
+using ::abs;
 using ::fma;
 using ::rsqrt;
 using ::sqrt;
@@ -108,6 +109,8 @@ __device__ __forceinline__ bool operator>(df64 a, df64 b) { return a.hi > b.hi |
 __device__ __forceinline__ bool operator<(df64 a, df64 b) { return b > a; }
 __device__ __forceinline__ bool operator>=(df64 a, df64 b) { return !(a < b); }
 __device__ __forceinline__ bool operator<=(df64 a, df64 b) { return !(a > b); }
+__device__ __forceinline__ bool operator==(df64 a, df64 b) { return a.hi == b.hi && a.lo == b.lo; }
+__device__ __forceinline__ bool operator!=(df64 a, df64 b) { return !(a == b); }
 
 // out += sum of three products, each product's high part exact and added with one
 // TwoSum, the low parts gathered in c, one renormalisation at the end (12 operations
@@ -213,7 +216,13 @@ __device__ __forceinline__ void vvvv_acc(df64 s, const df64* jx, const df64* jy,
   for (int m = 0; m < 4; ++m) out[m] = df64_acc3(out[m], xy, jz[m], yz, jx[m], xz2, jy[m]);
 }
 
-// lane exchange of a warp (both parts)
+__device__ __forceinline__ df64 abs(df64 a) { return a.hi < 0.f ? -a : a; }
+
+// lane exchange of a warp: any shuffled type, and double-float values in both parts
+template <typename T>
+__device__ __forceinline__ T shfl_xor(T v, int off) {
+  return __shfl_xor_sync(0xffffffffu, v, off);
+}
 __device__ __forceinline__ df64 shfl_xor(df64 v, int off) {
   return df64_make(__shfl_xor_sync(0xffffffffu, v.hi, off), __shfl_xor_sync(0xffffffffu, v.lo, off));
 }

@@ -34,11 +34,6 @@
 
 namespace rex {
 
-// lane exchange of a warp (df64.cuh overloads it for double-float values)
-template <typename T>
-__device__ __forceinline__ T shfl_xor(T v, int off) {
-  return __shfl_xor_sync(0xffffffffu, v, off);
-}
 
 template <int PROC>
 struct QcdProc;

@@ -23,6 +23,7 @@
 
 #include <type_traits>
 
+#include "df64.cuh"
 #include "fpconv.cuh"
 #include "qqg_amplitude.cuh"
 #include "rex_internal.cuh"
@@ -177,15 +178,15 @@ struct QqgTile {
                                   sm.inv[7][el], L, sp);
         for (int s = 0; s < lp.nmass; ++s) {
           R part = valid ? qqg_slot_split<R>(L, sm.mr[s], sm.dm2[s], sm.mw[s], &sp) : R(0);
-          part += __shfl_xor_sync(0xffffffffu, part, 1);
-          part += __shfl_xor_sync(0xffffffffu, part, 2);
+          part += shfl_xor(part, 1);
+          part += shfl_xor(part, 2);
           if (lane == 0) sm.me2s[el][s] = double(part);
         }
       } else {
       for (int s = 0; s < lp.nmass; ++s) {
         R part = valid ? qqg_slot<R>(L, sm.mr[s], sm.dm2[s], sm.mw[s]) : R(0);
-        part += __shfl_xor_sync(0xffffffffu, part, 1);
-        part += __shfl_xor_sync(0xffffffffu, part, 2);
+        part += shfl_xor(part, 1);
+        part += shfl_xor(part, 2);
         if (lane == 0) sm.me2s[el][s] = double(part);
       }
       }
@@ -194,7 +195,7 @@ struct QqgTile {
     const int nblk = (int)((nev - ev0) < EPB ? (nev - ev0) : EPB);
     if (lp.mode == OUT_RATIO) {
       const int k = lp.k;
-      if constexpr (std::is_same<R, double>::value) {
+      if constexpr (!std::is_same<R, float>::value) {   // FP64 and double-float
         for (int idx = tid; idx < nblk * k; idx += QQG_BLOCK) {
           const int e = idx / k;
           const int j = idx - e * k;

@@ -166,8 +166,9 @@ int default_variant(int kind, int precision) {
 int launch_qcd(const rex_proc* p, const double* mom, const double* w_in, int64_t nev, const QcdLaunch& lp,
                double* out, void* stream, const signed char* hel) {
   const int mixed = p->precision == REX_MIXED;
-  if (p->precision == REX_DF64) {   // gg_ttx and gg_ttxg only (rex_init_process), never exclusive
+  if (p->precision == REX_DF64) {   // gg_ttx, gg_ttxg, qq_ttxg (rex_init_process), never exclusive
     if (hel) return (int)cudaErrorInvalidValue;
+    if (p->kind == PROC_QQ_TTXG) return launch_qq_ttxg_df64(mom, w_in, nev, lp, out, stream, p->cross);
     return p->kind == PROC_GG_TTX ? launch_gg_ttx_df64(mom, w_in, nev, lp, out, stream)
                                   : launch_gg_ttxg_df64(mom, w_in, nev, lp, out, stream);
   }
@@ -885,8 +886,8 @@ int rex_init_process(const char* name, int precision, rex_proc** out) {
   if (kind < 0) return fail(REX_EINVAL, "unknown process '%s'", name);
   if (kind == PROC_EE_MUMU && precision != REX_FP64)
     return fail(REX_EUNSUPPORTED, "ee_mumu is implemented in FP64 only");
-  if (precision == REX_DF64 && kind != PROC_GG_TTX && kind != PROC_GG_TTXG)
-    return fail(REX_EUNSUPPORTED, "REX_DF64 is built for gg_ttx and gg_ttxg");
+  if (precision == REX_DF64 && kind != PROC_GG_TTX && kind != PROC_GG_TTXG && kind != PROC_QQ_TTXG)
+    return fail(REX_EUNSUPPORTED, "REX_DF64 is built for gg_ttx, gg_ttxg, qq_ttxg and its crossings");
   rex_proc* p = new (std::nothrow) rex_proc;
   if (!p) return fail(REX_ENOMEM, "out of host memory");
   std::memset(p, 0, sizeof *p);

@@ -290,7 +290,23 @@ int main() {
     const long long f_slot = RC::flops;
     std::printf("  \"qq_ttxg\": {\"nghel\": 1, \"event_setup\": %lld, \"mass_setup\": %lld, "
                 "\"polarisations\": 0, \"gluon_currents\": 0, \"quark_line_amp\": 0, "
-                "\"quark_line_acc\": 0}\n", 4 * f_setup, 4 * f_slot);
+                "\"quark_line_acc\": 0},\n", 4 * f_setup, 4 * f_slot);
+    // the same lanes in double-float (FP32 flops)
+    DC pdc[5][4];
+    for (int i = 0; i < 5; ++i)
+      for (int m = 0; m < 4; ++m) pdc[i][m] = DC(pd[i][m]);
+    QqgInvariants<DC> invd{DC(1e-6), DC(1e-6), DC(-1e-4), DC(-1e-4), DC(100.0), DC(120.0)};
+    QqgLane<DC> Ld;
+    DC::flops = 0;
+    qqg_lane_setup<DC>(pdc, 0, 0, Ld);
+    qqg_lane_scale<DC>(invd, Ld);
+    const long long d_setup = DC::flops;
+    DC::flops = 0;
+    qqg_slot<DC>(Ld, DC(171.0), DC(700.0), DC(0.0));
+    const long long d_slot = DC::flops;
+    std::printf("  \"qq_ttxg_df64\": {\"nghel\": 1, \"event_setup\": %lld, \"mass_setup\": %lld, "
+                "\"polarisations\": 0, \"gluon_currents\": 0, \"quark_line_amp\": 0, "
+                "\"quark_line_acc\": 0}\n", 4 * d_setup, 4 * d_slot);
   }
   std::printf("}\n");
   return 0;

@@ -50,9 +50,9 @@ def test_init_errors(rex):
     assert lib.rex_init_process(None, 0, ctypes.byref(h)) == rex.REX_EINVAL
     assert lib.rex_init_process(b"gg_ttxg", 0, None) == rex.REX_EINVAL
     assert lib.rex_init_process(b"ee_mumu", rex.MIXED, ctypes.byref(h)) == rex.REX_EUNSUPPORTED
-    for name in (b"gg_ttxgg", b"qq_ttx", b"qq_ttxg", b"qg_ttxq", b"ee_mumu"):   # double-float: g g -> t t~ (g)
+    for name in (b"gg_ttxgg", b"qq_ttx", b"ee_mumu"):   # double-float: g g -> t t~ (g), q q~ -> t t~ g
         assert lib.rex_init_process(name, rex.DF64, ctypes.byref(h)) == rex.REX_EUNSUPPORTED
-    for name in ("gg_ttx", "gg_ttxg"):
+    for name in ("gg_ttx", "gg_ttxg", "qq_ttxg", "qg_ttxq"):
         p = rex.Process(name, rex.DF64)
         assert p.num_variants == 1 and p.variant == 0
         p.close()

@@ -106,9 +106,33 @@ def test_full_size_headline_against_fp64(rex):
             assert err[i, j] <= 64 * EPS_DF * (k0 + kj), (i, j, err[i, j], k0, kj)
 
 
+@pytest.mark.parametrize("proc", ["qq_ttxg", "qxq_ttxg", "qg_ttxq", "gq_ttxq", "qxg_ttxqx", "gqx_ttxqx"])
+def test_qq_ttxg_and_crossings_parity(rex, proc):
+    """q q~ -> t t~ g and its crossings (the crossed light lines on the t-channel tile)
+    in double-float against the oracle: 3 tiles of 32 and a ragged tail, a width point,
+    negative weights; an unchanged point keeps the weight bit for bit and an alpha_s
+    point scales by (alpha_s'/alpha_s)^3."""
+    n = 75
+    mom = ps.make_events(proc, n, 82)
+    p = make(rex, proc)
+    for pt in (ORIG, dict(mt=169.0, wt=1.0, alphas=0.125)):
+        got = p.me2(dev(mom), pt).cpu().numpy()
+        assert np.max(rel(got, oracle_rw.me2(proc, mom, pt))) < TOL, pt
+    w = np.random.default_rng(12).uniform(-1.0, 2.0, n)
+    pts = ps.grid_gg_ttxg() + [dict(mt=172.0, wt=1.4, alphas=0.118), ORIG, dict(mt=173.0, wt=0.0, alphas=0.124)]
+    got = p.reweight(dev(mom), dev(w), pts).cpu().numpy()
+    ref = oracle_rw.reweight(proc, mom, w, ORIG, pts)
+    assert np.max(np.abs(got - ref) / np.abs(ref)) < TOL
+    j = pts.index(ORIG)
+    assert np.array_equal(got[:, j], w)
+    assert np.max(rel(got[:, j + 1], w * (0.124 / 0.118) ** 3)) < 1e-14
+    p.close()
+
+
 def test_df64_scope(rex):
-    """Built for gg_ttx and gg_ttxg, helicity-summed, outside the persistent kernels."""
-    for proc in ("gg_ttxgg", "qq_ttx", "qq_ttxg", "ee_mumu"):
+    """Built for g g -> t t~ (g) and q q~ -> t t~ g with its crossings, helicity-summed,
+    outside the persistent kernels."""
+    for proc in ("gg_ttxgg", "qq_ttx", "ee_mumu"):
         with pytest.raises(rex.RexError) as err:
             rex.Process(proc, rex.DF64)
         assert err.value.code == rex.REX_EUNSUPPORTED
