@@ -30,6 +30,7 @@
 #include "colour_tc.cuh"
 #include "df64.cuh"
 #include "generated/qcd_amplitudes.cuh"
+#include "gg_ttxg_df64.cuh"
 #include "rex_internal.cuh"
 
 namespace rex {
@@ -165,6 +166,9 @@ struct QcdTile {
   static_assert(!EXCL || (SPLIT == 0 && !TC), "helicity-exclusive tiles: one lane per gluon configuration");
 
   static constexpr bool F32 = std::is_same<R, float>::value;
+  // double-float g g -> t t~ g: the quark line as loops (gg_ttxg_df64.cuh), reading the
+  // lane's gluon currents from shared memory
+  static constexpr bool DF_LOOP = std::is_same<R, df64>::value && PROC == PROC_GG_TTXG && !EXCL && !TC_REQ;
   struct Smem {
     double me2s[EPB][F32 ? 1 : MAX_MASS + 1];   // exact mode: the slot sums; mixed mode: w
     float me2f[F32 ? EPB : 1][MAX_MASS + 1];   // mixed mode: the FP32 slot sums
@@ -175,6 +179,7 @@ struct QcdTile {
     typename P::template event<R> evs[EPB];
     typename P::template mass<R> mss[EPB];
     alignas(16) __half tc[TC ? QCD_BLOCK / 32 : 1][TC ? ColourTc<NF>::WARP_HALVES : 1];
+    typename P::template gluons<R> js[DF_LOOP ? EPB : 1][DF_LOOP ? NGH : 1];
   };
 
   // Slot group [s_lo, s_hi) (the persistent kernel's split of a tile's mass slots over
@@ -217,6 +222,9 @@ struct QcdTile {
     for (int g = 0; g < NG; ++g) pol_linear(evd.pg[g], (gh >> g) & 1, eps[g]);
     typename P::template gluons<R> J;
     P::gluon_currents(evd, eps, J);
+    if constexpr (DF_LOOP) {
+      if (hb_lo == 0) sm.js[el][gh] = J;   // read after the slot loop's first barrier
+    }
 
     // a6 on tensor cores: the colour matrix as MMA B fragments in this warp's smem
     if constexpr (TC) ColourTc<NF>::load(P::colour(), sm.tc[tid >> 5]);
@@ -262,6 +270,10 @@ struct QcdTile {
         auto form = [&](const cx<float> (&A)[2][NF]) { return ColourTc<NF>::template form<NH>(A, tcs); };
         s = P::template quark_line<R, R, WIDTH>(evd, sm.mss[el], J, hb_lo, hb_hi, form);
         if (!valid) s = R(0);
+      } else if constexpr (DF_LOOP) {
+        if (valid)
+          s = gg_ttxg_quark_line_df64<WIDTH>(evd, sm.mss[el],
+                                             reinterpret_cast<const df64(*)[4]>(&sm.js[el][gh]), hb_lo, hb_hi);
       } else {
         if (valid) s = P::template quark_line<R, R, WIDTH>(evd, sm.mss[el], J, hb_lo, hb_hi);
       }
