@@ -444,14 +444,15 @@ static int launch_exclusive(const double* mom, const double* w_in, int64_t nev, 
                  : launch_exclusive<KIND, double>(mom, w_in, nev, lp, out, hel, st);                    \
   }
 
-// double-float amplitudes (REX_DF64, df64.cuh): one mapping per process at the
-// register allocator's own occupancy (255 registers, 8 warps per SM).  g g -> t t~ g
-// splits the antitop helicity over two lanes (half the live state: 488 B of spill
-// against 956 B; 162.7 against 167.3 ms for 2^20 x 16; 3 blocks per SM, at 168
-// registers, spill 1.8 KB and took 184 ms).
+// double-float amplitudes (REX_DF64, df64.cuh): one mapping, split 0 (one lane per
+// gluon configuration), at the register allocator's own occupancy (255 registers,
+// 8 warps per SM).  g g -> t t~ g runs the looped quark line (gg_ttxg_df64.cuh): 2^20 x
+// 16 in 72.9 ms unsplit, 83.2 ms with the antitop helicity split over two lanes (which
+// helped the straight-line form: 162.7 against 167.3 ms), 89.5 ms split at 3 blocks per
+// SM (168 registers), 106.4 ms at 4 (128 registers, 344 B of spill).
 template <int PROC>
 constexpr int df64_split() {
-  return PROC == PROC_GG_TTXG ? 1 : 0;
+  return 0;
 }
 
 template <int PROC>
