@@ -46,6 +46,11 @@ struct df64 {
   __device__ __forceinline__ explicit operator double() const { return (double)hi + (double)lo; }
 };
 
+template <>
+struct expensive_arith<df64> {
+  static constexpr bool value = true;
+};
+
 __device__ __forceinline__ df64 df64_make(float hi, float lo) {
   df64 r;
   r.hi = hi;

@@ -41,6 +41,14 @@ struct cx {
   R re, im;
 };
 
+// Amplitude types whose every operation expands to many instructions (double-float,
+// df64.cuh, specialises it): loops that are unrolled for FP32 and FP64 stay rolled for
+// them, so that the code fits the instruction caches.
+template <typename R>
+struct expensive_arith {
+  static constexpr bool value = false;
+};
+
 template <typename R>
 __device__ __forceinline__ cx<R> cmk(R a, R b) { return cx<R>{a, b}; }
 template <typename R>

@@ -302,7 +302,8 @@ __device__ __forceinline__ R qqg_slot(const QqgLane<R>& L, R mr, R dm2, R mw) {
   const cx<R> f3 = L.is * cx<R>{d3 * n3, -mw * n3}, f4 = L.is * cx<R>{d4 * n4, -mw * n4};
   const R f5 = L.is * L.isp;
   R sum = R(0);
-#pragma unroll
+  constexpr int UNROLL_HEL = expensive_arith<R>::value ? 1 : 2;   // the helicity loops
+#pragma unroll UNROLL_HEL
   for (int l4 = 0; l4 < 2; ++l4) {
     cx<R> t1[4], t2[4], t3[4], s1[4], s2[4], s3[4];
     // eps-slash (a3-slash + m) J_in-slash v4
@@ -317,7 +318,7 @@ __device__ __forceinline__ R qqg_slot(const QqgLane<R>& L, R mr, R dm2, R mw) {
     slash_acc(R(1), L.eps, v4[l4], s1);
     slash_plus_scalar(L.a4, mr, s1, s2);
     cslash(L.jin, s2, s3);
-#pragma unroll
+#pragma unroll UNROLL_HEL
     for (int l3 = 0; l3 < 2; ++l3) {
       cx<R> jout[4];
       dirac_current(u3[l3], v4[l4], jout);
