@@ -88,10 +88,9 @@ extern "C" {
  *            invariants and the weight ratio stay FP64.  Same 1e-12 bound as
  *            REX_FP64 against the FP64 oracle (a unit roundoff near 2^-48; the
  *            largest error measured over 10^4 (event, mass) values of
- *            g g -> t t~ g is 1.3e-13).  Built for gg_ttx, gg_ttxg and qq_ttxg
- *            (its crossed channels, q g and q~ g in either beam order, run the
- *            FP64 t-channel tile, which is faster there), one kernel variant,
- *            helicity-summed only; REX_EUNSUPPORTED elsewhere. */
+ *            g g -> t t~ g is 1.3e-13).  Built for gg_ttx, gg_ttxg, qq_ttxg and
+ *            its crossings, one kernel variant, helicity-summed only;
+ *            REX_EUNSUPPORTED elsewhere. */
 #define REX_FP64 0
 #define REX_MIXED 1
 #define REX_DF64 2

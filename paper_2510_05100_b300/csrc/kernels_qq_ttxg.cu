@@ -32,10 +32,9 @@ int launch_qq_ttxg(int mixed, const double* mom, const double* w_in, int64_t nev
   return (int)cudaGetLastError();
 }
 
-// REX_DF64, helicity-summed: the direct tile in double-float (2^20 x 16: 32.0 ms against
-// 57.0 ms in FP64); a crossed light line keeps the FP64 t-channel tile, whose
-// double-float form (the gauge split's per-lane state in shared memory) took 70.6 ms
-// against 62.3 ms, at an error within the same bound
+// REX_DF64, helicity-summed: the direct and the t-channel tile in double-float, their
+// helicity loops rolled (2^20 x 16: 20.5 ms against 57.0 ms in FP64; q g 35.4 ms against
+// 62.3 ms; unrolled they took 32.0 and 70.6 ms)
 int launch_qq_ttxg_df64(const double* mom, const double* w_in, int64_t nev, const QcdLaunch& lp, double* out,
                         void* stream, const QqgCrossing& cross) {
   constexpr int EPB = QqgTile<df64>::EPB;
@@ -44,7 +43,7 @@ int launch_qq_ttxg_df64(const double* mom, const double* w_in, int64_t nev, cons
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const unsigned g = (unsigned)blocks;
   if (cross.neg[0] != 0 || cross.neg[1] != 0)
-    qq_ttxg_reweight_kernel<double, 1, false, true><<<g, QQG_BLOCK, 0, st>>>(mom, w_in, nev, lp, out, nullptr, cross);
+    qq_ttxg_reweight_kernel<df64, 1, false, true><<<g, QQG_BLOCK, 0, st>>>(mom, w_in, nev, lp, out, nullptr, cross);
   else
     qq_ttxg_reweight_kernel<df64, 1, false><<<g, QQG_BLOCK, 0, st>>>(mom, w_in, nev, lp, out, nullptr, cross);
   return (int)cudaGetLastError();

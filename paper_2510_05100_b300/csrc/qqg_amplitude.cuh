@@ -357,7 +357,8 @@ __device__ __forceinline__ R qqg_slot_split(const QqgLane<R>& L, R mr, R dm2, R 
   // al d3 and al d4 at this mass, d = delta (1, -p-hat)
   const R del3 = sp->h3 + dm2 * sp->g3, del4 = sp->h4 + dm2 * sp->g4;
   R sum = R(0);
-#pragma unroll
+  constexpr int UNROLL_HEL = expensive_arith<R>::value ? 1 : 2;   // the helicity loops
+#pragma unroll UNROLL_HEL
   for (int l4 = 0; l4 < 2; ++l4) {
     cx<R> t1[4], t2[4], t3[4], s1[4], s2[4], s3[4];
     {  // eps-slash (a3-slash + m) (J' + al d4)-slash v4
@@ -381,7 +382,7 @@ __device__ __forceinline__ R qqg_slot_split(const QqgLane<R>& L, R mr, R dm2, R 
       for (int m = 0; m < 4; ++m) j3[m] = L.jin[m] + (del3 * sp->n3[m]) * sp->al;
       cslash(j3, s2, s3);
     }
-#pragma unroll
+#pragma unroll UNROLL_HEL
     for (int l3 = 0; l3 < 2; ++l3) {
       cx<R> jout[4];
       dirac_current(u3[l3], v4[l4], jout);
