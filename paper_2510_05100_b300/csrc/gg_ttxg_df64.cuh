@@ -45,11 +45,12 @@ __device__ __forceinline__ void gg_ttxg_df_prop(const gg_ttxg_event<df64>& ev, c
   else fermion_prop_real(ev.q[k], mm.m, mm.idr[k], t, out);
 }
 
-// J: the lane's nine gluon currents, [9][4], in shared memory.
-template <bool WIDTH>
+// J: the lane's nine gluon currents, [9][4], in shared memory.  FORM: the colour form
+// of a helicity-exclusive tile (qcd_kernel.cuh), or NoColourForm for the helicity sum.
+template <bool WIDTH, typename FORM = NoColourForm>
 __device__ __forceinline__ df64 gg_ttxg_quark_line_df64(const gg_ttxg_event<df64>& ev,
                                                         const gg_ttxg_mass<df64>& mm, const df64 (*J)[4],
-                                                        int hb_lo, int hb_hi) {
+                                                        int hb_lo, int hb_hi, const FORM& form = FORM()) {
   df64 total = df64(0);
 #pragma unroll 1
   for (int hb = hb_lo; hb < hb_hi; ++hb) {
@@ -80,6 +81,10 @@ __device__ __forceinline__ df64 gg_ttxg_quark_line_df64(const gg_ttxg_event<df64
         A[0][r.flow] = ubar_dot(mm.ut[0], x);
         A[1][r.flow] = ubar_dot(mm.ut[1], x);
       }
+    }
+    if constexpr (!std::is_same<FORM, NoColourForm>::value) {
+      total = total + form(A);
+      continue;
     }
 #pragma unroll
     for (int ht = 0; ht < 2; ++ht) {

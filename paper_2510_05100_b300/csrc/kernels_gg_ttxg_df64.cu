@@ -4,4 +4,9 @@
 
 namespace rex {
 REX_DEFINE_QCD_DF64_LAUNCHER(PROC_GG_TTXG, gg_ttxg)
+
+int launch_gg_ttxg_df64_exclusive(const double* mom, const double* w_in, int64_t nev, const QcdLaunch& lp,
+                                  double* out, void* stream, const signed char* hel) {
+  return launch_df64_exclusive_t<PROC_GG_TTXG>(mom, w_in, nev, lp, out, hel, static_cast<cudaStream_t>(stream));
+}
 }  // namespace rex

@@ -112,7 +112,7 @@ constexpr int QCD_BLOCK = 128;
 // FP64, 1e-11 in FP32; the smallest physical term seen is 1.2e-11 of it (g g -> t t~ g).
 template <typename R, int NF, int NGH, int NG>
 struct ExclusiveColourForm {
-  static constexpr double ZERO_TERM = std::is_same<R, double>::value ? 1e-13 : 1e-11;
+  static constexpr double ZERO_TERM = std::is_same<R, float>::value ? 1e-11 : 1e-13;
   cx<R> c;        // this lane's coefficient
   int ht;         // the event's top helicity (0: -, 1: +)
   bool lead;      // lane 0 of the event
@@ -126,11 +126,11 @@ struct ExclusiveColourForm {
     for (int f = 0; f < NF; ++f) J[f] = c * J[f];
 #pragma unroll
     for (int off = 1; off < NGH; off <<= 1) {
-      scale += __shfl_xor_sync(0xffffffffu, scale, off);
+      scale += shfl_xor(scale, off);
 #pragma unroll
       for (int f = 0; f < NF; ++f) {
-        J[f].re += __shfl_xor_sync(0xffffffffu, J[f].re, off);
-        J[f].im += __shfl_xor_sync(0xffffffffu, J[f].im, off);
+        J[f].re += shfl_xor(J[f].re, off);
+        J[f].im += shfl_xor(J[f].im, off);
       }
     }
     const R s = form(J) * (R(1) / R(1 << NG));
@@ -168,7 +168,7 @@ struct QcdTile {
   static constexpr bool F32 = std::is_same<R, float>::value;
   // double-float g g -> t t~ g: the quark line as loops (gg_ttxg_df64.cuh), reading the
   // lane's gluon currents from shared memory
-  static constexpr bool DF_LOOP = std::is_same<R, df64>::value && PROC == PROC_GG_TTXG && !EXCL && !TC_REQ;
+  static constexpr bool DF_LOOP = std::is_same<R, df64>::value && PROC == PROC_GG_TTXG && !TC_REQ;
   struct Smem {
     double me2s[EPB][F32 ? 1 : MAX_MASS + 1];   // exact mode: the slot sums; mixed mode: w
     float me2f[F32 ? EPB : 1][MAX_MASS + 1];   // mixed mode: the FP32 slot sums
@@ -258,7 +258,11 @@ struct QcdTile {
       // a7: the helicity sum adds non-negative terms (no cancellation): FP64 in the
       // exact mode, FP32 in the mixed mode (relative error <= 64 * 2^-24)
       R s = R(0);
-      if constexpr (EXCL) {
+      if constexpr (EXCL && DF_LOOP) {
+        s = gg_ttxg_quark_line_df64<WIDTH>(evd, sm.mss[el], reinterpret_cast<const df64(*)[4]>(&sm.js[el][gh]),
+                                           hb_x, hb_x + 1, xform);
+        if (!valid) s = R(0);
+      } else if constexpr (EXCL) {
         // every lane takes part in the event's shuffles; only the event's own antitop
         // helicity is evaluated
         s = P::template quark_line<R, R, WIDTH>(evd, sm.mss[el], J, hb_x, hb_x + 1, xform);
@@ -466,6 +470,20 @@ static int launch_df64_t(const double* mom, const double* w_in, int64_t nev, con
     qcd_reweight_kernel<PROC, df64, true, SPLIT, 1><<<(unsigned)blocks, QCD_BLOCK, 0, st>>>(mom, w_in, nev, lp, out);
   else
     qcd_reweight_kernel<PROC, df64, false, SPLIT, 1><<<(unsigned)blocks, QCD_BLOCK, 0, st>>>(mom, w_in, nev, lp, out);
+  return (int)cudaGetLastError();
+}
+
+// helicity-exclusive double-float tile (g g -> t t~ g: the looped quark line)
+template <int PROC>
+static int launch_df64_exclusive_t(const double* mom, const double* w_in, int64_t nev, const QcdLaunch& lp,
+                                   double* out, const signed char* hel, cudaStream_t st) {
+  constexpr int EPB = QCD_BLOCK / QcdProc<PROC>::info::NGHEL;
+  const int64_t blocks = (nev + EPB - 1) / EPB;
+  if (blocks > 0x7fffffffLL) return (int)cudaErrorInvalidValue;
+  if (lp.has_width)
+    qcd_exclusive_kernel<PROC, df64, true><<<(unsigned)blocks, QCD_BLOCK, 0, st>>>(mom, w_in, nev, lp, out, hel);
+  else
+    qcd_exclusive_kernel<PROC, df64, false><<<(unsigned)blocks, QCD_BLOCK, 0, st>>>(mom, w_in, nev, lp, out, hel);
   return (int)cudaGetLastError();
 }
 

@@ -166,8 +166,8 @@ int default_variant(int kind, int precision) {
 int launch_qcd(const rex_proc* p, const double* mom, const double* w_in, int64_t nev, const QcdLaunch& lp,
                double* out, void* stream, const signed char* hel) {
   const int mixed = p->precision == REX_MIXED;
-  if (p->precision == REX_DF64) {   // gg_ttx, gg_ttxg, qq_ttxg (rex_init_process), never exclusive
-    if (hel) return (int)cudaErrorInvalidValue;
+  if (p->precision == REX_DF64) {   // gg_ttx, gg_ttxg, qq_ttxg (rex_init_process); exclusive: gg_ttxg
+    if (hel) return launch_gg_ttxg_df64_exclusive(mom, w_in, nev, lp, out, stream, hel);
     if (p->kind == PROC_QQ_TTXG) return launch_qq_ttxg_df64(mom, w_in, nev, lp, out, stream, p->cross);
     return p->kind == PROC_GG_TTX ? launch_gg_ttx_df64(mom, w_in, nev, lp, out, stream)
                                   : launch_gg_ttxg_df64(mom, w_in, nev, lp, out, stream);
@@ -937,8 +937,8 @@ int rex_reweight_helicity(rex_proc* proc, const double* momenta, const signed ch
                           void* stream) {
   const int rc = validate_proc(proc);
   if (rc) return rc;
-  if (proc->precision == REX_DF64)
-    return fail(REX_EUNSUPPORTED, "helicity-exclusive reweighting is built in FP64 and mixed precision");
+  if (proc->precision == REX_DF64 && proc->kind != PROC_GG_TTXG)
+    return fail(REX_EUNSUPPORTED, "helicity-exclusive double-float reweighting is built for gg_ttxg");
   if (proc->kind == PROC_QQ_TTXG && !is_direct(proc->cross))
     return fail(REX_EUNSUPPORTED,
                 "helicity-exclusive reweighting of q q~ -> t t~ g is built for the direct channel only; its "

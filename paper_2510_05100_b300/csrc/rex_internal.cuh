@@ -127,6 +127,8 @@ int launch_gg_ttx_df64(const double* mom, const double* w_in, int64_t nev, const
                        void* stream);
 int launch_gg_ttxg_df64(const double* mom, const double* w_in, int64_t nev, const QcdLaunch& lp, double* out,
                         void* stream);
+int launch_gg_ttxg_df64_exclusive(const double* mom, const double* w_in, int64_t nev, const QcdLaunch& lp,
+                                  double* out, void* stream, const signed char* hel);
 int launch_qq_ttxg_df64(const double* mom, const double* w_in, int64_t nev, const QcdLaunch& lp, double* out,
                         void* stream, const QqgCrossing& cross);
 int launch_gg_ttx_exclusive(int mixed, const double* mom, const double* w_in, int64_t nev, const QcdLaunch& lp,

@@ -130,16 +130,16 @@ def test_qq_ttxg_and_crossings_parity(rex, proc):
 
 
 def test_df64_scope(rex):
-    """Built for g g -> t t~ (g) and q q~ -> t t~ g with its crossings, helicity-summed,
-    outside the persistent kernels."""
+    """Built for g g -> t t~ (g) and q q~ -> t t~ g with its crossings, helicity-summed
+    (helicity-exclusive for g g -> t t~ g), outside the persistent kernels."""
     for proc in ("gg_ttxgg", "qq_ttx", "ee_mumu"):
         with pytest.raises(rex.RexError) as err:
             rex.Process(proc, rex.DF64)
         assert err.value.code == rex.REX_EUNSUPPORTED
-    p = make(rex, "gg_ttxg")
-    mom = dev(ps.make_events("gg_ttxg", 4, 1))
+    p = make(rex, "gg_ttx")     # helicity-exclusive double-float: g g -> t t~ g only
+    mom = dev(ps.make_events("gg_ttx", 4, 1))
     with pytest.raises(rex.RexError) as err:
-        p.reweight_helicity(mom, dev(np.ones((4, 5), dtype=np.int8)), dev(np.ones(4)), [ORIG])
+        p.reweight_helicity(mom, dev(np.ones((4, 4), dtype=np.int8)), dev(np.ones(4)), [ORIG])
     assert err.value.code == rex.REX_EUNSUPPORTED
     with pytest.raises(rex.RexError) as err:
         rex.Multi(rex.DF64)

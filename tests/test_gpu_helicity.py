@@ -103,6 +103,7 @@ def extended_reference(proc, mom, hel, w, pts):
 
 @pytest.mark.parametrize("proc,precision,tol,n", [("gg_ttx", 0, 1e-12, 300), ("gg_ttx", 1, 1e-5, 300),
                                                   ("gg_ttxg", 0, 1e-12, 97), ("gg_ttxg", 1, 1e-3, 97),
+                                                  ("gg_ttxg", 2, 1e-12, 97),
                                                   ("gg_ttxgg", 0, 1e-12, 13), ("gg_ttxgg", 1, 1e-3, 13)])
 def test_gg_exclusive_parity(rex, proc, precision, tol, n):
     """g g -> t t~ (+ g, + g g): each event with a random configuration of all its
@@ -129,7 +130,7 @@ def test_gg_exclusive_parity(rex, proc, precision, tol, n):
         zero = np.asarray(frac, dtype=np.float64) < 1e-12
         assert np.any(zero)
     assert np.all(got[zero] == 0.0)
-    eps = np.finfo(np.float64 if precision == 0 else np.float32).eps / 2
+    eps = {0: np.finfo(np.float64).eps / 2, 1: np.finfo(np.float32).eps / 2, 2: 2.0 ** -48}[precision]
     bound = helicity_tolerance(proc, mom, hel, QCD_ORIG, pts, tol, eps)
     err = np.abs(got[~zero] / ref[~zero] - 1.0)
     assert np.all(err < bound[~zero]), (np.max(err), np.max(err / bound[~zero]))
