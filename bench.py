@@ -795,7 +795,7 @@ def run_helicity_leg(dev, stream, pts, steps, nev=NEV):
     p64 = SM_COUNT * FP64_FMA_PER_SM_CLK * 2 * SM_MAX_MHZ * 1e6
     out = {"workload": f"{PROC}, {nev} events x {k} points, each event with a random helicity configuration "
                        "(the headline's sample and grid)",
-           "stated_rel_error": {"fp64": 1e-12, "mixed": 1e-3}}
+           "stated_rel_error": {"fp64": 1e-12, "mixed": 1e-3, "double_float": 1e-12}}
 
     def timed(fn):
         for _ in range(2):
@@ -809,7 +809,7 @@ def run_helicity_leg(dev, stream, pts, steps, nev=NEV):
         torch.cuda.synchronize(dev)
         return statistics.mean(a.elapsed_time(b) for a, b in ev) * 1e-3
 
-    for name, prec in (("fp64", rex.FP64), ("mixed", rex.MIXED)):
+    for name, prec in (("fp64", rex.FP64), ("mixed", rex.MIXED), ("double_float", rex.DF64)):
         proc = rex.Process(PROC, prec)
         proc.set_params(ORIGINAL)
         t = timed(lambda: proc.reweight_helicity(mom, hel, w_in, pts, w_out=w_out, stream=stream))
@@ -818,6 +818,9 @@ def run_helicity_leg(dev, stream, pts, steps, nev=NEV):
         cnt = flopmod.per_event(PROC, nmass, exclusive=True)
         if prec == rex.FP64:
             fl, pk, pipe = cnt["total"] * nev, p64, "FP64 FMA"
+        elif prec == rex.DF64:
+            fl = flopmod.per_event(PROC + "_df64", nmass, exclusive=True)["amp"] * nev
+            pk, pipe = FP32_PEAK, "FP32 FMA (double-float operations; lane shuffles not counted)"
         else:
             fl, pk, pipe = cnt["amp"] * nev, FP32_PEAK, "FP32 FMA (amplitudes; FP64 invariants not counted)"
         out[name] = {"value": nev * k / t, "unit": UNIT, "ms_per_launch": t * 1e3,

@@ -89,8 +89,9 @@ extern "C" {
  *            REX_FP64 against the FP64 oracle (a unit roundoff near 2^-48; the
  *            largest error measured over 10^4 (event, mass) values of
  *            g g -> t t~ g is 1.3e-13).  Built for gg_ttx, gg_ttxg, qq_ttxg and
- *            its crossings, one kernel variant, helicity-summed only;
- *            REX_EUNSUPPORTED elsewhere. */
+ *            its crossings, one kernel variant, helicity-summed (and
+ *            helicity-exclusive for gg_ttxg); REX_EUNSUPPORTED elsewhere and in
+ *            the persistent entry points. */
 #define REX_FP64 0
 #define REX_MIXED 1
 #define REX_DF64 2
@@ -182,11 +183,12 @@ int rex_reweight(rex_proc *proc, const double *momenta, const double *w_in,
  * e_lambda = (e1 - i lambda e2)/sqrt(2) up to a phase, before the colour sum; only
  * the event's own top and antitop helicities are evaluated.  The crossings of
  * qq_ttxg use the helicity sum's freedom in their wavefunctions and return
- * REX_EUNSUPPORTED.
+ * REX_EUNSUPPORTED.  In REX_DF64 only gg_ttxg is built (REX_EUNSUPPORTED for the
+ * others).
  * Error against FP64 per weight: the helicity sum's bound of the mode (1e-12 in
  * REX_FP64, the process's REX_MIXED bound), or, for a term far below its event's
  * helicity sum, up to 64 eps (sqrt(kappa_0) + sqrt(kappa_j)) with eps the mode's
- * unit roundoff and kappa = |M|^2 / |M_h|^2 at the original point and at point j:
+ * unit roundoff (2^-48 in REX_DF64) and kappa = |M|^2 / |M_h|^2 at the original point and at point j:
  * the amplitudes that cancel into a small |M_h| are of the size of the whole sum's
  * and leave their rounding on it.
  * Enqueue only.  Errors: REX_EUNSUPPORTED, REX_EINVAL (as rex_reweight, null

@@ -204,8 +204,8 @@ void count(const char* name, int nghel, ES es, MSF msf, GC gc, QL ql, QLX qlx, b
 
 // The same routines in double-float: FP32 flops per call (split 0 accounting: both
 // antitop helicities per quark-line call).
-template <int NG, class EV, class MS, class GL, class ES, class MSF, class GC, class QL>
-void count_df(const char* name, int nghel, ES es, MSF msf, GC gc, QL ql) {
+template <int NG, class EV, class MS, class GL, class ES, class MSF, class GC, class QL, class QLX>
+void count_df(const char* name, int nghel, ES es, MSF msf, GC gc, QL ql, QLX qlx) {
   double p[NG + 2][4];
   DC eps[NG][4], pr[NG + 2][4];
   for (int i = 0; i < NG + 2; ++i)
@@ -234,10 +234,13 @@ void count_df(const char* name, int nghel, ES es, MSF msf, GC gc, QL ql) {
   DC::flops = 0;
   ql(ev, mm, J);
   const long long f_line = DC::flops;
+  DC::flops = 0;
+  qlx(ev, mm, J);
+  const long long f_line_x = DC::flops;
   std::printf("  \"%s_df64\": {\"nghel\": %d, \"event_setup\": %lld, \"mass_setup\": %lld, "
               "\"polarisations\": %lld, \"gluon_currents\": %lld, \"quark_line_amp\": %lld, "
-              "\"quark_line_acc\": 0, \"quark_line_amp_one_antitop\": 0},\n",
-              name, nghel, f_event, f_mass, f_pol, f_gluon, f_line);
+              "\"quark_line_acc\": 0, \"quark_line_amp_one_antitop\": %lld},\n",
+              name, nghel, f_event, f_mass, f_pol, f_gluon, f_line, f_line_x);
 }
 
 #define REX_COUNT_DF(NAME, NG)                                                                      \
@@ -246,7 +249,8 @@ void count_df(const char* name, int nghel, ES es, MSF msf, GC gc, QL ql) {
       [](const double* p, auto& ev) { NAME##_event_phase1(p, ev, 0, 1); NAME##_event_phase2(ev, 173.0 * 173.0, 0, 1); }, \
       [](auto& ev, double m, double w, auto& mm) { NAME##_mass_setup<DC, false>(ev, m, w, DC(0.0), mm, 0, 1); }, \
       [](auto& ev, auto& eps, auto& J) { NAME##_gluon_currents(ev, eps, J); },                       \
-      [](auto& ev, auto& mm, auto& J) { return NAME##_quark_line<DC, DC, false, DC>(ev, mm, J); })
+      [](auto& ev, auto& mm, auto& J) { return NAME##_quark_line<DC, DC, false, DC>(ev, mm, J); },      \
+      [](auto& ev, auto& mm, auto& J) { return NAME##_quark_line<DC, DC, false, DC>(ev, mm, J, 0, 1); })
 
 int main() {
   std::printf("{\n");
