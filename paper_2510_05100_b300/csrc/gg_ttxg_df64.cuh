@@ -5,8 +5,8 @@
 // FP32 instructions, and that straight-line code outgrows the instruction caches: the
 // kernel then waits on instruction fetch.  This form computes the same currents in the
 // same order, but as a loop over the gluon attached first to the top line (a = 0, 1, 2)
-// with the two choices of the second gluon inside it, reading its operands through
-// index tables:
+// with a loop over the two choices of the second gluon inside it, reading its operands
+// through index tables:
 //   psi_a  = P(q_a)  (J_a  v)
 //   psi_ab = P(q_ab) (J_b psi_a  + s1 J_ab v)
 //   x_f    =          J_c psi_ab + s2 J_bc psi_a + J_abc v,   A_f(h) = ubar_h(p_t) x_f
@@ -64,7 +64,9 @@ __device__ __forceinline__ df64 gg_ttxg_quark_line_df64(const gg_ttxg_event<df64
         slash_acc(df64(1), J[a], v, t);
         gg_ttxg_df_prop<WIDTH>(ev, mm, a, t, psia);
       }
-#pragma unroll
+      // Rolled as well: the unrolled pair of branches doubled the loop's code and left
+      // the kernel 17 % slower (instruction fetch again), for no saving in registers.
+#pragma unroll 1
       for (int bi = 0; bi < 2; ++bi) {
         const GgTtxgDfRow r = kGgTtxgDfRows[2 * a + bi];
         cx<df64> psiab[4];
@@ -86,7 +88,7 @@ __device__ __forceinline__ df64 gg_ttxg_quark_line_df64(const gg_ttxg_event<df64
       total = total + form(A);
       continue;
     }
-#pragma unroll
+#pragma unroll 1
     for (int ht = 0; ht < 2; ++ht) {
       float s = 0.f, c = 0.f;
 #pragma unroll
