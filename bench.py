@@ -67,8 +67,8 @@ TRAFFIC = {
     # ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum of profile_case at 2^19
     # events (FP64, scaled x2 by events) and 2^20 events (mixed); summaries of the
     # captures are under profiles/
-    ("gg_ttxg", "fp64"): {"bytes_per_launch": 2 * (91.569152e6 + 34.721536e6), "source_hash": "0b3f380506c85520"},
-    ("gg_ttxg", "mixed"): {"bytes_per_launch": 177.080832e6 + 105.504256e6, "source_hash": "0b3f380506c85520"},
+    ("gg_ttxg", "fp64"): {"bytes_per_launch": 2 * (91.167232e6 + 34.621440e6), "source_hash": "fb0176ae6762d5e1"},
+    ("gg_ttxg", "mixed"): {"bytes_per_launch": 176.708608e6 + 104.756992e6, "source_hash": "fb0176ae6762d5e1"},
 }
 
 

@@ -189,6 +189,16 @@ __device__ __forceinline__ cx<df64> ubar_dot(const cx<df64>* u, const cx<df64>* 
   return cx<df64>{df64_dot(ar, br), df64_dot(ai, bi)};
 }
 
+// Minkowski product of complex 4-vectors without conjugation (cdotm of the q q~ g
+// amplitudes): real and imaginary parts each one eight-product sum
+__device__ __forceinline__ cx<df64> cdotm(const cx<df64>* a, const cx<df64>* b) {
+  const df64 ar[8] = {a[0].re, -a[0].im, -a[1].re, a[1].im, -a[2].re, a[2].im, -a[3].re, a[3].im};
+  const df64 br[8] = {b[0].re, b[0].im, b[1].re, b[1].im, b[2].re, b[2].im, b[3].re, b[3].im};
+  const df64 ai[8] = {a[0].re, a[0].im, -a[1].re, -a[1].im, -a[2].re, -a[2].im, -a[3].re, -a[3].im};
+  const df64 bi[8] = {b[0].im, b[0].re, b[1].im, b[1].re, b[2].im, b[2].re, b[3].im, b[3].re};
+  return cx<df64>{df64_dot(ar, br), df64_dot(ai, bi)};
+}
+
 // vvv_acc of helas.cuh (s = +-1 as a sign):
 // out += s [ (X.Y)(PY - PX) - (X.(PX + 2 PY)) Y + (Y.(2 PX + PY)) X ]
 __device__ __forceinline__ void vvv_acc(df64 s, const df64* jx, const df64* px, const df64* jy, const df64* py,

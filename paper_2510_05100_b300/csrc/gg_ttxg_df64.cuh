@@ -86,20 +86,20 @@ __device__ __forceinline__ df64 gg_ttxg_quark_line_df64(const gg_ttxg_event<df64
     }
     if constexpr (!std::is_same<FORM, NoColourForm>::value) {
       total = total + form(A);
-      continue;
-    }
+    } else {
 #pragma unroll 1
-    for (int ht = 0; ht < 2; ++ht) {
-      float s = 0.f, c = 0.f;
+      for (int ht = 0; ht < 2; ++ht) {
+        float s = 0.f, c = 0.f;
 #pragma unroll
-      for (int f = 0; f < 6; ++f)
+        for (int f = 0; f < 6; ++f)
 #pragma unroll
-        for (int g = f; g < 6; ++g) {
-          const df64 w = df64(gg_ttxg_colour_dev[f][g] * (f == g ? 1 : 2));
-          df64_acc_term(s, c, w * A[ht][f].re, A[ht][g].re);
-          df64_acc_term(s, c, w * A[ht][f].im, A[ht][g].im);
-        }
-      total = total + df64_renorm(s, c);
+          for (int g = f; g < 6; ++g) {
+            const df64 w = df64(gg_ttxg_colour_dev[f][g] * (f == g ? 1 : 2));
+            df64_acc_term(s, c, w * A[ht][f].re, A[ht][g].re);
+            df64_acc_term(s, c, w * A[ht][f].im, A[ht][g].im);
+          }
+        total = total + df64_renorm(s, c);
+      }
     }
   }
   return total;

@@ -285,6 +285,21 @@ __device__ __forceinline__ void qqg_lane_scale(const QqgInvariants<R>& inv, QqgL
   }
 }
 
+// Re(a^dag C a) for the lane's five amplitudes, C = 3 x the colour matrix
+// (double-float has its own form: one sum of products)
+template <typename R>
+__device__ __forceinline__ R qqg_form(const cx<R> (&a)[5]) {
+  R form = R(0);
+#pragma unroll
+  for (int d = 0; d < 5; ++d) {
+    form += R(qqg_colour(d, d)) * (a[d].re * a[d].re + a[d].im * a[d].im);
+#pragma unroll
+    for (int d2 = d + 1; d2 < 5; ++d2)
+      form += R(2 * qqg_colour(d, d2)) * (a[d].re * a[d2].re + a[d].im * a[d2].im);
+  }
+  return form;
+}
+
 // The lane's colour-summed |amplitude|^2 summed over the 4 top-helicity pairs at top
 // mass mr, with dm2 = m0^2 - m^2 and mw = m Gamma (g, colour 1/3 and averaging not
 // applied).
@@ -328,15 +343,7 @@ __device__ __forceinline__ R qqg_slot(const QqgLane<R>& L, R mr, R dm2, R mw) {
       a[2] = f3 * ubar_dot(u3[l3], t3);
       a[3] = f4 * ubar_dot(u3[l3], s3);
       a[4] = f5 * cdotm(L.e, jout);
-      R form = R(0);
-#pragma unroll
-      for (int d = 0; d < 5; ++d) {
-        form += R(qqg_colour(d, d)) * (a[d].re * a[d].re + a[d].im * a[d].im);
-#pragma unroll
-        for (int d2 = d + 1; d2 < 5; ++d2)
-          form += R(2 * qqg_colour(d, d2)) * (a[d].re * a[d2].re + a[d].im * a[d2].im);
-      }
-      sum += form;
+      sum += qqg_form(a);
     }
   }
   return sum;
@@ -405,15 +412,7 @@ __device__ __forceinline__ R qqg_slot_split(const QqgLane<R>& L, R mr, R dm2, R 
         a[2] = a[2] - f3 * iwx;
         a[3] = a[3] + f4 * iwx;
       }
-      R form = R(0);
-#pragma unroll
-      for (int d = 0; d < 5; ++d) {
-        form += R(qqg_colour(d, d)) * (a[d].re * a[d].re + a[d].im * a[d].im);
-#pragma unroll
-        for (int d2 = d + 1; d2 < 5; ++d2)
-          form += R(2 * qqg_colour(d, d2)) * (a[d].re * a[d2].re + a[d].im * a[d2].im);
-      }
-      sum += form;
+      sum += qqg_form(a);
     }
   }
   return sum;

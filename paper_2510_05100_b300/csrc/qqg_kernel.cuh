@@ -30,6 +30,25 @@
 
 namespace rex {
 
+// qqg_form for double-float amplitudes: the fifteen colour-weighted products as one
+// sum, each added with one TwoSum, one renormalisation at the end
+__device__ __forceinline__ df64 qqg_form(const cx<df64> (&a)[5]) {
+  float s = 0.f, c = 0.f;
+#pragma unroll
+  for (int d = 0; d < 5; ++d)
+#pragma unroll
+    for (int d2 = d; d2 < 5; ++d2) {
+      const df64 w = df64(qqg_colour(d, d2) * (d == d2 ? 1 : 2));
+      df64_acc_term(s, c, w * a[d].re, a[d2].re);
+      df64_acc_term(s, c, w * a[d].im, a[d2].im);
+    }
+  return df64_renorm(s, c);
+}
+
+}  // namespace rex
+
+namespace rex {
+
 constexpr int QQG_BLOCK = 128;
 constexpr int QQG_LANES = 4;
 

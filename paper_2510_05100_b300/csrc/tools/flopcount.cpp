@@ -67,7 +67,8 @@ using AC = Cnt<1>;    // colour / helicity accumulation
 // Double-float (REX_DF64) cost of each operation in FP32 flops as df64.cuh performs
 // them (an FMA counts two, a division or square root one): sum 10, product 10,
 // fused multiply-add 18, quotient 25, square root 12, reciprocal square root 37, and
-// slash_acc 404, ubar_dot 246, vvv_acc 501 and vvvv_acc 381 (below); sign flips, comparisons and
+// slash_acc 404, ubar_dot 246, vvv_acc 501, vvvv_acc 381, cdotm 246 and qqg_form 753
+// (below); sign flips, comparisons and
 // FP64 -> double-float conversions cost none.
 struct DC {
   static long long flops;
@@ -143,6 +144,24 @@ inline void vvvv_acc(DC s, const DC* jx, const DC* jy, const DC* jz, DC* out) {
 #include "../generated/qcd_amplitudes.cuh"
 #include "../qq_amplitude.cuh"
 #include "../qqg_amplitude.cuh"
+
+// df64.cuh's cdotm (two eight-product sums = 246) and qqg_kernel.cuh's qqg_form for
+// double-float values (30 colour-weighted products: 30 x (10 + 15) + one
+// renormalisation 3 = 753)
+inline rex::cx<DC> cdotm(const rex::cx<DC>* a, const rex::cx<DC>* b) {
+  const long long keep = DC::flops;
+  const rex::cx<DC> r = a[0] * b[0] - a[1] * b[1] - a[2] * b[2] - a[3] * b[3];
+  DC::flops = keep + 246;
+  return r;
+}
+inline DC qqg_form(const rex::cx<DC> (&a)[5]) {
+  double f = 0;
+  for (int d = 0; d < 5; ++d)
+    for (int d2 = d; d2 < 5; ++d2)
+      f += rex::qqg_colour(d, d2) * (d == d2 ? 1 : 2) * (a[d].re.v * a[d2].re.v + a[d].im.v * a[d2].im.v);
+  DC::flops += 753;
+  return DC(f);
+}
 
 using namespace rex;
 
